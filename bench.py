@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Benchmark of the state-vector hot path on GB300.
+
+Workload (default): 30-qubit random circuit on a 5x6 grid, depth 20, sqrt(X/Y/W)
+single-qubit gates and fSim(pi/2, pi/6) on four cycling edge patterns (845
+gates), complex64 state (8 GiB, far larger than the 129 MB L2), fused into
+blocks of at most 4 qubits.  One step = initialise |0..0>, apply every fused
+block, and reduce the squared norm in FP64 -- the whole hot path.
+
+metric: gate-apps/s = unfused gates applied per second (whole job).
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle (a
+plain complex128 C implementation) on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2111_06868_gb300 import circuits as C  # noqa: E402
+
+METRIC = "gate-apps/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return PEAKS_FALLBACK, "fallback"
+
+
+def workload(args, rank):
+    if args.workload == "n30":
+        circ = C.config_n30(seed=args.seed + rank)
+        desc = "n=30 5x6 grid depth-20 fSim(pi/2,pi/6) random circuit, 845 gates"
+    elif args.workload == "n33":
+        circ = C.config_n33(seed=args.seed + rank)
+        desc = "n=33 6x6-minus-3-corners depth-24 fSim random circuit, 1116 gates"
+    elif args.workload == "n12":
+        circ = C.config_small(seed=args.seed + rank)
+        desc = "n=12 3x4 grid depth-10 CZ random circuit, 163 gates"
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    return circ, desc
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def block_class(qs, m):
+    d = m.shape[0]
+    diag = not np.any(m[~np.eye(d, dtype=bool)])
+    return ("diag" if diag else "dense") + f"_k{len(qs)}"
+
+
+KERNEL_NAME = {"dense": "k_gather", "diag": "k_diag"}
+
+
+def cpu_baseline(circ, seconds: float = 12.0):
+    """The oracle as it stands, on all host cores, over the first gates of the
+    same circuit until ~`seconds` of CPU work; rate in unfused gate-apps/s."""
+    import oracle
+
+    cores = oracle.max_threads()
+    n = circ.n
+    psi = np.zeros(1 << n, np.complex128)
+    psi[0] = 1.0
+    done = 0
+    t0 = time.perf_counter()
+    for g in circ.gates:
+        oracle.apply_gate(psi, n, g.qubits, g.matrix)
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"first {done} of {len(circ.gates)} gates of the same n={n} circuit, complex128, "
+                      f"unfused, OpenMP over {cores} threads ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the same workload, each step a
+    bounded sample (the first gates of the circuit)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    circ, desc = workload(args, 0)
+    n = circ.n
+    cores = oracle.max_threads()
+    psi = np.zeros(1 << n, np.complex128)
+    psi[0] = 1.0
+    per_step = args.ref_gates
+    gates = circ.gates[:per_step]
+    for _ in range(args.warmup):
+        for g in gates:
+            oracle.apply_gate(psi, n, g.qubits, g.matrix)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for g in gates:
+            oracle.apply_gate(psi, n, g.qubits, g.matrix)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    sample = f"first {per_step} gates of the n={n} circuit per step, complex128, unfused, {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "gate-apps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "n": n, "state": "complex128 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hq", choices=["hq", "reference"])
+    ap.add_argument("--workload", default="n30", choices=["n30", "n33", "n12"])
+    ap.add_argument("--kmax", type=int, default=4)
+    ap.add_argument("--dtype", default="complex64", choices=["complex64", "complex128"])
+    ap.add_argument("--engine", default="auto")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--ref-gates", type=int, default=12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2111_06868_gb300 import build as hqbuild
+    from paper_2111_06868_gb300 import hq
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        hqbuild.build()
+    if dist:
+        dist.barrier()
+    hq.load()
+
+    circ, desc = workload(args, rank)
+    n, G = circ.n, len(circ.gates)
+    t_f = time.perf_counter()
+    blocks = hq.hq_fuse(n, circ.gates, args.kmax) if args.kmax > 0 else [(g.qubits, g.matrix) for g in circ.gates]
+    fuse_s = time.perf_counter() - t_f
+    B = len(blocks)
+    classes = [block_class(q, m) for q, m in blocks]
+    cdt = torch.complex64 if args.dtype == "complex64" else torch.complex128
+    S = 8 if cdt == torch.complex64 else 16
+    state = torch.empty(1 << n, dtype=cdt, device="cuda")
+    stream = torch.cuda.current_stream()
+    norm_term = [(1.0, ())]
+    engine = args.engine
+
+    def step(events=None):
+        hq.hq_state_init(state)
+        for i, b in enumerate(blocks):
+            if events is not None:
+                events[i].record(stream)
+            hq.hq_apply_blocks(state, [b], engine=engine)
+        if events is not None:
+            events[B].record(stream)
+        return hq.hq_expectation(state, norm_term)
+
+    for _ in range(args.warmup):
+        norm = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    per_step_events = [[torch.cuda.Event(enable_timing=True) for _ in range(B + 1)] for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0.record(stream)
+    for s in range(args.steps):
+        norm = step(per_step_events[s])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    if dist:
+        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    value = world * G * args.steps / elapsed
+
+    # per-class launch durations (CUDA events on the launching stream)
+    durs = {}
+    for ev in per_step_events:
+        for i in range(B):
+            durs.setdefault(classes[i], []).append(ev[i].elapsed_time(ev[i + 1]) / 1e3)
+    tot = {c: sum(v) for c, v in durs.items()}
+    dom = max(tot, key=tot.get)
+    avg = statistics.mean(durs[dom])
+    bytes_per_launch = 2 * (1 << n) * S
+    peaks, peak_kind = load_peaks()
+    achieved = bytes_per_launch / avg / 1e9
+    per_class = {c: {"launches_per_step": len(v) // args.steps, "avg_ms": 1e3 * statistics.mean(v),
+                     "GBps": bytes_per_launch / statistics.mean(v) / 1e9, "share": tot[c] / sum(tot.values())}
+                 for c, v in durs.items()}
+
+    # end to end through the public API: pinned host state in, norm out
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.zeros(1 << n, dtype=cdt).pin_memory()
+        host_in[0] = 1
+        out = torch.zeros(1, dtype=torch.float64).pin_memory()
+        for _ in range(1):
+            state.copy_(host_in, non_blocking=True)
+            hq.hq_apply_blocks(state, blocks, engine=engine)
+            out[0] = hq.hq_expectation(state, norm_term)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2e_steps = max(1, min(args.steps, 3))
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            state.copy_(host_in, non_blocking=True)
+            hq.hq_apply_blocks(state, blocks, engine=engine)
+            out[0] = hq.hq_expectation(state, norm_term)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        et = e0.elapsed_time(e1) / 1e3
+        if dist:
+            tt = torch.tensor([et], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            et = float(tt.item())
+        e2e = {"value": world * G * e2e_steps / et, "unit": METRIC, "h2d_bytes_per_step": (1 << n) * S,
+               "d2h_bytes_per_step": 8, "note": "pinned host state copied in, FP64 norm read back, every step"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(circ)
+
+    if rank == 0:
+        eff_gbs = B * bytes_per_launch * args.steps / (elapsed / world) / 1e9
+        rec = {
+            "metric": METRIC, "value": value, "unit": "gate-apps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if S == 8 else "f64", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "gates": G, "fused_blocks": B, "k_max": args.kmax,
+                       "state": args.dtype, "engine": engine, "l2": "state (8 GiB+) larger than L2; no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "effective_GBps": eff_gbs, "roofline_frac_effective": eff_gbs / peaks["hbm_gbs"],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": f"{KERNEL_NAME[dom.split('_')[0]]} ({dom})", "peak_source": peak_kind,
+                         "bytes_per_launch": bytes_per_launch},
+            "per_class": per_class,
+            "norm2": norm, "fuse_s": fuse_s,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": args.steps * (B + 3),
+        }
+        print(json.dumps(rec))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * hq.h -- C ABI of libhq.so, the GB300 (sm_103a) state-vector hot path.
+ *
+ * What the library computes (HybridQ, arXiv 2111.06868):
+ *   Sec. 4.2 "State Vector": the evolution engine multiplies each k-qubit gate
+ *   (a dense 2^k x 2^k complex matrix, the MatrixGate of Sec. 2) into the
+ *   2^n-amplitude state, after Sec. 3.1's compress() has fused neighbouring
+ *   gates into blocks of at most max_n_qubits qubits.
+ *
+ * Conventions (all entry points):
+ *   - State: 2^n contiguous interleaved complex amplitudes in DEVICE memory,
+ *     complex64 (float re, float im) or complex128 (double re, double im),
+ *     16-byte aligned, owned by the caller.  Amplitude index x is the C-order
+ *     index of the (2,)*n tensor: qubit q is bit (n-1-q) of x (Sec. 2.2's
+ *     Grover printout fixes this order).
+ *   - Gate matrix: HOST memory, 2^k x 2^k complex128, row-major, interleaved
+ *     (re, im).  Local basis index r = sum_j r_j 2^(k-1-j) with r_j the bit
+ *     of qubits[j]: qubits[0] is the most significant (the Kronecker order of
+ *     the qubit list, as for MatrixGate(M, qubits)).  The library copies what
+ *     it needs before returning; the caller may free it right after.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Device work is enqueued asynchronously on it unless
+ *     an entry point says it synchronises.
+ *   - Errors: every entry point returns hq_status; 0 is success, negative
+ *     values are errors.  Arguments are validated on the host before any work
+ *     is enqueued; on an argument error nothing is enqueued.  HQ_ERR_CUDA
+ *     means a CUDA runtime call failed (text from hq_last_error()).  No C++
+ *     exception crosses the boundary.
+ *   - Threading: entry points may be called from several host threads; the
+ *     per-device library state is set up once under a lock.
+ */
+#ifndef HQ_H
+#define HQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HQ_MAX_K 6      /* widest gate / fused block */
+#define HQ_MAX_N 34     /* widest state: 2^34 complex64 = 128 GiB */
+#define HQ_MAX_PAULI 8  /* factors per Pauli-string term */
+
+typedef int hq_status;
+#define HQ_OK 0
+#define HQ_ERR_NULL (-1)         /* a required pointer is NULL */
+#define HQ_ERR_QUBIT_RANGE (-2)  /* qubit index outside [0, n) */
+#define HQ_ERR_DUP_QUBIT (-3)    /* a qubit repeated within one gate / term */
+#define HQ_ERR_K_TOO_LARGE (-4)  /* k < 1 or k > HQ_MAX_K, or k > n */
+#define HQ_ERR_N_TOO_LARGE (-5)  /* n < 1 or n > HQ_MAX_N */
+#define HQ_ERR_DTYPE (-6)        /* unknown hq_dtype, or dtype not supported by the engine */
+#define HQ_ERR_ALLOC (-7)        /* device scratch allocation failed */
+#define HQ_ERR_CUDA (-8)         /* a CUDA runtime call failed */
+#define HQ_ERR_TIMEOUT (-9)      /* a bounded device-side wait ran out */
+#define HQ_ERR_TOKEN (-10)       /* initial-state token not in {0,1,+,-} */
+#define HQ_ERR_CAPACITY (-11)    /* an output buffer is too small */
+#define HQ_ERR_ARG (-12)         /* any other invalid argument */
+#define HQ_ERR_ALIGN (-13)       /* device pointer not 16-byte aligned */
+
+typedef enum { HQ_C64 = 0, HQ_C128 = 1 } hq_dtype;
+
+/* A gate / fused block: k qubits and a host matrix (see conventions). */
+typedef struct {
+    int k;
+    int qubits[HQ_MAX_K];
+    const double *matrix;
+} hq_gate;
+
+/* One operation of a parametrised circuit (hq_adjoint_grad). */
+#define HQ_OP_MATRIX 0 /* fixed gate: k, qubits, matrix as in hq_gate */
+#define HQ_OP_ROT 1    /* exp(-i theta P / 2) on qubits[0], P = axis, theta = params[param] */
+typedef struct {
+    int kind;
+    int k;
+    int qubits[HQ_MAX_K];
+    const double *matrix;
+    int axis; /* 'X', 'Y' or 'Z' (HQ_OP_ROT) */
+    int param; /* parameter index (HQ_OP_ROT) */
+} hq_op;
+
+/* One Pauli-string term coeff * prod_j ops[j]_{qubits[j]}; len = 0 is the identity. */
+typedef struct {
+    double coeff;
+    int len;
+    int qubits[HQ_MAX_PAULI];
+    char ops[HQ_MAX_PAULI]; /* 'X', 'Y' or 'Z' */
+} hq_pauli_term;
+
+/* Kernel choice for hq_apply_blocks. */
+#define HQ_ENGINE_AUTO 0      /* cheapest exact path: diagonal / gather / CUDA-core block */
+#define HQ_ENGINE_CUDA_CORE 1 /* FP32/FP64 CUDA-core kernels only */
+#define HQ_ENGINE_TC_F16 2    /* k >= 5 blocks on tcgen05 tensor cores, FP16 hi+lo split (complex64) */
+#define HQ_ENGINE_TC_BF16 3   /* same, BF16 hi+lo split (complex64) */
+typedef struct {
+    int engine;  /* HQ_ENGINE_* */
+    int tc_min_k; /* blocks with k >= tc_min_k use the tensor-core engine (default 5) */
+} hq_config;
+
+/* Human-readable name of a status code (static string). */
+const char *hq_status_string(hq_status s);
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *hq_last_error(void);
+/* Library version string. */
+const char *hq_version(void);
+
+/*
+ * hq_state_init -- Sec. 4.1 ("Initial and Final State Specification"):
+ * write the product state selected by `tokens` (n chars, each '0', '1', '+'
+ * or '-'; qubit q takes tokens[q]) into `state`; tokens == NULL gives |0..0>.
+ * Device write of 2^n amplitudes on `stream`.
+ * Errors: HQ_ERR_NULL (state), HQ_ERR_N_TOO_LARGE, HQ_ERR_DTYPE, HQ_ERR_TOKEN,
+ * HQ_ERR_ALIGN, HQ_ERR_CUDA.
+ */
+hq_status hq_state_init(void *state, int n, hq_dtype dt, const char *tokens, void *stream);
+
+/*
+ * hq_fuse -- Sec. 3.1 compress(circuit, max_n_qubits): greedily merge the G
+ * gates (host) into blocks of at most k_max qubits (1 <= k_max <= HQ_MAX_K).
+ * A gate joins the latest earlier block that shares a qubit with it when the
+ * union fits; otherwise the earliest later block (all of them disjoint from
+ * the gate, so the move commutes) whose union fits; otherwise it opens a new
+ * block.  Each block's qubits are sorted ascending and its matrix is the
+ * product of its members (later members on the left), embedded in that order,
+ * computed in double on the host.
+ *   blocks:     out, capacity *B on entry; *B = number of blocks on return.
+ *   pool:       out, host doubles receiving the block matrices (blocks[i].matrix
+ *               points into it); pool_len = its capacity in doubles.  Worst case
+ *               is G * 2 * 4^k_max.
+ *   gate_block: optional out (G ints): the block index of every gate.
+ * Host only; no device work.  Errors: HQ_ERR_NULL, HQ_ERR_ARG (k_max, G < 0),
+ * HQ_ERR_K_TOO_LARGE (a gate wider than k_max), HQ_ERR_QUBIT_RANGE,
+ * HQ_ERR_DUP_QUBIT, HQ_ERR_CAPACITY (blocks or pool too small).
+ */
+hq_status hq_fuse(int n, const hq_gate *gates, int G, int k_max, hq_gate *blocks, int *B, double *pool,
+                  int64_t pool_len, int *gate_block);
+
+/*
+ * hq_apply_gate -- Sec. 4.2: state <- (matrix on qubits[0..k-1]) state, for
+ * every group of 2^k amplitudes that differ only in the target bits.  Uses the
+ * diagonal kernel when every off-diagonal entry is exactly zero, the gather
+ * kernel for k <= 4 and the CUDA-core block kernel for k = 5, 6.
+ * Errors: HQ_ERR_NULL, HQ_ERR_N_TOO_LARGE, HQ_ERR_K_TOO_LARGE,
+ * HQ_ERR_QUBIT_RANGE, HQ_ERR_DUP_QUBIT, HQ_ERR_DTYPE, HQ_ERR_ALIGN,
+ * HQ_ERR_ALLOC, HQ_ERR_CUDA.
+ */
+hq_status hq_apply_gate(void *state, int n, hq_dtype dt, const int *qubits, int k, const double *matrix,
+                        void *stream);
+
+/*
+ * hq_apply_blocks -- apply G gates / fused blocks in order (the evolution
+ * loop of Sec. 4.2), choosing a kernel per block as configured (cfg NULL =
+ * HQ_ENGINE_AUTO).  Tensor-core engines apply only to complex64 states.
+ * Errors: as hq_apply_gate, plus HQ_ERR_ARG (G < 0 or unknown engine).
+ */
+hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates, int G, const hq_config *cfg,
+                          void *stream);
+
+/*
+ * hq_expectation -- <psi|H|psi> = sum_t coeff_t <psi|P_t|psi> for a Pauli sum
+ * (T terms), accumulated in double; a term of len 0 gives the squared norm.
+ * Result written to *out_host.  SYNCHRONISES `stream`.  Uses device scratch
+ * (per-block partial sums, a few hundred KB) from the stream-ordered
+ * allocator, released before returning.
+ * Errors: HQ_ERR_NULL, HQ_ERR_N_TOO_LARGE, HQ_ERR_DTYPE, HQ_ERR_QUBIT_RANGE,
+ * HQ_ERR_DUP_QUBIT, HQ_ERR_ARG (len out of [0, HQ_MAX_PAULI], bad op char,
+ * T < 0), HQ_ERR_ALIGN, HQ_ERR_ALLOC, HQ_ERR_CUDA.
+ */
+hq_status hq_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,
+                         double *out_host, void *stream);
+
+/*
+ * hq_adjoint_workspace_bytes -- device workspace hq_adjoint_grad needs for
+ * `batch` parameter sets of an n-qubit, G-operation, P-parameter circuit
+ * with `checkpoints` stored forward states per parameter set (0 = none).
+ */
+size_t hq_adjoint_workspace_bytes(int n, hq_dtype dt, int G, int P, int batch, int checkpoints);
+
+/*
+ * hq_adjoint_grad -- energy E_b = <psi_b|H|psi_b>, psi_b = U(theta_b)|tokens>,
+ * and its gradient dE_b/dtheta_b[p] for every parameter, for `batch`
+ * parameter sets (theta_host: batch x P doubles, row-major).  Not in the
+ * paper: the adjoint reverse sweep (Jones & Gacon, arXiv 2009.02823) with two
+ * state vectors per parameter set.  The reverse sweep recomputes earlier
+ * states by applying U^+; with checkpoints > 0 it also stores that many
+ * evenly spaced forward states and restores them on the way back.
+ *   workspace: caller-owned device memory of at least
+ *              hq_adjoint_workspace_bytes(...) bytes (ws_bytes).
+ *   energies_host: out, batch doubles.  grads_host: out, batch x P doubles.
+ * SYNCHRONISES `stream`.  Errors: as hq_apply_gate and hq_expectation, plus
+ * HQ_ERR_ARG (kind/axis/param out of range, batch < 1), HQ_ERR_CAPACITY
+ * (ws_bytes too small).
+ */
+hq_status hq_adjoint_grad(int n, hq_dtype dt, const hq_op *ops, int G, int P, const double *theta_host,
+                          int batch, const hq_pauli_term *H, int T, const char *tokens, int checkpoints,
+                          void *workspace, size_t ws_bytes, double *energies_host, double *grads_host,
+                          void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HQ_H */

@@ -1,0 +1,166 @@
+// hq_api.cu -- the extern "C" entry points of libhq.so (declared in include/hq.h):
+// argument validation on the host, then kernel dispatch on the caller's stream.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "hq_internal.cuh"
+
+namespace hq {
+
+static thread_local std::string t_last_error;
+
+void set_last_error(const char *what, cudaError_t e)
+{
+    t_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+hq_status cuda_status(const char *what, cudaError_t e)
+{
+    if (e == cudaSuccess) return HQ_OK;
+    set_last_error(what, e);
+    return HQ_ERR_CUDA;
+}
+
+int sm_count()
+{
+    static std::mutex mu;
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+hq_status check_qubits(int n, int k, const int *qubits, int kmax)
+{
+    if (!qubits) return HQ_ERR_NULL;
+    if (k < 1 || k > kmax || k > n) return HQ_ERR_K_TOO_LARGE;
+    for (int j = 0; j < k; ++j) {
+        if (qubits[j] < 0 || qubits[j] >= n) return HQ_ERR_QUBIT_RANGE;
+        for (int i = 0; i < j; ++i)
+            if (qubits[i] == qubits[j]) return HQ_ERR_DUP_QUBIT;
+    }
+    return HQ_OK;
+}
+
+static hq_status check_state(const void *state, int n, hq_dtype dt)
+{
+    if (!state) return HQ_ERR_NULL;
+    if (n < 1 || n > HQ_MAX_N) return HQ_ERR_N_TOO_LARGE;
+    if (dt != HQ_C64 && dt != HQ_C128) return HQ_ERR_DTYPE;
+    if (reinterpret_cast<uintptr_t>(state) & 15) return HQ_ERR_ALIGN;
+    return HQ_OK;
+}
+
+hq_status check_terms(int n, const hq_pauli_term *terms, int T)
+{
+    if (T < 0) return HQ_ERR_ARG;
+    if (T > 0 && !terms) return HQ_ERR_NULL;
+    for (int t = 0; t < T; ++t) {
+        if (terms[t].len < 0 || terms[t].len > HQ_MAX_PAULI) return HQ_ERR_ARG;
+        for (int j = 0; j < terms[t].len; ++j) {
+            const char op = terms[t].ops[j];
+            if (op != 'X' && op != 'Y' && op != 'Z') return HQ_ERR_ARG;
+            if (terms[t].qubits[j] < 0 || terms[t].qubits[j] >= n) return HQ_ERR_QUBIT_RANGE;
+            for (int i = 0; i < j; ++i)
+                if (terms[t].qubits[i] == terms[t].qubits[j]) return HQ_ERR_DUP_QUBIT;
+        }
+    }
+    return HQ_OK;
+}
+
+}  // namespace hq
+
+using namespace hq;
+
+extern "C" {
+
+const char *hq_status_string(hq_status s)
+{
+    switch (s) {
+    case HQ_OK: return "ok";
+    case HQ_ERR_NULL: return "null pointer argument";
+    case HQ_ERR_QUBIT_RANGE: return "qubit index out of range";
+    case HQ_ERR_DUP_QUBIT: return "duplicate qubit";
+    case HQ_ERR_K_TOO_LARGE: return "gate width k out of range";
+    case HQ_ERR_N_TOO_LARGE: return "qubit count n out of range";
+    case HQ_ERR_DTYPE: return "unsupported dtype";
+    case HQ_ERR_ALLOC: return "device allocation failed";
+    case HQ_ERR_CUDA: return "CUDA runtime error";
+    case HQ_ERR_TIMEOUT: return "device-side wait timed out";
+    case HQ_ERR_TOKEN: return "invalid initial-state token";
+    case HQ_ERR_CAPACITY: return "output buffer too small";
+    case HQ_ERR_ARG: return "invalid argument";
+    case HQ_ERR_ALIGN: return "device pointer not 16-byte aligned";
+    }
+    return "unknown status";
+}
+
+const char *hq_last_error(void) { return t_last_error.c_str(); }
+
+const char *hq_version(void) { return "hq-gb300 0.1 (sm_103a)"; }
+
+hq_status hq_state_init(void *state, int n, hq_dtype dt, const char *tokens, void *stream)
+{
+    hq_status st = check_state(state, n, dt);
+    if (st != HQ_OK) return st;
+    if (tokens)
+        for (int q = 0; q < n; ++q) {
+            const char t = tokens[q];
+            if (t != '0' && t != '1' && t != '+' && t != '-') return HQ_ERR_TOKEN;
+        }
+    return launch_init(state, n, dt, tokens, 1, (cudaStream_t)stream);
+}
+
+hq_status hq_apply_gate(void *state, int n, hq_dtype dt, const int *qubits, int k, const double *matrix, void *stream)
+{
+    hq_status st = check_state(state, n, dt);
+    if (st != HQ_OK) return st;
+    if ((st = check_qubits(n, k, qubits, HQ_MAX_K)) != HQ_OK) return st;
+    if (!matrix) return HQ_ERR_NULL;
+    return launch_gate(state, n, dt, k, qubits, matrix, 1, HQ_ENGINE_AUTO, (cudaStream_t)stream);
+}
+
+hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates, int G, const hq_config *cfg,
+                          void *stream)
+{
+    hq_status st = check_state(state, n, dt);
+    if (st != HQ_OK) return st;
+    if (G < 0) return HQ_ERR_ARG;
+    if (G > 0 && !gates) return HQ_ERR_NULL;
+    const int engine = cfg ? cfg->engine : HQ_ENGINE_AUTO;
+    const int tc_min_k = (cfg && cfg->tc_min_k > 0) ? cfg->tc_min_k : 5;
+    if (engine < HQ_ENGINE_AUTO || engine > HQ_ENGINE_TC_BF16) return HQ_ERR_ARG;
+    if ((engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16) && dt != HQ_C64) return HQ_ERR_DTYPE;
+    for (int g = 0; g < G; ++g) {
+        if ((st = check_qubits(n, gates[g].k, gates[g].qubits, HQ_MAX_K)) != HQ_OK) return st;
+        if (!gates[g].matrix) return HQ_ERR_NULL;
+    }
+    for (int g = 0; g < G; ++g) {
+        int eng = engine;
+        if ((eng == HQ_ENGINE_TC_F16 || eng == HQ_ENGINE_TC_BF16) && gates[g].k < tc_min_k) eng = HQ_ENGINE_AUTO;
+        st = launch_gate(state, n, dt, gates[g].k, gates[g].qubits, gates[g].matrix, 1, eng, (cudaStream_t)stream);
+        if (st != HQ_OK) return st;
+    }
+    return HQ_OK;
+}
+
+hq_status hq_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T, double *out_host,
+                         void *stream)
+{
+    hq_status st = check_state(state, n, dt);
+    if (st != HQ_OK) return st;
+    if (!out_host) return HQ_ERR_NULL;
+    if ((st = check_terms(n, terms, T)) != HQ_OK) return st;
+    return launch_expectation(state, n, dt, terms, T, out_host, (cudaStream_t)stream);
+}
+
+}  // extern "C"

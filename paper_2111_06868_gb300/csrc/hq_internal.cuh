@@ -1,0 +1,176 @@
+// hq_internal.cuh -- shared declarations of libhq's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hq.h"
+
+namespace hq {
+
+// ----------------------------------------------------------------------------
+// error plumbing
+// ----------------------------------------------------------------------------
+void set_last_error(const char *what, cudaError_t e);
+hq_status cuda_status(const char *what, cudaError_t e);  // HQ_OK or HQ_ERR_CUDA
+#define HQ_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e__ = (call);                                  \
+        if (e__ != cudaSuccess) return ::hq::cuda_status(#call, e__); \
+    } while (0)
+
+int sm_count();  // SMs of the current device (cached per device)
+// resident CTAs per SM of `fn` (sets the dynamic shared-memory attribute when
+// smem > 48 KB), and a grid of at most that many CTAs per SM
+int occupancy(const void *fn, int threads, size_t smem);
+int grid_for(const void *fn, int threads, size_t smem, int64_t work_items);
+
+// sum of v over the CTA (blockDim.x a multiple of 32, <= 1024); result in thread 0
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+// ----------------------------------------------------------------------------
+// complex helpers
+// ----------------------------------------------------------------------------
+template <typename R> struct C2;
+template <> struct C2<float> { using type = float2; };
+template <> struct C2<double> { using type = double2; };
+
+template <typename T2>
+__device__ __forceinline__ void cmac(T2 &acc, const T2 m, const T2 v)
+{
+    acc.x = fma(m.x, v.x, acc.x);
+    acc.x = fma(-m.y, v.y, acc.x);
+    acc.y = fma(m.x, v.y, acc.y);
+    acc.y = fma(m.y, v.x, acc.y);
+}
+
+template <typename T2>
+__device__ __forceinline__ T2 cmul(const T2 a, const T2 b)
+{
+    T2 r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// ----------------------------------------------------------------------------
+// Tile geometry of one gate application (see k_apply.cu)
+//
+// Bits of the flat amplitude index are numbered from the LSB.  For a gate on
+// bit positions b_j, the tile bit set T holds every target bit plus the lowest
+// (L - k) non-target bits, |T| = L.  The lowest c bits are all in T, so a tile
+// is 2^(L-c) contiguous runs of 2^c amplitudes; every bit of T above c is a
+// target ("high target").  Tiles are enumerated by the remaining (non-T) bits.
+// Tile-local index i has bit m <-> bit T[m] of the flat index.
+// ----------------------------------------------------------------------------
+struct TileGeom {
+    int n, L, c, k;
+    int n_hi;                  // targets >= c
+    int hi_bits[HQ_MAX_K];     // their flat bit positions, ascending
+    int n_tl;                  // = k
+    int tl_bits[HQ_MAX_K];     // tile-local positions of all targets, ascending
+    int64_t tiles_per_state;   // 2^(n - L)
+    int64_t total_tiles;       // tiles_per_state * nstates
+    int64_t state_stride;      // amplitudes between consecutive states (= 2^n)
+    int64_t runoff[1 << HQ_MAX_K];  // flat offset of run j (j < 2^(L-c))
+    int toff[1 << HQ_MAX_K];        // tile-local offset of local index r
+};
+
+// Builds the geometry for targets `qubits` (k of them) on n-qubit states.
+void make_geom(TileGeom &g, int n, int k, const int *qubits, int L, int64_t nstates);
+
+// ----------------------------------------------------------------------------
+// shared-memory swizzle: element i of a tile lives at swz(i); XOR of the
+// position inside a 128-byte row with the row number.
+// ----------------------------------------------------------------------------
+template <typename R> __device__ __forceinline__ int swz(int i);
+template <> __device__ __forceinline__ int swz<float>(int i) { return i ^ ((i >> 4) & 15); }
+template <> __device__ __forceinline__ int swz<double>(int i) { return i ^ ((i >> 3) & 7); }
+
+// flat offset of the first amplitude of tile t (state index folded in)
+__device__ __forceinline__ int64_t tile_base(const TileGeom &g, int64_t t)
+{
+    const int64_t s = t >> (g.n - g.L);
+    const int64_t o = t & (g.tiles_per_state - 1);
+    int64_t x = o << g.c;
+    for (int h = 0; h < g.n_hi; ++h) {
+        const int hb = g.hi_bits[h];
+        x = ((x >> hb) << (hb + 1)) | (x & ((int64_t(1) << hb) - 1));
+    }
+    return s * g.state_stride + x;
+}
+
+// tile-local index of local basis 0 of group grp
+template <int K>
+__device__ __forceinline__ int group_base(const TileGeom &g, int grp)
+{
+    int ib = grp;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int tb = g.tl_bits[j];
+        ib = ((ib >> tb) << (tb + 1)) | (ib & ((1 << tb) - 1));
+    }
+    return ib;
+}
+
+// global <-> shared copies of one tile (16-byte accesses)
+__device__ __forceinline__ void tile_load(const TileGeom &g, const float2 *__restrict__ base, float2 *tile)
+{
+    const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
+    for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
+        const float4 v = *reinterpret_cast<const float4 *>(base + g.runoff[i >> g.c] + (i & cmask));
+        const int f = (i >> 4) & 15;
+        const float4 w = (f & 1) ? make_float4(v.z, v.w, v.x, v.y) : v;
+        *reinterpret_cast<float4 *>(&tile[(i ^ f) & ~1]) = w;
+    }
+}
+__device__ __forceinline__ void tile_store(const TileGeom &g, float2 *__restrict__ base, const float2 *tile)
+{
+    const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
+    for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
+        const int f = (i >> 4) & 15;
+        const float4 w = *reinterpret_cast<const float4 *>(&tile[(i ^ f) & ~1]);
+        const float4 v = (f & 1) ? make_float4(w.z, w.w, w.x, w.y) : w;
+        *reinterpret_cast<float4 *>(base + g.runoff[i >> g.c] + (i & cmask)) = v;
+    }
+}
+__device__ __forceinline__ void tile_load(const TileGeom &g, const double2 *__restrict__ base, double2 *tile)
+{
+    const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
+    for (int i = threadIdx.x; i < TS; i += blockDim.x) tile[swz<double>(i)] = base[g.runoff[i >> g.c] + (i & cmask)];
+}
+__device__ __forceinline__ void tile_store(const TileGeom &g, double2 *__restrict__ base, const double2 *tile)
+{
+    const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
+    for (int i = threadIdx.x; i < TS; i += blockDim.x) base[g.runoff[i >> g.c] + (i & cmask)] = tile[swz<double>(i)];
+}
+
+// kernels launched by the API layer (k_apply.cu)
+hq_status launch_init(void *state, int n, hq_dtype dt, const char *tokens, int64_t nstates, cudaStream_t s);
+hq_status launch_gate(void *state, int n, hq_dtype dt, int k, const int *qubits, const double *matrix,
+                      int64_t nstates, int engine, cudaStream_t s);
+bool is_diagonal(int k, const double *matrix);
+
+// expectation (k_reduce.cu)
+hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,
+                             double *out_host, cudaStream_t s);
+
+// tensor-core block engine (k_tc.cu); complex64 only, k in {5, 6}
+hq_status launch_tc_block(void *state, int n, int k, const int *qubits, const double *matrix, int64_t nstates,
+                          int split_bf16, cudaStream_t s);
+
+// validation helpers (hq_api.cu)
+hq_status check_qubits(int n, int k, const int *qubits, int kmax);
+
+}  // namespace hq

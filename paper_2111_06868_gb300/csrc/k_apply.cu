@@ -1,0 +1,447 @@
+// k_apply.cu -- state initialisation and the per-gate / per-block kernels.
+//
+// HybridQ (arXiv 2111.06868) Sec. 4.2 applies a k-qubit gate as a matrix-vector
+// product on every group of 2^k amplitudes that differ only in the target bits.
+// On GB300 that is one HBM pass over the state per gate; the kernels here keep
+// it one pass for any target positions:
+//
+//   * k_gather<R, K> (K <= 4): a CTA stages one tile of 2^L amplitudes (all
+//     target bits plus the lowest non-target bits, see TileGeom) in shared
+//     memory with coalesced 16-byte loads of >= 2^(L-K)-long contiguous runs,
+//     multiplies every group in place with the matrix held in the kernel's
+//     parameter space (uniform constant-bank operands of the FMAs), and streams
+//     the tile back.  An XOR swizzle of the shared-memory index keeps both the
+//     linear copy and the strided group access free of bank conflicts.
+//   * k_diag<R, K>: diagonal gates (CZ, RZ, CPHASE and fused diagonal blocks)
+//     need no gather: out[x] = d[r(x)] * in[x], a pure stream.
+//   * k_block<R, K> (K = 5, 6): the same tile scheme for wide fused blocks on
+//     the CUDA cores (matrix in shared memory, 16 output rows per thread); the
+//     tensor-core engine for these widths is in k_tc.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "hq_internal.cuh"
+
+namespace hq {
+
+// ----------------------------------------------------------------------------
+// geometry
+// ----------------------------------------------------------------------------
+void make_geom(TileGeom &g, int n, int k, const int *qubits, int L, int64_t nstates)
+{
+    std::memset(&g, 0, sizeof(g));
+    g.n = n;
+    g.k = k;
+    g.L = L;
+    int b[HQ_MAX_K];
+    uint64_t tmask = 0;
+    for (int j = 0; j < k; ++j) {
+        b[j] = n - 1 - qubits[j];
+        tmask |= 1ull << b[j];
+    }
+    uint64_t T = tmask;
+    int need = L - k;
+    for (int p = 0; p < n && need > 0; ++p)
+        if (!((tmask >> p) & 1)) {
+            T |= 1ull << p;
+            --need;
+        }
+    int c = 0;
+    while (c < n && ((T >> c) & 1)) ++c;
+    g.c = c;
+    int Tl[64], m = 0, tlpos[64];
+    for (int p = 0; p < n; ++p)
+        if ((T >> p) & 1) {
+            tlpos[p] = m;
+            Tl[m++] = p;
+        }
+    // targets at or above c, ascending (all of T above c are targets)
+    g.n_hi = 0;
+    for (int i = c; i < L; ++i) g.hi_bits[g.n_hi++] = Tl[i];
+    g.n_tl = 0;
+    for (int i = 0; i < L; ++i)
+        if ((tmask >> Tl[i]) & 1) g.tl_bits[g.n_tl++] = i;
+    const int nruns = 1 << (L - c);
+    for (int j = 0; j < nruns; ++j) {
+        int64_t off = 0;
+        for (int q = 0; q < L - c; ++q)
+            if ((j >> q) & 1) off += int64_t(1) << Tl[c + q];
+        g.runoff[j] = off;
+    }
+    for (int r = 0; r < (1 << k); ++r) {
+        int off = 0;
+        for (int j = 0; j < k; ++j)
+            if ((r >> (k - 1 - j)) & 1) off += 1 << tlpos[b[j]];
+        g.toff[r] = off;
+    }
+    g.tiles_per_state = int64_t(1) << (n - L);
+    g.total_tiles = g.tiles_per_state * nstates;
+    g.state_stride = int64_t(1) << n;
+}
+
+bool is_diagonal(int k, const double *m)
+{
+    const int K = 1 << k;
+    for (int r = 0; r < K; ++r)
+        for (int c = 0; c < K; ++c)
+            if (r != c && (m[2 * (r * K + c)] != 0.0 || m[2 * (r * K + c) + 1] != 0.0)) return false;
+    return true;
+}
+
+// ----------------------------------------------------------------------------
+// launch-shape helpers
+// ----------------------------------------------------------------------------
+static std::mutex g_occ_mu;
+static std::map<std::pair<int, const void *>, int> g_occ;
+
+// resident CTAs per SM for `fn` with `threads` threads and `smem` dynamic bytes
+int occupancy(const void *fn, int threads, size_t smem)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto key = std::make_pair(dev * 1024 + int(smem >> 10), fn);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) nb = 1;
+    g_occ[key] = nb;
+    return nb;
+}
+
+int grid_for(const void *fn, int threads, size_t smem, int64_t work_items)
+{
+    int64_t cap = int64_t(sm_count()) * occupancy(fn, threads, smem);
+    return int(std::max<int64_t>(1, std::min<int64_t>(cap, work_items)));
+}
+
+// ----------------------------------------------------------------------------
+// gather kernel, K <= 4
+// ----------------------------------------------------------------------------
+template <typename R, int K> struct MatParam {
+    typename C2<R>::type a[1 << K][1 << K];
+};
+
+constexpr int kThreads = 256;
+
+// Rows of M one thread accumulates, and threads sharing one group.  K <= 2:
+// one thread owns a whole group and writes it back in place at once.  K = 3, 4:
+// a warp takes 32 groups and one 4-row chunk of M (so every lane reads the
+// same, compile-time-indexed M entries: constant-bank operands), holds its
+// accumulators across a barrier, then writes.
+template <int K> __host__ __device__ constexpr int gather_rows() { return K <= 2 ? (1 << K) : 4; }
+template <int K> __host__ __device__ constexpr int gather_tpg() { return (1 << K) / gather_rows<K>(); }
+// work items (group x chunk) per thread for a full tile of 2^Lmax amplitudes
+template <typename R, int K> __host__ __device__ constexpr int gather_items()
+{
+    return gather_tpg<K>() == 1 ? 1 : ((1 << ((sizeof(R) == 4 ? 12 : 11) - K)) * gather_tpg<K>()) / kThreads;
+}
+
+template <typename R, int K, int R0>
+__device__ __forceinline__ void gather_rows_acc(const MatParam<R, K> &m, const typename C2<R>::type *tile, int ib,
+                                                const TileGeom &g, typename C2<R>::type *acc)
+{
+    constexpr int NR = gather_rows<K>();
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) acc[rr].x = acc[rr].y = 0;
+#pragma unroll
+    for (int c = 0; c < (1 << K); ++c) {
+        const typename C2<R>::type v = tile[swz<R>(ib + g.toff[c])];
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) cmac(acc[rr], m.a[R0 + rr][c], v);
+    }
+}
+
+template <typename R, int K>
+__global__ void __launch_bounds__(kThreads) k_gather(const TileGeom g, const MatParam<R, K> m,
+                                                     typename C2<R>::type *__restrict__ state)
+{
+    using T2 = typename C2<R>::type;
+    constexpr int NR = gather_rows<K>(), TPG = gather_tpg<K>(), NI = gather_items<R, K>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw);
+    const int ngroups = (1 << g.L) >> K;
+    for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x) {
+        T2 *base = state + tile_base(g, t);
+        tile_load(g, base, tile);
+        __syncthreads();
+        if constexpr (TPG == 1) {
+            for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
+                const int ib = group_base<K>(g, grp);
+                T2 acc[NR];
+                gather_rows_acc<R, K, 0>(m, tile, ib, g, acc);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) tile[swz<R>(ib + g.toff[r])] = acc[r];
+            }
+            __syncthreads();
+        } else {
+            T2 acc[NI][NR];
+            int ibs[NI], chunk[NI];
+#pragma unroll
+            for (int it = 0; it < NI; ++it) {
+                const int w = it * kThreads + threadIdx.x;
+                const int wi = w >> 5;
+                chunk[it] = wi % TPG;
+                const int grp = (wi / TPG) * 32 + (w & 31);
+                ibs[it] = -1;
+                if (grp < ngroups) {
+                    ibs[it] = group_base<K>(g, grp);
+                    switch (chunk[it]) {
+                    case 0: gather_rows_acc<R, K, 0>(m, tile, ibs[it], g, acc[it]); break;
+                    case 1: gather_rows_acc<R, K, NR>(m, tile, ibs[it], g, acc[it]); break;
+                    case 2: gather_rows_acc<R, K, (2 * NR) % (1 << K)>(m, tile, ibs[it], g, acc[it]); break;
+                    default: gather_rows_acc<R, K, (3 * NR) % (1 << K)>(m, tile, ibs[it], g, acc[it]); break;
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int it = 0; it < NI; ++it)
+                if (ibs[it] >= 0)
+#pragma unroll
+                    for (int rr = 0; rr < NR; ++rr) tile[swz<R>(ibs[it] + g.toff[chunk[it] * NR + rr])] = acc[it][rr];
+            __syncthreads();
+        }
+        tile_store(g, base, tile);
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// wide blocks on CUDA cores, K = 5, 6 (matrix in shared memory)
+// ----------------------------------------------------------------------------
+constexpr int kRowsPerThread = 16;
+
+template <typename R, int K>
+__global__ void __launch_bounds__(kThreads) k_block(const TileGeom g, const typename C2<R>::type *__restrict__ mat,
+                                                    typename C2<R>::type *__restrict__ state)
+{
+    using T2 = typename C2<R>::type;
+    constexpr int D = 1 << K;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *msh = reinterpret_cast<T2 *>(smem_raw);
+    T2 *tile = msh + D * D;
+    for (int i = threadIdx.x; i < D * D; i += blockDim.x) msh[i] = mat[i];
+    const int ngroups = (1 << g.L) >> K;
+    const int nitems = ngroups * (D / kRowsPerThread);  // <= blockDim.x by construction
+    const int w = threadIdx.x;
+    const int grp = w % ngroups, r0 = (w / ngroups) * kRowsPerThread;
+    for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x) {
+        T2 *base = state + tile_base(g, t);
+        tile_load(g, base, tile);
+        __syncthreads();
+        T2 acc[kRowsPerThread];
+        int ib = 0;
+        if (w < nitems) {
+            ib = group_base<K>(g, grp);
+#pragma unroll
+            for (int rr = 0; rr < kRowsPerThread; ++rr) acc[rr].x = acc[rr].y = 0;
+#pragma unroll 4
+            for (int c = 0; c < D; ++c) {
+                const T2 v = tile[swz<R>(ib + g.toff[c])];
+#pragma unroll
+                for (int rr = 0; rr < kRowsPerThread; ++rr) cmac(acc[rr], msh[(r0 + rr) * D + c], v);
+            }
+        }
+        __syncthreads();
+        if (w < nitems) {
+#pragma unroll
+            for (int rr = 0; rr < kRowsPerThread; ++rr) tile[swz<R>(ib + g.toff[r0 + rr])] = acc[rr];
+        }
+        __syncthreads();
+        tile_store(g, base, tile);
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// diagonal gates
+// ----------------------------------------------------------------------------
+template <typename R, int K> struct DiagParam {
+    typename C2<R>::type d[1 << K];
+    int b[K];  // flat bit position of qubits[j]
+};
+
+template <typename R, int K>
+__global__ void __launch_bounds__(kThreads) k_diag(const DiagParam<R, K> p, typename C2<R>::type *__restrict__ state,
+                                                   int64_t total)
+{
+    using T2 = typename C2<R>::type;
+    __shared__ T2 d[1 << K];
+    for (int i = threadIdx.x; i < (1 << K); i += blockDim.x) d[i] = p.d[i];
+    __syncthreads();
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e * 16 < total * int64_t(sizeof(T2));
+         e += stride) {
+        if constexpr (sizeof(T2) == 8) {
+            float4 v = reinterpret_cast<float4 *>(state)[e];
+            const int64_t x = 2 * e;
+            int r0 = 0, r1 = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                r0 |= int((x >> p.b[j]) & 1) << (K - 1 - j);
+                r1 |= int(((x + 1) >> p.b[j]) & 1) << (K - 1 - j);
+            }
+            const float2 a = cmul(d[r0], make_float2(v.x, v.y));
+            const float2 b = cmul(d[r1], make_float2(v.z, v.w));
+            reinterpret_cast<float4 *>(state)[e] = make_float4(a.x, a.y, b.x, b.y);
+        } else {
+            const int64_t x = e;
+            int r = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) r |= int((x >> p.b[j]) & 1) << (K - 1 - j);
+            state[e] = cmul(d[r], state[e]);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// product-state initialisation (Sec. 4.1 tokens)
+//   amplitude(x) = [x & fixed_mask == fixed_val] * amp * (-1)^popc(x & minus_mask)
+// ----------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_init(typename C2<R>::type *__restrict__ state, int64_t total, int n,
+                                                   uint64_t fixed_mask, uint64_t fixed_val, uint64_t minus_mask,
+                                                   R amp)
+{
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    const uint64_t in_state = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    for (int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < total; x += stride) {
+        const uint64_t y = uint64_t(x) & in_state;
+        typename C2<R>::type v;
+        v.x = ((y & fixed_mask) == fixed_val) ? ((__popcll(y & minus_mask) & 1) ? -amp : amp) : R(0);
+        v.y = 0;
+        state[x] = v;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// host launchers
+// ----------------------------------------------------------------------------
+hq_status launch_init(void *state, int n, hq_dtype dt, const char *tokens, int64_t nstates, cudaStream_t s)
+{
+    uint64_t fmask = 0, fval = 0, mmask = 0;
+    int m = 0;
+    for (int q = 0; q < n; ++q) {
+        const char t = tokens ? tokens[q] : '0';
+        const uint64_t bit = 1ull << (n - 1 - q);
+        if (t == '0') fmask |= bit;
+        else if (t == '1') { fmask |= bit; fval |= bit; }
+        else if (t == '+') ++m;
+        else if (t == '-') { ++m; mmask |= bit; }
+        else return HQ_ERR_TOKEN;
+    }
+    const double amp = std::pow(2.0, -0.5 * m);
+    const int64_t total = nstates << n;
+    if (dt == HQ_C64) {
+        const void *fn = (const void *)k_init<float>;
+        const int grid = grid_for(fn, kThreads, 0, (total + kThreads - 1) / kThreads);
+        k_init<float><<<grid, kThreads, 0, s>>>((float2 *)state, total, n, fmask, fval, mmask, float(amp));
+    } else {
+        const void *fn = (const void *)k_init<double>;
+        const int grid = grid_for(fn, kThreads, 0, (total + kThreads - 1) / kThreads);
+        k_init<double><<<grid, kThreads, 0, s>>>((double2 *)state, total, n, fmask, fval, mmask, amp);
+    }
+    return cuda_status("k_init", cudaGetLastError());
+}
+
+template <typename R, int K>
+static hq_status run_diag(void *state, int n, const int *qubits, const double *mat, int64_t nstates, cudaStream_t s)
+{
+    DiagParam<R, K> p;
+    for (int r = 0; r < (1 << K); ++r) {
+        p.d[r].x = R(mat[2 * (r * (1 << K) + r)]);
+        p.d[r].y = R(mat[2 * (r * (1 << K) + r) + 1]);
+    }
+    for (int j = 0; j < K; ++j) p.b[j] = n - 1 - qubits[j];
+    const int64_t total = nstates << n;
+    const int64_t vec = total * int64_t(sizeof(typename C2<R>::type)) / 16;
+    const void *fn = (const void *)k_diag<R, K>;
+    const int grid = grid_for(fn, kThreads, 0, (vec + kThreads - 1) / kThreads);
+    k_diag<R, K><<<grid, kThreads, 0, s>>>(p, (typename C2<R>::type *)state, total);
+    return cuda_status("k_diag", cudaGetLastError());
+}
+
+template <typename R> static int tile_bits(int n) { return std::min(n, sizeof(R) == 4 ? 12 : 11); }
+
+template <typename R, int K>
+static hq_status run_gather(void *state, int n, const int *qubits, const double *mat, int64_t nstates, cudaStream_t s)
+{
+    TileGeom g;
+    make_geom(g, n, K, qubits, tile_bits<R>(n), nstates);
+    MatParam<R, K> m;
+    for (int r = 0; r < (1 << K); ++r)
+        for (int c = 0; c < (1 << K); ++c) {
+            m.a[r][c].x = R(mat[2 * (r * (1 << K) + c)]);
+            m.a[r][c].y = R(mat[2 * (r * (1 << K) + c) + 1]);
+        }
+    const size_t smem = size_t(sizeof(typename C2<R>::type)) << g.L;
+    const void *fn = (const void *)k_gather<R, K>;
+    const int grid = grid_for(fn, kThreads, smem, g.total_tiles);
+    k_gather<R, K><<<grid, kThreads, smem, s>>>(g, m, (typename C2<R>::type *)state);
+    return cuda_status("k_gather", cudaGetLastError());
+}
+
+template <typename R, int K>
+static hq_status run_block(void *state, int n, const int *qubits, const double *mat, int64_t nstates, cudaStream_t s)
+{
+    using T2 = typename C2<R>::type;
+    constexpr int D = 1 << K;
+    TileGeom g;
+    make_geom(g, n, K, qubits, std::min(n, 12), nstates);
+    std::vector<T2> hm(D * D);
+    for (int i = 0; i < D * D; ++i) {
+        hm[i].x = R(mat[2 * i]);
+        hm[i].y = R(mat[2 * i + 1]);
+    }
+    T2 *dm = nullptr;
+    if (cudaMallocAsync((void **)&dm, sizeof(T2) * D * D, s) != cudaSuccess) return HQ_ERR_ALLOC;
+    HQ_CUDA(cudaMemcpyAsync(dm, hm.data(), sizeof(T2) * D * D, cudaMemcpyHostToDevice, s));
+    const size_t smem = sizeof(T2) * (size_t(D * D) + (size_t(1) << g.L));
+    const void *fn = (const void *)k_block<R, K>;
+    const int grid = grid_for(fn, kThreads, smem, g.total_tiles);
+    k_block<R, K><<<grid, kThreads, smem, s>>>(g, dm, (T2 *)state);
+    hq_status st = cuda_status("k_block", cudaGetLastError());
+    cudaFreeAsync(dm, s);
+    return st;
+}
+
+template <typename R>
+static hq_status dispatch(void *state, int n, int k, const int *qubits, const double *mat, int64_t nstates,
+                          int engine, cudaStream_t s)
+{
+    if (is_diagonal(k, mat)) {
+        switch (k) {
+        case 1: return run_diag<R, 1>(state, n, qubits, mat, nstates, s);
+        case 2: return run_diag<R, 2>(state, n, qubits, mat, nstates, s);
+        case 3: return run_diag<R, 3>(state, n, qubits, mat, nstates, s);
+        case 4: return run_diag<R, 4>(state, n, qubits, mat, nstates, s);
+        case 5: return run_diag<R, 5>(state, n, qubits, mat, nstates, s);
+        case 6: return run_diag<R, 6>(state, n, qubits, mat, nstates, s);
+        }
+    }
+    switch (k) {
+    case 1: return run_gather<R, 1>(state, n, qubits, mat, nstates, s);
+    case 2: return run_gather<R, 2>(state, n, qubits, mat, nstates, s);
+    case 3: return run_gather<R, 3>(state, n, qubits, mat, nstates, s);
+    case 4: return run_gather<R, 4>(state, n, qubits, mat, nstates, s);
+    }
+    if (sizeof(R) == 4 && (engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16))
+        return launch_tc_block(state, n, k, qubits, mat, nstates, engine == HQ_ENGINE_TC_BF16, s);
+    if (k == 5) return run_block<R, 5>(state, n, qubits, mat, nstates, s);
+    return run_block<R, 6>(state, n, qubits, mat, nstates, s);
+}
+
+hq_status launch_gate(void *state, int n, hq_dtype dt, int k, const int *qubits, const double *matrix,
+                      int64_t nstates, int engine, cudaStream_t s)
+{
+    if (dt == HQ_C64) return dispatch<float>(state, n, k, qubits, matrix, nstates, engine, s);
+    return dispatch<double>(state, n, k, qubits, matrix, nstates, engine, s);
+}
+
+}  // namespace hq

@@ -1,0 +1,217 @@
+// k_reduce.cu -- <psi|H|psi> for a Pauli sum, accumulated in FP64.
+//
+// A Pauli string P = prod_q sigma_q acts as
+//   (P psi)_x = (-i)^{#Y} (-1)^{popc(x & zmask)} psi_{x ^ xmask}
+// with xmask = bits carrying X or Y and zmask = bits carrying Z or Y
+// (Y = i X Z per qubit).  Terms sharing an xmask are evaluated in one pass:
+// each thread visits pairs (x, x ^ xmask) once (x with the top bit of xmask
+// clear), or single amplitudes when xmask = 0, and accumulates
+//   Re[ conj(psi_x) psi_{x^m} f(x) + conj(psi_{x^m}) psi_x f(x^m) ],
+//   f(y) = sum_t w_t (-1)^{popc(y & zmask_t)},  w_t = coeff_t (-i)^{#Y_t}.
+// One launch covers every xmask group (grid.y); per-CTA FP64 partials go to
+// scratch and a single-CTA kernel sums them in a fixed order, so the result is
+// deterministic for a given launch shape.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "hq_internal.cuh"
+
+namespace hq {
+
+struct ExpTerm {
+    uint64_t zm;
+    double wr, wi;
+};
+struct ExpGroup {
+    uint64_t xm;
+    int hb;  // top bit of xm (-1 when xm == 0)
+    int t0, nt;
+};
+constexpr int kMaxGroups = 32;
+constexpr int kMaxTerms = 96;
+struct ExpParams {
+    int ngroups;
+    int n;
+    int64_t nstates;
+    ExpGroup grp[kMaxGroups];
+    ExpTerm term[kMaxTerms];
+};
+
+constexpr int kRedThreads = 256;
+
+template <typename R>
+__device__ __forceinline__ void eval_f(const ExpParams &p, const ExpGroup &gr, uint64_t y, R &fr, R &fi)
+{
+    fr = 0;
+    fi = 0;
+    for (int t = gr.t0; t < gr.t0 + gr.nt; ++t) {
+        const R sg = (__popcll(y & p.term[t].zm) & 1) ? R(-1) : R(1);
+        fr += sg * R(p.term[t].wr);
+        fi += sg * R(p.term[t].wi);
+    }
+}
+
+// partials[group * gridDim.x + blockIdx.x]
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_expect(const ExpParams p, const typename C2<R>::type *__restrict__ psi,
+                                                        double *__restrict__ partials)
+{
+    const ExpGroup gr = p.grp[blockIdx.y];
+    const int64_t dim = int64_t(1) << p.n;
+    const int64_t items = (gr.hb < 0 ? dim : dim >> 1) * p.nstates;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    constexpr int kChunk = 8;  // items summed in R before joining the FP64 accumulator
+    double acc = 0;
+    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; base < items; base += stride * kChunk) {
+        R part = 0;
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+            const int64_t it = base + u * stride;
+            if (it >= items) break;
+            if (gr.hb < 0) {
+                const typename C2<R>::type a = psi[it];
+                R fr, fi;
+                eval_f<R>(p, gr, uint64_t(it) & uint64_t(dim - 1), fr, fi);
+                part += (a.x * a.x + a.y * a.y) * fr;
+            } else {
+                const int hb = gr.hb;
+                const int64_t s = it >> (p.n - 1);
+                const int64_t q = it & ((dim >> 1) - 1);
+                const int64_t x = ((q >> hb) << (hb + 1)) | (q & ((int64_t(1) << hb) - 1));
+                const int64_t x2 = x ^ int64_t(gr.xm);
+                const typename C2<R>::type a = psi[s * dim + x], b = psi[s * dim + x2];
+                // z = conj(a) * b
+                const R zr = a.x * b.x + a.y * b.y, zi = a.x * b.y - a.y * b.x;
+                R fr, fi, gr_, gi;
+                eval_f<R>(p, gr, uint64_t(x), fr, fi);
+                eval_f<R>(p, gr, uint64_t(x2), gr_, gi);
+                // Re[z f(x)] + Re[conj(z) f(x2)]
+                part += zr * fr - zi * fi + zr * gr_ + zi * gi;
+            }
+        }
+        acc += double(part);
+    }
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = s;
+}
+
+// one CTA: out[0] = sum over groups of (sum over that group's partials)
+__global__ void __launch_bounds__(kRedThreads) k_expect_final(const double *__restrict__ partials, int ngroups,
+                                                              int per_group, double *__restrict__ out)
+{
+    double total = 0;
+    for (int g = 0; g < ngroups; ++g) {
+        double v = 0;
+        for (int i = threadIdx.x; i < per_group; i += blockDim.x) v += partials[int64_t(g) * per_group + i];
+        const double s = block_sum(v);
+        if (threadIdx.x == 0) total += s;
+    }
+    if (threadIdx.x == 0) out[0] = total;
+}
+
+// Builds the xmask groups (host).  Returns HQ_ERR_ARG on a bad term.
+static hq_status build_groups(int n, const hq_pauli_term *terms, int T, std::vector<ExpGroup> &groups,
+                              std::vector<ExpTerm> &flat)
+{
+    struct Tm {
+        uint64_t xm, zm;
+        double wr, wi;
+    };
+    std::vector<Tm> tms;
+    for (int t = 0; t < T; ++t) {
+        uint64_t xm = 0, zm = 0;
+        int ny = 0;
+        for (int j = 0; j < terms[t].len; ++j) {
+            const uint64_t bit = 1ull << (n - 1 - terms[t].qubits[j]);
+            const char op = terms[t].ops[j];
+            if (op == 'X') xm |= bit;
+            else if (op == 'Z') zm |= bit;
+            else if (op == 'Y') { xm |= bit; zm |= bit; ++ny; }
+            else return HQ_ERR_ARG;
+        }
+        // (-i)^ny
+        static const double pr[4] = {1, 0, -1, 0}, pi[4] = {0, -1, 0, 1};
+        tms.push_back({xm, zm, terms[t].coeff * pr[ny & 3], terms[t].coeff * pi[ny & 3]});
+    }
+    std::stable_sort(tms.begin(), tms.end(), [](const Tm &a, const Tm &b) { return a.xm < b.xm; });
+    for (size_t i = 0; i < tms.size();) {
+        size_t j = i;
+        while (j < tms.size() && tms[j].xm == tms[i].xm) ++j;
+        // one group per xmask, split so that no group exceeds half a parameter block
+        for (size_t u0 = i; u0 < j; u0 += kMaxTerms / 2) {
+            const size_t u1 = std::min(j, u0 + kMaxTerms / 2);
+            ExpGroup g;
+            g.xm = tms[i].xm;
+            g.hb = g.xm ? 63 - __builtin_clzll(g.xm) : -1;
+            g.t0 = int(flat.size());
+            g.nt = int(u1 - u0);
+            for (size_t u = u0; u < u1; ++u) flat.push_back({tms[u].zm, tms[u].wr, tms[u].wi});
+            groups.push_back(g);
+        }
+        i = j;
+    }
+    return HQ_OK;
+}
+
+hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,
+                             double *out_host, cudaStream_t s)
+{
+    std::vector<ExpGroup> groups;
+    std::vector<ExpTerm> flat;
+    hq_status st = build_groups(n, terms, T, groups, flat);
+    if (st != HQ_OK) return st;
+    if (groups.empty()) {
+        *out_host = 0.0;
+        return HQ_OK;
+    }
+    const int64_t dim = int64_t(1) << n;
+    const int gx = int(std::max<int64_t>(1, std::min<int64_t>(2 * sm_count(), dim / (kRedThreads * 8))));
+    // batches of groups that fit the parameter block
+    std::vector<std::pair<int, int>> chunks;  // [g0, g1)
+    for (int g0 = 0; g0 < int(groups.size());) {
+        int g1 = g0, nt = 0;
+        while (g1 < int(groups.size()) && g1 - g0 < kMaxGroups && nt + groups[g1].nt <= kMaxTerms) nt += groups[g1++].nt;
+        chunks.push_back({g0, g1});
+        g0 = g1;
+    }
+    const size_t npart = size_t(groups.size()) * gx;
+    double *scratch = nullptr;
+    if (cudaMallocAsync((void **)&scratch, sizeof(double) * (npart + 1), s) != cudaSuccess) return HQ_ERR_ALLOC;
+    hq_status rc = HQ_OK;
+    for (auto &ch : chunks) {
+        ExpParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.n = n;
+        p.nstates = 1;
+        p.ngroups = ch.second - ch.first;
+        int nt = 0;
+        for (int g = ch.first; g < ch.second; ++g) {
+            ExpGroup gg = groups[g];
+            for (int t = 0; t < gg.nt; ++t) p.term[nt + t] = flat[gg.t0 + t];
+            gg.t0 = nt;
+            nt += gg.nt;
+            p.grp[g - ch.first] = gg;
+        }
+        dim3 grid(gx, p.ngroups);
+        double *part = scratch + size_t(ch.first) * gx;
+        if (dt == HQ_C64)
+            k_expect<float><<<grid, kRedThreads, 0, s>>>(p, (const float2 *)state, part);
+        else
+            k_expect<double><<<grid, kRedThreads, 0, s>>>(p, (const double2 *)state, part);
+        if ((rc = cuda_status("k_expect", cudaGetLastError())) != HQ_OK) break;
+    }
+    if (rc == HQ_OK) {
+        k_expect_final<<<1, kRedThreads, 0, s>>>(scratch, int(groups.size()), gx, scratch + npart);
+        rc = cuda_status("k_expect_final", cudaGetLastError());
+    }
+    double result = 0;
+    if (rc == HQ_OK) rc = cuda_status("copy result", cudaMemcpyAsync(&result, scratch + npart, sizeof(double),
+                                                                       cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(scratch, s);
+    if (rc == HQ_OK) rc = cuda_status("sync", cudaStreamSynchronize(s));
+    if (rc == HQ_OK) *out_host = result;
+    return rc;
+}
+
+}  // namespace hq

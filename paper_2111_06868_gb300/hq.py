@@ -1,0 +1,289 @@
+"""Thin ctypes binding of libhq.so (include/hq.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  State vectors are
+torch tensors (complex64 / complex128, 2^n elements, CUDA, contiguous); the
+stream is torch's current stream unless one is given.  Every step of the path
+runs in libhq.so's kernels; if the library is missing or a call fails, these
+functions raise -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhq.so")
+
+HQ_MAX_K = 6
+HQ_MAX_N = 34
+HQ_MAX_PAULI = 8
+HQ_C64, HQ_C128 = 0, 1
+HQ_OP_MATRIX, HQ_OP_ROT = 0, 1
+HQ_ENGINE_AUTO, HQ_ENGINE_CUDA_CORE, HQ_ENGINE_TC_F16, HQ_ENGINE_TC_BF16 = 0, 1, 2, 3
+ENGINES = {"auto": 0, "cuda_core": 1, "tc_f16": 2, "tc_bf16": 3}
+
+STATUS = {
+    0: "HQ_OK", -1: "HQ_ERR_NULL", -2: "HQ_ERR_QUBIT_RANGE", -3: "HQ_ERR_DUP_QUBIT", -4: "HQ_ERR_K_TOO_LARGE",
+    -5: "HQ_ERR_N_TOO_LARGE", -6: "HQ_ERR_DTYPE", -7: "HQ_ERR_ALLOC", -8: "HQ_ERR_CUDA", -9: "HQ_ERR_TIMEOUT",
+    -10: "HQ_ERR_TOKEN", -11: "HQ_ERR_CAPACITY", -12: "HQ_ERR_ARG", -13: "HQ_ERR_ALIGN",
+}
+
+
+class HQError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{where}: {self.name}" + (f" ({detail})" if detail else ""))
+
+
+class hq_gate(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("qubits", ctypes.c_int * HQ_MAX_K), ("matrix", ctypes.c_void_p)]
+
+
+class hq_op(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int), ("k", ctypes.c_int), ("qubits", ctypes.c_int * HQ_MAX_K),
+        ("matrix", ctypes.c_void_p), ("axis", ctypes.c_int), ("param", ctypes.c_int),
+    ]
+
+
+class hq_pauli_term(ctypes.Structure):
+    _fields_ = [
+        ("coeff", ctypes.c_double), ("len", ctypes.c_int), ("qubits", ctypes.c_int * HQ_MAX_PAULI),
+        ("ops", ctypes.c_char * HQ_MAX_PAULI),
+    ]
+
+
+class hq_config(ctypes.Structure):
+    _fields_ = [("engine", ctypes.c_int), ("tc_min_k", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libhq.so (built by ``paper_2111_06868_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build the CUDA library first (paper_2111_06868_gb300.build.build())")
+    lib = ctypes.CDLL(p)
+    V, I, D, P = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER
+    sig = {
+        "hq_status_string": ([I], ctypes.c_char_p),
+        "hq_last_error": ([], ctypes.c_char_p),
+        "hq_version": ([], ctypes.c_char_p),
+        "hq_state_init": ([V, I, I, ctypes.c_char_p, V], I),
+        "hq_fuse": ([I, V, I, I, V, P(I), V, ctypes.c_int64, V], I),
+        "hq_apply_gate": ([V, I, I, V, I, V, V], I),
+        "hq_apply_blocks": ([V, I, I, V, I, V, V], I),
+        "hq_expectation": ([V, I, I, V, I, P(D), V], I),
+        "hq_adjoint_workspace_bytes": ([I, I, I, I, I, I], ctypes.c_size_t),
+        "hq_adjoint_grad": ([I, I, V, I, I, V, I, V, I, ctypes.c_char_p, I, V, ctypes.c_size_t, V, V, V], I),
+    }
+    for name, (args, res) in sig.items():
+        if hasattr(lib, name):
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        detail = ""
+        if st == -8:
+            detail = load().hq_last_error().decode()
+        raise HQError(st, where, detail)
+
+
+# ----------------------------------------------------------------------------
+# marshalling helpers
+# ----------------------------------------------------------------------------
+def _dtype_code(t) -> int:
+    import torch
+
+    if t.dtype == torch.complex64:
+        return HQ_C64
+    if t.dtype == torch.complex128:
+        return HQ_C128
+    raise TypeError(f"state must be complex64 or complex128, got {t.dtype}")
+
+
+def _state_args(state, nstates: int = 1):
+    if not state.is_cuda or not state.is_contiguous():
+        raise ValueError("state must be a contiguous CUDA tensor")
+    numel = state.numel() // nstates
+    n = numel.bit_length() - 1
+    if numel != 1 << n:
+        raise ValueError("state length must be a power of two")
+    return ctypes.c_void_p(state.data_ptr()), n, _dtype_code(state)
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _gate_struct(qubits: Sequence[int], matrix: np.ndarray, keep: list) -> hq_gate:
+    m = np.ascontiguousarray(matrix, np.complex128)
+    keep.append(m)
+    g = hq_gate()
+    g.k = len(qubits)
+    for j, q in enumerate(qubits):
+        g.qubits[j] = int(q)
+    g.matrix = m.ctypes.data
+    return g
+
+
+def _gates_array(gates: Iterable, keep: list):
+    gl = list(gates)
+    arr = (hq_gate * max(1, len(gl)))()
+    for i, g in enumerate(gl):
+        qs, m = (g.qubits, g.matrix) if hasattr(g, "qubits") else g
+        arr[i] = _gate_struct(qs, m, keep)
+    return arr, len(gl)
+
+
+def _terms_array(H) -> tuple:
+    arr = (hq_pauli_term * max(1, len(H)))()
+    for t, (c, term) in enumerate(H):
+        arr[t].coeff = float(c)
+        arr[t].len = len(term)
+        for j, (q, _) in enumerate(term):
+            arr[t].qubits[j] = int(q)
+        arr[t].ops = "".join(p for _, p in term).encode()
+    return arr, len(H)
+
+
+# ----------------------------------------------------------------------------
+# entry points
+# ----------------------------------------------------------------------------
+def hq_status_string(st: int) -> str:
+    return load().hq_status_string(st).decode()
+
+
+def hq_version() -> str:
+    return load().hq_version().decode()
+
+
+def hq_state_init(state, tokens: str | None = None, stream=None):
+    ptr, n, dt = _state_args(state)
+    tok = None
+    if tokens is not None:
+        tok = (tokens * n if len(tokens) == 1 else tokens).encode()
+        if len(tok) != n:
+            raise ValueError("need one token per qubit")
+    _check(load().hq_state_init(ptr, n, dt, tok, _stream(stream)), "hq_state_init")
+    return state
+
+
+def hq_apply_gate(state, qubits: Sequence[int], matrix, stream=None):
+    ptr, n, dt = _state_args(state)
+    q = (ctypes.c_int * max(1, len(qubits)))(*[int(x) for x in qubits])
+    m = np.ascontiguousarray(matrix, np.complex128)
+    _check(load().hq_apply_gate(ptr, n, dt, q, len(qubits), m.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+           "hq_apply_gate")
+    return state
+
+
+def hq_fuse(n: int, gates: Iterable, k_max: int, with_members: bool = False):
+    """Returns blocks as a list of (qubits tuple, complex128 matrix)."""
+    keep: list = []
+    arr, G = _gates_array(gates, keep)
+    cap = max(1, G)
+    blocks = (hq_gate * cap)()
+    B = ctypes.c_int(cap)
+    pool = np.zeros(2 * max(1, G) * (4 ** k_max), np.float64)
+    members = np.zeros(max(1, G), np.int32)
+    _check(load().hq_fuse(n, arr, G, k_max, blocks, ctypes.byref(B), pool.ctypes.data_as(ctypes.c_void_p),
+                          pool.size, members.ctypes.data_as(ctypes.c_void_p)), "hq_fuse")
+    out = []
+    base = pool.ctypes.data
+    for i in range(B.value):
+        b = blocks[i]
+        qs = tuple(b.qubits[j] for j in range(b.k))
+        off = (b.matrix - base) // 8
+        d = 1 << b.k
+        m = pool[off: off + 2 * d * d].view(np.complex128).reshape(d, d).copy()
+        out.append((qs, m))
+    if with_members:
+        return out, members[:G].copy()
+    return out
+
+
+def hq_apply_blocks(state, blocks: Iterable, engine: str | int = "auto", tc_min_k: int = 5, stream=None):
+    ptr, n, dt = _state_args(state)
+    keep: list = []
+    arr, G = _gates_array(blocks, keep)
+    cfg = hq_config(ENGINES[engine] if isinstance(engine, str) else int(engine), tc_min_k)
+    _check(load().hq_apply_blocks(ptr, n, dt, arr, G, ctypes.byref(cfg), _stream(stream)), "hq_apply_blocks")
+    return state
+
+
+def hq_expectation(state, H, stream=None) -> float:
+    ptr, n, dt = _state_args(state)
+    arr, T = _terms_array(H)
+    out = ctypes.c_double(0.0)
+    _check(load().hq_expectation(ptr, n, dt, arr, T, ctypes.byref(out), _stream(stream)), "hq_expectation")
+    return out.value
+
+
+def _ops_array(circuit, keep: list):
+    arr = (hq_op * max(1, len(circuit.gates)))()
+    for i, g in enumerate(circuit.gates):
+        op = arr[i]
+        op.k = g.k
+        for j, q in enumerate(g.qubits):
+            op.qubits[j] = int(q)
+        if g.matrix is not None:
+            m = np.ascontiguousarray(g.matrix, np.complex128)
+            keep.append(m)
+            op.kind = HQ_OP_MATRIX
+            op.matrix = m.ctypes.data
+        else:
+            op.kind = HQ_OP_ROT
+            op.axis = ord(g.axis)
+            op.param = int(g.param)
+    return arr, len(circuit.gates)
+
+
+def hq_adjoint_workspace_bytes(n: int, dtype_code: int, G: int, P: int, batch: int, checkpoints: int = 0) -> int:
+    return int(load().hq_adjoint_workspace_bytes(n, dtype_code, G, P, batch, checkpoints))
+
+
+def hq_adjoint_grad(circuit, H, theta, dtype="complex64", tokens: str | None = None, checkpoints: int = 0,
+                    workspace=None, stream=None):
+    """Energies (batch,) and gradients (batch, P) for theta of shape (batch, P)."""
+    import torch
+
+    th = np.ascontiguousarray(np.atleast_2d(theta), np.float64)
+    batch, P = th.shape
+    if P != circuit.n_params:
+        raise ValueError("theta must have circuit.n_params columns")
+    dt = HQ_C64 if str(dtype).endswith("64") and "128" not in str(dtype) else HQ_C128
+    need = hq_adjoint_workspace_bytes(circuit.n, dt, len(circuit.gates), P, batch, checkpoints)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+    keep: list = []
+    ops, G = _ops_array(circuit, keep)
+    terms, T = _terms_array(H)
+    tok = None
+    if tokens is not None:
+        tok = (tokens * circuit.n if len(tokens) == 1 else tokens).encode()
+    e = np.zeros(batch, np.float64)
+    g = np.zeros((batch, max(P, 1)), np.float64)
+    _check(load().hq_adjoint_grad(circuit.n, dt, ops, G, P, th.ctypes.data_as(ctypes.c_void_p), batch, terms, T, tok,
+                                  checkpoints, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                  e.ctypes.data_as(ctypes.c_void_p), g.ctypes.data_as(ctypes.c_void_p),
+                                  _stream(stream)), "hq_adjoint_grad")
+    return e, g[:, :P]

@@ -1,0 +1,266 @@
+"""GPU parity: libhq.so (through the C ABI) against the CPU oracle on the same
+seeded inputs.  Tolerances: complex128 max-abs <= 1e-12; complex64 relative L2
+<= 2e-5 * max(1, G/1000) with G the number of unfused gates."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_06868_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2111_06868_gb300 import build
+    from paper_2111_06868_gb300 import hq as _hq
+
+    build.build()
+    _hq.load()
+    return _hq
+
+
+DT = {"c64": torch.complex64, "c128": torch.complex128}
+
+
+def to_dev(psi, dt):
+    return torch.from_numpy(psi.astype(np.complex128)).to(DT[dt]).cuda()
+
+
+def to_host(t):
+    return t.cpu().numpy().astype(np.complex128)
+
+
+def assert_close(got, want, dt, G=1):
+    if dt == "c128":
+        err = np.max(np.abs(got - want))
+        assert err <= 1e-12, f"max-abs {err:.3e}"
+    else:
+        rel = np.linalg.norm(got - want) / np.linalg.norm(want)
+        tol = 2e-5 * max(1.0, G / 1000)
+        assert rel <= tol, f"rel L2 {rel:.3e} > {tol:.1e}"
+
+
+def random_state(n, seed):
+    """Seeded normalised Gaussian state (input only)."""
+    rng = C.SplitMix64(seed)
+    v = np.empty(2 << n)
+    for i in range(0, v.size, 2):
+        u1, u2 = max(rng.uniform(), 1e-300), rng.uniform()
+        r = math.sqrt(-2 * math.log(u1))
+        v[i], v[i + 1] = r * math.cos(2 * math.pi * u2), r * math.sin(2 * math.pi * u2)
+    psi = v[0::2] + 1j * v[1::2]
+    return psi / np.linalg.norm(psi)
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("tokens", ["0", "1", "+", "-", "01+-", "+-+-10+"])
+@pytest.mark.parametrize("n", [1, 3, 7, 13])
+def test_state_init(hq, dt, tokens, n):
+    tok = (tokens * n)[:n]
+    st = torch.empty(1 << n, dtype=DT[dt], device="cuda")
+    hq.hq_state_init(st, tok)
+    assert_close(to_host(st), oracle.state_init(n, tok), dt)
+
+
+def qubit_sets(n, k, seed):
+    rng = C.SplitMix64(seed)
+    sets = [list(range(n - k, n)),             # lowest bits (qubits n-1..)
+            list(range(k)),                    # highest bits
+            list(range(n - 1, n - 1 - k, -1))]  # lowest bits, reversed order
+    rnd = []
+    while len(rnd) < k:
+        q = rng.randint(0, n - 1)
+        if q not in rnd:
+            rnd.append(q)
+    sets.append(rnd)
+    if k >= 2:
+        sets.append([n - 1] + list(range(k - 1)))  # mixed: one low bit, the rest high
+    return sets
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("n", [6, 9, 13, 17])
+def test_apply_gate_every_position_class(hq, dt, k, n):
+    if k > n:
+        pytest.skip()
+    rng = C.SplitMix64(1000 * n + k)
+    psi = random_state(n, n * 31 + k)
+    st = to_dev(psi, dt)
+    want = psi.copy()
+    for qs in qubit_sets(n, k, n + 7 * k):
+        M = C.random_unitary(k, rng)
+        hq.hq_apply_gate(st, qs, M)
+        oracle.apply_gate(want, n, qs, M)
+    assert_close(to_host(st), want, dt, G=5)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("k", [1, 2, 3, 6])
+def test_apply_gate_k_equals_n(hq, dt, k):
+    n = k
+    rng = C.SplitMix64(77 + k)
+    psi = random_state(n, 5 + k)
+    M = C.random_unitary(k, rng)
+    qs = list(range(n))[::-1]
+    st = to_dev(psi, dt)
+    hq.hq_apply_gate(st, qs, M)
+    oracle.apply_gate(psi, n, qs, M)
+    assert_close(to_host(st), psi, dt)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_diagonal_gates(hq, dt, k):
+    n = 14
+    rng = C.SplitMix64(500 + k)
+    psi = random_state(n, 900 + k)
+    st = to_dev(psi, dt)
+    for qs in qubit_sets(n, k, 3 * k):
+        d = np.exp(2j * math.pi * np.array([rng.uniform() for _ in range(1 << k)]))
+        M = np.diag(d)
+        hq.hq_apply_gate(st, qs, M)
+        oracle.apply_gate(psi, n, qs, M)
+    assert_close(to_host(st), psi, dt, G=5)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("kmax", [0, 2, 3, 4, 5, 6])
+def test_circuit_n12_per_gate_and_fused(hq, dt, kmax):
+    circ = C.config_small(seed=1)
+    want = oracle.simulate(circ)
+    st = torch.empty(1 << circ.n, dtype=DT[dt], device="cuda")
+    hq.hq_state_init(st)
+    blocks = hq.hq_fuse(circ.n, circ.gates, kmax) if kmax else circ.gates
+    hq.hq_apply_blocks(st, blocks)
+    assert_close(to_host(st), want, dt, G=len(circ.gates))
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("kmax", [0, 4])
+def test_circuit_grid_fsim_n20(hq, dt, kmax):
+    """4x5 grid, depth 12, fSim entanglers: spans many tiles and every bit class."""
+    circ = C.random_circuit(C.grid(4, 5), 12, seed=11, two_qubit="fsim")
+    want = oracle.simulate(circ, tokens="+")
+    st = torch.empty(1 << circ.n, dtype=DT[dt], device="cuda")
+    hq.hq_state_init(st, "+")
+    blocks = hq.hq_fuse(circ.n, circ.gates, kmax) if kmax else circ.gates
+    hq.hq_apply_blocks(st, blocks)
+    assert_close(to_host(st), want, dt, G=len(circ.gates))
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_dense_circuit_wide_blocks(hq, dt):
+    """Random dense gates fused up to 6 qubits (CUDA-core block kernel)."""
+    circ = C.random_dense_circuit(15, 60, seed=4, kmax=3)
+    psi0 = random_state(15, 12)
+    want = oracle.apply_circuit(psi0.copy(), circ)
+    st = to_dev(psi0, dt)
+    hq.hq_apply_blocks(st, hq.hq_fuse(15, circ.gates, 6), engine="cuda_core")
+    assert_close(to_host(st), want, dt, G=60)
+
+
+def test_empty_block_list_is_identity(hq):
+    psi = random_state(10, 3)
+    st = to_dev(psi, "c128")
+    hq.hq_apply_blocks(st, [])
+    assert_close(to_host(st), psi, "c128")
+
+
+# --------------------------------------------------------------------------
+# expectation
+# --------------------------------------------------------------------------
+def random_hamiltonian(n, T, seed):
+    rng = C.SplitMix64(seed)
+    H = []
+    for _ in range(T):
+        L = rng.randint(0, min(4, n))
+        qs = []
+        while len(qs) < L:
+            q = rng.randint(0, n - 1)
+            if q not in qs:
+                qs.append(q)
+        H.append((rng.uniform() - 0.5, tuple((q, "XYZ"[rng.randint(0, 2)]) for q in qs)))
+    return H
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n", [1, 2, 5, 11, 16])
+def test_expectation_random_pauli_sums(hq, dt, n):
+    psi = random_state(n, 40 + n)
+    H = random_hamiltonian(n, 12, 7 * n)
+    want = oracle.expectation(psi, H)
+    got = hq.hq_expectation(to_dev(psi, dt), H)
+    tol = 1e-12 if dt == "c128" else 1e-5 * max(1.0, sum(abs(c) for c, _ in H))
+    assert abs(got - want) <= tol
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_expectation_norm_and_ansatz_hamiltonian(hq, dt):
+    n = 14
+    circ = C.ansatz(n, 2)
+    th = C.ansatz_params(circ.n_params, 1, 3)[0]
+    psi = oracle.simulate(circ, theta=th)
+    st = to_dev(psi, dt)
+    H = C.ansatz_hamiltonian(n)
+    tol = 1e-12 if dt == "c128" else 2e-5
+    assert abs(hq.hq_expectation(st, [(1.0, ())]) - 1.0) <= tol
+    assert abs(hq.hq_expectation(st, H) - oracle.expectation(psi, H)) <= tol * 10
+
+
+def test_expectation_many_groups(hq):
+    """More xmask groups and terms than one parameter block holds."""
+    n = 12
+    psi = random_state(n, 99)
+    H = [(0.1 * (i + 1), ((i % n, "X"), ((i + 3) % n, "Y"))) for i in range(40)]
+    H += [(0.05, ((q, "Z"),)) for q in range(n)] * 9
+    assert abs(hq.hq_expectation(to_dev(psi, "c128"), H) - oracle.expectation(psi, H)) <= 1e-12
+
+
+# --------------------------------------------------------------------------
+# errors come back as status codes, before any work is enqueued
+# --------------------------------------------------------------------------
+def test_argument_errors(hq):
+    st = torch.zeros(1 << 5, dtype=torch.complex64, device="cuda")
+    M = np.eye(2)
+    with pytest.raises(hq.HQError, match="QUBIT_RANGE"):
+        hq.hq_apply_gate(st, [5], M)
+    with pytest.raises(hq.HQError, match="DUP_QUBIT"):
+        hq.hq_apply_gate(st, [1, 1], np.eye(4))
+    with pytest.raises(hq.HQError, match="K_TOO_LARGE"):
+        hq.hq_apply_gate(st, list(range(5)) + [0], np.eye(64))
+    with pytest.raises(hq.HQError, match="TOKEN"):
+        hq.hq_state_init(st, "0+x01")
+    m = np.eye(2, dtype=np.complex128)
+    q = (hq.ctypes.c_int * 1)(0)
+    rc = hq.load().hq_apply_gate(hq.ctypes.c_void_p(st.data_ptr() + 8), 5, hq.HQ_C64, q, 1,
+                                 m.ctypes.data_as(hq.ctypes.c_void_p), None)
+    assert hq.STATUS[rc] == "HQ_ERR_ALIGN"
+
+
+# --------------------------------------------------------------------------
+# full-size properties (n = 30): norm, and C followed by C^+ returns |0..0>
+# --------------------------------------------------------------------------
+@pytest.mark.slow
+def test_n30_fused_norm_and_inverse(hq):
+    circ = C.config_n30(seed=0)
+    G = len(circ.gates)
+    blocks = hq.hq_fuse(circ.n, circ.gates, 4)
+    st = torch.empty(1 << 30, dtype=torch.complex64, device="cuda")
+    hq.hq_state_init(st)
+    hq.hq_apply_blocks(st, blocks)
+    assert abs(hq.hq_expectation(st, [(1.0, ())]) - 1.0) <= 2e-5 * max(1, G / 1000)
+    inv = [(q, m.conj().T.copy()) for q, m in reversed(blocks)]
+    hq.hq_apply_blocks(st, inv)
+    a0 = complex(st[0].item())
+    assert abs(a0 - 1.0) <= 2 * 2e-5 * max(1, 2 * G / 1000)
+    del st
+    torch.cuda.empty_cache()
