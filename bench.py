@@ -50,6 +50,9 @@ def workload(args, rank):
     elif args.workload == "n33":
         circ = C.config_n33(seed=args.seed + rank)
         desc = "n=33 6x6-minus-3-corners depth-24 fSim random circuit, 1116 gates"
+    elif args.workload == "n27":
+        circ = C.random_circuit(C.grid(5, 6, first=27), 20, args.seed + rank, "fsim")
+        desc = "n=27 (first 27 sites of the 5x6 grid) depth-20 fSim random circuit (profiling size)"
     elif args.workload == "n12":
         circ = C.config_small(seed=args.seed + rank)
         desc = "n=12 3x4 grid depth-10 CZ random circuit, 163 gates"
@@ -111,13 +114,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def block_class(qs, m):
+def block_class(qs, m, engine, tc_min_k):
+    """Which kernel libhq launches for this block (mirrors its dispatch)."""
     d = m.shape[0]
-    diag = not np.any(m[~np.eye(d, dtype=bool)])
-    return ("diag" if diag else "dense") + f"_k{len(qs)}"
-
-
-KERNEL_NAME = {"dense": "k_gather", "diag": "k_diag"}
+    k = len(qs)
+    if not np.any(m[~np.eye(d, dtype=bool)]):
+        return f"k_diag_k{k}"
+    if engine.startswith("tc") and k >= tc_min_k:
+        return f"k_tc_{engine[3:]}_k{k}"
+    return f"k_gather_k{k}" if k <= 4 else f"k_block_k{k}"
 
 
 def cpu_baseline(circ, seconds: float = 12.0):
@@ -183,10 +188,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hq", choices=["hq", "reference"])
-    ap.add_argument("--workload", default="n30", choices=["n30", "n33", "n12"])
+    ap.add_argument("--workload", default="n30", choices=["n30", "n33", "n27", "n12"])
     ap.add_argument("--kmax", type=int, default=4)
     ap.add_argument("--dtype", default="complex64", choices=["complex64", "complex128"])
-    ap.add_argument("--engine", default="auto")
+    ap.add_argument("--engine", default="auto", choices=["auto", "cuda_core", "tc_f16", "tc_bf16"])
+    ap.add_argument("--tc-min-k", type=int, default=5)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--ref-gates", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -222,7 +228,7 @@ def main():
     blocks = hq.hq_fuse(n, circ.gates, args.kmax) if args.kmax > 0 else [(g.qubits, g.matrix) for g in circ.gates]
     fuse_s = time.perf_counter() - t_f
     B = len(blocks)
-    classes = [block_class(q, m) for q, m in blocks]
+    classes = [block_class(q, m, args.engine, args.tc_min_k) for q, m in blocks]
     cdt = torch.complex64 if args.dtype == "complex64" else torch.complex128
     S = 8 if cdt == torch.complex64 else 16
     state = torch.empty(1 << n, dtype=cdt, device="cuda")
@@ -235,7 +241,7 @@ def main():
         for i, b in enumerate(blocks):
             if events is not None:
                 events[i].record(stream)
-            hq.hq_apply_blocks(state, [b], engine=engine)
+            hq.hq_apply_blocks(state, [b], engine=engine, tc_min_k=args.tc_min_k)
         if events is not None:
             events[B].record(stream)
         return hq.hq_expectation(state, norm_term)
@@ -291,7 +297,7 @@ def main():
         out = torch.zeros(1, dtype=torch.float64).pin_memory()
         for _ in range(1):
             state.copy_(host_in, non_blocking=True)
-            hq.hq_apply_blocks(state, blocks, engine=engine)
+            hq.hq_apply_blocks(state, blocks, engine=engine, tc_min_k=args.tc_min_k)
             out[0] = hq.hq_expectation(state, norm_term)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -299,7 +305,7 @@ def main():
         e0.record(stream)
         for _ in range(e2e_steps):
             state.copy_(host_in, non_blocking=True)
-            hq.hq_apply_blocks(state, blocks, engine=engine)
+            hq.hq_apply_blocks(state, blocks, engine=engine, tc_min_k=args.tc_min_k)
             out[0] = hq.hq_expectation(state, norm_term)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -327,7 +333,7 @@ def main():
             "effective_GBps": eff_gbs, "roofline_frac_effective": eff_gbs / peaks["hbm_gbs"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                         "kernel": f"{KERNEL_NAME[dom.split('_')[0]]} ({dom})", "peak_source": peak_kind,
+                         "kernel": dom, "peak_source": peak_kind,
                          "bytes_per_launch": bytes_per_launch},
             "per_class": per_class,
             "norm2": norm, "fuse_s": fuse_s,

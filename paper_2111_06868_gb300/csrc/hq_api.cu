@@ -160,7 +160,8 @@ hq_status hq_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_t
     if (st != HQ_OK) return st;
     if (!out_host) return HQ_ERR_NULL;
     if ((st = check_terms(n, terms, T)) != HQ_OK) return st;
-    return launch_expectation(state, n, dt, terms, T, out_host, (cudaStream_t)stream);
+    if ((st = launch_expectation(state, n, dt, terms, T, out_host, (cudaStream_t)stream)) != HQ_OK) return st;
+    return device_error_status();
 }
 
 }  // extern "C"

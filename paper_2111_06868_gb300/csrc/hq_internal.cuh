@@ -170,6 +170,10 @@ hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pau
 hq_status launch_tc_block(void *state, int n, int k, const int *qubits, const double *matrix, int64_t nstates,
                           int split_bf16, cudaStream_t s);
 
+// HQ_ERR_TIMEOUT (and clears the flag) if a bounded device-side wait ran out
+// since the last call; synchronous.
+hq_status device_error_status();
+
 // validation helpers (hq_api.cu)
 hq_status check_qubits(int n, int k, const int *qubits, int kmax);
 

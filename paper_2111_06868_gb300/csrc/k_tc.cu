@@ -1,11 +1,452 @@
-// k_tc.cu -- tensor-core engine for fused k = 5, 6 blocks (complex64).
+// k_tc.cu -- tensor-core engine for fused k = 5, 6 blocks on complex64 states.
+//
+// Sec. 3.1's compress() fuses gates into wide blocks because wide gates use the
+// hardware's vector units better; on GB300 the unit for a dense 2^k x 2^k block
+// is the 5th-generation tensor core.  One block application is the real GEMM
+//     D[n][j] = sum_kk A[n][kk] B[kk][j]
+// with n = one group of 2^k amplitudes that differ only in the target bits
+// (128 groups per tile = MMA M), kk = input components (Re x_0..x_{D-1},
+// Im x_0..x_{D-1}), j = output components in the same order, and B the real
+// representation [[Mr, -Mi], [Mi, Mr]] of the block matrix (D = 2^k).
+//
+// Precision: FP16 (or BF16) operands, FP32 accumulation, split products.  Each
+// group is scaled by a power of two s_n that brings its largest component to
+// [2^13, 2^14); hi = f16(x s), lo = f16((x s - hi) 2^11) (2^8 for BF16), and
+// the matrix likewise (one scale).  Three products are kept:
+//     D1 = A_hi B_hi,   D2 = A_hi B_lo + A_lo B_hi,   out = (D1 + 2^-11 D2) / (s_n s_M)
+// (the lo*lo term, ~2^-22 relative, is dropped).
+//
+// Kernel shape (persistent, 1 CTA per SM for k = 6, 2 for k = 5; 256 threads):
+//   warps 0-3  producers: thread p loads group p of a tile straight from HBM into
+//              registers (lanes = consecutive groups, so each load instruction is
+//              coalesced), splits and stores it as row p of A_hi / A_lo in the
+//              K-major no-swizzle core-matrix layout; thread 0 then issues the
+//              tcgen05.mma sequence and commits it to an mbarrier.
+//   warps 4-7  epilogue: wait for the MMAs of a tile, tcgen05.ld their TMEM lanes
+//              (lane = group), combine, unscale and store the outputs to HBM.
+//   A and the TMEM accumulators are double-buffered, so loads of tile t+1
+//   overlap the MMAs and epilogue of tile t.  Every wait is bounded by a
+//   %globaltimer deadline; on expiry the kernel raises a device error flag
+//   (read back as HQ_ERR_TIMEOUT), leaves its loops and frees its TMEM.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "hq_internal.cuh"
 
 namespace hq {
 
-hq_status launch_tc_block(void *, int, int, const int *, const double *, int64_t, int, cudaStream_t)
+__device__ unsigned int g_device_error;  // bit 0: a tensor-core wait timed out
+
+constexpr int kTcThreads = 256;
+constexpr int kTcGroups = 128;                    // MMA M
+constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s per wait
+
+// ----------------------------------------------------------------------------
+// PTX wrappers
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
-    return HQ_ERR_ARG;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for phase `parity` of `bar`; false (and the abort flag raised) if the
+// deadline passes or another thread already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    const uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            atomicOr(&g_device_error, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void named_bar_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// bar.sync over `count` threads that also returns the OR of `v` over them
+__device__ __forceinline__ bool named_bar_or(int id, int count, bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(uint32_t(v)), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle.  Core matrices are 8
+// rows x 16 bytes; LBO = byte step between core matrices along K, SBO = byte
+// step between 8-row groups; version field 1 (bits 46-47).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return uint64_t((addr & 0x3FFFFu) >> 4) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+}
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A/B format
+// (bits 7-9 / 10-12: 0 = F16, 1 = BF16), both K-major, N >> 3 at bit 17,
+// M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, bool bf16)
+{
+    return (1u << 4) | (uint32_t(bf16) << 7) | (uint32_t(bf16) << 10) | (uint32_t(N >> 3) << 17) |
+           (uint32_t(M >> 4) << 24);
+}
+
+// byte offset of element (row, kk) in a K-major core-matrix tile with Kdim columns
+__host__ __device__ __forceinline__ uint32_t core_off(int row, int kk, int Kdim)
+{
+    return uint32_t((row >> 3) * (Kdim * 16) + (kk >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
+}
+
+template <bool BF16> struct Split;
+template <> struct Split<false> {
+    static constexpr float lo_mul = 2048.f;
+    __device__ static uint32_t pack(float a, float b, uint32_t &lo)
+    {
+        const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+        const __half la = __float2half_rn((a - __half2float(ha)) * lo_mul);
+        const __half lb = __float2half_rn((b - __half2float(hb)) * lo_mul);
+        lo = uint32_t(__half_as_ushort(la)) | (uint32_t(__half_as_ushort(lb)) << 16);
+        return uint32_t(__half_as_ushort(ha)) | (uint32_t(__half_as_ushort(hb)) << 16);
+    }
+};
+template <> struct Split<true> {
+    static constexpr float lo_mul = 256.f;
+    __device__ static uint32_t pack(float a, float b, uint32_t &lo)
+    {
+        const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+        const __nv_bfloat16 la = __float2bfloat16_rn((a - __bfloat162float(ha)) * lo_mul);
+        const __nv_bfloat16 lb = __float2bfloat16_rn((b - __bfloat162float(hb)) * lo_mul);
+        lo = uint32_t(__bfloat16_as_ushort(la)) | (uint32_t(__bfloat16_as_ushort(lb)) << 16);
+        return uint32_t(__bfloat16_as_ushort(ha)) | (uint32_t(__bfloat16_as_ushort(hb)) << 16);
+    }
+};
+
+struct TcParams {
+    TileGeom g;               // K = k, L = k + 7
+    const uint4 *bmat;        // B_hi then B_lo, each 2D x 2D in core-matrix order
+    float out_mul;            // 1 / s_M
+};
+
+template <int K, bool BF16>
+struct TcLayout {
+    static constexpr int D = 1 << K;
+    static constexpr int D2 = 2 * D;                          // GEMM K and N
+    static constexpr int kBBytes = D2 * D2 * 2;               // one of B_hi / B_lo
+    static constexpr int kABytes = kTcGroups * D2 * 2;        // one of A_hi / A_lo
+    static constexpr int kOffBhi = 0, kOffBlo = kBBytes;
+    static constexpr int kOffA = 2 * kBBytes;                 // A[buf][hi/lo]
+    static constexpr int kOffScale = kOffA + 4 * kABytes;     // float[2][128]
+    static constexpr int kOffBar = kOffScale + 2 * kTcGroups * 4;  // mma_done[2], acc_free[2]
+    static constexpr int kOffMisc = kOffBar + 4 * 8;          // tmem addr, abort flag
+    static constexpr int kBytes = kOffMisc + 16;
+    static constexpr uint32_t kTmemCols = 4 * D2;             // (D1, D2) x 2 buffers
+};
+
+template <int K, bool BF16>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcParams p, float2 *__restrict__ state)
+{
+    using Lay = TcLayout<K, BF16>;
+    constexpr int D = Lay::D, D2 = Lay::D2;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Lay::kOffBar);  // [0,1] mma_done, [2,3] acc_free
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Lay::kOffMisc);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + Lay::kOffMisc + 4);
+    float *inv_scale = reinterpret_cast<float *>(smem + Lay::kOffScale);
+    const TileGeom &g = p.g;
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // stage the split matrix, set up barriers and TMEM
+    for (int i = tid; i < 2 * Lay::kBBytes / 16; i += kTcThreads)
+        reinterpret_cast<uint4 *>(smem)[i] = p.bmat[i];
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], kTcGroups);
+        mbar_init(&bar[3], kTcGroups);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, Lay::kTmemCols);
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t smem_base = smem_u32(smem);
+    const int cmask = (1 << g.c) - 1;
+
+    if (warp < 4) {
+        // ---------------- producers + MMA issue ----------------
+        const int n = tid;  // group within the tile
+        constexpr uint32_t idesc = instr_desc(kTcGroups, D2, BF16);
+        int it = 0, issued = 0;
+        for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
+            const int buf = it & 1;
+            const int64_t gb = tile_base(g, t);
+            const int ib = group_base<K>(g, n);
+            float2 x[D];
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                const int i = ib + g.toff[r];
+                x[r] = state[gb + g.runoff[i >> g.c] + (i & cmask)];
+            }
+            float m = 0.f;
+#pragma unroll
+            for (int r = 0; r < D; ++r) m = fmaxf(m, fmaxf(fabsf(x[r].x), fabsf(x[r].y)));
+            int e = 0;
+            frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+            const float s = (m > 0.f) ? ldexpf(1.f, 14 - e) : 1.f;
+            // A[buf] is free once the epilogue of tile it-2 released its accumulators
+            const bool ok = it < 2 || mbar_wait(&bar[2 + buf], uint32_t((it / 2 - 1) & 1), abort_flag);
+            if (ok) {
+                unsigned char *ahi = smem + Lay::kOffA + buf * 2 * Lay::kABytes;
+                unsigned char *alo = ahi + Lay::kABytes;
+#pragma unroll
+                for (int ch = 0; ch < D2 / 8; ++ch) {
+                    uint32_t hv[4], lv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int k0 = ch * 8 + 2 * q;  // components k0, k0 + 1
+                        const float a = (k0 < D ? x[k0 % D].x : x[k0 % D].y) * s;
+                        const float b = (k0 + 1 < D ? x[(k0 + 1) % D].x : x[(k0 + 1) % D].y) * s;
+                        hv[q] = Split<BF16>::pack(a, b, lv[q]);
+                    }
+                    const uint32_t off = core_off(n, ch * 8, D2);
+                    *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+                    *reinterpret_cast<uint4 *>(alo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                }
+                inv_scale[buf * kTcGroups + n] = 1.f / s;
+                fence_proxy_async();
+            }
+            // every producer takes the same exit decision
+            if (named_bar_or(1, kTcGroups, !ok || *abort_flag)) break;
+            if (n == 0) {
+                tc_fence_after();
+                const uint32_t a_hi = smem_base + Lay::kOffA + buf * 2 * Lay::kABytes;
+                const uint32_t a_lo = a_hi + Lay::kABytes;
+                const uint32_t b_hi = smem_base + Lay::kOffBhi, b_lo = smem_base + Lay::kOffBlo;
+                const uint32_t d1 = tmem + uint32_t(buf * 2 * D2), d2 = d1 + uint32_t(D2);
+                constexpr uint32_t sbo = D2 * 16;
+#pragma unroll
+                for (int kk = 0; kk < D2 / 16; ++kk) {
+                    const uint32_t o = uint32_t(kk) * 256u;
+                    mma_f16(d1, smem_desc(a_hi + o, 128, sbo), smem_desc(b_hi + o, 128, sbo), idesc, kk > 0);
+                    mma_f16(d2, smem_desc(a_hi + o, 128, sbo), smem_desc(b_lo + o, 128, sbo), idesc, kk > 0);
+                    mma_f16(d2, smem_desc(a_lo + o, 128, sbo), smem_desc(b_hi + o, 128, sbo), idesc, 1);
+                }
+                mma_commit(&bar[buf]);
+            }
+            ++issued;
+        }
+        // drain: the last commit of each buffer must land before TMEM is freed
+        if (n == 0) {
+            volatile int no_abort = 0;
+            for (int b = 0; b < 2; ++b) {
+                const int cnt = (issued + 1 - b) / 2;  // tiles issued into buffer b
+                if (cnt > 0) mbar_wait(&bar[b], uint32_t((cnt - 1) & 1), &no_abort);
+            }
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        const int n = tid - kTcGroups;            // group = TMEM lane
+        const uint32_t lane_off = uint32_t((warp - 4) * 32) << 16;
+        constexpr float lo_scale = 1.f / Split<BF16>::lo_mul;
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
+            const int buf = it & 1;
+            // warp-uniform exit: tcgen05.ld below is .sync.aligned
+            if (!__all_sync(0xffffffffu, mbar_wait(&bar[buf], uint32_t((it / 2) & 1), abort_flag))) break;
+            tc_fence_after();
+            const float mul = inv_scale[buf * kTcGroups + n] * p.out_mul;
+            const int64_t gb = tile_base(g, t);
+            const int ib = group_base<K>(g, n);
+            const uint32_t d1 = tmem + lane_off + uint32_t(buf * 2 * D2), d2 = d1 + uint32_t(D2);
+#pragma unroll
+            for (int c0 = 0; c0 < D; c0 += 16) {
+                uint32_t r1[16], i1[16], r2[16], i2[16];
+                tmem_ld16(d1 + c0, r1);
+                tmem_ld16(d1 + D + c0, i1);
+                tmem_ld16(d2 + c0, r2);
+                tmem_ld16(d2 + D + c0, i2);
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    float2 o;
+                    o.x = fmaf(__uint_as_float(r2[u]), lo_scale, __uint_as_float(r1[u])) * mul;
+                    o.y = fmaf(__uint_as_float(i2[u]), lo_scale, __uint_as_float(i1[u])) * mul;
+                    const int i = ib + g.toff[c0 + u];
+                    state[gb + g.runoff[i >> g.c] + (i & cmask)] = o;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bar[2 + buf]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, Lay::kTmemCols);
+}
+
+// ----------------------------------------------------------------------------
+// host side
+// ----------------------------------------------------------------------------
+// Real representation of M (D x D complex, row-major interleaved), scaled by
+// a power of two, split into hi/lo and laid out as the K-major B operand:
+// row j = output component, column kk = input component.
+template <bool BF16>
+static float prepare_b(int k, const double *mat, std::vector<uint16_t> &out)
+{
+    const int D = 1 << k, D2 = 2 * D;
+    double mx = 0;
+    for (int i = 0; i < 2 * D * D; ++i) mx = std::max(mx, std::fabs(mat[i]));
+    int e = 0;
+    std::frexp(mx > 0 ? mx : 1.0, &e);
+    const double sm = std::ldexp(1.0, 14 - e);
+    out.assign(size_t(2) * D2 * D2, 0);
+    uint16_t *hi = out.data(), *lo = out.data() + size_t(D2) * D2;
+    const float lo_mul = BF16 ? 256.f : 2048.f;
+    for (int j = 0; j < D2; ++j)
+        for (int kk = 0; kk < D2; ++kk) {
+            const int r = j % D, c = kk % D;
+            const double mr = mat[2 * (r * D + c)], mi = mat[2 * (r * D + c) + 1];
+            double v;
+            if (j < D) v = (kk < D) ? mr : -mi;
+            else v = (kk < D) ? mi : mr;
+            const float f = float(v * sm);
+            uint16_t h, l;
+            if (BF16) {
+                const __nv_bfloat16 bh = __float2bfloat16_rn(f);
+                const __nv_bfloat16 bl = __float2bfloat16_rn((f - __bfloat162float(bh)) * lo_mul);
+                h = __bfloat16_as_ushort(bh);
+                l = __bfloat16_as_ushort(bl);
+            } else {
+                const __half hh = __float2half_rn(f);
+                const __half hl = __float2half_rn((f - __half2float(hh)) * lo_mul);
+                h = __half_as_ushort(hh);
+                l = __half_as_ushort(hl);
+            }
+            const uint32_t off = core_off(j, kk, D2) / 2;
+            hi[off] = h;
+            lo[off] = l;
+        }
+    return float(1.0 / sm);
+}
+
+template <int K, bool BF16>
+static hq_status run_tc(void *state, int n, const int *qubits, const double *mat, int64_t nstates, cudaStream_t s)
+{
+    using Lay = TcLayout<K, BF16>;
+    TcParams p;
+    make_geom(p.g, n, K, qubits, K + 7, nstates);
+    std::vector<uint16_t> hb;
+    p.out_mul = prepare_b<BF16>(K, mat, hb);
+    uint4 *dmat = nullptr;
+    const size_t bytes = hb.size() * sizeof(uint16_t);
+    if (cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
+    hq_status st = cuda_status("copy split matrix", cudaMemcpyAsync(dmat, hb.data(), bytes, cudaMemcpyHostToDevice, s));
+    if (st == HQ_OK) {
+        p.bmat = dmat;
+        const void *fn = (const void *)k_tc<K, BF16>;
+        const int grid = grid_for(fn, kTcThreads, Lay::kBytes, p.g.total_tiles);
+        k_tc<K, BF16><<<grid, kTcThreads, Lay::kBytes, s>>>(p, (float2 *)state);
+        st = cuda_status("k_tc", cudaGetLastError());
+    }
+    cudaFreeAsync(dmat, s);
+    return st;
+}
+
+hq_status launch_tc_block(void *state, int n, int k, const int *qubits, const double *matrix, int64_t nstates,
+                          int split_bf16, cudaStream_t s)
+{
+    if (k == 5) return split_bf16 ? run_tc<5, true>(state, n, qubits, matrix, nstates, s)
+                                  : run_tc<5, false>(state, n, qubits, matrix, nstates, s);
+    if (k == 6) return split_bf16 ? run_tc<6, true>(state, n, qubits, matrix, nstates, s)
+                                  : run_tc<6, false>(state, n, qubits, matrix, nstates, s);
+    return HQ_ERR_K_TOO_LARGE;
+}
+
+hq_status device_error_status()
+{
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_error, sizeof(v));
+    if (e != cudaSuccess) return cuda_status("read device error flag", e);
+    if (v) {
+        const unsigned int zero = 0;
+        cudaMemcpyToSymbol(g_device_error, &zero, sizeof(zero));
+        return HQ_ERR_TIMEOUT;
+    }
+    return HQ_OK;
 }
 
 }  // namespace hq

@@ -1,0 +1,150 @@
+"""Tensor-core engine (tcgen05, split FP16/BF16 products, FP32 accumulate) for
+fused k = 5, 6 blocks, against the oracle.  FP16 hi+lo must meet the complex64
+bar (relative L2 <= 2e-5 per 1000 unfused gates); BF16 hi+lo has ~16
+significant bits and only its measured error is checked against a loose
+bound."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_06868_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2111_06868_gb300 import build
+    from paper_2111_06868_gb300 import hq as _hq
+
+    build.build()
+    _hq.load()
+    return _hq
+
+
+def random_state(n, seed):
+    rng = np.random.default_rng(seed)  # input only
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    return psi / np.linalg.norm(psi)
+
+
+def rel_l2(got, want):
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+
+def qsets(n, k, seed):
+    rng = C.SplitMix64(seed)
+    rnd = []
+    while len(rnd) < k:
+        q = rng.randint(0, n - 1)
+        if q not in rnd:
+            rnd.append(q)
+    return [list(range(n - k, n)), list(range(k)), rnd, [n - 1, 0] + list(range(1, k - 1))[::-1]]
+
+
+@pytest.mark.parametrize("engine,tol", [("tc_f16", 2e-6), ("tc_bf16", 3e-4)])
+@pytest.mark.parametrize("k", [5, 6])
+@pytest.mark.parametrize("n", [13, 16, 20])
+def test_single_block_every_position_class(hq, engine, tol, k, n):
+    if n < k + 7:
+        pytest.skip()
+    rng = C.SplitMix64(31 * n + k)
+    psi = random_state(n, n + k)
+    st = torch.from_numpy(psi).to(torch.complex64).cuda()
+    for qs in qsets(n, k, 7 * n + k):
+        M = C.random_unitary(k, rng)
+        hq.hq_apply_blocks(st, [(qs, M)], engine=engine)
+        oracle.apply_gate(psi, n, qs, M)
+        err = rel_l2(st.cpu().numpy().astype(np.complex128), psi)
+        assert err <= tol, (qs, err)
+
+
+@pytest.mark.parametrize("scale", [1e-3, 37.0])
+def test_non_unitary_scaling(hq, scale):
+    n, k = 14, 6
+    rng = C.SplitMix64(5)
+    M = scale * C.random_unitary(k, rng)
+    psi = random_state(n, 3)
+    st = torch.from_numpy(psi).to(torch.complex64).cuda()
+    qs = [2, 9, 4, 13, 0, 7]
+    hq.hq_apply_blocks(st, [(qs, M)], engine="tc_f16")
+    oracle.apply_gate(psi, n, qs, M)
+    assert rel_l2(st.cpu().numpy().astype(np.complex128), psi) <= 2e-6
+
+
+def test_sparse_state_zero_groups(hq):
+    """|0..0> leaves almost every group all-zero (scale 1 path)."""
+    n = 16
+    rng = C.SplitMix64(8)
+    st = torch.zeros(1 << n, dtype=torch.complex64, device="cuda")
+    hq.hq_state_init(st)
+    psi = oracle.state_init(n)
+    for qs in ([0, 3, 5, 8, 11, 15], [15, 14, 13, 12, 11]):
+        M = C.random_unitary(len(qs), rng)
+        hq.hq_apply_blocks(st, [(qs, M)], engine="tc_f16")
+        oracle.apply_gate(psi, n, qs, M)
+    assert rel_l2(st.cpu().numpy().astype(np.complex128), psi) <= 2e-6
+
+
+@pytest.mark.parametrize("kmax", [5, 6])
+def test_fused_grid_circuit_fp16_meets_complex64_bar(hq, kmax):
+    circ = C.random_circuit(C.grid(4, 5), 16, seed=3, two_qubit="fsim")
+    want = oracle.simulate(circ)
+    blocks = hq.hq_fuse(circ.n, circ.gates, kmax)
+    st = torch.empty(1 << circ.n, dtype=torch.complex64, device="cuda")
+    hq.hq_state_init(st)
+    hq.hq_apply_blocks(st, blocks, engine="tc_f16", tc_min_k=5)
+    err = rel_l2(st.cpu().numpy().astype(np.complex128), want)
+    assert err <= 2e-5 * max(1, len(circ.gates) / 1000), err
+
+
+def test_fused_grid_circuit_bf16_error_reported(hq):
+    circ = C.random_circuit(C.grid(4, 5), 16, seed=3, two_qubit="fsim")
+    want = oracle.simulate(circ)
+    st = torch.empty(1 << circ.n, dtype=torch.complex64, device="cuda")
+    hq.hq_state_init(st)
+    hq.hq_apply_blocks(st, hq.hq_fuse(circ.n, circ.gates, 6), engine="tc_bf16", tc_min_k=5)
+    err = rel_l2(st.cpu().numpy().astype(np.complex128), want)
+    print(f"bf16 hi+lo relative L2 error over {len(circ.gates)} gates: {err:.3e}")
+    assert err <= 5e-3
+
+
+@pytest.mark.slow
+def test_n28_subset_against_fp64(hq):
+    """The 28-qubit subset of the 33-qubit layout: tensor-core k=6 blocks in
+    complex64 against the complex128 per-gate path (itself pinned to the oracle
+    at smaller n)."""
+    circ = C.config_n33(seed=0, first=28)
+    G = len(circ.gates)
+    ref = torch.empty(1 << 28, dtype=torch.complex128, device="cuda")
+    hq.hq_state_init(ref)
+    hq.hq_apply_blocks(ref, circ.gates)
+    st = torch.empty(1 << 28, dtype=torch.complex64, device="cuda")
+    hq.hq_state_init(st)
+    hq.hq_apply_blocks(st, hq.hq_fuse(28, circ.gates, 6), engine="tc_f16")
+    d = (st.to(torch.complex128) - ref).norm().item() / ref.norm().item()
+    print(f"n=28 subset, {G} gates, tc_f16 k<=6 vs complex128: rel L2 {d:.3e}")
+    assert d <= 2e-5 * max(1, G / 1000)
+    del st, ref
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.slow
+def test_n33_tc_norm_and_inverse(hq):
+    circ = C.config_n33(seed=0)
+    G = len(circ.gates)
+    blocks = hq.hq_fuse(33, circ.gates, 6)
+    st = torch.empty(1 << 33, dtype=torch.complex64, device="cuda")
+    hq.hq_state_init(st)
+    hq.hq_apply_blocks(st, blocks, engine="tc_f16")
+    nrm = hq.hq_expectation(st, [(1.0, ())])
+    assert abs(nrm - 1) <= 2e-5 * max(1, G / 1000)
+    hq.hq_apply_blocks(st, [(q, m.conj().T.copy()) for q, m in reversed(blocks)], engine="tc_f16")
+    assert abs(complex(st[0].item()) - 1) <= 4e-5 * max(1, 2 * G / 1000)
+    del st
+    torch.cuda.empty_cache()
