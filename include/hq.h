@@ -171,6 +171,32 @@ hq_status hq_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_t
                          double *out_host, void *stream);
 
 /*
+ * hq_expectation_static -- the same result as hq_expectation, computed
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc (or any
+ * allocator) at the point of the call -- for example a host that hands all
+ * device memory to its own pool up front, a serving loop that forbids
+ * allocator calls for predictable latency, or code that must not allocate
+ * while another component is capturing or replaying work on the device.
+ *
+ * The per-block partial sums live in a file-scope device array of
+ * 64 x 512 + 1 doubles (256 KiB + 8 bytes) that every GPU which loads
+ * libhq.so keeps until the process exits.  Limits: at most 64 X-mask groups
+ * after splitting (terms that share their X/Y positions form one group; a
+ * group holds at most 48 terms), otherwise HQ_ERR_CAPACITY with the reason
+ * in hq_last_error(); every other argument rule is that of hq_expectation.
+ * The first call on a device looks up the array's device address (with that
+ * device current) and caches it: make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * each call writes every slot it reads, so no clearing is needed, but calls
+ * whose work overlaps on the GPU (different streams or host threads) race on
+ * it and must be serialised by the caller.  Result written to *out_host;
+ * SYNCHRONISES `stream`.
+ */
+hq_status hq_expectation_static(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,
+                                double *out_host, void *stream);
+
+/*
  * hq_adjoint_workspace_bytes -- device workspace hq_adjoint_grad needs for
  * `batch` parameter sets of an n-qubit, G-operation, P-parameter circuit
  * with `checkpoints` stored forward states per parameter set (0 = none).

@@ -16,6 +16,8 @@ void set_last_error(const char *what, cudaError_t e)
     t_last_error = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
 }
 
+void set_last_error_text(const std::string &text) { t_last_error = text; }
+
 hq_status cuda_status(const char *what, cudaError_t e)
 {
     if (e == cudaSuccess) return HQ_OK;
@@ -161,6 +163,17 @@ hq_status hq_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_t
     if (!out_host) return HQ_ERR_NULL;
     if ((st = check_terms(n, terms, T)) != HQ_OK) return st;
     if ((st = launch_expectation(state, n, dt, terms, T, out_host, (cudaStream_t)stream)) != HQ_OK) return st;
+    return device_error_status();
+}
+
+hq_status hq_expectation_static(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,
+                                double *out_host, void *stream)
+{
+    hq_status st = check_state(state, n, dt);
+    if (st != HQ_OK) return st;
+    if (!out_host) return HQ_ERR_NULL;
+    if ((st = check_terms(n, terms, T)) != HQ_OK) return st;
+    if ((st = launch_expectation_static(state, n, dt, terms, T, out_host, (cudaStream_t)stream)) != HQ_OK) return st;
     return device_error_status();
 }
 

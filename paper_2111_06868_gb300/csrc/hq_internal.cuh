@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/hq.h"
 
 namespace hq {
@@ -12,6 +14,7 @@ namespace hq {
 // error plumbing
 // ----------------------------------------------------------------------------
 void set_last_error(const char *what, cudaError_t e);
+void set_last_error_text(const std::string &text);
 hq_status cuda_status(const char *what, cudaError_t e);  // HQ_OK or HQ_ERR_CUDA
 #define HQ_CUDA(call)                                              \
     do {                                                           \
@@ -169,6 +172,9 @@ hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pau
 // tensor-core block engine (k_tc.cu); complex64 only, k in {5, 6}
 hq_status launch_tc_block(void *state, int n, int k, const int *qubits, const double *matrix, int64_t nstates,
                           int split_bf16, cudaStream_t s);
+
+hq_status launch_expectation_static(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,
+                                    double *out_host, cudaStream_t s);
 
 // HQ_ERR_TIMEOUT (and clears the flag) if a bounded device-side wait ran out
 // since the last call; synchronous.

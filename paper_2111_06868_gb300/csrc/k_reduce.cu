@@ -13,6 +13,8 @@
 // deterministic for a given launch shape.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "hq_internal.cuh"
@@ -212,6 +214,105 @@ hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pau
     if (rc == HQ_OK) rc = cuda_status("sync", cudaStreamSynchronize(s));
     if (rc == HQ_OK) *out_host = result;
     return rc;
+}
+
+// ----------------------------------------------------------------------------
+// Allocation-free variant (hq_expectation_static).
+//
+// Same kernels as hq_expectation, but the per-CTA partial sums live in this
+// file-scope device array instead of stream-ordered scratch, so the call never
+// allocates.  Every GPU that loads libhq.so holds the array until the process
+// exits.  Host code cannot pass the array's name to a kernel (on the host it is
+// only a stand-in for the device symbol), so the first call on each device
+// looks up its device address with cudaGetSymbolAddress, with that device
+// current, and caches it.  All calls share the array and it keeps the last
+// call's contents; every slot a call reads is written by that same call first,
+// so nothing needs clearing.  Calls whose work overlaps on the GPU (other
+// streams, other host threads) race on the array.
+// ----------------------------------------------------------------------------
+constexpr int kStaticMaxGroups = 64;   // X-mask groups (after splitting) per call
+constexpr int kStaticMaxCtas = 512;    // partial sums per group
+constexpr size_t kStaticScratchDoubles = size_t(kStaticMaxGroups) * kStaticMaxCtas + 1;  // 256 KiB + 8 B
+
+static __device__ __align__(256) double g_expect_static_scratch[kStaticScratchDoubles];
+
+static std::mutex g_static_mu;
+static double *g_static_ptr[64] = {nullptr};  // device address of the array, per device ordinal
+
+// Device address of the array for the current device (set-up on first use).
+static hq_status static_scratch(double **out)
+{
+    int dev = 0;
+    hq_status st = cuda_status("cudaGetDevice", cudaGetDevice(&dev));
+    if (st != HQ_OK) return st;
+    if (dev < 0 || dev >= 64) return HQ_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        st = cuda_status("cudaGetSymbolAddress", cudaGetSymbolAddress(&p, g_expect_static_scratch));
+        if (st != HQ_OK) return st;
+        g_static_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return HQ_OK;
+}
+
+hq_status launch_expectation_static(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,
+                                    double *out_host, cudaStream_t s)
+{
+    std::vector<ExpGroup> groups;
+    std::vector<ExpTerm> flat;
+    hq_status st = build_groups(n, terms, T, groups, flat);
+    if (st != HQ_OK) return st;
+    if (int(groups.size()) > kStaticMaxGroups) {
+        set_last_error_text("hq_expectation_static: the Pauli sum needs " + std::to_string(groups.size()) +
+                            " X-mask groups; the static scratch holds at most " + std::to_string(kStaticMaxGroups));
+        return HQ_ERR_CAPACITY;
+    }
+    double *scratch = nullptr;
+    if ((st = static_scratch(&scratch)) != HQ_OK) return st;
+    if (groups.empty()) {
+        *out_host = 0.0;
+        return HQ_OK;
+    }
+    const int64_t dim = int64_t(1) << n;
+    const int gx = int(std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>(2 * sm_count(), kStaticMaxCtas), dim / (kRedThreads * 8))));
+    const size_t npart = size_t(groups.size()) * gx;
+    for (int g0 = 0; g0 < int(groups.size());) {
+        int g1 = g0, nt = 0;
+        while (g1 < int(groups.size()) && g1 - g0 < kMaxGroups && nt + groups[g1].nt <= kMaxTerms) nt += groups[g1++].nt;
+        ExpParams p;
+        std::memset(&p, 0, sizeof(p));
+        p.n = n;
+        p.nstates = 1;
+        p.ngroups = g1 - g0;
+        nt = 0;
+        for (int g = g0; g < g1; ++g) {
+            ExpGroup gg = groups[g];
+            for (int t = 0; t < gg.nt; ++t) p.term[nt + t] = flat[gg.t0 + t];
+            gg.t0 = nt;
+            nt += gg.nt;
+            p.grp[g - g0] = gg;
+        }
+        dim3 grid(gx, p.ngroups);
+        double *part = scratch + size_t(g0) * gx;
+        if (dt == HQ_C64)
+            k_expect<float><<<grid, kRedThreads, 0, s>>>(p, (const float2 *)state, part);
+        else
+            k_expect<double><<<grid, kRedThreads, 0, s>>>(p, (const double2 *)state, part);
+        if ((st = cuda_status("k_expect", cudaGetLastError())) != HQ_OK) return st;
+        g0 = g1;
+    }
+    k_expect_final<<<1, kRedThreads, 0, s>>>(scratch, int(groups.size()), gx, scratch + npart);
+    if ((st = cuda_status("k_expect_final", cudaGetLastError())) != HQ_OK) return st;
+    double result = 0;
+    if ((st = cuda_status("copy result", cudaMemcpyAsync(&result, scratch + npart, sizeof(double),
+                                                         cudaMemcpyDeviceToHost, s))) != HQ_OK)
+        return st;
+    if ((st = cuda_status("sync", cudaStreamSynchronize(s))) != HQ_OK) return st;
+    *out_host = result;
+    return HQ_OK;
 }
 
 }  // namespace hq

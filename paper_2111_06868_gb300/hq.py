@@ -83,6 +83,7 @@ def load(path: str | None = None):
         "hq_apply_gate": ([V, I, I, V, I, V, V], I),
         "hq_apply_blocks": ([V, I, I, V, I, V, V], I),
         "hq_expectation": ([V, I, I, V, I, P(D), V], I),
+        "hq_expectation_static": ([V, I, I, V, I, P(D), V], I),
         "hq_adjoint_workspace_bytes": ([I, I, I, I, I, I], ctypes.c_size_t),
         "hq_adjoint_grad": ([I, I, V, I, I, V, I, V, I, ctypes.c_char_p, I, V, ctypes.c_size_t, V, V, V], I),
     }
@@ -235,6 +236,19 @@ def hq_expectation(state, H, stream=None) -> float:
     arr, T = _terms_array(H)
     out = ctypes.c_double(0.0)
     _check(load().hq_expectation(ptr, n, dt, arr, T, ctypes.byref(out), _stream(stream)), "hq_expectation")
+    return out.value
+
+
+def hq_expectation_static(state, H, stream=None) -> float:
+    """hq_expectation without any device allocation (shared static scratch;
+    see include/hq.h for its limits and the rule on overlapping calls)."""
+    ptr, n, dt = _state_args(state)
+    arr, T = _terms_array(H)
+    out = ctypes.c_double(0.0)
+    st = load().hq_expectation_static(ptr, n, dt, arr, T, ctypes.byref(out), _stream(stream))
+    if st == -11:
+        raise HQError(st, "hq_expectation_static", load().hq_last_error().decode())
+    _check(st, "hq_expectation_static")
     return out.value
 
 
