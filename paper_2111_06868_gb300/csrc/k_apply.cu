@@ -425,15 +425,15 @@ static hq_status dispatch(void *state, int n, int k, const int *qubits, const do
         case 6: return run_diag<R, 6>(state, n, qubits, mat, nstates, s);
         }
     }
+    // the tensor-core engine needs at least one full tile of 128 groups
+    if (sizeof(R) == 4 && (engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16) && k >= 4 && n >= k + 7)
+        return launch_tc_block(state, n, k, qubits, mat, nstates, engine == HQ_ENGINE_TC_BF16, s);
     switch (k) {
     case 1: return run_gather<R, 1>(state, n, qubits, mat, nstates, s);
     case 2: return run_gather<R, 2>(state, n, qubits, mat, nstates, s);
     case 3: return run_gather<R, 3>(state, n, qubits, mat, nstates, s);
     case 4: return run_gather<R, 4>(state, n, qubits, mat, nstates, s);
     }
-    // the tensor-core engine needs at least one full tile of 128 groups
-    if (sizeof(R) == 4 && (engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16) && n >= k + 7)
-        return launch_tc_block(state, n, k, qubits, mat, nstates, engine == HQ_ENGINE_TC_BF16, s);
     if (k == 5) return run_block<R, 5>(state, n, qubits, mat, nstates, s);
     return run_block<R, 6>(state, n, qubits, mat, nstates, s);
 }

@@ -1,33 +1,41 @@
-// k_tc.cu -- tensor-core engine for fused k = 5, 6 blocks on complex64 states.
+// k_tc.cu -- tensor-core engine for fused k = 4, 5, 6 blocks on complex64 states.
 //
 // Sec. 3.1's compress() fuses gates into wide blocks because wide gates use the
 // hardware's vector units better; on GB300 the unit for a dense 2^k x 2^k block
 // is the 5th-generation tensor core.  One block application is the real GEMM
 //     D[n][j] = sum_kk A[n][kk] B[kk][j]
 // with n = one group of 2^k amplitudes that differ only in the target bits
-// (128 groups per tile = MMA M), kk = input components (Re x_0..x_{D-1},
-// Im x_0..x_{D-1}), j = output components in the same order, and B the real
-// representation [[Mr, -Mi], [Mi, Mr]] of the block matrix (D = 2^k).
+// (128 groups per tile = MMA M), kk = 2c + {0, 1} the real and imaginary part
+// of input amplitude c, j = 2r + {0, 1} those of output amplitude r, and B the
+// real representation of the block matrix (Re = Mr Re x - Mi Im x,
+// Im = Mi Re x + Mr Im x).  D = 2^k; the GEMM is M = 128, N = K = 2D.
 //
 // Precision: FP16 (or BF16) operands, FP32 accumulation, split products.  Each
 // group is scaled by a power of two s_n that brings its largest component to
-// [2^13, 2^14); hi = f16(x s), lo = f16((x s - hi) 2^11) (2^8 for BF16), and
-// the matrix likewise (one scale).  Three products are kept:
-//     D1 = A_hi B_hi,   D2 = A_hi B_lo + A_lo B_hi,   out = (D1 + 2^-11 D2) / (s_n s_M)
-// (the lo*lo term, ~2^-22 relative, is dropped).
+// [2^13, 2^14), the matrix by one power of two s_M likewise; hi = round(v),
+// lo = round(v - hi) (the residual stays in FP16's normal range at that
+// scale).  One FP32 accumulator takes the three products
+//     D = (A_hi B_lo + A_lo B_hi) + A_hi B_hi,     out = D / (s_n s_M)
+// with the small cross terms accumulated first (the lo*lo term, ~2^-22
+// relative, is dropped).
 //
-// Kernel shape (persistent, 1 CTA per SM for k = 6, 2 for k = 5; 256 threads):
-//   warps 0-3  producers: thread p loads group p of a tile straight from HBM into
-//              registers (lanes = consecutive groups, so each load instruction is
-//              coalesced), splits and stores it as row p of A_hi / A_lo in the
-//              K-major no-swizzle core-matrix layout; thread 0 then issues the
-//              tcgen05.mma sequence and commits it to an mbarrier.
-//   warps 4-7  epilogue: wait for the MMAs of a tile, tcgen05.ld their TMEM lanes
-//              (lane = group), combine, unscale and store the outputs to HBM.
-//   A and the TMEM accumulators are double-buffered, so loads of tile t+1
-//   overlap the MMAs and epilogue of tile t.  Every wait is bounded by a
-//   %globaltimer deadline; on expiry the kernel raises a device error flag
-//   (read back as HQ_ERR_TIMEOUT), leaves its loops and frees its TMEM.
+// Kernel shape (persistent; 256 threads; 1, 2 or 4 CTAs per SM for k = 6, 5, 4
+// so that the CTAs' TMEM fits the SM's 512 columns):
+//   warps 0-3  producers: thread p owns group p of every tile.  It copies the
+//              group's amplitudes for the NEXT tile into its own padded row of
+//              a shared-memory staging buffer with 8-byte cp.async (lanes =
+//              consecutive groups, so each copy instruction is coalesced, and
+//              the data in flight holds no registers), then splits the current
+//              tile's row and writes it to TMEM lane p (tcgen05.st) as the A
+//              operand.  Thread 0 issues the tcgen05.mma sequence (A from TMEM,
+//              B from shared memory) and commits it to an mbarrier.
+//   warps 4-7  epilogue: wait for a tile's MMAs, tcgen05.ld its TMEM lanes
+//              (lane = group), unscale and store the outputs to HBM.
+//   Staging, TMEM operands and accumulators are double-buffered, so the loads
+//   of tile t+1, the MMAs of tile t and the stores of tile t-1 overlap.  Every
+//   wait is bounded by a %globaltimer deadline; on expiry the kernel raises a
+//   device error flag (read back as HQ_ERR_TIMEOUT), leaves its loops, waits
+//   for its own copies and MMAs, and frees its TMEM.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -120,29 +128,52 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
 {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
 __device__ __forceinline__ void mma_commit(uint64_t *bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate)
 {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src)
+{
+    asm volatile("{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %1;\n\tcp.async.ca.shared.global [%0], [g], 8;\n\t}" ::"r"(dst),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: K-major, no swizzle.  Core matrices are 8
 // rows x 16 bytes; LBO = byte step between core matrices along K, SBO = byte
@@ -167,25 +198,24 @@ __host__ __device__ __forceinline__ uint32_t core_off(int row, int kk, int Kdim)
     return uint32_t((row >> 3) * (Kdim * 16) + (kk >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
 }
 
+// hi = round(v), lo = round(v - hi), packed in pairs (16-bit each)
 template <bool BF16> struct Split;
 template <> struct Split<false> {
-    static constexpr float lo_mul = 2048.f;
     __device__ static uint32_t pack(float a, float b, uint32_t &lo)
     {
         const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
-        const __half la = __float2half_rn((a - __half2float(ha)) * lo_mul);
-        const __half lb = __float2half_rn((b - __half2float(hb)) * lo_mul);
+        const __half la = __float2half_rn(a - __half2float(ha));
+        const __half lb = __float2half_rn(b - __half2float(hb));
         lo = uint32_t(__half_as_ushort(la)) | (uint32_t(__half_as_ushort(lb)) << 16);
         return uint32_t(__half_as_ushort(ha)) | (uint32_t(__half_as_ushort(hb)) << 16);
     }
 };
 template <> struct Split<true> {
-    static constexpr float lo_mul = 256.f;
     __device__ static uint32_t pack(float a, float b, uint32_t &lo)
     {
         const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-        const __nv_bfloat16 la = __float2bfloat16_rn((a - __bfloat162float(ha)) * lo_mul);
-        const __nv_bfloat16 lb = __float2bfloat16_rn((b - __bfloat162float(hb)) * lo_mul);
+        const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+        const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
         lo = uint32_t(__bfloat16_as_ushort(la)) | (uint32_t(__bfloat16_as_ushort(lb)) << 16);
         return uint32_t(__bfloat16_as_ushort(ha)) | (uint32_t(__bfloat16_as_ushort(hb)) << 16);
     }
@@ -197,25 +227,30 @@ struct TcParams {
     float out_mul;            // 1 / s_M
 };
 
-template <int K, bool BF16>
+template <int K>
 struct TcLayout {
     static constexpr int D = 1 << K;
     static constexpr int D2 = 2 * D;                          // GEMM K and N
     static constexpr int kBBytes = D2 * D2 * 2;               // one of B_hi / B_lo
-    static constexpr int kABytes = kTcGroups * D2 * 2;        // one of A_hi / A_lo
-    static constexpr int kOffBhi = 0, kOffBlo = kBBytes;
-    static constexpr int kOffA = 2 * kBBytes;                 // A[buf][hi/lo]
-    static constexpr int kOffScale = kOffA + 4 * kABytes;     // float[2][128]
+    static constexpr int kRowStride = D * 8 + 8;              // staging bytes per group (padded: 2-way banks)
+    static constexpr int kStageBytes = kTcGroups * kRowStride;
+    static constexpr int kOffStage = 2 * kBBytes;             // stage[2]
+    static constexpr int kOffScale = kOffStage + 2 * kStageBytes;  // float[2][128]
     static constexpr int kOffBar = kOffScale + 2 * kTcGroups * 4;  // mma_done[2], acc_free[2]
     static constexpr int kOffMisc = kOffBar + 4 * 8;          // tmem addr, abort flag
     static constexpr int kBytes = kOffMisc + 16;
-    static constexpr uint32_t kTmemCols = 4 * D2;             // (D1, D2) x 2 buffers
+    // TMEM per buffer: A_hi (D cols), A_lo (D cols), accumulator (2D cols)
+    static constexpr uint32_t kBufCols = 4 * D;
+    static constexpr uint32_t kTmemCols = 2 * kBufCols;       // 128 (k=4), 256 (k=5), 512 (k=6)
+    static constexpr int kCtasPerSm = int(512 / kTmemCols);   // TMEM-bound residency
 };
 
+template <int K> __host__ __device__ constexpr int tc_min_blocks() { return K == 6 ? 1 : (K == 5 ? 2 : 4); }
+
 template <int K, bool BF16>
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcParams p, float2 *__restrict__ state)
+__global__ void __launch_bounds__(kTcThreads, tc_min_blocks<K>()) k_tc(const TcParams p, float2 *__restrict__ state)
 {
-    using Lay = TcLayout<K, BF16>;
+    using Lay = TcLayout<K>;
     constexpr int D = Lay::D, D2 = Lay::D2;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Lay::kOffBar);  // [0,1] mma_done, [2,3] acc_free
@@ -247,67 +282,87 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcParams p, float2 *
 
     if (warp < 4) {
         // ---------------- producers + MMA issue ----------------
-        const int n = tid;  // group within the tile
+        const int n = tid;  // group within the tile = TMEM lane
+        const uint32_t lane_off = uint32_t(warp * 32) << 16;
+        const uint32_t stage0 = smem_base + Lay::kOffStage + uint32_t(n * Lay::kRowStride);
+        const unsigned char *my_stage[2] = {smem + Lay::kOffStage + n * Lay::kRowStride,
+                                            smem + Lay::kOffStage + Lay::kStageBytes + n * Lay::kRowStride};
         constexpr uint32_t idesc = instr_desc(kTcGroups, D2, BF16);
-        int it = 0, issued = 0;
-        for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
-            const int buf = it & 1;
+        // this thread's group of tile t -> its staging row
+        auto issue = [&](int64_t t, int sb) {
             const int64_t gb = tile_base(g, t);
             const int ib = group_base<K>(g, n);
-            float2 x[D];
+            const uint32_t dst = stage0 + uint32_t(sb * Lay::kStageBytes);
 #pragma unroll
             for (int r = 0; r < D; ++r) {
                 const int i = ib + g.toff[r];
-                x[r] = state[gb + g.runoff[i >> g.c] + (i & cmask)];
+                cp_async8(dst + uint32_t(r * 8), state + gb + g.runoff[i >> g.c] + (i & cmask));
             }
+        };
+        if (int64_t(blockIdx.x) < g.total_tiles) issue(blockIdx.x, 0);
+        cp_async_commit();
+        int it = 0, issued = 0;
+        for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
+            const int buf = it & 1;
+            if (t + gridDim.x < g.total_tiles) issue(t + gridDim.x, buf ^ 1);
+            cp_async_commit();
+            cp_async_wait1();  // this thread's copies for tile t have landed
+            const float2 *x = reinterpret_cast<const float2 *>(my_stage[buf]);
             float m = 0.f;
 #pragma unroll
-            for (int r = 0; r < D; ++r) m = fmaxf(m, fmaxf(fabsf(x[r].x), fabsf(x[r].y)));
+            for (int r = 0; r < D; ++r) {
+                const float2 v = x[r];
+                m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
             int e = 0;
             frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
             const float s = (m > 0.f) ? ldexpf(1.f, 14 - e) : 1.f;
-            // A[buf] is free once the epilogue of tile it-2 released its accumulators
+            // TMEM buffer `buf` is free once the epilogue of tile it-2 released it
             const bool ok = it < 2 || mbar_wait(&bar[2 + buf], uint32_t((it / 2 - 1) & 1), abort_flag);
             if (ok) {
-                unsigned char *ahi = smem + Lay::kOffA + buf * 2 * Lay::kABytes;
-                unsigned char *alo = ahi + Lay::kABytes;
+                const uint32_t a_hi = tmem + lane_off + uint32_t(buf) * Lay::kBufCols;
+                const uint32_t a_lo = a_hi + uint32_t(D);
 #pragma unroll
-                for (int ch = 0; ch < D2 / 8; ++ch) {
-                    uint32_t hv[4], lv[4];
+                for (int c0 = 0; c0 < D; c0 += 16) {
+                    uint32_t hv[16], lv[16];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int k0 = ch * 8 + 2 * q;  // components k0, k0 + 1
-                        const float a = (k0 < D ? x[k0 % D].x : x[k0 % D].y) * s;
-                        const float b = (k0 + 1 < D ? x[(k0 + 1) % D].x : x[(k0 + 1) % D].y) * s;
-                        hv[q] = Split<BF16>::pack(a, b, lv[q]);
+                    for (int u = 0; u < 16; ++u) {
+                        const float2 v = x[c0 + u];
+                        hv[u] = Split<BF16>::pack(v.x * s, v.y * s, lv[u]);
                     }
-                    const uint32_t off = core_off(n, ch * 8, D2);
-                    *reinterpret_cast<uint4 *>(ahi + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                    *reinterpret_cast<uint4 *>(alo + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+                    tmem_st16(a_hi + uint32_t(c0), hv);
+                    tmem_st16(a_lo + uint32_t(c0), lv);
                 }
+                tmem_wait_st();
                 inv_scale[buf * kTcGroups + n] = 1.f / s;
-                fence_proxy_async();
             }
+            tc_fence_before();
             // every producer takes the same exit decision
             if (named_bar_or(1, kTcGroups, !ok || *abort_flag)) break;
             if (n == 0) {
                 tc_fence_after();
-                const uint32_t a_hi = smem_base + Lay::kOffA + buf * 2 * Lay::kABytes;
-                const uint32_t a_lo = a_hi + Lay::kABytes;
-                const uint32_t b_hi = smem_base + Lay::kOffBhi, b_lo = smem_base + Lay::kOffBlo;
-                const uint32_t d1 = tmem + uint32_t(buf * 2 * D2), d2 = d1 + uint32_t(D2);
+                const uint32_t a_hi = tmem + uint32_t(buf) * Lay::kBufCols;
+                const uint32_t a_lo = a_hi + uint32_t(D);
+                const uint32_t acc = a_hi + uint32_t(2 * D);
+                const uint32_t b_hi = smem_base, b_lo = smem_base + Lay::kBBytes;
                 constexpr uint32_t sbo = D2 * 16;
+                // The small cross terms go first, into a still-small accumulator, so
+                // their low bits survive; the large hi*hi products are added last.
 #pragma unroll
                 for (int kk = 0; kk < D2 / 16; ++kk) {
-                    const uint32_t o = uint32_t(kk) * 256u;
-                    mma_f16(d1, smem_desc(a_hi + o, 128, sbo), smem_desc(b_hi + o, 128, sbo), idesc, kk > 0);
-                    mma_f16(d2, smem_desc(a_hi + o, 128, sbo), smem_desc(b_lo + o, 128, sbo), idesc, kk > 0);
-                    mma_f16(d2, smem_desc(a_lo + o, 128, sbo), smem_desc(b_hi + o, 128, sbo), idesc, 1);
+                    const uint32_t bo = uint32_t(kk) * 256u;  // two 16-byte K chunks
+                    const uint32_t ac = uint32_t(kk) * 8u;    // 16 halves = 8 TMEM columns
+                    mma_ts(acc, a_hi + ac, smem_desc(b_lo + bo, 128, sbo), idesc, kk > 0);
+                    mma_ts(acc, a_lo + ac, smem_desc(b_hi + bo, 128, sbo), idesc, 1);
                 }
+#pragma unroll
+                for (int kk = 0; kk < D2 / 16; ++kk)
+                    mma_ts(acc, a_hi + uint32_t(kk) * 8u, smem_desc(b_hi + uint32_t(kk) * 256u, 128, sbo), idesc, 1);
                 mma_commit(&bar[buf]);
             }
             ++issued;
         }
+        cp_async_wait0();  // no copy may land after the CTA exits
         // drain: the last commit of each buffer must land before TMEM is freed
         if (n == 0) {
             volatile int no_abort = 0;
@@ -320,7 +375,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcParams p, float2 *
         // ---------------- epilogue ----------------
         const int n = tid - kTcGroups;            // group = TMEM lane
         const uint32_t lane_off = uint32_t((warp - 4) * 32) << 16;
-        constexpr float lo_scale = 1.f / Split<BF16>::lo_mul;
         int it = 0;
         for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
             const int buf = it & 1;
@@ -330,21 +384,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcParams p, float2 *
             const float mul = inv_scale[buf * kTcGroups + n] * p.out_mul;
             const int64_t gb = tile_base(g, t);
             const int ib = group_base<K>(g, n);
-            const uint32_t d1 = tmem + lane_off + uint32_t(buf * 2 * D2), d2 = d1 + uint32_t(D2);
+            const uint32_t acc = tmem + lane_off + uint32_t(buf) * Lay::kBufCols + uint32_t(2 * D);
 #pragma unroll
-            for (int c0 = 0; c0 < D; c0 += 16) {
-                uint32_t r1[16], i1[16], r2[16], i2[16];
-                tmem_ld16(d1 + c0, r1);
-                tmem_ld16(d1 + D + c0, i1);
-                tmem_ld16(d2 + c0, r2);
-                tmem_ld16(d2 + D + c0, i2);
+            for (int c0 = 0; c0 < D2; c0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(acc + uint32_t(c0), v);
                 tmem_wait_ld();
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     float2 o;
-                    o.x = fmaf(__uint_as_float(r2[u]), lo_scale, __uint_as_float(r1[u])) * mul;
-                    o.y = fmaf(__uint_as_float(i2[u]), lo_scale, __uint_as_float(i1[u])) * mul;
-                    const int i = ib + g.toff[c0 + u];
+                    o.x = __uint_as_float(v[2 * u]) * mul;
+                    o.y = __uint_as_float(v[2 * u + 1]) * mul;
+                    const int i = ib + g.toff[c0 / 2 + u];
                     state[gb + g.runoff[i >> g.c] + (i & cmask)] = o;
                 }
             }
@@ -361,9 +412,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc(const TcParams p, float2 *
 // ----------------------------------------------------------------------------
 // host side
 // ----------------------------------------------------------------------------
-// Real representation of M (D x D complex, row-major interleaved), scaled by
-// a power of two, split into hi/lo and laid out as the K-major B operand:
-// row j = output component, column kk = input component.
+// Real representation of M (D x D complex, row-major interleaved) with
+// interleaved components: input kk = 2c + {0: Re x_c, 1: Im x_c}, output
+// j = 2r + {0: Re, 1: Im}.  Scaled by a power of two, split into hi and lo,
+// laid out as the K-major B operand (row j, column kk).
 template <bool BF16>
 static float prepare_b(int k, const double *mat, std::vector<uint16_t> &out)
 {
@@ -375,26 +427,23 @@ static float prepare_b(int k, const double *mat, std::vector<uint16_t> &out)
     const double sm = std::ldexp(1.0, 14 - e);
     out.assign(size_t(2) * D2 * D2, 0);
     uint16_t *hi = out.data(), *lo = out.data() + size_t(D2) * D2;
-    const float lo_mul = BF16 ? 256.f : 2048.f;
     for (int j = 0; j < D2; ++j)
         for (int kk = 0; kk < D2; ++kk) {
-            const int r = j % D, c = kk % D;
+            const int r = j >> 1, c = kk >> 1;
             const double mr = mat[2 * (r * D + c)], mi = mat[2 * (r * D + c) + 1];
             double v;
-            if (j < D) v = (kk < D) ? mr : -mi;
-            else v = (kk < D) ? mi : mr;
+            if ((j & 1) == 0) v = (kk & 1) ? -mi : mr;  // Re out = Mr Re x - Mi Im x
+            else v = (kk & 1) ? mr : mi;                // Im out = Mi Re x + Mr Im x
             const float f = float(v * sm);
             uint16_t h, l;
             if (BF16) {
                 const __nv_bfloat16 bh = __float2bfloat16_rn(f);
-                const __nv_bfloat16 bl = __float2bfloat16_rn((f - __bfloat162float(bh)) * lo_mul);
                 h = __bfloat16_as_ushort(bh);
-                l = __bfloat16_as_ushort(bl);
+                l = __bfloat16_as_ushort(__float2bfloat16_rn(f - __bfloat162float(bh)));
             } else {
                 const __half hh = __float2half_rn(f);
-                const __half hl = __float2half_rn((f - __half2float(hh)) * lo_mul);
                 h = __half_as_ushort(hh);
-                l = __half_as_ushort(hl);
+                l = __half_as_ushort(__float2half_rn(f - __half2float(hh)));
             }
             const uint32_t off = core_off(j, kk, D2) / 2;
             hi[off] = h;
@@ -406,7 +455,7 @@ static float prepare_b(int k, const double *mat, std::vector<uint16_t> &out)
 template <int K, bool BF16>
 static hq_status run_tc(void *state, int n, const int *qubits, const double *mat, int64_t nstates, cudaStream_t s)
 {
-    using Lay = TcLayout<K, BF16>;
+    using Lay = TcLayout<K>;
     TcParams p;
     make_geom(p.g, n, K, qubits, K + 7, nstates);
     std::vector<uint16_t> hb;
@@ -417,9 +466,14 @@ static hq_status run_tc(void *state, int n, const int *qubits, const double *mat
     hq_status st = cuda_status("copy split matrix", cudaMemcpyAsync(dmat, hb.data(), bytes, cudaMemcpyHostToDevice, s));
     if (st == HQ_OK) {
         p.bmat = dmat;
+        // Dynamic shared memory is padded so that no more CTAs share an SM than
+        // its 512 TMEM columns hold (an allocation beyond that would stall).
+        constexpr size_t kSmPerSm = 228 * 1024;
+        const size_t smem = std::max<size_t>(Lay::kBytes, kSmPerSm / (Lay::kCtasPerSm + 1) + 1024);
         const void *fn = (const void *)k_tc<K, BF16>;
-        const int grid = grid_for(fn, kTcThreads, Lay::kBytes, p.g.total_tiles);
-        k_tc<K, BF16><<<grid, kTcThreads, Lay::kBytes, s>>>(p, (float2 *)state);
+        const int per_sm = std::min(occupancy(fn, kTcThreads, smem), Lay::kCtasPerSm);
+        const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(sm_count()) * per_sm, p.g.total_tiles)));
+        k_tc<K, BF16><<<grid, kTcThreads, smem, s>>>(p, (float2 *)state);
         st = cuda_status("k_tc", cudaGetLastError());
     }
     cudaFreeAsync(dmat, s);
@@ -429,10 +483,14 @@ static hq_status run_tc(void *state, int n, const int *qubits, const double *mat
 hq_status launch_tc_block(void *state, int n, int k, const int *qubits, const double *matrix, int64_t nstates,
                           int split_bf16, cudaStream_t s)
 {
-    if (k == 5) return split_bf16 ? run_tc<5, true>(state, n, qubits, matrix, nstates, s)
-                                  : run_tc<5, false>(state, n, qubits, matrix, nstates, s);
-    if (k == 6) return split_bf16 ? run_tc<6, true>(state, n, qubits, matrix, nstates, s)
-                                  : run_tc<6, false>(state, n, qubits, matrix, nstates, s);
+    switch (k) {
+    case 4: return split_bf16 ? run_tc<4, true>(state, n, qubits, matrix, nstates, s)
+                              : run_tc<4, false>(state, n, qubits, matrix, nstates, s);
+    case 5: return split_bf16 ? run_tc<5, true>(state, n, qubits, matrix, nstates, s)
+                              : run_tc<5, false>(state, n, qubits, matrix, nstates, s);
+    case 6: return split_bf16 ? run_tc<6, true>(state, n, qubits, matrix, nstates, s)
+                              : run_tc<6, false>(state, n, qubits, matrix, nstates, s);
+    }
     return HQ_ERR_K_TOO_LARGE;
 }
 

@@ -48,7 +48,7 @@ def qsets(n, k, seed):
 
 
 @pytest.mark.parametrize("engine,tol", [("tc_f16", 2e-6), ("tc_bf16", 3e-4)])
-@pytest.mark.parametrize("k", [5, 6])
+@pytest.mark.parametrize("k", [4, 5, 6])
 @pytest.mark.parametrize("n", [13, 16, 20])
 def test_single_block_every_position_class(hq, engine, tol, k, n):
     if n < k + 7:
@@ -58,7 +58,7 @@ def test_single_block_every_position_class(hq, engine, tol, k, n):
     st = torch.from_numpy(psi).to(torch.complex64).cuda()
     for qs in qsets(n, k, 7 * n + k):
         M = C.random_unitary(k, rng)
-        hq.hq_apply_blocks(st, [(qs, M)], engine=engine)
+        hq.hq_apply_blocks(st, [(qs, M)], engine=engine, tc_min_k=4)
         oracle.apply_gate(psi, n, qs, M)
         err = rel_l2(st.cpu().numpy().astype(np.complex128), psi)
         assert err <= tol, (qs, err)
@@ -91,14 +91,14 @@ def test_sparse_state_zero_groups(hq):
     assert rel_l2(st.cpu().numpy().astype(np.complex128), psi) <= 2e-6
 
 
-@pytest.mark.parametrize("kmax", [5, 6])
+@pytest.mark.parametrize("kmax", [4, 5, 6])
 def test_fused_grid_circuit_fp16_meets_complex64_bar(hq, kmax):
     circ = C.random_circuit(C.grid(4, 5), 16, seed=3, two_qubit="fsim")
     want = oracle.simulate(circ)
     blocks = hq.hq_fuse(circ.n, circ.gates, kmax)
     st = torch.empty(1 << circ.n, dtype=torch.complex64, device="cuda")
     hq.hq_state_init(st)
-    hq.hq_apply_blocks(st, blocks, engine="tc_f16", tc_min_k=5)
+    hq.hq_apply_blocks(st, blocks, engine="tc_f16", tc_min_k=4)
     err = rel_l2(st.cpu().numpy().astype(np.complex128), want)
     assert err <= 2e-5 * max(1, len(circ.gates) / 1000), err
 
@@ -108,7 +108,7 @@ def test_fused_grid_circuit_bf16_error_reported(hq):
     want = oracle.simulate(circ)
     st = torch.empty(1 << circ.n, dtype=torch.complex64, device="cuda")
     hq.hq_state_init(st)
-    hq.hq_apply_blocks(st, hq.hq_fuse(circ.n, circ.gates, 6), engine="tc_bf16", tc_min_k=5)
+    hq.hq_apply_blocks(st, hq.hq_fuse(circ.n, circ.gates, 6), engine="tc_bf16", tc_min_k=4)
     err = rel_l2(st.cpu().numpy().astype(np.complex128), want)
     print(f"bf16 hi+lo relative L2 error over {len(circ.gates)} gates: {err:.3e}")
     assert err <= 5e-3
