@@ -223,6 +223,64 @@ hq_status hq_adjoint_grad(int n, hq_dtype dt, const hq_op *ops, int G, int P, co
                           void *workspace, size_t ws_bytes, double *energies_host, double *grads_host,
                           void *stream);
 
+/*
+ * Batched runs -- many independent circuits of uneven size in ONE persistent
+ * kernel launch, captured once into a CUDA graph and replayed (serving-style
+ * loads).  Not in the paper beyond its evolution of each circuit (Sec. 4.2)
+ * and its gate grouping (Sec. 3.1): every circuit starts from |0..0> and its
+ * gates (k <= 2, host matrices) are grouped into passes; one pass = one read
+ * and one write of the state, during which each tile of 2^tile_bits
+ * amplitudes (the lowest tile_bits - max_high bits as one contiguous run, plus
+ * up to max_high higher bits) stays in shared memory while the pass's gates
+ * are applied.  A circuit with n <= tile_bits is one pass over one tile.
+ */
+typedef struct {
+    int n;                /* qubits, 1..30 */
+    int G;                /* gates */
+    const hq_gate *gates; /* host; each k <= 2 */
+    void *state;          /* device, 2^n complex64, 16-byte aligned, caller-owned; overwritten */
+} hq_circuit;
+
+typedef struct {
+    int tile_bits;   /* log2 amplitudes per shared-memory tile, 6..13 (0 = 12) */
+    int max_high;    /* high bits per pass, 1..8, < tile_bits (0 = 6) */
+    int ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
+} hq_batch_config;
+
+typedef struct hq_batch hq_batch; /* opaque plan + instantiated CUDA graph */
+
+/* Device workspace hq_batch_create needs for this batch (0 on invalid input). */
+size_t hq_batch_workspace_bytes(const hq_circuit *cs, int C, const hq_batch_config *cfg);
+
+/*
+ * hq_batch_create -- validate, plan (host), upload the plan into `workspace`
+ * (caller-owned device memory of >= hq_batch_workspace_bytes bytes, 256-byte
+ * aligned) and capture the run (counter reset + persistent kernel) into a CUDA
+ * graph.  SYNCHRONISES `stream`.  The circuits' gates are copied; their state
+ * buffers and the workspace must outlive the handle.
+ * Errors: HQ_ERR_NULL, HQ_ERR_ARG (C < 1, bad config), HQ_ERR_N_TOO_LARGE,
+ * HQ_ERR_K_TOO_LARGE (a gate with k > 2), HQ_ERR_QUBIT_RANGE,
+ * HQ_ERR_DUP_QUBIT, HQ_ERR_ALIGN, HQ_ERR_CAPACITY, HQ_ERR_CUDA.
+ */
+hq_status hq_batch_create(const hq_circuit *cs, int C, const hq_batch_config *cfg, void *workspace, size_t ws_bytes,
+                          void *stream, hq_batch **out);
+
+/* hq_batch_run -- enqueue one replay of the captured graph on `stream` (async):
+ * every circuit's state is rebuilt from |0..0> and evolved. */
+hq_status hq_batch_run(hq_batch *b, void *stream);
+
+/*
+ * hq_batch_latencies -- after a run on `stream` (SYNCHRONISES it): completion
+ * time of each circuit (latency_us, C floats, may be NULL) and of the whole
+ * batch (makespan_us), in microseconds since the kernel started.  Returns
+ * HQ_ERR_TIMEOUT if the run stopped because its bounded scheduler wait ran
+ * out (2 s without progress).
+ */
+hq_status hq_batch_latencies(hq_batch *b, void *stream, float *latency_us, double *makespan_us);
+
+/* hq_batch_destroy -- release the graph and the handle (not the workspace). */
+void hq_batch_destroy(hq_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,60 @@
+"""Project-written autotuner for batched runs: picks the shared-memory tile
+shape (tile_bits, max_high) and CTAs per SM by timing candidate plans of the
+actual batch on the device, and caches the winner per (device, batch
+signature) in a JSON file."""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+from . import hq
+
+CANDIDATES = [(12, 6, 0), (13, 7, 0), (13, 6, 0), (11, 5, 0), (12, 5, 0), (12, 6, 2)]
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hq_gb300", "autotune.json")
+
+
+def signature(circuits) -> str:
+    h = hashlib.sha1()
+    for c in circuits:
+        h.update(f"{c.n}:{len(c.gates)};".encode())
+    return h.hexdigest()[:16]
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def tune(circuits, states=None, candidates=CANDIDATES, reps: int = 3, cache_path: str | None = DEFAULT_CACHE):
+    """Returns (tile_bits, max_high, ctas_per_sm, timings) with the shortest
+    median makespan; reuses the cached choice when the signature matches."""
+    import torch
+
+    dev = torch.cuda.get_device_name()
+    key = f"{dev}|{signature(circuits)}"
+    if cache_path:
+        cached = _load(cache_path).get(key)
+        if cached:
+            return tuple(cached["choice"]) + (cached.get("timings", {}),)
+    timings = {}
+    for cand in candidates:
+        b = hq.Batch(circuits, states, *cand)
+        b.run()
+        spans = []
+        for _ in range(reps):
+            b.run()
+            spans.append(b.latencies()[1])
+        b.close()
+        timings[str(cand)] = sorted(spans)[len(spans) // 2]
+    best = min(candidates, key=lambda c: timings[str(c)])
+    if cache_path:
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        data = _load(cache_path)
+        data[key] = {"choice": list(best), "timings": timings}
+        with open(cache_path, "w") as f:
+            json.dump(data, f, indent=1)
+    return tuple(best) + (timings,)

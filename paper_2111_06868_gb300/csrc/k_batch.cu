@@ -1,0 +1,528 @@
+// k_batch.cu -- many circuits of uneven size in one persistent launch
+// (hq_batch_*), for serving-style loads.
+//
+// Each circuit is evolved from |0..0> by Sec. 4.2's gate-by-gate product, with
+// its gates grouped into "passes": a pass is one read and one write of the
+// state, during which every tile of 2^(R+|H|) amplitudes -- the R lowest bits
+// (one contiguous run) plus a set H of at most h higher bits -- stays in shared
+// memory while the pass's gates are applied to it one after another.  Gates
+// join passes greedily in circuit order; a gate may move into an earlier pass
+// only past passes it shares no qubit with (so the moves commute), as in
+// Sec. 3.1's compress().  A circuit with n <= R + h is one pass over one tile:
+// it never leaves shared memory except for the final store.
+//
+// Scheduling: one persistent kernel (grid = SMs x CTAs per SM) pulls work from
+// a device-side ready queue of passes.  The queue starts with every circuit's
+// first pass (largest circuits first); CTAs take tiles of the queue head with
+// an atomic counter; the CTA finishing the last tile of a pass appends the
+// circuit's next pass.  The first pass builds |0..0> in shared memory instead of
+// loading it.  Tile data written by other CTAs is read through L2 (ld.global.cg)
+// after an acquire fence, because L1 is not coherent within a launch.  Every
+// wait is bounded: with no progress for 2 s the kernel raises the device error
+// flag and exits (reported as HQ_ERR_TIMEOUT).  Per-circuit completion times
+// come from %globaltimer.  The launch (counter reset + kernel) is captured once
+// into a CUDA graph and replayed by hq_batch_run.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "hq_internal.cuh"
+
+struct hq_batch {
+    int C;
+    int ctas;
+    size_t smem;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    char *ws;                 // device workspace base
+    size_t off_end_ns, off_t0; // offsets of the timing arrays
+    int64_t total_gates;
+};
+
+namespace hq {
+
+extern __device__ unsigned int g_device_error;
+
+constexpr int kBThreads = 256;
+constexpr int kBMaxHigh = 8;
+constexpr uint64_t kBatchStallNs = 2000000000ull;
+
+struct BGate {
+    int k;          // 1 or 2
+    int diag;       // matrix is diagonal
+    int tpos[2];    // tile positions of qubits[0], qubits[1]
+    float2 m[16];   // 2^k x 2^k, row-major (complex64)
+};
+struct BPass {
+    int circuit;
+    int R;           // low run bits
+    int nh;          // high bits
+    int hb[kBMaxHigh];  // high bit positions, ascending
+    int g0, ng;      // gates [g0, g0 + ng)
+    int next;        // next pass of the circuit, -1 if last
+    int first;       // first pass of its circuit (builds |0..0>)
+    int64_t ntiles;  // 2^(n - R - nh)
+};
+struct BCircuit {
+    float2 *state;
+    int n;
+};
+struct BatchParams {
+    const BCircuit *circ;
+    const BPass *pass;
+    const BGate *gate;
+    int C, P;
+    // per-run counters (zeroed by the graph before every launch)
+    int *next_tile;          // [P]
+    int *done_tile;          // [P]
+    int *queue;              // [P] pass ids, -1 = not yet written
+    int *qhead, *qtail;      // queue counters (qtail preset to C)
+    int *completed;
+    unsigned long long *end_ns;  // [C]
+    unsigned long long *t0;      // kernel start (min over CTAs)
+};
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
+
+// tile-local element i (R low bits, then the nh high bits) -> offset in the state
+__device__ __forceinline__ int64_t elem_offset(const BPass &ps, int64_t base, int i)
+{
+    int64_t off = base + (i & ((1 << ps.R) - 1));
+    const int hi = i >> ps.R;
+    for (int j = 0; j < ps.nh; ++j)
+        if ((hi >> j) & 1) off += int64_t(1) << ps.hb[j];
+    return off;
+}
+
+__global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw);
+    __shared__ int s_pass, s_stop;
+    __shared__ long long s_tile;
+    __shared__ BPass s_ps;
+    if (threadIdx.x == 0) atomicMin(p.t0, now_ns());
+
+    for (;;) {
+        // ---------------- find work (thread 0) ----------------
+        if (threadIdx.x == 0) {
+            int stop = 0, pid = -1;
+            long long tid = -1;
+            unsigned long long last_progress = now_ns();
+            while (pid < 0 && !stop) {
+                if (ld_volatile(p.completed) >= p.C) { stop = 1; break; }
+                const int h = ld_volatile(p.qhead);
+                if (h < ld_volatile(p.qtail)) {
+                    const int q = ld_volatile(&p.queue[h]);
+                    if (q >= 0) {
+                        __threadfence();
+                        const int t = atomicAdd(&p.next_tile[q], 1);
+                        const long long nt = p.pass[q].ntiles;
+                        if (t < nt) {
+                            pid = q;
+                            tid = t;
+                            if (t == nt - 1) atomicCAS(p.qhead, h, h + 1);  // pass fully handed out
+                            break;
+                        }
+                        atomicCAS(p.qhead, h, h + 1);
+                        last_progress = now_ns();
+                        continue;
+                    }
+                }
+                if (now_ns() - last_progress > kBatchStallNs) {
+                    atomicOr(&g_device_error, 2u);
+                    stop = 1;
+                }
+            }
+            s_pass = pid;
+            s_tile = tid;
+            s_stop = stop;
+            if (pid >= 0) s_ps = p.pass[pid];
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const BPass &ps = s_ps;
+        const BCircuit cc = p.circ[ps.circuit];
+        const int L = ps.R + ps.nh, TS = 1 << L;
+        // flat offset of tile s_tile: its bits fill the positions outside the tile
+        int64_t base = int64_t(s_tile) << ps.R;
+        for (int j = 0; j < ps.nh; ++j) {
+            const int hb = ps.hb[j];
+            base = ((base >> hb) << (hb + 1)) | (base & ((int64_t(1) << hb) - 1));
+        }
+        // ---------------- load (or build |0..0>) ----------------
+        if (ps.first) {
+            for (int i = threadIdx.x; i < TS; i += blockDim.x)
+                tile[swz<float>(i)] = make_float2((base == 0 && i == 0) ? 1.f : 0.f, 0.f);
+        } else {
+            for (int i = threadIdx.x; i < TS; i += blockDim.x)
+                tile[swz<float>(i)] = __ldcg(cc.state + elem_offset(ps, base, i));
+        }
+        __syncthreads();
+        // ---------------- gates, in order ----------------
+        for (int gi = ps.g0; gi < ps.g0 + ps.ng; ++gi) {
+            const BGate &gt = p.gate[gi];
+            if (gt.diag) {
+                for (int i = threadIdx.x; i < TS; i += blockDim.x) {
+                    int r = (i >> gt.tpos[0]) & 1;
+                    if (gt.k == 2) r = (r << 1) | ((i >> gt.tpos[1]) & 1);
+                    const int D = 1 << gt.k;
+                    tile[swz<float>(i)] = cmul(gt.m[r * D + r], tile[swz<float>(i)]);
+                }
+            } else if (gt.k == 1) {
+                const int tp = gt.tpos[0];
+                const float2 m00 = gt.m[0], m01 = gt.m[1], m10 = gt.m[2], m11 = gt.m[3];
+                for (int grp = threadIdx.x; grp < TS / 2; grp += blockDim.x) {
+                    const int i0 = ((grp >> tp) << (tp + 1)) | (grp & ((1 << tp) - 1));
+                    const int a = swz<float>(i0), b = swz<float>(i0 | (1 << tp));
+                    const float2 x0 = tile[a], x1 = tile[b];
+                    float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+                    cmac(y0, m00, x0);
+                    cmac(y0, m01, x1);
+                    cmac(y1, m10, x0);
+                    cmac(y1, m11, x1);
+                    tile[a] = y0;
+                    tile[b] = y1;
+                }
+            } else {
+                const int p0 = gt.tpos[0], p1 = gt.tpos[1];
+                const int lo = min(p0, p1), hi = max(p0, p1);
+                for (int grp = threadIdx.x; grp < TS / 4; grp += blockDim.x) {
+                    int i0 = ((grp >> lo) << (lo + 1)) | (grp & ((1 << lo) - 1));
+                    i0 = ((i0 >> hi) << (hi + 1)) | (i0 & ((1 << hi) - 1));
+                    int idx[4];
+                    float2 x[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        idx[r] = swz<float>(i0 | (((r >> 1) & 1) << p0) | ((r & 1) << p1));
+                        x[r] = tile[idx[r]];
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) cmac(y, gt.m[r * 4 + c], x[c]);
+                        tile[idx[r]] = y;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // ---------------- store, then report the tile ----------------
+        for (int i = threadIdx.x; i < TS; i += blockDim.x) __stcg(cc.state + elem_offset(ps, base, i), tile[swz<float>(i)]);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int pid = s_pass;
+            const int d = atomicAdd(&p.done_tile[pid], 1);
+            if (d == ps.ntiles - 1) {
+                __threadfence();
+                if (ps.next < 0) {
+                    p.end_ns[ps.circuit] = now_ns();
+                    __threadfence();
+                    atomicAdd(p.completed, 1);
+                } else {
+                    const int slot = atomicAdd(p.qtail, 1);
+                    atomicExch(&p.queue[slot], ps.next);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+static size_t align_up256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct BatchPlan {
+    std::vector<BCircuit> circ;
+    std::vector<BPass> pass;
+    std::vector<BGate> gate;
+    std::vector<int> first_pass;  // per circuit
+    int64_t total_gates = 0;
+};
+
+// Groups one circuit's gates into passes (see the file comment).
+static hq_status plan_circuit(const hq_circuit &c, int ci, int R0, int h, BatchPlan &pl)
+{
+    const int n = c.n;
+    const int R = std::min(n, R0);
+    struct P {
+        uint64_t qset = 0;   // qubits touched (as flat bits)
+        uint64_t high = 0;   // bits >= R
+        std::vector<int> gates;
+    };
+    std::vector<P> ps;
+    for (int g = 0; g < c.G; ++g) {
+        const hq_gate &gt = c.gates[g];
+        uint64_t Q = 0, Qh = 0;
+        for (int j = 0; j < gt.k; ++j) {
+            const int b = n - 1 - gt.qubits[j];
+            Q |= 1ull << b;
+            if (b >= R) Qh |= 1ull << b;
+        }
+        int i = int(ps.size()) - 1;
+        while (i >= 0 && !(ps[i].qset & Q)) --i;
+        int target = -1;
+        if (i >= 0 && __builtin_popcountll(ps[i].high | Qh) <= h) target = i;
+        for (int j = i + 1; target < 0 && j < int(ps.size()); ++j)
+            if (__builtin_popcountll(ps[j].high | Qh) <= h) target = j;
+        if (target < 0) {
+            ps.emplace_back();
+            target = int(ps.size()) - 1;
+        }
+        ps[target].qset |= Q;
+        ps[target].high |= Qh;
+        ps[target].gates.push_back(g);
+    }
+    if (ps.empty()) ps.emplace_back();  // G = 0: one pass that writes |0..0>
+    const int base_pass = int(pl.pass.size());
+    pl.first_pass.push_back(base_pass);
+    for (size_t pi = 0; pi < ps.size(); ++pi) {
+        BPass bp;
+        std::memset(&bp, 0, sizeof(bp));
+        bp.circuit = ci;
+        bp.R = R;
+        bp.nh = 0;
+        for (int b = R; b < n; ++b)
+            if ((ps[pi].high >> b) & 1) bp.hb[bp.nh++] = b;
+        bp.g0 = int(pl.gate.size());
+        bp.ng = int(ps[pi].gates.size());
+        bp.next = (pi + 1 < ps.size()) ? base_pass + int(pi) + 1 : -1;
+        bp.first = pi == 0;
+        bp.ntiles = int64_t(1) << (n - R - bp.nh);
+        auto tpos = [&](int b) {
+            if (b < R) return b;
+            for (int j = 0; j < bp.nh; ++j)
+                if (bp.hb[j] == b) return R + j;
+            return -1;
+        };
+        for (int g : ps[pi].gates) {
+            const hq_gate &gt = c.gates[g];
+            BGate bg;
+            std::memset(&bg, 0, sizeof(bg));
+            bg.k = gt.k;
+            bg.diag = is_diagonal(gt.k, gt.matrix);
+            for (int j = 0; j < gt.k; ++j) bg.tpos[j] = tpos(n - 1 - gt.qubits[j]);
+            const int D = 1 << gt.k;
+            for (int e = 0; e < D * D; ++e) bg.m[e] = make_float2(float(gt.matrix[2 * e]), float(gt.matrix[2 * e + 1]));
+            pl.gate.push_back(bg);
+        }
+        pl.pass.push_back(bp);
+    }
+    pl.total_gates += c.G;
+    return HQ_OK;
+}
+
+struct BatchLayout {
+    size_t circ, pass, gate, next_tile, done_tile, queue, qhead, end_ns, image, total, counters_begin,
+        counters_bytes;
+};
+
+static BatchLayout batch_layout(size_t C, size_t P, size_t G)
+{
+    BatchLayout L;
+    L.circ = 0;
+    L.pass = align_up256(L.circ + C * sizeof(BCircuit));
+    L.gate = align_up256(L.pass + P * sizeof(BPass));
+    L.next_tile = align_up256(L.gate + std::max<size_t>(G, 1) * sizeof(BGate));
+    L.done_tile = L.next_tile + P * sizeof(int);
+    L.queue = L.done_tile + P * sizeof(int);
+    L.qhead = align_up256(L.queue + P * sizeof(int));  // qhead, qtail, completed, pad, t0 (u64)
+    L.end_ns = align_up256(L.qhead + 32);
+    L.image = align_up256(L.end_ns + C * sizeof(unsigned long long));
+    L.counters_begin = L.next_tile;
+    L.counters_bytes = L.image - L.next_tile;
+    L.total = align_up256(L.image + L.counters_bytes);  // + the reset image of the counters
+    return L;
+}
+
+static hq_status check_batch(const hq_circuit *cs, int C, const hq_batch_config *cfg, int &R0, int &h, int &per_sm)
+{
+    if (C < 1) return HQ_ERR_ARG;
+    if (!cs) return HQ_ERR_NULL;
+    const int L = (cfg && cfg->tile_bits) ? cfg->tile_bits : 12;
+    h = (cfg && cfg->max_high) ? cfg->max_high : 6;
+    per_sm = (cfg && cfg->ctas_per_sm) ? cfg->ctas_per_sm : 0;
+    if (L < 6 || L > 13 || h < 1 || h > kBMaxHigh || h >= L || per_sm < 0 || per_sm > 8) return HQ_ERR_ARG;
+    R0 = L - h;
+    for (int c = 0; c < C; ++c) {
+        if (cs[c].n < 1 || cs[c].n > 30) return HQ_ERR_N_TOO_LARGE;
+        if (cs[c].G < 0) return HQ_ERR_ARG;
+        if (cs[c].G > 0 && !cs[c].gates) return HQ_ERR_NULL;
+        if (!cs[c].state) return HQ_ERR_NULL;
+        if (reinterpret_cast<uintptr_t>(cs[c].state) & 15) return HQ_ERR_ALIGN;
+        for (int g = 0; g < cs[c].G; ++g) {
+            hq_status st = check_qubits(cs[c].n, cs[c].gates[g].k, cs[c].gates[g].qubits, 2);
+            if (st != HQ_OK) return st;
+            if (!cs[c].gates[g].matrix) return HQ_ERR_NULL;
+        }
+    }
+    return HQ_OK;
+}
+
+static hq_status plan_batch(const hq_circuit *cs, int C, int R0, int h, BatchPlan &pl)
+{
+    // circuits in descending size order: big passes are queued first
+    std::vector<int> order(C);
+    for (int c = 0; c < C; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cs[a].n > cs[b].n; });
+    pl.circ.resize(C);
+    std::vector<int> fp(C);
+    for (int c = 0; c < C; ++c) {
+        pl.circ[c].state = static_cast<float2 *>(cs[c].state);
+        pl.circ[c].n = cs[c].n;
+        hq_status st = plan_circuit(cs[c], c, R0, h, pl);
+        if (st != HQ_OK) return st;
+        fp[c] = pl.first_pass.back();
+    }
+    pl.first_pass.clear();
+    for (int c : order) pl.first_pass.push_back(fp[c]);
+    return HQ_OK;
+}
+
+}  // namespace hq
+
+using namespace hq;
+
+extern "C" size_t hq_batch_workspace_bytes(const hq_circuit *cs, int C, const hq_batch_config *cfg)
+{
+    int R0, h, per_sm;
+    if (check_batch(cs, C, cfg, R0, h, per_sm) != HQ_OK) return 0;
+    BatchPlan pl;
+    if (plan_batch(cs, C, R0, h, pl) != HQ_OK) return 0;
+    return batch_layout(C, pl.pass.size(), pl.gate.size()).total;
+}
+
+extern "C" hq_status hq_batch_create(const hq_circuit *cs, int C, const hq_batch_config *cfg, void *workspace,
+                                     size_t ws_bytes, void *stream, hq_batch **out)
+{
+    if (!out) return HQ_ERR_NULL;
+    *out = nullptr;
+    int R0, h, per_sm;
+    hq_status st = check_batch(cs, C, cfg, R0, h, per_sm);
+    if (st != HQ_OK) return st;
+    if (!workspace) return HQ_ERR_NULL;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return HQ_ERR_ALIGN;
+    BatchPlan pl;
+    if ((st = plan_batch(cs, C, R0, h, pl)) != HQ_OK) return st;
+    const size_t P = pl.pass.size();
+    const BatchLayout L = batch_layout(C, P, pl.gate.size());
+    if (ws_bytes < L.total) return HQ_ERR_CAPACITY;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = static_cast<char *>(workspace);
+    HQ_CUDA(cudaMemcpyAsync(ws + L.circ, pl.circ.data(), C * sizeof(BCircuit), cudaMemcpyHostToDevice, s));
+    HQ_CUDA(cudaMemcpyAsync(ws + L.pass, pl.pass.data(), P * sizeof(BPass), cudaMemcpyHostToDevice, s));
+    if (!pl.gate.empty())
+        HQ_CUDA(cudaMemcpyAsync(ws + L.gate, pl.gate.data(), pl.gate.size() * sizeof(BGate), cudaMemcpyHostToDevice, s));
+    HQ_CUDA(cudaStreamSynchronize(s));
+
+    // per-run counter image: queue = first passes then -1, qtail = C, t0 = max
+    std::vector<char> image(L.counters_bytes, 0);
+    int *q = reinterpret_cast<int *>(image.data() + (L.queue - L.counters_begin));
+    for (size_t i = 0; i < P; ++i) q[i] = i < size_t(C) ? pl.first_pass[i] : -1;
+    int *qc = reinterpret_cast<int *>(image.data() + (L.qhead - L.counters_begin));
+    qc[0] = 0;  // head
+    qc[1] = C;  // tail
+    qc[2] = 0;  // completed
+    *reinterpret_cast<unsigned long long *>(image.data() + (L.qhead - L.counters_begin) + 16) = ~0ull;  // t0
+
+    int smem_L = 0;
+    for (auto &ps : pl.pass) smem_L = std::max(smem_L, ps.R + ps.nh);
+    const size_t smem = sizeof(float2) << smem_L;
+
+    BatchParams bp;
+    bp.circ = reinterpret_cast<const BCircuit *>(ws + L.circ);
+    bp.pass = reinterpret_cast<const BPass *>(ws + L.pass);
+    bp.gate = reinterpret_cast<const BGate *>(ws + L.gate);
+    bp.C = C;
+    bp.P = int(P);
+    bp.next_tile = reinterpret_cast<int *>(ws + L.next_tile);
+    bp.done_tile = reinterpret_cast<int *>(ws + L.done_tile);
+    bp.queue = reinterpret_cast<int *>(ws + L.queue);
+    bp.qhead = reinterpret_cast<int *>(ws + L.qhead);
+    bp.qtail = bp.qhead + 1;
+    bp.completed = bp.qhead + 2;
+    bp.t0 = reinterpret_cast<unsigned long long *>(ws + L.qhead + 16);
+    bp.end_ns = reinterpret_cast<unsigned long long *>(ws + L.end_ns);
+
+    const int occ = occupancy((const void *)k_batch, kBThreads, smem);
+    const int ctas = sm_count() * (per_sm ? std::min(per_sm, occ) : occ);
+
+    hq_batch *b = new hq_batch();
+    b->C = C;
+    b->ctas = ctas;
+    b->smem = smem;
+    b->ws = ws;
+    b->off_end_ns = L.end_ns;
+    b->off_t0 = L.qhead + 16;
+    b->total_gates = pl.total_gates;
+    b->graph = nullptr;
+    b->exec = nullptr;
+
+    // the reset image lives in the workspace; the graph copies it over the counters
+    HQ_CUDA(cudaMemcpyAsync(ws + L.image, image.data(), image.size(), cudaMemcpyHostToDevice, s));
+    HQ_CUDA(cudaStreamSynchronize(s));
+    cudaStream_t cap = nullptr;
+    st = cuda_status("capture stream", cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    if (st == HQ_OK) st = cuda_status("begin capture", cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    if (st == HQ_OK) {
+        cudaMemcpyAsync(ws + L.counters_begin, ws + L.image, image.size(), cudaMemcpyDeviceToDevice, cap);
+        k_batch<<<ctas, kBThreads, smem, cap>>>(bp);
+        cudaError_t e1 = cudaGetLastError();
+        cudaError_t e2 = cudaStreamEndCapture(cap, &b->graph);
+        st = cuda_status("capture", e1 != cudaSuccess ? e1 : e2);
+    }
+    if (st == HQ_OK) st = cuda_status("instantiate", cudaGraphInstantiate(&b->exec, b->graph, 0));
+    if (cap) cudaStreamDestroy(cap);
+    if (st != HQ_OK) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return HQ_OK;
+}
+
+extern "C" hq_status hq_batch_run(hq_batch *b, void *stream)
+{
+    if (!b) return HQ_ERR_NULL;
+    return cuda_status("graph launch", cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+}
+
+extern "C" hq_status hq_batch_latencies(hq_batch *b, void *stream, float *latency_us, double *makespan_us)
+{
+    if (!b) return HQ_ERR_NULL;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<unsigned long long> end(b->C);
+    unsigned long long t0 = 0;
+    HQ_CUDA(cudaMemcpyAsync(end.data(), b->ws + b->off_end_ns, sizeof(unsigned long long) * b->C,
+                            cudaMemcpyDeviceToHost, s));
+    HQ_CUDA(cudaMemcpyAsync(&t0, b->ws + b->off_t0, sizeof(t0), cudaMemcpyDeviceToHost, s));
+    HQ_CUDA(cudaStreamSynchronize(s));
+    hq_status st = device_error_status();
+    if (st != HQ_OK) return st;
+    unsigned long long mx = t0;
+    for (int c = 0; c < b->C; ++c) {
+        if (latency_us) latency_us[c] = float(double(end[c] - t0) * 1e-3);
+        mx = std::max(mx, end[c]);
+    }
+    if (makespan_us) *makespan_us = double(mx - t0) * 1e-3;
+    return HQ_OK;
+}
+
+extern "C" void hq_batch_destroy(hq_batch *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+}

@@ -61,6 +61,14 @@ class hq_config(ctypes.Structure):
     _fields_ = [("engine", ctypes.c_int), ("tc_min_k", ctypes.c_int)]
 
 
+class hq_circuit(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("G", ctypes.c_int), ("gates", ctypes.c_void_p), ("state", ctypes.c_void_p)]
+
+
+class hq_batch_config(ctypes.Structure):
+    _fields_ = [("tile_bits", ctypes.c_int), ("max_high", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+
+
 _lib = None
 
 
@@ -86,6 +94,11 @@ def load(path: str | None = None):
         "hq_expectation_static": ([V, I, I, V, I, P(D), V], I),
         "hq_adjoint_workspace_bytes": ([I, I, I, I, I, I], ctypes.c_size_t),
         "hq_adjoint_grad": ([I, I, V, I, I, V, I, V, I, ctypes.c_char_p, I, V, ctypes.c_size_t, V, V, V], I),
+        "hq_batch_workspace_bytes": ([V, I, V], ctypes.c_size_t),
+        "hq_batch_create": ([V, I, V, V, ctypes.c_size_t, V, P(V)], I),
+        "hq_batch_run": ([V, V], I),
+        "hq_batch_latencies": ([V, V, V, P(D)], I),
+        "hq_batch_destroy": ([V], None),
     }
     for name, (args, res) in sig.items():
         if hasattr(lib, name):
@@ -301,3 +314,74 @@ def hq_adjoint_grad(circuit, H, theta, dtype="complex64", tokens: str | None = N
                                   e.ctypes.data_as(ctypes.c_void_p), g.ctypes.data_as(ctypes.c_void_p),
                                   _stream(stream)), "hq_adjoint_grad")
     return e, g[:, :P]
+
+
+# ----------------------------------------------------------------------------
+# batched persistent runs
+# ----------------------------------------------------------------------------
+def _batch_structs(circuits, states):
+    keep: list = []
+    arr = (hq_circuit * len(circuits))()
+    for i, c in enumerate(circuits):
+        garr, G = _gates_array(c.gates, keep)
+        keep.append(garr)
+        arr[i].n = c.n
+        arr[i].G = G
+        arr[i].gates = ctypes.cast(garr, ctypes.c_void_p)
+        arr[i].state = states[i].data_ptr() if states is not None else (1 << 20) * (i + 1)
+    return arr, keep
+
+
+def hq_batch_workspace_bytes(circuits, tile_bits: int = 0, max_high: int = 0, ctas_per_sm: int = 0) -> int:
+    arr, keep = _batch_structs(circuits, None)
+    cfg = hq_batch_config(tile_bits, max_high, ctas_per_sm)
+    return int(load().hq_batch_workspace_bytes(arr, len(circuits), ctypes.byref(cfg)))
+
+
+class Batch:
+    """hq_batch_create / run / latencies / destroy over torch-owned buffers.
+    ``states`` (one complex64 tensor of 2^n per circuit) is allocated if not given."""
+
+    def __init__(self, circuits, states=None, tile_bits: int = 0, max_high: int = 0, ctas_per_sm: int = 0,
+                 stream=None):
+        import torch
+
+        self.circuits = list(circuits)
+        if states is None:
+            states = [torch.empty(1 << c.n, dtype=torch.complex64, device="cuda") for c in self.circuits]
+        self.states = states
+        self.cfg = hq_batch_config(tile_bits, max_high, ctas_per_sm)
+        arr, keep = _batch_structs(self.circuits, states)
+        need = load().hq_batch_workspace_bytes(arr, len(self.circuits), ctypes.byref(self.cfg))
+        if need == 0:
+            # the planner refused the input: let hq_batch_create report why
+            need = 256
+        self.workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+        h = ctypes.c_void_p()
+        self._h = None
+        _check(load().hq_batch_create(arr, len(self.circuits), ctypes.byref(self.cfg),
+                                      ctypes.c_void_p(self.workspace.data_ptr()), need, _stream(stream),
+                                      ctypes.byref(h)), "hq_batch_create")
+        self._h = h
+        self.gates = sum(len(c.gates) for c in self.circuits)
+
+    def run(self, stream=None):
+        _check(load().hq_batch_run(self._h, _stream(stream)), "hq_batch_run")
+
+    def latencies(self, stream=None):
+        lat = np.zeros(len(self.circuits), np.float32)
+        mk = ctypes.c_double()
+        _check(load().hq_batch_latencies(self._h, _stream(stream), lat.ctypes.data_as(ctypes.c_void_p),
+                                         ctypes.byref(mk)), "hq_batch_latencies")
+        return lat, mk.value
+
+    def close(self):
+        if self._h is not None:
+            load().hq_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

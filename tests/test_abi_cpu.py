@@ -130,3 +130,14 @@ def test_fuse_errors(hq):
 
 def test_fuse_empty_circuit(hq):
     assert hq.hq_fuse(3, [], 4) == []
+
+
+def test_batch_planner_host_only(hq):
+    """hq_batch_workspace_bytes plans on the host (no device work): positive
+    for a valid batch, 0 for invalid input."""
+    cs = C.config_batch(8, seed=2, n_range=(3, 14), depth_range=(2, 6))
+    assert hq.hq_batch_workspace_bytes(cs) > 0
+    assert hq.hq_batch_workspace_bytes(cs, 13, 7) > 0
+    assert hq.hq_batch_workspace_bytes(cs, 14, 6) == 0        # tile_bits out of range
+    wide = C.Circuit(4, [C.Gate("U", (0, 1, 2), np.eye(8, dtype=np.complex128))])
+    assert hq.hq_batch_workspace_bytes([wide]) == 0           # k > 2

@@ -142,7 +142,7 @@ def test_n33_tc_norm_and_inverse(hq):
     st = torch.empty(1 << 33, dtype=torch.complex64, device="cuda")
     hq.hq_state_init(st)
     hq.hq_apply_blocks(st, blocks, engine="tc_f16")
-    nrm = hq.hq_expectation(st, [(1.0, ())])
+    nrm = hq.hq_expectation(st, [(1.0, ())]) ** 0.5
     assert abs(nrm - 1) <= 2e-5 * max(1, G / 1000)
     hq.hq_apply_blocks(st, [(q, m.conj().T.copy()) for q, m in reversed(blocks)], engine="tc_f16")
     assert abs(complex(st[0].item()) - 1) <= 4e-5 * max(1, 2 * G / 1000)
