@@ -50,7 +50,6 @@ namespace hq {
 
 __device__ unsigned int g_device_error;  // bit 0: a tensor-core wait timed out
 
-constexpr int kTcThreads = 256;
 constexpr int kTcGroups = 128;                    // MMA M
 constexpr uint64_t kWaitNs = 2000000000ull;        // 2 s per wait
 
@@ -236,7 +235,8 @@ struct TcLayout {
     static constexpr int kStageBytes = kTcGroups * kRowStride;
     static constexpr int kOffStage = 2 * kBBytes;             // stage[2]
     static constexpr int kOffScale = kOffStage + 2 * kStageBytes;  // float[2][128]
-    static constexpr int kOffBar = kOffScale + 2 * kTcGroups * 4;  // mma_done[2], acc_free[2]
+    static constexpr int kOffPartMax = kOffScale + 2 * kTcGroups * 4;  // float[2][128] (split groups)
+    static constexpr int kOffBar = kOffPartMax + 2 * kTcGroups * 4;  // mma_done[2], acc_free[2]
     static constexpr int kOffMisc = kOffBar + 4 * 8;          // tmem addr, abort flag
     static constexpr int kBytes = kOffMisc + 16;
     // TMEM per buffer: A_hi (D cols), A_lo (D cols), accumulator (2D cols)
@@ -246,28 +246,38 @@ struct TcLayout {
 };
 
 template <int K> __host__ __device__ constexpr int tc_min_blocks() { return K == 6 ? 1 : (K == 5 ? 2 : 4); }
+// Threads sharing one group: k = 6 has one CTA per SM, so each group is split
+// over two producer and two epilogue warps (16 warps per SM) to keep enough
+// warps issuing; k = 4, 5 already run 2-4 CTAs per SM.
+template <int K> __host__ __device__ constexpr int tc_split() { return K == 6 ? 2 : 1; }
+template <int K> __host__ __device__ constexpr int tc_threads() { return 2 * kTcGroups * tc_split<K>(); }
 
 template <int K, bool BF16>
-__global__ void __launch_bounds__(kTcThreads, tc_min_blocks<K>()) k_tc(const TcParams p, float2 *__restrict__ state)
+__global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(const TcParams p, float2 *__restrict__ state)
 {
     using Lay = TcLayout<K>;
     constexpr int D = Lay::D, D2 = Lay::D2;
+    constexpr int SPLIT = tc_split<K>();
+    constexpr int NP = kTcGroups * SPLIT;   // producer threads (warps 0 .. NP/32-1)
+    constexpr int NT = tc_threads<K>();
+    constexpr int DP = D / SPLIT;           // amplitudes per producer thread
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Lay::kOffBar);  // [0,1] mma_done, [2,3] acc_free
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Lay::kOffMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + Lay::kOffMisc + 4);
     float *inv_scale = reinterpret_cast<float *>(smem + Lay::kOffScale);
+    float *part_max = reinterpret_cast<float *>(smem + Lay::kOffPartMax);  // [SPLIT][128]
     const TileGeom &g = p.g;
     const int tid = threadIdx.x, warp = tid >> 5;
 
     // stage the split matrix, set up barriers and TMEM
-    for (int i = tid; i < 2 * Lay::kBBytes / 16; i += kTcThreads)
+    for (int i = tid; i < 2 * Lay::kBBytes / 16; i += NT)
         reinterpret_cast<uint4 *>(smem)[i] = p.bmat[i];
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
-        mbar_init(&bar[2], kTcGroups);
-        mbar_init(&bar[3], kTcGroups);
+        mbar_init(&bar[2], NT - NP);
+        mbar_init(&bar[3], NT - NP);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -280,21 +290,23 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<K>()) k_tc(const TcP
     const uint32_t smem_base = smem_u32(smem);
     const int cmask = (1 << g.c) - 1;
 
-    if (warp < 4) {
+    if (tid < NP) {
         // ---------------- producers + MMA issue ----------------
-        const int n = tid;  // group within the tile = TMEM lane
-        const uint32_t lane_off = uint32_t(warp * 32) << 16;
+        const int quarter = warp & 3, part = warp >> 2;
+        const int n = quarter * 32 + (tid & 31);  // group within the tile = TMEM lane
+        const int r0 = part * DP;                 // this thread's amplitudes [r0, r0 + DP)
+        const uint32_t lane_off = uint32_t(quarter * 32) << 16;
         const uint32_t stage0 = smem_base + Lay::kOffStage + uint32_t(n * Lay::kRowStride);
         const unsigned char *my_stage[2] = {smem + Lay::kOffStage + n * Lay::kRowStride,
                                             smem + Lay::kOffStage + Lay::kStageBytes + n * Lay::kRowStride};
         constexpr uint32_t idesc = instr_desc(kTcGroups, D2, BF16);
-        // this thread's group of tile t -> its staging row
+        // this thread's share of its group of tile t -> its staging row
         auto issue = [&](int64_t t, int sb) {
             const int64_t gb = tile_base(g, t);
             const int ib = group_base<K>(g, n);
             const uint32_t dst = stage0 + uint32_t(sb * Lay::kStageBytes);
-#pragma unroll
-            for (int r = 0; r < D; ++r) {
+#pragma unroll 8
+            for (int r = r0; r < r0 + DP; ++r) {
                 const int i = ib + g.toff[r];
                 cp_async8(dst + uint32_t(r * 8), state + gb + g.runoff[i >> g.c] + (i & cmask));
             }
@@ -309,10 +321,16 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<K>()) k_tc(const TcP
             cp_async_wait1();  // this thread's copies for tile t have landed
             const float2 *x = reinterpret_cast<const float2 *>(my_stage[buf]);
             float m = 0.f;
-#pragma unroll
-            for (int r = 0; r < D; ++r) {
+#pragma unroll 8
+            for (int r = r0; r < r0 + DP; ++r) {
                 const float2 v = x[r];
                 m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
+            if (SPLIT > 1) {
+                part_max[part * kTcGroups + n] = m;
+                named_bar_sync(1, NP);
+#pragma unroll
+                for (int h = 0; h < SPLIT; ++h) m = fmaxf(m, part_max[h * kTcGroups + n]);
             }
             int e = 0;
             frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
@@ -322,8 +340,8 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<K>()) k_tc(const TcP
             if (ok) {
                 const uint32_t a_hi = tmem + lane_off + uint32_t(buf) * Lay::kBufCols;
                 const uint32_t a_lo = a_hi + uint32_t(D);
-#pragma unroll
-                for (int c0 = 0; c0 < D; c0 += 16) {
+#pragma unroll 1
+                for (int c0 = r0; c0 < r0 + DP; c0 += 16) {
                     uint32_t hv[16], lv[16];
 #pragma unroll
                     for (int u = 0; u < 16; ++u) {
@@ -334,12 +352,12 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<K>()) k_tc(const TcP
                     tmem_st16(a_lo + uint32_t(c0), lv);
                 }
                 tmem_wait_st();
-                inv_scale[buf * kTcGroups + n] = 1.f / s;
+                if (part == 0) inv_scale[buf * kTcGroups + n] = 1.f / s;
             }
             tc_fence_before();
             // every producer takes the same exit decision
-            if (named_bar_or(1, kTcGroups, !ok || *abort_flag)) break;
-            if (n == 0) {
+            if (named_bar_or(2, NP, !ok || *abort_flag)) break;
+            if (tid == 0) {
                 tc_fence_after();
                 const uint32_t a_hi = tmem + uint32_t(buf) * Lay::kBufCols;
                 const uint32_t a_lo = a_hi + uint32_t(D);
@@ -364,7 +382,7 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<K>()) k_tc(const TcP
         }
         cp_async_wait0();  // no copy may land after the CTA exits
         // drain: the last commit of each buffer must land before TMEM is freed
-        if (n == 0) {
+        if (tid == 0) {
             volatile int no_abort = 0;
             for (int b = 0; b < 2; ++b) {
                 const int cnt = (issued + 1 - b) / 2;  // tiles issued into buffer b
@@ -373,8 +391,11 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<K>()) k_tc(const TcP
         }
     } else {
         // ---------------- epilogue ----------------
-        const int n = tid - kTcGroups;            // group = TMEM lane
-        const uint32_t lane_off = uint32_t((warp - 4) * 32) << 16;
+        const int ew = warp - NP / 32;
+        const int quarter = ew & 3, part = ew >> 2;
+        const int n = quarter * 32 + (tid & 31);  // group = TMEM lane
+        const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+        constexpr int CP = D2 / SPLIT;            // accumulator columns per thread
         int it = 0;
         for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
             const int buf = it & 1;
@@ -385,8 +406,8 @@ __global__ void __launch_bounds__(kTcThreads, tc_min_blocks<K>()) k_tc(const TcP
             const int64_t gb = tile_base(g, t);
             const int ib = group_base<K>(g, n);
             const uint32_t acc = tmem + lane_off + uint32_t(buf) * Lay::kBufCols + uint32_t(2 * D);
-#pragma unroll
-            for (int c0 = 0; c0 < D2; c0 += 32) {
+#pragma unroll 1
+            for (int c0 = part * CP; c0 < (part + 1) * CP; c0 += 32) {
                 uint32_t v[32];
                 tmem_ld32(acc + uint32_t(c0), v);
                 tmem_wait_ld();
@@ -471,9 +492,9 @@ static hq_status run_tc(void *state, int n, const int *qubits, const double *mat
         constexpr size_t kSmPerSm = 228 * 1024;
         const size_t smem = std::max<size_t>(Lay::kBytes, kSmPerSm / (Lay::kCtasPerSm + 1) + 1024);
         const void *fn = (const void *)k_tc<K, BF16>;
-        const int per_sm = std::min(occupancy(fn, kTcThreads, smem), Lay::kCtasPerSm);
+        const int per_sm = std::min(occupancy(fn, tc_threads<K>(), smem), Lay::kCtasPerSm);
         const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(sm_count()) * per_sm, p.g.total_tiles)));
-        k_tc<K, BF16><<<grid, kTcThreads, smem, s>>>(p, (float2 *)state);
+        k_tc<K, BF16><<<grid, tc_threads<K>(), smem, s>>>(p, (float2 *)state);
         st = cuda_status("k_tc", cudaGetLastError());
     }
     cudaFreeAsync(dmat, s);
