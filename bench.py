@@ -4,8 +4,12 @@
 Workload (default): 30-qubit random circuit on a 5x6 grid, depth 20, sqrt(X/Y/W)
 single-qubit gates and fSim(pi/2, pi/6) on four cycling edge patterns (845
 gates), complex64 state (8 GiB, far larger than the 129 MB L2), fused into
-blocks of at most 4 qubits.  One step = initialise |0..0>, apply every fused
-block, and reduce the squared norm in FP64 -- the whole hot path.
+blocks of at most 6 qubits applied on the tensor cores (FP16 hi+lo split).
+One step = initialise |0..0>, apply every fused block, and reduce the squared
+norm in FP64 -- the whole hot path.  The other workloads (per-gate path,
+complex128, n=33 tensor-core vs CUDA-core blocks, adjoint gradients, the
+512-circuit batch) are measured after the main line and reported under
+"extras".
 
 metric: gate-apps/s = unfused gates applied per second (whole job).
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle (a
@@ -114,6 +118,35 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_sources_sha(kernel_class):
+    """Hash of the sources the kernel class is built from (ties ncu traffic
+    figures to the code they were measured on)."""
+    import hashlib
+
+    files = {"k_tc": ["k_tc.cu"], "k_gather": ["k_apply.cu"], "k_diag": ["k_apply.cu"], "k_block": ["k_apply.cu"]}
+    key = next((k for k in files if kernel_class.startswith(k)), None)
+    if key is None:
+        return None
+    h = hashlib.sha256()
+    for f in files[key] + ["hq_internal.cuh"]:
+        with open(os.path.join(ROOT, "paper_2111_06868_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel_class, n):
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json),
+    scaled by the state size; None if absent or if the kernel changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            entry = json.load(f).get(kernel_class)
+    except (OSError, ValueError):
+        return None
+    if not entry or entry.get("source_sha") != kernel_sources_sha(kernel_class):
+        return None
+    return entry["dram_bytes_per_amplitude"] * (1 << n)
+
+
 def block_class(qs, m, engine, tc_min_k):
     """Which kernel libhq launches for this block (mirrors its dispatch)."""
     d = m.shape[0]
@@ -182,6 +215,111 @@ def run_reference(args):
     }))
 
 
+def _events():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _time_blocks(n, blocks, engine, dtype, reps=1, tc_min_k=4):
+    """Seconds per pass of `blocks` over a fresh |0..0> state (CUDA events)."""
+    import torch
+    from paper_2111_06868_gb300 import hq
+
+    st = torch.empty(1 << n, dtype=dtype, device="cuda")
+    hq.hq_state_init(st)
+    hq.hq_apply_blocks(st, blocks[:2], engine=engine, tc_min_k=tc_min_k)  # warm the code paths
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        hq.hq_state_init(st)
+        hq.hq_apply_blocks(st, blocks, engine=engine, tc_min_k=tc_min_k)
+    e1.record()
+    torch.cuda.synchronize()
+    return st, e0.elapsed_time(e1) / 1e3 / reps
+
+
+def measure_extras(args):
+    """One measurement of every other workload (CUDA events)."""
+    import torch
+    from paper_2111_06868_gb300 import hq
+
+    out = {}
+    # n=30, unfused: every gate its own launch
+    circ = C.config_n30(seed=args.seed)
+    G = len(circ.gates)
+    st, t = _time_blocks(30, [(g.qubits, g.matrix) for g in circ.gates], "auto", torch.complex64)
+    out["n30_per_gate_c64"] = {"gate_apps_per_s": G / t, "s": t, "launches": G}
+    del st
+    # n=30, complex128 (FP64), unfused, on the first 120 gates
+    sub = circ.gates[:120]
+    st, t = _time_blocks(30, [(g.qubits, g.matrix) for g in sub], "auto", torch.complex128)
+    out["n30_per_gate_c128_first120"] = {"gate_apps_per_s": len(sub) / t, "s": t,
+                                         "GBps": len(sub) * 2 * (1 << 30) * 16 / t / 1e9}
+    del st
+    torch.cuda.empty_cache()
+    # n=33: fused k <= 6 on tensor cores vs CUDA cores (64 GiB state)
+    c33 = C.config_n33(seed=args.seed)
+    b33 = hq.hq_fuse(33, c33.gates, 6)
+    st, t_tc = _time_blocks(33, b33, "tc_f16", torch.complex64)
+    nrm = hq.hq_expectation(st, [(1.0, ())])
+    _, t_cc = _time_blocks(33, b33[:8], "cuda_core", torch.complex64)
+    t_cc = t_cc * len(b33) / 8
+    out["n33_fused_k6"] = {"blocks": len(b33), "gates": len(c33.gates),
+                           "tc_f16_gate_apps_per_s": len(c33.gates) / t_tc, "tc_f16_s": t_tc,
+                           "tc_f16_GBps_per_block": len(b33) * 2 * (1 << 33) * 8 / t_tc / 1e9,
+                           "cuda_core_s_extrapolated_from_8_blocks": t_cc,
+                           "tc_speedup_vs_cuda_core": t_cc / t_tc, "norm_minus_1": nrm ** 0.5 - 1}
+    del st
+    torch.cuda.empty_cache()
+    # accuracy of the tensor-core path against FP64 on the n=28 subset
+    c28 = C.config_n33(seed=args.seed, first=28)
+    ref = torch.empty(1 << 28, dtype=torch.complex128, device="cuda")
+    hq.hq_state_init(ref)
+    hq.hq_apply_blocks(ref, c28.gates)
+    st = torch.empty(1 << 28, dtype=torch.complex64, device="cuda")
+    errs = {}
+    for eng in ("tc_f16", "tc_bf16", "cuda_core"):
+        hq.hq_state_init(st)
+        hq.hq_apply_blocks(st, hq.hq_fuse(28, c28.gates, 6), engine=eng, tc_min_k=4)
+        errs[eng] = (st.to(torch.complex128) - ref).norm().item() / ref.norm().item()
+    out["n28_subset_rel_l2_vs_fp64"] = {"gates": len(c28.gates), **errs, "bar": 2e-5}
+    del st, ref
+    torch.cuda.empty_cache()
+    # adjoint gradients: n=20 ansatz, 320 angles, batch 64
+    ans = C.ansatz(20, 8)
+    H = C.ansatz_hamiltonian(20)
+    th = C.ansatz_params(ans.n_params, 64, seed=0)
+    adj = {}
+    for dt in ("complex64", "complex128"):
+        hq.hq_adjoint_grad(ans, H, th[:2], dtype=dt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hq.hq_adjoint_grad(ans, H, th, dtype=dt)
+        t = time.perf_counter() - t0
+        adj[dt] = {"grad_per_s": 64 * ans.n_params / t, "s": t}
+    out["adjoint_n20_batch64"] = adj
+    # batched serving load: 512 circuits, n ~ U{10..24}
+    cs = C.config_batch(512, seed=0)
+    Gb = sum(len(c.gates) for c in cs)
+    b = hq.Batch(cs, None, 13, 7, 0)
+    b.run()
+    e0, e1 = _events()
+    e0.record()
+    b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    lat, span = b.latencies()
+    out["batch512"] = {"gate_apps_per_s": Gb / t, "s": t, "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                       "p99_ms": float(np.percentile(lat, 99)) / 1e3, "tile": [13, 7],
+                       "launches": 1, "graph": True}
+    b.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -189,10 +327,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hq", choices=["hq", "reference"])
     ap.add_argument("--workload", default="n30", choices=["n30", "n33", "n27", "n12"])
-    ap.add_argument("--kmax", type=int, default=4)
+    ap.add_argument("--kmax", type=int, default=6)
     ap.add_argument("--dtype", default="complex64", choices=["complex64", "complex128"])
-    ap.add_argument("--engine", default="auto", choices=["auto", "cuda_core", "tc_f16", "tc_bf16"])
-    ap.add_argument("--tc-min-k", type=int, default=5)
+    ap.add_argument("--engine", default="tc_f16", choices=["auto", "cuda_core", "tc_f16", "tc_bf16"])
+    ap.add_argument("--tc-min-k", type=int, default=4)
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' sub-measurements")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--ref-gates", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -321,6 +460,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(circ)
 
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras and args.workload == "n30":
+        del state
+        torch.cuda.empty_cache()
+        extras = measure_extras(args)
+
     if rank == 0:
         eff_gbs = B * bytes_per_launch * args.steps / (elapsed / world) / 1e9
         rec = {
@@ -332,12 +477,12 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "effective_GBps": eff_gbs, "roofline_frac_effective": eff_gbs / peaks["hbm_gbs"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom, n),
                          "kernel": dom, "peak_source": peak_kind,
                          "bytes_per_launch": bytes_per_launch},
             "per_class": per_class,
             "norm2": norm, "fuse_s": fuse_s,
-            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "extras": extras,
             "gpu_launches": args.steps * (B + 3),
         }
         print(json.dumps(rec))
