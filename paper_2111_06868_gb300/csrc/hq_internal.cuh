@@ -88,6 +88,10 @@ struct TileGeom {
     int64_t state_stride;      // amplitudes between consecutive states (= 2^n)
     int64_t runoff[1 << HQ_MAX_K];  // flat offset of run j (j < 2^(L-c))
     int toff[1 << HQ_MAX_K];        // tile-local offset of local index r
+    // flat offset of local index r of group 0 in a tile; a group's base index
+    // only has non-target bits below c, so amplitude r of group n sits at
+    // tile_base + group_base(n) + goff[r]
+    int64_t goff[1 << HQ_MAX_K];
 };
 
 // Builds the geometry for targets `qubits` (k of them) on n-qubit states.

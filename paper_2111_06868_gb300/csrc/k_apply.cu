@@ -78,6 +78,8 @@ void make_geom(TileGeom &g, int n, int k, const int *qubits, int L, int64_t nsta
             if ((r >> (k - 1 - j)) & 1) off += 1 << tlpos[b[j]];
         g.toff[r] = off;
     }
+    for (int r = 0; r < (1 << k); ++r)
+        g.goff[r] = g.runoff[g.toff[r] >> c] + (g.toff[r] & ((1 << c) - 1));
     g.tiles_per_state = int64_t(1) << (n - L);
     g.total_tiles = g.tiles_per_state * nstates;
     g.state_stride = int64_t(1) << n;

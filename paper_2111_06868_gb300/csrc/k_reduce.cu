@@ -168,7 +168,8 @@ hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pau
         return HQ_OK;
     }
     const int64_t dim = int64_t(1) << n;
-    const int gx = int(std::max<int64_t>(1, std::min<int64_t>(2 * sm_count(), dim / (kRedThreads * 8))));
+    // enough CTAs per group to keep HBM busy (several per SM)
+    const int gx = int(std::max<int64_t>(1, std::min<int64_t>(8 * sm_count(), dim / (kRedThreads * 8))));
     // batches of groups that fit the parameter block
     std::vector<std::pair<int, int>> chunks;  // [g0, g1)
     for (int g0 = 0; g0 < int(groups.size());) {

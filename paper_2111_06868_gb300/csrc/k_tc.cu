@@ -42,6 +42,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "hq_internal.cuh"
@@ -288,7 +289,6 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const uint32_t smem_base = smem_u32(smem);
-    const int cmask = (1 << g.c) - 1;
 
     if (tid < NP) {
         // ---------------- producers + MMA issue ----------------
@@ -300,16 +300,19 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
         const unsigned char *my_stage[2] = {smem + Lay::kOffStage + n * Lay::kRowStride,
                                             smem + Lay::kOffStage + Lay::kStageBytes + n * Lay::kRowStride};
         constexpr uint32_t idesc = instr_desc(kTcGroups, D2, BF16);
-        // this thread's share of its group of tile t -> its staging row
+        // this thread's share of its group of tile t -> its staging row; the
+        // amplitude indices are compile-time so goff[] is a constant operand
+        const int ibase = group_base<K>(g, n);
+        auto issue_part = [&](auto part_c, const float2 *gsrc, uint32_t dst) {
+            constexpr int R0 = decltype(part_c)::value * DP;
+#pragma unroll
+            for (int r = R0; r < R0 + DP; ++r) cp_async8(dst + uint32_t(r * 8), gsrc + g.goff[r]);
+        };
         auto issue = [&](int64_t t, int sb) {
-            const int64_t gb = tile_base(g, t);
-            const int ib = group_base<K>(g, n);
+            const float2 *gsrc = state + tile_base(g, t) + ibase;
             const uint32_t dst = stage0 + uint32_t(sb * Lay::kStageBytes);
-#pragma unroll 8
-            for (int r = r0; r < r0 + DP; ++r) {
-                const int i = ib + g.toff[r];
-                cp_async8(dst + uint32_t(r * 8), state + gb + g.runoff[i >> g.c] + (i & cmask));
-            }
+            if (part == 0) issue_part(std::integral_constant<int, 0>{}, gsrc, dst);
+            else issue_part(std::integral_constant<int, SPLIT - 1>{}, gsrc, dst);
         };
         if (int64_t(blockIdx.x) < g.total_tiles) issue(blockIdx.x, 0);
         cp_async_commit();
@@ -394,6 +397,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
         const int ew = warp - NP / 32;
         const int quarter = ew & 3, part = ew >> 2;
         const int n = quarter * 32 + (tid & 31);  // group = TMEM lane
+        const int ibase = group_base<K>(g, n);
         const uint32_t lane_off = uint32_t(quarter * 32) << 16;
         constexpr int CP = D2 / SPLIT;            // accumulator columns per thread
         int it = 0;
@@ -403,23 +407,26 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
             if (!__all_sync(0xffffffffu, mbar_wait(&bar[buf], uint32_t((it / 2) & 1), abort_flag))) break;
             tc_fence_after();
             const float mul = inv_scale[buf * kTcGroups + n] * p.out_mul;
-            const int64_t gb = tile_base(g, t);
-            const int ib = group_base<K>(g, n);
+            float2 *gdst = state + tile_base(g, t) + ibase;
             const uint32_t acc = tmem + lane_off + uint32_t(buf) * Lay::kBufCols + uint32_t(2 * D);
-#pragma unroll 1
-            for (int c0 = part * CP; c0 < (part + 1) * CP; c0 += 32) {
-                uint32_t v[32];
-                tmem_ld32(acc + uint32_t(c0), v);
-                tmem_wait_ld();
+            auto drain_part = [&](auto part_c) {
+                constexpr int C0 = decltype(part_c)::value * CP;
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    float2 o;
-                    o.x = __uint_as_float(v[2 * u]) * mul;
-                    o.y = __uint_as_float(v[2 * u + 1]) * mul;
-                    const int i = ib + g.toff[c0 / 2 + u];
-                    state[gb + g.runoff[i >> g.c] + (i & cmask)] = o;
+                for (int c0 = C0; c0 < C0 + CP; c0 += 32) {
+                    uint32_t v[32];
+                    tmem_ld32(acc + uint32_t(c0), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        float2 o;
+                        o.x = __uint_as_float(v[2 * u]) * mul;
+                        o.y = __uint_as_float(v[2 * u + 1]) * mul;
+                        gdst[g.goff[c0 / 2 + u]] = o;
+                    }
                 }
-            }
+            };
+            if (part == 0) drain_part(std::integral_constant<int, 0>{});
+            else drain_part(std::integral_constant<int, SPLIT - 1>{});
             tc_fence_before();
             mbar_arrive(&bar[2 + buf]);
         }
