@@ -304,8 +304,23 @@ static hq_status plan_circuit(const hq_circuit &c, int ci, int R0, int h, BatchP
                 if (bp.hb[j] == b) return R + j;
             return -1;
         };
-        for (int g : ps[pi].gates) {
-            const hq_gate &gt = c.gates[g];
+        // the pass's gates, fused with the same compress rule into blocks of at
+        // most 2 qubits (fewer sweeps over the tile in shared memory)
+        std::vector<hq_gate> pg;
+        for (int g : ps[pi].gates) pg.push_back(c.gates[g]);
+        std::vector<hq_gate> fb(std::max<size_t>(pg.size(), 1));
+        std::vector<double> pool(std::max<size_t>(pg.size(), 1) * 2 * 16);
+        int nb = int(fb.size());
+        if (!pg.empty()) {
+            const hq_status fst = hq_fuse(n, pg.data(), int(pg.size()), 2, fb.data(), &nb, pool.data(),
+                                          int64_t(pool.size()), nullptr);
+            if (fst != HQ_OK) return fst;
+        } else {
+            nb = 0;
+        }
+        bp.ng = nb;
+        for (int i = 0; i < nb; ++i) {
+            const hq_gate &gt = fb[i];
             BGate bg;
             std::memset(&bg, 0, sizeof(bg));
             bg.k = gt.k;

@@ -198,26 +198,27 @@ __host__ __device__ __forceinline__ uint32_t core_off(int row, int kk, int Kdim)
     return uint32_t((row >> 3) * (Kdim * 16) + (kk >> 3) * 128 + (row & 7) * 16 + (kk & 7) * 2);
 }
 
-// hi = round(v), lo = round(v - hi), packed in pairs (16-bit each)
+// hi = round(v), lo = round(v - hi), packed in pairs (16-bit each); the
+// packed conversions run on the full-rate pipes
 template <bool BF16> struct Split;
 template <> struct Split<false> {
     __device__ static uint32_t pack(float a, float b, uint32_t &lo)
     {
-        const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
-        const __half la = __float2half_rn(a - __half2float(ha));
-        const __half lb = __float2half_rn(b - __half2float(hb));
-        lo = uint32_t(__half_as_ushort(la)) | (uint32_t(__half_as_ushort(lb)) << 16);
-        return uint32_t(__half_as_ushort(ha)) | (uint32_t(__half_as_ushort(hb)) << 16);
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+        return *reinterpret_cast<const uint32_t *>(&h);
     }
 };
 template <> struct Split<true> {
     __device__ static uint32_t pack(float a, float b, uint32_t &lo)
     {
-        const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-        const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
-        const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
-        lo = uint32_t(__bfloat16_as_ushort(la)) | (uint32_t(__bfloat16_as_ushort(lb)) << 16);
-        return uint32_t(__bfloat16_as_ushort(ha)) | (uint32_t(__bfloat16_as_ushort(hb)) << 16);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+        lo = *reinterpret_cast<const uint32_t *>(&l);
+        return *reinterpret_cast<const uint32_t *>(&h);
     }
 };
 
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
             cp_async_wait1();  // this thread's copies for tile t have landed
             const float2 *x = reinterpret_cast<const float2 *>(my_stage[buf]);
             float m = 0.f;
-#pragma unroll 8
+#pragma unroll
             for (int r = r0; r < r0 + DP; ++r) {
                 const float2 v = x[r];
                 m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
             if (ok) {
                 const uint32_t a_hi = tmem + lane_off + uint32_t(buf) * Lay::kBufCols;
                 const uint32_t a_lo = a_hi + uint32_t(D);
-#pragma unroll 1
+#pragma unroll
                 for (int c0 = r0; c0 < r0 + DP; c0 += 16) {
                     uint32_t hv[16], lv[16];
 #pragma unroll
