@@ -300,23 +300,28 @@ def measure_extras(args):
         t = time.perf_counter() - t0
         adj[dt] = {"grad_per_s": 64 * ans.n_params / t, "s": t}
     out["adjoint_n20_batch64"] = adj
-    # batched serving load: 512 circuits, n ~ U{10..24}
+    # batched serving load: 512 circuits, n ~ U{10..24}; largest-first queue
+    # (throughput) and smallest-first queue (median latency)
     cs = C.config_batch(512, seed=0)
     Gb = sum(len(c.gates) for c in cs)
-    b = hq.Batch(cs, None, 13, 7, 0)
-    b.run()
-    e0, e1 = _events()
-    e0.record()
-    b.run()
-    e1.record()
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3
-    lat, span = b.latencies()
-    out["batch512"] = {"gate_apps_per_s": Gb / t, "s": t, "p50_ms": float(np.percentile(lat, 50)) / 1e3,
-                       "p99_ms": float(np.percentile(lat, 99)) / 1e3, "tile": [13, 7],
-                       "launches": 1, "graph": True}
-    b.close()
-    torch.cuda.empty_cache()
+    bres = {}
+    for name, small_first in (("largest_first", 0), ("smallest_first", 1)):
+        b = hq.Batch(cs, None, 13, 7, 0, small_first)
+        b.run()
+        e0, e1 = _events()
+        e0.record()
+        b.run()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        lat, span = b.latencies()
+        bres[name] = {"gate_apps_per_s": Gb / t, "s": t, "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                      "p99_ms": float(np.percentile(lat, 99)) / 1e3}
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+    out["batch512"] = {"circuits": len(cs), "gates": Gb, "tile": [13, 7], "launches_per_run": 1, "graph": True,
+                       **bres}
     return out
 
 

@@ -245,6 +245,7 @@ typedef struct {
     int tile_bits;   /* log2 amplitudes per shared-memory tile, 6..13 (0 = 12) */
     int max_high;    /* high bits per pass, 1..8, < tile_bits (0 = 6) */
     int ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
+    int small_first; /* queue circuits smallest first (lower median latency) instead of largest first */
 } hq_batch_config;
 
 typedef struct hq_batch hq_batch; /* opaque plan + instantiated CUDA graph */

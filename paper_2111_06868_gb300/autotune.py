@@ -8,9 +8,11 @@ import hashlib
 import json
 import os
 
+import numpy as np
+
 from . import hq
 
-CANDIDATES = [(12, 6, 0), (13, 7, 0), (13, 6, 0), (11, 5, 0), (12, 5, 0), (12, 6, 2)]
+CANDIDATES = [(12, 6, 0, 0), (13, 7, 0, 0), (13, 6, 0, 0), (11, 5, 0, 0), (13, 7, 0, 1), (12, 6, 0, 1)]
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "hq_gb300", "autotune.json")
 
 
@@ -29,17 +31,20 @@ def _load(path):
         return {}
 
 
-def tune(circuits, states=None, candidates=CANDIDATES, reps: int = 3, cache_path: str | None = DEFAULT_CACHE):
-    """Returns (tile_bits, max_high, ctas_per_sm, timings) with the shortest
-    median makespan; reuses the cached choice when the signature matches."""
+def tune(circuits, states=None, candidates=CANDIDATES, reps: int = 3, cache_path: str | None = DEFAULT_CACHE,
+         objective: str = "makespan"):
+    """Returns (tile_bits, max_high, ctas_per_sm, small_first, timings) with the
+    best score -- median makespan, or median per-circuit latency when
+    objective="p50" -- reusing the cached choice when the signature matches."""
     import torch
 
     dev = torch.cuda.get_device_name()
-    key = f"{dev}|{signature(circuits)}"
+    key = f"{dev}|{signature(circuits)}|{objective}"
     if cache_path:
         cached = _load(cache_path).get(key)
         if cached:
             return tuple(cached["choice"]) + (cached.get("timings", {}),)
+    candidates = [tuple(c) + (0,) * (4 - len(c)) for c in candidates]
     timings = {}
     for cand in candidates:
         b = hq.Batch(circuits, states, *cand)
@@ -47,7 +52,8 @@ def tune(circuits, states=None, candidates=CANDIDATES, reps: int = 3, cache_path
         spans = []
         for _ in range(reps):
             b.run()
-            spans.append(b.latencies()[1])
+            lat, span = b.latencies()
+            spans.append(float(np.percentile(lat, 50)) if objective == "p50" else span)
         b.close()
         timings[str(cand)] = sorted(spans)[len(spans) // 2]
     best = min(candidates, key=lambda c: timings[str(c)])

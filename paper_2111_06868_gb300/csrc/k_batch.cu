@@ -11,12 +11,15 @@
 // Sec. 3.1's compress().  A circuit with n <= R + h is one pass over one tile:
 // it never leaves shared memory except for the final store.
 //
-// Scheduling: one persistent kernel (grid = SMs x CTAs per SM) pulls work from
-// a device-side ready queue of passes.  The queue starts with every circuit's
-// first pass (largest circuits first); CTAs take tiles of the queue head with
-// an atomic counter; the CTA finishing the last tile of a pass appends the
-// circuit's next pass.  The first pass builds |0..0> in shared memory instead of
-// loading it.  Tile data written by other CTAs is read through L2 (ld.global.cg)
+// Scheduling: one persistent kernel (grid = SMs x CTAs per SM) pulls tiles by
+// priority.  Circuits sit in a priority list (largest first for makespan, or
+// smallest first for median latency); each circuit has a current pass.  Warp 0
+// of a CTA scans the list 32 circuits at a time (ballot) from a watermark that
+// skips finished circuits and takes a tile of the first current pass that still
+// has one (atomic counter); the CTA finishing a pass's last tile advances the
+// circuit to its next pass in place, so a circuit runs its passes back to back
+// instead of waiting behind every other circuit.  The first pass builds |0..0>
+// in shared memory instead of loading it.  Tile data written by other CTAs is read through L2 (ld.global.cg)
 // after an acquire fence, because L1 is not coherent within a launch.  Every
 // wait is bounded: with no progress for 2 s the kernel raises the device error
 // flag and exits (reported as HQ_ERR_TIMEOUT).  Per-circuit completion times
@@ -76,8 +79,9 @@ struct BatchParams {
     // per-run counters (zeroed by the graph before every launch)
     int *next_tile;          // [P]
     int *done_tile;          // [P]
-    int *queue;              // [P] pass ids, -1 = not yet written
-    int *qhead, *qtail;      // queue counters (qtail preset to C)
+    const int *prio;         // [C] circuit ids, highest priority first
+    int *cur_pass;           // [C] current pass of each circuit, -1 once finished
+    int *wm;                 // prio[0 .. *wm) are finished
     int *completed;
     unsigned long long *end_ns;  // [C]
     unsigned long long *t0;      // kernel start (min over CTAs)
@@ -112,40 +116,62 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
     if (threadIdx.x == 0) atomicMin(p.t0, now_ns());
 
     for (;;) {
-        // ---------------- find work (thread 0) ----------------
-        if (threadIdx.x == 0) {
+        // ---------------- find work (warp 0) ----------------
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
             int stop = 0, pid = -1;
-            long long tid = -1;
-            unsigned long long last_progress = now_ns();
-            while (pid < 0 && !stop) {
-                if (ld_volatile(p.completed) >= p.C) { stop = 1; break; }
-                const int h = ld_volatile(p.qhead);
-                if (h < ld_volatile(p.qtail)) {
-                    const int q = ld_volatile(&p.queue[h]);
-                    if (q >= 0) {
-                        __threadfence();
-                        const int t = atomicAdd(&p.next_tile[q], 1);
-                        const long long nt = p.pass[q].ntiles;
-                        if (t < nt) {
-                            pid = q;
-                            tid = t;
-                            if (t == nt - 1) atomicCAS(p.qhead, h, h + 1);  // pass fully handed out
+            long long tile = -1;
+            const unsigned long long t_start = now_ns();
+            for (;;) {
+                if (ld_volatile(p.completed) >= p.C) {
+                    stop = 1;
+                    break;
+                }
+                const int w = ld_volatile(p.wm);
+                bool found = false;
+                for (int base = w; base < p.C && !found; base += 32) {
+                    const int i = base + lane;
+                    int q = -1;
+                    bool avail = false;
+                    if (i < p.C) {
+                        q = ld_volatile(&p.cur_pass[p.prio[i]]);
+                        if (q >= 0) avail = ld_volatile(&p.next_tile[q]) < p.pass[q].ntiles;
+                    }
+                    if (base == w) {  // move the watermark over finished circuits at the front
+                        const unsigned fin = __ballot_sync(0xffffffffu, i < p.C && q < 0);
+                        const int lead = (~fin) ? __ffs(~fin) - 1 : 32;
+                        if (lane == 0 && lead > 0) atomicMax(p.wm, w + lead);
+                    }
+                    unsigned mask = __ballot_sync(0xffffffffu, avail);
+                    while (mask) {
+                        const int leader = __ffs(mask) - 1;
+                        int t = 0;
+                        if (lane == leader) t = atomicAdd(&p.next_tile[q], 1);
+                        t = __shfl_sync(0xffffffffu, t, leader);
+                        const int qq = __shfl_sync(0xffffffffu, q, leader);
+                        if (t < p.pass[qq].ntiles) {
+                            pid = qq;
+                            tile = t;
+                            found = true;
                             break;
                         }
-                        atomicCAS(p.qhead, h, h + 1);
-                        last_progress = now_ns();
-                        continue;
+                        mask &= mask - 1;
                     }
                 }
-                if (now_ns() - last_progress > kBatchStallNs) {
-                    atomicOr(&g_device_error, 2u);
+                if (found) break;
+                if (now_ns() - t_start > kBatchStallNs) {
+                    if (lane == 0) atomicOr(&g_device_error, 2u);
                     stop = 1;
+                    break;
                 }
             }
-            s_pass = pid;
-            s_tile = tid;
-            s_stop = stop;
-            if (pid >= 0) s_ps = p.pass[pid];
+            if (lane == 0) {
+                __threadfence();  // acquire: the pass's input was written by other CTAs
+                s_pass = pid;
+                s_tile = tile;
+                s_stop = stop;
+                if (pid >= 0) s_ps = p.pass[pid];
+            }
         }
         __syncthreads();
         if (s_stop) break;
@@ -228,10 +254,10 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
                 if (ps.next < 0) {
                     p.end_ns[ps.circuit] = now_ns();
                     __threadfence();
+                    atomicExch(&p.cur_pass[ps.circuit], -1);
                     atomicAdd(p.completed, 1);
                 } else {
-                    const int slot = atomicAdd(p.qtail, 1);
-                    atomicExch(&p.queue[slot], ps.next);
+                    atomicExch(&p.cur_pass[ps.circuit], ps.next);
                 }
             }
         }
@@ -246,6 +272,7 @@ struct BatchPlan {
     std::vector<BPass> pass;
     std::vector<BGate> gate;
     std::vector<int> first_pass;  // per circuit
+    std::vector<int> prio;        // circuit ids, highest priority first
     int64_t total_gates = 0;
 };
 
@@ -337,7 +364,7 @@ static hq_status plan_circuit(const hq_circuit &c, int ci, int R0, int h, BatchP
 }
 
 struct BatchLayout {
-    size_t circ, pass, gate, next_tile, done_tile, queue, qhead, end_ns, image, total, counters_begin,
+    size_t circ, pass, gate, prio, next_tile, done_tile, cur_pass, wm, end_ns, image, total, counters_begin,
         counters_bytes;
 };
 
@@ -347,11 +374,13 @@ static BatchLayout batch_layout(size_t C, size_t P, size_t G)
     L.circ = 0;
     L.pass = align_up256(L.circ + C * sizeof(BCircuit));
     L.gate = align_up256(L.pass + P * sizeof(BPass));
-    L.next_tile = align_up256(L.gate + std::max<size_t>(G, 1) * sizeof(BGate));
+    L.prio = align_up256(L.gate + std::max<size_t>(G, 1) * sizeof(BGate));
+    // per-run counters from here on, reset from the image before every run
+    L.next_tile = align_up256(L.prio + C * sizeof(int));
     L.done_tile = L.next_tile + P * sizeof(int);
-    L.queue = L.done_tile + P * sizeof(int);
-    L.qhead = align_up256(L.queue + P * sizeof(int));  // qhead, qtail, completed, pad, t0 (u64)
-    L.end_ns = align_up256(L.qhead + 32);
+    L.cur_pass = L.done_tile + P * sizeof(int);
+    L.wm = align_up256(L.cur_pass + C * sizeof(int));  // wm, completed, pad, pad, t0 (u64)
+    L.end_ns = align_up256(L.wm + 32);
     L.image = align_up256(L.end_ns + C * sizeof(unsigned long long));
     L.counters_begin = L.next_tile;
     L.counters_bytes = L.image - L.next_tile;
@@ -383,23 +412,22 @@ static hq_status check_batch(const hq_circuit *cs, int C, const hq_batch_config 
     return HQ_OK;
 }
 
-static hq_status plan_batch(const hq_circuit *cs, int C, int R0, int h, BatchPlan &pl)
+static hq_status plan_batch(const hq_circuit *cs, int C, int R0, int h, int small_first, BatchPlan &pl)
 {
-    // circuits in descending size order: big passes are queued first
+    // priority order of the circuits: largest first (shortest
+    // makespan) or smallest first (lowest median completion time)
     std::vector<int> order(C);
     for (int c = 0; c < C; ++c) order[c] = c;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cs[a].n > cs[b].n; });
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return small_first ? cs[a].n < cs[b].n : cs[a].n > cs[b].n; });
     pl.circ.resize(C);
-    std::vector<int> fp(C);
     for (int c = 0; c < C; ++c) {
         pl.circ[c].state = static_cast<float2 *>(cs[c].state);
         pl.circ[c].n = cs[c].n;
         hq_status st = plan_circuit(cs[c], c, R0, h, pl);
         if (st != HQ_OK) return st;
-        fp[c] = pl.first_pass.back();
     }
-    pl.first_pass.clear();
-    for (int c : order) pl.first_pass.push_back(fp[c]);
+    pl.prio = order;
     return HQ_OK;
 }
 
@@ -412,7 +440,7 @@ extern "C" size_t hq_batch_workspace_bytes(const hq_circuit *cs, int C, const hq
     int R0, h, per_sm;
     if (check_batch(cs, C, cfg, R0, h, per_sm) != HQ_OK) return 0;
     BatchPlan pl;
-    if (plan_batch(cs, C, R0, h, pl) != HQ_OK) return 0;
+    if (plan_batch(cs, C, R0, h, cfg ? cfg->small_first : 0, pl) != HQ_OK) return 0;
     return batch_layout(C, pl.pass.size(), pl.gate.size()).total;
 }
 
@@ -427,7 +455,7 @@ extern "C" hq_status hq_batch_create(const hq_circuit *cs, int C, const hq_batch
     if (!workspace) return HQ_ERR_NULL;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return HQ_ERR_ALIGN;
     BatchPlan pl;
-    if ((st = plan_batch(cs, C, R0, h, pl)) != HQ_OK) return st;
+    if ((st = plan_batch(cs, C, R0, h, cfg ? cfg->small_first : 0, pl)) != HQ_OK) return st;
     const size_t P = pl.pass.size();
     const BatchLayout L = batch_layout(C, P, pl.gate.size());
     if (ws_bytes < L.total) return HQ_ERR_CAPACITY;
@@ -439,15 +467,13 @@ extern "C" hq_status hq_batch_create(const hq_circuit *cs, int C, const hq_batch
         HQ_CUDA(cudaMemcpyAsync(ws + L.gate, pl.gate.data(), pl.gate.size() * sizeof(BGate), cudaMemcpyHostToDevice, s));
     HQ_CUDA(cudaStreamSynchronize(s));
 
-    // per-run counter image: queue = first passes then -1, qtail = C, t0 = max
+    HQ_CUDA(cudaMemcpyAsync(ws + L.prio, pl.prio.data(), C * sizeof(int), cudaMemcpyHostToDevice, s));
+    // per-run counter image: tile counters 0, every circuit at its first pass,
+    // watermark 0, nothing completed, t0 = max
     std::vector<char> image(L.counters_bytes, 0);
-    int *q = reinterpret_cast<int *>(image.data() + (L.queue - L.counters_begin));
-    for (size_t i = 0; i < P; ++i) q[i] = i < size_t(C) ? pl.first_pass[i] : -1;
-    int *qc = reinterpret_cast<int *>(image.data() + (L.qhead - L.counters_begin));
-    qc[0] = 0;  // head
-    qc[1] = C;  // tail
-    qc[2] = 0;  // completed
-    *reinterpret_cast<unsigned long long *>(image.data() + (L.qhead - L.counters_begin) + 16) = ~0ull;  // t0
+    int *cp = reinterpret_cast<int *>(image.data() + (L.cur_pass - L.counters_begin));
+    for (int c = 0; c < C; ++c) cp[c] = pl.first_pass[c];
+    *reinterpret_cast<unsigned long long *>(image.data() + (L.wm - L.counters_begin) + 16) = ~0ull;  // t0
 
     int smem_L = 0;
     for (auto &ps : pl.pass) smem_L = std::max(smem_L, ps.R + ps.nh);
@@ -461,11 +487,11 @@ extern "C" hq_status hq_batch_create(const hq_circuit *cs, int C, const hq_batch
     bp.P = int(P);
     bp.next_tile = reinterpret_cast<int *>(ws + L.next_tile);
     bp.done_tile = reinterpret_cast<int *>(ws + L.done_tile);
-    bp.queue = reinterpret_cast<int *>(ws + L.queue);
-    bp.qhead = reinterpret_cast<int *>(ws + L.qhead);
-    bp.qtail = bp.qhead + 1;
-    bp.completed = bp.qhead + 2;
-    bp.t0 = reinterpret_cast<unsigned long long *>(ws + L.qhead + 16);
+    bp.prio = reinterpret_cast<const int *>(ws + L.prio);
+    bp.cur_pass = reinterpret_cast<int *>(ws + L.cur_pass);
+    bp.wm = reinterpret_cast<int *>(ws + L.wm);
+    bp.completed = bp.wm + 1;
+    bp.t0 = reinterpret_cast<unsigned long long *>(ws + L.wm + 16);
     bp.end_ns = reinterpret_cast<unsigned long long *>(ws + L.end_ns);
 
     const int occ = occupancy((const void *)k_batch, kBThreads, smem);
@@ -477,7 +503,7 @@ extern "C" hq_status hq_batch_create(const hq_circuit *cs, int C, const hq_batch
     b->smem = smem;
     b->ws = ws;
     b->off_end_ns = L.end_ns;
-    b->off_t0 = L.qhead + 16;
+    b->off_t0 = L.wm + 16;
     b->total_gates = pl.total_gates;
     b->graph = nullptr;
     b->exec = nullptr;

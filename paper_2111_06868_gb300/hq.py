@@ -66,7 +66,8 @@ class hq_circuit(ctypes.Structure):
 
 
 class hq_batch_config(ctypes.Structure):
-    _fields_ = [("tile_bits", ctypes.c_int), ("max_high", ctypes.c_int), ("ctas_per_sm", ctypes.c_int)]
+    _fields_ = [("tile_bits", ctypes.c_int), ("max_high", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("small_first", ctypes.c_int)]
 
 
 _lib = None
@@ -332,9 +333,10 @@ def _batch_structs(circuits, states):
     return arr, keep
 
 
-def hq_batch_workspace_bytes(circuits, tile_bits: int = 0, max_high: int = 0, ctas_per_sm: int = 0) -> int:
+def hq_batch_workspace_bytes(circuits, tile_bits: int = 0, max_high: int = 0, ctas_per_sm: int = 0,
+                             small_first: int = 0) -> int:
     arr, keep = _batch_structs(circuits, None)
-    cfg = hq_batch_config(tile_bits, max_high, ctas_per_sm)
+    cfg = hq_batch_config(tile_bits, max_high, ctas_per_sm, small_first)
     return int(load().hq_batch_workspace_bytes(arr, len(circuits), ctypes.byref(cfg)))
 
 
@@ -343,14 +345,14 @@ class Batch:
     ``states`` (one complex64 tensor of 2^n per circuit) is allocated if not given."""
 
     def __init__(self, circuits, states=None, tile_bits: int = 0, max_high: int = 0, ctas_per_sm: int = 0,
-                 stream=None):
+                 small_first: int = 0, stream=None):
         import torch
 
         self.circuits = list(circuits)
         if states is None:
             states = [torch.empty(1 << c.n, dtype=torch.complex64, device="cuda") for c in self.circuits]
         self.states = states
-        self.cfg = hq_batch_config(tile_bits, max_high, ctas_per_sm)
+        self.cfg = hq_batch_config(tile_bits, max_high, ctas_per_sm, small_first)
         arr, keep = _batch_structs(self.circuits, states)
         need = load().hq_batch_workspace_bytes(arr, len(self.circuits), ctypes.byref(self.cfg))
         if need == 0:

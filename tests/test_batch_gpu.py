@@ -33,7 +33,7 @@ def rel_l2(got, want):
     return float(np.linalg.norm(got - want) / np.linalg.norm(want))
 
 
-@pytest.mark.parametrize("cfg", [(0, 0, 0), (8, 3, 0), (11, 5, 2), (13, 7, 0), (6, 1, 1)])
+@pytest.mark.parametrize("cfg", [(0, 0, 0, 0), (8, 3, 0, 1), (11, 5, 2, 0), (13, 7, 0, 1), (6, 1, 1, 0)])
 def test_batch_matches_oracle(hq, cfg):
     cs = small_batch()
     b = hq.Batch(cs, None, *cfg)
@@ -82,7 +82,10 @@ def test_autotuner_picks_a_candidate(hq, tmp_path):
     from paper_2111_06868_gb300 import autotune
 
     cs = small_batch()[:12]
-    best = autotune.tune(cs, candidates=[(12, 6, 0), (11, 5, 0)], reps=2, cache_path=str(tmp_path / "a.json"))
-    assert best[:3] in [(12, 6, 0), (11, 5, 0)]
-    again = autotune.tune(cs, candidates=[(12, 6, 0), (11, 5, 0)], reps=2, cache_path=str(tmp_path / "a.json"))
-    assert again[:3] == best[:3]
+    cands = [(12, 6, 0, 0), (11, 5, 0, 1)]
+    best = autotune.tune(cs, candidates=cands, reps=2, cache_path=str(tmp_path / "a.json"))
+    assert best[:4] in cands
+    again = autotune.tune(cs, candidates=cands, reps=2, cache_path=str(tmp_path / "a.json"))
+    assert again[:4] == best[:4]
+    p50 = autotune.tune(cs, candidates=cands, reps=2, cache_path=str(tmp_path / "a.json"), objective="p50")
+    assert p50[:4] in cands
