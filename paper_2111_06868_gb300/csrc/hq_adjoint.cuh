@@ -1,0 +1,50 @@
+// hq_adjoint.cuh -- pass plan of the adjoint sweep (k_adjoint_pass.cu).
+#pragma once
+
+#include <vector>
+
+#include "hq_internal.cuh"
+
+namespace hq {
+
+constexpr int kApMaxHigh = 8;
+constexpr int kApMaxRot = 128;  // rotations per pass (one shared-memory accumulator each)
+
+// One gate of a pass, at tile positions tpos (qubits[0], qubits[1]).
+struct AOp {
+    int kind;      // 0 dense 1q, 1 dense 2q, 2 diagonal (k = 1, 2), 3 rotation
+    int k;
+    int tpos[2];
+    int axis;      // rotation: 'X', 'Y', 'Z'
+    int param;     // rotation: parameter index
+    int row;       // rotation: index among the circuit's rotations (partial-sum row)
+    int slot;      // rotation: accumulator slot within the pass
+    double2 m[16]; // fixed gates: 2^k x 2^k matrix, row-major
+};
+
+struct APass {
+    int R, nh;
+    int hb[kApMaxHigh];
+    int o0, no;     // ops [o0, o0 + no)
+    int nrot;
+    int64_t ntiles; // tiles per state
+};
+
+struct AdjPlan {
+    std::vector<APass> pass;
+    std::vector<AOp> op;
+    int tile_bits = 0;
+};
+
+// Plans the passes; false when an op is wider than two qubits (the caller
+// then uses the one-launch-per-op sweep).
+bool adj_plan(int n, hq_dtype dt, const hq_op *ops, int G, AdjPlan &plan);
+
+// Launches one pass over all `batch` sets (rev: phi and lambda, gradients).
+hq_status adj_launch_pass(hq_dtype dt, bool rev, const APass &ps, const AOp *dev_ops, void *phi, int n, int batch,
+                          const double2 *cs, int P, double *partials, int nbx, cudaStream_t s);
+
+// cs[i] = (cos theta_i/2, sin theta_i/2)
+hq_status adj_half_angles(const double *theta, int64_t count, double2 *cs, cudaStream_t s);
+
+}  // namespace hq

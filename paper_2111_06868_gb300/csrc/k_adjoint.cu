@@ -16,14 +16,18 @@
 // recomputed phi is replaced by the stored one (bounds the drift of
 // recomputing by U^+ in complex64).
 //
-// Rotation kernels reuse the coalesced shared-memory tile of k_apply.cu with
-// K = 1; each CTA works on one parameter set (grid.y), so its 2x2 matrix comes
-// from that set's angle and its FP64 partial sums belong to that set.
+// When every op acts on at most two qubits (the common case) the sweeps run
+// as tile-resident passes of many gates each (k_adjoint_pass.cu).  Otherwise
+// each op is one launch: rotation kernels reuse the coalesced shared-memory
+// tile of k_apply.cu with K = 1; each CTA works on one parameter set (grid.y),
+// so its 2x2 matrix comes from that set's angle and its FP64 partial sums
+// belong to that set.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
+#include "hq_adjoint.cuh"
 #include "hq_internal.cuh"
 
 namespace hq {
@@ -179,7 +183,7 @@ static int ctas_per_state(int n) { return int(std::min<int64_t>(64, std::max<int
 static size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct AdjLayout {
-    size_t phi, ckpt, theta, part, res, total;
+    size_t phi, ckpt, theta, cs, ops, part, res, total;
 };
 
 static AdjLayout adj_layout(int n, hq_dtype dt, int G, int P, int batch, int checkpoints)
@@ -191,7 +195,9 @@ static AdjLayout adj_layout(int n, hq_dtype dt, int G, int P, int batch, int che
     L.phi = 0;
     L.ckpt = align_up(L.phi + 2 * state);
     L.theta = align_up(L.ckpt + size_t(checkpoints) * state);
-    L.part = align_up(L.theta + sizeof(double) * size_t(batch) * std::max(P, 1));
+    L.cs = align_up(L.theta + sizeof(double) * size_t(batch) * std::max(P, 1));
+    L.ops = align_up(L.cs + sizeof(double2) * size_t(batch) * std::max(P, 1));
+    L.part = align_up(L.ops + sizeof(AOp) * size_t(std::max(G, 1)));
     L.res = align_up(L.part + sizeof(double) * (size_t(G) + 1) * batch * nbx);
     L.total = align_up(L.res + sizeof(double) * (size_t(G) + 1) * batch);
     return L;
@@ -287,23 +293,39 @@ extern "C" hq_status hq_adjoint_grad(int n, hq_dtype dt, const hq_op *ops, int G
         HQ_CUDA(cudaMemcpyAsync(theta, theta_host, sizeof(double) * size_t(batch) * P, cudaMemcpyHostToDevice, s));
     if ((st = launch_init(phi, n, dt, tokens, batch, s)) != HQ_OK) return st;
 
-    // checkpoint m_c = round((c+1) G / (C+1)): forward state after m_c ops
+    // Gates on at most two qubits: tile-resident passes (k_adjoint_pass.cu);
+    // otherwise one launch per op.  Checkpoint m_c = round((c+1) U / (C+1))
+    // stores the forward state after m_c units (passes or ops).
+    AdjPlan plan;
+    const bool passes = adj_plan(n, dt, ops, G, plan);
+    const int units = passes ? int(plan.pass.size()) : G;
     std::vector<int> ck(checkpoints);
     for (int c = 0; c < checkpoints; ++c) {
-        ck[c] = int((int64_t(c + 1) * G) / (checkpoints + 1));
-        if (ck[c] < 1 || ck[c] > G - 1 || (c > 0 && ck[c] == ck[c - 1])) ck[c] = -1;  // unused slot
+        ck[c] = int((int64_t(c + 1) * units) / (checkpoints + 1));
+        if (ck[c] < 1 || ck[c] > units - 1 || (c > 0 && ck[c] == ck[c - 1])) ck[c] = -1;  // unused slot
+    }
+    double2 *cs = reinterpret_cast<double2 *>(ws + L.cs);
+    AOp *dev_ops = reinterpret_cast<AOp *>(ws + L.ops);
+    if (passes) {
+        if ((st = adj_half_angles(theta, int64_t(batch) * P, cs, s)) != HQ_OK) return st;
+        if (!plan.op.empty())
+            HQ_CUDA(cudaMemcpyAsync(dev_ops, plan.op.data(), sizeof(AOp) * plan.op.size(), cudaMemcpyHostToDevice, s));
     }
 
     // forward
-    for (int g = 0; g < G; ++g) {
-        const hq_op &o = ops[g];
-        if (o.kind == HQ_OP_MATRIX)
-            st = launch_gate(phi, n, dt, o.k, o.qubits, o.matrix, batch, HQ_ENGINE_AUTO, s);
-        else
-            st = run_rot_dt(dt, false, phi, n, o.qubits[0], o.axis, o.param, theta, P, batch, nullptr, s);
+    for (int u = 0; u < units; ++u) {
+        if (passes) {
+            st = adj_launch_pass(dt, false, plan.pass[u], dev_ops, phi, n, batch, cs, P, nullptr, nbx, s);
+        } else {
+            const hq_op &o = ops[u];
+            if (o.kind == HQ_OP_MATRIX)
+                st = launch_gate(phi, n, dt, o.k, o.qubits, o.matrix, batch, HQ_ENGINE_AUTO, s);
+            else
+                st = run_rot_dt(dt, false, phi, n, o.qubits[0], o.axis, o.param, theta, P, batch, nullptr, s);
+        }
         if (st != HQ_OK) return st;
         for (int c = 0; c < checkpoints; ++c)
-            if (ck[c] == g + 1)
+            if (ck[c] == u + 1)
                 HQ_CUDA(cudaMemcpyAsync(ckpt + c * state_bytes, phi, state_bytes, cudaMemcpyDeviceToDevice, s));
     }
 
@@ -343,24 +365,29 @@ extern "C" hq_status hq_adjoint_grad(int n, hq_dtype dt, const hq_op *ops, int G
             if (ops[g].kind == HQ_OP_ROT) rot_index[g] = r++;
     }
     std::vector<double> dag;
-    for (int g = G - 1; g >= 0; --g) {
-        const hq_op &o = ops[g];
-        if (o.kind == HQ_OP_MATRIX) {
-            const int K = 1 << o.k;
-            dag.assign(2 * K * K, 0.0);
-            for (int r = 0; r < K; ++r)
-                for (int c = 0; c < K; ++c) {
-                    dag[2 * (r * K + c)] = o.matrix[2 * (c * K + r)];
-                    dag[2 * (r * K + c) + 1] = -o.matrix[2 * (c * K + r) + 1];
-                }
-            st = launch_gate(phi, n, dt, o.k, o.qubits, dag.data(), 2 * int64_t(batch), HQ_ENGINE_AUTO, s);
+    for (int u = units - 1; u >= 0; --u) {
+        if (passes) {
+            st = adj_launch_pass(dt, true, plan.pass[u], dev_ops, phi, n, batch, cs, P, part, nbx, s);
         } else {
-            st = run_rot_dt(dt, true, phi, n, o.qubits[0], o.axis, o.param, theta, P, batch,
-                            part + size_t(rot_index[g]) * batch * nbx, s);
+            const int g = u;
+            const hq_op &o = ops[g];
+            if (o.kind == HQ_OP_MATRIX) {
+                const int K = 1 << o.k;
+                dag.assign(2 * K * K, 0.0);
+                for (int r = 0; r < K; ++r)
+                    for (int c = 0; c < K; ++c) {
+                        dag[2 * (r * K + c)] = o.matrix[2 * (c * K + r)];
+                        dag[2 * (r * K + c) + 1] = -o.matrix[2 * (c * K + r) + 1];
+                    }
+                st = launch_gate(phi, n, dt, o.k, o.qubits, dag.data(), 2 * int64_t(batch), HQ_ENGINE_AUTO, s);
+            } else {
+                st = run_rot_dt(dt, true, phi, n, o.qubits[0], o.axis, o.param, theta, P, batch,
+                                part + size_t(rot_index[g]) * batch * nbx, s);
+            }
         }
         if (st != HQ_OK) return st;
         for (int c = 0; c < checkpoints; ++c)
-            if (ck[c] == g)
+            if (ck[c] == u)
                 HQ_CUDA(cudaMemcpyAsync(phi, ckpt + c * state_bytes, state_bytes, cudaMemcpyDeviceToDevice, s));
     }
 

@@ -1,0 +1,346 @@
+// k_adjoint_pass.cu -- tile-resident passes for the adjoint gradient sweep.
+//
+// The adjoint method (Jones & Gacon, arXiv 2009.02823; not in the paper)
+// walks the circuit forward once and backward once.  Applying every gate as
+// its own pass over HBM costs one read and one write of every state per gate
+// (two states in the reverse sweep).  Here consecutive gates are grouped into
+// passes the way the batched runner groups them (a gate moves into an earlier
+// pass only past passes it shares no qubit with, as in Sec. 3.1's compress):
+// a pass touches only the R lowest bits plus at most h higher bits of the
+// state index, so every tile of 2^(R+|H|) amplitudes stays in shared memory
+// while all of the pass's gates are applied to it.
+//
+// Forward mode applies the pass's gates in order to phi.  Reverse mode holds
+// the tiles of phi and lambda together and walks the gates backwards: for a
+// rotation R_P(t) = exp(-i t P/2) it first adds Im<lambda|P phi> over the tile
+// (dE/dt, since dR/dt = -(i/2) P R) to a shared-memory accumulator, then
+// applies R^+ to both tiles; fixed gates get M^+.  Each CTA handles one
+// parameter set (grid.y) and writes one FP64 partial per rotation at the end.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hq_internal.cuh"
+#include "hq_adjoint.cuh"
+
+namespace hq {
+
+constexpr int kApThreads = 256;
+
+__device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
+
+template <typename T2> __device__ __forceinline__ T2 cvt2(double2 a);
+template <> __device__ __forceinline__ float2 cvt2<float2>(double2 a) { return make_float2(float(a.x), float(a.y)); }
+template <> __device__ __forceinline__ double2 cvt2<double2>(double2 a) { return a; }
+
+// 2x2 matrix of R_P(t) (adjoint when rev) from (cos t/2, sin t/2)
+template <typename T2>
+__device__ __forceinline__ void rot2(int axis, double2 cs, bool rev, T2 (&m)[4])
+{
+    using R = decltype(m[0].x);
+    const R c = R(cs.x), s = rev ? R(-cs.y) : R(cs.y);
+    m[0].x = c; m[0].y = 0; m[3].x = c; m[3].y = 0;
+    m[1].x = 0; m[1].y = 0; m[2].x = 0; m[2].y = 0;
+    if (axis == 'X') { m[1].y = -s; m[2].y = -s; }
+    else if (axis == 'Y') { m[1].x = -s; m[2].x = s; }
+    else { m[0].y = -s; m[3].y = s; }
+}
+
+// Im( conj(l0) (P a)_0 + conj(l1) (P a)_1 ) for the single-qubit Pauli P
+template <typename T2>
+__device__ __forceinline__ double pauli_im2(int axis, const T2 a0, const T2 a1, const T2 l0, const T2 l1)
+{
+    T2 p0, p1;
+    if (axis == 'X') { p0 = a1; p1 = a0; }
+    else if (axis == 'Y') { p0.x = a1.y; p0.y = -a1.x; p1.x = -a0.y; p1.y = a0.x; }  // -i a1, i a0
+    else { p0 = a0; p1.x = -a1.x; p1.y = -a1.y; }
+    return double(l0.x * p0.y - l0.y * p0.x) + double(l1.x * p1.y - l1.y * p1.x);
+}
+
+template <typename T2>
+__device__ __forceinline__ void mul2(const T2 (&m)[4], T2 &x0, T2 &x1)
+{
+    T2 y0, y1;
+    y0.x = 0; y0.y = 0; y1.x = 0; y1.y = 0;
+    cmac(y0, m[0], x0);
+    cmac(y0, m[1], x1);
+    cmac(y1, m[2], x0);
+    cmac(y1, m[3], x1);
+    x0 = y0;
+    x1 = y1;
+}
+
+// one pass over the tiles of parameter set blockIdx.y
+template <typename R, bool REV>
+__global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const AOp *__restrict__ ops,
+                                                         typename C2<R>::type *__restrict__ phi, int64_t lam_off,
+                                                         int64_t stride, const double2 *__restrict__ cs, int P,
+                                                         double *__restrict__ partials, int batch)
+{
+    using T2 = typename C2<R>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = ps.R + ps.nh, TS = 1 << L;
+    T2 *tp = reinterpret_cast<T2 *>(smem_raw);
+    T2 *tl = tp + TS;
+    __shared__ double gacc[kApMaxRot];
+    const int b = blockIdx.y;
+    if (REV)
+        for (int j = threadIdx.x; j < ps.nrot; j += blockDim.x) gacc[j] = 0.0;
+    T2 *sphi = phi + int64_t(b) * stride;
+    T2 *slam = sphi + lam_off;
+    const double2 *scs = cs + int64_t(b) * P;
+    for (int64_t t = blockIdx.x; t < ps.ntiles; t += gridDim.x) {
+        int64_t base = t << ps.R;
+        for (int j = 0; j < ps.nh; ++j) {
+            const int hb = ps.hb[j];
+            base = ((base >> hb) << (hb + 1)) | (base & ((int64_t(1) << hb) - 1));
+        }
+        // element i of the tile: its R low bits, then its high bits at hb[]
+        auto off = [&](int i) {
+            int64_t o = base + (i & ((1 << ps.R) - 1));
+            const int hi = i >> ps.R;
+            for (int j = 0; j < ps.nh; ++j)
+                if ((hi >> j) & 1) o += int64_t(1) << ps.hb[j];
+            return o;
+        };
+        for (int i = threadIdx.x; i < TS; i += blockDim.x) {
+            const int64_t o = off(i);
+            tp[swz<R>(i)] = sphi[o];
+            if (REV) tl[swz<R>(i)] = slam[o];
+        }
+        __syncthreads();
+        for (int q = 0; q < ps.no; ++q) {
+            const AOp &op = ops[ps.o0 + (REV ? ps.no - 1 - q : q)];
+            if (op.kind == 1) {
+                // dense two-qubit gate: M (forward) or M^+ (reverse)
+                T2 m[16];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        m[r * 4 + c] = cvt2<T2>(REV ? conj2(op.m[c * 4 + r]) : op.m[r * 4 + c]);
+                const int p0 = op.tpos[0], p1 = op.tpos[1];
+                const int lo = min(p0, p1), hi = max(p0, p1);
+                for (int grp = threadIdx.x; grp < TS / 4; grp += blockDim.x) {
+                    int i0 = ((grp >> lo) << (lo + 1)) | (grp & ((1 << lo) - 1));
+                    i0 = ((i0 >> hi) << (hi + 1)) | (i0 & ((1 << hi) - 1));
+                    int idx[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) idx[r] = swz<R>(i0 | (((r >> 1) & 1) << p0) | ((r & 1) << p1));
+#pragma unroll
+                    for (int s2 = 0; s2 < (REV ? 2 : 1); ++s2) {
+                        T2 *tt = s2 ? tl : tp;
+                        T2 x[4], y[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) x[r] = tt[idx[r]];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            y[r].x = 0;
+                            y[r].y = 0;
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) cmac(y[r], m[r * 4 + c], x[c]);
+                        }
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) tt[idx[r]] = y[r];
+                    }
+                }
+            } else if (op.kind == 2) {
+                // diagonal gate (k = 1 or 2): elementwise
+                const int D = 1 << op.k;
+                T2 d[4];
+                for (int r = 0; r < D; ++r) d[r] = cvt2<T2>(REV ? conj2(op.m[r * D + r]) : op.m[r * D + r]);
+                for (int i = threadIdx.x; i < TS; i += blockDim.x) {
+                    int r = (i >> op.tpos[0]) & 1;
+                    if (op.k == 2) r = (r << 1) | ((i >> op.tpos[1]) & 1);
+                    const int si = swz<R>(i);
+                    tp[si] = cmul(d[r], tp[si]);
+                    if (REV) tl[si] = cmul(d[r], tl[si]);
+                }
+            } else {
+                // one-qubit gate: dense matrix (kind 0) or rotation (kind 3)
+                T2 m[4];
+                if (op.kind == 3) {
+                    rot2<T2>(op.axis, scs[op.param], REV, m);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c)
+                            m[r * 2 + c] = cvt2<T2>(REV ? conj2(op.m[c * 2 + r]) : op.m[r * 2 + c]);
+                }
+                const int tp0 = op.tpos[0];
+                double g = 0.0;
+                for (int grp = threadIdx.x; grp < TS / 2; grp += blockDim.x) {
+                    const int i0 = ((grp >> tp0) << (tp0 + 1)) | (grp & ((1 << tp0) - 1));
+                    const int a = swz<R>(i0), bb = swz<R>(i0 | (1 << tp0));
+                    T2 x0 = tp[a], x1 = tp[bb];
+                    if (REV) {
+                        T2 l0 = tl[a], l1 = tl[bb];
+                        if (op.kind == 3) g += pauli_im2(op.axis, x0, x1, l0, l1);
+                        mul2(m, l0, l1);
+                        tl[a] = l0;
+                        tl[bb] = l1;
+                    }
+                    mul2(m, x0, x1);
+                    tp[a] = x0;
+                    tp[bb] = x1;
+                }
+                if (REV && op.kind == 3) {
+                    for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
+                    if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[op.slot], g);
+                }
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < TS; i += blockDim.x) {
+            const int64_t o = off(i);
+            sphi[o] = tp[swz<R>(i)];
+            if (REV) slam[o] = tl[swz<R>(i)];
+        }
+        __syncthreads();
+    }
+    if (REV) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < ps.no; q += blockDim.x) {
+            const AOp &op = ops[ps.o0 + q];
+            if (op.kind == 3) partials[(int64_t(op.row) * batch + b) * gridDim.x + blockIdx.x] = gacc[op.slot];
+        }
+    }
+}
+
+// (cos t/2, sin t/2) for every parameter of every set
+__global__ void k_half_angles(const double *__restrict__ theta, int64_t count, double2 *__restrict__ cs)
+{
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x) {
+        double s, c;
+        sincos(0.5 * theta[i], &s, &c);
+        cs[i] = make_double2(c, s);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// host side
+// ----------------------------------------------------------------------------
+bool adj_plan(int n, hq_dtype dt, const hq_op *ops, int G, AdjPlan &plan)
+{
+    for (int g = 0; g < G; ++g)
+        if (ops[g].kind == HQ_OP_MATRIX && ops[g].k > 2) return false;
+    // 2^tile_bits amplitudes of one state in 32 KB of shared memory
+    plan.tile_bits = dt == HQ_C64 ? 12 : 11;
+    const int h = dt == HQ_C64 ? 6 : 5;
+    const int R = std::min(n, plan.tile_bits - h);
+    struct P {
+        uint64_t qset = 0, high = 0;
+        int nrot = 0;
+        std::vector<int> ops;
+    };
+    std::vector<P> ps;
+    for (int g = 0; g < G; ++g) {
+        const hq_op &o = ops[g];
+        const int k = o.kind == HQ_OP_ROT ? 1 : o.k;
+        uint64_t Q = 0, Qh = 0;
+        for (int j = 0; j < k; ++j) {
+            const int b = n - 1 - o.qubits[j];
+            Q |= 1ull << b;
+            if (b >= R) Qh |= 1ull << b;
+        }
+        const int rot = o.kind == HQ_OP_ROT;
+        auto fits = [&](const P &p) {
+            return __builtin_popcountll(p.high | Qh) <= h && p.nrot + rot <= kApMaxRot;
+        };
+        int i = int(ps.size()) - 1;
+        while (i >= 0 && !(ps[i].qset & Q)) --i;
+        int target = -1;
+        if (i >= 0 && fits(ps[i])) target = i;
+        for (int j = i + 1; target < 0 && j < int(ps.size()); ++j)
+            if (fits(ps[j])) target = j;
+        if (target < 0) {
+            ps.emplace_back();
+            target = int(ps.size()) - 1;
+        }
+        ps[target].qset |= Q;
+        ps[target].high |= Qh;
+        ps[target].nrot += rot;
+        ps[target].ops.push_back(g);
+    }
+    std::vector<int> row(G, -1);
+    for (int g = 0, r = 0; g < G; ++g)
+        if (ops[g].kind == HQ_OP_ROT) row[g] = r++;
+    plan.pass.clear();
+    plan.op.clear();
+    for (const P &p : ps) {
+        APass ap;
+        std::memset(&ap, 0, sizeof(ap));
+        ap.R = R;
+        for (int b = R; b < n; ++b)
+            if ((p.high >> b) & 1) ap.hb[ap.nh++] = b;
+        ap.o0 = int(plan.op.size());
+        ap.no = int(p.ops.size());
+        ap.ntiles = int64_t(1) << (n - R - ap.nh);
+        auto tpos = [&](int q) {
+            const int b = n - 1 - q;
+            if (b < R) return b;
+            for (int j = 0; j < ap.nh; ++j)
+                if (ap.hb[j] == b) return R + j;
+            return -1;
+        };
+        for (int g : p.ops) {
+            const hq_op &o = ops[g];
+            AOp a;
+            std::memset(&a, 0, sizeof(a));
+            if (o.kind == HQ_OP_ROT) {
+                a.kind = 3;
+                a.k = 1;
+                a.tpos[0] = tpos(o.qubits[0]);
+                a.axis = o.axis;
+                a.param = o.param;
+                a.row = row[g];
+                a.slot = ap.nrot++;
+            } else {
+                a.k = o.k;
+                a.kind = is_diagonal(o.k, o.matrix) ? 2 : (o.k == 1 ? 0 : 1);
+                for (int j = 0; j < o.k; ++j) a.tpos[j] = tpos(o.qubits[j]);
+                const int D = 1 << o.k;
+                for (int e = 0; e < D * D; ++e) a.m[e] = make_double2(o.matrix[2 * e], o.matrix[2 * e + 1]);
+            }
+            plan.op.push_back(a);
+        }
+        plan.pass.push_back(ap);
+    }
+    return true;
+}
+
+template <typename R, bool REV>
+static hq_status launch_pass_t(const APass &ps, const AOp *dev_ops, void *phi, int n, int batch, const double2 *cs,
+                               int P, double *partials, int nbx, cudaStream_t s)
+{
+    using T2 = typename C2<R>::type;
+    const size_t smem = sizeof(T2) * (size_t(1) << (ps.R + ps.nh)) * (REV ? 2 : 1);
+    occupancy((const void *)k_adj_pass<R, REV>, kApThreads, smem);
+    dim3 grid(nbx, batch);
+    const int64_t stride = int64_t(1) << n;
+    k_adj_pass<R, REV><<<grid, kApThreads, smem, s>>>(ps, dev_ops, (T2 *)phi, int64_t(batch) * stride, stride, cs, P,
+                                                      partials, batch);
+    return cuda_status("k_adj_pass", cudaGetLastError());
+}
+
+hq_status adj_launch_pass(hq_dtype dt, bool rev, const APass &ps, const AOp *dev_ops, void *phi, int n, int batch,
+                          const double2 *cs, int P, double *partials, int nbx, cudaStream_t s)
+{
+    if (dt == HQ_C64)
+        return rev ? launch_pass_t<float, true>(ps, dev_ops, phi, n, batch, cs, P, partials, nbx, s)
+                   : launch_pass_t<float, false>(ps, dev_ops, phi, n, batch, cs, P, partials, nbx, s);
+    return rev ? launch_pass_t<double, true>(ps, dev_ops, phi, n, batch, cs, P, partials, nbx, s)
+               : launch_pass_t<double, false>(ps, dev_ops, phi, n, batch, cs, P, partials, nbx, s);
+}
+
+hq_status adj_half_angles(const double *theta, int64_t count, double2 *cs, cudaStream_t s)
+{
+    if (count <= 0) return HQ_OK;
+    const int grid = int(std::min<int64_t>((count + 255) / 256, 1024));
+    k_half_angles<<<grid, 256, 0, s>>>(theta, count, cs);
+    return cuda_status("k_half_angles", cudaGetLastError());
+}
+
+}  // namespace hq
