@@ -21,13 +21,12 @@
 //
 // Kernel shape (persistent; 256 threads; 1, 2 or 4 CTAs per SM for k = 6, 5, 4
 // so that the CTAs' TMEM fits the SM's 512 columns):
-//   warps 0-3  producers: thread p owns group p of every tile.  It copies the
-//              group's amplitudes for the NEXT tile into its own padded row of
-//              a shared-memory staging buffer with 8-byte cp.async (lanes =
-//              consecutive groups, so each copy instruction is coalesced, and
-//              the data in flight holds no registers), then splits the current
-//              tile's row and writes it to TMEM lane p (tcgen05.st) as the A
-//              operand.  Thread 0 issues the tcgen05.mma sequence (A from TMEM,
+//   producer warps: thread 0 copies the NEXT tile's contiguous runs (>= 1 KB
+//              each) into a shared-memory tile buffer with bulk (TMA) copies
+//              that complete on an mbarrier; meanwhile each producer thread
+//              reads its group's amplitudes of the current tile from the other
+//              buffer, splits them and writes them to TMEM lane p
+//              (tcgen05.st) as the A operand.  Thread 0 issues the tcgen05.mma sequence (A from TMEM,
 //              B from shared memory) and commits it to an mbarrier.
 //   warps 4-7  epilogue: wait for a tile's MMAs, tcgen05.ld its TMEM lanes
 //              (lane = group), unscale and store the outputs to HBM.
@@ -165,15 +164,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
-__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 {
-    asm volatile("{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %1;\n\tcp.async.ca.shared.global [%0], [g], 8;\n\t}" ::"r"(dst),
-                 "l"(src)
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// bulk (TMA) copy of `bytes` contiguous global bytes into shared memory,
+// completing on `bar` (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .u64 g;\n\tcvta.to.global.u64 g, %1;\n\t"
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [g], %2, [%3];\n\t}" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
 
 // Shared-memory matrix descriptor: K-major, no swizzle.  Core matrices are 8
 // rows x 16 bytes; LBO = byte step between core matrices along K, SBO = byte
@@ -233,13 +240,12 @@ struct TcLayout {
     static constexpr int D = 1 << K;
     static constexpr int D2 = 2 * D;                          // GEMM K and N
     static constexpr int kBBytes = D2 * D2 * 2;               // one of B_hi / B_lo
-    static constexpr int kRowStride = D * 8 + 8;              // staging bytes per group (padded: 2-way banks)
-    static constexpr int kStageBytes = kTcGroups * kRowStride;
-    static constexpr int kOffStage = 2 * kBBytes;             // stage[2]
-    static constexpr int kOffScale = kOffStage + 2 * kStageBytes;  // float[2][128]
+    static constexpr int kTileBytes = kTcGroups * D * 8;      // one tile of complex64, tile-local order
+    static constexpr int kOffTile = 2 * kBBytes;              // tile[2]
+    static constexpr int kOffScale = kOffTile + 2 * kTileBytes;  // float[2][128]
     static constexpr int kOffPartMax = kOffScale + 2 * kTcGroups * 4;  // float[2][128] (split groups)
-    static constexpr int kOffBar = kOffPartMax + 2 * kTcGroups * 4;  // mma_done[2], acc_free[2]
-    static constexpr int kOffMisc = kOffBar + 4 * 8;          // tmem addr, abort flag
+    static constexpr int kOffBar = kOffPartMax + 2 * kTcGroups * 4;  // mma_done[2], acc_free[2], full[2]
+    static constexpr int kOffMisc = kOffBar + 6 * 8;          // tmem addr, abort flag
     static constexpr int kBytes = kOffMisc + 16;
     // TMEM per buffer: A_hi (D cols), A_lo (D cols), accumulator (2D cols)
     static constexpr uint32_t kBufCols = 4 * D;
@@ -280,6 +286,8 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
         mbar_init(&bar[1], 1);
         mbar_init(&bar[2], NT - NP);
         mbar_init(&bar[3], NT - NP);
+        mbar_init(&bar[4], 1);
+        mbar_init(&bar[5], 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -295,41 +303,49 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
         // ---------------- producers + MMA issue ----------------
         const int quarter = warp & 3, part = warp >> 2;
         const int n = quarter * 32 + (tid & 31);  // group within the tile = TMEM lane
-        const int r0 = part * DP;                 // this thread's amplitudes [r0, r0 + DP)
         const uint32_t lane_off = uint32_t(quarter * 32) << 16;
-        const uint32_t stage0 = smem_base + Lay::kOffStage + uint32_t(n * Lay::kRowStride);
-        const unsigned char *my_stage[2] = {smem + Lay::kOffStage + n * Lay::kRowStride,
-                                            smem + Lay::kOffStage + Lay::kStageBytes + n * Lay::kRowStride};
         constexpr uint32_t idesc = instr_desc(kTcGroups, D2, BF16);
-        // this thread's share of its group of tile t -> its staging row; the
-        // amplitude indices are compile-time so goff[] is a constant operand
+        // Warp 0 copies tile t's contiguous runs (2^c amplitudes each) into
+        // tile buffer sb with bulk copies completing on full[sb]: lane 0 posts
+        // the byte count, then every lane issues every 32nd run.
+        const int nruns = 1 << (g.L - g.c);
+        const uint32_t run_bytes = uint32_t(8) << g.c;
+        auto load_tile = [&](int64_t t, int sb) {
+            const float2 *src = state + tile_base(g, t);
+            const uint32_t dst = smem_base + Lay::kOffTile + uint32_t(sb * Lay::kTileBytes);
+            fence_proxy_async();  // earlier generic reads of this buffer come first
+            if ((tid & 31) == 0) mbar_expect_tx(&bar[4 + sb], uint32_t(Lay::kTileBytes));
+            __syncwarp();
+            for (int j = tid & 31; j < nruns; j += 32)
+                bulk_g2s(dst + uint32_t(j) * run_bytes, src + g.runoff[j], run_bytes, &bar[4 + sb]);
+        };
+        // this thread's amplitudes of its group, at tile-local index ibase + toff[r];
+        // the amplitude indices are compile-time so toff[] is a constant operand
         const int ibase = group_base<K>(g, n);
-        auto issue_part = [&](auto part_c, const float2 *gsrc, uint32_t dst) {
+        auto max_part = [&](auto part_c, const float2 *x) {
             constexpr int R0 = decltype(part_c)::value * DP;
-#pragma unroll
-            for (int r = R0; r < R0 + DP; ++r) cp_async8(dst + uint32_t(r * 8), gsrc + g.goff[r]);
-        };
-        auto issue = [&](int64_t t, int sb) {
-            const float2 *gsrc = state + tile_base(g, t) + ibase;
-            const uint32_t dst = stage0 + uint32_t(sb * Lay::kStageBytes);
-            if (part == 0) issue_part(std::integral_constant<int, 0>{}, gsrc, dst);
-            else issue_part(std::integral_constant<int, SPLIT - 1>{}, gsrc, dst);
-        };
-        if (int64_t(blockIdx.x) < g.total_tiles) issue(blockIdx.x, 0);
-        cp_async_commit();
-        int it = 0, issued = 0;
-        for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
-            const int buf = it & 1;
-            if (t + gridDim.x < g.total_tiles) issue(t + gridDim.x, buf ^ 1);
-            cp_async_commit();
-            cp_async_wait1();  // this thread's copies for tile t have landed
-            const float2 *x = reinterpret_cast<const float2 *>(my_stage[buf]);
             float m = 0.f;
 #pragma unroll
-            for (int r = r0; r < r0 + DP; ++r) {
-                const float2 v = x[r];
+            for (int r = R0; r < R0 + DP; ++r) {
+                const float2 v = x[g.toff[r]];
                 m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
             }
+            return m;
+        };
+        if (warp == 0 && int64_t(blockIdx.x) < g.total_tiles) load_tile(blockIdx.x, 0);
+        int it = 0, issued = 0, loaded = (int64_t(blockIdx.x) < g.total_tiles) ? 1 : 0;
+        for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
+            const int buf = it & 1;
+            // the buffer of tile it-1 was read by every producer before the last barrier
+            if (t + gridDim.x < g.total_tiles) {
+                if (warp == 0) load_tile(t + gridDim.x, buf ^ 1);
+                ++loaded;
+            }
+            const bool landed = mbar_wait(&bar[4 + buf], uint32_t((it / 2) & 1), abort_flag);
+            const float2 *x = reinterpret_cast<const float2 *>(smem + Lay::kOffTile + buf * Lay::kTileBytes) + ibase;
+            float m = landed ? (part == 0 ? max_part(std::integral_constant<int, 0>{}, x)
+                                          : max_part(std::integral_constant<int, SPLIT - 1>{}, x))
+                             : 0.f;
             if (SPLIT > 1) {
                 part_max[part * kTcGroups + n] = m;
                 named_bar_sync(1, NP);
@@ -340,21 +356,26 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
             frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
             const float s = (m > 0.f) ? ldexpf(1.f, 14 - e) : 1.f;
             // TMEM buffer `buf` is free once the epilogue of tile it-2 released it
-            const bool ok = it < 2 || mbar_wait(&bar[2 + buf], uint32_t((it / 2 - 1) & 1), abort_flag);
+            const bool ok = landed && (it < 2 || mbar_wait(&bar[2 + buf], uint32_t((it / 2 - 1) & 1), abort_flag));
             if (ok) {
                 const uint32_t a_hi = tmem + lane_off + uint32_t(buf) * Lay::kBufCols;
                 const uint32_t a_lo = a_hi + uint32_t(D);
+                auto convert_part = [&](auto part_c) {
+                    constexpr int R0 = decltype(part_c)::value * DP;
 #pragma unroll
-                for (int c0 = r0; c0 < r0 + DP; c0 += 16) {
-                    uint32_t hv[16], lv[16];
+                    for (int c0 = R0; c0 < R0 + DP; c0 += 16) {
+                        uint32_t hv[16], lv[16];
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const float2 v = x[c0 + u];
-                        hv[u] = Split<BF16>::pack(v.x * s, v.y * s, lv[u]);
+                        for (int u = 0; u < 16; ++u) {
+                            const float2 v = x[g.toff[c0 + u]];
+                            hv[u] = Split<BF16>::pack(v.x * s, v.y * s, lv[u]);
+                        }
+                        tmem_st16(a_hi + uint32_t(c0), hv);
+                        tmem_st16(a_lo + uint32_t(c0), lv);
                     }
-                    tmem_st16(a_hi + uint32_t(c0), hv);
-                    tmem_st16(a_lo + uint32_t(c0), lv);
-                }
+                };
+                if (part == 0) convert_part(std::integral_constant<int, 0>{});
+                else convert_part(std::integral_constant<int, SPLIT - 1>{});
                 tmem_wait_st();
                 if (part == 0) inv_scale[buf * kTcGroups + n] = 1.f / s;
             }
@@ -384,7 +405,15 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
             }
             ++issued;
         }
-        cp_async_wait0();  // no copy may land after the CTA exits
+        // no bulk copy may land after the CTA exits: wait for the last load of
+        // each buffer (the loop consumed every load when it ran to the end)
+        if (tid == 0) {
+            volatile int no_abort = 0;
+            for (int b = 0; b < 2; ++b) {
+                const int cnt = (loaded + 1 - b) / 2;  // loads issued into buffer b
+                if (cnt > 0) mbar_wait(&bar[4 + b], uint32_t((cnt - 1) & 1), &no_abort);
+            }
+        }
         // drain: the last commit of each buffer must land before TMEM is freed
         if (tid == 0) {
             volatile int no_abort = 0;
