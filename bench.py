@@ -325,6 +325,21 @@ def measure_extras(args):
     return out
 
 
+def whole_job_rate(local_seconds: float, local_units: float, dist=None, device=None):
+    """Replicas: every rank processed its own units; the job rate is the sum
+    of the units over the slowest rank's time (max over ranks)."""
+    if dist is None:
+        return local_units / local_seconds, local_seconds
+    import torch
+
+    t = torch.tensor([local_seconds, local_units], dtype=torch.float64, device=device)
+    tmax = t[:1].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    units = t[1:].clone()
+    dist.all_reduce(units, op=dist.ReduceOp.SUM)
+    return float(units.item()) / float(tmax.item()), float(tmax.item())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -412,11 +427,7 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     elapsed = t0.elapsed_time(t1) / 1e3
-    if dist:
-        tt = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
-    value = world * G * args.steps / elapsed
+    value, elapsed = whole_job_rate(elapsed, G * args.steps, dist, "cuda")
 
     # per-class launch durations (CUDA events on the launching stream)
     durs = {}
@@ -454,11 +465,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         et = e0.elapsed_time(e1) / 1e3
-        if dist:
-            tt = torch.tensor([et], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            et = float(tt.item())
-        e2e = {"value": world * G * e2e_steps / et, "unit": METRIC, "h2d_bytes_per_step": (1 << n) * S,
+        e2e_value, et = whole_job_rate(et, G * e2e_steps, dist, "cuda")
+        e2e = {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": (1 << n) * S,
                "d2h_bytes_per_step": 8, "note": "pinned host state copied in, FP64 norm read back, every step"}
 
     cpu = None
