@@ -31,6 +31,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hq_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# Test hook: a prebuilt library to load instead (the mutation test points this
+# at deliberately broken copies to show that the pins catch them).
+_OVERRIDE = os.environ.get("HQ_ORACLE_LIB")
 _lib = None
 _lock = threading.Lock()
 
@@ -50,8 +53,11 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB_PATH)
+            if _OVERRIDE:
+                lib = ctypes.CDLL(_OVERRIDE)
+            else:
+                build()
+                lib = ctypes.CDLL(_LIB_PATH)
             P = ctypes.c_void_p
             i = ctypes.c_int
             lib.or_state_init.argtypes = [i, ctypes.c_char_p, P]
