@@ -35,6 +35,7 @@
 //   wait is bounded by a %globaltimer deadline; on expiry the kernel raises a
 //   device error flag (read back as HQ_ERR_TIMEOUT), leaves its loops, waits
 //   for its own copies and MMAs, and frees its TMEM.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -182,6 +183,45 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
         : "memory");
 }
 
+// tensor-map (TMA) copy of one box of `map` at coordinates c[0 .. dims-1]
+// into shared memory, completing on `bar`
+__device__ __forceinline__ void tensor_g2s(uint32_t dst, const CUtensorMap *map, int dims, const int (&c)[5],
+                                           uint64_t *bar)
+{
+    const uint64_t m = reinterpret_cast<uint64_t>(map);
+    const uint32_t b = smem_u32(bar);
+    switch (dims) {
+    case 2:
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+            "[%4];" ::"r"(dst),
+            "l"(m), "r"(c[0]), "r"(c[1]), "r"(b)
+            : "memory");
+        break;
+    case 3:
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4}], [%5];" ::"r"(dst),
+            "l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(b)
+            : "memory");
+        break;
+    case 4:
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4, %5}], [%6];" ::"r"(dst),
+            "l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(b)
+            : "memory");
+        break;
+    default:
+        asm volatile(
+            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+            "%4, %5, %6}], [%7];" ::"r"(dst),
+            "l"(m), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(b)
+            : "memory");
+        break;
+    }
+}
+
 // Shared-memory matrix descriptor: K-major, no swizzle.  Core matrices are 8
 // rows x 16 bytes; LBO = byte step between core matrices along K, SBO = byte
 // step between 8-row groups; version field 1 (bits 46-47).
@@ -233,6 +273,12 @@ struct TcParams {
     TileGeom g;               // K = k, L = k + 7
     const uint4 *bmat;        // B_hi then B_lo, each 2D x 2D in core-matrix order
     float out_mul;            // 1 / s_M
+    // Tile loads.  tm_dims = 0: one bulk copy per contiguous run.  Otherwise
+    // the state is viewed as a tensor of tm_dims dimensions (dimension d =
+    // flat bits [tm_shift[d], tm_shift[d+1])) in which a tile is tm_copies
+    // boxes; box j holds tile-local indices [j << tm_copy_bits, (j+1) << ...).
+    int tm_dims, tm_copies, tm_copy_bits;
+    int tm_shift[5];
 };
 
 template <int K>
@@ -261,7 +307,7 @@ template <int K> __host__ __device__ constexpr int tc_split() { return K == 6 ? 
 template <int K> __host__ __device__ constexpr int tc_threads() { return 2 * kTcGroups * tc_split<K>(); }
 
 template <int K, bool BF16>
-__global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(const TcParams p, float2 *__restrict__ state)
+__global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(const TcParams p, const __grid_constant__ CUtensorMap tmap, float2 *__restrict__ state)
 {
     using Lay = TcLayout<K>;
     constexpr int D = Lay::D, D2 = Lay::D2;
@@ -305,19 +351,36 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
         const int n = quarter * 32 + (tid & 31);  // group within the tile = TMEM lane
         const uint32_t lane_off = uint32_t(quarter * 32) << 16;
         constexpr uint32_t idesc = instr_desc(kTcGroups, D2, BF16);
-        // Warp 0 copies tile t's contiguous runs (2^c amplitudes each) into
-        // tile buffer sb with bulk copies completing on full[sb]: lane 0 posts
-        // the byte count, then every lane issues every 32nd run.
+        // Warp 0 copies tile t into tile buffer sb, completing on full[sb]:
+        // lane 0 posts the byte count, then the lanes issue either one bulk
+        // copy per contiguous run (2^c amplitudes) or the tile's tensor-map
+        // boxes (for short runs, which as separate copies load slowly).
         const int nruns = 1 << (g.L - g.c);
         const uint32_t run_bytes = uint32_t(8) << g.c;
         auto load_tile = [&](int64_t t, int sb) {
-            const float2 *src = state + tile_base(g, t);
+            const int64_t base = tile_base(g, t);
             const uint32_t dst = smem_base + Lay::kOffTile + uint32_t(sb * Lay::kTileBytes);
             fence_proxy_async();  // earlier generic reads of this buffer come first
             if ((tid & 31) == 0) mbar_expect_tx(&bar[4 + sb], uint32_t(Lay::kTileBytes));
             __syncwarp();
-            for (int j = tid & 31; j < nruns; j += 32)
-                bulk_g2s(dst + uint32_t(j) * run_bytes, src + g.runoff[j], run_bytes, &bar[4 + sb]);
+            if (p.tm_dims) {
+                for (int j = tid & 31; j < p.tm_copies; j += 32) {
+                    const int i0 = j << p.tm_copy_bits;  // first tile-local index of box j
+                    const int64_t x = base + g.runoff[i0 >> g.c];
+                    int c[5];
+#pragma unroll
+                    for (int d = 0; d < 5; ++d) {
+                        const int64_t v = x >> p.tm_shift[d];
+                        c[d] = d + 1 < p.tm_dims ? int(v & ((int64_t(1) << (p.tm_shift[d + 1] - p.tm_shift[d])) - 1))
+                                                 : (d + 1 == p.tm_dims ? int(v) : 0);
+                    }
+                    tensor_g2s(dst + uint32_t(i0) * 8u, &tmap, p.tm_dims, c, &bar[4 + sb]);
+                }
+            } else {
+                const float2 *src = state + base;
+                for (int j = tid & 31; j < nruns; j += 32)
+                    bulk_g2s(dst + uint32_t(j) * run_bytes, src + g.runoff[j], run_bytes, &bar[4 + sb]);
+            }
         };
         // this thread's amplitudes of its group, at tile-local index ibase + toff[r];
         // the amplitude indices are compile-time so toff[] is a constant operand
@@ -510,6 +573,78 @@ static float prepare_b(int k, const double *mat, std::vector<uint16_t> &out)
     return float(1.0 / sm);
 }
 
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled()
+{
+    static const EncodeTiledFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Tensor-map view of the states for tiles whose runs are short (2^c <= 256
+// amplitudes, i.e. <= 2 KB).  Dimension 0 = flat bits [0, h_1) with box 2^c;
+// dimension d >= 1 starts at the d-th group of consecutive high target bits,
+// whose bits are its box, and runs up to the next group (the last one to the
+// top bit, times the number of states).  A tensor copy has at most 5
+// dimensions: target groups beyond the 4th become coordinates instead, and the
+// tile is then loaded as 2^(their bits) boxes.  Leaves p.tm_dims = 0 (bulk
+// copies per run) when the view does not apply.
+static void make_tile_map(const TileGeom &g, int n, int64_t nstates, void *state, TcParams &p, CUtensorMap &map)
+{
+    p.tm_dims = 0;
+    p.tm_copies = 1;
+    p.tm_copy_bits = g.L;
+    for (int d = 0; d < 5; ++d) p.tm_shift[d] = 0;
+    std::memset(&map, 0, sizeof(map));
+    if (g.c > 8 || g.n_hi == 0) return;
+    int gfirst[HQ_MAX_K], gsize[HQ_MAX_K], ng = 0;
+    for (int h = 0; h < g.n_hi; ++h) {
+        if (ng > 0 && gfirst[ng - 1] + gsize[ng - 1] == g.hi_bits[h]) {
+            ++gsize[ng - 1];
+        } else {
+            gfirst[ng] = g.hi_bits[h];
+            gsize[ng++] = 1;
+        }
+    }
+    const int nbox = std::min(ng, 4), dims = 1 + nbox;
+    int extra = 0;
+    for (int i = nbox; i < ng; ++i) extra += gsize[i];
+    cuuint64_t gdim[5], gstride[4];
+    cuuint32_t box[5], estride[5];
+    int shift[6];
+    shift[0] = 0;
+    for (int d = 1; d < dims; ++d) shift[d] = gfirst[d - 1];
+    shift[dims] = n;
+    for (int d = 0; d < dims; ++d) {
+        const uint64_t span = uint64_t(1) << (shift[d + 1] - shift[d]);
+        gdim[d] = (d + 1 == dims) ? span * uint64_t(nstates) : span;
+        if (gdim[d] > (uint64_t(1) << 31)) return;  // coordinates are signed 32-bit
+        if (d > 0) gstride[d - 1] = cuuint64_t(8) << shift[d];
+        box[d] = d == 0 ? (1u << g.c) : (1u << gsize[d - 1]);
+        estride[d] = 1;
+    }
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return;
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, cuuint32_t(dims), state, gdim, gstride, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return;
+    p.tm_dims = dims;
+    p.tm_copies = 1 << extra;
+    p.tm_copy_bits = g.L - extra;
+    for (int d = 0; d < dims; ++d) p.tm_shift[d] = shift[d];
+}
+
 template <int K, bool BF16>
 static hq_status run_tc(void *state, int n, const int *qubits, const double *mat, int64_t nstates, cudaStream_t s)
 {
@@ -518,6 +653,8 @@ static hq_status run_tc(void *state, int n, const int *qubits, const double *mat
     make_geom(p.g, n, K, qubits, K + 7, nstates);
     std::vector<uint16_t> hb;
     p.out_mul = prepare_b<BF16>(K, mat, hb);
+    CUtensorMap tmap;
+    make_tile_map(p.g, n, nstates, state, p, tmap);
     uint4 *dmat = nullptr;
     const size_t bytes = hb.size() * sizeof(uint16_t);
     if (cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
@@ -531,7 +668,7 @@ static hq_status run_tc(void *state, int n, const int *qubits, const double *mat
         const void *fn = (const void *)k_tc<K, BF16>;
         const int per_sm = std::min(occupancy(fn, tc_threads<K>(), smem), Lay::kCtasPerSm);
         const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(sm_count()) * per_sm, p.g.total_tiles)));
-        k_tc<K, BF16><<<grid, tc_threads<K>(), smem, s>>>(p, (float2 *)state);
+        k_tc<K, BF16><<<grid, tc_threads<K>(), smem, s>>>(p, tmap, (float2 *)state);
         st = cuda_status("k_tc", cudaGetLastError());
     }
     cudaFreeAsync(dmat, s);
