@@ -165,6 +165,43 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
+// .16x256b shapes: a warp moves 16 TMEM lanes x 8 columns per repetition;
+// thread t holds, for repetition j, registers 4j, 4j+1 = lane t/4, columns
+// 8j + 2(t%4) + {0, 1}, and registers 4j+2, 4j+3 = lane t/4 + 8, same columns.
+__device__ __forceinline__ void tmem_st_16x256b(uint32_t taddr, const uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.16x256b.x2.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_st_16x256b(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.16x256b.x4.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+            taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_16x256b(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_16x256b(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
@@ -279,6 +316,7 @@ struct TcParams {
     // boxes; box j holds tile-local indices [j << tm_copy_bits, (j+1) << ...).
     int tm_dims, tm_copies, tm_copy_bits;
     int tm_shift[5];
+    int am_pair16;            // AM mapping: a thread's two amplitudes are adjacent (16-byte reads)
 };
 
 template <int K>
@@ -306,8 +344,15 @@ template <int K> __host__ __device__ constexpr int tc_min_blocks() { return K ==
 template <int K> __host__ __device__ constexpr int tc_split() { return K == 6 ? 2 : 1; }
 template <int K> __host__ __device__ constexpr int tc_threads() { return 2 * kTcGroups * tc_split<K>(); }
 
-template <int K, bool BF16>
-__global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(const TcParams p, const __grid_constant__ CUtensorMap tmap, float2 *__restrict__ state)
+// AM selects the producer/epilogue thread mapping.  false: thread = group
+// (TMEM lane), reading one amplitude per instruction (conflict-free when the
+// lowest tile bits are group bits).  true: four threads per group, each with
+// two adjacent amplitudes per 8-column slice, moved with the .16x256b TMEM
+// shapes (conflict-free reads and whole-sector stores when the lowest tile
+// bits are targets).
+template <int K, bool BF16, bool AM>
+__global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
+    k_tc(const TcParams p, const __grid_constant__ CUtensorMap tmap, float2 *__restrict__ state)
 {
     using Lay = TcLayout<K>;
     constexpr int D = Lay::D, D2 = Lay::D2;
@@ -385,6 +430,28 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
         // this thread's amplitudes of its group, at tile-local index ibase + toff[r];
         // the amplitude indices are compile-time so toff[] is a constant operand
         const int ibase = group_base<K>(g, n);
+        // AM mapping: lane = 4 row + p4 serves TMEM lanes quarter*32 + 16 hf + row + 8 u
+        // (group index gi = 2 hf + u) and amplitudes R0 + 8 j + 2 p4 + e (slot 2 j + e)
+        const int p4 = tid & 3, row4 = (tid & 31) >> 2;
+        int am_gb[AM ? 4 : 1] = {}, am_off[AM ? DP / 4 : 1] = {};
+        if constexpr (AM) {
+#pragma unroll
+            for (int gi = 0; gi < 4; ++gi)
+                am_gb[gi] = group_base<K>(g, quarter * 32 + 16 * (gi >> 1) + row4 + 8 * (gi & 1));
+#pragma unroll
+            for (int s = 0; s < DP / 4; ++s) am_off[s] = g.toff[part * DP + 8 * (s >> 1) + 2 * p4 + (s & 1)];
+        }
+        // amplitudes of slots 2j, 2j+1 of group gi (one 16-byte read when adjacent)
+        auto am_pair = [&](const float2 *xt, int gi, int j, float2 &a, float2 &b) {
+            if (p.am_pair16) {
+                const float4 w = *reinterpret_cast<const float4 *>(xt + am_gb[gi] + am_off[2 * j]);
+                a = make_float2(w.x, w.y);
+                b = make_float2(w.z, w.w);
+            } else {
+                a = xt[am_gb[gi] + am_off[2 * j]];
+                b = xt[am_gb[gi] + am_off[2 * j + 1]];
+            }
+        };
         auto max_part = [&](auto part_c, const float2 *x) {
             constexpr int R0 = decltype(part_c)::value * DP;
             float m = 0.f;
@@ -405,42 +472,116 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
                 ++loaded;
             }
             const bool landed = mbar_wait(&bar[4 + buf], uint32_t((it / 2) & 1), abort_flag);
-            const float2 *x = reinterpret_cast<const float2 *>(smem + Lay::kOffTile + buf * Lay::kTileBytes) + ibase;
-            float m = landed ? (part == 0 ? max_part(std::integral_constant<int, 0>{}, x)
-                                          : max_part(std::integral_constant<int, SPLIT - 1>{}, x))
-                             : 0.f;
-            if (SPLIT > 1) {
-                part_max[part * kTcGroups + n] = m;
-                named_bar_sync(1, NP);
+            const float2 *xt = reinterpret_cast<const float2 *>(smem + Lay::kOffTile + buf * Lay::kTileBytes);
+            const float2 *x = xt + ibase;
+            float s = 1.f, am_s[AM ? 4 : 1];
+            if constexpr (!AM) {
+                float m = landed ? (part == 0 ? max_part(std::integral_constant<int, 0>{}, x)
+                                              : max_part(std::integral_constant<int, SPLIT - 1>{}, x))
+                                 : 0.f;
+                if (SPLIT > 1) {
+                    part_max[part * kTcGroups + n] = m;
+                    named_bar_sync(1, NP);
 #pragma unroll
-                for (int h = 0; h < SPLIT; ++h) m = fmaxf(m, part_max[h * kTcGroups + n]);
+                    for (int h = 0; h < SPLIT; ++h) m = fmaxf(m, part_max[h * kTcGroups + n]);
+                }
+                int e = 0;
+                frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+                s = (m > 0.f) ? ldexpf(1.f, 14 - e) : 1.f;
+            } else {
+                float m4[4] = {0.f, 0.f, 0.f, 0.f};
+                if (landed) {
+#pragma unroll
+                    for (int gi = 0; gi < 4; ++gi)
+#pragma unroll
+                        for (int j = 0; j < DP / 8; ++j) {
+                            float2 a, b;
+                            am_pair(xt, gi, j, a, b);
+                            m4[gi] = fmaxf(m4[gi], fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(b.x), fabsf(b.y))));
+                        }
+                }
+#pragma unroll
+                for (int gi = 0; gi < 4; ++gi) {
+                    m4[gi] = fmaxf(m4[gi], __shfl_xor_sync(0xffffffffu, m4[gi], 1));
+                    m4[gi] = fmaxf(m4[gi], __shfl_xor_sync(0xffffffffu, m4[gi], 2));
+                }
+                if (SPLIT > 1) {
+                    if (p4 == 0) {
+#pragma unroll
+                        for (int gi = 0; gi < 4; ++gi)
+                            part_max[part * kTcGroups + quarter * 32 + 16 * (gi >> 1) + row4 + 8 * (gi & 1)] = m4[gi];
+                    }
+                    named_bar_sync(1, NP);
+#pragma unroll
+                    for (int gi = 0; gi < 4; ++gi)
+#pragma unroll
+                        for (int h = 0; h < SPLIT; ++h)
+                            m4[gi] = fmaxf(m4[gi],
+                                           part_max[h * kTcGroups + quarter * 32 + 16 * (gi >> 1) + row4 + 8 * (gi & 1)]);
+                }
+#pragma unroll
+                for (int gi = 0; gi < 4; ++gi) {
+                    int e = 0;
+                    frexpf(m4[gi], &e);
+                    am_s[gi] = (m4[gi] > 0.f) ? ldexpf(1.f, 14 - e) : 1.f;
+                }
             }
-            int e = 0;
-            frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
-            const float s = (m > 0.f) ? ldexpf(1.f, 14 - e) : 1.f;
             // TMEM buffer `buf` is free once the epilogue of tile it-2 released it
             const bool ok = landed && (it < 2 || mbar_wait(&bar[2 + buf], uint32_t((it / 2 - 1) & 1), abort_flag));
-            if (ok) {
-                const uint32_t a_hi = tmem + lane_off + uint32_t(buf) * Lay::kBufCols;
-                const uint32_t a_lo = a_hi + uint32_t(D);
-                auto convert_part = [&](auto part_c) {
-                    constexpr int R0 = decltype(part_c)::value * DP;
+            if constexpr (AM) {
+                if (ok) {
+                    const uint32_t a_hi = tmem + uint32_t(buf) * Lay::kBufCols + uint32_t(part * DP);
+                    const uint32_t a_lo = a_hi + uint32_t(D);
 #pragma unroll
-                    for (int c0 = R0; c0 < R0 + DP; c0 += 16) {
-                        uint32_t hv[16], lv[16];
+                    for (int hf = 0; hf < 2; ++hf) {
+                        uint32_t hv[DP / 2], lv[DP / 2];
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) {
-                            const float2 v = x[g.toff[c0 + u]];
-                            hv[u] = Split<BF16>::pack(v.x * s, v.y * s, lv[u]);
-                        }
-                        tmem_st16(a_hi + uint32_t(c0), hv);
-                        tmem_st16(a_lo + uint32_t(c0), lv);
+                        for (int j = 0; j < DP / 8; ++j)
+#pragma unroll
+                            for (int u = 0; u < 2; ++u) {
+                                const int gi = 2 * hf + u;
+                                float2 a, b;
+                                am_pair(xt, gi, j, a, b);
+                                hv[4 * j + 2 * u] =
+                                    Split<BF16>::pack(a.x * am_s[gi], a.y * am_s[gi], lv[4 * j + 2 * u]);
+                                hv[4 * j + 2 * u + 1] =
+                                    Split<BF16>::pack(b.x * am_s[gi], b.y * am_s[gi], lv[4 * j + 2 * u + 1]);
+                            }
+                        const uint32_t lanes = uint32_t(quarter * 32 + 16 * hf) << 16;
+                        tmem_st_16x256b(a_hi + lanes, hv);
+                        tmem_st_16x256b(a_lo + lanes, lv);
                     }
-                };
-                if (part == 0) convert_part(std::integral_constant<int, 0>{});
-                else convert_part(std::integral_constant<int, SPLIT - 1>{});
-                tmem_wait_st();
-                if (part == 0) inv_scale[buf * kTcGroups + n] = 1.f / s;
+                    tmem_wait_st();
+                    if (part == 0 && p4 == 0) {
+#pragma unroll
+                        for (int gi = 0; gi < 4; ++gi)
+                            inv_scale[buf * kTcGroups + quarter * 32 + 16 * (gi >> 1) + row4 + 8 * (gi & 1)] =
+                                1.f / am_s[gi];
+                    }
+                }
+            } else {
+                if (ok) {
+                    const uint32_t a_hi = tmem + lane_off + uint32_t(buf) * Lay::kBufCols;
+                    const uint32_t a_lo = a_hi + uint32_t(D);
+                    auto convert_part = [&](auto part_c) {
+                        constexpr int R0 = decltype(part_c)::value * DP;
+#pragma unroll
+                        for (int c0 = R0; c0 < R0 + DP; c0 += 16) {
+                            uint32_t hv[16], lv[16];
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) {
+                                const float2 v = x[g.toff[c0 + u]];
+                                hv[u] = Split<BF16>::pack(v.x * s, v.y * s, lv[u]);
+                            }
+                            tmem_st16(a_hi + uint32_t(c0), hv);
+                            tmem_st16(a_lo + uint32_t(c0), lv);
+                        }
+                    };
+                    if (part == 0) convert_part(std::integral_constant<int, 0>{});
+                    else convert_part(std::integral_constant<int, SPLIT - 1>{});
+                    tmem_wait_st();
+                    if (part == 0) inv_scale[buf * kTcGroups + n] = 1.f / s;
+                }
             }
             tc_fence_before();
             // every producer takes the same exit decision
@@ -493,12 +634,51 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>()) k_tc(cons
         const int ibase = group_base<K>(g, n);
         const uint32_t lane_off = uint32_t(quarter * 32) << 16;
         constexpr int CP = D2 / SPLIT;            // accumulator columns per thread
+        // AM mapping (see the producers): lane = 4 row + p4 holds outputs
+        // part*CP/2 + 4 j + p4 of TMEM lanes quarter*32 + 16 hf + row + 8 u
+        const int p4 = tid & 3, row4 = (tid & 31) >> 2;
+        int am_gb[AM ? 4 : 1] = {};
+        int64_t am_go[AM ? CP / 8 : 1] = {};
+        if constexpr (AM) {
+#pragma unroll
+            for (int gi = 0; gi < 4; ++gi)
+                am_gb[gi] = group_base<K>(g, quarter * 32 + 16 * (gi >> 1) + row4 + 8 * (gi & 1));
+#pragma unroll
+            for (int j = 0; j < CP / 8; ++j) am_go[j] = g.goff[part * (CP / 2) + 4 * j + p4];
+        }
         int it = 0;
         for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
             const int buf = it & 1;
             // warp-uniform exit: tcgen05.ld below is .sync.aligned
             if (!__all_sync(0xffffffffu, mbar_wait(&bar[buf], uint32_t((it / 2) & 1), abort_flag))) break;
             tc_fence_after();
+            if constexpr (AM) {
+                const uint32_t acc = tmem + uint32_t(buf) * Lay::kBufCols + uint32_t(2 * D + part * CP);
+                float2 *tb = state + tile_base(g, t);
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    uint32_t v[CP / 2];
+                    tmem_ld_16x256b(acc + (uint32_t(quarter * 32 + 16 * hf) << 16), v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int gi = 2 * hf + u;
+                        const float mul =
+                            inv_scale[buf * kTcGroups + quarter * 32 + 16 * hf + row4 + 8 * u] * p.out_mul;
+                        float2 *gd = tb + am_gb[gi];
+#pragma unroll
+                        for (int j = 0; j < CP / 8; ++j) {
+                            float2 o;
+                            o.x = __uint_as_float(v[4 * j + 2 * u]) * mul;
+                            o.y = __uint_as_float(v[4 * j + 2 * u + 1]) * mul;
+                            gd[am_go[j]] = o;
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&bar[2 + buf]);
+                continue;
+            }
             const float mul = inv_scale[buf * kTcGroups + n] * p.out_mul;
             float2 *gdst = state + tile_base(g, t) + ibase;
             const uint32_t acc = tmem + lane_off + uint32_t(buf) * Lay::kBufCols + uint32_t(2 * D);
@@ -645,31 +825,136 @@ static void make_tile_map(const TileGeom &g, int n, int64_t nstates, void *state
     for (int d = 0; d < dims; ++d) p.tm_shift[d] = shift[d];
 }
 
+// Targets in ascending qubit order (local-index bit j = the j-th lowest flat
+// bit) with the matrix permuted to match; the block is the same operator.
+static void sort_targets(int k, const int *qubits, const double *mat, int *qs, std::vector<double> &m)
+{
+    const int D = 1 << k;
+    int order[HQ_MAX_K];
+    for (int i = 0; i < k; ++i) order[i] = i;
+    std::sort(order, order + k, [&](int a, int b) { return qubits[a] < qubits[b]; });
+    for (int i = 0; i < k; ++i) qs[i] = qubits[order[i]];
+    // new local index bit (k-1-i) is old bit (k-1-order[i])
+    auto old_index = [&](int r) {
+        int o = 0;
+        for (int i = 0; i < k; ++i)
+            if ((r >> (k - 1 - i)) & 1) o |= 1 << (k - 1 - order[i]);
+        return o;
+    };
+    m.resize(size_t(2) * D * D);
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            const size_t src = size_t(old_index(r)) * D + size_t(old_index(c));
+            m[2 * (size_t(r) * D + c)] = mat[2 * src];
+            m[2 * (size_t(r) * D + c) + 1] = mat[2 * src + 1];
+        }
+}
+
+// Shared-memory wavefronts of one warp-wide read in which lane l reads `w`
+// consecutive 4-byte words from word address a[l]: each of the 32 banks serves
+// one distinct word per wavefront.
+static int smem_wavefronts(const int (&a)[32], int w)
+{
+    int worst = 0;
+    for (int b = 0; b < 32; ++b) {
+        int words[128], nw = 0;
+        for (int l = 0; l < 32; ++l)
+            for (int i = 0; i < w; ++i) {
+                const int wd = a[l] + i;
+                if ((wd & 31) != b) continue;
+                bool seen = false;
+                for (int q = 0; q < nw && !seen; ++q) seen = words[q] == wd;
+                if (!seen) words[nw++] = wd;
+            }
+        worst = std::max(worst, nw);
+    }
+    return worst;
+}
+
+// Chooses the thread mapping for a tile geometry from a model of its shared-
+// memory reads (wavefronts) and global stores (32-byte sectors), both per 32
+// amplitudes.  Offsets are additive over disjoint bits, so one instruction of
+// each kind stands for all of them.
+static bool prefer_am(const TileGeom &g, int k, int &pair16)
+{
+    auto gbase = [&](int n) {  // tile-local base of group n
+        int ib = n;
+        for (int j = 0; j < k; ++j) {
+            const int tb = g.tl_bits[j];
+            ib = ((ib >> tb) << (tb + 1)) | (ib & ((1 << tb) - 1));
+        }
+        return ib;
+    };
+    auto flat = [&](int i) { return g.runoff[i >> g.c] + (i & ((1 << g.c) - 1)); };
+    pair16 = (g.toff[1] == 1) ? 1 : 0;  // the lowest target is tile bit 0
+    int a[32];
+    // GM: lane = group, one amplitude
+    for (int l = 0; l < 32; ++l) a[l] = 2 * gbase(l);
+    const double rd_gm = smem_wavefronts(a, 2);
+    // AM: lane = 4 row + p4 reads amplitude 2 p4 (+1) of group `row`
+    double rd_am;
+    if (pair16) {
+        for (int l = 0; l < 32; ++l) a[l] = 2 * (gbase(l >> 2) + g.toff[2 * (l & 3)]);
+        rd_am = smem_wavefronts(a, 4) / 2.0;
+    } else {
+        for (int l = 0; l < 32; ++l) a[l] = 2 * (gbase(l >> 2) + g.toff[2 * (l & 3)]);
+        rd_am = smem_wavefronts(a, 2);
+    }
+    // stores: sectors per warp instruction, averaged over the outputs
+    const int D = 1 << k;
+    double st_gm = 0, st_am = 0;
+    for (int r = 0; r < D; ++r) {
+        int64_t sec[32];
+        for (int l = 0; l < 32; ++l) sec[l] = (flat(gbase(l) + g.toff[r])) >> 2;
+        std::sort(sec, sec + 32);
+        st_gm += double(std::unique(sec, sec + 32) - sec);
+    }
+    for (int j = 0; j < D / 4; ++j) {
+        int64_t sec[32];
+        for (int l = 0; l < 32; ++l) sec[l] = (flat(gbase(l >> 2) + g.toff[4 * j + (l & 3)])) >> 2;
+        std::sort(sec, sec + 32);
+        st_am += double(std::unique(sec, sec + 32) - sec);
+    }
+    st_gm /= D;
+    st_am /= D / 4;
+    return rd_am + st_am / 4 < rd_gm + st_gm / 4;
+}
+
+template <int K, bool BF16, bool AM>
+static hq_status launch_tc(TcParams &p, const CUtensorMap &tmap, void *state, cudaStream_t s)
+{
+    using Lay = TcLayout<K>;
+    // Dynamic shared memory is padded so that no more CTAs share an SM than
+    // its 512 TMEM columns hold (an allocation beyond that would stall).
+    constexpr size_t kSmPerSm = 228 * 1024;
+    const size_t smem = std::max<size_t>(Lay::kBytes, kSmPerSm / (Lay::kCtasPerSm + 1) + 1024);
+    const void *fn = (const void *)k_tc<K, BF16, AM>;
+    const int per_sm = std::min(occupancy(fn, tc_threads<K>(), smem), Lay::kCtasPerSm);
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(sm_count()) * per_sm, p.g.total_tiles)));
+    k_tc<K, BF16, AM><<<grid, tc_threads<K>(), smem, s>>>(p, tmap, (float2 *)state);
+    return cuda_status("k_tc", cudaGetLastError());
+}
+
 template <int K, bool BF16>
 static hq_status run_tc(void *state, int n, const int *qubits, const double *mat, int64_t nstates, cudaStream_t s)
 {
-    using Lay = TcLayout<K>;
     TcParams p;
-    make_geom(p.g, n, K, qubits, K + 7, nstates);
+    int qs[HQ_MAX_K];
+    std::vector<double> ms;
+    sort_targets(K, qubits, mat, qs, ms);
+    make_geom(p.g, n, K, qs, K + 7, nstates);
     std::vector<uint16_t> hb;
-    p.out_mul = prepare_b<BF16>(K, mat, hb);
+    p.out_mul = prepare_b<BF16>(K, ms.data(), hb);
     CUtensorMap tmap;
     make_tile_map(p.g, n, nstates, state, p, tmap);
+    const bool am = prefer_am(p.g, K, p.am_pair16);
     uint4 *dmat = nullptr;
     const size_t bytes = hb.size() * sizeof(uint16_t);
     if (cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
     hq_status st = cuda_status("copy split matrix", cudaMemcpyAsync(dmat, hb.data(), bytes, cudaMemcpyHostToDevice, s));
     if (st == HQ_OK) {
         p.bmat = dmat;
-        // Dynamic shared memory is padded so that no more CTAs share an SM than
-        // its 512 TMEM columns hold (an allocation beyond that would stall).
-        constexpr size_t kSmPerSm = 228 * 1024;
-        const size_t smem = std::max<size_t>(Lay::kBytes, kSmPerSm / (Lay::kCtasPerSm + 1) + 1024);
-        const void *fn = (const void *)k_tc<K, BF16>;
-        const int per_sm = std::min(occupancy(fn, tc_threads<K>(), smem), Lay::kCtasPerSm);
-        const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(sm_count()) * per_sm, p.g.total_tiles)));
-        k_tc<K, BF16><<<grid, tc_threads<K>(), smem, s>>>(p, tmap, (float2 *)state);
-        st = cuda_status("k_tc", cudaGetLastError());
+        st = am ? launch_tc<K, BF16, true>(p, tmap, state, s) : launch_tc<K, BF16, false>(p, tmap, state, s);
     }
     cudaFreeAsync(dmat, s);
     return st;

@@ -64,6 +64,33 @@ def test_single_block_every_position_class(hq, engine, tol, k, n):
         assert err <= tol, (qs, err)
 
 
+LOW_BIT_PATTERNS = [[0, 1, 2, 3, 4, 5], [1, 2, 3, 4, 7, 8], [0, 1, 6, 7, 12, 13], [2, 3, 4, 8, 9, 10],
+                    [0, 2, 4, 6, 8, 10], [3, 4, 5, 9, 10, 11]]
+
+
+@pytest.mark.parametrize("engine,tol", [("tc_f16", 2e-6), ("tc_bf16", 3e-4)])
+@pytest.mark.parametrize("k", [4, 5, 6])
+@pytest.mark.parametrize("pattern", range(len(LOW_BIT_PATTERNS)))
+def test_low_bit_targets_in_any_order(hq, engine, tol, k, pattern):
+    """Targets on the lowest flat bits (the four-threads-per-group mapping,
+    with and without adjacent amplitude pairs), given in shuffled order."""
+    n = 18
+    bits = LOW_BIT_PATTERNS[pattern][:k]
+    rng = C.SplitMix64(97 * k + pattern)
+    qs = [n - 1 - b for b in bits]
+    for i in range(len(qs) - 1, 0, -1):  # seeded shuffle of the target order
+        j = rng.randint(0, i)
+        qs[i], qs[j] = qs[j], qs[i]
+    psi = random_state(n, 5 * k + pattern)
+    st = torch.from_numpy(psi).to(torch.complex64).cuda()
+    for _ in range(2):
+        M = C.random_unitary(k, rng)
+        hq.hq_apply_blocks(st, [(qs, M)], engine=engine, tc_min_k=4)
+        oracle.apply_gate(psi, n, qs, M)
+    err = rel_l2(st.cpu().numpy().astype(np.complex128), psi)
+    assert err <= tol, (qs, err)
+
+
 @pytest.mark.parametrize("scale", [1e-3, 37.0])
 def test_non_unitary_scaling(hq, scale):
     n, k = 14, 6
