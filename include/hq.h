@@ -93,6 +93,8 @@ typedef struct {
 #define HQ_ENGINE_CUDA_CORE 1 /* FP32/FP64 CUDA-core kernels only */
 #define HQ_ENGINE_TC_F16 2    /* k >= 5 blocks on tcgen05 tensor cores, FP16 hi+lo split (complex64) */
 #define HQ_ENGINE_TC_BF16 3   /* same, BF16 hi+lo split (complex64) */
+#define HQ_ENGINE_TC_PASS 4   /* blocks (k <= 6) grouped two at a time into 13-qubit tile passes on tcgen05
+                                 tensor cores, FP16 hi+lo split (complex64, n >= 14; smaller n: as TC_F16) */
 typedef struct {
     int engine;  /* HQ_ENGINE_* */
     int tc_min_k; /* blocks with k >= tc_min_k use the tensor-core engine (default 5) */
@@ -152,10 +154,33 @@ hq_status hq_apply_gate(void *state, int n, hq_dtype dt, const int *qubits, int 
  * hq_apply_blocks -- apply G gates / fused blocks in order (the evolution
  * loop of Sec. 4.2), choosing a kernel per block as configured (cfg NULL =
  * HQ_ENGINE_AUTO).  Tensor-core engines apply only to complex64 states.
+ * HQ_ENGINE_TC_PASS applies the same operators in the same order (blocks
+ * with disjoint targets may swap), up to two per read and write of the state:
+ * see hq_plan_passes.  It moves qubits between bit positions while it runs and
+ * restores the caller's order before it returns (stream order).
  * Errors: as hq_apply_gate, plus HQ_ERR_ARG (G < 0 or unknown engine).
  */
 hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates, int G, const hq_config *cfg,
                           void *stream);
+
+/*
+ * hq_plan_passes -- the plan HQ_ENGINE_TC_PASS executes for these gates (for
+ * inspection and tests).  A pass holds a tile of 13 physical bit positions
+ * that includes bits 0..6, applies up to max_blocks (1 or 2) of the gates to
+ * it in order, and moves the qubit at each of its positions to another of
+ * them; passes with no gate only move qubits (the final ones restore the
+ * caller's order).  Physical bit x initially holds qubit n-1-x.
+ *   records: out, max_passes records of HQ_PASS_RECORD ints each:
+ *            slots[13] (ascending), nb, gate[2] (indices into gates, -1
+ *            unused), dest[13] (new position of the qubit at slots[j]).
+ * Returns the number of passes (which may exceed max_passes: then only the
+ * first max_passes are written), or a negative hq_status: HQ_ERR_NULL,
+ * HQ_ERR_ARG (n < 14 or > 40, G < 0, max_blocks not 1 or 2),
+ * HQ_ERR_K_TOO_LARGE (k > 6), HQ_ERR_QUBIT_RANGE, HQ_ERR_DUP_QUBIT.
+ * Host only; no device work.
+ */
+#define HQ_PASS_RECORD 29
+int hq_plan_passes(int n, const hq_gate *gates, int G, int max_blocks, int *records, int max_passes);
 
 /*
  * hq_expectation -- <psi|H|psi> = sum_t coeff_t <psi|P_t|psi> for a Pauli sum

@@ -131,6 +131,17 @@ hq_status hq_apply_gate(void *state, int n, hq_dtype dt, const int *qubits, int 
     return launch_gate(state, n, dt, k, qubits, matrix, 1, HQ_ENGINE_AUTO, (cudaStream_t)stream);
 }
 
+static hq_status hq_apply_blocks_tc_f16(void *state, int n, hq_dtype dt, const hq_gate *gates, int G, int tc_min_k,
+                                        void *stream)
+{
+    for (int g = 0; g < G; ++g) {
+        const int eng = gates[g].k < tc_min_k ? HQ_ENGINE_AUTO : HQ_ENGINE_TC_F16;
+        hq_status st = launch_gate(state, n, dt, gates[g].k, gates[g].qubits, gates[g].matrix, 1, eng, (cudaStream_t)stream);
+        if (st != HQ_OK) return st;
+    }
+    return HQ_OK;
+}
+
 hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates, int G, const hq_config *cfg,
                           void *stream)
 {
@@ -140,11 +151,16 @@ hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates,
     if (G > 0 && !gates) return HQ_ERR_NULL;
     const int engine = cfg ? cfg->engine : HQ_ENGINE_AUTO;
     const int tc_min_k = (cfg && cfg->tc_min_k > 0) ? cfg->tc_min_k : 5;
-    if (engine < HQ_ENGINE_AUTO || engine > HQ_ENGINE_TC_BF16) return HQ_ERR_ARG;
-    if ((engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16) && dt != HQ_C64) return HQ_ERR_DTYPE;
+    if (engine < HQ_ENGINE_AUTO || engine > HQ_ENGINE_TC_PASS) return HQ_ERR_ARG;
+    if ((engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16 || engine == HQ_ENGINE_TC_PASS) && dt != HQ_C64)
+        return HQ_ERR_DTYPE;
     for (int g = 0; g < G; ++g) {
         if ((st = check_qubits(n, gates[g].k, gates[g].qubits, HQ_MAX_K)) != HQ_OK) return st;
         if (!gates[g].matrix) return HQ_ERR_NULL;
+    }
+    if (engine == HQ_ENGINE_TC_PASS) {
+        if (n >= 14 && G > 0) return launch_tc_passes(state, n, gates, G, 2, (cudaStream_t)stream);
+        return hq_apply_blocks_tc_f16(state, n, dt, gates, G, tc_min_k, stream);
     }
     for (int g = 0; g < G; ++g) {
         int eng = engine;
@@ -153,6 +169,28 @@ hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates,
         if (st != HQ_OK) return st;
     }
     return HQ_OK;
+}
+
+int hq_plan_passes(int n, const hq_gate *gates, int G, int max_blocks, int *records, int max_passes)
+{
+    if (G < 0 || max_blocks < 1 || max_blocks > 2 || n < 14 || n > 40 || max_passes < 0) return HQ_ERR_ARG;
+    if ((G > 0 && !gates) || (max_passes > 0 && !records)) return HQ_ERR_NULL;
+    for (int g = 0; g < G; ++g) {
+        if (gates[g].k > 6) return HQ_ERR_K_TOO_LARGE;
+        hq_status st = check_qubits(n, gates[g].k, gates[g].qubits, HQ_MAX_K);
+        if (st != HQ_OK) return st;
+    }
+    std::vector<PassPlanEntry> plan;
+    plan_passes(n, gates, G, max_blocks, plan);
+    for (int i = 0; i < int(plan.size()) && i < max_passes; ++i) {
+        int *r = records + size_t(i) * HQ_PASS_RECORD;
+        for (int j = 0; j < 13; ++j) r[j] = plan[i].slots[j];
+        r[13] = plan[i].nb;
+        r[14] = plan[i].nb > 0 ? plan[i].gate[0] : -1;
+        r[15] = plan[i].nb > 1 ? plan[i].gate[1] : -1;
+        for (int j = 0; j < 13; ++j) r[16 + j] = plan[i].dest[j];
+    }
+    return int(plan.size());
 }
 
 hq_status hq_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T, double *out_host,

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/hq.h"
 
@@ -183,6 +184,19 @@ hq_status launch_expectation_static(const void *state, int n, hq_dtype dt, const
 // HQ_ERR_TIMEOUT (and clears the flag) if a bounded device-side wait ran out
 // since the last call; synchronous.
 hq_status device_error_status();
+
+// Tile passes (k_pass.cu).  One pass holds a 13-bit tile that contains the 7
+// lowest physical bits, applies up to two fused blocks to it and permutes its
+// qubits among its own bit positions; passes with nb = 0 only relayout.
+struct PassPlanEntry {
+    int slots[13];  // physical bit positions of the tile, ascending
+    int nb;         // fused blocks applied
+    int gate[2];    // their indices in the caller's list, in application order
+    int dest[13];   // new physical position of the qubit at slots[j]
+};
+void plan_passes(int n, const hq_gate *gates, int G, int max_blocks, std::vector<PassPlanEntry> &plan);
+hq_status launch_tc_passes(void *state, int n, const hq_gate *gates, int G, int max_blocks, cudaStream_t s);
+hq_status pass_error_status();
 
 // validation helpers (hq_api.cu)
 hq_status check_qubits(int n, int k, const int *qubits, int kmax);

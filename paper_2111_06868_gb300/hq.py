@@ -23,7 +23,8 @@ HQ_MAX_PAULI = 8
 HQ_C64, HQ_C128 = 0, 1
 HQ_OP_MATRIX, HQ_OP_ROT = 0, 1
 HQ_ENGINE_AUTO, HQ_ENGINE_CUDA_CORE, HQ_ENGINE_TC_F16, HQ_ENGINE_TC_BF16 = 0, 1, 2, 3
-ENGINES = {"auto": 0, "cuda_core": 1, "tc_f16": 2, "tc_bf16": 3}
+ENGINES = {"auto": 0, "cuda_core": 1, "tc_f16": 2, "tc_bf16": 3, "tc_pass": 4}
+PASS_RECORD = 29
 
 STATUS = {
     0: "HQ_OK", -1: "HQ_ERR_NULL", -2: "HQ_ERR_QUBIT_RANGE", -3: "HQ_ERR_DUP_QUBIT", -4: "HQ_ERR_K_TOO_LARGE",
@@ -89,6 +90,7 @@ def load(path: str | None = None):
         "hq_version": ([], ctypes.c_char_p),
         "hq_state_init": ([V, I, I, ctypes.c_char_p, V], I),
         "hq_fuse": ([I, V, I, I, V, P(I), V, ctypes.c_int64, V], I),
+        "hq_plan_passes": ([I, V, I, I, V, I], I),
         "hq_apply_gate": ([V, I, I, V, I, V, V], I),
         "hq_apply_blocks": ([V, I, I, V, I, V, V], I),
         "hq_expectation": ([V, I, I, V, I, P(D), V], I),
@@ -209,6 +211,29 @@ def hq_apply_gate(state, qubits: Sequence[int], matrix, stream=None):
     _check(load().hq_apply_gate(ptr, n, dt, q, len(qubits), m.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
            "hq_apply_gate")
     return state
+
+
+def hq_plan_passes(n: int, blocks: Iterable, max_blocks: int = 2):
+    """The tile-pass plan (list of dicts: slots, gates, dest) that the
+    "tc_pass" engine runs for these blocks; host only."""
+    keep: list = []
+    arr, G = _gates_array(blocks, keep)
+    lib = load()
+    cap = 2 * G + 16
+    while True:
+        rec = np.zeros(cap * PASS_RECORD, np.int32)
+        cnt = lib.hq_plan_passes(n, arr, G, max_blocks, rec.ctypes.data_as(ctypes.c_void_p), cap)
+        if cnt < 0:
+            raise HQError(cnt, "hq_plan_passes", "")
+        if cnt <= cap:
+            break
+        cap = cnt
+    out = []
+    for i in range(cnt):
+        r = rec[i * PASS_RECORD:(i + 1) * PASS_RECORD]
+        out.append({"slots": [int(x) for x in r[:13]], "gates": [int(x) for x in r[14:14 + int(r[13])]],
+                    "dest": [int(x) for x in r[16:29]]})
+    return out
 
 
 def hq_fuse(n: int, gates: Iterable, k_max: int, with_members: bool = False):
