@@ -131,17 +131,6 @@ hq_status hq_apply_gate(void *state, int n, hq_dtype dt, const int *qubits, int 
     return launch_gate(state, n, dt, k, qubits, matrix, 1, HQ_ENGINE_AUTO, (cudaStream_t)stream);
 }
 
-static hq_status hq_apply_blocks_tc_f16(void *state, int n, hq_dtype dt, const hq_gate *gates, int G, int tc_min_k,
-                                        void *stream)
-{
-    for (int g = 0; g < G; ++g) {
-        const int eng = gates[g].k < tc_min_k ? HQ_ENGINE_AUTO : HQ_ENGINE_TC_F16;
-        hq_status st = launch_gate(state, n, dt, gates[g].k, gates[g].qubits, gates[g].matrix, 1, eng, (cudaStream_t)stream);
-        if (st != HQ_OK) return st;
-    }
-    return HQ_OK;
-}
-
 hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates, int G, const hq_config *cfg,
                           void *stream)
 {
@@ -160,12 +149,12 @@ hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates,
     }
     if (engine == HQ_ENGINE_TC_PASS) {
         if (n >= 14 && G > 0) return launch_tc_passes(state, n, gates, G, 2, (cudaStream_t)stream);
-        return hq_apply_blocks_tc_f16(state, n, dt, gates, G, tc_min_k, stream);
+        return launch_tc_blocks(state, n, gates, G, tc_min_k, 0, (cudaStream_t)stream);
     }
+    if (engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16)
+        return launch_tc_blocks(state, n, gates, G, tc_min_k, engine == HQ_ENGINE_TC_BF16, (cudaStream_t)stream);
     for (int g = 0; g < G; ++g) {
-        int eng = engine;
-        if ((eng == HQ_ENGINE_TC_F16 || eng == HQ_ENGINE_TC_BF16) && gates[g].k < tc_min_k) eng = HQ_ENGINE_AUTO;
-        st = launch_gate(state, n, dt, gates[g].k, gates[g].qubits, gates[g].matrix, 1, eng, (cudaStream_t)stream);
+        st = launch_gate(state, n, dt, gates[g].k, gates[g].qubits, gates[g].matrix, 1, engine, (cudaStream_t)stream);
         if (st != HQ_OK) return st;
     }
     return HQ_OK;

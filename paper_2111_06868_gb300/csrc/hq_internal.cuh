@@ -184,6 +184,11 @@ hq_status launch_expectation_static(const void *state, int n, hq_dtype dt, const
 // HQ_ERR_TIMEOUT (and clears the flag) if a bounded device-side wait ran out
 // since the last call; synchronous.
 hq_status device_error_status();
+// Tensor-core engine over a list of gates: every gate with tc_min_k <= k
+// (k >= 4, not diagonal) runs on k_tc, the others through launch_gate; all
+// split matrices are prepared on the host and copied in one transfer.
+hq_status launch_tc_blocks(void *state, int n, const hq_gate *gates, int G, int tc_min_k, int split_bf16,
+                           cudaStream_t s);
 
 // Tile passes (k_pass.cu).  One pass holds a 13-bit tile that contains the 7
 // lowest physical bits, applies up to two fused blocks to it and permutes its

@@ -24,6 +24,7 @@ namespace hq {
 struct ExpTerm {
     uint64_t zm;
     double wr, wi;
+    float wrf, wif;  // the same weights in FP32 (complex64 states: no FP64 conversion per amplitude)
 };
 struct ExpGroup {
     uint64_t xm;
@@ -49,51 +50,150 @@ __device__ __forceinline__ void eval_f(const ExpParams &p, const ExpGroup &gr, u
     fi = 0;
     for (int t = gr.t0; t < gr.t0 + gr.nt; ++t) {
         const R sg = (__popcll(y & p.term[t].zm) & 1) ? R(-1) : R(1);
-        fr += sg * R(p.term[t].wr);
-        fi += sg * R(p.term[t].wi);
+        if constexpr (sizeof(R) == 4) {
+            fr += sg * p.term[t].wrf;
+            fi += sg * p.term[t].wif;
+        } else {
+            fr += sg * p.term[t].wr;
+            fi += sg * p.term[t].wi;
+        }
     }
 }
 
 // partials[group * gridDim.x + blockIdx.x]
+//
+// Each thread first issues a chunk of kChunk independent loads (for xmask = 0
+// two adjacent amplitudes per load), then evaluates them: enough bytes in
+// flight per SM to keep HBM busy.  Chunk sums are formed in R and joined to
+// an FP64 accumulator.
 template <typename R>
-__global__ void __launch_bounds__(kRedThreads) k_expect(const ExpParams p, const typename C2<R>::type *__restrict__ psi,
+__global__ void __launch_bounds__(kRedThreads, sizeof(R) == 4 ? 3 : 1) k_expect(const ExpParams p, const typename C2<R>::type *__restrict__ psi,
                                                         double *__restrict__ partials)
 {
+    using V = typename C2<R>::type;
     const ExpGroup gr = p.grp[blockIdx.y];
     const int64_t dim = int64_t(1) << p.n;
-    const int64_t items = (gr.hb < 0 ? dim : dim >> 1) * p.nstates;
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
-    constexpr int kChunk = 8;  // items summed in R before joining the FP64 accumulator
+    const int64_t tid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t items = (dim >> 1) * p.nstates;  // pairs (x, x + 1) or (x, x ^ xmask)
+    constexpr int kChunk = 8;
+    // complex64: compensated (Kahan) FP32 sum per thread, joined in FP64 at
+    // the block reduction (GB300's FP64 pipe is too narrow for one FP64 add
+    // per chunk); complex128: FP64 throughout
     double acc = 0;
-    for (int64_t base = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; base < items; base += stride * kChunk) {
+    float accf = 0.f, comp = 0.f;
+    auto add = [&](R v) {
+        if constexpr (sizeof(R) == 4) {
+            const float y = v - comp;
+            const float s = accf + y;
+            comp = (s - accf) - y;
+            accf = s;
+        } else {
+            acc += v;
+        }
+    };
+    // item `it`: the indices of its two amplitudes within the state
+    auto index = [&](int64_t it, uint64_t &x, uint64_t &x2) {
+        if (gr.hb < 0) {
+            x = uint64_t(2 * it) & uint64_t(dim - 1);
+            x2 = x + 1;
+        } else {
+            const int hb = gr.hb;
+            const int64_t q = it & ((dim >> 1) - 1);
+            x = uint64_t(((q >> hb) << (hb + 1)) | (q & ((int64_t(1) << hb) - 1)));
+            x2 = x ^ gr.xm;
+        }
+    };
+    // item `it`: its two amplitudes
+    auto load = [&](int64_t it, V &a, V &b) {
+        if (gr.hb < 0) {
+            if constexpr (sizeof(R) == 4) {  // one 16-byte load
+                const float4 w = reinterpret_cast<const float4 *>(psi)[it];
+                a = make_float2(w.x, w.y);
+                b = make_float2(w.z, w.w);
+            } else {
+                a = psi[2 * it];
+                b = psi[2 * it + 1];
+            }
+        } else {
+            uint64_t x, x2;
+            index(it, x, x2);
+            const int64_t s = it >> (p.n - 1);
+            a = psi[s * dim + int64_t(x)];
+            b = psi[s * dim + int64_t(x2)];
+        }
+    };
+    auto term = [&](const V &a, const V &b, uint64_t x, uint64_t x2) -> R {
+        R fr, fi, gr_, gi;
+        eval_f<R>(p, gr, x, fr, fi);
+        eval_f<R>(p, gr, x2, gr_, gi);
+        if (gr.hb < 0) return (a.x * a.x + a.y * a.y) * fr + (b.x * b.x + b.y * b.y) * gr_;
+        // z = conj(a) * b;  Re[z f(x)] + Re[conj(z) f(x2)]
+        const R zr = a.x * b.x + a.y * b.y, zi = a.x * b.y - a.y * b.x;
+        return zr * fr - zi * fi + zr * gr_ + zi * gi;
+    };
+    // each CTA reads kChunk * blockDim.x consecutive items per step (all loads
+    // issued before any use); the last, partial span goes item by item
+    const int64_t span = int64_t(kChunk) * blockDim.x;
+    const int64_t full = items / span;
+    if (gr.hb < 0 && gr.nt == 1) {
+        // one diagonal term w (-1)^popc(x & zm): sum the signed |psi_x|^2,
+        // multiply by Re w once (the norm when zm = 0)
+        const uint64_t zm = p.term[gr.t0].zm;
+        const uint64_t xmask = uint64_t(dim - 1);
+        for (int64_t c = blockIdx.x; c < full; c += gridDim.x) {
+            const int64_t base = c * span + threadIdx.x;
+            V a[kChunk], b[kChunk];
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) load(base + u * blockDim.x, a[u], b[u]);
+            R part = 0;
+#pragma unroll
+            for (int u = 0; u < kChunk; ++u) {
+                const R na = a[u].x * a[u].x + a[u].y * a[u].y, nb = b[u].x * b[u].x + b[u].y * b[u].y;
+                if (zm == 0) {
+                    part += na + nb;
+                } else {
+                    const uint64_t x = uint64_t(2 * (base + u * blockDim.x)) & xmask;
+                    part += ((__popcll(x & zm) & 1) ? -na : na) + ((__popcll((x + 1) & zm) & 1) ? -nb : nb);
+                }
+            }
+            add(part);
+        }
+        for (int64_t it = full * span + tid; it < items; it += stride) {
+            V a, b;
+            load(it, a, b);
+            const uint64_t x = uint64_t(2 * it) & xmask;
+            const R na = a.x * a.x + a.y * a.y, nb = b.x * b.x + b.y * b.y;
+            add(((__popcll(x & zm) & 1) ? -na : na) + ((__popcll((x + 1) & zm) & 1) ? -nb : nb));
+        }
+        if constexpr (sizeof(R) == 4) acc = double(accf) - double(comp);
+        acc *= p.term[gr.t0].wr;
+        const double s = block_sum(acc);
+        if (threadIdx.x == 0) partials[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = s;
+        return;
+    }
+    for (int64_t c = blockIdx.x; c < full; c += gridDim.x) {
+        const int64_t base = c * span + threadIdx.x;
+        V a[kChunk], b[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) load(base + u * blockDim.x, a[u], b[u]);
         R part = 0;
 #pragma unroll
         for (int u = 0; u < kChunk; ++u) {
-            const int64_t it = base + u * stride;
-            if (it >= items) break;
-            if (gr.hb < 0) {
-                const typename C2<R>::type a = psi[it];
-                R fr, fi;
-                eval_f<R>(p, gr, uint64_t(it) & uint64_t(dim - 1), fr, fi);
-                part += (a.x * a.x + a.y * a.y) * fr;
-            } else {
-                const int hb = gr.hb;
-                const int64_t s = it >> (p.n - 1);
-                const int64_t q = it & ((dim >> 1) - 1);
-                const int64_t x = ((q >> hb) << (hb + 1)) | (q & ((int64_t(1) << hb) - 1));
-                const int64_t x2 = x ^ int64_t(gr.xm);
-                const typename C2<R>::type a = psi[s * dim + x], b = psi[s * dim + x2];
-                // z = conj(a) * b
-                const R zr = a.x * b.x + a.y * b.y, zi = a.x * b.y - a.y * b.x;
-                R fr, fi, gr_, gi;
-                eval_f<R>(p, gr, uint64_t(x), fr, fi);
-                eval_f<R>(p, gr, uint64_t(x2), gr_, gi);
-                // Re[z f(x)] + Re[conj(z) f(x2)]
-                part += zr * fr - zi * fi + zr * gr_ + zi * gi;
-            }
+            uint64_t x, x2;
+            index(base + u * blockDim.x, x, x2);
+            part += term(a[u], b[u], x, x2);
         }
-        acc += double(part);
+        add(part);
     }
+    for (int64_t it = full * span + tid; it < items; it += stride) {
+        V a, b;
+        uint64_t x, x2;
+        load(it, a, b);
+        index(it, x, x2);
+        add(term(a, b, x, x2));
+    }
+    if constexpr (sizeof(R) == 4) acc = double(accf) - double(comp);
     const double s = block_sum(acc);
     if (threadIdx.x == 0) partials[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = s;
 }
@@ -148,7 +248,8 @@ static hq_status build_groups(int n, const hq_pauli_term *terms, int T, std::vec
             g.hb = g.xm ? 63 - __builtin_clzll(g.xm) : -1;
             g.t0 = int(flat.size());
             g.nt = int(u1 - u0);
-            for (size_t u = u0; u < u1; ++u) flat.push_back({tms[u].zm, tms[u].wr, tms[u].wi});
+            for (size_t u = u0; u < u1; ++u)
+                flat.push_back({tms[u].zm, tms[u].wr, tms[u].wi, float(tms[u].wr), float(tms[u].wi)});
             groups.push_back(g);
         }
         i = j;

@@ -651,43 +651,97 @@ static hq_status launch_tc(TcParams &p, const CUtensorMap &tmap, void *state, cu
     return cuda_status("k_tc", cudaGetLastError());
 }
 
-template <int K, bool BF16>
-static hq_status run_tc(void *state, int n, const int *qubits, const double *mat, int64_t nstates, cudaStream_t s)
-{
+// A block ready to launch: parameters, tensor map, the launcher of its
+// (K, BF16, mapping) instantiation, and its split matrix (host copy).
+struct TcPrepared {
     TcParams p;
+    CUtensorMap tmap;
+    hq_status (*launch)(TcParams &, const CUtensorMap &, void *, cudaStream_t);
+    std::vector<uint16_t> b;
+};
+
+template <int K, bool BF16>
+static void prepare_tc(void *state, int n, const int *qubits, const double *mat, int64_t nstates, TcPrepared &out)
+{
+    TcParams &p = out.p;
     int qs[HQ_MAX_K];
     std::vector<double> ms;
     sort_targets(K, qubits, mat, qs, ms);
     make_geom(p.g, n, K, qs, K + 7, nstates);
-    std::vector<uint16_t> hb;
-    p.out_mul = prepare_b<BF16>(K, ms.data(), hb);
-    CUtensorMap tmap;
-    make_tile_map(p.g, n, nstates, state, p.ld, tmap);
-    const bool am = prefer_am(p.g, K, p.am_pair16);
-    uint4 *dmat = nullptr;
-    const size_t bytes = hb.size() * sizeof(uint16_t);
-    if (cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
-    hq_status st = cuda_status("copy split matrix", cudaMemcpyAsync(dmat, hb.data(), bytes, cudaMemcpyHostToDevice, s));
-    if (st == HQ_OK) {
-        p.bmat = dmat;
-        st = am ? launch_tc<K, BF16, true>(p, tmap, state, s) : launch_tc<K, BF16, false>(p, tmap, state, s);
+    p.out_mul = prepare_b<BF16>(K, ms.data(), out.b);
+    make_tile_map(p.g, n, nstates, state, p.ld, out.tmap);
+    out.launch = prefer_am(p.g, K, p.am_pair16) ? &launch_tc<K, BF16, true> : &launch_tc<K, BF16, false>;
+}
+
+static void prepare_tc_any(void *state, int n, int k, const int *qubits, const double *mat, int64_t nstates,
+                           int split_bf16, TcPrepared &out)
+{
+    switch (k) {
+    case 4: return split_bf16 ? prepare_tc<4, true>(state, n, qubits, mat, nstates, out)
+                              : prepare_tc<4, false>(state, n, qubits, mat, nstates, out);
+    case 5: return split_bf16 ? prepare_tc<5, true>(state, n, qubits, mat, nstates, out)
+                              : prepare_tc<5, false>(state, n, qubits, mat, nstates, out);
+    default: return split_bf16 ? prepare_tc<6, true>(state, n, qubits, mat, nstates, out)
+                               : prepare_tc<6, false>(state, n, qubits, mat, nstates, out);
     }
-    cudaFreeAsync(dmat, s);
+}
+
+// Bytes of the split matrix (B_hi and B_lo) of a k-qubit block.
+static size_t tc_matrix_bytes(int k) { return size_t(2) * (size_t(4) << (2 * k)) * sizeof(uint16_t); }
+
+static bool tc_eligible(int n, const hq_gate &gt, int tc_min_k)
+{
+    return gt.k >= tc_min_k && gt.k >= 4 && gt.k <= 6 && n >= gt.k + 7 && !is_diagonal(gt.k, gt.matrix);
+}
+
+// Launches the gates in order: tensor-core blocks take their split matrix
+// from one device buffer allocated up front (each block is prepared on the
+// host and copied just before its launch, so the host work overlaps the
+// kernels already queued); the other gates go through launch_gate.
+static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G, int tc_min_k, int split_bf16,
+                                int64_t nstates, cudaStream_t s)
+{
+    size_t bytes = 0;
+    for (int g = 0; g < G; ++g)
+        if (tc_eligible(n, gates[g], tc_min_k)) bytes += tc_matrix_bytes(gates[g].k);
+    char *dmat = nullptr;
+    if (bytes && cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
+    hq_status st = HQ_OK;
+    size_t off = 0;
+    TcPrepared b;
+    for (int g = 0; g < G && st == HQ_OK; ++g) {
+        const hq_gate &gt = gates[g];
+        if (!tc_eligible(n, gt, tc_min_k)) {
+            st = launch_gate(state, n, HQ_C64, gt.k, gt.qubits, gt.matrix, nstates, HQ_ENGINE_AUTO, s);
+            continue;
+        }
+        prepare_tc_any(state, n, gt.k, gt.qubits, gt.matrix, nstates, split_bf16, b);
+        const size_t nb = b.b.size() * sizeof(uint16_t);
+        st = cuda_status("copy split matrix", cudaMemcpyAsync(dmat + off, b.b.data(), nb, cudaMemcpyHostToDevice, s));
+        if (st != HQ_OK) break;
+        b.p.bmat = reinterpret_cast<const uint4 *>(dmat + off);
+        st = b.launch(b.p, b.tmap, state, s);
+        off += nb;
+    }
+    if (dmat) cudaFreeAsync(dmat, s);
     return st;
 }
 
 hq_status launch_tc_block(void *state, int n, int k, const int *qubits, const double *matrix, int64_t nstates,
                           int split_bf16, cudaStream_t s)
 {
-    switch (k) {
-    case 4: return split_bf16 ? run_tc<4, true>(state, n, qubits, matrix, nstates, s)
-                              : run_tc<4, false>(state, n, qubits, matrix, nstates, s);
-    case 5: return split_bf16 ? run_tc<5, true>(state, n, qubits, matrix, nstates, s)
-                              : run_tc<5, false>(state, n, qubits, matrix, nstates, s);
-    case 6: return split_bf16 ? run_tc<6, true>(state, n, qubits, matrix, nstates, s)
-                              : run_tc<6, false>(state, n, qubits, matrix, nstates, s);
-    }
-    return HQ_ERR_K_TOO_LARGE;
+    if (k < 4 || k > 6) return HQ_ERR_K_TOO_LARGE;
+    hq_gate gt;
+    gt.k = k;
+    for (int j = 0; j < k; ++j) gt.qubits[j] = qubits[j];
+    gt.matrix = matrix;
+    return launch_tc_list(state, n, &gt, 1, 4, split_bf16, nstates, s);
+}
+
+hq_status launch_tc_blocks(void *state, int n, const hq_gate *gates, int G, int tc_min_k, int split_bf16,
+                           cudaStream_t s)
+{
+    return launch_tc_list(state, n, gates, G, tc_min_k, split_bf16, 1, s);
 }
 
 hq_status device_error_status()
