@@ -147,14 +147,15 @@ def measured_traffic(kernel_class, n):
     return entry["dram_bytes_per_amplitude"] * (1 << n)
 
 
-def block_class(qs, m, engine, tc_min_k):
-    """Which kernel libhq launches for this block (mirrors its dispatch)."""
+def block_class(qs, m, engine, tc_min_k, n=30):
+    """Which kernel libhq launches for this block (mirrors its dispatch:
+    tensor-core blocks of k = 4, 5 run widened to 6 qubits when n >= 13)."""
     d = m.shape[0]
     k = len(qs)
     if not np.any(m[~np.eye(d, dtype=bool)]):
         return f"k_diag_k{k}"
-    if engine.startswith("tc") and k >= tc_min_k:
-        return f"k_tc_{engine[3:]}_k{k}"
+    if engine.startswith("tc") and k >= max(tc_min_k, 4) and n >= k + 7:
+        return f"k_tc_{engine[3:]}_k{6 if n >= 13 else k}"
     return f"k_gather_k{k}" if k <= 4 else f"k_block_k{k}"
 
 
@@ -387,7 +388,7 @@ def main():
     blocks = hq.hq_fuse(n, circ.gates, args.kmax) if args.kmax > 0 else [(g.qubits, g.matrix) for g in circ.gates]
     fuse_s = time.perf_counter() - t_f
     B = len(blocks)
-    classes = [block_class(q, m, args.engine, args.tc_min_k) for q, m in blocks]
+    classes = [block_class(q, m, args.engine, args.tc_min_k, n) for q, m in blocks]
     cdt = torch.complex64 if args.dtype == "complex64" else torch.complex128
     S = 8 if cdt == torch.complex64 else 16
     state = torch.empty(1 << n, dtype=cdt, device="cuda")

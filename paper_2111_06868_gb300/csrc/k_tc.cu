@@ -591,7 +591,7 @@ int smem_wavefronts(const int (&a)[32], int w)
 // memory reads (wavefronts) and global stores (32-byte sectors), both per 32
 // amplitudes.  Offsets are additive over disjoint bits, so one instruction of
 // each kind stands for all of them.
-static bool prefer_am(const TileGeom &g, int k, int &pair16)
+static bool prefer_am(const TileGeom &g, int k, int &pair16, double *best_cost = nullptr)
 {
     auto gbase = [&](int n) {  // tile-local base of group n
         int ib = n;
@@ -633,7 +633,9 @@ static bool prefer_am(const TileGeom &g, int k, int &pair16)
     }
     st_gm /= D;
     st_am /= D / 4;
-    return rd_am + st_am / 4 < rd_gm + st_gm / 4;
+    const double c_gm = rd_gm + st_gm / 4, c_am = rd_am + st_am / 4;
+    if (best_cost) *best_cost = std::min(c_gm, c_am);
+    return c_am < c_gm;
 }
 
 template <int K, bool BF16, bool AM>
@@ -694,6 +696,63 @@ static bool tc_eligible(int n, const hq_gate &gt, int tc_min_k)
     return gt.k >= tc_min_k && gt.k >= 4 && gt.k <= 6 && n >= gt.k + 7 && !is_diagonal(gt.k, gt.matrix);
 }
 
+// Blocks of k = 4, 5 run as 6-qubit blocks M (x) I on 6 - k more qubits: the
+// 6-qubit kernel is bound by HBM, the narrower ones by per-tile overheads
+// (measured on n=30: k=4 ~2.7-3.5 TB/s, widened ~5-5.9 TB/s).  The extra
+// qubits are the pair (or single qubit), among a few candidates (lowest and
+// highest free bits), whose tile geometry the bank/sector model rates best.
+static void widen_to_6(int n, const hq_gate &gt, hq_gate &w, std::vector<double> &mat)
+{
+    const int k = gt.k, pad = 6 - k, D = 1 << k;
+    std::vector<int> free_bits;  // flat bits not targeted, ascending
+    for (int b = 0; b < n; ++b) {
+        bool used = false;
+        for (int j = 0; j < k; ++j) used = used || (n - 1 - gt.qubits[j]) == b;
+        if (!used) free_bits.push_back(b);
+    }
+    std::vector<std::vector<int>> cands;  // pad bits
+    const int nf = int(free_bits.size());
+    if (pad == 1) {
+        for (int i : {0, 1, nf - 1}) cands.push_back({free_bits[i]});
+    } else {
+        cands.push_back({free_bits[0], free_bits[1]});
+        cands.push_back({free_bits[nf - 2], free_bits[nf - 1]});
+        cands.push_back({free_bits[0], free_bits[nf - 1]});
+        cands.push_back({free_bits[1], free_bits[nf - 1]});
+    }
+    double best = 1e300;
+    std::vector<int> pick;
+    for (const auto &c : cands) {
+        int qs[6];
+        for (int j = 0; j < k; ++j) qs[j] = gt.qubits[j];
+        for (int j = 0; j < pad; ++j) qs[k + j] = n - 1 - c[j];
+        std::sort(qs, qs + 6);
+        TileGeom g;
+        make_geom(g, n, 6, qs, 13, 1);
+        int pair16 = 0;
+        double cost = 0;
+        prefer_am(g, 6, pair16, &cost);
+        if (cost < best) {
+            best = cost;
+            pick = c;
+        }
+    }
+    w.k = 6;
+    for (int j = 0; j < k; ++j) w.qubits[j] = gt.qubits[j];
+    for (int j = 0; j < pad; ++j) w.qubits[k + j] = n - 1 - pick[j];
+    // M (x) I: the original qubits are the high local bits, the pads the low ones
+    mat.assign(size_t(2) * 64 * 64, 0.0);
+    const int pm = (1 << pad) - 1;
+    for (int r = 0; r < 64; ++r)
+        for (int c = 0; c < 64; ++c)
+            if ((r & pm) == (c & pm)) {
+                const size_t src = size_t(r >> pad) * D + size_t(c >> pad);
+                mat[2 * (size_t(r) * 64 + c)] = gt.matrix[2 * src];
+                mat[2 * (size_t(r) * 64 + c) + 1] = gt.matrix[2 * src + 1];
+            }
+    w.matrix = mat.data();
+}
+
 // Launches the gates in order: tensor-core blocks take their split matrix
 // from one device buffer allocated up front (each block is prepared on the
 // host and copied just before its launch, so the host work overlaps the
@@ -703,7 +762,7 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
 {
     size_t bytes = 0;
     for (int g = 0; g < G; ++g)
-        if (tc_eligible(n, gates[g], tc_min_k)) bytes += tc_matrix_bytes(gates[g].k);
+        if (tc_eligible(n, gates[g], tc_min_k)) bytes += tc_matrix_bytes(n >= 13 ? 6 : gates[g].k);
     char *dmat = nullptr;
     if (bytes && cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
     hq_status st = HQ_OK;
@@ -715,7 +774,14 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
             st = launch_gate(state, n, HQ_C64, gt.k, gt.qubits, gt.matrix, nstates, HQ_ENGINE_AUTO, s);
             continue;
         }
-        prepare_tc_any(state, n, gt.k, gt.qubits, gt.matrix, nstates, split_bf16, b);
+        if (gt.k < 6 && n >= 13) {
+            hq_gate w;
+            std::vector<double> wm;
+            widen_to_6(n, gt, w, wm);
+            prepare_tc_any(state, n, 6, w.qubits, w.matrix, nstates, split_bf16, b);
+        } else {
+            prepare_tc_any(state, n, gt.k, gt.qubits, gt.matrix, nstates, split_bf16, b);
+        }
         const size_t nb = b.b.size() * sizeof(uint16_t);
         st = cuda_status("copy split matrix", cudaMemcpyAsync(dmat + off, b.b.data(), nb, cudaMemcpyHostToDevice, s));
         if (st != HQ_OK) break;

@@ -49,8 +49,10 @@ def qsets(n, k, seed):
 
 @pytest.mark.parametrize("engine,tol", [("tc_f16", 2e-6), ("tc_bf16", 3e-4)])
 @pytest.mark.parametrize("k", [4, 5, 6])
-@pytest.mark.parametrize("n", [13, 16, 20])
+@pytest.mark.parametrize("n", [11, 12, 13, 16, 20])
 def test_single_block_every_position_class(hq, engine, tol, k, n):
+    """n >= 13: k = 4, 5 blocks run widened to 6 qubits; n = 11, 12 keep the
+    4- and 5-qubit kernels."""
     if n < k + 7:
         pytest.skip()
     rng = C.SplitMix64(31 * n + k)
