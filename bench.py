@@ -123,7 +123,7 @@ def kernel_sources_sha(kernel_class):
     figures to the code they were measured on)."""
     import hashlib
 
-    files = {"k_tc": ["k_tc.cu"], "k_gather": ["k_apply.cu"], "k_diag": ["k_apply.cu"], "k_block": ["k_apply.cu"]}
+    files = {"k_tc": ["k_tc.cu", "hq_tcgen05.cuh"], "k_gather": ["k_apply.cu"], "k_diag": ["k_apply.cu"], "k_block": ["k_apply.cu"]}
     key = next((k for k in files if kernel_class.startswith(k)), None)
     if key is None:
         return None
@@ -350,7 +350,7 @@ def main():
     ap.add_argument("--workload", default="n30", choices=["n30", "n33", "n27", "n12"])
     ap.add_argument("--kmax", type=int, default=6)
     ap.add_argument("--dtype", default="complex64", choices=["complex64", "complex128"])
-    ap.add_argument("--engine", default="tc_f16", choices=["auto", "cuda_core", "tc_f16", "tc_bf16"])
+    ap.add_argument("--engine", default="tc_f16", choices=["auto", "cuda_core", "tc_f16", "tc_bf16", "tc_pass"])
     ap.add_argument("--tc-min-k", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' sub-measurements")
     ap.add_argument("--seed", type=int, default=0)
@@ -396,8 +396,18 @@ def main():
     norm_term = [(1.0, ())]
     engine = args.engine
 
+    passes = len(hq.hq_plan_passes(n, blocks)) if engine == "tc_pass" else 0
+
     def step(events=None):
         hq.hq_state_init(state)
+        if engine == "tc_pass":
+            # the pass engine plans over the whole list: one call, bracketed
+            if events is not None:
+                events[0].record(stream)
+            hq.hq_apply_blocks(state, blocks, engine=engine)
+            if events is not None:
+                events[B].record(stream)
+            return hq.hq_expectation(state, norm_term)
         for i, b in enumerate(blocks):
             if events is not None:
                 events[i].record(stream)
@@ -433,6 +443,9 @@ def main():
     # per-class launch durations (CUDA events on the launching stream)
     durs = {}
     for ev in per_step_events:
+        if engine == "tc_pass":  # one bracket per step; averaged over its passes
+            durs.setdefault("k_pass (all passes)", []).extend([ev[0].elapsed_time(ev[B]) / 1e3 / passes] * passes)
+            continue
         for i in range(B):
             durs.setdefault(classes[i], []).append(ev[i].elapsed_time(ev[i + 1]) / 1e3)
     tot = {c: sum(v) for c, v in durs.items()}
@@ -488,7 +501,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if S == 8 else "f64", "data": "synthetic",
             "config": {"workload": desc, "n": n, "gates": G, "fused_blocks": B, "k_max": args.kmax,
                        "state": args.dtype, "engine": engine, "l2": "state (8 GiB+) larger than L2; no flush",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       **({"passes": passes} if engine == "tc_pass" else {})},
             "effective_GBps": eff_gbs, "roofline_frac_effective": eff_gbs / peaks["hbm_gbs"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom, n),
