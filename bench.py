@@ -458,30 +458,55 @@ def main():
                      "GBps": bytes_per_launch / statistics.mean(v) / 1e9, "share": tot[c] / sum(tot.values())}
                  for c, v in durs.items()}
 
-    # end to end through the public API: pinned host state in, norm out
+    # end to end through the public API: pinned host state in, norm out.  Two
+    # state buffers: the next step's input is copied on its own stream while
+    # the current step computes (every step's copy and result read stay inside
+    # the timed region)
     e2e = None
     if not args.no_e2e:
         host_in = torch.zeros(1 << n, dtype=cdt).pin_memory()
         host_in[0] = 1
         out = torch.zeros(1, dtype=torch.float64).pin_memory()
-        for _ in range(1):
-            state.copy_(host_in, non_blocking=True)
-            hq.hq_apply_blocks(state, blocks, engine=engine, tc_min_k=args.tc_min_k)
-            out[0] = hq.hq_expectation(state, norm_term)
+        bufs = [state, torch.empty_like(state)]
+        copy_stream = torch.cuda.Stream()
+
+        def e2e_run(steps, start=None):
+            copied = [None, None]
+            with torch.cuda.stream(copy_stream):
+                if start is not None:
+                    copy_stream.wait_event(start)
+                bufs[0].copy_(host_in, non_blocking=True)
+                copied[0] = torch.cuda.Event()
+                copied[0].record(copy_stream)
+            for s in range(steps):
+                cur = bufs[s % 2]
+                stream.wait_event(copied[s % 2])
+                hq.hq_apply_blocks(cur, blocks, engine=engine, tc_min_k=args.tc_min_k, stream=stream)
+                if s + 1 < steps:
+                    nxt = (s + 1) % 2
+                    # the buffer's previous step ended with a synchronous norm
+                    with torch.cuda.stream(copy_stream):
+                        bufs[nxt].copy_(host_in, non_blocking=True)
+                        copied[nxt] = torch.cuda.Event()
+                        copied[nxt].record(copy_stream)
+                out[0] = hq.hq_expectation(cur, norm_term, stream=stream)
+
+        e2e_run(2)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(e2e_steps):
-            state.copy_(host_in, non_blocking=True)
-            hq.hq_apply_blocks(state, blocks, engine=engine, tc_min_k=args.tc_min_k)
-            out[0] = hq.hq_expectation(state, norm_term)
+        e2e_run(e2e_steps, start=e0)
         e1.record(stream)
         torch.cuda.synchronize()
         et = e0.elapsed_time(e1) / 1e3
         e2e_value, et = whole_job_rate(et, G * e2e_steps, dist, "cuda")
         e2e = {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": (1 << n) * S,
-               "d2h_bytes_per_step": 8, "note": "pinned host state copied in, FP64 norm read back, every step"}
+               "d2h_bytes_per_step": 8,
+               "note": "pinned host state copied in and FP64 norm read back every step; the next step's copy "
+                       "overlaps the current step on a second stream (two state buffers)"}
+        del bufs
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
