@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_rot(const TileGeom g, typename 
 
 struct HamTerm {
     uint64_t xm, zm;
-    double wr, wi;  // coeff * (-i)^#Y
+    double wr, wi;   // coeff * (-i)^#Y
+    float wrf, wif;  // the same in FP32 (complex64 states: no FP64 conversion per amplitude)
 };
 constexpr int kMaxHamTerms = 128;
 struct HamParams {
@@ -145,7 +146,9 @@ __global__ void __launch_bounds__(kAdjThreads) k_ham(const HamParams p, const ty
     const int64_t dim = int64_t(1) << p.n;
     const T2 *sp = phi + int64_t(blockIdx.y) * dim;
     T2 *sl = lam + int64_t(blockIdx.y) * dim;
+    // complex64: compensated FP32 sum per thread (FP64 from the block sum on)
     double acc = 0;
+    R accr = 0, comp = 0;
     for (int64_t x = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; x < dim; x += int64_t(gridDim.x) * blockDim.x) {
         T2 out;
         out.x = 0;
@@ -154,14 +157,27 @@ __global__ void __launch_bounds__(kAdjThreads) k_ham(const HamParams p, const ty
             const T2 a = sp[x ^ int64_t(p.t[t].xm)];
             const R sg = (__popcll(uint64_t(x) & p.t[t].zm) & 1) ? R(-1) : R(1);
             T2 w;
-            w.x = sg * R(p.t[t].wr);
-            w.y = sg * R(p.t[t].wi);
+            if constexpr (sizeof(R) == 4) {
+                w.x = sg * p.t[t].wrf;
+                w.y = sg * p.t[t].wif;
+            } else {
+                w.x = sg * p.t[t].wr;
+                w.y = sg * p.t[t].wi;
+            }
             cmac(out, w, a);
         }
         sl[x] = out;
         const T2 a = sp[x];
-        acc += double(a.x * out.x + a.y * out.y);
+        const R v = a.x * out.x + a.y * out.y;
+        if constexpr (sizeof(R) == 4) {
+            const R y = v - comp, s2 = accr + y;
+            comp = (s2 - accr) - y;
+            accr = s2;
+        } else {
+            acc += v;
+        }
     }
+    if constexpr (sizeof(R) == 4) acc = double(accr) - double(comp);
     const double s = block_sum(acc);
     if (threadIdx.x == 0) partials[int64_t(blockIdx.y) * gridDim.x + blockIdx.x] = s;
 }
@@ -344,7 +360,8 @@ extern "C" hq_status hq_adjoint_grad(int n, hq_dtype dt, const hq_op *ops, int G
             else { xm |= bit; zm |= bit; ++ny; }
         }
         static const double pr[4] = {1, 0, -1, 0}, pi[4] = {0, -1, 0, 1};
-        hp.t[t] = {xm, zm, H[t].coeff * pr[ny & 3], H[t].coeff * pi[ny & 3]};
+        hp.t[t] = {xm, zm, H[t].coeff * pr[ny & 3], H[t].coeff * pi[ny & 3], float(H[t].coeff * pr[ny & 3]),
+                   float(H[t].coeff * pi[ny & 3])};
     }
     void *lam = static_cast<char *>(phi) + state_bytes;
     double *epart = part + size_t(G) * batch * nbx;

@@ -47,15 +47,17 @@ __device__ __forceinline__ void rot2(int axis, double2 cs, bool rev, T2 (&m)[4])
     else { m[0].y = -s; m[3].y = s; }
 }
 
-// Im( conj(l0) (P a)_0 + conj(l1) (P a)_1 ) for the single-qubit Pauli P
+// Im( conj(l0) (P a)_0 + conj(l1) (P a)_1 ) for the single-qubit Pauli P, in
+// the state's precision (a thread sums a few pairs per tile in it; the warp
+// total joins the FP64 accumulator once)
 template <typename T2>
-__device__ __forceinline__ double pauli_im2(int axis, const T2 a0, const T2 a1, const T2 l0, const T2 l1)
+__device__ __forceinline__ auto pauli_im2(int axis, const T2 a0, const T2 a1, const T2 l0, const T2 l1)
 {
     T2 p0, p1;
     if (axis == 'X') { p0 = a1; p1 = a0; }
     else if (axis == 'Y') { p0.x = a1.y; p0.y = -a1.x; p1.x = -a0.y; p1.y = a0.x; }  // -i a1, i a0
     else { p0 = a0; p1.x = -a1.x; p1.y = -a1.y; }
-    return double(l0.x * p0.y - l0.y * p0.x) + double(l1.x * p1.y - l1.y * p1.x);
+    return (l0.x * p0.y - l0.y * p0.x) + (l1.x * p1.y - l1.y * p1.x);
 }
 
 template <typename T2>
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
                             m[r * 2 + c] = cvt2<T2>(REV ? conj2(op.m[c * 2 + r]) : op.m[r * 2 + c]);
                 }
                 const int tp0 = op.tpos[0];
-                double g = 0.0;
+                R g = 0;
                 for (int grp = threadIdx.x; grp < TS / 2; grp += blockDim.x) {
                     const int i0 = ((grp >> tp0) << (tp0 + 1)) | (grp & ((1 << tp0) - 1));
                     const int a = swz<R>(i0), bb = swz<R>(i0 | (1 << tp0));
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
                 }
                 if (REV && op.kind == 3) {
                     for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
-                    if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[op.slot], g);
+                    if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[op.slot], double(g));
                 }
             }
             __syncthreads();
