@@ -20,6 +20,11 @@ struct AOp {
     int row;       // rotation: index among the circuit's rotations (partial-sum row)
     int slot;      // rotation: accumulator slot within the pass
     double2 m[16]; // fixed gates: 2^k x 2^k matrix, row-major
+    // sweep: ops [sw0, sw0 + swn) of the pass share one pass over the tile;
+    // swt = the tile position whose amplitude pairs it visits (kind 1: the
+    // op's own quad sweep)
+    int sw0, swn, swt;
+    int swc;  // the sweep's context position (-1: none)
 };
 
 struct APass {

@@ -27,6 +27,7 @@
 namespace hq {
 
 constexpr int kApThreads = 256;
+constexpr int kSweepOps = 4;  // ops sharing one pass over the tile
 
 __device__ __forceinline__ double2 conj2(double2 a) { return make_double2(a.x, -a.y); }
 
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
     T2 *tp = reinterpret_cast<T2 *>(smem_raw);
     T2 *tl = tp + TS;
     __shared__ double gacc[kApMaxRot];
+    __shared__ __align__(16) double2 sweep_mat[kSweepOps * 2 * 4];  // one sweep's 2x2 matrices (T2)
     const int b = blockIdx.y;
     if (REV)
         for (int j = threadIdx.x; j < ps.nrot; j += blockDim.x) gacc[j] = 0.0;
@@ -112,9 +114,12 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
             if (REV) tl[swz<R>(i)] = slam[o];
         }
         __syncthreads();
-        for (int q = 0; q < ps.no; ++q) {
-            const AOp &op = ops[ps.o0 + (REV ? ps.no - 1 - q : q)];
-            if (op.kind == 1) {
+        // sweeps in circuit order (reverse: last sweep first, its ops backwards)
+        for (int q = 0; q < ps.no;) {
+            const AOp &last = ops[ps.o0 + (REV ? ps.no - 1 - q : q)];
+            const int f = last.sw0, len = last.swn;
+            if (last.kind == 1) {
+                const AOp &op = last;
                 // dense two-qubit gate: M (forward) or M^+ (reverse)
                 T2 m[16];
 #pragma unroll
@@ -147,8 +152,9 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
                         for (int r = 0; r < 4; ++r) tt[idx[r]] = y[r];
                     }
                 }
-            } else if (op.kind == 2) {
-                // diagonal gate (k = 1 or 2): elementwise
+            } else if (sizeof(R) == 8 && len == 1 && last.kind == 2) {
+                // complex128, one diagonal gate (k = 1 or 2): elementwise
+                const AOp &op = last;
                 const int D = 1 << op.k;
                 T2 d[4];
                 for (int r = 0; r < D; ++r) d[r] = cvt2<T2>(REV ? conj2(op.m[r * D + r]) : op.m[r * D + r]);
@@ -159,8 +165,12 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
                     tp[si] = cmul(d[r], tp[si]);
                     if (REV) tl[si] = cmul(d[r], tl[si]);
                 }
-            } else {
-                // one-qubit gate: dense matrix (kind 0) or rotation (kind 3)
+            } else if (sizeof(R) == 8 && len == 1) {
+                // complex128, one one-qubit gate: dense matrix (kind 0) or
+                // rotation (kind 3), its matrix in registers (the shared table
+                // below would add 64 bytes of loads per pair to an FP64-bound
+                // loop)
+                const AOp &op = last;
                 T2 m[4];
                 if (op.kind == 3) {
                     rot2<T2>(op.axis, scs[op.param], REV, m);
@@ -168,8 +178,8 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
 #pragma unroll
                     for (int r = 0; r < 2; ++r)
 #pragma unroll
-                        for (int c = 0; c < 2; ++c)
-                            m[r * 2 + c] = cvt2<T2>(REV ? conj2(op.m[c * 2 + r]) : op.m[r * 2 + c]);
+                        for (int cc = 0; cc < 2; ++cc)
+                            m[r * 2 + cc] = cvt2<T2>(REV ? conj2(op.m[cc * 2 + r]) : op.m[r * 2 + cc]);
                 }
                 const int tp0 = op.tpos[0];
                 R g = 0;
@@ -192,8 +202,103 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
                     for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
                     if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[op.slot], double(g));
                 }
+            } else {
+                // pair sweep on tile position t: every op acts on the pair
+                // (x_i0, x_i1) as a 2x2 matrix chosen by the context bit c of
+                // i0 (diagonal ops on another position); the sweep's matrices
+                // are built once into shared memory, then each pair is loaded
+                // once and carried through the ops in order (reverse: adjoints
+                // backwards, each rotation's Im<lambda|P phi> taken just before
+                // its R^+)
+                const int t = last.swt, c = last.swc;
+                T2 *swm = reinterpret_cast<T2 *>(sweep_mat);  // [op][ctx][4]
+                if (threadIdx.x < len) {
+                    const int j = threadIdx.x;
+                    const AOp &o = ops[ps.o0 + f + (REV ? len - 1 - j : j)];
+                    T2 mm[4];
+                    for (int cx = 0; cx < 2; ++cx) {
+                        if (o.kind == 3) {
+                            rot2<T2>(o.axis, scs[o.param], REV, mm);
+                        } else if (o.kind == 0) {
+                            for (int r = 0; r < 2; ++r)
+                                for (int cc = 0; cc < 2; ++cc)
+                                    mm[r * 2 + cc] = cvt2<T2>(REV ? conj2(o.m[cc * 2 + r]) : o.m[r * 2 + cc]);
+                        } else {
+                            const int D = 1 << o.k;
+                            auto dg = [&](int r) { return cvt2<T2>(REV ? conj2(o.m[r * D + r]) : o.m[r * D + r]); };
+                            T2 d0, d1;
+                            if (o.k == 1) {
+                                if (o.tpos[0] == t) { d0 = dg(0); d1 = dg(1); }
+                                else { d0 = dg(cx); d1 = d0; }
+                            } else if (o.tpos[0] == t) {
+                                d0 = dg(cx); d1 = dg(2 + cx);
+                            } else {
+                                d0 = dg(2 * cx); d1 = dg(2 * cx + 1);
+                            }
+                            mm[0] = d0; mm[3] = d1;
+                            mm[1].x = 0; mm[1].y = 0; mm[2].x = 0; mm[2].y = 0;
+                        }
+                        for (int r = 0; r < 4; ++r) swm[(j * 2 + cx) * 4 + r] = mm[r];
+                    }
+                }
+                int ax[kSweepOps];
+                unsigned rotmask = 0;
+#pragma unroll
+                for (int j = 0; j < kSweepOps; ++j) {
+                    ax[j] = 0;
+                    if (j < len) {
+                        const AOp &o = ops[ps.o0 + f + (REV ? len - 1 - j : j)];
+                        if (o.kind == 3) {
+                            rotmask |= 1u << j;
+                            ax[j] = o.axis;
+                        }
+                    }
+                }
+                __syncthreads();
+                R g[kSweepOps];
+#pragma unroll
+                for (int j = 0; j < kSweepOps; ++j) g[j] = 0;
+                for (int grp = threadIdx.x; grp < TS / 2; grp += blockDim.x) {
+                    const int i0 = ((grp >> t) << (t + 1)) | (grp & ((1 << t) - 1));
+                    const int cx = c >= 0 ? (i0 >> c) & 1 : 0;
+                    const int a = swz<R>(i0), bb = swz<R>(i0 | (1 << t));
+                    T2 x0 = tp[a], x1 = tp[bb], l0, l1;
+                    if (REV) {
+                        l0 = tl[a];
+                        l1 = tl[bb];
+                    }
+#pragma unroll
+                    for (int j = 0; j < kSweepOps; ++j) {
+                        if (j >= len) break;
+                        T2 mm[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) mm[r] = swm[(j * 2 + cx) * 4 + r];
+                        if (REV && ((rotmask >> j) & 1)) g[j] += pauli_im2(ax[j], x0, x1, l0, l1);
+                        mul2(mm, x0, x1);
+                        if (REV) mul2(mm, l0, l1);
+                    }
+                    tp[a] = x0;
+                    tp[bb] = x1;
+                    if (REV) {
+                        tl[a] = l0;
+                        tl[bb] = l1;
+                    }
+                }
+                if (REV) {
+#pragma unroll
+                    for (int j = 0; j < kSweepOps; ++j) {
+                        if (!((rotmask >> j) & 1)) continue;
+                        R v = g[j];
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+                        if ((threadIdx.x & 31) == 0) {
+                            const AOp &op = ops[ps.o0 + f + (REV ? len - 1 - j : j)];
+                            atomicAdd(&gacc[op.slot], double(v));
+                        }
+                    }
+                }
             }
             __syncthreads();
+            q += len;
         }
         for (int i = threadIdx.x; i < TS; i += blockDim.x) {
             const int64_t o = off(i);
@@ -224,6 +329,74 @@ __global__ void k_half_angles(const double *__restrict__ theta, int64_t count, d
 // ----------------------------------------------------------------------------
 // host side
 // ----------------------------------------------------------------------------
+// Groups a pass's ops into sweeps: a sweep visits the amplitude pairs of one
+// tile position t once and applies, in circuit order, up to kSweepOps ops that
+// act on t alone (dense one-qubit gates, rotations) or are diagonal (any
+// positions: elementwise).  An op joins a sweep only if it shares no position
+// with an op skipped before it, so the reordering moves ops past commuting
+// ops only (which leaves every adjoint gradient unchanged).  Dense two-qubit
+// gates keep a sweep of their own.
+static void build_sweeps(std::vector<AOp> &v, int cap)
+{
+    auto posmask = [](const AOp &o) {
+        uint64_t m = 0;
+        for (int j = 0; j < o.k; ++j) m |= uint64_t(1) << o.tpos[j];
+        return m;
+    };
+    std::vector<AOp> out;
+    out.reserve(v.size());
+    std::vector<bool> used(v.size(), false);
+    for (size_t h = 0; h < v.size(); ++h) {
+        if (used[h]) continue;
+        std::vector<size_t> sw{h};
+        used[h] = true;
+        int t = -1;
+        uint64_t diagpos = 0;  // positions of the sweep's diagonal ops
+        // a sweep's ops act on the pair (x_i0, x_i1) of position t as 2x2
+        // matrices chosen by at most one other bit (the context): diagonal
+        // ops may touch t and one more position
+        auto ctx_ok = [&](int tt, uint64_t dp) { return __builtin_popcountll(tt >= 0 ? dp & ~(uint64_t(1) << tt) : dp) <= (tt >= 0 ? 1 : 2); };
+        if (v[h].kind != 1) {
+            if (v[h].kind == 0 || v[h].kind == 3) t = v[h].tpos[0];
+            else diagpos = posmask(v[h]);
+            uint64_t blocked = 0;
+            for (size_t j = h + 1; j < v.size() && int(sw.size()) < cap; ++j) {
+                if (used[j]) continue;
+                const AOp &o = v[j];
+                const bool one = o.kind == 0 || o.kind == 3;
+                bool fits = o.kind == 2 || (one && (t < 0 || o.tpos[0] == t));
+                if (fits) {
+                    const int t2 = (one && t < 0) ? o.tpos[0] : t;
+                    const uint64_t dp2 = diagpos | (o.kind == 2 ? posmask(o) : 0);
+                    // with no target yet, the pair position is one of the diagonal positions
+                    fits = t2 >= 0 ? ctx_ok(t2, dp2) : __builtin_popcountll(dp2) <= 2;
+                }
+                if (fits && !(posmask(o) & blocked)) {
+                    if (one && t < 0) t = o.tpos[0];
+                    if (o.kind == 2) diagpos |= posmask(o);
+                    sw.push_back(j);
+                    used[j] = true;
+                } else {
+                    blocked |= posmask(o);
+                }
+            }
+        }
+        if (t < 0) t = diagpos ? __builtin_ctzll(diagpos) : 0;  // diagonal-only sweep
+        const uint64_t rest = diagpos & ~(uint64_t(1) << t);
+        const int ctx = rest ? __builtin_ctzll(rest) : -1;
+        const int first = int(out.size());
+        for (size_t idx : sw) {
+            AOp a = v[idx];
+            a.sw0 = first;
+            a.swn = int(sw.size());
+            a.swt = t;
+            a.swc = ctx;
+            out.push_back(a);
+        }
+    }
+    v.swap(out);
+}
+
 bool adj_plan(int n, hq_dtype dt, const hq_op *ops, int G, AdjPlan &plan)
 {
     for (int g = 0; g < G; ++g)
@@ -287,6 +460,7 @@ bool adj_plan(int n, hq_dtype dt, const hq_op *ops, int G, AdjPlan &plan)
                 if (ap.hb[j] == b) return R + j;
             return -1;
         };
+        std::vector<AOp> pv;
         for (int g : p.ops) {
             const hq_op &o = ops[g];
             AOp a;
@@ -306,8 +480,12 @@ bool adj_plan(int n, hq_dtype dt, const hq_op *ops, int G, AdjPlan &plan)
                 const int D = 1 << o.k;
                 for (int e = 0; e < D * D; ++e) a.m[e] = make_double2(o.matrix[2 * e], o.matrix[2 * e + 1]);
             }
-            plan.op.push_back(a);
+            pv.push_back(a);
         }
+        // complex128 is bound by FP64 arithmetic, which merging does not
+        // reduce: one op per sweep there
+        build_sweeps(pv, dt == HQ_C64 ? kSweepOps : 1);
+        plan.op.insert(plan.op.end(), pv.begin(), pv.end());
         plan.pass.push_back(ap);
     }
     return true;
