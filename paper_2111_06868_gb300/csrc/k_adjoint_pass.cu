@@ -212,35 +212,60 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
                 // its R^+)
                 const int t = last.swt, c = last.swc;
                 T2 *swm = reinterpret_cast<T2 *>(sweep_mat);  // [op][ctx][4]
-                if (threadIdx.x < len) {
-                    const int j = threadIdx.x;
+                // the 2x2 matrix of op j of the sweep (in application order) for context cx
+                auto op_matrix = [&](int j, int cx, T2 (&mm)[4]) {
                     const AOp &o = ops[ps.o0 + f + (REV ? len - 1 - j : j)];
-                    T2 mm[4];
-                    for (int cx = 0; cx < 2; ++cx) {
-                        if (o.kind == 3) {
-                            rot2<T2>(o.axis, scs[o.param], REV, mm);
-                        } else if (o.kind == 0) {
-                            for (int r = 0; r < 2; ++r)
-                                for (int cc = 0; cc < 2; ++cc)
-                                    mm[r * 2 + cc] = cvt2<T2>(REV ? conj2(o.m[cc * 2 + r]) : o.m[r * 2 + cc]);
+                    if (o.kind == 3) {
+                        rot2<T2>(o.axis, scs[o.param], REV, mm);
+                    } else if (o.kind == 0) {
+                        for (int r = 0; r < 2; ++r)
+                            for (int cc = 0; cc < 2; ++cc)
+                                mm[r * 2 + cc] = cvt2<T2>(REV ? conj2(o.m[cc * 2 + r]) : o.m[r * 2 + cc]);
+                    } else {
+                        const int D = 1 << o.k;
+                        auto dg = [&](int r) { return cvt2<T2>(REV ? conj2(o.m[r * D + r]) : o.m[r * D + r]); };
+                        T2 d0, d1;
+                        if (o.k == 1) {
+                            if (o.tpos[0] == t) { d0 = dg(0); d1 = dg(1); }
+                            else { d0 = dg(cx); d1 = d0; }
+                        } else if (o.tpos[0] == t) {
+                            d0 = dg(cx); d1 = dg(2 + cx);
                         } else {
-                            const int D = 1 << o.k;
-                            auto dg = [&](int r) { return cvt2<T2>(REV ? conj2(o.m[r * D + r]) : o.m[r * D + r]); };
-                            T2 d0, d1;
-                            if (o.k == 1) {
-                                if (o.tpos[0] == t) { d0 = dg(0); d1 = dg(1); }
-                                else { d0 = dg(cx); d1 = d0; }
-                            } else if (o.tpos[0] == t) {
-                                d0 = dg(cx); d1 = dg(2 + cx);
-                            } else {
-                                d0 = dg(2 * cx); d1 = dg(2 * cx + 1);
-                            }
-                            mm[0] = d0; mm[3] = d1;
-                            mm[1].x = 0; mm[1].y = 0; mm[2].x = 0; mm[2].y = 0;
+                            d0 = dg(2 * cx); d1 = dg(2 * cx + 1);
                         }
-                        for (int r = 0; r < 4; ++r) swm[(j * 2 + cx) * 4 + r] = mm[r];
+                        mm[0] = d0; mm[3] = d1;
+                        mm[1].x = 0; mm[1].y = 0; mm[2].x = 0; mm[2].y = 0;
                     }
+                };
+                if (REV) {
+                    if (threadIdx.x < len) {
+                        T2 mm[4];
+                        for (int cx = 0; cx < 2; ++cx) {
+                            op_matrix(threadIdx.x, cx, mm);
+                            for (int r = 0; r < 4; ++r) swm[(threadIdx.x * 2 + cx) * 4 + r] = mm[r];
+                        }
+                    }
+                } else if (threadIdx.x < 2) {
+                    // forward: no intermediate states are needed, so the sweep
+                    // is one matrix per context, the product of its ops
+                    const int cx = threadIdx.x;
+                    T2 pm[4], mm[4];
+                    op_matrix(0, cx, pm);
+                    for (int j = 1; j < len; ++j) {
+                        op_matrix(j, cx, mm);
+                        T2 q[4];
+                        for (int r = 0; r < 2; ++r)
+                            for (int cc = 0; cc < 2; ++cc) {
+                                q[r * 2 + cc].x = 0;
+                                q[r * 2 + cc].y = 0;
+                                cmac(q[r * 2 + cc], mm[r * 2], pm[cc]);
+                                cmac(q[r * 2 + cc], mm[r * 2 + 1], pm[2 + cc]);
+                            }
+                        for (int r = 0; r < 4; ++r) pm[r] = q[r];
+                    }
+                    for (int r = 0; r < 4; ++r) swm[cx * 4 + r] = pm[r];
                 }
+                const int nsw = REV ? len : 1;  // matrices applied per pair
                 int ax[kSweepOps];
                 unsigned rotmask = 0;
 #pragma unroll
@@ -269,7 +294,7 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
                     }
 #pragma unroll
                     for (int j = 0; j < kSweepOps; ++j) {
-                        if (j >= len) break;
+                        if (j >= nsw) break;
                         T2 mm[4];
 #pragma unroll
                         for (int r = 0; r < 4; ++r) mm[r] = swm[(j * 2 + cx) * 4 + r];
