@@ -61,6 +61,19 @@ __device__ __forceinline__ auto pauli_im2(int axis, const T2 a0, const T2 a1, co
     return (l0.x * p0.y - l0.y * p0.x) + (l1.x * p1.y - l1.y * p1.x);
 }
 
+// (x0, x1) <- M (x0, x1) for a real M (imaginary parts of m[] are zero)
+template <typename T2>
+__device__ __forceinline__ void mul2_real(const T2 (&m)[4], T2 &x0, T2 &x1)
+{
+    T2 y0, y1;
+    y0.x = m[0].x * x0.x + m[1].x * x1.x;
+    y0.y = m[0].x * x0.y + m[1].x * x1.y;
+    y1.x = m[2].x * x0.x + m[3].x * x1.x;
+    y1.y = m[2].x * x0.y + m[3].x * x1.y;
+    x0 = y0;
+    x1 = y1;
+}
+
 template <typename T2>
 __device__ __forceinline__ void mul2(const T2 (&m)[4], T2 &x0, T2 &x1)
 {
@@ -267,7 +280,7 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
                 }
                 const int nsw = REV ? len : 1;  // matrices applied per pair
                 int ax[kSweepOps];
-                unsigned rotmask = 0;
+                unsigned rotmask = 0, diagmask = 0, realmask = 0;
 #pragma unroll
                 for (int j = 0; j < kSweepOps; ++j) {
                     ax[j] = 0;
@@ -280,6 +293,21 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
                     }
                 }
                 __syncthreads();
+                // matrix structure of each applied matrix (exact zeros; uniform
+                // over the CTA): diagonal, or all-real, else general
+#pragma unroll
+                for (int j = 0; j < kSweepOps; ++j) {
+                    if (j >= nsw) break;
+                    bool dg = true, re = true;
+                    for (int cx = 0; cx < 2; ++cx)
+                        for (int r = 0; r < 4; ++r) {
+                            const T2 v = swm[(j * 2 + cx) * 4 + r];
+                            if ((r == 1 || r == 2) && (v.x != 0 || v.y != 0)) dg = false;
+                            if (v.y != 0) re = false;
+                        }
+                    if (dg) diagmask |= 1u << j;
+                    else if (re) realmask |= 1u << j;
+                }
                 R g[kSweepOps];
 #pragma unroll
                 for (int j = 0; j < kSweepOps; ++j) g[j] = 0;
@@ -299,8 +327,20 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
 #pragma unroll
                         for (int r = 0; r < 4; ++r) mm[r] = swm[(j * 2 + cx) * 4 + r];
                         if (REV && ((rotmask >> j) & 1)) g[j] += pauli_im2(ax[j], x0, x1, l0, l1);
-                        mul2(mm, x0, x1);
-                        if (REV) mul2(mm, l0, l1);
+                        if ((diagmask >> j) & 1) {
+                            x0 = cmul(mm[0], x0);
+                            x1 = cmul(mm[3], x1);
+                            if (REV) {
+                                l0 = cmul(mm[0], l0);
+                                l1 = cmul(mm[3], l1);
+                            }
+                        } else if ((realmask >> j) & 1) {
+                            mul2_real(mm, x0, x1);
+                            if (REV) mul2_real(mm, l0, l1);
+                        } else {
+                            mul2(mm, x0, x1);
+                            if (REV) mul2(mm, l0, l1);
+                        }
                     }
                     tp[a] = x0;
                     tp[bb] = x1;
