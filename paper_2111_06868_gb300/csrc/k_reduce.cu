@@ -212,15 +212,137 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_final(const double *__re
     if (threadIdx.x == 0) out[0] = total;
 }
 
-// Builds the xmask groups (host).  Returns HQ_ERR_ARG on a bad term.
-static hq_status build_groups(int n, const hq_pauli_term *terms, int T, std::vector<ExpGroup> &groups,
-                              std::vector<ExpTerm> &flat)
+// ----------------------------------------------------------------------------
+// Tiled evaluation: every term whose X mask lies in a tile of 2^L amplitudes
+// is evaluated from that tile in shared memory, so one read of the state
+// serves all of them.  Pass 0 tiles the L lowest bits (all diagonal terms and
+// the low X masks); further passes take 7 low bits plus up to 6 higher bits
+// (runs of 1 KB) for the terms whose X masks reach higher.
+//   <psi|P|psi> = sum_x conj(psi_x) w (-1)^popc(x & zm) psi_{x ^ xm}
+// with x = tile_base + flat(i): the parity splits into the tile-local part
+// popc(i & zl) and the tile base's part, folded into the weight once per tile.
+// ----------------------------------------------------------------------------
+constexpr int kTileTerms = 96;
+struct TileTerm {
+    int xl, zl;      // tile-local X and Z masks
+    uint64_t zh;     // Z bits outside the tile
+    double wr, wi;   // coeff * (-i)^#Y
+};
+struct TileExpParams {
+    TileGeom g;
+    int nt, nd;  // terms; the first nd are diagonal (X mask 0)
+    TileTerm t[kTileTerms];
+};
+constexpr int kTileElems = 4;  // elements a thread holds while it walks the terms
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_expect_tile(const TileExpParams p,
+                                                             const typename C2<R>::type *__restrict__ psi,
+                                                             double *__restrict__ partials)
 {
-    struct Tm {
-        uint64_t xm, zm;
-        double wr, wi;
-    };
-    std::vector<Tm> tms;
+    using V = typename C2<R>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *tile = reinterpret_cast<V *>(smem_raw);
+    __shared__ int sxl[kTileTerms], szl[kTileTerms];
+    __shared__ V sw[kTileTerms];  // weight with the tile base's sign
+    const TileGeom &g = p.g;
+    const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
+    double acc = 0;
+    R accr = 0, comp = 0;
+    for (int k = threadIdx.x; k < p.nt; k += blockDim.x) {
+        sxl[k] = p.t[k].xl;
+        szl[k] = p.t[k].zl;
+    }
+    for (int64_t tl = blockIdx.x; tl < g.total_tiles; tl += gridDim.x) {
+        const int64_t base = tile_base(g, tl);
+        const V *src = psi + base;
+        for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
+            const int64_t o = g.runoff[i >> g.c] + (i & cmask);
+            if constexpr (sizeof(R) == 4) {
+                const float4 w = *reinterpret_cast<const float4 *>(src + o);
+                tile[i] = make_float2(w.x, w.y);
+                tile[i + 1] = make_float2(w.z, w.w);
+            } else {
+                tile[i] = src[o];
+                tile[i + 1] = src[o + 1];
+            }
+        }
+        for (int k = threadIdx.x; k < p.nt; k += blockDim.x) {
+            const R sg = (__popcll(uint64_t(base) & p.t[k].zh) & 1) ? R(-1) : R(1);
+            sw[k].x = sg * R(p.t[k].wr);
+            sw[k].y = sg * R(p.t[k].wi);
+        }
+        __syncthreads();
+        R part = 0;
+        for (int i0 = threadIdx.x; i0 < TS; i0 += blockDim.x * kTileElems) {
+            V a[kTileElems];
+            int ii[kTileElems];
+#pragma unroll
+            for (int u = 0; u < kTileElems; ++u) {
+                ii[u] = i0 + u * blockDim.x;
+                a[u] = tile[ii[u] < TS ? ii[u] : 0];
+            }
+            // diagonal terms: |a|^2 times the signed sum of their real weights
+            R f[kTileElems];
+#pragma unroll
+            for (int u = 0; u < kTileElems; ++u) f[u] = 0;
+            for (int k = 0; k < p.nd; ++k) {
+                const int zl = szl[k];
+                const R w = sw[k].x;
+#pragma unroll
+                for (int u = 0; u < kTileElems; ++u) f[u] += (__popc(ii[u] & zl) & 1) ? -w : w;
+            }
+#pragma unroll
+            for (int u = 0; u < kTileElems; ++u)
+                if (ii[u] < TS) part += (a[u].x * a[u].x + a[u].y * a[u].y) * f[u];
+            for (int k = p.nd; k < p.nt; ++k) {
+                const int xl = sxl[k], zl = szl[k];
+                const V w = sw[k];
+                if (zl == 0 && w.y == 0) {
+                    // real-weighted X string: w Re(conj(a) b)
+                    R d = 0;
+#pragma unroll
+                    for (int u = 0; u < kTileElems; ++u) {
+                        if (ii[u] >= TS) continue;
+                        const V b = tile[ii[u] ^ xl];
+                        d += a[u].x * b.x + a[u].y * b.y;
+                    }
+                    part += w.x * d;
+                    continue;
+                }
+#pragma unroll
+                for (int u = 0; u < kTileElems; ++u) {
+                    if (ii[u] >= TS) continue;
+                    const V b = tile[ii[u] ^ xl];
+                    // Re( conj(a) w b ) with the tile-local parity of x
+                    const R zr = a[u].x * b.x + a[u].y * b.y, zi = a[u].x * b.y - a[u].y * b.x;
+                    const R v = zr * w.x - zi * w.y;
+                    part += (__popc(ii[u] & zl) & 1) ? -v : v;
+                }
+            }
+        }
+        if constexpr (sizeof(R) == 4) {
+            const R y = part - comp, s2 = accr + y;
+            comp = (s2 - accr) - y;
+            accr = s2;
+        } else {
+            acc += part;
+        }
+        __syncthreads();
+    }
+    if constexpr (sizeof(R) == 4) acc = double(accr) - double(comp);
+    const double s = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// Builds the xmask groups (host).  Returns HQ_ERR_ARG on a bad term.
+struct Tm {
+    uint64_t xm, zm;
+    double wr, wi;  // coeff * (-i)^#Y
+};
+
+static hq_status parse_terms(int n, const hq_pauli_term *terms, int T, std::vector<Tm> &tms)
+{
     for (int t = 0; t < T; ++t) {
         uint64_t xm = 0, zm = 0;
         int ny = 0;
@@ -236,6 +358,15 @@ static hq_status build_groups(int n, const hq_pauli_term *terms, int T, std::vec
         static const double pr[4] = {1, 0, -1, 0}, pi[4] = {0, -1, 0, 1};
         tms.push_back({xm, zm, terms[t].coeff * pr[ny & 3], terms[t].coeff * pi[ny & 3]});
     }
+    return HQ_OK;
+}
+
+static hq_status build_groups(int n, const hq_pauli_term *terms, int T, std::vector<ExpGroup> &groups,
+                              std::vector<ExpTerm> &flat)
+{
+    std::vector<Tm> tms;
+    hq_status st = parse_terms(n, terms, T, tms);
+    if (st != HQ_OK) return st;
     std::stable_sort(tms.begin(), tms.end(), [](const Tm &a, const Tm &b) { return a.xm < b.xm; });
     for (size_t i = 0; i < tms.size();) {
         size_t j = i;
@@ -257,9 +388,135 @@ static hq_status build_groups(int n, const hq_pauli_term *terms, int T, std::vec
     return HQ_OK;
 }
 
+// Tile passes for the tiled evaluation: terms whose X mask has no bit above
+// the first tile go to pass 0; the others are packed greedily into passes of 7
+// low bits plus at most h higher bits.  Terms needing more than h higher bits
+// are left out (evaluated by the per-group kernel).
+struct TilePass {
+    std::vector<int> high;   // flat bits of the tile above the low run
+    std::vector<Tm> terms;
+};
+
+static void plan_tile_passes(int n, int L, const std::vector<Tm> &tms, std::vector<TilePass> &passes,
+                             std::vector<Tm> &rest)
+{
+    const int low = 7, h = L - low;
+    passes.assign(1, TilePass());
+    uint64_t cur = 0;
+    int ci = -1;
+    for (const Tm &m : tms) {
+        if ((m.xm >> L) == 0) {
+            passes[0].terms.push_back(m);
+            continue;
+        }
+        const uint64_t need = m.xm & ~((uint64_t(1) << low) - 1);
+        if (__builtin_popcountll(need) > h) {
+            rest.push_back(m);
+            continue;
+        }
+        if (ci < 0 || __builtin_popcountll(cur | need) > h || int(passes[ci].terms.size()) >= kTileTerms) {
+            passes.emplace_back();
+            ci = int(passes.size()) - 1;
+            cur = 0;
+        }
+        cur |= need;
+        passes[ci].terms.push_back(m);
+        passes[ci].high.clear();
+        for (int b = low; b < n; ++b)
+            if ((cur >> b) & 1) passes[ci].high.push_back(b);
+    }
+    if (passes[0].terms.empty()) passes.erase(passes.begin());
+}
+
+// sum over the tile passes, into scratch[0]; scratch holds >= passes * grid + 1 doubles
+static hq_status launch_tiled(const void *state, int n, hq_dtype dt, const std::vector<TilePass> &passes, int grid,
+                              double *scratch, cudaStream_t s)
+{
+    const int L = dt == HQ_C64 ? 13 : 12;
+    const size_t smem = (dt == HQ_C64 ? 8 : 16) * (size_t(1) << L);
+    for (size_t pi = 0; pi < passes.size(); ++pi) {
+        const TilePass &tp = passes[pi];
+        TileExpParams p;
+        std::memset(&p, 0, sizeof(p));
+        const int k = int(tp.high.size());
+        int q[64];
+        for (int j = 0; j < k; ++j) q[j] = n - 1 - tp.high[j];
+        make_geom(p.g, n, k, q, pi == 0 && k == 0 ? L : 7 + k, 1);
+        // tile-local position of every tile bit: [0, c) then the high bits
+        int pos[64];
+        for (int b = 0; b < 64; ++b) pos[b] = -1;
+        for (int b = 0; b < p.g.c; ++b) pos[b] = b;
+        for (int j = 0; j < p.g.n_hi; ++j) pos[p.g.hi_bits[j]] = p.g.c + j;
+        uint64_t tmask = 0;
+        for (int b = 0; b < n; ++b)
+            if (pos[b] >= 0) tmask |= uint64_t(1) << b;
+        // diagonal terms first
+        std::vector<Tm> ord;
+        for (const Tm &m : tp.terms)
+            if (!m.xm) ord.push_back(m);
+        p.nd = int(ord.size());
+        for (const Tm &m : tp.terms)
+            if (m.xm) ord.push_back(m);
+        p.nt = int(ord.size());
+        for (int j = 0; j < p.nt; ++j) {
+            const Tm &m = ord[j];
+            TileTerm &tt = p.t[j];
+            for (int b = 0; b < n; ++b) {
+                if ((m.xm >> b) & 1) tt.xl |= 1 << pos[b];
+                if (((m.zm & tmask) >> b) & 1) tt.zl |= 1 << pos[b];
+            }
+            tt.zh = m.zm & ~tmask;
+            tt.wr = m.wr;
+            tt.wi = m.wi;
+        }
+        const int gx = int(std::min<int64_t>(grid, p.g.total_tiles));
+        double *part = scratch + 1 + pi * size_t(grid);
+        if (dt == HQ_C64) {
+            occupancy((const void *)k_expect_tile<float>, kRedThreads, smem);
+            k_expect_tile<float><<<gx, kRedThreads, smem, s>>>(p, (const float2 *)state, part);
+        } else {
+            occupancy((const void *)k_expect_tile<double>, kRedThreads, smem);
+            k_expect_tile<double><<<gx, kRedThreads, smem, s>>>(p, (const double2 *)state, part);
+        }
+        hq_status st = cuda_status("k_expect_tile", cudaGetLastError());
+        if (st != HQ_OK) return st;
+        if (gx < grid) cudaMemsetAsync(part + gx, 0, sizeof(double) * size_t(grid - gx), s);
+    }
+    k_expect_final<<<1, kRedThreads, 0, s>>>(scratch + 1, int(passes.size()), grid, scratch);
+    return cuda_status("k_expect_final", cudaGetLastError());
+}
+
 hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,
                              double *out_host, cudaStream_t s)
 {
+    // several X-mask groups: one read of the state per tile pass instead of one per group
+    if (n >= 13 && T > 0) {
+        std::vector<Tm> tms;
+        hq_status st = parse_terms(n, terms, T, tms);
+        if (st != HQ_OK) return st;
+        std::vector<uint64_t> xms;
+        for (const Tm &m : tms) xms.push_back(m.xm);
+        std::sort(xms.begin(), xms.end());
+        const int ngroups = int(std::unique(xms.begin(), xms.end()) - xms.begin());
+        std::vector<TilePass> passes;
+        std::vector<Tm> rest;
+        plan_tile_passes(n, dt == HQ_C64 ? 13 : 12, tms, passes, rest);
+        if (ngroups >= 2 && rest.empty() && int(passes.size()) < ngroups) {
+            const int grid = 3 * sm_count();
+            double *scratch = nullptr;
+            const size_t nd = 1 + passes.size() * size_t(grid);
+            if (cudaMallocAsync((void **)&scratch, sizeof(double) * nd, s) != cudaSuccess) return HQ_ERR_ALLOC;
+            st = launch_tiled(state, n, dt, passes, grid, scratch, s);
+            double result = 0;
+            if (st == HQ_OK)
+                st = cuda_status("copy result", cudaMemcpyAsync(&result, scratch, sizeof(double), cudaMemcpyDeviceToHost, s));
+            cudaFreeAsync(scratch, s);
+            if (st == HQ_OK) st = cuda_status("sync", cudaStreamSynchronize(s));
+            if (st == HQ_OK) *out_host = result;
+            return st;
+        }
+    }
+
     std::vector<ExpGroup> groups;
     std::vector<ExpTerm> flat;
     hq_status st = build_groups(n, terms, T, groups, flat);

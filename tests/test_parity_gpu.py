@@ -216,6 +216,36 @@ def test_expectation_norm_and_ansatz_hamiltonian(hq, dt):
     assert abs(hq.hq_expectation(st, H) - oracle.expectation(psi, H)) <= tol * 10
 
 
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n,seed", [(13, 1), (17, 2), (20, 3)])
+def test_expectation_tiled_passes(hq, dt, n, seed):
+    """Pauli sums whose X masks reach the high qubits: one read of the state per
+    tile pass (low tile, then 7 low bits + up to 6 high bits), signs from the
+    tile base folded per tile."""
+    rng = C.SplitMix64(seed)
+    psi = random_state(n, 60 + n)
+    H = [(0.5, ((q, "Z"), ((q + 1) % n, "Z"))) for q in range(n)]
+    H += [(rng.uniform() - 0.5, ((q, "X"),)) for q in range(n)]
+    H += [(rng.uniform() - 0.5, ((q, "Y"), ((q + 5) % n, "X"), ((q + 9) % n, "Z"))) for q in range(0, n, 3)]
+    H += [(0.25, ())]
+    want = oracle.expectation(psi, H)
+    got = hq.hq_expectation(to_dev(psi, dt), H)
+    tol = 1e-12 if dt == "c128" else 1e-5 * max(1.0, sum(abs(c) for c, _ in H))
+    assert abs(got - want) <= tol
+
+
+def test_expectation_term_wider_than_a_tile_pass(hq):
+    """A term whose X mask needs more high bits than a tile pass holds sends
+    the sum to the per-group kernel."""
+    n = 18
+    psi = random_state(n, 71)
+    H = [(0.3, tuple((q, "X") for q in range(8))), (0.2, ((17, "Z"),)), (0.1, ((0, "X"),))]
+    for dt in ("c64", "c128"):
+        got = hq.hq_expectation(to_dev(psi, dt), H)
+        tol = 1e-12 if dt == "c128" else 1e-5
+        assert abs(got - oracle.expectation(psi, H)) <= tol
+
+
 def test_expectation_many_groups(hq):
     """More xmask groups and terms than one parameter block holds."""
     n = 12
