@@ -99,17 +99,25 @@ bool is_diagonal(int k, const double *m)
 // ----------------------------------------------------------------------------
 static std::mutex g_occ_mu;
 static std::map<std::pair<int, const void *>, int> g_occ;
+static std::map<std::pair<int, const void *>, size_t> g_smem_limit;  // largest limit set per (device, kernel)
 
-// resident CTAs per SM for `fn` with `threads` threads and `smem` dynamic bytes
+// Resident CTAs per SM for `fn` with `threads` threads and `smem` dynamic
+// bytes; also raises the kernel's dynamic shared-memory limit to cover `smem`
+// (the limit only ever grows, so launches of one kernel with different sizes
+// stay valid).
 int occupancy(const void *fn, int threads, size_t smem)
 {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_occ_mu);
+    size_t &lim = g_smem_limit[std::make_pair(dev, fn)];
+    if (smem > 48 * 1024 && smem > lim) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        lim = smem;
+    }
     auto key = std::make_pair(dev * 1024 + int(smem >> 10), fn);
     auto it = g_occ.find(key);
     if (it != g_occ.end()) return it->second;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess || nb < 1) nb = 1;
     g_occ[key] = nb;
