@@ -154,6 +154,9 @@ def block_class(qs, m, engine, tc_min_k, n=30):
     k = len(qs)
     if not np.any(m[~np.eye(d, dtype=bool)]):
         return f"k_diag_k{k}"
+    nz = np.abs(m) > 4 * np.finfo(np.float64).eps * np.abs(m).max()
+    if k <= 4 and np.all(nz.sum(axis=0) == 1) and np.all(nz.sum(axis=1) == 1):
+        return f"k_mono_k{k}"
     if engine.startswith("tc") and k >= max(tc_min_k, 4) and n >= k + 7:
         return f"k_tc_{engine[3:]}_k{6 if n >= 13 else k}"
     return f"k_gather_k{k}" if k <= 4 else f"k_block_k{k}"

@@ -169,6 +169,8 @@ hq_status launch_init(void *state, int n, hq_dtype dt, const char *tokens, int64
 hq_status launch_gate(void *state, int n, hq_dtype dt, int k, const int *qubits, const double *matrix,
                       int64_t nstates, int engine, cudaStream_t s);
 bool is_diagonal(int k, const double *matrix);
+// exactly one nonzero per row and column; perm[r] = column of row r (may be NULL)
+bool is_monomial(int k, const double *matrix, int *perm);
 
 // expectation (k_reduce.cu)
 hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,

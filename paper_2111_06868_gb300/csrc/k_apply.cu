@@ -14,6 +14,10 @@
 //     linear copy and the strided group access free of bank conflicts.
 //   * k_diag<R, K>: diagonal gates (CZ, RZ, CPHASE and fused diagonal blocks)
 //     need no gather: out[x] = d[r(x)] * in[x], a pure stream.
+//   * k_mono<R, K> (K <= 4): monomial gates, one nonzero per row and column
+//     (X, Y, CNOT, SWAP, iSWAP, Toffoli, fSim(pi/2, phi)): the tile scheme of
+//     k_gather with out_r = d_r * in_{pi(r)} per group, one complex multiply
+//     per amplitude instead of 2^K complex MACs.
 //   * k_block<R, K> (K = 5, 6): the same tile scheme for wide fused blocks on
 //     the CUDA cores (matrix in shared memory, 16 output rows per thread); the
 //     tensor-core engine for these widths is in k_tc.cu.
@@ -83,6 +87,32 @@ void make_geom(TileGeom &g, int n, int k, const int *qubits, int L, int64_t nsta
     g.tiles_per_state = int64_t(1) << (n - L);
     g.total_tiles = g.tiles_per_state * nstates;
     g.state_stride = int64_t(1) << n;
+}
+
+// Monomial (permutation times diagonal): one nonzero per row and per column.
+// perm[r] = the column of row r's nonzero.  Entries below 4 epsilon (FP64) of
+// the largest magnitude count as zero: what they would add to a product is
+// below the rounding of the dense product itself (fSim(pi/2, phi) as built
+// from cos(pi/2) = 6.1e-17 is monomial by this test).
+bool is_monomial(int k, const double *m, int *perm)
+{
+    const int K = 1 << k;
+    double mx = 0;
+    for (int e = 0; e < K * K; ++e) mx = std::max(mx, std::hypot(m[2 * e], m[2 * e + 1]));
+    const double tiny = 4.0 * 2.220446049250313e-16 * mx;
+    int used = 0;
+    for (int r = 0; r < K; ++r) {
+        int col = -1;
+        for (int c = 0; c < K; ++c)
+            if (std::hypot(m[2 * (r * K + c)], m[2 * (r * K + c) + 1]) > tiny) {
+                if (col >= 0) return false;
+                col = c;
+            }
+        if (col < 0 || ((used >> col) & 1)) return false;
+        used |= 1 << col;
+        if (perm) perm[r] = col;
+    }
+    return true;
 }
 
 bool is_diagonal(int k, const double *m)
@@ -217,6 +247,40 @@ __global__ void __launch_bounds__(kThreads) k_gather(const TileGeom g, const Mat
                     for (int rr = 0; rr < NR; ++rr) tile[swz<R>(ibs[it] + g.toff[chunk[it] * NR + rr])] = acc[it][rr];
             __syncthreads();
         }
+        tile_store(g, base, tile);
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// monomial gates, K <= 4
+// ----------------------------------------------------------------------------
+template <typename R, int K> struct MonoParam {
+    typename C2<R>::type d[1 << K];  // nonzero of row r
+    int src[1 << K];                 // tile-local offset of column pi(r) (= g.toff[pi(r)])
+};
+
+template <typename R, int K>
+__global__ void __launch_bounds__(kThreads) k_mono(const TileGeom g, const MonoParam<R, K> m,
+                                                   typename C2<R>::type *__restrict__ state)
+{
+    using T2 = typename C2<R>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *tile = reinterpret_cast<T2 *>(smem_raw);
+    const int ngroups = (1 << g.L) >> K;
+    for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x) {
+        T2 *base = state + tile_base(g, t);
+        tile_load(g, base, tile);
+        __syncthreads();
+        for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
+            const int ib = group_base<K>(g, grp);
+            T2 out[1 << K];
+#pragma unroll
+            for (int r = 0; r < (1 << K); ++r) out[r] = cmul(m.d[r], tile[swz<R>(ib + m.src[r])]);
+#pragma unroll
+            for (int r = 0; r < (1 << K); ++r) tile[swz<R>(ib + g.toff[r])] = out[r];
+        }
+        __syncthreads();
         tile_store(g, base, tile);
         __syncthreads();
     }
@@ -380,6 +444,25 @@ static hq_status run_diag(void *state, int n, const int *qubits, const double *m
 template <typename R> static int tile_bits(int n) { return std::min(n, sizeof(R) == 4 ? 12 : 11); }
 
 template <typename R, int K>
+static hq_status run_mono(void *state, int n, const int *qubits, const double *mat, const int *perm, int64_t nstates,
+                          cudaStream_t s)
+{
+    TileGeom g;
+    make_geom(g, n, K, qubits, tile_bits<R>(n), nstates);
+    MonoParam<R, K> m;
+    for (int r = 0; r < (1 << K); ++r) {
+        m.d[r].x = R(mat[2 * (r * (1 << K) + perm[r])]);
+        m.d[r].y = R(mat[2 * (r * (1 << K) + perm[r]) + 1]);
+        m.src[r] = g.toff[perm[r]];
+    }
+    const size_t smem = size_t(sizeof(typename C2<R>::type)) << g.L;
+    const void *fn = (const void *)k_mono<R, K>;
+    const int grid = grid_for(fn, kThreads, smem, g.total_tiles);
+    k_mono<R, K><<<grid, kThreads, smem, s>>>(g, m, (typename C2<R>::type *)state);
+    return cuda_status("k_mono", cudaGetLastError());
+}
+
+template <typename R, int K>
 static hq_status run_gather(void *state, int n, const int *qubits, const double *mat, int64_t nstates, cudaStream_t s)
 {
     TileGeom g;
@@ -433,6 +516,16 @@ static hq_status dispatch(void *state, int n, int k, const int *qubits, const do
         case 4: return run_diag<R, 4>(state, n, qubits, mat, nstates, s);
         case 5: return run_diag<R, 5>(state, n, qubits, mat, nstates, s);
         case 6: return run_diag<R, 6>(state, n, qubits, mat, nstates, s);
+        }
+    }
+    // monomial gates: a permuted, phased copy of each group
+    int perm[16];
+    if (k <= 4 && is_monomial(k, mat, perm)) {
+        switch (k) {
+        case 1: return run_mono<R, 1>(state, n, qubits, mat, perm, nstates, s);
+        case 2: return run_mono<R, 2>(state, n, qubits, mat, perm, nstates, s);
+        case 3: return run_mono<R, 3>(state, n, qubits, mat, perm, nstates, s);
+        case 4: return run_mono<R, 4>(state, n, qubits, mat, perm, nstates, s);
         }
     }
     // the tensor-core engine needs at least one full tile of 128 groups
