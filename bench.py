@@ -162,26 +162,61 @@ def block_class(qs, m, engine, tc_min_k, n=30):
     return f"k_gather_k{k}" if k <= 4 else f"k_block_k{k}"
 
 
-def cpu_baseline(circ, seconds: float = 12.0):
-    """The oracle as it stands, on all host cores, over the first gates of the
-    same circuit until ~`seconds` of CPU work; rate in unfused gate-apps/s."""
+def cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo), or the platform string."""
+    import platform
+
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:  # Arm hosts: /proc/cpuinfo has no model name, lscpu does
+        import subprocess
+
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(circ, seconds: float = 12.0, single_seconds: float = 6.0):
+    """The oracle as it stands over the first gates of the same circuit: on all
+    host cores until ~`seconds` of CPU work (the reported rate), then on one
+    thread for ~`single_seconds`; rates in unfused gate-apps/s."""
     import oracle
 
     cores = oracle.max_threads()
     n = circ.n
-    psi = np.zeros(1 << n, np.complex128)
-    psi[0] = 1.0
-    done = 0
-    t0 = time.perf_counter()
-    for g in circ.gates:
-        oracle.apply_gate(psi, n, g.qubits, g.matrix)
-        done += 1
-        if time.perf_counter() - t0 > seconds:
-            break
-    dt = time.perf_counter() - t0
+
+    def run(limit):
+        psi = np.zeros(1 << n, np.complex128)
+        psi[0] = 1.0
+        done = 0
+        t0 = time.perf_counter()
+        for g in circ.gates:
+            oracle.apply_gate(psi, n, g.qubits, g.matrix)
+            done += 1
+            if time.perf_counter() - t0 > limit:
+                break
+        return done, time.perf_counter() - t0
+
+    done, dt = run(seconds)
+    oracle.set_threads(1)
+    try:
+        done1, dt1 = run(single_seconds)
+    finally:
+        oracle.set_threads(cores)
     return {"value": done / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
             "sample": f"first {done} of {len(circ.gates)} gates of the same n={n} circuit, complex128, "
-                      f"unfused, OpenMP over {cores} threads ({dt:.1f} s)"}
+                      f"unfused, OpenMP over {cores} threads ({dt:.1f} s)",
+            "single_thread": {"value": done1 / dt1, "sample": f"first {done1} gates on 1 thread ({dt1:.1f} s)"},
+            "cpu": cpu_model(), "nproc": os.cpu_count()}
 
 
 def run_reference(args):
