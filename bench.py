@@ -279,6 +279,40 @@ def _time_blocks(n, blocks, engine, dtype, reps=1, tc_min_k=4):
     return st, e0.elapsed_time(e1) / 1e3 / reps
 
 
+def measure_small_circuit(reps: int = 20):
+    """One small circuit (n=12, 163 gates; latency-bound): per-block launches
+    of the fused circuit against one persistent launch of the batch runner."""
+    import torch
+    from paper_2111_06868_gb300 import hq
+
+    c12 = C.config_small(seed=0)
+    st12 = torch.empty(1 << c12.n, dtype=torch.complex64, device="cuda")
+    b12 = hq.hq_fuse(c12.n, c12.gates, 4)
+    hq.hq_state_init(st12)
+    hq.hq_apply_blocks(st12, b12)
+    torch.cuda.synchronize()
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        hq.hq_state_init(st12)
+        hq.hq_apply_blocks(st12, b12)
+    e1.record()
+    torch.cuda.synchronize()
+    t_blocks = e0.elapsed_time(e1) / 1e3 / reps
+    b = hq.Batch([c12], None, 12, 6, 0, 0)
+    b.run()
+    e0, e1 = _events()
+    e0.record()
+    for _ in range(reps):
+        b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3 / reps
+    b.close()
+    return {"gates": len(c12.gates), "fused_blocks_k4": len(b12), "apply_blocks_us": 1e6 * t_blocks,
+            "batch_runner_us": 1e6 * t_batch, "gate_apps_per_s_batch_runner": len(c12.gates) / t_batch}
+
+
 def measure_extras(args):
     """One measurement of every other workload (CUDA events)."""
     import torch
@@ -361,6 +395,7 @@ def measure_extras(args):
         torch.cuda.empty_cache()
     out["batch512"] = {"circuits": len(cs), "gates": Gb, "tile": [13, 7], "launches_per_run": 1, "graph": True,
                        **bres}
+    out["n12_one_circuit"] = measure_small_circuit()
     return out
 
 
