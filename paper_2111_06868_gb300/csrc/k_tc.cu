@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
         };
         if (warp == 0 && int64_t(blockIdx.x) < g.total_tiles) load_tile(blockIdx.x, 0);
         int it = 0, issued = 0, loaded = (int64_t(blockIdx.x) < g.total_tiles) ? 1 : 0;
+        float prov = 0.f;  // scale of the largest tile maximum seen so far (0: none yet)
         for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
             const int buf = it & 1;
             // the buffer of tile it-1 was read by every producer before the last barrier
@@ -190,62 +191,61 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
             const bool landed = mbar_wait(&bar[4 + buf], uint32_t((it / 2) & 1), abort_flag, &g_device_error);
             const float2 *xt = reinterpret_cast<const float2 *>(smem + Lay::kOffTile + buf * Lay::kTileBytes);
             const float2 *x = xt + ibase;
-            float s = 1.f, am_s[AM ? 4 : 1];
-            if constexpr (!AM) {
-                float m = landed ? (part == 0 ? max_part(std::integral_constant<int, 0>{}, x)
-                                              : max_part(std::integral_constant<int, SPLIT - 1>{}, x))
-                                 : 0.f;
-                if (SPLIT > 1) {
-                    part_max[part * kTcGroups + n] = m;
-                    named_bar_sync(1, NP);
-#pragma unroll
-                    for (int h = 0; h < SPLIT; ++h) m = fmaxf(m, part_max[h * kTcGroups + n]);
-                }
+            // One power-of-two scale per tile.  The split needs only that no
+            // scaled value overflows FP16 and that the significant ones stay
+            // normal, so the tile is converted with a provisional scale (that
+            // of the largest tile maximum this CTA has seen) while its own
+            // maximum is taken in the same pass; a tile whose scaled maximum
+            // falls outside [2^-2, 2^15) is converted again with its own scale.
+            // Within the window a scaled value keeps hi + lo to ~2^-22 of
+            // itself down to 2^-3, where lo turns subnormal; beneath, its
+            // error stays below 2^-25, i.e. below 2^-23 of the tile maximum,
+            // the size of an FP32 rounding.  The first tile of a CTA takes an
+            // exact maximum.
+            auto scale_of = [](float m) {
                 int e = 0;
                 frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
-                s = (m > 0.f) ? ldexpf(1.f, 14 - e) : 1.f;
-            } else {
-                float m4[4] = {0.f, 0.f, 0.f, 0.f};
+                return m > 0.f ? ldexpf(1.f, 14 - e) : 1.f;
+            };
+            auto warp_max = [](float m) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                return m;
+            };
+            float *tmax = part_max;  // [0, 32): first-tile maxima; [32 + 32 * (it & 1), ...): per-tile maxima
+            float s = prov;
+            if (s == 0.f) {
+                float m = 0.f;
                 if (landed) {
-#pragma unroll
-                    for (int gi = 0; gi < 4; ++gi)
-#pragma unroll
-                        for (int j = 0; j < DP / 8; ++j) {
-                            float2 a, b;
-                            am_pair(xt, gi, j, a, b);
-                            m4[gi] = fmaxf(m4[gi], fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(b.x), fabsf(b.y))));
-                        }
-                }
-#pragma unroll
-                for (int gi = 0; gi < 4; ++gi) {
-                    m4[gi] = fmaxf(m4[gi], __shfl_xor_sync(0xffffffffu, m4[gi], 1));
-                    m4[gi] = fmaxf(m4[gi], __shfl_xor_sync(0xffffffffu, m4[gi], 2));
-                }
-                if (SPLIT > 1) {
-                    if (p4 == 0) {
+                    if constexpr (!AM) {
+                        m = part == 0 ? max_part(std::integral_constant<int, 0>{}, x)
+                                      : max_part(std::integral_constant<int, SPLIT - 1>{}, x);
+                    } else {
 #pragma unroll
                         for (int gi = 0; gi < 4; ++gi)
-                            part_max[part * kTcGroups + quarter * 32 + 16 * (gi >> 1) + row4 + 8 * (gi & 1)] = m4[gi];
+#pragma unroll
+                            for (int j = 0; j < DP / 8; ++j) {
+                                float2 a, b;
+                                am_pair(xt, gi, j, a, b);
+                                m = fmaxf(m, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(b.x), fabsf(b.y))));
+                            }
                     }
-                    named_bar_sync(1, NP);
-#pragma unroll
-                    for (int gi = 0; gi < 4; ++gi)
-#pragma unroll
-                        for (int h = 0; h < SPLIT; ++h)
-                            m4[gi] = fmaxf(m4[gi],
-                                           part_max[h * kTcGroups + quarter * 32 + 16 * (gi >> 1) + row4 + 8 * (gi & 1)]);
                 }
+                m = warp_max(m);
+                if ((tid & 31) == 0) tmax[warp] = m;
+                named_bar_sync(1, NP);
+                float M = 0.f;
 #pragma unroll
-                for (int gi = 0; gi < 4; ++gi) {
-                    int e = 0;
-                    frexpf(m4[gi], &e);
-                    am_s[gi] = (m4[gi] > 0.f) ? ldexpf(1.f, 14 - e) : 1.f;
-                }
+                for (int w = 0; w < NP / 32; ++w) M = fmaxf(M, tmax[w]);
+                s = scale_of(M);
             }
             // TMEM buffer `buf` is free once the epilogue of tile it-2 released it
             const bool ok = landed && (it < 2 || mbar_wait(&bar[2 + buf], uint32_t((it / 2 - 1) & 1), abort_flag, &g_device_error));
-            if constexpr (AM) {
-                if (ok) {
+            // converts this thread's amplitudes with scale sc into TMEM buffer buf;
+            // returns the largest |component| seen
+            auto convert = [&](float sc) -> float {
+                float mx = 0.f;
+                if constexpr (AM) {
                     const uint32_t a_hi = tmem + uint32_t(buf) * Lay::kBufCols + uint32_t(part * DP);
                     const uint32_t a_lo = a_hi + uint32_t(D);
 #pragma unroll
@@ -258,25 +258,15 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                                 const int gi = 2 * hf + u;
                                 float2 a, b;
                                 am_pair(xt, gi, j, a, b);
-                                hv[4 * j + 2 * u] =
-                                    Split<BF16>::pack(a.x * am_s[gi], a.y * am_s[gi], lv[4 * j + 2 * u]);
-                                hv[4 * j + 2 * u + 1] =
-                                    Split<BF16>::pack(b.x * am_s[gi], b.y * am_s[gi], lv[4 * j + 2 * u + 1]);
+                                mx = fmaxf(mx, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(b.x), fabsf(b.y))));
+                                hv[4 * j + 2 * u] = Split<BF16>::pack(a.x * sc, a.y * sc, lv[4 * j + 2 * u]);
+                                hv[4 * j + 2 * u + 1] = Split<BF16>::pack(b.x * sc, b.y * sc, lv[4 * j + 2 * u + 1]);
                             }
                         const uint32_t lanes = uint32_t(quarter * 32 + 16 * hf) << 16;
                         tmem_st_16x256b(a_hi + lanes, hv);
                         tmem_st_16x256b(a_lo + lanes, lv);
                     }
-                    tmem_wait_st();
-                    if (part == 0 && p4 == 0) {
-#pragma unroll
-                        for (int gi = 0; gi < 4; ++gi)
-                            inv_scale[buf * kTcGroups + quarter * 32 + 16 * (gi >> 1) + row4 + 8 * (gi & 1)] =
-                                1.f / am_s[gi];
-                    }
-                }
-            } else {
-                if (ok) {
+                } else {
                     const uint32_t a_hi = tmem + lane_off + uint32_t(buf) * Lay::kBufCols;
                     const uint32_t a_lo = a_hi + uint32_t(D);
                     auto convert_part = [&](auto part_c) {
@@ -287,7 +277,8 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
 #pragma unroll
                             for (int u = 0; u < 16; ++u) {
                                 const float2 v = x[g.toff[c0 + u]];
-                                hv[u] = Split<BF16>::pack(v.x * s, v.y * s, lv[u]);
+                                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+                                hv[u] = Split<BF16>::pack(v.x * sc, v.y * sc, lv[u]);
                             }
                             tmem_st16(a_hi + uint32_t(c0), hv);
                             tmem_st16(a_lo + uint32_t(c0), lv);
@@ -295,14 +286,30 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                     };
                     if (part == 0) convert_part(std::integral_constant<int, 0>{});
                     else convert_part(std::integral_constant<int, SPLIT - 1>{});
-                    tmem_wait_st();
-                    if (part == 0) inv_scale[buf * kTcGroups + n] = 1.f / s;
                 }
-            }
+                tmem_wait_st();
+                return mx;
+            };
+            float mx = 0.f;
+            if (ok) mx = convert(s);
+            mx = warp_max(mx);
+            if ((tid & 31) == 0) tmax[32 + 32 * (it & 1) + warp] = mx;
             tc_fence_before();
             // every producer takes the same exit decision
             if (named_bar_or(2, NP, !ok || *abort_flag)) break;
+            float M = 0.f;
+#pragma unroll
+            for (int w = 0; w < NP / 32; ++w) M = fmaxf(M, tmax[32 + 32 * (it & 1) + w]);
+            if (M > 0.f && (M * s >= 32768.f || M * s < 0.25f)) {  // uniform: every producer read the same maxima
+                s = scale_of(M);
+                convert(s);
+                tc_fence_before();
+                named_bar_sync(1, NP);
+            }
+            if (M > 0.f) prov = prov == 0.f ? scale_of(M) : fminf(prov, scale_of(M));
             if (tid == 0) {
+                inv_scale[buf * kTcGroups] = 1.f / s;
+                __threadfence_block();  // before the MMAs whose completion the epilogue waits for
                 tc_fence_after();
                 const uint32_t a_hi = tmem + uint32_t(buf) * Lay::kBufCols;
                 const uint32_t a_lo = a_hi + uint32_t(D);
@@ -379,8 +386,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         const int gi = 2 * hf + u;
-                        const float mul =
-                            inv_scale[buf * kTcGroups + quarter * 32 + 16 * hf + row4 + 8 * u] * p.out_mul;
+                        const float mul = inv_scale[buf * kTcGroups] * p.out_mul;
                         float2 *gd = tb + am_gb[gi];
 #pragma unroll
                         for (int j = 0; j < CP / 8; ++j) {
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                 mbar_arrive(&bar[2 + buf]);
                 continue;
             }
-            const float mul = inv_scale[buf * kTcGroups + n] * p.out_mul;
+            const float mul = inv_scale[buf * kTcGroups] * p.out_mul;
             float2 *gdst = state + tile_base(g, t) + ibase;
             const uint32_t acc = tmem + lane_off + uint32_t(buf) * Lay::kBufCols + uint32_t(2 * D);
             auto drain_part = [&](auto part_c) {
