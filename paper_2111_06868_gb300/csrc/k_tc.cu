@@ -66,9 +66,9 @@ struct TcLayout {
     static constexpr int kBBytes = D2 * D2 * 2;               // one of B_hi / B_lo
     static constexpr int kTileBytes = kTcGroups * D * 8;      // one tile of complex64, tile-local order
     static constexpr int kOffTile = 2 * kBBytes;              // tile[2]
-    static constexpr int kOffScale = kOffTile + 2 * kTileBytes;  // float[2][128]
-    static constexpr int kOffPartMax = kOffScale + 2 * kTcGroups * 4;  // float[2][128] (split groups)
-    static constexpr int kOffBar = kOffPartMax + 2 * kTcGroups * 4;  // mma_done[2], acc_free[2], full[2]
+    static constexpr int kOffScale = kOffTile + 2 * kTileBytes;  // float[2]: 1 / scale of each buffer's tile
+    static constexpr int kOffPartMax = kOffScale + 16;          // float[2][32]: per-warp tile maxima
+    static constexpr int kOffBar = kOffPartMax + 2 * 32 * 4;    // mma_done[2], acc_free[2], full[2]
     static constexpr int kOffMisc = kOffBar + 6 * 8;          // tmem addr, abort flag
     static constexpr int kBytes = kOffMisc + 16;
     // TMEM per buffer: A_hi (D cols), A_lo (D cols), accumulator (2D cols)
@@ -100,12 +100,13 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
     constexpr int NP = kTcGroups * SPLIT;   // producer threads (warps 0 .. NP/32-1)
     constexpr int NT = tc_threads<K>();
     constexpr int DP = D / SPLIT;           // amplitudes per producer thread
+    static_assert(NP / 32 <= 32, "per-warp tile maxima hold 32 warps");
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Lay::kOffBar);  // [0,1] mma_done, [2,3] acc_free
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + Lay::kOffMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + Lay::kOffMisc + 4);
     float *inv_scale = reinterpret_cast<float *>(smem + Lay::kOffScale);
-    float *part_max = reinterpret_cast<float *>(smem + Lay::kOffPartMax);  // [SPLIT][128]
+    float *part_max = reinterpret_cast<float *>(smem + Lay::kOffPartMax);  // [2][32] per-warp tile maxima
     const TileGeom &g = p.g;
     const int tid = threadIdx.x, warp = tid >> 5;
 
@@ -168,16 +169,6 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                 b = xt[am_gb[gi] + am_off[2 * j + 1]];
             }
         };
-        auto max_part = [&](auto part_c, const float2 *x) {
-            constexpr int R0 = decltype(part_c)::value * DP;
-            float m = 0.f;
-#pragma unroll
-            for (int r = R0; r < R0 + DP; ++r) {
-                const float2 v = x[g.toff[r]];
-                m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
-            }
-            return m;
-        };
         if (warp == 0 && int64_t(blockIdx.x) < g.total_tiles) load_tile(blockIdx.x, 0);
         int it = 0, issued = 0, loaded = (int64_t(blockIdx.x) < g.total_tiles) ? 1 : 0;
         float prov = 0.f;  // scale of the largest tile maximum seen so far (0: none yet)
@@ -200,8 +191,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
             // Within the window a scaled value keeps hi + lo to ~2^-22 of
             // itself down to 2^-3, where lo turns subnormal; beneath, its
             // error stays below 2^-25, i.e. below 2^-23 of the tile maximum,
-            // the size of an FP32 rounding.  The first tile of a CTA takes an
-            // exact maximum.
+            // the size of an FP32 rounding.
             auto scale_of = [](float m) {
                 int e = 0;
                 frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
@@ -212,33 +202,8 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                 for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
                 return m;
             };
-            float *tmax = part_max;  // [0, 32): first-tile maxima; [32 + 32 * (it & 1), ...): per-tile maxima
-            float s = prov;
-            if (s == 0.f) {
-                float m = 0.f;
-                if (landed) {
-                    if constexpr (!AM) {
-                        m = part == 0 ? max_part(std::integral_constant<int, 0>{}, x)
-                                      : max_part(std::integral_constant<int, SPLIT - 1>{}, x);
-                    } else {
-#pragma unroll
-                        for (int gi = 0; gi < 4; ++gi)
-#pragma unroll
-                            for (int j = 0; j < DP / 8; ++j) {
-                                float2 a, b;
-                                am_pair(xt, gi, j, a, b);
-                                m = fmaxf(m, fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(b.x), fabsf(b.y))));
-                            }
-                    }
-                }
-                m = warp_max(m);
-                if ((tid & 31) == 0) tmax[warp] = m;
-                named_bar_sync(1, NP);
-                float M = 0.f;
-#pragma unroll
-                for (int w = 0; w < NP / 32; ++w) M = fmaxf(M, tmax[w]);
-                s = scale_of(M);
-            }
+            float *tmax = part_max + 32 * (it & 1);  // per-warp maxima of this tile
+            float s = prov != 0.f ? prov : 1.f;  // before any nonzero tile: a guess the check below corrects
             // TMEM buffer `buf` is free once the epilogue of tile it-2 released it
             const bool ok = landed && (it < 2 || mbar_wait(&bar[2 + buf], uint32_t((it / 2 - 1) & 1), abort_flag, &g_device_error));
             // converts this thread's amplitudes with scale sc into TMEM buffer buf;
@@ -293,13 +258,13 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
             float mx = 0.f;
             if (ok) mx = convert(s);
             mx = warp_max(mx);
-            if ((tid & 31) == 0) tmax[32 + 32 * (it & 1) + warp] = mx;
+            if ((tid & 31) == 0) tmax[warp] = mx;
             tc_fence_before();
             // every producer takes the same exit decision
             if (named_bar_or(2, NP, !ok || *abort_flag)) break;
             float M = 0.f;
 #pragma unroll
-            for (int w = 0; w < NP / 32; ++w) M = fmaxf(M, tmax[32 + 32 * (it & 1) + w]);
+            for (int w = 0; w < NP / 32; ++w) M = fmaxf(M, tmax[w]);
             if (M > 0.f && (M * s >= 32768.f || M * s < 0.25f)) {  // uniform: every producer read the same maxima
                 s = scale_of(M);
                 convert(s);
@@ -308,7 +273,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
             }
             if (M > 0.f) prov = prov == 0.f ? scale_of(M) : fminf(prov, scale_of(M));
             if (tid == 0) {
-                inv_scale[buf * kTcGroups] = 1.f / s;
+                inv_scale[buf] = 1.f / s;
                 __threadfence_block();  // before the MMAs whose completion the epilogue waits for
                 tc_fence_after();
                 const uint32_t a_hi = tmem + uint32_t(buf) * Lay::kBufCols;
@@ -386,7 +351,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         const int gi = 2 * hf + u;
-                        const float mul = inv_scale[buf * kTcGroups] * p.out_mul;
+                        const float mul = inv_scale[buf] * p.out_mul;
                         float2 *gd = tb + am_gb[gi];
 #pragma unroll
                         for (int j = 0; j < CP / 8; ++j) {
@@ -401,7 +366,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                 mbar_arrive(&bar[2 + buf]);
                 continue;
             }
-            const float mul = inv_scale[buf * kTcGroups] * p.out_mul;
+            const float mul = inv_scale[buf] * p.out_mul;
             float2 *gdst = state + tile_base(g, t) + ibase;
             const uint32_t acc = tmem + lane_off + uint32_t(buf) * Lay::kBufCols + uint32_t(2 * D);
             auto drain_part = [&](auto part_c) {

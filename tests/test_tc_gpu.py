@@ -120,6 +120,33 @@ def test_sparse_state_zero_groups(hq):
     assert rel_l2(st.cpu().numpy().astype(np.complex128), psi) <= 2e-6
 
 
+@pytest.mark.parametrize("bits", [[0, 1, 2, 3, 4, 5], [6, 7, 8, 9, 10, 11], [1, 3, 4, 8, 10, 12]])
+def test_tile_maxima_spanning_many_octaves(hq, bits):
+    """Each tile is converted with a provisional power-of-two scale and redone
+    when its maximum falls outside the window; tiles whose magnitudes jump by
+    up to 2^80 in either direction along a CTA's tile sequence (and by 2^20
+    between groups of one tile) must each keep FP32-level error relative to
+    their own maximum.  The targets lie in the low 13 flat bits, so every tile
+    is one aligned run of 2^13 amplitudes."""
+    n, k = 22, 6
+    rng = C.SplitMix64(41 + bits[0])
+    psi = random_state(n, 17 + bits[0]).reshape(-1, 1 << 13)
+    tiles = psi.shape[0]
+    tile_exp = np.array([-20 * ((7 * t + (t >> 3)) % 5) for t in range(tiles)])
+    within = np.array([-10 * ((i >> 6) % 3) for i in range(1 << 13)])
+    psi = (psi * np.exp2(tile_exp)[:, None] * np.exp2(within)[None, :]).reshape(-1)
+    st = torch.from_numpy(psi).to(torch.complex64).cuda()
+    psi = st.cpu().numpy().astype(np.complex128)  # the oracle starts from the rounded input
+    qs = [n - 1 - b for b in bits]
+    M = C.random_unitary(k, rng)
+    hq.hq_apply_blocks(st, [(qs, M)], engine="tc_f16")
+    oracle.apply_gate(psi, n, qs, M)
+    got = st.cpu().numpy().astype(np.complex128).reshape(tiles, -1)
+    want = psi.reshape(tiles, -1)
+    err = np.abs(got - want).max(axis=1) / np.abs(want).max(axis=1)
+    assert err.max() <= 2e-6, (int(err.argmax()), float(err.max()))
+
+
 @pytest.mark.parametrize("kmax", [4, 5, 6])
 def test_fused_grid_circuit_fp16_meets_complex64_bar(hq, kmax):
     circ = C.random_circuit(C.grid(4, 5), 16, seed=3, two_qubit="fsim")
