@@ -598,7 +598,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if S == 8 else "f64", "data": "synthetic",
             "config": {"workload": desc, "n": n, "gates": G, "fused_blocks": B, "k_max": args.kmax,
-                       "state": args.dtype, "engine": engine, "l2": "state (8 GiB+) larger than L2; no flush",
+                       "state": args.dtype, "engine": engine, "l2": (f"state ({S * (1 << n) / 2**30:g} GiB) larger than the 129 MB L2; no flush" if S << n > 129e6
+                              else f"state ({S << n} B) fits in L2 and is not flushed"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        **({"passes": passes} if engine == "tc_pass" else {})},
             "effective_GBps": eff_gbs, "roofline_frac_effective": eff_gbs / peaks["hbm_gbs"],
