@@ -118,6 +118,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def fuse(hq, n, gates, kmax, args):
+    """The fusion step (host): hq_fuse_dag by default, hq_fuse on --fuse greedy."""
+    return hq.hq_fuse(n, gates, kmax, method=args.fuse, restarts=args.fuse_restarts)
+
+
 def kernel_sources_sha(kernel_class):
     """Hash of the sources the kernel class is built from (ties ncu traffic
     figures to the code they were measured on)."""
@@ -279,7 +284,7 @@ def _time_blocks(n, blocks, engine, dtype, reps=1, tc_min_k=4):
     return st, e0.elapsed_time(e1) / 1e3 / reps
 
 
-def measure_small_circuit(reps: int = 20):
+def measure_small_circuit(args, reps: int = 20):
     """One small circuit (n=12, 163 gates; latency-bound): per-block launches
     of the fused circuit against one persistent launch of the batch runner."""
     import torch
@@ -287,7 +292,7 @@ def measure_small_circuit(reps: int = 20):
 
     c12 = C.config_small(seed=0)
     st12 = torch.empty(1 << c12.n, dtype=torch.complex64, device="cuda")
-    b12 = hq.hq_fuse(c12.n, c12.gates, 4)
+    b12 = fuse(hq, c12.n, c12.gates, 4, args)
     hq.hq_state_init(st12)
     hq.hq_apply_blocks(st12, b12)
     torch.cuda.synchronize()
@@ -334,7 +339,7 @@ def measure_extras(args):
     torch.cuda.empty_cache()
     # n=33: fused k <= 6 on tensor cores vs CUDA cores (64 GiB state)
     c33 = C.config_n33(seed=args.seed)
-    b33 = hq.hq_fuse(33, c33.gates, 6)
+    b33 = fuse(hq, 33, c33.gates, 6, args)
     st, t_tc = _time_blocks(33, b33, "tc_f16", torch.complex64)
     nrm = hq.hq_expectation(st, [(1.0, ())])
     _, t_cc = _time_blocks(33, b33[:8], "cuda_core", torch.complex64)
@@ -355,7 +360,7 @@ def measure_extras(args):
     errs = {}
     for eng in ("tc_f16", "tc_bf16", "cuda_core"):
         hq.hq_state_init(st)
-        hq.hq_apply_blocks(st, hq.hq_fuse(28, c28.gates, 6), engine=eng, tc_min_k=4)
+        hq.hq_apply_blocks(st, fuse(hq, 28, c28.gates, 6, args), engine=eng, tc_min_k=4)
         errs[eng] = (st.to(torch.complex128) - ref).norm().item() / ref.norm().item()
     out["n28_subset_rel_l2_vs_fp64"] = {"gates": len(c28.gates), **errs, "bar": 2e-5}
     del st, ref
@@ -395,7 +400,7 @@ def measure_extras(args):
         torch.cuda.empty_cache()
     out["batch512"] = {"circuits": len(cs), "gates": Gb, "tile": [13, 7], "launches_per_run": 1, "graph": True,
                        **bres}
-    out["n12_one_circuit"] = measure_small_circuit()
+    out["n12_one_circuit"] = measure_small_circuit(args)
     return out
 
 
@@ -422,6 +427,9 @@ def main():
     ap.add_argument("--impl", default="hq", choices=["hq", "reference"])
     ap.add_argument("--workload", default="n30", choices=["n30", "n33", "n27", "n12"])
     ap.add_argument("--kmax", type=int, default=6)
+    ap.add_argument("--fuse", default="dag", choices=["dag", "greedy"],
+                    help="hq_fuse_dag (DAG frontier, restarts) or hq_fuse (greedy rule)")
+    ap.add_argument("--fuse-restarts", type=int, default=64)
     ap.add_argument("--dtype", default="complex64", choices=["complex64", "complex128"])
     ap.add_argument("--engine", default="tc_f16", choices=["auto", "cuda_core", "tc_f16", "tc_bf16", "tc_pass"])
     ap.add_argument("--tc-min-k", type=int, default=4)
@@ -458,7 +466,7 @@ def main():
     circ, desc = workload(args, rank)
     n, G = circ.n, len(circ.gates)
     t_f = time.perf_counter()
-    blocks = hq.hq_fuse(n, circ.gates, args.kmax) if args.kmax > 0 else [(g.qubits, g.matrix) for g in circ.gates]
+    blocks = fuse(hq, n, circ.gates, args.kmax, args) if args.kmax > 0 else [(g.qubits, g.matrix) for g in circ.gates]
     fuse_s = time.perf_counter() - t_f
     B = len(blocks)
     classes = [block_class(q, m, args.engine, args.tc_min_k, n) for q, m in blocks]
@@ -598,6 +606,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if S == 8 else "f64", "data": "synthetic",
             "config": {"workload": desc, "n": n, "gates": G, "fused_blocks": B, "k_max": args.kmax,
+                       "fusion": (f"{args.fuse} ({args.fuse_restarts} restarts)" if args.fuse == "dag" else args.fuse),
                        "state": args.dtype, "engine": engine, "l2": (f"state ({S * (1 << n) / 2**30:g} GiB) larger than the 129 MB L2; no flush" if S << n > 129e6
                               else f"state ({S << n} B) fits in L2 and is not flushed"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

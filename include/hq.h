@@ -139,6 +139,28 @@ hq_status hq_fuse(int n, const hq_gate *gates, int G, int k_max, hq_gate *blocks
                   int64_t pool_len, int *gate_block);
 
 /*
+ * hq_fuse_dag -- Sec. 3.1 compress(circuit, max_n_qubits) with a different
+ * rule: the same output as hq_fuse (blocks of at most k_max qubits, qubits
+ * sorted ascending, matrix = product of the members, FP64 on the host), in
+ * usually fewer blocks.  The circuit is read as a DAG (gates keep their order
+ * on every qubit, which fixes the product).  Blocks are placed one at a time
+ * from the DAG frontier: from each frontier gate a qubit set is grown one
+ * qubit at a time, each time by the qubit that lets the block absorb the most
+ * frontier gates inside the set (3 points per multi-qubit gate, 1 per
+ * single-qubit gate), and the best such block is placed.  A final pass merges
+ * a block into an earlier or later one when every block in between shares no
+ * qubit with it and the union fits.
+ *   restarts: >= 1 runs; run 0 breaks ties by the lowest index, run r > 0 at
+ *             random from SplitMix64 seeded with seed + r; the run with the
+ *             fewest blocks is returned (the first of equal runs).
+ *   other arguments, ownership and errors: as hq_fuse (restarts < 1: HQ_ERR_ARG).
+ * Host only; no device work.  Cost: about restarts x (a few ms per 1000
+ * gates).
+ */
+hq_status hq_fuse_dag(int n, const hq_gate *gates, int G, int k_max, int restarts, uint64_t seed,
+                      hq_gate *blocks, int *B, double *pool, int64_t pool_len, int *gate_block);
+
+/*
  * hq_apply_gate -- Sec. 4.2: state <- (matrix on qubits[0..k-1]) state, for
  * every group of 2^k amplitudes that differ only in the target bits.  Uses the
  * diagonal kernel when every off-diagonal entry is exactly zero, the gather

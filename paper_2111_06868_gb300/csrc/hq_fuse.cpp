@@ -16,6 +16,7 @@
 // A block's qubits are then sorted ascending and its matrix is the product
 // of its members in circuit order, each embedded in that qubit order.
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <vector>
 
@@ -61,10 +62,14 @@ void apply_to_columns(int kb, double *M, int k, const int *lp, const double *g)
         }
 }
 
-}  // namespace
+struct Blk {
+    uint64_t set;
+    std::vector<int> members;  // gate indices, in the order they are applied
+};
 
-extern "C" hq_status hq_fuse(int n, const hq_gate *gates, int G, int k_max, hq_gate *blocks, int *B, double *pool,
-                             int64_t pool_len, int *gate_block)
+int popc(uint64_t v) { return __builtin_popcountll(v); }
+
+hq_status check_gates(int n, const hq_gate *gates, int G, int k_max, int *B, hq_gate *blocks, double *pool)
 {
     if (!B || (G > 0 && (!gates || !blocks || !pool))) return HQ_ERR_NULL;
     if (G < 0 || k_max < 1 || k_max > HQ_MAX_K) return HQ_ERR_ARG;
@@ -75,28 +80,14 @@ extern "C" hq_status hq_fuse(int n, const hq_gate *gates, int G, int k_max, hq_g
         hq_status st = hq::check_qubits(n, gates[g].k, gates[g].qubits, HQ_MAX_K);
         if (st != HQ_OK) return st;
     }
-    struct Blk {
-        uint64_t set;
-        std::vector<int> members;
-    };
-    std::vector<Blk> bl;
-    auto popc = [](uint64_t v) { return __builtin_popcountll(v); };
-    for (int g = 0; g < G; ++g) {
-        uint64_t Q = 0;
-        for (int j = 0; j < gates[g].k; ++j) Q |= 1ull << gates[g].qubits[j];
-        int i = int(bl.size()) - 1;
-        while (i >= 0 && !(bl[i].set & Q)) --i;
-        int target = -1;
-        if (i >= 0 && popc(bl[i].set | Q) <= k_max) target = i;
-        for (int j = i + 1; target < 0 && j < int(bl.size()); ++j)
-            if (popc(bl[j].set | Q) <= k_max) target = j;
-        if (target < 0) {
-            bl.push_back({0, {}});
-            target = int(bl.size()) - 1;
-        }
-        bl[target].set |= Q;
-        bl[target].members.push_back(g);
-    }
+    return HQ_OK;
+}
+
+// Writes the blocks: qubits sorted ascending, matrix = product of the members
+// in order (later members on the left), embedded in that qubit order.
+hq_status emit_blocks(const std::vector<Blk> &bl, const hq_gate *gates, hq_gate *blocks, int *B, double *pool,
+                      int64_t pool_len, int *gate_block)
+{
     if (int(bl.size()) > *B) {
         *B = int(bl.size());
         return HQ_ERR_CAPACITY;
@@ -128,4 +119,228 @@ extern "C" hq_status hq_fuse(int n, const hq_gate *gates, int G, int k_max, hq_g
     }
     *B = int(bl.size());
     return HQ_OK;
+}
+
+// SplitMix64 (Steele, Lea and Flood, 2014): breaks ties between equally good
+// blocks in the restarts of the frontier fusion.
+struct SplitMix64 {
+    uint64_t s;
+    uint64_t next()
+    {
+        uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        return z ^ (z >> 31);
+    }
+};
+
+// Frontier fusion.  The circuit is a DAG: on every qubit its gates keep their
+// order.  Blocks are built one at a time from the frontier (the gates whose
+// predecessors are all placed): for a qubit set S, absorb(S) takes every gate
+// that becomes a frontier gate with its qubits inside S, repeatedly, which is
+// the largest block on S at this point.  S is grown from each frontier gate
+// one qubit at a time (the qubit whose addition absorbs the most), the best
+// of these blocks is placed, and the frontier advances past it.  A block
+// scores 3 per multi-qubit gate and 1 per single-qubit gate.  Any order that
+// keeps every qubit's gate order gives the same product, so the result equals
+// the circuit.
+class Frontier {
+public:
+    Frontier(int n, const hq_gate *gates, int G, int k_max)
+        : n_(n), G_(G), kmax_(k_max), mask_(G), weight_(G), k_(G), pos_(G), qubit_(G), per_q_(n)
+    {
+        for (int g = 0; g < G; ++g) {
+            uint64_t m = 0;
+            for (int j = 0; j < gates[g].k; ++j) {
+                const int q = gates[g].qubits[j];
+                m |= 1ull << q;
+                pos_[g][j] = int(per_q_[q].size());
+                per_q_[q].push_back(g);
+            }
+            mask_[g] = m;
+            weight_[g] = gates[g].k > 1 ? 3 : 1;
+            for (int j = 0; j < gates[g].k; ++j) qubit_[g][j] = gates[g].qubits[j];
+            k_[g] = gates[g].k;
+        }
+    }
+
+    // One greedy run; rng == nullptr breaks ties by the lowest index.
+    std::vector<Blk> run(SplitMix64 *rng) const
+    {
+        std::vector<Blk> out;
+        Ptr ptr{};
+        int left = G_;
+        while (left > 0) {
+            uint64_t best_set = 0;
+            int best_score = -1, ties = 0;
+            for (int q = 0; q < n_; ++q) {  // each frontier gate once, through its lowest qubit
+                if (ptr[q] >= int(per_q_[q].size())) continue;
+                const int g0 = per_q_[q][ptr[q]];
+                if (__builtin_ctzll(mask_[g0]) != q || !is_head(g0, ptr)) continue;
+                const uint64_t S = grow(mask_[g0], ptr, rng);
+                Ptr tmp;
+                const int sc = absorb(S, ptr, tmp, nullptr);
+                if (sc > best_score) {
+                    best_score = sc, best_set = S, ties = 1;
+                } else if (sc == best_score && rng && rng->next() % uint64_t(++ties) == 0) {
+                    best_set = S;
+                }
+            }
+            Blk b{best_set, {}};
+            Ptr next;
+            absorb(best_set, ptr, next, &b.members);
+            ptr = next;
+            left -= int(b.members.size());
+            out.push_back(std::move(b));
+        }
+        merge(out);
+        return out;
+    }
+
+private:
+    using Ptr = std::array<int, 64>;
+
+    bool is_head(int g, const Ptr &ptr) const
+    {
+        for (int j = 0; j < k_[g]; ++j)
+            if (ptr[qubit_[g][j]] != pos_[g][j]) return false;
+        return true;
+    }
+
+    // Absorbs into S every gate reachable from the frontier `ptr` whose qubits
+    // lie in S; `after` receives the advanced frontier.  Returns the score.
+    int absorb(uint64_t S, const Ptr &ptr, Ptr &after, std::vector<int> *members) const
+    {
+        after = ptr;
+        int score = 0;
+        for (bool changed = true; changed;) {
+            changed = false;
+            for (uint64_t s = S; s; s &= s - 1) {
+                const int q = __builtin_ctzll(s);
+                while (after[q] < int(per_q_[q].size())) {
+                    const int g = per_q_[q][after[q]];
+                    if ((mask_[g] & ~S) || !is_head(g, after)) break;
+                    for (int j = 0; j < k_[g]; ++j) ++after[qubit_[g][j]];
+                    score += weight_[g];
+                    if (members) members->push_back(g);
+                    changed = true;
+                }
+            }
+        }
+        return score;
+    }
+
+    // Grows S one qubit at a time, each time by the qubit (among those of the
+    // next few gates on S's qubits) that lets absorb() take the most.
+    uint64_t grow(uint64_t S, const Ptr &ptr, SplitMix64 *rng) const
+    {
+        constexpr int kLook = 6;
+        while (popc(S) < kmax_) {
+            uint64_t cand = 0;
+            for (uint64_t s = S; s; s &= s - 1) {
+                const int q = __builtin_ctzll(s);
+                const int end = std::min(int(per_q_[q].size()), ptr[q] + kLook);
+                for (int i = ptr[q]; i < end; ++i) cand |= mask_[per_q_[q][i]];
+            }
+            cand &= ~S;
+            if (!cand) break;
+            int best = -1, ties = 0;
+            uint64_t pick = 0;
+            Ptr tmp;
+            for (uint64_t c = cand; c; c &= c - 1) {
+                const uint64_t bit = c & (~c + 1);
+                const int sc = absorb(S | bit, ptr, tmp, nullptr);
+                if (sc > best) {
+                    best = sc, pick = bit, ties = 1;
+                } else if (sc == best && rng && rng->next() % uint64_t(++ties) == 0) {
+                    pick = bit;
+                }
+            }
+            S |= pick;
+        }
+        return S;
+    }
+
+    // Merges a block into an earlier (later) one when every block in between
+    // shares no qubit with it and the union fits: it commutes there.
+    void merge(std::vector<Blk> &bl) const
+    {
+        for (bool changed = true; changed;) {
+            changed = false;
+            for (int b = int(bl.size()) - 1; b >= 0 && !changed; --b) {
+                const uint64_t Sb = bl[b].set;
+                for (int a = b - 1; a >= 0; --a) {
+                    if (popc(bl[a].set | Sb) <= kmax_) {
+                        bl[a].set |= Sb;
+                        bl[a].members.insert(bl[a].members.end(), bl[b].members.begin(), bl[b].members.end());
+                        bl.erase(bl.begin() + b);
+                        changed = true;
+                        break;
+                    }
+                    if (bl[a].set & Sb) break;
+                }
+                if (changed) break;
+                for (int c = b + 1; c < int(bl.size()); ++c) {
+                    if (popc(bl[c].set | Sb) <= kmax_) {
+                        bl[c].set |= Sb;
+                        bl[c].members.insert(bl[c].members.begin(), bl[b].members.begin(), bl[b].members.end());
+                        bl.erase(bl.begin() + b);
+                        changed = true;
+                        break;
+                    }
+                    if (bl[c].set & Sb) break;
+                }
+            }
+        }
+    }
+
+    int n_, G_, kmax_;
+    std::vector<uint64_t> mask_;
+    std::vector<int> weight_, k_;
+    std::vector<std::array<int, HQ_MAX_K>> pos_;    // index of gate g in the gate list of its j-th qubit
+    std::vector<std::array<int, HQ_MAX_K>> qubit_;  // qubits of gate g
+    std::vector<std::vector<int>> per_q_;           // gates on each qubit, in circuit order
+};
+
+}  // namespace
+
+extern "C" hq_status hq_fuse(int n, const hq_gate *gates, int G, int k_max, hq_gate *blocks, int *B, double *pool,
+                             int64_t pool_len, int *gate_block)
+{
+    hq_status st = check_gates(n, gates, G, k_max, B, blocks, pool);
+    if (st != HQ_OK) return st;
+    std::vector<Blk> bl;
+    for (int g = 0; g < G; ++g) {
+        uint64_t Q = 0;
+        for (int j = 0; j < gates[g].k; ++j) Q |= 1ull << gates[g].qubits[j];
+        int i = int(bl.size()) - 1;
+        while (i >= 0 && !(bl[i].set & Q)) --i;
+        int target = -1;
+        if (i >= 0 && popc(bl[i].set | Q) <= k_max) target = i;
+        for (int j = i + 1; target < 0 && j < int(bl.size()); ++j)
+            if (popc(bl[j].set | Q) <= k_max) target = j;
+        if (target < 0) {
+            bl.push_back({0, {}});
+            target = int(bl.size()) - 1;
+        }
+        bl[target].set |= Q;
+        bl[target].members.push_back(g);
+    }
+    return emit_blocks(bl, gates, blocks, B, pool, pool_len, gate_block);
+}
+
+extern "C" hq_status hq_fuse_dag(int n, const hq_gate *gates, int G, int k_max, int restarts, uint64_t seed,
+                                 hq_gate *blocks, int *B, double *pool, int64_t pool_len, int *gate_block)
+{
+    hq_status st = check_gates(n, gates, G, k_max, B, blocks, pool);
+    if (st != HQ_OK) return st;
+    if (restarts < 1) return HQ_ERR_ARG;
+    const Frontier f(n, gates, G, k_max);
+    std::vector<Blk> best = f.run(nullptr);
+    for (int r = 1; r < restarts; ++r) {
+        SplitMix64 rng{seed + uint64_t(r)};
+        std::vector<Blk> bl = f.run(&rng);
+        if (bl.size() < best.size()) best = std::move(bl);
+    }
+    return emit_blocks(best, gates, blocks, B, pool, pool_len, gate_block);
 }

@@ -90,6 +90,7 @@ def load(path: str | None = None):
         "hq_version": ([], ctypes.c_char_p),
         "hq_state_init": ([V, I, I, ctypes.c_char_p, V], I),
         "hq_fuse": ([I, V, I, I, V, P(I), V, ctypes.c_int64, V], I),
+        "hq_fuse_dag": ([I, V, I, I, I, ctypes.c_uint64, V, P(I), V, ctypes.c_int64, V], I),
         "hq_plan_passes": ([I, V, I, I, V, I], I),
         "hq_apply_gate": ([V, I, I, V, I, V, V], I),
         "hq_apply_blocks": ([V, I, I, V, I, V, V], I),
@@ -236,8 +237,10 @@ def hq_plan_passes(n: int, blocks: Iterable, max_blocks: int = 2):
     return out
 
 
-def hq_fuse(n: int, gates: Iterable, k_max: int, with_members: bool = False):
-    """Returns blocks as a list of (qubits tuple, complex128 matrix)."""
+def hq_fuse(n: int, gates: Iterable, k_max: int, with_members: bool = False, method: str = "greedy",
+            restarts: int = 64, seed: int = 0):
+    """Returns blocks as a list of (qubits tuple, complex128 matrix).
+    method "greedy": hq_fuse; "dag": hq_fuse_dag with `restarts` and `seed`."""
     keep: list = []
     arr, G = _gates_array(gates, keep)
     cap = max(1, G)
@@ -245,8 +248,14 @@ def hq_fuse(n: int, gates: Iterable, k_max: int, with_members: bool = False):
     B = ctypes.c_int(cap)
     pool = np.zeros(2 * max(1, G) * (4 ** k_max), np.float64)
     members = np.zeros(max(1, G), np.int32)
-    _check(load().hq_fuse(n, arr, G, k_max, blocks, ctypes.byref(B), pool.ctypes.data_as(ctypes.c_void_p),
-                          pool.size, members.ctypes.data_as(ctypes.c_void_p)), "hq_fuse")
+    tail = (blocks, ctypes.byref(B), pool.ctypes.data_as(ctypes.c_void_p), pool.size,
+            members.ctypes.data_as(ctypes.c_void_p))
+    if method == "greedy":
+        _check(load().hq_fuse(n, arr, G, k_max, *tail), "hq_fuse")
+    elif method == "dag":
+        _check(load().hq_fuse_dag(n, arr, G, k_max, restarts, seed, *tail), "hq_fuse_dag")
+    else:
+        raise ValueError(f"unknown fusion method {method!r}")
     out = []
     base = pool.ctypes.data
     for i in range(B.value):

@@ -84,13 +84,15 @@ def test_fuse_reproduces_compress_example(hq):
     assert [q for q, _ in blocks] == want
 
 
+@pytest.mark.parametrize("method", ["greedy", "dag"])
 @pytest.mark.parametrize("kmax", [1, 2, 3, 4, 5, 6])
-def test_fused_blocks_equal_their_members(hq, kmax):
+def test_fused_blocks_equal_their_members(hq, kmax, method):
     """Every block matrix equals the oracle's matrix of its member sequence,
     and the fused circuit leaves the same state as the unfused one."""
     circ = C.random_dense_circuit(8, 40, seed=kmax, kmax=min(kmax, 3))
-    blocks, members = hq.hq_fuse(8, circ.gates, kmax, with_members=True)
+    blocks, members = hq.hq_fuse(8, circ.gates, kmax, with_members=True, method=method, restarts=8)
     assert all(len(q) <= kmax for q, _ in blocks)
+    assert sorted(set(members.tolist())) == list(range(len(blocks)))
     for b, (qs, m) in enumerate(blocks):
         assert list(qs) == sorted(qs)
         mem = [circ.gates[i] for i in range(len(circ.gates)) if members[i] == b]
@@ -99,6 +101,46 @@ def test_fused_blocks_equal_their_members(hq, kmax):
     fused = C.Circuit(8, [C.Gate("B", q, m) for q, m in blocks])
     np.testing.assert_allclose(oracle.apply_circuit(psi0.copy(), fused), oracle.apply_circuit(psi0.copy(), circ),
                                atol=1e-12)
+
+
+def per_qubit_block_order_kept(n, gates, members):
+    """Along every qubit, the blocks of its gates never go back: the fused
+    circuit is a reordering of the DAG that keeps every qubit's gate order."""
+    last = [-1] * n
+    for g, b in zip(gates, members):
+        for q in g.qubits:
+            if b < last[q]:
+                return False
+            last[q] = b
+    return True
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_fuse_dag_keeps_qubit_order_and_state(hq, seed):
+    circ = C.random_circuit(C.grid(3, 4), 12, seed=seed, two_qubit="fsim" if seed % 2 else "cz")
+    for kmax in (3, 4, 6):
+        blocks, members = hq.hq_fuse(12, circ.gates, kmax, with_members=True, method="dag", restarts=16,
+                                     seed=seed)
+        assert per_qubit_block_order_kept(12, circ.gates, members)
+        assert all(len(q) <= kmax for q, _ in blocks)
+        psi0 = oracle.state_init(12, "+-+0-+-1+-+-")
+        fused = C.Circuit(12, [C.Gate("B", q, m) for q, m in blocks])
+        np.testing.assert_allclose(oracle.apply_circuit(psi0.copy(), fused),
+                                   oracle.apply_circuit(psi0.copy(), circ), atol=1e-12)
+
+
+def test_fuse_dag_is_deterministic_and_not_worse(hq):
+    """Fewer blocks than the greedy rule on the grid circuits (n=30: 61 -> 43
+    at k_max = 6), and the same blocks for the same seed."""
+    for circ, bound in [(C.config_n30(0), 45), (C.config_n33(0), 60)]:
+        greedy = hq.hq_fuse(circ.n, circ.gates, 6)
+        dag = hq.hq_fuse(circ.n, circ.gates, 6, method="dag")
+        assert len(dag) <= bound < len(greedy)
+        again = hq.hq_fuse(circ.n, circ.gates, 6, method="dag")
+        assert [q for q, _ in again] == [q for q, _ in dag]
+        assert all(np.array_equal(a, b) for (_, a), (_, b) in zip(again, dag))
+        one = hq.hq_fuse(circ.n, circ.gates, 6, method="dag", restarts=1)
+        assert len(dag) <= len(one)
 
 
 def test_fuse_grid_circuit_reduces_passes(hq):
@@ -116,6 +158,10 @@ def test_fuse_errors(hq):
         hq.hq_fuse(4, circ.gates, 2)
     with pytest.raises(hq.HQError, match="ARG"):
         hq.hq_fuse(4, circ.gates, 7)
+    with pytest.raises(hq.HQError, match="ARG"):
+        hq.hq_fuse(4, circ.gates, 3, method="dag", restarts=0)
+    with pytest.raises(hq.HQError, match="K_TOO_LARGE"):
+        hq.hq_fuse(4, circ.gates, 2, method="dag")
     # capacity: one slot for two disjoint-but-too-wide gates
     gates = (hq.hq_gate * 2)()
     keep = []
@@ -130,6 +176,7 @@ def test_fuse_errors(hq):
 
 def test_fuse_empty_circuit(hq):
     assert hq.hq_fuse(3, [], 4) == []
+    assert hq.hq_fuse(3, [], 4, method="dag") == []
 
 
 def test_batch_planner_host_only(hq):

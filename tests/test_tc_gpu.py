@@ -147,11 +147,12 @@ def test_tile_maxima_spanning_many_octaves(hq, bits):
     assert err.max() <= 2e-6, (int(err.argmax()), float(err.max()))
 
 
+@pytest.mark.parametrize("method", ["greedy", "dag"])
 @pytest.mark.parametrize("kmax", [4, 5, 6])
-def test_fused_grid_circuit_fp16_meets_complex64_bar(hq, kmax):
+def test_fused_grid_circuit_fp16_meets_complex64_bar(hq, kmax, method):
     circ = C.random_circuit(C.grid(4, 5), 16, seed=3, two_qubit="fsim")
     want = oracle.simulate(circ)
-    blocks = hq.hq_fuse(circ.n, circ.gates, kmax)
+    blocks = hq.hq_fuse(circ.n, circ.gates, kmax, method=method)
     st = torch.empty(1 << circ.n, dtype=torch.complex64, device="cuda")
     hq.hq_state_init(st)
     hq.hq_apply_blocks(st, blocks, engine="tc_f16", tc_min_k=4)
