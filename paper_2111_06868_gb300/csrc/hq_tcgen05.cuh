@@ -315,7 +315,7 @@ __device__ __forceinline__ void load_tile_async(const TileGeom &g, const TileLoa
 }
 
 // host side (k_tc.cu)
-// Builds the tensor-map view for tiles with short runs (2^c <= 256
+// Builds the tensor-map view for tiles with short runs (2^c <= 512
 // amplitudes); leaves tl.tm_dims = 0 (bulk copies per run) otherwise.
 void make_tile_map(const TileGeom &g, int n, int64_t nstates, void *state, TileLoad &tl, CUtensorMap &map);
 // Shared-memory wavefronts of one warp-wide read in which lane l reads `w`

@@ -458,14 +458,23 @@ static EncodeTiledFn encode_tiled()
     return fn;
 }
 
-// Tensor-map view of the states for tiles whose runs are short (2^c <= 256
-// amplitudes, i.e. <= 2 KB).  Dimension 0 = flat bits [0, h_1) with box 2^c;
-// dimension d >= 1 starts at the d-th group of consecutive high target bits,
-// whose bits are its box, and runs up to the next group (the last one to the
-// top bit, times the number of states).  A tensor copy has at most 5
-// dimensions: target groups beyond the 4th become coordinates instead, and the
-// tile is then loaded as 2^(their bits) boxes.  Leaves p.tm_dims = 0 (bulk
+// Longest contiguous run (log2 amplitudes) that a tile loads as tensor-map
+// boxes rather than one bulk copy per run (measured at n=30: 16 bulk copies of
+// 4 KB per tile ~5.8 TB/s, the same tile as boxes ~6.5 TB/s; from 8 KB runs on
+// bulk copies are as fast or faster).
+constexpr int kTmMaxRunBits = 9;
+
+// Tensor-map view of the states for tiles whose runs are short (2^c <=
+// 2^kTmMaxRunBits amplitudes).  Dimension 0 = flat bits [0, h_1) with box 2^c
+// (for c > 8, whose rows would exceed the 256-element box limit: dimension 0
+// = bits [0, 8) with box 256 and dimension 1 = bits [8, h_1) with box
+// 2^(c-8)); each further dimension starts at a group of consecutive high
+// target bits, whose bits are its box, and runs up to the next group (the last
+// one to the top bit, times the number of states).  A tensor copy has at most
+// 5 dimensions: target groups beyond those become coordinates instead, and
+// the tile is then loaded as 2^(their bits) boxes.  Leaves p.tm_dims = 0 (bulk
 // copies per run) when the view does not apply.
+
 void make_tile_map(const TileGeom &g, int n, int64_t nstates, void *state, TileLoad &p, CUtensorMap &map)
 {
     p.tm_dims = 0;
@@ -473,7 +482,10 @@ void make_tile_map(const TileGeom &g, int n, int64_t nstates, void *state, TileL
     p.tm_copy_bits = g.L;
     for (int d = 0; d < 5; ++d) p.tm_shift[d] = 0;
     std::memset(&map, 0, sizeof(map));
-    if (g.c > 8 || g.n_hi == 0) return;
+    // runs of up to 2^kTmMaxRunBits amplitudes come in as boxes; a box row holds
+    // at most 256 elements, so longer runs take two dimensions (bits 0-7, 8-c-1)
+    if (g.c > kTmMaxRunBits || g.n_hi == 0) return;
+    const int split = g.c > 8 ? 1 : 0;
     int gfirst[HQ_MAX_K], gsize[HQ_MAX_K], ng = 0;
     for (int h = 0; h < g.n_hi; ++h) {
         if (ng > 0 && gfirst[ng - 1] + gsize[ng - 1] == g.hi_bits[h]) {
@@ -483,21 +495,22 @@ void make_tile_map(const TileGeom &g, int n, int64_t nstates, void *state, TileL
             gsize[ng++] = 1;
         }
     }
-    const int nbox = std::min(ng, 4), dims = 1 + nbox;
+    const int nbox = std::min(ng, 4 - split), dims = 1 + split + nbox;
     int extra = 0;
     for (int i = nbox; i < ng; ++i) extra += gsize[i];
     cuuint64_t gdim[5], gstride[4];
     cuuint32_t box[5], estride[5];
     int shift[6];
     shift[0] = 0;
-    for (int d = 1; d < dims; ++d) shift[d] = gfirst[d - 1];
+    if (split) shift[1] = 8;
+    for (int d = 1 + split; d < dims; ++d) shift[d] = gfirst[d - 1 - split];
     shift[dims] = n;
     for (int d = 0; d < dims; ++d) {
         const uint64_t span = uint64_t(1) << (shift[d + 1] - shift[d]);
         gdim[d] = (d + 1 == dims) ? span * uint64_t(nstates) : span;
         if (gdim[d] > (uint64_t(1) << 31)) return;  // coordinates are signed 32-bit
         if (d > 0) gstride[d - 1] = cuuint64_t(8) << shift[d];
-        box[d] = d == 0 ? (1u << g.c) : (1u << gsize[d - 1]);
+        box[d] = d == 0 ? (1u << (split ? 8 : g.c)) : d == split ? (1u << (g.c - 8)) : (1u << gsize[d - 1 - split]);
         estride[d] = 1;
     }
     const EncodeTiledFn enc = encode_tiled();

@@ -93,6 +93,29 @@ def test_low_bit_targets_in_any_order(hq, engine, tol, k, pattern):
     assert err <= tol, (qs, err)
 
 
+# Targets that leave a 9-bit contiguous run (2^9 amplitudes) at the bottom of
+# the tile: tensor-map boxes whose rows take two dimensions, with 1-4 groups of
+# high targets (the last one also loaded as two boxes).
+SPLIT_ROW_PATTERNS = [[4, 5, 10, 11, 17, 23], [7, 8, 13, 14, 15, 20], [4, 5, 10, 11, 16, 17],
+                      [7, 8, 12, 14, 16, 18], [0, 1, 11, 13, 15, 17]]
+
+
+@pytest.mark.parametrize("pattern", range(len(SPLIT_ROW_PATTERNS)))
+def test_nine_bit_runs_as_two_dimensional_box_rows(hq, pattern):
+    n, k = 24, 6
+    bits = SPLIT_ROW_PATTERNS[pattern]
+    qs = [n - 1 - b for b in bits]
+    rng = C.SplitMix64(211 + pattern)
+    psi = random_state(n, 19 + pattern)
+    st = torch.from_numpy(psi).to(torch.complex64).cuda()
+    for _ in range(2):
+        M = C.random_unitary(k, rng)
+        hq.hq_apply_blocks(st, [(qs, M)], engine="tc_f16")
+        oracle.apply_gate(psi, n, qs, M)
+    err = rel_l2(st.cpu().numpy().astype(np.complex128), psi)
+    assert err <= 2e-6, (bits, err)
+
+
 @pytest.mark.parametrize("scale", [1e-3, 37.0])
 def test_non_unitary_scaling(hq, scale):
     n, k = 14, 6
