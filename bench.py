@@ -152,11 +152,19 @@ def measured_traffic(kernel_class, n):
     return entry["dram_bytes_per_amplitude"] * (1 << n)
 
 
-def block_class(qs, m, engine, tc_min_k, n=30):
+def block_class(qs, m, engine, tc_min_k, n=30, elem_bytes=8):
     """Which kernel libhq launches for this block (mirrors its dispatch:
-    tensor-core blocks of k = 4, 5 run widened to 6 qubits when n >= 13)."""
+    controlled gates first, tensor-core blocks of k = 4, 5 run widened to 6
+    qubits when n >= 13)."""
+    from paper_2111_06868_gb300 import hq
+
     d = m.shape[0]
     k = len(qs)
+    s, mask, _ = hq.hq_gate_structure(m)
+    nc = bin(mask).count("1")
+    sector_bits = 2 if elem_bytes == 8 else 1
+    if nc and k - nc <= 2 and any((mask >> j) & 1 and n - 1 - q >= sector_bits for j, q in enumerate(qs)):
+        return f"k_ctrl_kt{k - nc}"
     if not np.any(m[~np.eye(d, dtype=bool)]):
         return f"k_diag_k{k}"
     nz = np.abs(m) > 4 * np.finfo(np.float64).eps * np.abs(m).max()
@@ -165,6 +173,19 @@ def block_class(qs, m, engine, tc_min_k, n=30):
     if engine.startswith("tc") and k >= max(tc_min_k, 4) and n >= k + 7:
         return f"k_tc_{engine[3:]}_k{6 if n >= 13 else k}"
     return f"k_gather_k{k}" if k <= 4 else f"k_block_k{k}"
+
+
+def touched_fraction(qs, m, n, elem_bytes):
+    """Fraction of the state's bytes one gate reads and writes: 2^-c for the
+    controlled-gate kernel with c controls at or above the 32-byte sector,
+    else 1."""
+    from paper_2111_06868_gb300 import hq
+
+    if not block_class(qs, m, "auto", 4, n, elem_bytes).startswith("k_ctrl"):
+        return 1.0
+    _, mask, _ = hq.hq_gate_structure(m)
+    sector_bits = 2 if elem_bytes == 8 else 1
+    return 2.0 ** -sum(1 for j, q in enumerate(qs) if (mask >> j) & 1 and n - 1 - q >= sector_bits)
 
 
 def cpu_model() -> str:
@@ -337,6 +358,17 @@ def measure_extras(args):
                                          "GBps": len(sub) * 2 * (1 << 30) * 16 / t / 1e9}
     del st
     torch.cuda.empty_cache()
+    # n=30 QFT, unfused: 435 controlled phases (the controlled-gate kernel reads
+    # and writes only the amplitudes whose controls are 1), 30 H, 15 SWAP
+    qft = [(g.qubits, g.matrix) for g in C.qft_circuit(30).gates]
+    for name, dt, S in (("c64", torch.complex64, 8), ("c128", torch.complex128, 16)):
+        st, t = _time_blocks(30, qft, "auto", dt)
+        touched = sum(touched_fraction(q, m, 30, S) for q, m in qft) * 2 * (1 << 30) * S
+        out[f"n30_qft_per_gate_{name}"] = {"gates": len(qft), "gate_apps_per_s": len(qft) / t, "s": t,
+                                           "touched_GBps": touched / t / 1e9,
+                                           "full_pass_equivalents": touched / (2 * (1 << 30) * S)}
+        del st
+        torch.cuda.empty_cache()
     # n=33: fused k <= 6 on tensor cores vs CUDA cores (64 GiB state)
     c33 = C.config_n33(seed=args.seed)
     b33 = fuse(hq, 33, c33.gates, 6, args)
@@ -469,9 +501,9 @@ def main():
     blocks = fuse(hq, n, circ.gates, args.kmax, args) if args.kmax > 0 else [(g.qubits, g.matrix) for g in circ.gates]
     fuse_s = time.perf_counter() - t_f
     B = len(blocks)
-    classes = [block_class(q, m, args.engine, args.tc_min_k, n) for q, m in blocks]
     cdt = torch.complex64 if args.dtype == "complex64" else torch.complex128
     S = 8 if cdt == torch.complex64 else 16
+    classes = [block_class(q, m, args.engine, args.tc_min_k, n, S) for q, m in blocks]
     state = torch.empty(1 << n, dtype=cdt, device="cuda")
     stream = torch.cuda.current_stream()
     norm_term = [(1.0, ())]

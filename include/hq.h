@@ -161,10 +161,35 @@ hq_status hq_fuse_dag(int n, const hq_gate *gates, int G, int k_max, int restart
                       hq_gate *blocks, int *B, double *pool, int64_t pool_len, int *gate_block);
 
 /*
+ * hq_gate_structure -- the structure hq_apply_gate looks for in a k-qubit
+ * matrix (complex128, row-major as in hq_gate; host only, no device work).
+ * Returns a bit set (>= 0) of
+ *   HQ_STRUCT_DIAGONAL   every off-diagonal entry exactly 0;
+ *   HQ_STRUCT_MONOMIAL   one nonzero per row and column (entries within
+ *                        4 FP64 epsilon of the largest magnitude count as 0);
+ *   HQ_STRUCT_CONTROLLED at least one control (Sec. 2's Control gates): the
+ *                        matrix is the identity on every row and column where
+ *                        that qubit is 0 (same tolerance);
+ * or HQ_ERR_NULL (matrix) / HQ_ERR_K_TOO_LARGE (k out of [1, HQ_MAX_K]).
+ *   control_mask: optional out; bit j set when qubits[j] is a control.
+ *   u: optional out, 2 * 4^kt doubles for kt = k - (number of controls): the
+ *      matrix on the remaining targets (in their order, first = MSB of the
+ *      local index) where every control is 1.
+ */
+#define HQ_STRUCT_DIAGONAL 1
+#define HQ_STRUCT_MONOMIAL 2
+#define HQ_STRUCT_CONTROLLED 4
+int hq_gate_structure(int k, const double *matrix, int *control_mask, double *u);
+
+/*
  * hq_apply_gate -- Sec. 4.2: state <- (matrix on qubits[0..k-1]) state, for
- * every group of 2^k amplitudes that differ only in the target bits.  Uses the
- * diagonal kernel when every off-diagonal entry is exactly zero, the gather
- * kernel for k <= 4 and the CUDA-core block kernel for k = 5, 6.
+ * every group of 2^k amplitudes that differ only in the target bits.  Picks a
+ * kernel from the matrix's structure and the target positions: controlled
+ * gates with at most 2 targets and a control above the 32-byte sector read
+ * and write only the amplitudes whose controls are all 1; then diagonal
+ * gates a stream over the state; monomial gates (k <= 4) a permuted, phased
+ * copy; dense k <= 4 the shared-memory gather kernel; k = 5, 6 the CUDA-core
+ * block kernel.
  * Errors: HQ_ERR_NULL, HQ_ERR_N_TOO_LARGE, HQ_ERR_K_TOO_LARGE,
  * HQ_ERR_QUBIT_RANGE, HQ_ERR_DUP_QUBIT, HQ_ERR_DTYPE, HQ_ERR_ALIGN,
  * HQ_ERR_ALLOC, HQ_ERR_CUDA.

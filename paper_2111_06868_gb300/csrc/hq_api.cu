@@ -122,6 +122,20 @@ hq_status hq_state_init(void *state, int n, hq_dtype dt, const char *tokens, voi
     return launch_init(state, n, dt, tokens, 1, (cudaStream_t)stream);
 }
 
+int hq_gate_structure(int k, const double *matrix, int *control_mask, double *u)
+{
+    if (!matrix) return HQ_ERR_NULL;
+    if (k < 1 || k > HQ_MAX_K) return HQ_ERR_K_TOO_LARGE;
+    int cm = 0;
+    const int nc = hq::control_split(k, matrix, &cm, u);
+    if (control_mask) *control_mask = cm;
+    int s = 0;
+    if (hq::is_diagonal(k, matrix)) s |= HQ_STRUCT_DIAGONAL;
+    if (hq::is_monomial(k, matrix, nullptr)) s |= HQ_STRUCT_MONOMIAL;
+    if (nc > 0) s |= HQ_STRUCT_CONTROLLED;
+    return s;
+}
+
 hq_status hq_apply_gate(void *state, int n, hq_dtype dt, const int *qubits, int k, const double *matrix, void *stream)
 {
     hq_status st = check_state(state, n, dt);

@@ -171,6 +171,19 @@ hq_status launch_gate(void *state, int n, hq_dtype dt, int k, const int *qubits,
 bool is_diagonal(int k, const double *matrix);
 // exactly one nonzero per row and column; perm[r] = column of row r (may be NULL)
 bool is_monomial(int k, const double *matrix, int *perm);
+// Controls of a gate: bit j of *ctrl_mask is set when the matrix is the
+// identity on every row and column where qubits[j] is 0 (entries within 4 FP64
+// epsilon of the largest count as exact).  u (may be NULL) receives, row-major,
+// the 2^kt x 2^kt matrix on the kt = k - controls remaining targets (in their
+// order) where every control is 1.  Returns the number of controls.
+int control_split(int k, const double *matrix, int *ctrl_mask, double *u);
+// Widest target set the controlled-gate kernel takes.
+constexpr int kMaxCtrlTargets = 2;
+// True when the controlled-gate kernel applies and saves traffic: at least
+// one control, at most kMaxCtrlTargets targets, and a control at or above the
+// 32-byte sector (flat bit 2 for complex64, 1 for complex128).
+bool use_control_path(int n, int k, const int *qubits, const double *matrix, int elem_bytes, int *ctrl_mask,
+                      double *u);
 
 // expectation (k_reduce.cu)
 hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,

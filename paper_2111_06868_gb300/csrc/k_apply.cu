@@ -18,6 +18,11 @@
 //     (X, Y, CNOT, SWAP, iSWAP, Toffoli, fSim(pi/2, phi)): the tile scheme of
 //     k_gather with out_r = d_r * in_{pi(r)} per group, one complex multiply
 //     per amplitude instead of 2^K complex MACs.
+//   * k_ctrl<R, KT> (KT <= 2): controlled gates (CNOT, CZ, CPHASE, Toffoli,
+//     controlled-U): the matrix is the identity wherever a control qubit is 0,
+//     so only the amplitudes whose control bits are all 1 are read and
+//     written -- a fraction 2^-c of the state for c controls above the
+//     32-byte sector, instead of all of it.
 //   * k_block<R, K> (K = 5, 6): the same tile scheme for wide fused blocks on
 //     the CUDA cores (matrix in shared memory, 16 output rows per thread); the
 //     tensor-core engine for these widths is in k_tc.cu.
@@ -112,6 +117,63 @@ bool is_monomial(int k, const double *m, int *perm)
         used |= 1 << col;
         if (perm) perm[r] = col;
     }
+    return true;
+}
+
+int control_split(int k, const double *m, int *ctrl_mask, double *u)
+{
+    const int K = 1 << k;
+    double mx = 0;
+    for (int e = 0; e < K * K; ++e) mx = std::max(mx, std::hypot(m[2 * e], m[2 * e + 1]));
+    const double tiny = 4.0 * 2.220446049250313e-16 * mx;
+    auto identity_entry = [&](int r, int c) {
+        return std::hypot(m[2 * (r * K + c)] - (r == c ? 1.0 : 0.0), m[2 * (r * K + c) + 1]) <= tiny;
+    };
+    int cm = 0;
+    for (int j = 0; j < k; ++j) {
+        const int bit = 1 << (k - 1 - j);
+        bool ok = true;
+        for (int r = 0; r < K && ok; ++r)
+            for (int c = 0; c < K && ok; ++c)
+                if (!(r & bit) || !(c & bit)) ok = identity_entry(r, c);
+        if (ok) cm |= 1 << j;
+    }
+    *ctrl_mask = cm;
+    if (u) {
+        int tq[HQ_MAX_K], kt = 0, all = 0;
+        for (int j = 0; j < k; ++j) {
+            if ((cm >> j) & 1) all |= 1 << (k - 1 - j);
+            else tq[kt++] = j;
+        }
+        auto row = [&](int a) {  // local index with every control 1 and target bits from a
+            int r = all;
+            for (int i = 0; i < kt; ++i)
+                if ((a >> (kt - 1 - i)) & 1) r |= 1 << (k - 1 - tq[i]);
+            return r;
+        };
+        const int KT = 1 << kt;
+        for (int a = 0; a < KT; ++a)
+            for (int b = 0; b < KT; ++b) {
+                u[2 * (a * KT + b)] = m[2 * (row(a) * K + row(b))];
+                u[2 * (a * KT + b) + 1] = m[2 * (row(a) * K + row(b)) + 1];
+            }
+    }
+    return __builtin_popcount(unsigned(cm));
+}
+
+bool use_control_path(int n, int k, const int *qubits, const double *m, int elem_bytes, int *ctrl_mask, double *u)
+{
+    int cm = 0;
+    const int nc = control_split(k, m, &cm, nullptr);
+    if (nc == 0 || k - nc > kMaxCtrlTargets) return false;
+    // a control below the 32-byte sector saves no HBM traffic
+    const int sector_bits = elem_bytes == 8 ? 2 : 1;
+    bool saves = false;
+    for (int j = 0; j < k; ++j)
+        if (((cm >> j) & 1) && n - 1 - qubits[j] >= sector_bits) saves = true;
+    if (!saves) return false;
+    if (u) control_split(k, m, ctrl_mask, u);
+    else *ctrl_mask = cm;
     return true;
 }
 
@@ -375,6 +437,65 @@ __global__ void __launch_bounds__(kThreads) k_diag(const DiagParam<R, K> p, type
 }
 
 // ----------------------------------------------------------------------------
+// controlled gates, KT <= 2 targets
+// ----------------------------------------------------------------------------
+template <typename R, int KT> struct CtrlParam {
+    typename C2<R>::type u[1 << KT][1 << KT];  // the gate where every control is 1
+    int64_t toff[1 << KT];                     // flat offset of target index a
+    uint64_t cmask;                            // flat bits of the controls
+    int fixed[HQ_MAX_K];                       // flat bits of controls and targets, ascending
+    int nfixed, free_bits, n;                  // free_bits = n - nfixed
+};
+
+constexpr int kCtrlUnroll = 4;  // groups in flight per thread
+
+// Group f (over nstates * 2^free_bits) = the free bits of f spread over the
+// non-fixed bit positions, every control bit 1, every target bit 0; the other
+// amplitudes of the state are never touched.
+template <typename R, int KT>
+__global__ void __launch_bounds__(kThreads) k_ctrl(const CtrlParam<R, KT> p, typename C2<R>::type *__restrict__ state,
+                                                   int64_t groups)
+{
+    using T2 = typename C2<R>::type;
+    constexpr int D = 1 << KT;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x * kCtrlUnroll;
+    const int64_t fmask = (int64_t(1) << p.free_bits) - 1;
+    for (int64_t f0 = int64_t(blockIdx.x) * blockDim.x * kCtrlUnroll + threadIdx.x; f0 < groups; f0 += stride) {
+        T2 *a[kCtrlUnroll];
+        T2 v[kCtrlUnroll][D];
+#pragma unroll
+        for (int i = 0; i < kCtrlUnroll; ++i) {
+            const int64_t f = f0 + int64_t(i) * blockDim.x;
+            a[i] = nullptr;
+            if (f < groups) {
+                uint64_t x = uint64_t(f & fmask);
+#pragma unroll
+                for (int j = 0; j < HQ_MAX_K; ++j)
+                    if (j < p.nfixed) {
+                        const int b = p.fixed[j];
+                        x = ((x >> b) << (b + 1)) | (x & ((uint64_t(1) << b) - 1));
+                    }
+                a[i] = state + ((f >> p.free_bits) << p.n) + int64_t(x | p.cmask);
+#pragma unroll
+                for (int c = 0; c < D; ++c) v[i][c] = a[i][p.toff[c]];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kCtrlUnroll; ++i) {
+            if (!a[i]) continue;
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                T2 acc;
+                acc.x = acc.y = 0;
+#pragma unroll
+                for (int c = 0; c < D; ++c) cmac(acc, p.u[r][c], v[i][c]);
+                a[i][p.toff[r]] = acc;
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
 // product-state initialisation (Sec. 4.1 tokens)
 //   amplitude(x) = [x & fixed_mask == fixed_val] * amp * (-1)^popc(x & minus_mask)
 // ----------------------------------------------------------------------------
@@ -439,6 +560,40 @@ static hq_status run_diag(void *state, int n, const int *qubits, const double *m
     const int grid = grid_for(fn, kThreads, 0, (vec + kThreads - 1) / kThreads);
     k_diag<R, K><<<grid, kThreads, 0, s>>>(p, (typename C2<R>::type *)state, total);
     return cuda_status("k_diag", cudaGetLastError());
+}
+
+template <typename R, int KT>
+static hq_status run_ctrl(void *state, int n, int k, const int *qubits, int ctrl_mask, const double *u,
+                          int64_t nstates, cudaStream_t s)
+{
+    CtrlParam<R, KT> p;
+    std::memset(&p, 0, sizeof(p));
+    int tb[HQ_MAX_K], kt = 0;
+    for (int j = 0; j < k; ++j) {
+        const int b = n - 1 - qubits[j];
+        p.fixed[p.nfixed++] = b;
+        if ((ctrl_mask >> j) & 1) p.cmask |= uint64_t(1) << b;
+        else tb[kt++] = b;
+    }
+    std::sort(p.fixed, p.fixed + p.nfixed);
+    p.free_bits = n - p.nfixed;
+    p.n = n;
+    for (int a = 0; a < (1 << KT); ++a) {
+        int64_t off = 0;
+        for (int i = 0; i < KT; ++i)
+            if ((a >> (KT - 1 - i)) & 1) off += int64_t(1) << tb[i];
+        p.toff[a] = off;
+        for (int b = 0; b < (1 << KT); ++b) {
+            p.u[a][b].x = R(u[2 * (a * (1 << KT) + b)]);
+            p.u[a][b].y = R(u[2 * (a * (1 << KT) + b) + 1]);
+        }
+    }
+    const int64_t groups = nstates << p.free_bits;
+    const void *fn = (const void *)k_ctrl<R, KT>;
+    const int64_t per_cta = int64_t(kThreads) * kCtrlUnroll;
+    const int grid = grid_for(fn, kThreads, 0, (groups + per_cta - 1) / per_cta);
+    k_ctrl<R, KT><<<grid, kThreads, 0, s>>>(p, (typename C2<R>::type *)state, groups);
+    return cuda_status("k_ctrl", cudaGetLastError());
 }
 
 template <typename R> static int tile_bits(int n) { return std::min(n, sizeof(R) == 4 ? 12 : 11); }
@@ -508,6 +663,16 @@ template <typename R>
 static hq_status dispatch(void *state, int n, int k, const int *qubits, const double *mat, int64_t nstates,
                           int engine, cudaStream_t s)
 {
+    // controlled gates: only the amplitudes whose controls are all 1
+    int cm = 0;
+    double u[2 << (2 * kMaxCtrlTargets)];
+    if (use_control_path(n, k, qubits, mat, int(sizeof(typename C2<R>::type)), &cm, u)) {
+        switch (k - __builtin_popcount(unsigned(cm))) {
+        case 0: return run_ctrl<R, 0>(state, n, k, qubits, cm, u, nstates, s);
+        case 1: return run_ctrl<R, 1>(state, n, k, qubits, cm, u, nstates, s);
+        default: return run_ctrl<R, 2>(state, n, k, qubits, cm, u, nstates, s);
+        }
+    }
     if (is_diagonal(k, mat)) {
         switch (k) {
         case 1: return run_diag<R, 1>(state, n, qubits, mat, nstates, s);

@@ -677,8 +677,10 @@ static size_t tc_matrix_bytes(int k) { return size_t(2) * (size_t(4) << (2 * k))
 
 static bool tc_eligible(int n, const hq_gate &gt, int tc_min_k)
 {
+    int cm = 0;
     return gt.k >= tc_min_k && gt.k >= 4 && gt.k <= 6 && n >= gt.k + 7 && !is_diagonal(gt.k, gt.matrix) &&
-           !(gt.k <= 4 && is_monomial(gt.k, gt.matrix, nullptr));
+           !(gt.k <= 4 && is_monomial(gt.k, gt.matrix, nullptr)) &&
+           !use_control_path(n, gt.k, gt.qubits, gt.matrix, 8, &cm, nullptr);
 }
 
 // Blocks of k = 4, 5 run as 6-qubit blocks M (x) I on 6 - k more qubits: the

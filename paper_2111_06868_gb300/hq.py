@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "hq_state_init": ([V, I, I, ctypes.c_char_p, V], I),
         "hq_fuse": ([I, V, I, I, V, P(I), V, ctypes.c_int64, V], I),
         "hq_fuse_dag": ([I, V, I, I, I, ctypes.c_uint64, V, P(I), V, ctypes.c_int64, V], I),
+        "hq_gate_structure": ([I, V, P(I), V], I),
         "hq_plan_passes": ([I, V, I, I, V, I], I),
         "hq_apply_gate": ([V, I, I, V, I, V, V], I),
         "hq_apply_blocks": ([V, I, I, V, I, V, V], I),
@@ -235,6 +236,27 @@ def hq_plan_passes(n: int, blocks: Iterable, max_blocks: int = 2):
         out.append({"slots": [int(x) for x in r[:13]], "gates": [int(x) for x in r[14:14 + int(r[13])]],
                     "dest": [int(x) for x in r[16:29]]})
     return out
+
+
+STRUCT_DIAGONAL, STRUCT_MONOMIAL, STRUCT_CONTROLLED = 1, 2, 4
+
+
+def hq_gate_structure(matrix):
+    """(structure bits, control mask, matrix on the targets where every control
+    is 1) of a 2^k x 2^k matrix, as hq_apply_gate classifies it."""
+    m = np.ascontiguousarray(matrix, np.complex128)
+    k = int(m.shape[0]).bit_length() - 1
+    if m.shape != (1 << k, 1 << k):
+        raise ValueError("matrix must be 2^k x 2^k")
+    u = np.zeros(2 * 4 ** k, np.float64)
+    cm = ctypes.c_int(0)
+    s = load().hq_gate_structure(k, m.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cm),
+                                 u.ctypes.data_as(ctypes.c_void_p))
+    if s < 0:
+        _check(s, "hq_gate_structure")
+    kt = k - bin(cm.value).count("1")
+    d = 1 << kt
+    return s, cm.value, u[: 2 * d * d].view(np.complex128).reshape(d, d).copy()
 
 
 def hq_fuse(n: int, gates: Iterable, k_max: int, with_members: bool = False, method: str = "greedy",
