@@ -369,6 +369,24 @@ def measure_extras(args):
                                            "full_pass_equivalents": touched / (2 * (1 << 30) * S)}
         del st
         torch.cuda.empty_cache()
+    # n=30 <Z_0> after the circuit: Sec. 3.1 pop (light cone of qubit 0) and
+    # simplify ahead of fusion, against fusing the whole circuit
+    t_h = time.perf_counter()
+    kept = hq.hq_simplify(30, hq.hq_pop(30, circ.gates, [0]))
+    b_pop = fuse(hq, 30, kept, 6, args)
+    t_h = time.perf_counter() - t_h
+    b_full = fuse(hq, 30, circ.gates, 6, args)
+    z0 = [(1.0, ((0, "Z"),))]
+    st, t_full = _time_blocks(30, b_full, "tc_f16", torch.complex64)
+    e_full = hq.hq_expectation(st, z0)
+    del st
+    st, t_pop = _time_blocks(30, b_pop, "tc_f16", torch.complex64)
+    e_pop = hq.hq_expectation(st, z0)
+    del st
+    torch.cuda.empty_cache()
+    out["n30_z0_light_cone"] = {"gates_full": G, "gates_kept": len(kept), "blocks_full": len(b_full),
+                                "blocks_kept": len(b_pop), "s_full": t_full, "s_kept": t_pop,
+                                "speedup": t_full / t_pop, "host_s": t_h, "z0_full": e_full, "z0_kept": e_pop}
     # n=33: fused k <= 6 on tensor cores vs CUDA cores (64 GiB state)
     c33 = C.config_n33(seed=args.seed)
     b33 = fuse(hq, 33, c33.gates, 6, args)

@@ -161,6 +161,44 @@ hq_status hq_fuse_dag(int n, const hq_gate *gates, int G, int k_max, int restart
                       hq_gate *blocks, int *B, double *pool, int64_t pool_len, int *gate_block);
 
 /*
+ * hq_pop -- Sec. 3.1 pop(circuit, pinned_qubits): mark the gates inside the
+ * light cone of the pinned qubits (host only).  HQ_POP_RIGHT walks from the
+ * last gate back: a gate is kept when it shares a qubit with the cone, whose
+ * qubits then join the cone; the gates dropped act, after every kept gate
+ * that touches their qubits, on qubits that never reach the pinned ones, so
+ * the reduced state of the pinned qubits (and every expectation value of an
+ * observable on them) is unchanged.  HQ_POP_LEFT walks from the first gate
+ * forward (the same for the inverse circuit).  Matrices are not read (may be
+ * NULL).
+ *   pinned: npinned qubit indices (repeats allowed).
+ *   keep:   out, G ints: 1 = kept, 0 = dropped.
+ * Returns the number of kept gates, or HQ_ERR_NULL, HQ_ERR_ARG (G < 0,
+ * npinned < 0, direction), HQ_ERR_N_TOO_LARGE (n outside [1, 64]),
+ * HQ_ERR_QUBIT_RANGE, HQ_ERR_K_TOO_LARGE, HQ_ERR_DUP_QUBIT.
+ */
+#define HQ_POP_RIGHT 0
+#define HQ_POP_LEFT 1
+int hq_pop(int n, const hq_gate *gates, int G, const int *pinned, int npinned, int direction, int *keep);
+
+/*
+ * hq_simplify -- Sec. 3.1 simplify(circuit, use_matrix_commutation): mark
+ * the gates that remain after dropping (host only, FP64)
+ *   - every gate within atol of the identity (max-abs over its entries), and
+ *   - pairs g < h on the same qubit set whose product h g is within atol of
+ *     the identity, where h commutes with every kept gate between them that
+ *     shares a qubit with it: by having no qubit in common, or, with
+ *     use_matrix_commutation, by |[A, B]| <= atol on the union of their qubits
+ *     (unions wider than 8 qubits count as not commuting).
+ * Pairs are removed until none is left.  The kept gates, in their order, give
+ * the same operator within the tolerances.
+ *   keep: out, G ints: 1 = kept, 0 = dropped.
+ * Returns the number of kept gates, or HQ_ERR_NULL, HQ_ERR_ARG (G < 0, atol
+ * negative or NaN), HQ_ERR_N_TOO_LARGE (n outside [1, 64]),
+ * HQ_ERR_QUBIT_RANGE, HQ_ERR_K_TOO_LARGE, HQ_ERR_DUP_QUBIT.
+ */
+int hq_simplify(int n, const hq_gate *gates, int G, int use_matrix_commutation, double atol, int *keep);
+
+/*
  * hq_gate_structure -- the structure hq_apply_gate looks for in a k-qubit
  * matrix (complex128, row-major as in hq_gate; host only, no device work).
  * Returns a bit set (>= 0) of

@@ -1,4 +1,7 @@
-// hq_fuse.cpp -- greedy gate fusion (host), HybridQ Sec. 3.1 compress().
+// hq_fuse.cpp -- host circuit utilities of HybridQ Sec. 3.1: compress()
+// (hq_fuse, hq_fuse_dag), pop() (hq_pop) and simplify() (hq_simplify).
+//
+// compress -- greedy gate fusion:
 //
 // compress(circuit, max_n_qubits) merges gates into MatrixGates of at most
 // max_n_qubits qubits because wider gates use the hardware's vector units
@@ -17,6 +20,7 @@
 // of its members in circuit order, each embedded in that qubit order.
 #include <algorithm>
 #include <array>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -343,4 +347,141 @@ extern "C" hq_status hq_fuse_dag(int n, const hq_gate *gates, int G, int k_max, 
         if (bl.size() < best.size()) best = std::move(bl);
     }
     return emit_blocks(best, gates, blocks, B, pool, pool_len, gate_block);
+}
+
+// ----------------------------------------------------------------------------
+// pop(circuit, pinned_qubits, direction): the light cone of the pinned qubits
+// ----------------------------------------------------------------------------
+extern "C" int hq_pop(int n, const hq_gate *gates, int G, const int *pinned, int npinned, int direction, int *keep)
+{
+    if ((G > 0 && (!gates || !keep)) || (npinned > 0 && !pinned)) return HQ_ERR_NULL;
+    if (G < 0 || npinned < 0 || (direction != HQ_POP_RIGHT && direction != HQ_POP_LEFT)) return HQ_ERR_ARG;
+    if (n < 1 || n > 64) return HQ_ERR_N_TOO_LARGE;
+    uint64_t cone = 0;
+    for (int i = 0; i < npinned; ++i) {
+        if (pinned[i] < 0 || pinned[i] >= n) return HQ_ERR_QUBIT_RANGE;
+        cone |= 1ull << pinned[i];
+    }
+    for (int g = 0; g < G; ++g) {
+        hq_status st = hq::check_qubits(n, gates[g].k, gates[g].qubits, HQ_MAX_K);
+        if (st != HQ_OK) return st;
+    }
+    int kept = 0;
+    for (int i = 0; i < G; ++i) {
+        const int g = direction == HQ_POP_RIGHT ? G - 1 - i : i;
+        uint64_t m = 0;
+        for (int j = 0; j < gates[g].k; ++j) m |= 1ull << gates[g].qubits[j];
+        keep[g] = (m & cone) ? 1 : 0;
+        if (keep[g]) {
+            cone |= m;
+            ++kept;
+        }
+    }
+    return kept;
+}
+
+// ----------------------------------------------------------------------------
+// simplify(circuit, use_matrix_commutation)
+// ----------------------------------------------------------------------------
+namespace {
+
+constexpr int kCommuteMaxQubits = 8;  // widest union checked for commutation
+
+// The matrix of gate g (then gate h, if given) applied to the identity on the
+// qubits `u` (ascending): h * g as a 2^|u| x 2^|u| row-major matrix.
+void product_on(const std::vector<int> &u, const hq_gate &g, const hq_gate *h, std::vector<double> &M)
+{
+    const int ku = int(u.size()), D = 1 << ku;
+    M.assign(size_t(2) * D * D, 0.0);
+    for (int r = 0; r < D; ++r) M[2 * (size_t(r) * D + r)] = 1.0;
+    for (const hq_gate *x : {&g, h}) {
+        if (!x) continue;
+        int lp[HQ_MAX_K];
+        for (int j = 0; j < x->k; ++j) lp[j] = int(std::find(u.begin(), u.end(), x->qubits[j]) - u.begin());
+        apply_to_columns(ku, M.data(), x->k, lp, x->matrix);
+    }
+}
+
+std::vector<int> qubit_union(const hq_gate &a, const hq_gate &b)
+{
+    std::vector<int> u(a.qubits, a.qubits + a.k);
+    for (int j = 0; j < b.k; ++j)
+        if (std::find(u.begin(), u.end(), b.qubits[j]) == u.end()) u.push_back(b.qubits[j]);
+    std::sort(u.begin(), u.end());
+    return u;
+}
+
+double max_dev(const std::vector<double> &A, const std::vector<double> &B)
+{
+    double d = 0;
+    for (size_t i = 0; i < A.size(); i += 2) d = std::max(d, std::hypot(A[i] - B[i], A[i + 1] - B[i + 1]));
+    return d;
+}
+
+double dev_from_identity(const std::vector<double> &A, int D)
+{
+    double d = 0;
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c)
+            d = std::max(d, std::hypot(A[2 * (size_t(r) * D + c)] - (r == c ? 1.0 : 0.0), A[2 * (size_t(r) * D + c) + 1]));
+    return d;
+}
+
+bool commute(const hq_gate &a, const hq_gate &b, double atol)
+{
+    const std::vector<int> u = qubit_union(a, b);
+    if (int(u.size()) > kCommuteMaxQubits) return false;
+    std::vector<double> ab, ba;
+    product_on(u, b, &a, ab);  // a * b
+    product_on(u, a, &b, ba);  // b * a
+    return max_dev(ab, ba) <= atol;
+}
+
+}  // namespace
+
+extern "C" int hq_simplify(int n, const hq_gate *gates, int G, int use_matrix_commutation, double atol, int *keep)
+{
+    if (G > 0 && (!gates || !keep)) return HQ_ERR_NULL;
+    if (G < 0 || !(atol >= 0.0)) return HQ_ERR_ARG;
+    if (n < 1 || n > 64) return HQ_ERR_N_TOO_LARGE;
+    std::vector<uint64_t> mask(size_t(std::max(G, 0)));
+    for (int g = 0; g < G; ++g) {
+        if (!gates[g].matrix) return HQ_ERR_NULL;
+        hq_status st = hq::check_qubits(n, gates[g].k, gates[g].qubits, HQ_MAX_K);
+        if (st != HQ_OK) return st;
+        for (int j = 0; j < gates[g].k; ++j) mask[g] |= 1ull << gates[g].qubits[j];
+    }
+    std::vector<double> M;
+    for (int g = 0; g < G; ++g) {
+        std::vector<int> u(gates[g].qubits, gates[g].qubits + gates[g].k);
+        std::sort(u.begin(), u.end());
+        product_on(u, gates[g], nullptr, M);
+        keep[g] = dev_from_identity(M, 1 << gates[g].k) <= atol ? 0 : 1;
+    }
+    // Gate h cancels against the nearest earlier kept gate g on the same qubit
+    // set when h * g is the identity and h commutes with every kept gate in
+    // between that shares a qubit with it (h X g = X h g = X).
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (int h = 0; h < G; ++h) {
+            if (!keep[h]) continue;
+            for (int x = h - 1; x >= 0; --x) {
+                if (!keep[x] || !(mask[x] & mask[h])) continue;
+                if (mask[x] == mask[h]) {
+                    std::vector<int> u(gates[h].qubits, gates[h].qubits + gates[h].k);
+                    std::sort(u.begin(), u.end());
+                    product_on(u, gates[x], &gates[h], M);
+                    if (dev_from_identity(M, 1 << gates[h].k) <= atol) {
+                        keep[x] = keep[h] = 0;
+                        changed = true;
+                        break;
+                    }
+                }
+                if (!use_matrix_commutation || !commute(gates[x], gates[h], atol)) break;
+            }
+        }
+    }
+    int kept = 0;
+    for (int g = 0; g < G; ++g) kept += keep[g];
+    return kept;
 }

@@ -92,6 +92,8 @@ def load(path: str | None = None):
         "hq_fuse": ([I, V, I, I, V, P(I), V, ctypes.c_int64, V], I),
         "hq_fuse_dag": ([I, V, I, I, I, ctypes.c_uint64, V, P(I), V, ctypes.c_int64, V], I),
         "hq_gate_structure": ([I, V, P(I), V], I),
+        "hq_pop": ([I, V, I, V, I, I, V], I),
+        "hq_simplify": ([I, V, I, I, ctypes.c_double, V], I),
         "hq_plan_passes": ([I, V, I, I, V, I], I),
         "hq_apply_gate": ([V, I, I, V, I, V, V], I),
         "hq_apply_blocks": ([V, I, I, V, I, V, V], I),
@@ -239,6 +241,35 @@ def hq_plan_passes(n: int, blocks: Iterable, max_blocks: int = 2):
 
 
 STRUCT_DIAGONAL, STRUCT_MONOMIAL, STRUCT_CONTROLLED = 1, 2, 4
+POP_DIRECTIONS = {"right": 0, "left": 1}
+
+
+def hq_pop(n: int, gates, pinned, direction: str = "right") -> list:
+    """The gates (as given) inside the light cone of the pinned qubits."""
+    gates = list(gates)
+    keep_alive: list = []
+    arr, G = _gates_array(gates, keep_alive)
+    keep = np.zeros(max(1, G), np.int32)
+    pq = np.ascontiguousarray(list(pinned), np.int32)
+    r = load().hq_pop(n, arr, G, pq.ctypes.data_as(ctypes.c_void_p), len(pq), POP_DIRECTIONS[direction],
+                      keep.ctypes.data_as(ctypes.c_void_p))
+    if r < 0:
+        _check(r, "hq_pop")
+    return [g for g, k in zip(gates, keep[:G]) if k]
+
+
+def hq_simplify(n: int, gates, use_matrix_commutation: bool = True, atol: float = 1e-12) -> list:
+    """The gates (as given) that remain after dropping identities and
+    cancelling pairs."""
+    gates = list(gates)
+    keep_alive: list = []
+    arr, G = _gates_array(gates, keep_alive)
+    keep = np.zeros(max(1, G), np.int32)
+    r = load().hq_simplify(n, arr, G, int(bool(use_matrix_commutation)), float(atol),
+                           keep.ctypes.data_as(ctypes.c_void_p))
+    if r < 0:
+        _check(r, "hq_simplify")
+    return [g for g, k in zip(gates, keep[:G]) if k]
 
 
 def hq_gate_structure(matrix):

@@ -294,3 +294,21 @@ def test_n30_fused_norm_and_inverse(hq):
     assert abs(a0 - 1.0) <= 2 * 2e-5 * max(1, 2 * G / 1000)
     del st
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("pinned", [[0], [7, 12]])
+def test_popped_fused_circuit_expectation(hq, pinned):
+    """Sec. 3.1 pop, then simplify and DAG fusion, then the tensor-core
+    engine: expectation values on the pinned qubits equal the oracle's on the
+    full circuit."""
+    circ = C.random_circuit(C.grid(4, 5), 14, seed=5, two_qubit="fsim")
+    kept = hq.hq_pop(circ.n, circ.gates, pinned)
+    kept = hq.hq_simplify(circ.n, kept)
+    assert len(kept) < len(circ.gates)
+    blocks = hq.hq_fuse(circ.n, kept, 6, method="dag", restarts=8)
+    st = torch.empty(1 << circ.n, dtype=torch.complex64, device="cuda")
+    hq.hq_state_init(st)
+    hq.hq_apply_blocks(st, blocks, engine="tc_f16", tc_min_k=4)
+    H = [(1.0, ((pinned[0], "Z"),)), (0.5, ((pinned[-1], "X"),))]
+    want = oracle.expectation(oracle.simulate(circ), H)
+    assert abs(hq.hq_expectation(st, H) - want) <= 1e-5 * 1.5
