@@ -161,6 +161,57 @@ hq_status hq_fuse_dag(int n, const hq_gate *gates, int G, int k_max, int restart
                       hq_gate *blocks, int *B, double *pool, int64_t pool_len, int *gate_block);
 
 /*
+ * hq_reduced_density_matrix -- the reduced density matrix of k <= 2 qubits
+ * of a pure state: rho_ab = sum over the other qubits' indices y of
+ * psi(y, a) conj(psi(y, b)), a and b local indices with qubits[0] as MSB
+ * (Sec. 5; the one-qubit case is the paper's noisy tensor-network example).
+ * One read of the state, FP64 sums; synchronous.
+ *   rho_host: out, 2 * 4^k doubles, row-major complex.
+ * Errors: HQ_ERR_NULL, HQ_ERR_N_TOO_LARGE, HQ_ERR_DTYPE, HQ_ERR_ALIGN,
+ * HQ_ERR_K_TOO_LARGE (k < 1 or k > 2), HQ_ERR_QUBIT_RANGE, HQ_ERR_DUP_QUBIT,
+ * HQ_ERR_ALLOC, HQ_ERR_CUDA.
+ */
+hq_status hq_reduced_density_matrix(const void *state, int n, hq_dtype dt, const int *qubits, int k,
+                                    double *rho_host, void *stream);
+
+/*
+ * hq_apply_kraus_sampled -- Sec. 5 pure-state sampling of the Kraus
+ * operators K_0..K_{nK-1} of a channel on k <= 2 qubits: p_i = ||K_i psi||^2
+ * (from the operators alone when every K_i^dag K_i is a multiple of the
+ * identity, e.g. Pauli channels; else Tr(K_i rho K_i^dag) from
+ * hq_reduced_density_matrix, synchronous), i = the first index whose
+ * cumulative probability exceeds u * sum p, then psi <- K_i psi / sqrt(p_i).
+ *   kraus:  nK matrices of 2^k x 2^k complex128, row-major, one after another.
+ *   u:      a uniform number in [0, 1) drawn by the caller.
+ *   chosen: out (may be NULL), the index i.
+ * Errors: as hq_reduced_density_matrix, plus HQ_ERR_ARG (nK outside
+ * [1, 64], u outside [0, 1), or every p_i = 0).
+ */
+hq_status hq_apply_kraus_sampled(void *state, int n, hq_dtype dt, const int *qubits, int k, int nK,
+                                 const double *kraus, double u, int *chosen, void *stream);
+
+/* one operation of a noisy circuit (hq_run_trajectory) */
+typedef struct {
+    int k;               /* qubits acted on: 1..HQ_MAX_K for gates, 1..2 for channels */
+    int qubits[HQ_MAX_K];
+    int nkraus;          /* 0: a gate (matrix = one 2^k x 2^k matrix); >= 1: a channel with nkraus Kraus operators */
+    const double *matrix; /* complex128, row-major, host; nkraus matrices one after another for a channel */
+} hq_noisy_op;
+
+/*
+ * hq_run_trajectory -- one pure-state trajectory of a noisy circuit (Sec. 5):
+ * gates applied as hq_apply_blocks applies them (engine from cfg, NULL =
+ * HQ_ENGINE_AUTO), each channel as hq_apply_kraus_sampled with the next
+ * entry of u.
+ *   u:      one uniform in [0, 1) per channel, in operation order.
+ *   chosen: out (may be NULL), the sampled Kraus index per channel.
+ * Synchronous at every channel whose probabilities depend on the state.
+ * Errors: as hq_apply_gate and hq_apply_kraus_sampled; HQ_ERR_ARG (nops < 0).
+ */
+hq_status hq_run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops, int nops, const double *u,
+                            int *chosen, const hq_config *cfg, void *stream);
+
+/*
  * hq_pop -- Sec. 3.1 pop(circuit, pinned_qubits): mark the gates inside the
  * light cone of the pinned qubits (host only).  HQ_POP_RIGHT walks from the
  * last gate back: a gate is kept when it shares a qubit with the cone, whose

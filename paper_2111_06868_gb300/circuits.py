@@ -422,3 +422,52 @@ def pauli_string(n: int, term) -> str:
     for q, p in term:
         s[q] = p
     return "".join(s)
+
+
+# ----------------------------------------------------------------------------
+# Noise channels (Sec. 2.1 "Noisy gates") as Kraus operator lists, and noisy
+# circuits as operation lists ("gate", qubits, matrix) / ("kraus", qubits, Ks)
+# ----------------------------------------------------------------------------
+def depolarizing(p: float, k: int = 1) -> list:
+    """rho -> (1 - p) rho + p I / 2^k on k qubits, as Kraus operators: every
+    k-fold Pauli product P with weight p / 4^k, plus 1 - p on the identity."""
+    out = []
+    paulis = [""]
+    for _ in range(k):
+        paulis = [s + c for s in paulis for c in "IXYZ"]
+    for s in paulis:
+        m = np.ones((1, 1), dtype=np.complex128)
+        for c in s:
+            m = np.kron(m, PAULI[c])
+        weight = p / 4 ** k + (1.0 - p if s == "I" * k else 0.0)
+        out.append(math.sqrt(weight) * m)
+    return out
+
+
+def dephasing(p: float, sigma: str = "Z") -> list:
+    """rho -> (1 - p) rho + p sigma rho sigma."""
+    return [math.sqrt(1.0 - p) * PAULI["I"], math.sqrt(p) * PAULI[sigma]]
+
+
+def amplitude_damping(gamma: float, excitation: float = 0.0) -> list:
+    """Decay |1> -> |0> at rate gamma, and |0> -> |1> at the excitation rate."""
+    ops = [np.diag([math.sqrt(1.0 - excitation), math.sqrt(1.0 - gamma)]).astype(np.complex128),
+           math.sqrt(gamma) * np.array([[0, 1], [0, 0]], dtype=np.complex128)]
+    if excitation > 0:
+        ops.append(math.sqrt(excitation) * np.array([[0, 0], [1, 0]], dtype=np.complex128))
+    return ops
+
+
+def noisy_ops(circuit: Circuit, p1: float = 0.0, p2: float = 0.0, gamma: float = 0.0) -> list:
+    """The circuit's gates with a depolarizing channel after each one (p1 for
+    one-qubit, p2 for two-qubit gates) and amplitude damping (gamma) on the
+    qubit of every one-qubit gate."""
+    ops = []
+    for g in circuit.gates:
+        ops.append(("gate", tuple(g.qubits), g.matrix))
+        p = p1 if g.k == 1 else p2
+        if p > 0 and g.k <= 2:
+            ops.append(("kraus", tuple(g.qubits), depolarizing(p, g.k)))
+        if gamma > 0 and g.k == 1:
+            ops.append(("kraus", tuple(g.qubits), amplitude_damping(gamma)))
+    return ops

@@ -4,6 +4,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "hq_internal.cuh"
 
@@ -170,6 +171,83 @@ hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates,
     for (int g = 0; g < G; ++g) {
         st = launch_gate(state, n, dt, gates[g].k, gates[g].qubits, gates[g].matrix, 1, engine, (cudaStream_t)stream);
         if (st != HQ_OK) return st;
+    }
+    return HQ_OK;
+}
+
+hq_status hq_reduced_density_matrix(const void *state, int n, hq_dtype dt, const int *qubits, int k,
+                                    double *rho_host, void *stream)
+{
+    hq_status st = check_state(state, n, dt);
+    if (st != HQ_OK) return st;
+    if (k < 1 || k > 2) return HQ_ERR_K_TOO_LARGE;
+    if ((st = check_qubits(n, k, qubits, 2)) != HQ_OK) return st;
+    if (!rho_host) return HQ_ERR_NULL;
+    return launch_rdm(state, n, dt, qubits, k, rho_host, (cudaStream_t)stream);
+}
+
+static hq_status check_channel(int n, int k, const int *qubits, int nK, const double *kraus)
+{
+    if (k < 1 || k > 2) return HQ_ERR_K_TOO_LARGE;
+    hq_status st = check_qubits(n, k, qubits, 2);
+    if (st != HQ_OK) return st;
+    if (!kraus) return HQ_ERR_NULL;
+    if (nK < 1 || nK > 64) return HQ_ERR_ARG;
+    return HQ_OK;
+}
+
+hq_status hq_apply_kraus_sampled(void *state, int n, hq_dtype dt, const int *qubits, int k, int nK,
+                                 const double *kraus, double u, int *chosen, void *stream)
+{
+    hq_status st = check_state(state, n, dt);
+    if (st != HQ_OK) return st;
+    if ((st = check_channel(n, k, qubits, nK, kraus)) != HQ_OK) return st;
+    if (!(u >= 0.0 && u < 1.0)) return HQ_ERR_ARG;
+    return kraus_sampled(state, n, dt, qubits, k, nK, kraus, u, chosen, (cudaStream_t)stream);
+}
+
+hq_status hq_run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops, int nops, const double *u,
+                            int *chosen, const hq_config *cfg, void *stream)
+{
+    hq_status st = check_state(state, n, dt);
+    if (st != HQ_OK) return st;
+    if (nops < 0) return HQ_ERR_ARG;
+    if (nops > 0 && !ops) return HQ_ERR_NULL;
+    int nch = 0;
+    for (int i = 0; i < nops; ++i) {
+        if (ops[i].nkraus < 0) return HQ_ERR_ARG;
+        if (ops[i].nkraus == 0) {
+            if ((st = check_qubits(n, ops[i].k, ops[i].qubits, HQ_MAX_K)) != HQ_OK) return st;
+            if (!ops[i].matrix) return HQ_ERR_NULL;
+        } else {
+            if ((st = check_channel(n, ops[i].k, ops[i].qubits, ops[i].nkraus, ops[i].matrix)) != HQ_OK) return st;
+            if (!u) return HQ_ERR_NULL;
+            if (!(u[nch] >= 0.0 && u[nch] < 1.0)) return HQ_ERR_ARG;
+            ++nch;
+        }
+    }
+    // runs of gates go through hq_apply_blocks; channels are sampled in between
+    std::vector<hq_gate> run;
+    int c = 0;
+    for (int i = 0; i <= nops; ++i) {
+        if (i < nops && ops[i].nkraus == 0) {
+            hq_gate g;
+            std::memset(&g, 0, sizeof(g));
+            g.k = ops[i].k;
+            for (int j = 0; j < g.k; ++j) g.qubits[j] = ops[i].qubits[j];
+            g.matrix = ops[i].matrix;
+            run.push_back(g);
+            continue;
+        }
+        if (!run.empty()) {
+            if ((st = hq_apply_blocks(state, n, dt, run.data(), int(run.size()), cfg, stream)) != HQ_OK) return st;
+            run.clear();
+        }
+        if (i == nops) break;
+        st = kraus_sampled(state, n, dt, ops[i].qubits, ops[i].k, ops[i].nkraus, ops[i].matrix, u[c],
+                           chosen ? chosen + c : nullptr, (cudaStream_t)stream);
+        if (st != HQ_OK) return st;
+        ++c;
     }
     return HQ_OK;
 }

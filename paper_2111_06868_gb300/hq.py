@@ -58,6 +58,11 @@ class hq_pauli_term(ctypes.Structure):
     ]
 
 
+class hq_noisy_op(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("qubits", ctypes.c_int * HQ_MAX_K), ("nkraus", ctypes.c_int),
+                ("matrix", ctypes.c_void_p)]
+
+
 class hq_config(ctypes.Structure):
     _fields_ = [("engine", ctypes.c_int), ("tc_min_k", ctypes.c_int)]
 
@@ -93,6 +98,9 @@ def load(path: str | None = None):
         "hq_fuse_dag": ([I, V, I, I, I, ctypes.c_uint64, V, P(I), V, ctypes.c_int64, V], I),
         "hq_gate_structure": ([I, V, P(I), V], I),
         "hq_pop": ([I, V, I, V, I, I, V], I),
+        "hq_reduced_density_matrix": ([V, I, I, V, I, V, V], I),
+        "hq_apply_kraus_sampled": ([V, I, I, V, I, I, V, ctypes.c_double, V, V], I),
+        "hq_run_trajectory": ([V, I, I, V, I, V, V, V, V], I),
         "hq_simplify": ([I, V, I, I, ctypes.c_double, V], I),
         "hq_plan_passes": ([I, V, I, I, V, I], I),
         "hq_apply_gate": ([V, I, I, V, I, V, V], I),
@@ -330,6 +338,67 @@ def hq_apply_blocks(state, blocks: Iterable, engine: str | int = "auto", tc_min_
     cfg = hq_config(ENGINES[engine] if isinstance(engine, str) else int(engine), tc_min_k)
     _check(load().hq_apply_blocks(ptr, n, dt, arr, G, ctypes.byref(cfg), _stream(stream)), "hq_apply_blocks")
     return state
+
+
+def hq_reduced_density_matrix(state, qubits: Sequence[int], stream=None) -> np.ndarray:
+    """Reduced density matrix of 1 or 2 qubits (qubits[0] = MSB of the index)."""
+    ptr, n, dt = _state_args(state)
+    k = len(qubits)
+    q = (ctypes.c_int * max(1, k))(*[int(x) for x in qubits])
+    out = np.zeros(2 * 4 ** max(k, 1), np.float64)
+    _check(load().hq_reduced_density_matrix(ptr, n, dt, q, k, out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+           "hq_reduced_density_matrix")
+    return out.view(np.complex128).reshape(1 << k, 1 << k)
+
+
+def _kraus_block(kraus) -> np.ndarray:
+    return np.ascontiguousarray(np.stack([np.asarray(K, np.complex128) for K in kraus]), np.complex128)
+
+
+def hq_apply_kraus_sampled(state, qubits: Sequence[int], kraus, u: float, stream=None) -> int:
+    """Sample one Kraus operator of the channel with the uniform u and apply
+    it (renormalised); returns its index."""
+    ptr, n, dt = _state_args(state)
+    k = len(qubits)
+    q = (ctypes.c_int * max(1, k))(*[int(x) for x in qubits])
+    ks = _kraus_block(kraus)
+    chosen = ctypes.c_int(-1)
+    _check(load().hq_apply_kraus_sampled(ptr, n, dt, q, k, len(ks), ks.ctypes.data_as(ctypes.c_void_p), float(u),
+                                         ctypes.byref(chosen), _stream(stream)), "hq_apply_kraus_sampled")
+    return chosen.value
+
+
+def hq_run_trajectory(state, ops, u, engine: str | int = "auto", tc_min_k: int = 4, stream=None) -> np.ndarray:
+    """One trajectory of a noisy circuit.  ops: ("gate", qubits, matrix) or
+    ("kraus", qubits, [K_0, ...]); u: one uniform per channel.  Returns the
+    sampled Kraus index of every channel."""
+    ptr, n, dt = _state_args(state)
+    keep: list = []
+    arr = (hq_noisy_op * max(1, len(ops)))()
+    for i, (kind, qubits, m) in enumerate(ops):
+        arr[i].k = len(qubits)
+        for j, q in enumerate(qubits):
+            arr[i].qubits[j] = int(q)
+        if kind == "gate":
+            mm = np.ascontiguousarray(m, np.complex128)
+            arr[i].nkraus = 0
+        elif kind == "kraus":
+            mm = _kraus_block(m)
+            arr[i].nkraus = len(mm)
+        else:
+            raise ValueError(f"unknown op kind {kind!r}")
+        keep.append(mm)
+        arr[i].matrix = mm.ctypes.data
+    uu = np.ascontiguousarray(u, np.float64)
+    nch = sum(1 for kind, _, _ in ops if kind == "kraus")
+    if uu.size < nch:
+        raise ValueError("one uniform per channel is needed")
+    chosen = np.full(max(1, nch), -1, np.int32)
+    cfg = hq_config(ENGINES[engine] if isinstance(engine, str) else int(engine), tc_min_k)
+    _check(load().hq_run_trajectory(ptr, n, dt, arr, len(ops), uu.ctypes.data_as(ctypes.c_void_p),
+                                    chosen.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cfg), _stream(stream)),
+           "hq_run_trajectory")
+    return chosen[:nch]
 
 
 def hq_expectation(state, H, stream=None) -> float:
