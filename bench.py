@@ -387,6 +387,30 @@ def measure_extras(args):
     out["n30_z0_light_cone"] = {"gates_full": G, "gates_kept": len(kept), "blocks_full": len(b_full),
                                 "blocks_kept": len(b_pop), "s_full": t_full, "s_kept": t_pop,
                                 "speedup": t_full / t_pop, "host_s": t_h, "z0_full": e_full, "z0_kept": e_pop}
+    # noisy n=24 grid circuit, pure-state sampling of its Kraus channels
+    # (Sec. 5): depolarizing after every gate, amplitude damping (whose branch
+    # probabilities depend on the state) after every one-qubit gate
+    c24 = C.random_circuit(C.layout_for(24), 12, seed=args.seed, two_qubit="cz")
+    ops = C.noisy_ops(c24, p1=1e-3, p2=1e-2, gamma=1e-3)
+    nch = sum(1 for o in ops if o[0] == "kraus")
+    rng = np.random.default_rng(args.seed)  # the uniforms the sampling draws
+    st = torch.empty(1 << 24, dtype=torch.complex64, device="cuda")
+    hq.hq_state_init(st)
+    hq.hq_run_trajectory(st, ops, rng.random(nch))
+    torch.cuda.synchronize()
+    T, z = 8, []
+    t0 = time.perf_counter()
+    for _ in range(T):
+        hq.hq_state_init(st)
+        hq.hq_run_trajectory(st, ops, rng.random(nch))
+        z.append(hq.hq_expectation(st, [(1.0, ((0, "Z"),))]))
+    dt_traj = (time.perf_counter() - t0) / T
+    out["n24_noisy_trajectories"] = {"gates": len(c24.gates), "channels": nch,
+                                     "state_dependent_channels": sum(1 for g in c24.gates if g.k == 1),
+                                     "trajectories_per_s": 1 / dt_traj, "ms_per_trajectory": 1e3 * dt_traj,
+                                     "z0_mean": float(np.mean(z)), "timing": "wall clock, host waits included"}
+    del st
+    torch.cuda.empty_cache()
     # n=33: fused k <= 6 on tensor cores vs CUDA cores (64 GiB state)
     c33 = C.config_n33(seed=args.seed)
     b33 = fuse(hq, 33, c33.gates, 6, args)

@@ -203,7 +203,16 @@ hq_status hq_apply_kraus_sampled(void *state, int n, hq_dtype dt, const int *qub
     if (st != HQ_OK) return st;
     if ((st = check_channel(n, k, qubits, nK, kraus)) != HQ_OK) return st;
     if (!(u >= 0.0 && u < 1.0)) return HQ_ERR_ARG;
-    return kraus_sampled(state, n, dt, qubits, k, nK, kraus, u, chosen, (cudaStream_t)stream);
+    hq_noisy_op op;
+    std::memset(&op, 0, sizeof(op));
+    op.k = k;
+    for (int j = 0; j < k; ++j) op.qubits[j] = qubits[j];
+    op.nkraus = nK;
+    op.matrix = kraus;
+    int c = -1;
+    st = run_trajectory(state, n, dt, &op, 1, &u, &c, nullptr, (cudaStream_t)stream);
+    if (st == HQ_OK && chosen) *chosen = c;
+    return st;
 }
 
 hq_status hq_run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops, int nops, const double *u,
@@ -226,30 +235,7 @@ hq_status hq_run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *
             ++nch;
         }
     }
-    // runs of gates go through hq_apply_blocks; channels are sampled in between
-    std::vector<hq_gate> run;
-    int c = 0;
-    for (int i = 0; i <= nops; ++i) {
-        if (i < nops && ops[i].nkraus == 0) {
-            hq_gate g;
-            std::memset(&g, 0, sizeof(g));
-            g.k = ops[i].k;
-            for (int j = 0; j < g.k; ++j) g.qubits[j] = ops[i].qubits[j];
-            g.matrix = ops[i].matrix;
-            run.push_back(g);
-            continue;
-        }
-        if (!run.empty()) {
-            if ((st = hq_apply_blocks(state, n, dt, run.data(), int(run.size()), cfg, stream)) != HQ_OK) return st;
-            run.clear();
-        }
-        if (i == nops) break;
-        st = kraus_sampled(state, n, dt, ops[i].qubits, ops[i].k, ops[i].nkraus, ops[i].matrix, u[c],
-                           chosen ? chosen + c : nullptr, (cudaStream_t)stream);
-        if (st != HQ_OK) return st;
-        ++c;
-    }
-    return HQ_OK;
+    return run_trajectory(state, n, dt, ops, nops, u, chosen, cfg, (cudaStream_t)stream);
 }
 
 int hq_plan_passes(int n, const hq_gate *gates, int G, int max_blocks, int *records, int max_passes)

@@ -189,10 +189,10 @@ bool use_control_path(int n, int k, const int *qubits, const double *matrix, int
 // reduced density matrix of k <= 2 qubits (row-major 2^k x 2^k complex, host), synchronous
 hq_status launch_rdm(const void *state, int n, hq_dtype dt, const int *qubits, int k, double *out_host,
                      cudaStream_t s);
-// one sampled Kraus operator of a k <= 2 qubit channel (synchronous when the
-// probabilities depend on the state)
-hq_status kraus_sampled(void *state, int n, hq_dtype dt, const int *qubits, int k, int nK, const double *kraus,
-                        double u, int *chosen, cudaStream_t s);
+// one pure-state trajectory of a noisy circuit (arguments validated by the
+// caller); synchronous once, at the end, when a channel was sampled on the device
+hq_status run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops, int nops, const double *u,
+                         int *chosen, const hq_config *cfg, cudaStream_t s);
 
 // expectation (k_reduce.cu)
 hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pauli_term *terms, int T,

@@ -5,9 +5,10 @@
 //     the other qubits, in one read of the state.  Pure-state sampling of a
 //     Kraus channel (Sec. 5) takes its branch probabilities from it:
 //     p_i = ||K_i psi||^2 = Tr(K_i rho K_i^dag).
-//   * k_dm_pauli<R>: Tr(rho P) for Pauli strings P of a density matrix held
-//     as a 2n-qubit vector (row index on the first n qubits, column index on
-//     the last n): sum_i rho[i][i ^ x] <i ^ x|P|i>, 2^n reads.
+//   * k_kraus_pick, k_apply_sel: the branch of a state-dependent channel
+//     picked on the device from k_rdm's partial sums and a caller-drawn
+//     uniform, and the renormalised Kraus operator applied, with no host
+//     round trip.
 // Partial sums are FP64 per CTA and joined by one CTA in a fixed order.
 #include <algorithm>
 #include <cmath>
@@ -98,10 +99,9 @@ __global__ void __launch_bounds__(kNoiseThreads) k_noise_final(const double *__r
     }
 }
 
-template <typename R, int K>
-static hq_status run_rdm(const void *state, int n, const int *qubits, double *out_host, cudaStream_t s)
+template <typename R, int K> static RdmParam<R, K> rdm_param(int n, const int *qubits)
 {
-    constexpr int D = 1 << K, NE = rdm_entries<K>();
+    constexpr int D = 1 << K;
     RdmParam<R, K> p;
     std::memset(&p, 0, sizeof(p));
     for (int j = 0; j < K; ++j) p.fixed[j] = n - 1 - qubits[j];
@@ -113,16 +113,35 @@ static hq_status run_rdm(const void *state, int n, const int *qubits, double *ou
         p.toff[a] = off;
     }
     p.free_bits = n - K;
-    const int64_t groups = int64_t(1) << p.free_bits;
-    const void *fn = (const void *)k_rdm<R, K>;
+    return p;
+}
+
+template <typename R, int K> static int rdm_grid(int n)
+{
     const int64_t per_cta = int64_t(kNoiseThreads) * kRdmUnroll;
-    const int grid = grid_for(fn, kNoiseThreads, 0, (groups + per_cta - 1) / per_cta);
+    return grid_for((const void *)k_rdm<R, K>, kNoiseThreads, 0, ((int64_t(1) << (n - K)) + per_cta - 1) / per_cta);
+}
+
+// per-CTA partial sums (rdm_grid<R, K>(n) rows of 2 * rdm_entries<K>() doubles)
+template <typename R, int K>
+static hq_status rdm_partials(const void *state, int n, const int *qubits, double *partials, cudaStream_t s)
+{
+    const RdmParam<R, K> p = rdm_param<R, K>(n, qubits);
+    k_rdm<R, K><<<rdm_grid<R, K>(n), kNoiseThreads, 0, s>>>(p, (const typename C2<R>::type *)state,
+                                                             int64_t(1) << p.free_bits, partials);
+    return cuda_status("k_rdm", cudaGetLastError());
+}
+
+template <typename R, int K>
+static hq_status run_rdm(const void *state, int n, const int *qubits, double *out_host, cudaStream_t s)
+{
+    constexpr int D = 1 << K, NE = rdm_entries<K>();
+    const int grid = rdm_grid<R, K>(n);
     const int width = 2 * NE;
     double *scratch = nullptr;
     if (cudaMallocAsync((void **)&scratch, sizeof(double) * (size_t(grid) + 1) * width, s) != cudaSuccess)
         return HQ_ERR_ALLOC;
-    k_rdm<R, K><<<grid, kNoiseThreads, 0, s>>>(p, (const typename C2<R>::type *)state, groups, scratch);
-    hq_status rc = cuda_status("k_rdm", cudaGetLastError());
+    hq_status rc = rdm_partials<R, K>(state, n, qubits, scratch, s);
     double *out_dev = scratch + size_t(grid) * width;
     if (rc == HQ_OK) {
         k_noise_final<<<1, kNoiseThreads, 0, s>>>(scratch, grid, width, out_dev);
@@ -190,55 +209,328 @@ static double scalar_of(int D, const std::vector<double> &G)
     return c;
 }
 
-hq_status kraus_sampled(void *state, int n, hq_dtype dt, const int *qubits, int k, int nK, const double *kraus,
-                        double u, int *chosen, cudaStream_t s)
+// Device side of a state-dependent channel: k_rdm's partial sums -> the
+// branch (one CTA) -> the renormalised operator applied.  `sel` holds the
+// chosen operator (2 D^2 doubles) and, after it, 1.0 when that operator is
+// the identity to rounding (then nothing is applied).
+constexpr int kMaxKraus = 64;
+struct PickArgs {
+    const double *partials;
+    int nparts, width, D, nK;
+    const double *K;  // nK row-major D x D complex matrices, interleaved re/im
+    const double *G;  // their Gram matrices K^dag K
+    const double *u;  // the uniform in [0, 1)
+    int *chosen;
+    double *sel;
+    int *status;      // set to 1 when every p_i is 0
+};
+
+__global__ void __launch_bounds__(kNoiseThreads) k_kraus_pick(const PickArgs a)
 {
-    const int D = 1 << k;
-    const size_t msz = size_t(2) * D * D;
-    std::vector<double> p(nK), G;
-    bool mixture = true;  // every K_i^dag K_i = p_i I: probabilities without reading the state
-    for (int i = 0; i < nK && mixture; ++i) {
-        gram(D, kraus + i * msz, G);
-        p[i] = scalar_of(D, G);
-        mixture = p[i] >= 0;
+    __shared__ double tri[2 * rdm_entries<2>()];
+    for (int j = 0; j < a.width; ++j) {
+        double v = 0;
+        for (int i = threadIdx.x; i < a.nparts; i += blockDim.x) v += a.partials[int64_t(i) * a.width + j];
+        const double s = block_sum(v);
+        if (threadIdx.x == 0) tri[j] = s;
     }
-    if (!mixture) {
-        std::vector<double> rho(msz);
-        hq_status st = launch_rdm(state, n, dt, qubits, k, rho.data(), s);
-        if (st != HQ_OK) return st;
-        for (int i = 0; i < nK; ++i) {
-            // Tr(K rho K^dag) = Tr(rho K^dag K) = sum_rc rho[r][c] G[c][r]
-            gram(D, kraus + i * msz, G);
-            double t = 0;
-            for (int r = 0; r < D; ++r)
-                for (int c = 0; c < D; ++c)
-                    t += rho[2 * (r * D + c)] * G[2 * (c * D + r)] - rho[2 * (r * D + c) + 1] * G[2 * (c * D + r) + 1];
-            p[i] = std::max(t, 0.0);
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    const int D = a.D, DD = D * D;
+    double rr[4][4], ri[4][4];
+    for (int x = 0, e = 0; x < D; ++x)
+        for (int y = x; y < D; ++y, ++e) {
+            rr[x][y] = rr[y][x] = tri[2 * e];
+            ri[x][y] = tri[2 * e + 1];
+            ri[y][x] = -tri[2 * e + 1];
         }
+    double p[kMaxKraus], total = 0;
+    for (int i = 0; i < a.nK; ++i) {
+        // p_i = Tr(K rho K^dag) = Tr(rho K^dag K) = sum_rc rho[r][c] G[c][r]
+        const double *G = a.G + size_t(i) * 2 * DD;
+        double t = 0;
+        for (int r = 0; r < D; ++r)
+            for (int c = 0; c < D; ++c) t += rr[r][c] * G[2 * (c * D + r)] - ri[r][c] * G[2 * (c * D + r) + 1];
+        p[i] = fmax(t, 0.0);
+        total += p[i];
     }
-    double total = 0;
-    for (double v : p) total += v;
     if (!(total > 0)) {
-        set_last_error_text("kraus_sampled: every Kraus operator annihilates the state");
-        return HQ_ERR_ARG;
+        *a.status = 1;
+        *a.chosen = -1;
+        a.sel[2 * DD] = 1.0;
+        return;
     }
-    // the first i whose cumulative probability exceeds u * total
-    const double target = u * total;
+    // the first i whose cumulative probability exceeds u * total (the last
+    // nonzero one if rounding leaves none)
+    const double target = *a.u * total;
     int pick = -1;
     double cum = 0;
-    for (int i = 0; i < nK; ++i) {
+    for (int i = 0; i < a.nK; ++i) {
         cum += p[i];
-        if (p[i] > 0) pick = i;  // last nonzero, the fallback at the top end
+        if (p[i] > 0) pick = i;
         if (cum > target && p[i] > 0) {
             pick = i;
             break;
         }
     }
-    std::vector<double> m(kraus + pick * msz, kraus + (pick + 1) * msz);
-    const double sc = 1.0 / std::sqrt(p[pick]);
-    for (double &v : m) v *= sc;
-    if (chosen) *chosen = pick;
-    return launch_gate(state, n, dt, k, qubits, m.data(), 1, HQ_ENGINE_AUTO, s);
+    const double sc = 1.0 / sqrt(p[pick]);
+    const double *Kp = a.K + size_t(pick) * 2 * DD;
+    bool identity = true;
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            const double mr = Kp[2 * (r * D + c)] * sc, mi = Kp[2 * (r * D + c) + 1] * sc;
+            a.sel[2 * (r * D + c)] = mr;
+            a.sel[2 * (r * D + c) + 1] = mi;
+            identity = identity && hypot(mr - (r == c ? 1.0 : 0.0), mi) <= 4.0 * 2.220446049250313e-16;
+        }
+    a.sel[2 * DD] = identity ? 1.0 : 0.0;
+    *a.chosen = pick;
+}
+
+template <typename R, int K>
+__global__ void __launch_bounds__(kNoiseThreads) k_apply_sel(const RdmParam<R, K> p, const double *__restrict__ sel,
+                                                             typename C2<R>::type *__restrict__ psi, int64_t groups)
+{
+    using T2 = typename C2<R>::type;
+    constexpr int D = 1 << K;
+    if (sel[2 * D * D] != 0.0) return;  // the identity
+    T2 m[D][D];
+#pragma unroll
+    for (int r = 0; r < D; ++r)
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            m[r][c].x = R(sel[2 * (r * D + c)]);
+            m[r][c].y = R(sel[2 * (r * D + c) + 1]);
+        }
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x * kRdmUnroll;
+    for (int64_t f0 = int64_t(blockIdx.x) * blockDim.x * kRdmUnroll + threadIdx.x; f0 < groups; f0 += stride) {
+        T2 v[kRdmUnroll][D];
+        int64_t base[kRdmUnroll];
+#pragma unroll
+        for (int u = 0; u < kRdmUnroll; ++u) {
+            const int64_t f = f0 + int64_t(u) * blockDim.x;
+            base[u] = -1;
+            if (f < groups) {
+                uint64_t x = uint64_t(f);
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const int b = p.fixed[j];
+                    x = ((x >> b) << (b + 1)) | (x & ((uint64_t(1) << b) - 1));
+                }
+                base[u] = int64_t(x);
+#pragma unroll
+                for (int a = 0; a < D; ++a) v[u][a] = psi[base[u] + p.toff[a]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kRdmUnroll; ++u) {
+            if (base[u] < 0) continue;
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                T2 acc;
+                acc.x = acc.y = 0;
+#pragma unroll
+                for (int c = 0; c < D; ++c) cmac(acc, m[r][c], v[u][c]);
+                psi[base[u] + p.toff[r]] = acc;
+            }
+        }
+    }
+}
+
+template <typename R, int K>
+static hq_status sample_on_device(void *state, int n, const int *qubits, PickArgs a, cudaStream_t s)
+{
+    hq_status st = rdm_partials<R, K>(state, n, qubits, const_cast<double *>(a.partials), s);
+    if (st != HQ_OK) return st;
+    a.nparts = rdm_grid<R, K>(n);
+    a.width = 2 * rdm_entries<K>();
+    a.D = 1 << K;
+    k_kraus_pick<<<1, kNoiseThreads, 0, s>>>(a);
+    if ((st = cuda_status("k_kraus_pick", cudaGetLastError())) != HQ_OK) return st;
+    const RdmParam<R, K> p = rdm_param<R, K>(n, qubits);
+    const int64_t groups = int64_t(1) << p.free_bits;
+    k_apply_sel<R, K><<<rdm_grid<R, K>(n), kNoiseThreads, 0, s>>>(p, a.sel, (typename C2<R>::type *)state, groups);
+    return cuda_status("k_apply_sel", cudaGetLastError());
+}
+
+// K^dag K as a row-major D x D complex matrix
+static void gram(int D, const double *K, double *G)
+{
+    for (int r = 0; r < D; ++r)
+        for (int c = 0; c < D; ++c) {
+            double gr = 0, gi = 0;
+            for (int m = 0; m < D; ++m) {
+                // conj(K[m][r]) * K[m][c]
+                const double ar = K[2 * (m * D + r)], ai = -K[2 * (m * D + r) + 1];
+                const double br = K[2 * (m * D + c)], bi = K[2 * (m * D + c) + 1];
+                gr += ar * br - ai * bi;
+                gi += ar * bi + ai * br;
+            }
+            G[2 * (r * D + c)] = gr;
+            G[2 * (r * D + c) + 1] = gi;
+        }
+}
+
+// c when G = c I within 1e-12 of G's largest entry, else -1
+static double scalar_of(int D, const double *G)
+{
+    double mx = 0;
+    for (int i = 0; i < 2 * D * D; ++i) mx = std::max(mx, std::fabs(G[i]));
+    const double c = G[0], tol = 1e-12 * std::max(mx, 1e-300);
+    for (int r = 0; r < D; ++r)
+        for (int cc = 0; cc < D; ++cc) {
+            const double wr = r == cc ? c : 0.0;
+            if (std::fabs(G[2 * (r * D + cc)] - wr) > tol || std::fabs(G[2 * (r * D + cc) + 1]) > tol) return -1.0;
+        }
+    return c;
+}
+
+hq_status run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops, int nops, const double *u,
+                         int *chosen, const hq_config *cfg, cudaStream_t s)
+{
+    // Channels whose Kraus operators all have K^dag K = p_i I (Pauli channels)
+    // are sampled here from p_i alone: the chosen, renormalised operator joins
+    // the run of gates (nothing at all when it is the identity).  The others
+    // are sampled on the device from the state.
+    struct Dev { int op, ch; size_t koff, goff; };
+    std::vector<Dev> dev;
+    std::vector<double> hostbuf;  // K then G of each device-sampled channel, then their uniforms
+    std::vector<std::vector<double>> kept;  // renormalised operators the gate runs point into
+    std::vector<int> plan(nops, 0);         // 0 gate, 1 host-sampled (applied), 2 host-sampled identity, 3 device
+    std::vector<int> pick_of(nops, -1);
+    int nch = 0;
+    std::vector<double> G;
+    for (int i = 0; i < nops; ++i) {
+        if (ops[i].nkraus == 0) continue;
+        const int D = 1 << ops[i].k, nK = ops[i].nkraus;
+        const size_t msz = size_t(2) * D * D;
+        G.assign(msz * nK, 0.0);
+        bool mixture = true;
+        std::vector<double> p(nK);
+        for (int j = 0; j < nK; ++j) {
+            gram(D, ops[i].matrix + j * msz, G.data() + j * msz);
+            p[j] = scalar_of(D, G.data() + j * msz);
+            mixture = mixture && p[j] >= 0;
+        }
+        if (mixture) {
+            double total = 0;
+            for (double v : p) total += v;
+            if (!(total > 0)) {
+                set_last_error_text("hq_run_trajectory: a channel whose Kraus operators are all zero");
+                return HQ_ERR_ARG;
+            }
+            const double target = u[nch] * total;
+            int pick = -1;
+            double cum = 0;
+            for (int j = 0; j < nK; ++j) {
+                cum += p[j];
+                if (p[j] > 0) pick = j;
+                if (cum > target && p[j] > 0) {
+                    pick = j;
+                    break;
+                }
+            }
+            std::vector<double> m(ops[i].matrix + pick * msz, ops[i].matrix + (pick + 1) * msz);
+            const double sc = 1.0 / std::sqrt(p[pick]);
+            bool identity = true;
+            for (int r = 0; r < D; ++r)
+                for (int c = 0; c < D; ++c) {
+                    m[2 * (r * D + c)] *= sc;
+                    m[2 * (r * D + c) + 1] *= sc;
+                    identity = identity && std::hypot(m[2 * (r * D + c)] - (r == c ? 1.0 : 0.0),
+                                                      m[2 * (r * D + c) + 1]) <= 4.0 * 2.220446049250313e-16;
+                }
+            plan[i] = identity ? 2 : 1;
+            pick_of[i] = pick;
+            if (chosen) chosen[nch] = pick;
+            kept.push_back(std::move(m));
+        } else {
+            plan[i] = 3;
+            Dev d{i, nch, hostbuf.size(), 0};
+            hostbuf.insert(hostbuf.end(), ops[i].matrix, ops[i].matrix + msz * nK);
+            d.goff = hostbuf.size();
+            hostbuf.insert(hostbuf.end(), G.begin(), G.end());
+            dev.push_back(d);
+        }
+        ++nch;
+    }
+    // device workspace: operator data, uniforms, partial sums, the selected
+    // operator, chosen indices, status
+    const size_t uoff = hostbuf.size();
+    for (const Dev &d : dev) hostbuf.push_back(u[d.ch]);
+    const int width = 2 * rdm_entries<2>();
+    const int grid = std::max(dt == HQ_C64 ? std::max(rdm_grid<float, 1>(n), rdm_grid<float, 2>(n))
+                                           : std::max(rdm_grid<double, 1>(n), rdm_grid<double, 2>(n)), 1);
+    const size_t nd = hostbuf.size() + size_t(grid) * width + 2 * 16 + 1;
+    const size_t bytes = nd * sizeof(double) + sizeof(int) * (dev.size() + 1);
+    char *ws = nullptr;
+    if (!dev.empty()) {
+        if (cudaMallocAsync((void **)&ws, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
+        HQ_CUDA(cudaMemcpyAsync(ws, hostbuf.data(), sizeof(double) * hostbuf.size(), cudaMemcpyHostToDevice, s));
+        HQ_CUDA(cudaMemsetAsync(ws + nd * sizeof(double), 0, sizeof(int) * (dev.size() + 1), s));
+    }
+    double *dbuf = reinterpret_cast<double *>(ws);
+    double *partials = dbuf ? dbuf + hostbuf.size() : nullptr;
+    double *sel = partials ? partials + size_t(grid) * width : nullptr;
+    int *chosen_dev = ws ? reinterpret_cast<int *>(ws + nd * sizeof(double)) : nullptr;
+    int *status_dev = chosen_dev ? chosen_dev + dev.size() : nullptr;
+
+    hq_status st = HQ_OK;
+    std::vector<hq_gate> run;
+    size_t kk = 0, di = 0;
+    auto flush = [&]() -> hq_status {
+        if (run.empty()) return HQ_OK;
+        hq_status r = hq_apply_blocks(state, n, dt, run.data(), int(run.size()), cfg, s);
+        run.clear();
+        return r;
+    };
+    for (int i = 0; i < nops && st == HQ_OK; ++i) {
+        if (plan[i] == 0 || plan[i] == 1) {
+            hq_gate g;
+            std::memset(&g, 0, sizeof(g));
+            g.k = ops[i].k;
+            for (int j = 0; j < g.k; ++j) g.qubits[j] = ops[i].qubits[j];
+            g.matrix = plan[i] == 0 ? ops[i].matrix : kept[kk].data();
+            run.push_back(g);
+        }
+        if (plan[i] == 1 || plan[i] == 2) ++kk;
+        if (plan[i] != 3) continue;
+        if ((st = flush()) != HQ_OK) break;
+        const Dev &d = dev[di];
+        PickArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.partials = partials;
+        a.nK = ops[i].nkraus;
+        a.K = dbuf + d.koff;
+        a.G = dbuf + d.goff;
+        a.u = dbuf + uoff + di;
+        a.chosen = chosen_dev + di;
+        a.sel = sel;
+        a.status = status_dev;
+        if (dt == HQ_C64)
+            st = ops[i].k == 1 ? sample_on_device<float, 1>(state, n, ops[i].qubits, a, s)
+                               : sample_on_device<float, 2>(state, n, ops[i].qubits, a, s);
+        else
+            st = ops[i].k == 1 ? sample_on_device<double, 1>(state, n, ops[i].qubits, a, s)
+                               : sample_on_device<double, 2>(state, n, ops[i].qubits, a, s);
+        ++di;
+    }
+    if (st == HQ_OK) st = flush();
+    if (!ws) return st;
+    std::vector<int> back(dev.size() + 1, 0);
+    if (st == HQ_OK)
+        st = cuda_status("copy chosen", cudaMemcpyAsync(back.data(), chosen_dev, sizeof(int) * back.size(),
+                                                        cudaMemcpyDeviceToHost, s));
+    cudaFreeAsync(ws, s);
+    if (st == HQ_OK) st = cuda_status("sync", cudaStreamSynchronize(s));
+    if (st != HQ_OK) return st;
+    if (back[dev.size()]) {
+        set_last_error_text("hq_run_trajectory: every Kraus operator of a channel annihilates the state");
+        return HQ_ERR_ARG;
+    }
+    if (chosen)
+        for (size_t j = 0; j < dev.size(); ++j) chosen[dev[j].ch] = back[j];
+    return HQ_OK;
 }
 
 }  // namespace hq
