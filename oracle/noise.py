@@ -15,6 +15,11 @@ the CUDA path or its Python binding.
   * ``apply_map(rho, n, qubits, L, R, s)``: the general map of Sec. 5,
     Lambda[X] = sum_ij s_ij L_i X R_j^dag, every operator embedded on
     ``qubits`` of an n-qubit register as a full 2^n x 2^n matrix.
+  * ``apply_superop(rho, n, qubits, S)``: the MatrixSuperGate of Sec. 2 --
+    rho vectorised and multiplied by a 4^k x 4^k matrix S on the entries
+    rho[(a, y), (b, z)] with a, b the local row and column indices of the k
+    qubits (pair index a 2^k + b, qubits[0] the most significant bit of a and
+    of b) and y, z those of the other qubits, which S leaves alone.
   * ``dm_expectation(rho, H)``: Tr(rho H) for a Pauli sum, H built as an
     explicit Kronecker product.
   * ``trajectory_step(psi, n, qubits, kraus, u)``: one step of the pure-state
@@ -29,8 +34,10 @@ trace preserving and reduces to the paper's two operators at e = 0.
 Pinned by ``tests/test_oracle_noise_pins.py``: the depolarizing closed form
 (through a partial trace), the decay of <X> under depolarizing noise during Z
 rotations (the paper's depolarizing figure), amplitude-damping closed forms,
-trace preservation, unitary maps against the state-vector oracle, and the
-trajectory average against the exact map.
+trace preservation, unitary maps against the state-vector oracle, the
+trajectory average against the exact map, and the superoperator against the
+map it vectorises (row-major vec(A X B) = (A (x) B^T) vec(X)) and against
+closed forms that fix its row/column order.
 """
 from __future__ import annotations
 
@@ -116,6 +123,18 @@ def apply_map(rho, n, qubits, L, R=None, s=None):
             if s[i][j] != 0:
                 out += s[i][j] * (li @ rho @ rj.conj().T)
     return out
+
+
+def apply_superop(rho, n, qubits, S):
+    """rho' = S acting on vec(rho) (MatrixSuperGate, Sec. 2): for every pair
+    (y, z) of indices of the other qubits, the 4^k entries rho[(a, y), (b, z)]
+    form a vector indexed by a 2^k + b, and S multiplies it."""
+    k = len(qubits)
+    rest = [q for q in range(n) if q not in qubits]
+    order = list(qubits) + [n + q for q in qubits] + rest + [n + q for q in rest]
+    t = rho.reshape((2,) * (2 * n)).transpose(order).reshape(4 ** k, -1)
+    t = (np.asarray(S, dtype=np.complex128) @ t).reshape((2,) * (2 * n))
+    return t.transpose(np.argsort(order)).reshape(1 << n, 1 << n)
 
 
 def apply_unitary_dm(rho, n, qubits, U):

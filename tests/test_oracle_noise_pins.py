@@ -144,3 +144,56 @@ def test_trajectory_branch_choice_and_average():
         vals.append(oracle.expectation(psi, H))
     vals = np.array(vals)
     assert abs(vals.mean() - exact) <= 5 * vals.std() / np.sqrt(len(vals))
+
+
+def _random_ops(k, count, rng):
+    d = 1 << k
+    return [rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d)) for _ in range(count)]
+
+
+@pytest.mark.parametrize("qs", [[2], [0, 3], [3, 1], [1, 3, 0]])
+def test_superop_vectorises_the_general_map(qs):
+    """Sec. 5's map sum_ij s_ij L_i rho R_j^dag with random non-Hermitian L, R
+    and complex s, through the superoperator S = sum_ij s_ij L_i (x) conj(R_j)
+    (row-major vec(A X B) = (A (x) B^T) vec(X), with B = R^dag): a swapped row
+    and column order, a missing conjugate or a transposed S each fail here."""
+    n = 4
+    rng = np.random.default_rng(11 + len(qs))  # input only
+    k = len(qs)
+    L, R = _random_ops(k, 2, rng), _random_ops(k, 3, rng)
+    s = rng.standard_normal((2, 3)) + 1j * rng.standard_normal((2, 3))
+    rho = random_rho(n, 5)
+    S = sum(s[i, j] * np.kron(L[i], R[j].conj()) for i in range(2) for j in range(3))
+    np.testing.assert_allclose(N.apply_superop(rho, n, qs, S), N.apply_map(rho, n, qs, L, R, s), atol=1e-12)
+
+
+def test_superop_closed_forms():
+    """Row/column order of the pair index fixed by maps with a closed form on
+    qubit q of a random 3-qubit rho (tensor axes: rows 0..2, columns 3..5)."""
+    n, q = 3, 1
+    rho = random_rho(n, 8)
+    t = rho.reshape((2,) * 6)
+    # full depolarization: S = vec(I) vec(I)^T / 2 -> I/2 (x) Tr_q rho
+    vI = np.eye(2).reshape(4)
+    np.testing.assert_allclose(N.apply_superop(rho, n, [q], np.outer(vI, vI) / 2),
+                               N.partial_trace_replace(rho, n, [q]), atol=1e-15)
+    # the partial transpose on q: S[(a, b), (c, d)] = [a == d][b == c]
+    T = np.zeros((4, 4))
+    for a in range(2):
+        for b in range(2):
+            T[2 * a + b, 2 * b + a] = 1
+    want = np.swapaxes(t, q, n + q).reshape(8, 8)
+    np.testing.assert_allclose(N.apply_superop(rho, n, [q], T), want, atol=0)
+    # S[(0, 1), (0, 0)] = 1: row bit 0 and column bit 1 on q receive the
+    # (row 0, column 0) block; everything else becomes 0
+    E = np.zeros((4, 4))
+    E[1, 0] = 1
+    got = N.apply_superop(rho, n, [q], E).reshape((2,) * 6)
+    want = np.zeros_like(t)
+    idx = [slice(None)] * 6
+    src = list(idx)
+    src[q], src[n + q] = 0, 0
+    dst = list(idx)
+    dst[q], dst[n + q] = 0, 1
+    want[tuple(dst)] = t[tuple(src)]
+    np.testing.assert_allclose(got, want, atol=0)
