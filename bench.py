@@ -411,6 +411,38 @@ def measure_extras(args):
                                      "z0_mean": float(np.mean(z)), "timing": "wall clock, host waits included"}
     del st
     torch.cuda.empty_cache()
+    # n=15 noisy circuit at the density-matrix level (Sec. 5): rho as a
+    # 30-qubit vector (8 GiB), every gate and channel as its superoperator
+    # (Sec. 2 MatrixSuperGate), fused into <= 6 vector-qubit blocks on the
+    # tensor cores; the same circuit and channels as the trajectories above
+    c15 = C.random_circuit(C.layout_for(15), 10, seed=args.seed, two_qubit="cz")
+    ops15 = C.noisy_ops(c15, p1=1e-3, p2=1e-2, gamma=1e-3)
+    t_h = time.perf_counter()
+    sup = [(tuple(qs) + tuple(15 + q for q in qs), hq.hq_dm_superop([m] if kind == "gate" else m))
+           for kind, qs, m in ops15]
+    bdm = hq.hq_fuse(30, sup, 6, method="dag", restarts=8, seed=0)  # as hq_dm_apply fuses
+    t_h = time.perf_counter() - t_h
+    st, t_dm = _time_blocks(30, bdm, "tc_f16", torch.complex64)
+    rho = st.view(1 << 15, 1 << 15)
+    tr = hq.hq_dm_expectation(rho, [(1.0, ())])
+    z0 = hq.hq_dm_expectation(rho, [(1.0, ((0, "Z"),))])
+    pur = hq.hq_dm_purity(rho)
+    reps = 3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        hq.hq_dm_init(rho)
+        hq.hq_dm_apply(rho, ops15, k_max=6, engine="tc_f16")
+    torch.cuda.synchronize()
+    t_api = (time.perf_counter() - t0) / reps
+    out["n15_density_matrix"] = {
+        "ops": len(ops15), "gates": len(c15.gates), "channels": sum(1 for o in ops15 if o[0] == "kraus"),
+        "vector_qubits": 30, "blocks": len(bdm), "device_s": t_dm, "noisy_ops_per_s": len(ops15) / t_dm,
+        "GBps_per_block": 2 * 8 * 2 ** 30 * len(bdm) / t_dm / 1e9, "api_s": t_api,
+        "api_note": "hq_dm_apply wall clock: host superoperators and fusion included",
+        "host_superop_and_fuse_s": t_h, "trace": tr, "z0": z0, "purity": pur}
+    del st, rho
+    torch.cuda.empty_cache()
     # n=33: fused k <= 6 on tensor cores vs CUDA cores (64 GiB state)
     c33 = C.config_n33(seed=args.seed)
     b33 = fuse(hq, 33, c33.gates, 6, args)

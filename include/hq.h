@@ -178,8 +178,8 @@ hq_status hq_reduced_density_matrix(const void *state, int n, hq_dtype dt, const
  * hq_apply_kraus_sampled -- Sec. 5 pure-state sampling of the Kraus
  * operators K_0..K_{nK-1} of a channel on k <= 2 qubits: p_i = ||K_i psi||^2
  * (from the operators alone when every K_i^dag K_i is a multiple of the
- * identity, e.g. Pauli channels; else Tr(K_i rho K_i^dag) from
- * hq_reduced_density_matrix, synchronous), i = the first index whose
+ * identity, e.g. Pauli channels; else Tr(K_i rho K_i^dag) from the
+ * reduced density matrix, on the device), i = the first index whose
  * cumulative probability exceeds u * sum p, then psi <- K_i psi / sqrt(p_i).
  *   kraus:  nK matrices of 2^k x 2^k complex128, row-major, one after another.
  *   u:      a uniform number in [0, 1) drawn by the caller.
@@ -205,11 +205,99 @@ typedef struct {
  * entry of u.
  *   u:      one uniform in [0, 1) per channel, in operation order.
  *   chosen: out (may be NULL), the sampled Kraus index per channel.
- * Synchronous at every channel whose probabilities depend on the state.
+ * Channels whose operators all have K_i^dag K_i = p_i I are sampled on the
+ * host from p_i alone; the others on the device (reduced density matrix,
+ * branch and renormalised operator picked by one CTA, no host round trip).
+ * Synchronous once, at the end, when a channel was sampled on the device.
  * Errors: as hq_apply_gate and hq_apply_kraus_sampled; HQ_ERR_ARG (nops < 0).
  */
 hq_status hq_run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops, int nops, const double *u,
                             int *chosen, const hq_config *cfg, void *stream);
+
+/*
+ * Density matrices -- Sec. 5 ("Simulations with noise"): exact evolution of
+ * rho under maps Lambda[X] = sum_ij s_ij L_i X R_j^dag (Sec. 2's
+ * KrausSuperGate), each applied, as Sec. 2's MatrixSuperGate does, as one
+ * matrix-vector product on the vectorised rho.
+ * Layout: rho (2^n x 2^n) is the 2n-qubit state vector vec(rho), row-major:
+ * entry (x, y) at flat index x 2^n + y, so (in the state-vector conventions
+ * above) qubit q of the row index is vector qubit q and qubit q of the
+ * column index is vector qubit n + q.  4^n complex entries in DEVICE memory,
+ * complex64 or complex128, 16-byte aligned, caller-owned; 1 <= n <= 17.
+ * The map of a k-qubit operation is the 2k-qubit gate
+ *   S = sum_ij s_ij L_i (x) conj(R_j)   (row-major vec(A X B) = (A (x) B^T) vec X)
+ * on vector qubits (q_0..q_{k-1}, n+q_0..n+q_{k-1}): its pair index is
+ * a 2^k + b for the local row index a and column index b (qubits[0] the most
+ * significant bit of each).
+ */
+#define HQ_DM_MAX_K 3      /* widest operation: its superoperator spans 2k <= HQ_MAX_K vector qubits */
+#define HQ_DM_MAX_OPS 4096 /* most left (or right) operators of one map */
+#define HQ_DM_MAP 0        /* Lambda[rho] = sum_ij s_ij L_i rho R_j^dag (KrausSuperGate) */
+#define HQ_DM_SUPER 1      /* a 4^k x 4^k superoperator matrix on the pair index (MatrixSuperGate) */
+typedef struct {
+    int kind;             /* HQ_DM_MAP or HQ_DM_SUPER */
+    int k;                /* 1..HQ_DM_MAX_K */
+    int qubits[HQ_DM_MAX_K];
+    int nl, nr;           /* HQ_DM_MAP: numbers of left and right operators */
+    const double *left;   /* HQ_DM_MAP: nl matrices 2^k x 2^k, one after another; HQ_DM_SUPER: the
+                             4^k x 4^k matrix.  complex128, row-major, host */
+    const double *right;  /* HQ_DM_MAP: nr matrices, or NULL for R = L (nr ignored) */
+    const double *s;      /* HQ_DM_MAP: nl x nr complex128 coefficients, row-major, or NULL for the
+                             identity (needs nl == nr) */
+} hq_dm_op;
+/* A unitary gate U: HQ_DM_MAP, nl = 1, left = U, right = s = NULL (rho -> U rho U^dag).
+   A Kraus channel {K_i}: HQ_DM_MAP, nl = number of operators, right = s = NULL. */
+
+/*
+ * hq_dm_superop -- the superoperator S of a map (host, FP64; see above):
+ * S_out receives 2 * 16^k doubles (4^k x 4^k complex, row-major).
+ * Errors: HQ_ERR_NULL, HQ_ERR_K_TOO_LARGE (k outside [1, HQ_DM_MAX_K]),
+ * HQ_ERR_ARG (nl or nr outside [1, HQ_DM_MAX_OPS]; s == NULL with nr != nl).
+ */
+hq_status hq_dm_superop(int k, int nl, const double *left, int nr, const double *right, const double *s,
+                        double *S_out);
+
+/*
+ * hq_dm_init -- rho = |psi0><psi0| for the product state of hq_state_init's
+ * tokens (NULL: |0..0><0..0|); written as the 2n-qubit product state with
+ * the tokens repeated (the token amplitudes are real).  Device write of 4^n
+ * entries on `stream`.  Errors: as hq_state_init (n outside [1, 17]:
+ * HQ_ERR_N_TOO_LARGE).
+ */
+hq_status hq_dm_init(void *rho, int n, hq_dtype dt, const char *tokens, void *stream);
+
+/*
+ * hq_dm_apply -- rho <- Lambda_nops ... Lambda_1 [rho] exactly (the density-
+ * matrix level of Sec. 5).  Every operation becomes its superoperator (host,
+ * FP64); with k_max >= 2 they are fused by hq_fuse_dag into blocks of at most
+ * k_max vector qubits (8 seeded runs, seed 0); k_max = 0 applies one block per
+ * operation.  The blocks run through hq_apply_blocks with cfg (NULL =
+ * HQ_ENGINE_AUTO) on the 2n-qubit vector, asynchronously on `stream`.
+ * Errors: as hq_dm_init and hq_apply_blocks; HQ_ERR_ARG (nops < 0, k_max
+ * outside [0, HQ_MAX_K], unknown kind, operator counts as hq_dm_superop),
+ * HQ_ERR_K_TOO_LARGE (an operation with 2k > k_max > 0), HQ_ERR_QUBIT_RANGE,
+ * HQ_ERR_DUP_QUBIT.
+ */
+hq_status hq_dm_apply(void *rho, int n, hq_dtype dt, const hq_dm_op *ops, int nops, int k_max, const hq_config *cfg,
+                      void *stream);
+
+/*
+ * hq_dm_expectation -- Tr(rho H) = sum_t coeff_t sum_x rho[x][x ^ m_t] P_t[x ^ m_t][x]
+ * for a Pauli sum (hq_pauli_term, as hq_expectation; len 0 gives Tr rho),
+ * the real part, accumulated in double: reads 2^n of the 4^n entries per
+ * term.  SYNCHRONISES `stream`; device scratch (per-CTA partial sums) from
+ * the stream-ordered allocator, released before returning.
+ * Errors: as hq_expectation (n outside [1, 17]: HQ_ERR_N_TOO_LARGE).
+ */
+hq_status hq_dm_expectation(const void *rho, int n, hq_dtype dt, const hq_pauli_term *terms, int T,
+                            double *out_host, void *stream);
+
+/*
+ * hq_dm_purity -- Tr(rho^2) = sum_xy |rho_xy|^2 for a Hermitian rho (the
+ * squared norm of vec(rho), as hq_expectation computes it).  SYNCHRONISES
+ * `stream`.  Errors: as hq_dm_expectation.
+ */
+hq_status hq_dm_purity(const void *rho, int n, hq_dtype dt, double *out_host, void *stream);
 
 /*
  * hq_pop -- Sec. 3.1 pop(circuit, pinned_qubits): mark the gates inside the

@@ -229,5 +229,6 @@ hq_status pass_error_status();
 
 // validation helpers (hq_api.cu)
 hq_status check_qubits(int n, int k, const int *qubits, int kmax);
+hq_status check_terms(int n, const hq_pauli_term *terms, int T);
 
 }  // namespace hq

@@ -63,6 +63,16 @@ class hq_noisy_op(ctypes.Structure):
                 ("matrix", ctypes.c_void_p)]
 
 
+HQ_DM_MAX_K = 3
+HQ_DM_MAP, HQ_DM_SUPER = 0, 1
+
+
+class hq_dm_op(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("k", ctypes.c_int), ("qubits", ctypes.c_int * HQ_DM_MAX_K),
+                ("nl", ctypes.c_int), ("nr", ctypes.c_int), ("left", ctypes.c_void_p), ("right", ctypes.c_void_p),
+                ("s", ctypes.c_void_p)]
+
+
 class hq_config(ctypes.Structure):
     _fields_ = [("engine", ctypes.c_int), ("tc_min_k", ctypes.c_int)]
 
@@ -102,6 +112,11 @@ def load(path: str | None = None):
         "hq_apply_kraus_sampled": ([V, I, I, V, I, I, V, ctypes.c_double, V, V], I),
         "hq_run_trajectory": ([V, I, I, V, I, V, V, V, V], I),
         "hq_simplify": ([I, V, I, I, ctypes.c_double, V], I),
+        "hq_dm_superop": ([I, I, V, I, V, V, V], I),
+        "hq_dm_init": ([V, I, I, ctypes.c_char_p, V], I),
+        "hq_dm_apply": ([V, I, I, V, I, I, V, V], I),
+        "hq_dm_expectation": ([V, I, I, V, I, P(D), V], I),
+        "hq_dm_purity": ([V, I, I, P(D), V], I),
         "hq_plan_passes": ([I, V, I, I, V, I], I),
         "hq_apply_gate": ([V, I, I, V, I, V, V], I),
         "hq_apply_blocks": ([V, I, I, V, I, V, V], I),
@@ -543,3 +558,104 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------
+# density matrices: rho (2^n x 2^n) as the 2n-qubit vector vec(rho), row-major
+# ----------------------------------------------------------------------------
+def _dm_args(rho):
+    ptr, n2, dt = _state_args(rho.reshape(-1))
+    if n2 % 2:
+        raise ValueError("a density matrix has 4^n entries")
+    return ptr, n2 // 2, dt
+
+
+def _ops_block(ops) -> np.ndarray:
+    return np.ascontiguousarray(np.stack([np.asarray(m, np.complex128) for m in ops]), np.complex128)
+
+
+def hq_dm_superop(left, right=None, s=None) -> np.ndarray:
+    """S = sum_ij s_ij L_i (x) conj(R_j) (4^k x 4^k) of the map
+    rho -> sum_ij s_ij L_i rho R_j^dag; right None: R = L; s None: identity."""
+    L = _ops_block(left)
+    k = int(L.shape[1]).bit_length() - 1
+    R = None if right is None else _ops_block(right)
+    sc = None if s is None else np.ascontiguousarray(s, np.complex128)
+    out = np.zeros((4 ** k, 4 ** k), np.complex128)
+    _check(load().hq_dm_superop(k, len(L), L.ctypes.data_as(ctypes.c_void_p), 0 if R is None else len(R),
+                                None if R is None else R.ctypes.data_as(ctypes.c_void_p),
+                                None if sc is None else sc.ctypes.data_as(ctypes.c_void_p),
+                                out.ctypes.data_as(ctypes.c_void_p)), "hq_dm_superop")
+    return out
+
+
+def hq_dm_init(rho, tokens: str | None = None, stream=None):
+    ptr, n, dt = _dm_args(rho)
+    tok = None
+    if tokens is not None:
+        tok = (tokens * n if len(tokens) == 1 else tokens).encode()
+        if len(tok) != n:
+            raise ValueError("need one token per qubit")
+    _check(load().hq_dm_init(ptr, n, dt, tok, _stream(stream)), "hq_dm_init")
+    return rho
+
+
+def hq_dm_apply(rho, ops, k_max: int = 6, engine: str | int = "auto", tc_min_k: int = 4, stream=None):
+    """rho <- the operations in order.  ops: ("gate", qubits, U),
+    ("kraus", qubits, [K_0, ...]), ("map", qubits, (L list, R list or None,
+    s or None)) or ("super", qubits, S)."""
+    ptr, n, dt = _dm_args(rho)
+    ops = list(ops)
+    arr = (hq_dm_op * max(1, len(ops)))()
+    keep: list = []
+    for i, (kind, qs, m) in enumerate(ops):
+        o = arr[i]
+        o.k = len(qs)
+        for j, q in enumerate(qs):
+            o.qubits[j] = int(q)
+        if kind == "super":
+            o.kind = HQ_DM_SUPER
+            S = np.ascontiguousarray(m, np.complex128)
+            keep.append(S)
+            o.left = S.ctypes.data
+            continue
+        o.kind = HQ_DM_MAP
+        if kind == "gate":
+            L, R, sc = [m], None, None
+        elif kind == "kraus":
+            L, R, sc = m, None, None
+        elif kind == "map":
+            L, R, sc = m
+        else:
+            raise ValueError(f"unknown operation {kind!r}")
+        Lb = _ops_block(L)
+        keep.append(Lb)
+        o.nl, o.left = len(Lb), Lb.ctypes.data
+        if R is not None:
+            Rb = _ops_block(R)
+            keep.append(Rb)
+            o.nr, o.right = len(Rb), Rb.ctypes.data
+        if sc is not None:
+            sb = np.ascontiguousarray(sc, np.complex128)
+            keep.append(sb)
+            o.s = sb.ctypes.data
+    cfg = hq_config(ENGINES[engine] if isinstance(engine, str) else int(engine), tc_min_k)
+    _check(load().hq_dm_apply(ptr, n, dt, arr, len(ops), int(k_max), ctypes.byref(cfg), _stream(stream)),
+           "hq_dm_apply")
+    return rho
+
+
+def hq_dm_expectation(rho, H, stream=None) -> float:
+    """Tr(rho H) for H = [(coeff, ((qubit, 'X'|'Y'|'Z'), ...)), ...]."""
+    ptr, n, dt = _dm_args(rho)
+    arr, T = _terms_array(H)
+    out = ctypes.c_double(0.0)
+    _check(load().hq_dm_expectation(ptr, n, dt, arr, T, ctypes.byref(out), _stream(stream)), "hq_dm_expectation")
+    return out.value
+
+
+def hq_dm_purity(rho, stream=None) -> float:
+    ptr, n, dt = _dm_args(rho)
+    out = ctypes.c_double(0.0)
+    _check(load().hq_dm_purity(ptr, n, dt, ctypes.byref(out), _stream(stream)), "hq_dm_purity")
+    return out.value
