@@ -12,6 +12,9 @@
 //     parameter space (uniform constant-bank operands of the FMAs), and streams
 //     the tile back.  An XOR swizzle of the shared-memory index keeps both the
 //     linear copy and the strided group access free of bank conflicts.
+//     complex64 runs k_gather_pipe, the same with two tile buffers: the
+//     cp.async copy of the next tile is in flight while the current one is
+//     multiplied and stored.
 //   * k_diag<R, K>: diagonal gates (CZ, RZ, CPHASE and fused diagonal blocks)
 //     need no gather: out[x] = d[r(x)] * in[x], a pure stream.
 //   * k_mono<R, K> (K <= 4): monomial gates, one nonzero per row and column
@@ -259,59 +262,149 @@ __device__ __forceinline__ void gather_rows_acc(const MatParam<R, K> &m, const t
     }
 }
 
+// One tile in shared memory multiplied in place (every group of 2^K
+// amplitudes by the matrix); ends with a barrier.
+template <typename R, int K>
+__device__ __forceinline__ void gather_tile(const TileGeom &g, const MatParam<R, K> &m, typename C2<R>::type *tile)
+{
+    using T2 = typename C2<R>::type;
+    constexpr int NR = gather_rows<K>(), TPG = gather_tpg<K>(), NI = gather_items<R, K>();
+    const int ngroups = (1 << g.L) >> K;
+    if constexpr (TPG == 1) {
+        for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
+            const int ib = group_base<K>(g, grp);
+            T2 acc[NR];
+            gather_rows_acc<R, K, 0>(m, tile, ib, g, acc);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) tile[swz<R>(ib + g.toff[r])] = acc[r];
+        }
+        __syncthreads();
+    } else {
+        T2 acc[NI][NR];
+        int ibs[NI], chunk[NI];
+#pragma unroll
+        for (int it = 0; it < NI; ++it) {
+            const int w = it * kThreads + threadIdx.x;
+            const int wi = w >> 5;
+            chunk[it] = wi % TPG;
+            const int grp = (wi / TPG) * 32 + (w & 31);
+            ibs[it] = -1;
+            if (grp < ngroups) {
+                ibs[it] = group_base<K>(g, grp);
+                switch (chunk[it]) {
+                case 0: gather_rows_acc<R, K, 0>(m, tile, ibs[it], g, acc[it]); break;
+                case 1: gather_rows_acc<R, K, NR>(m, tile, ibs[it], g, acc[it]); break;
+                case 2: gather_rows_acc<R, K, (2 * NR) % (1 << K)>(m, tile, ibs[it], g, acc[it]); break;
+                default: gather_rows_acc<R, K, (3 * NR) % (1 << K)>(m, tile, ibs[it], g, acc[it]); break;
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < NI; ++it)
+            if (ibs[it] >= 0)
+#pragma unroll
+                for (int rr = 0; rr < NR; ++rr) tile[swz<R>(ibs[it] + g.toff[chunk[it] * NR + rr])] = acc[it][rr];
+        __syncthreads();
+    }
+}
+
 template <typename R, int K>
 __global__ void __launch_bounds__(kThreads) k_gather(const TileGeom g, const MatParam<R, K> m,
                                                      typename C2<R>::type *__restrict__ state)
 {
     using T2 = typename C2<R>::type;
-    constexpr int NR = gather_rows<K>(), TPG = gather_tpg<K>(), NI = gather_items<R, K>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2 *tile = reinterpret_cast<T2 *>(smem_raw);
-    const int ngroups = (1 << g.L) >> K;
     for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x) {
         T2 *base = state + tile_base(g, t);
         tile_load(g, base, tile);
         __syncthreads();
-        if constexpr (TPG == 1) {
-            for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
-                const int ib = group_base<K>(g, grp);
-                T2 acc[NR];
-                gather_rows_acc<R, K, 0>(m, tile, ib, g, acc);
-#pragma unroll
-                for (int r = 0; r < NR; ++r) tile[swz<R>(ib + g.toff[r])] = acc[r];
-            }
-            __syncthreads();
-        } else {
-            T2 acc[NI][NR];
-            int ibs[NI], chunk[NI];
-#pragma unroll
-            for (int it = 0; it < NI; ++it) {
-                const int w = it * kThreads + threadIdx.x;
-                const int wi = w >> 5;
-                chunk[it] = wi % TPG;
-                const int grp = (wi / TPG) * 32 + (w & 31);
-                ibs[it] = -1;
-                if (grp < ngroups) {
-                    ibs[it] = group_base<K>(g, grp);
-                    switch (chunk[it]) {
-                    case 0: gather_rows_acc<R, K, 0>(m, tile, ibs[it], g, acc[it]); break;
-                    case 1: gather_rows_acc<R, K, NR>(m, tile, ibs[it], g, acc[it]); break;
-                    case 2: gather_rows_acc<R, K, (2 * NR) % (1 << K)>(m, tile, ibs[it], g, acc[it]); break;
-                    default: gather_rows_acc<R, K, (3 * NR) % (1 << K)>(m, tile, ibs[it], g, acc[it]); break;
-                    }
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int it = 0; it < NI; ++it)
-                if (ibs[it] >= 0)
-#pragma unroll
-                    for (int rr = 0; rr < NR; ++rr) tile[swz<R>(ibs[it] + g.toff[chunk[it] * NR + rr])] = acc[it][rr];
-            __syncthreads();
-        }
+        gather_tile<R, K>(g, m, tile);
         tile_store(g, base, tile);
         __syncthreads();
     }
+}
+
+// ----------------------------------------------------------------------------
+// gather kernel with the next tile's load in flight (complex64)
+//
+// Two tile buffers per CTA: the copy of tile t + grid into one (cp.async,
+// global -> shared without registers) is issued before tile t is multiplied
+// and stored from the other, so every CTA keeps a load in flight while it
+// computes.  The shared-memory layout is k_gather's (swizzled float2): a
+// 16-byte pair whose row swizzle is even lands as one 16-byte copy, one
+// whose swizzle is odd (the two amplitudes trade places) as two 8-byte
+// copies.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void tile_load_async(const TileGeom &g, const float2 *__restrict__ base, float2 *tile)
+{
+    const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
+    for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
+        const float2 *src = base + g.runoff[i >> g.c] + (i & cmask);
+        const int f = (i >> 4) & 15;
+        if (f & 1) {
+            cp_async8(&tile[i ^ f], src);
+            cp_async8(&tile[(i + 1) ^ f], src + 1);
+        } else {
+            cp_async16(&tile[i ^ f], src);
+        }
+    }
+}
+
+// Tile of 2^12 complex64 (32 KB per buffer, 3 CTAs per SM) for K <= 3; 2^11
+// for K = 4, whose 64-register, instruction-bound threads gain from the
+// extra CTAs (n=30, GB/s: K=3 4734-4959 at 12 bits vs 4536-4954 at 11;
+// K=4 2144-2175 vs 2404-2598).
+template <int K> constexpr int gather_pipe_tile_bits() { return K == 4 ? 11 : 12; }
+
+// Every tile of g through `op` (which multiplies a tile in shared memory in
+// place and ends with a barrier), with the copy of the CTA's next tile in
+// flight meanwhile.  Dynamic shared memory: two tiles of 2^g.L complex64.
+template <typename Op>
+__device__ __forceinline__ void tiles_pipelined(const TileGeom &g, float2 *__restrict__ state, Op op)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *cur = reinterpret_cast<float2 *>(smem_raw), *nxt = cur + (1 << g.L);
+    int64_t t = blockIdx.x;
+    if (t >= g.total_tiles) return;
+    tile_load_async(g, state + tile_base(g, t), cur);
+    cp_async_commit();
+    for (; t < g.total_tiles; t += gridDim.x) {
+        const int64_t tn = t + gridDim.x;
+        // nxt was last read by the store of tile t - grid, before the barrier that ended it
+        if (tn < g.total_tiles) tile_load_async(g, state + tile_base(g, tn), nxt);
+        cp_async_commit();  // possibly empty: every thread waits on the same group count
+        cp_async_wait<1>(); // this thread's copies of tile t have landed
+        __syncthreads();    // ... and everyone else's
+        op(cur);
+        tile_store(g, state + tile_base(g, t), cur);
+        __syncthreads();
+        float2 *const tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    cp_async_wait<0>();
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_gather_pipe(const TileGeom g, const MatParam<float, K> m,
+                                                          float2 *__restrict__ state)
+{
+    tiles_pipelined(g, state, [&](float2 *tile) { gather_tile<float, K>(g, m, tile); });
 }
 
 // ----------------------------------------------------------------------------
@@ -322,6 +415,23 @@ template <typename R, int K> struct MonoParam {
     int src[1 << K];                 // tile-local offset of column pi(r) (= g.toff[pi(r)])
 };
 
+// out_r = d_r * in_{pi(r)} for every group of a tile in shared memory; ends with a barrier
+template <typename R, int K>
+__device__ __forceinline__ void mono_tile(const TileGeom &g, const MonoParam<R, K> &m, typename C2<R>::type *tile)
+{
+    using T2 = typename C2<R>::type;
+    const int ngroups = (1 << g.L) >> K;
+    for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
+        const int ib = group_base<K>(g, grp);
+        T2 out[1 << K];
+#pragma unroll
+        for (int r = 0; r < (1 << K); ++r) out[r] = cmul(m.d[r], tile[swz<R>(ib + m.src[r])]);
+#pragma unroll
+        for (int r = 0; r < (1 << K); ++r) tile[swz<R>(ib + g.toff[r])] = out[r];
+    }
+    __syncthreads();
+}
+
 template <typename R, int K>
 __global__ void __launch_bounds__(kThreads) k_mono(const TileGeom g, const MonoParam<R, K> m,
                                                    typename C2<R>::type *__restrict__ state)
@@ -329,23 +439,21 @@ __global__ void __launch_bounds__(kThreads) k_mono(const TileGeom g, const MonoP
     using T2 = typename C2<R>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2 *tile = reinterpret_cast<T2 *>(smem_raw);
-    const int ngroups = (1 << g.L) >> K;
     for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x) {
         T2 *base = state + tile_base(g, t);
         tile_load(g, base, tile);
         __syncthreads();
-        for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
-            const int ib = group_base<K>(g, grp);
-            T2 out[1 << K];
-#pragma unroll
-            for (int r = 0; r < (1 << K); ++r) out[r] = cmul(m.d[r], tile[swz<R>(ib + m.src[r])]);
-#pragma unroll
-            for (int r = 0; r < (1 << K); ++r) tile[swz<R>(ib + g.toff[r])] = out[r];
-        }
-        __syncthreads();
+        mono_tile<R, K>(g, m, tile);
         tile_store(g, base, tile);
         __syncthreads();
     }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads) k_mono_pipe(const TileGeom g, const MonoParam<float, K> m,
+                                                        float2 *__restrict__ state)
+{
+    tiles_pipelined(g, state, [&](float2 *tile) { mono_tile<float, K>(g, m, tile); });
 }
 
 // ----------------------------------------------------------------------------
@@ -610,6 +718,14 @@ static hq_status run_mono(void *state, int n, const int *qubits, const double *m
         m.d[r].y = R(mat[2 * (r * (1 << K) + perm[r]) + 1]);
         m.src[r] = g.toff[perm[r]];
     }
+    if constexpr (sizeof(R) == 4) {
+        // complex64: the next tile's load in flight under the current one
+        const size_t smem = size_t(2 * sizeof(float2)) << g.L;
+        const void *fn = (const void *)k_mono_pipe<K>;
+        const int grid = grid_for(fn, kThreads, smem, g.total_tiles);
+        k_mono_pipe<K><<<grid, kThreads, smem, s>>>(g, m, (float2 *)state);
+        return cuda_status("k_mono_pipe", cudaGetLastError());
+    }
     const size_t smem = size_t(sizeof(typename C2<R>::type)) << g.L;
     const void *fn = (const void *)k_mono<R, K>;
     const int grid = grid_for(fn, kThreads, smem, g.total_tiles);
@@ -628,6 +744,16 @@ static hq_status run_gather(void *state, int n, const int *qubits, const double 
             m.a[r][c].x = R(mat[2 * (r * (1 << K) + c)]);
             m.a[r][c].y = R(mat[2 * (r * (1 << K) + c) + 1]);
         }
+    if constexpr (sizeof(R) == 4) {
+        // complex64: the FP32 work of a tile is short next to its HBM time, so
+        // the next tile's load runs under it (two buffers per CTA)
+        make_geom(g, n, K, qubits, std::min(n, gather_pipe_tile_bits<K>()), nstates);
+        const size_t smem = size_t(2 * sizeof(float2)) << g.L;
+        const void *fn = (const void *)k_gather_pipe<K>;
+        const int grid = grid_for(fn, kThreads, smem, g.total_tiles);
+        k_gather_pipe<K><<<grid, kThreads, smem, s>>>(g, m, (float2 *)state);
+        return cuda_status("k_gather_pipe", cudaGetLastError());
+    }
     const size_t smem = size_t(sizeof(typename C2<R>::type)) << g.L;
     const void *fn = (const void *)k_gather<R, K>;
     const int grid = grid_for(fn, kThreads, smem, g.total_tiles);

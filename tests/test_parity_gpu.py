@@ -104,6 +104,30 @@ def test_apply_gate_every_position_class(hq, dt, k, n):
 
 
 @pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_apply_gate_many_tiles_per_cta(hq, dt, k):
+    """n = 22: 1024 (complex64) or 2048 (complex128) tiles, more than the
+    CTAs of one launch, so every CTA takes several tiles (and the complex64
+    gather kernel's copy of the next tile overlaps the current one)."""
+    n = 22
+    rng = C.SplitMix64(4200 + k)
+    g = np.random.default_rng(77 + k)  # input only
+    psi = g.standard_normal(1 << n) + 1j * g.standard_normal(1 << n)
+    psi /= np.linalg.norm(psi)
+    st = to_dev(psi, dt)
+    sets = qubit_sets(n, k, 5 * k)
+    for qs in sets:
+        M = C.random_unitary(k, rng)
+        # and a monomial gate (permutation times phases: the permute-and-phase kernel)
+        P = np.zeros((1 << k, 1 << k), np.complex128)
+        P[np.arange(1 << k), g.permutation(1 << k)] = np.exp(2j * np.pi * g.random(1 << k))
+        for A in (M, P):
+            hq.hq_apply_gate(st, qs, A)
+            oracle.apply_gate(psi, n, qs, A)
+    assert_close(to_host(st), psi, dt, G=2 * len(sets))
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
 @pytest.mark.parametrize("k", [1, 2, 3, 6])
 def test_apply_gate_k_equals_n(hq, dt, k):
     n = k
