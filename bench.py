@@ -339,6 +339,56 @@ def measure_small_circuit(args, reps: int = 20):
             "batch_runner_us": 1e6 * t_batch, "gate_apps_per_s_batch_runner": len(c12.gates) / t_batch}
 
 
+def measure_adjoint(dtypes=("complex64", "complex128")):
+    """Adjoint gradients: n=20 ansatz, 320 angles, batch 64 (wall clock of
+    one synchronous hq_adjoint_grad call after a warm-up call)."""
+    import torch
+    from paper_2111_06868_gb300 import hq
+
+    ans = C.ansatz(20, 8)
+    H = C.ansatz_hamiltonian(20)
+    th = C.ansatz_params(ans.n_params, 64, seed=0)
+    adj = {}
+    for dt in dtypes:
+        hq.hq_adjoint_grad(ans, H, th[:2], dtype=dt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hq.hq_adjoint_grad(ans, H, th, dtype=dt)
+        t = time.perf_counter() - t0
+        adj[dt] = {"grad_per_s": 64 * ans.n_params / t, "s": t}
+    return adj
+
+
+def measure_trajectories(args, T=8):
+    """Noisy n=24 grid circuit by pure-state sampling of its Kraus channels
+    (Sec. 5): depolarizing after every gate, amplitude damping (whose branch
+    probabilities depend on the state) after every one-qubit gate."""
+    import torch
+    from paper_2111_06868_gb300 import hq
+
+    c24 = C.random_circuit(C.layout_for(24), 12, seed=args.seed, two_qubit="cz")
+    ops = C.noisy_ops(c24, p1=1e-3, p2=1e-2, gamma=1e-3)
+    nch = sum(1 for o in ops if o[0] == "kraus")
+    rng = np.random.default_rng(args.seed)  # the uniforms the sampling draws
+    st = torch.empty(1 << 24, dtype=torch.complex64, device="cuda")
+    hq.hq_state_init(st)
+    hq.hq_run_trajectory(st, ops, rng.random(nch))
+    torch.cuda.synchronize()
+    z = []
+    t0 = time.perf_counter()
+    for _ in range(T):
+        hq.hq_state_init(st)
+        hq.hq_run_trajectory(st, ops, rng.random(nch))
+        z.append(hq.hq_expectation(st, [(1.0, ((0, "Z"),))]))
+    dt_traj = (time.perf_counter() - t0) / T
+    del st
+    torch.cuda.empty_cache()
+    return {"gates": len(c24.gates), "channels": nch,
+            "state_dependent_channels": sum(1 for g in c24.gates if g.k == 1),
+            "trajectories_per_s": 1 / dt_traj, "ms_per_trajectory": 1e3 * dt_traj,
+            "z0_mean": float(np.mean(z)), "timing": "wall clock, host waits included"}
+
+
 def measure_extras(args):
     """One measurement of every other workload (CUDA events)."""
     import torch
@@ -387,30 +437,7 @@ def measure_extras(args):
     out["n30_z0_light_cone"] = {"gates_full": G, "gates_kept": len(kept), "blocks_full": len(b_full),
                                 "blocks_kept": len(b_pop), "s_full": t_full, "s_kept": t_pop,
                                 "speedup": t_full / t_pop, "host_s": t_h, "z0_full": e_full, "z0_kept": e_pop}
-    # noisy n=24 grid circuit, pure-state sampling of its Kraus channels
-    # (Sec. 5): depolarizing after every gate, amplitude damping (whose branch
-    # probabilities depend on the state) after every one-qubit gate
-    c24 = C.random_circuit(C.layout_for(24), 12, seed=args.seed, two_qubit="cz")
-    ops = C.noisy_ops(c24, p1=1e-3, p2=1e-2, gamma=1e-3)
-    nch = sum(1 for o in ops if o[0] == "kraus")
-    rng = np.random.default_rng(args.seed)  # the uniforms the sampling draws
-    st = torch.empty(1 << 24, dtype=torch.complex64, device="cuda")
-    hq.hq_state_init(st)
-    hq.hq_run_trajectory(st, ops, rng.random(nch))
-    torch.cuda.synchronize()
-    T, z = 8, []
-    t0 = time.perf_counter()
-    for _ in range(T):
-        hq.hq_state_init(st)
-        hq.hq_run_trajectory(st, ops, rng.random(nch))
-        z.append(hq.hq_expectation(st, [(1.0, ((0, "Z"),))]))
-    dt_traj = (time.perf_counter() - t0) / T
-    out["n24_noisy_trajectories"] = {"gates": len(c24.gates), "channels": nch,
-                                     "state_dependent_channels": sum(1 for g in c24.gates if g.k == 1),
-                                     "trajectories_per_s": 1 / dt_traj, "ms_per_trajectory": 1e3 * dt_traj,
-                                     "z0_mean": float(np.mean(z)), "timing": "wall clock, host waits included"}
-    del st
-    torch.cuda.empty_cache()
+    out["n24_noisy_trajectories"] = measure_trajectories(args)
     # n=15 noisy circuit at the density-matrix level (Sec. 5): rho as a
     # 30-qubit vector (8 GiB), every gate and channel as its superoperator
     # (Sec. 2 MatrixSuperGate), fused into <= 6 vector-qubit blocks on the
@@ -471,19 +498,7 @@ def measure_extras(args):
     out["n28_subset_rel_l2_vs_fp64"] = {"gates": len(c28.gates), **errs, "bar": 2e-5}
     del st, ref
     torch.cuda.empty_cache()
-    # adjoint gradients: n=20 ansatz, 320 angles, batch 64
-    ans = C.ansatz(20, 8)
-    H = C.ansatz_hamiltonian(20)
-    th = C.ansatz_params(ans.n_params, 64, seed=0)
-    adj = {}
-    for dt in ("complex64", "complex128"):
-        hq.hq_adjoint_grad(ans, H, th[:2], dtype=dt)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hq.hq_adjoint_grad(ans, H, th, dtype=dt)
-        t = time.perf_counter() - t0
-        adj[dt] = {"grad_per_s": 64 * ans.n_params / t, "s": t}
-    out["adjoint_n20_batch64"] = adj
+    out["adjoint_n20_batch64"] = measure_adjoint()
     # batched serving load: 512 circuits, n ~ U{10..24}; largest-first queue
     # (throughput) and smallest-first queue (median latency)
     cs = C.config_batch(512, seed=0)
@@ -544,6 +559,8 @@ def main():
     ap.add_argument("--ref-gates", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", choices=["adjoint", "trajectories"],
+                    help="run one of the extra workloads alone (for profiling) and print its result")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -568,6 +585,10 @@ def main():
     if dist:
         dist.barrier()
     hq.load()
+    if args.only:
+        res = measure_adjoint(("complex64",)) if args.only == "adjoint" else measure_trajectories(args, T=2)
+        print(json.dumps({"only": args.only, **res}))
+        return
 
     circ, desc = workload(args, rank)
     n, G = circ.n, len(circ.gates)

@@ -21,6 +21,7 @@
 #include <cstring>
 #include <vector>
 
+#include "hq_cp_async.cuh"
 #include "hq_internal.cuh"
 #include "hq_adjoint.cuh"
 
@@ -87,9 +88,54 @@ __device__ __forceinline__ void mul2(const T2 (&m)[4], T2 &x0, T2 &x1)
     x1 = y1;
 }
 
+// Copies of one state's tile between global and shared memory.  Element i
+// of the tile is at o(i) = base + (i & (2^r - 1)) + hioff[i >> r] in global
+// memory and at swz(i) in shared memory.  In: cp.async (the caller commits
+// and waits), 16 bytes per pair of amplitudes (complex64; r >= 1 keeps a
+// pair inside one run) or per amplitude (complex128).
+__device__ __forceinline__ void adj_tile_in(float2 *tile, const float2 *src, int64_t base, const int64_t *hioff,
+                                            int r, int TS)
+{
+    const int rmask = (1 << r) - 1;
+    for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
+        const float2 *g = src + base + (i & rmask) + hioff[i >> r];
+        const int f = (i >> 4) & 15;
+        if (f & 1) {
+            cp_async8(&tile[i ^ f], g);
+            cp_async8(&tile[(i + 1) ^ f], g + 1);
+        } else {
+            cp_async16(&tile[i ^ f], g);
+        }
+    }
+}
+__device__ __forceinline__ void adj_tile_in(double2 *tile, const double2 *src, int64_t base, const int64_t *hioff,
+                                            int r, int TS)
+{
+    const int rmask = (1 << r) - 1;
+    for (int i = threadIdx.x; i < TS; i += blockDim.x)
+        cp_async16(&tile[swz<double>(i)], src + base + (i & rmask) + hioff[i >> r]);
+}
+__device__ __forceinline__ void adj_tile_out(const float2 *tile, float2 *dst, int64_t base, const int64_t *hioff,
+                                             int r, int TS)
+{
+    const int rmask = (1 << r) - 1;
+    for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
+        const int f = (i >> 4) & 15;
+        const float4 w = *reinterpret_cast<const float4 *>(&tile[(i ^ f) & ~1]);
+        const float4 v = (f & 1) ? make_float4(w.z, w.w, w.x, w.y) : w;
+        *reinterpret_cast<float4 *>(dst + base + (i & rmask) + hioff[i >> r]) = v;
+    }
+}
+__device__ __forceinline__ void adj_tile_out(const double2 *tile, double2 *dst, int64_t base, const int64_t *hioff,
+                                             int r, int TS)
+{
+    const int rmask = (1 << r) - 1;
+    for (int i = threadIdx.x; i < TS; i += blockDim.x) dst[base + (i & rmask) + hioff[i >> r]] = tile[swz<double>(i)];
+}
+
 // one pass over the tiles of parameter set blockIdx.y
 template <typename R, bool REV>
-__global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const AOp *__restrict__ ops,
+__global__ void __launch_bounds__(kApThreads, sizeof(R) == 4 ? (REV ? 3 : 4) : 2) k_adj_pass(const APass ps, const AOp *__restrict__ ops,
                                                          typename C2<R>::type *__restrict__ phi, int64_t lam_off,
                                                          int64_t stride, const double2 *__restrict__ cs, int P,
                                                          double *__restrict__ partials, int batch)
@@ -101,9 +147,17 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
     T2 *tl = tp + TS;
     __shared__ double gacc[kApMaxRot];
     __shared__ __align__(16) double2 sweep_mat[kSweepOps * 2 * 4];  // one sweep's 2x2 matrices (T2)
+    __shared__ int64_t hioff[1 << kApMaxHigh];  // global offset of the tile's high-bit pattern h
     const int b = blockIdx.y;
     if (REV)
         for (int j = threadIdx.x; j < ps.nrot; j += blockDim.x) gacc[j] = 0.0;
+    for (int h = threadIdx.x; h < (1 << ps.nh); h += blockDim.x) {
+        int64_t o = 0;
+        for (int j = 0; j < ps.nh; ++j)
+            if ((h >> j) & 1) o += int64_t(1) << ps.hb[j];
+        hioff[h] = o;
+    }
+    __syncthreads();
     T2 *sphi = phi + int64_t(b) * stride;
     T2 *slam = sphi + lam_off;
     const double2 *scs = cs + int64_t(b) * P;
@@ -114,18 +168,10 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
             base = ((base >> hb) << (hb + 1)) | (base & ((int64_t(1) << hb) - 1));
         }
         // element i of the tile: its R low bits, then its high bits at hb[]
-        auto off = [&](int i) {
-            int64_t o = base + (i & ((1 << ps.R) - 1));
-            const int hi = i >> ps.R;
-            for (int j = 0; j < ps.nh; ++j)
-                if ((hi >> j) & 1) o += int64_t(1) << ps.hb[j];
-            return o;
-        };
-        for (int i = threadIdx.x; i < TS; i += blockDim.x) {
-            const int64_t o = off(i);
-            tp[swz<R>(i)] = sphi[o];
-            if (REV) tl[swz<R>(i)] = slam[o];
-        }
+        adj_tile_in(tp, sphi, base, hioff, ps.R, TS);
+        if (REV) adj_tile_in(tl, slam, base, hioff, ps.R, TS);
+        cp_async_commit();
+        cp_async_wait<0>();
         __syncthreads();
         // sweeps in circuit order (reverse: last sweep first, its ops backwards)
         for (int q = 0; q < ps.no;) {
@@ -365,11 +411,8 @@ __global__ void __launch_bounds__(kApThreads) k_adj_pass(const APass ps, const A
             __syncthreads();
             q += len;
         }
-        for (int i = threadIdx.x; i < TS; i += blockDim.x) {
-            const int64_t o = off(i);
-            sphi[o] = tp[swz<R>(i)];
-            if (REV) slam[o] = tl[swz<R>(i)];
-        }
+        adj_tile_out(tp, sphi, base, hioff, ps.R, TS);
+        if (REV) adj_tile_out(tl, slam, base, hioff, ps.R, TS);
         __syncthreads();
     }
     if (REV) {

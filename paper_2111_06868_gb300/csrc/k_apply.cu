@@ -36,6 +36,7 @@
 #include <mutex>
 #include <vector>
 
+#include "hq_cp_async.cuh"
 #include "hq_internal.cuh"
 
 namespace hq {
@@ -337,19 +338,6 @@ __global__ void __launch_bounds__(kThreads) k_gather(const TileGeom g, const Mat
 // whose swizzle is odd (the two amplitudes trade places) as two 8-byte
 // copies.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    const unsigned d = unsigned(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src)
-{
-    const unsigned d = unsigned(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
 __device__ __forceinline__ void tile_load_async(const TileGeom &g, const float2 *__restrict__ base, float2 *tile)
 {
     const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
