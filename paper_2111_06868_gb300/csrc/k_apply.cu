@@ -235,24 +235,29 @@ template <typename R, int K> struct MatParam {
 
 constexpr int kThreads = 256;
 
-// Rows of M one thread accumulates, and threads sharing one group.  K <= 2:
-// one thread owns a whole group and writes it back in place at once.  K = 3, 4:
-// a warp takes 32 groups and one 4-row chunk of M (so every lane reads the
-// same, compile-time-indexed M entries: constant-bank operands), holds its
-// accumulators across a barrier, then writes.
-template <int K> __host__ __device__ constexpr int gather_rows() { return K <= 2 ? (1 << K) : 4; }
-template <int K> __host__ __device__ constexpr int gather_tpg() { return (1 << K) / gather_rows<K>(); }
-// work items (group x chunk) per thread for a full tile of 2^Lmax amplitudes
-template <typename R, int K> __host__ __device__ constexpr int gather_items()
+// Rows of M one thread accumulates, and threads sharing one group.  K <= 2,
+// and K = 3 in complex64: one thread owns a whole group and writes it back in
+// place at once (the pipelined complex64 kernel runs 3 CTAs per SM, which
+// leaves room for the 8 inputs and 8 accumulators).  Otherwise (K = 4, and
+// K = 3 in complex128): a warp takes 32 groups and one 4-row chunk of M (so
+// every lane reads the same, compile-time-indexed M entries: constant-bank
+// operands), holds its accumulators across a barrier, then writes.
+template <typename R, int K> __host__ __device__ constexpr int gather_rows()
 {
-    return gather_tpg<K>() == 1 ? 1 : ((1 << ((sizeof(R) == 4 ? 12 : 11) - K)) * gather_tpg<K>()) / kThreads;
+    return K <= 2 ? (1 << K) : (K == 3 && sizeof(R) == 4) ? 8 : 4;
+}
+template <typename R, int K> __host__ __device__ constexpr int gather_tpg() { return (1 << K) / gather_rows<R, K>(); }
+// work items (group x chunk) per thread for a full tile of 2^LB amplitudes
+template <typename R, int K, int LB> __host__ __device__ constexpr int gather_items()
+{
+    return gather_tpg<R, K>() == 1 ? 1 : ((1 << (LB - K)) * gather_tpg<R, K>()) / kThreads;
 }
 
 template <typename R, int K, int R0>
 __device__ __forceinline__ void gather_rows_acc(const MatParam<R, K> &m, const typename C2<R>::type *tile, int ib,
                                                 const TileGeom &g, typename C2<R>::type *acc)
 {
-    constexpr int NR = gather_rows<K>();
+    constexpr int NR = gather_rows<R, K>();
 #pragma unroll
     for (int rr = 0; rr < NR; ++rr) acc[rr].x = acc[rr].y = 0;
 #pragma unroll
@@ -263,13 +268,19 @@ __device__ __forceinline__ void gather_rows_acc(const MatParam<R, K> &m, const t
     }
 }
 
+// Tile of 2^12 complex64 (32 KB per buffer, 3 CTAs per SM) for K <= 3; 2^11
+// for K = 4, whose 64-register, instruction-bound threads gain from the
+// extra CTAs (n=30, GB/s: K=3 4734-4959 at 12 bits vs 4536-4954 at 11;
+// K=4 2144-2175 vs 2404-2598).
+template <int K> constexpr int gather_pipe_tile_bits() { return K == 4 ? 11 : 12; }
+
 // One tile in shared memory multiplied in place (every group of 2^K
 // amplitudes by the matrix); ends with a barrier.
-template <typename R, int K>
+template <typename R, int K, int LB>
 __device__ __forceinline__ void gather_tile(const TileGeom &g, const MatParam<R, K> &m, typename C2<R>::type *tile)
 {
     using T2 = typename C2<R>::type;
-    constexpr int NR = gather_rows<K>(), TPG = gather_tpg<K>(), NI = gather_items<R, K>();
+    constexpr int NR = gather_rows<R, K>(), TPG = gather_tpg<R, K>(), NI = gather_items<R, K, LB>();
     const int ngroups = (1 << g.L) >> K;
     if constexpr (TPG == 1) {
         for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
@@ -321,7 +332,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(const TileGeom g, const Mat
         T2 *base = state + tile_base(g, t);
         tile_load(g, base, tile);
         __syncthreads();
-        gather_tile<R, K>(g, m, tile);
+        gather_tile<R, K, (sizeof(R) == 4 ? 12 : 11)>(g, m, tile);
         tile_store(g, base, tile);
         __syncthreads();
     }
@@ -353,11 +364,6 @@ __device__ __forceinline__ void tile_load_async(const TileGeom &g, const float2 
     }
 }
 
-// Tile of 2^12 complex64 (32 KB per buffer, 3 CTAs per SM) for K <= 3; 2^11
-// for K = 4, whose 64-register, instruction-bound threads gain from the
-// extra CTAs (n=30, GB/s: K=3 4734-4959 at 12 bits vs 4536-4954 at 11;
-// K=4 2144-2175 vs 2404-2598).
-template <int K> constexpr int gather_pipe_tile_bits() { return K == 4 ? 11 : 12; }
 
 // Every tile of g through `op` (which multiplies a tile in shared memory in
 // place and ends with a barrier), with the copy of the CTA's next tile in
@@ -392,7 +398,7 @@ template <int K>
 __global__ void __launch_bounds__(kThreads) k_gather_pipe(const TileGeom g, const MatParam<float, K> m,
                                                           float2 *__restrict__ state)
 {
-    tiles_pipelined(g, state, [&](float2 *tile) { gather_tile<float, K>(g, m, tile); });
+    tiles_pipelined(g, state, [&](float2 *tile) { gather_tile<float, K, gather_pipe_tile_bits<K>()>(g, m, tile); });
 }
 
 // ----------------------------------------------------------------------------

@@ -176,49 +176,21 @@ hq_status launch_rdm(const void *state, int n, hq_dtype dt, const int *qubits, i
 // ----------------------------------------------------------------------------
 // Pure-state sampling of a Kraus channel
 // ----------------------------------------------------------------------------
-// K^dag K as a row-major D x D complex matrix
-static void gram(int D, const double *K, std::vector<double> &G)
-{
-    G.assign(size_t(2) * D * D, 0.0);
-    for (int r = 0; r < D; ++r)
-        for (int c = 0; c < D; ++c) {
-            double gr = 0, gi = 0;
-            for (int m = 0; m < D; ++m) {
-                // conj(K[m][r]) * K[m][c]
-                const double ar = K[2 * (m * D + r)], ai = -K[2 * (m * D + r) + 1];
-                const double br = K[2 * (m * D + c)], bi = K[2 * (m * D + c) + 1];
-                gr += ar * br - ai * bi;
-                gi += ar * bi + ai * br;
-            }
-            G[2 * (r * D + c)] = gr;
-            G[2 * (r * D + c) + 1] = gi;
-        }
-}
-
-// c when G = c I within 1e-12 of G's largest entry, else -1
-static double scalar_of(int D, const std::vector<double> &G)
-{
-    double mx = 0;
-    for (double v : G) mx = std::max(mx, std::fabs(v));
-    const double c = G[0], tol = 1e-12 * std::max(mx, 1e-300);
-    for (int r = 0; r < D; ++r)
-        for (int cc = 0; cc < D; ++cc) {
-            const double wr = r == cc ? c : 0.0;
-            if (std::fabs(G[2 * (r * D + cc)] - wr) > tol || std::fabs(G[2 * (r * D + cc) + 1]) > tol) return -1.0;
-        }
-    return c;
-}
-
 // Device side of a state-dependent channel: k_rdm's partial sums -> the
 // branch (one CTA) -> the renormalised operator applied.  `sel` holds the
 // chosen operator (2 D^2 doubles) and, after it, 1.0 when that operator is
-// the identity to rounding (then nothing is applied).
+// the identity to rounding (then nothing is applied).  The gates that come
+// right before the channel on the same qubits are not applied on their own:
+// their product A is folded in, the branch probabilities taken from
+// A rho A^dag (rho of the state before them) and K_i A / sqrt(p_i) applied,
+// one read of the state and one read-write instead of two more passes.
 constexpr int kMaxKraus = 64;
 struct PickArgs {
     const double *partials;
     int nparts, width, D, nK;
     const double *K;  // nK row-major D x D complex matrices, interleaved re/im
     const double *G;  // their Gram matrices K^dag K
+    const double *A;  // the absorbed gates' product (D x D; the identity when none)
     const double *u;  // the uniform in [0, 1)
     int *chosen;
     double *sel;
@@ -237,12 +209,36 @@ __global__ void __launch_bounds__(kNoiseThreads) k_kraus_pick(const PickArgs a)
     __syncthreads();
     if (threadIdx.x != 0) return;
     const int D = a.D, DD = D * D;
-    double rr[4][4], ri[4][4];
+    double r0r[4][4], r0i[4][4];
     for (int x = 0, e = 0; x < D; ++x)
         for (int y = x; y < D; ++y, ++e) {
-            rr[x][y] = rr[y][x] = tri[2 * e];
-            ri[x][y] = tri[2 * e + 1];
-            ri[y][x] = -tri[2 * e + 1];
+            r0r[x][y] = r0r[y][x] = tri[2 * e];
+            r0i[x][y] = tri[2 * e + 1];
+            r0i[y][x] = -tri[2 * e + 1];
+        }
+    // rho = A rho0 A^dag: T = A rho0, then rho[x][y] = sum_z T[x][z] conj(A[y][z])
+    double tr_[4][4], ti_[4][4], rr[4][4], ri[4][4];
+    for (int x = 0; x < D; ++x)
+        for (int y = 0; y < D; ++y) {
+            double sr = 0, si = 0;
+            for (int z = 0; z < D; ++z) {
+                const double ar = a.A[2 * (x * D + z)], ai = a.A[2 * (x * D + z) + 1];
+                sr += ar * r0r[z][y] - ai * r0i[z][y];
+                si += ar * r0i[z][y] + ai * r0r[z][y];
+            }
+            tr_[x][y] = sr;
+            ti_[x][y] = si;
+        }
+    for (int x = 0; x < D; ++x)
+        for (int y = 0; y < D; ++y) {
+            double sr = 0, si = 0;
+            for (int z = 0; z < D; ++z) {
+                const double br = a.A[2 * (y * D + z)], bi = -a.A[2 * (y * D + z) + 1];
+                sr += tr_[x][z] * br - ti_[x][z] * bi;
+                si += tr_[x][z] * bi + ti_[x][z] * br;
+            }
+            rr[x][y] = sr;
+            ri[x][y] = si;
         }
     double p[kMaxKraus], total = 0;
     for (int i = 0; i < a.nK; ++i) {
@@ -278,7 +274,16 @@ __global__ void __launch_bounds__(kNoiseThreads) k_kraus_pick(const PickArgs a)
     bool identity = true;
     for (int r = 0; r < D; ++r)
         for (int c = 0; c < D; ++c) {
-            const double mr = Kp[2 * (r * D + c)] * sc, mi = Kp[2 * (r * D + c) + 1] * sc;
+            // (K_pick A)[r][c] / sqrt(p_pick)
+            double mr = 0, mi = 0;
+            for (int z = 0; z < D; ++z) {
+                const double kr = Kp[2 * (r * D + z)], ki = Kp[2 * (r * D + z) + 1];
+                const double ar = a.A[2 * (z * D + c)], ai = a.A[2 * (z * D + c) + 1];
+                mr += kr * ar - ki * ai;
+                mi += kr * ai + ki * ar;
+            }
+            mr *= sc;
+            mi *= sc;
             a.sel[2 * (r * D + c)] = mr;
             a.sel[2 * (r * D + c) + 1] = mi;
             identity = identity && hypot(mr - (r == c ? 1.0 : 0.0), mi) <= 4.0 * 2.220446049250313e-16;
@@ -392,16 +397,22 @@ hq_status run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops
     // are sampled here from p_i alone: the chosen, renormalised operator joins
     // the run of gates (nothing at all when it is the identity).  The others
     // are sampled on the device from the state.
-    struct Dev { int op, ch; size_t koff, goff; };
+    struct Dev { int op, ch; size_t koff, goff, aoff; };
     std::vector<Dev> dev;
     std::vector<double> hostbuf;  // K then G of each device-sampled channel, then their uniforms
     std::vector<std::vector<double>> kept;  // renormalised operators the gate runs point into
-    std::vector<int> plan(nops, 0);         // 0 gate, 1 host-sampled (applied), 2 host-sampled identity, 3 device
+    // 0 gate, 1 host-sampled (applied), 2 host-sampled identity, 3 device,
+    // 4 absorbed into the next device-sampled channel
+    std::vector<int> plan(nops, 0);
     std::vector<int> pick_of(nops, -1);
+    std::vector<const double *> mat_of(nops, nullptr);  // the matrix applied for plans 0 and 1
     int nch = 0;
     std::vector<double> G;
     for (int i = 0; i < nops; ++i) {
-        if (ops[i].nkraus == 0) continue;
+        if (ops[i].nkraus == 0) {
+            mat_of[i] = ops[i].matrix;
+            continue;
+        }
         const int D = 1 << ops[i].k, nK = ops[i].nkraus;
         const size_t msz = size_t(2) * D * D;
         G.assign(msz * nK, 0.0);
@@ -444,12 +455,43 @@ hq_status run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops
             pick_of[i] = pick;
             if (chosen) chosen[nch] = pick;
             kept.push_back(std::move(m));
+            if (!identity) mat_of[i] = kept.back().data();
         } else {
             plan[i] = 3;
-            Dev d{i, nch, hostbuf.size(), 0};
+            Dev d{i, nch, hostbuf.size(), 0, 0};
             hostbuf.insert(hostbuf.end(), ops[i].matrix, ops[i].matrix + msz * nK);
             d.goff = hostbuf.size();
             hostbuf.insert(hostbuf.end(), G.begin(), G.end());
+            // absorb the operators applied right before, on the same qubits in
+            // the same order (identity branches in between apply nothing):
+            // A = M_last ... M_first
+            std::vector<double> A(msz, 0.0), T(msz);
+            for (int r = 0; r < D; ++r) A[2 * (r * D + r)] = 1.0;
+            for (int j = i - 1; j >= 0; --j) {
+                if (plan[j] == 2) continue;
+                if (plan[j] != 0 && plan[j] != 1) break;
+                if (ops[j].k != ops[i].k) break;
+                bool same = true;
+                for (int q = 0; q < ops[i].k; ++q) same = same && ops[j].qubits[q] == ops[i].qubits[q];
+                if (!same) break;
+                const double *M = mat_of[j];  // A <- A M (M came before the ops already in A)
+                for (int r = 0; r < D; ++r)
+                    for (int c = 0; c < D; ++c) {
+                        double tr = 0, ti = 0;
+                        for (int z = 0; z < D; ++z) {
+                            const double ar = A[2 * (r * D + z)], ai = A[2 * (r * D + z) + 1];
+                            const double mr = M[2 * (z * D + c)], mi = M[2 * (z * D + c) + 1];
+                            tr += ar * mr - ai * mi;
+                            ti += ar * mi + ai * mr;
+                        }
+                        T[2 * (r * D + c)] = tr;
+                        T[2 * (r * D + c) + 1] = ti;
+                    }
+                A.swap(T);
+                plan[j] = 4;
+            }
+            d.aoff = hostbuf.size();
+            hostbuf.insert(hostbuf.end(), A.begin(), A.end());
             dev.push_back(d);
         }
         ++nch;
@@ -477,7 +519,7 @@ hq_status run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops
 
     hq_status st = HQ_OK;
     std::vector<hq_gate> run;
-    size_t kk = 0, di = 0;
+    size_t di = 0;
     auto flush = [&]() -> hq_status {
         if (run.empty()) return HQ_OK;
         hq_status r = hq_apply_blocks(state, n, dt, run.data(), int(run.size()), cfg, s);
@@ -490,10 +532,9 @@ hq_status run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops
             std::memset(&g, 0, sizeof(g));
             g.k = ops[i].k;
             for (int j = 0; j < g.k; ++j) g.qubits[j] = ops[i].qubits[j];
-            g.matrix = plan[i] == 0 ? ops[i].matrix : kept[kk].data();
+            g.matrix = mat_of[i];
             run.push_back(g);
         }
-        if (plan[i] == 1 || plan[i] == 2) ++kk;
         if (plan[i] != 3) continue;
         if ((st = flush()) != HQ_OK) break;
         const Dev &d = dev[di];
@@ -503,6 +544,7 @@ hq_status run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops
         a.nK = ops[i].nkraus;
         a.K = dbuf + d.koff;
         a.G = dbuf + d.goff;
+        a.A = dbuf + d.aoff;
         a.u = dbuf + uoff + di;
         a.chosen = chosen_dev + di;
         a.sel = sel;
