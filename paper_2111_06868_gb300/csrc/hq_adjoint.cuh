@@ -9,6 +9,7 @@ namespace hq {
 
 constexpr int kApMaxHigh = 8;
 constexpr int kApMaxRot = 128;  // rotations per pass (one shared-memory accumulator each)
+constexpr int kApMaxOps = 96;   // ops per pass (complex64: their 2x2 matrices stay in shared memory)
 
 // One gate of a pass, at tile positions tpos (qubits[0], qubits[1]).
 struct AOp {
@@ -25,6 +26,10 @@ struct AOp {
     // op's own quad sweep)
     int sw0, swn, swt;
     int swc;  // the sweep's context position (-1: none)
+    // the sweep's ops in circuit order, bit (byte) j for op j: swrot rotation,
+    // swax its axis, swdiag / swreal its 2x2 matrices diagonal / real (exact
+    // zeros); swprod: their product is 0 general, 1 diagonal, 2 real
+    int swrot, swax, swdiag, swreal, swprod;
 };
 
 struct APass {

@@ -88,6 +88,34 @@ __device__ __forceinline__ void mul2(const T2 (&m)[4], T2 &x0, T2 &x1)
     x1 = y1;
 }
 
+// The 2x2 matrix (adjoint when REV) of a one-qubit or diagonal op on the
+// amplitude pairs of tile position t, for context value cx (diagonal ops on
+// a second position pick their entries by it).
+template <typename T2, bool REV>
+__device__ __forceinline__ void op_mat(const AOp &o, int t, int cx, const double2 *scs, T2 (&mm)[4])
+{
+    if (o.kind == 3) {
+        rot2<T2>(o.axis, scs[o.param], REV, mm);
+    } else if (o.kind == 0) {
+        for (int r = 0; r < 2; ++r)
+            for (int cc = 0; cc < 2; ++cc) mm[r * 2 + cc] = cvt2<T2>(REV ? conj2(o.m[cc * 2 + r]) : o.m[r * 2 + cc]);
+    } else {
+        const int D = 1 << o.k;
+        auto dg = [&](int r) { return cvt2<T2>(REV ? conj2(o.m[r * D + r]) : o.m[r * D + r]); };
+        T2 d0, d1;
+        if (o.k == 1) {
+            if (o.tpos[0] == t) { d0 = dg(0); d1 = dg(1); }
+            else { d0 = dg(cx); d1 = d0; }
+        } else if (o.tpos[0] == t) {
+            d0 = dg(cx); d1 = dg(2 + cx);
+        } else {
+            d0 = dg(2 * cx); d1 = dg(2 * cx + 1);
+        }
+        mm[0] = d0; mm[3] = d1;
+        mm[1].x = 0; mm[1].y = 0; mm[2].x = 0; mm[2].y = 0;
+    }
+}
+
 // Copies of one state's tile between global and shared memory.  Element i
 // of the tile is at o(i) = base + (i & (2^r - 1)) + hioff[i >> r] in global
 // memory and at swz(i) in shared memory.  In: cp.async (the caller commits
@@ -146,7 +174,6 @@ __global__ void __launch_bounds__(kApThreads, sizeof(R) == 4 ? (REV ? 3 : 4) : 2
     T2 *tp = reinterpret_cast<T2 *>(smem_raw);
     T2 *tl = tp + TS;
     __shared__ double gacc[kApMaxRot];
-    __shared__ __align__(16) double2 sweep_mat[kSweepOps * 2 * 4];  // one sweep's 2x2 matrices (T2)
     __shared__ int64_t hioff[1 << kApMaxHigh];  // global offset of the tile's high-bit pattern h
     const int b = blockIdx.y;
     if (REV)
@@ -157,10 +184,38 @@ __global__ void __launch_bounds__(kApThreads, sizeof(R) == 4 ? (REV ? 3 : 4) : 2
             if ((h >> j) & 1) o += int64_t(1) << ps.hb[j];
         hioff[h] = o;
     }
-    __syncthreads();
     T2 *sphi = phi + int64_t(b) * stride;
     T2 *slam = sphi + lam_off;
     const double2 *scs = cs + int64_t(b) * P;
+    // complex64: every pair sweep's 2x2 matrices, built once per CTA (they
+    // depend on the parameter set, not on the tile), after the tiles:
+    // mtab[(q * 2 + cx) * 4 + r] for op q of the pass (reverse: each op's
+    // adjoint; forward: at a sweep's first op, the product of its ops)
+    T2 *mtab = tp + (REV ? 2 * TS : TS);
+    if constexpr (sizeof(R) == 4) {
+        for (int w = threadIdx.x; w < 2 * ps.no; w += blockDim.x) {
+            const int q = w >> 1, cx = w & 1;
+            const AOp &o = ops[ps.o0 + q];
+            if (o.kind == 1 || (!REV && o.sw0 != q)) continue;
+            T2 pm[4];
+            op_mat<T2, REV>(o, o.swt, cx, scs, pm);
+            if (!REV)
+                for (int j = 1; j < o.swn; ++j) {
+                    T2 mm[4], qm[4];
+                    op_mat<T2, REV>(ops[ps.o0 + q + j], o.swt, cx, scs, mm);
+                    for (int r = 0; r < 2; ++r)
+                        for (int cc = 0; cc < 2; ++cc) {
+                            qm[r * 2 + cc].x = 0;
+                            qm[r * 2 + cc].y = 0;
+                            cmac(qm[r * 2 + cc], mm[r * 2], pm[cc]);
+                            cmac(qm[r * 2 + cc], mm[r * 2 + 1], pm[2 + cc]);
+                        }
+                    for (int r = 0; r < 4; ++r) pm[r] = qm[r];
+                }
+            for (int r = 0; r < 4; ++r) mtab[(q * 2 + cx) * 4 + r] = pm[r];
+        }
+    }
+    __syncthreads();
     for (int64_t t = blockIdx.x; t < ps.ntiles; t += gridDim.x) {
         int64_t base = t << ps.R;
         for (int j = 0; j < ps.nh; ++j) {
@@ -264,96 +319,35 @@ __global__ void __launch_bounds__(kApThreads, sizeof(R) == 4 ? (REV ? 3 : 4) : 2
             } else {
                 // pair sweep on tile position t: every op acts on the pair
                 // (x_i0, x_i1) as a 2x2 matrix chosen by the context bit c of
-                // i0 (diagonal ops on another position); the sweep's matrices
-                // are built once into shared memory, then each pair is loaded
-                // once and carried through the ops in order (reverse: adjoints
-                // backwards, each rotation's Im<lambda|P phi> taken just before
-                // its R^+)
+                // i0 (diagonal ops on another position), from the CTA's matrix
+                // table; each pair is loaded once and carried through the ops
+                // in order (reverse: adjoints backwards, each rotation's
+                // Im<lambda|P phi> taken just before its R^+)
                 const int t = last.swt, c = last.swc;
-                T2 *swm = reinterpret_cast<T2 *>(sweep_mat);  // [op][ctx][4]
-                // the 2x2 matrix of op j of the sweep (in application order) for context cx
-                auto op_matrix = [&](int j, int cx, T2 (&mm)[4]) {
-                    const AOp &o = ops[ps.o0 + f + (REV ? len - 1 - j : j)];
-                    if (o.kind == 3) {
-                        rot2<T2>(o.axis, scs[o.param], REV, mm);
-                    } else if (o.kind == 0) {
-                        for (int r = 0; r < 2; ++r)
-                            for (int cc = 0; cc < 2; ++cc)
-                                mm[r * 2 + cc] = cvt2<T2>(REV ? conj2(o.m[cc * 2 + r]) : o.m[r * 2 + cc]);
-                    } else {
-                        const int D = 1 << o.k;
-                        auto dg = [&](int r) { return cvt2<T2>(REV ? conj2(o.m[r * D + r]) : o.m[r * D + r]); };
-                        T2 d0, d1;
-                        if (o.k == 1) {
-                            if (o.tpos[0] == t) { d0 = dg(0); d1 = dg(1); }
-                            else { d0 = dg(cx); d1 = d0; }
-                        } else if (o.tpos[0] == t) {
-                            d0 = dg(cx); d1 = dg(2 + cx);
-                        } else {
-                            d0 = dg(2 * cx); d1 = dg(2 * cx + 1);
-                        }
-                        mm[0] = d0; mm[3] = d1;
-                        mm[1].x = 0; mm[1].y = 0; mm[2].x = 0; mm[2].y = 0;
-                    }
-                };
-                if (REV) {
-                    if (threadIdx.x < len) {
-                        T2 mm[4];
-                        for (int cx = 0; cx < 2; ++cx) {
-                            op_matrix(threadIdx.x, cx, mm);
-                            for (int r = 0; r < 4; ++r) swm[(threadIdx.x * 2 + cx) * 4 + r] = mm[r];
-                        }
-                    }
-                } else if (threadIdx.x < 2) {
-                    // forward: no intermediate states are needed, so the sweep
-                    // is one matrix per context, the product of its ops
-                    const int cx = threadIdx.x;
-                    T2 pm[4], mm[4];
-                    op_matrix(0, cx, pm);
-                    for (int j = 1; j < len; ++j) {
-                        op_matrix(j, cx, mm);
-                        T2 q[4];
-                        for (int r = 0; r < 2; ++r)
-                            for (int cc = 0; cc < 2; ++cc) {
-                                q[r * 2 + cc].x = 0;
-                                q[r * 2 + cc].y = 0;
-                                cmac(q[r * 2 + cc], mm[r * 2], pm[cc]);
-                                cmac(q[r * 2 + cc], mm[r * 2 + 1], pm[2 + cc]);
-                            }
-                        for (int r = 0; r < 4; ++r) pm[r] = q[r];
-                    }
-                    for (int r = 0; r < 4; ++r) swm[cx * 4 + r] = pm[r];
-                }
                 const int nsw = REV ? len : 1;  // matrices applied per pair
                 int ax[kSweepOps];
                 unsigned rotmask = 0, diagmask = 0, realmask = 0;
 #pragma unroll
                 for (int j = 0; j < kSweepOps; ++j) {
                     ax[j] = 0;
-                    if (j < len) {
-                        const AOp &o = ops[ps.o0 + f + (REV ? len - 1 - j : j)];
-                        if (o.kind == 3) {
-                            rotmask |= 1u << j;
-                            ax[j] = o.axis;
+                    if (j < nsw) {
+                        if (REV) {
+                            const int cj = len - 1 - j;  // op j applied = op cj of the sweep in circuit order
+                            if ((last.swrot >> cj) & 1) {
+                                rotmask |= 1u << j;
+                                ax[j] = (last.swax >> (8 * cj)) & 255;
+                            }
+                            if ((last.swdiag >> cj) & 1) diagmask |= 1u << j;
+                            else if ((last.swreal >> cj) & 1) realmask |= 1u << j;
+                        } else if (last.swprod == 1) {
+                            diagmask |= 1u;
+                        } else if (last.swprod == 2) {
+                            realmask |= 1u;
                         }
                     }
                 }
-                __syncthreads();
-                // matrix structure of each applied matrix (exact zeros; uniform
-                // over the CTA): diagonal, or all-real, else general
-#pragma unroll
-                for (int j = 0; j < kSweepOps; ++j) {
-                    if (j >= nsw) break;
-                    bool dg = true, re = true;
-                    for (int cx = 0; cx < 2; ++cx)
-                        for (int r = 0; r < 4; ++r) {
-                            const T2 v = swm[(j * 2 + cx) * 4 + r];
-                            if ((r == 1 || r == 2) && (v.x != 0 || v.y != 0)) dg = false;
-                            if (v.y != 0) re = false;
-                        }
-                    if (dg) diagmask |= 1u << j;
-                    else if (re) realmask |= 1u << j;
-                }
+                // matrix of applied op j, context cx: mt[cx * 4 + r - 8 j] (reverse) / mt[cx * 4 + r] (forward)
+                const T2 *mt = mtab + size_t(REV ? f + len - 1 : f) * 8;
                 R g[kSweepOps];
 #pragma unroll
                 for (int j = 0; j < kSweepOps; ++j) g[j] = 0;
@@ -371,7 +365,7 @@ __global__ void __launch_bounds__(kApThreads, sizeof(R) == 4 ? (REV ? 3 : 4) : 2
                         if (j >= nsw) break;
                         T2 mm[4];
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) mm[r] = swm[(j * 2 + cx) * 4 + r];
+                        for (int r = 0; r < 4; ++r) mm[r] = mt[cx * 4 + r - (REV ? 8 * j : 0)];
                         if (REV && ((rotmask >> j) & 1)) g[j] += pauli_im2(ax[j], x0, x1, l0, l1);
                         if ((diagmask >> j) & 1) {
                             x0 = cmul(mm[0], x0);
@@ -493,12 +487,40 @@ static void build_sweeps(std::vector<AOp> &v, int cap)
         const uint64_t rest = diagpos & ~(uint64_t(1) << t);
         const int ctx = rest ? __builtin_ctzll(rest) : -1;
         const int first = int(out.size());
+        // structure of each op's 2x2 matrices (any context) and of their product
+        int rotm = 0, axes = 0, diagm = 0, realm = 0;
+        for (size_t j = 0; j < sw.size(); ++j) {
+            const AOp &o = v[sw[j]];
+            bool dg = false, re = false;
+            if (o.kind == 3) {
+                rotm |= 1 << j;
+                axes |= (o.axis & 255) << (8 * j);
+                dg = o.axis == 'Z';
+                re = o.axis == 'Y';
+            } else if (o.kind == 0) {
+                dg = o.m[1].x == 0 && o.m[1].y == 0 && o.m[2].x == 0 && o.m[2].y == 0;
+                re = o.m[0].y == 0 && o.m[1].y == 0 && o.m[2].y == 0 && o.m[3].y == 0;
+            } else if (o.kind == 2) {
+                dg = true;
+                re = true;
+                for (int r = 0; r < (1 << o.k); ++r) re = re && o.m[r * (1 << o.k) + r].y == 0;
+            }
+            if (dg) diagm |= 1 << j;
+            if (re) realm |= 1 << j;
+        }
+        const int all = (1 << sw.size()) - 1;
+        const int prod = (diagm == all) ? 1 : (realm == all) ? 2 : 0;
         for (size_t idx : sw) {
             AOp a = v[idx];
             a.sw0 = first;
             a.swn = int(sw.size());
             a.swt = t;
             a.swc = ctx;
+            a.swrot = rotm;
+            a.swax = axes;
+            a.swdiag = diagm;
+            a.swreal = realm;
+            a.swprod = prod;
             out.push_back(a);
         }
     }
@@ -530,7 +552,8 @@ bool adj_plan(int n, hq_dtype dt, const hq_op *ops, int G, AdjPlan &plan)
         }
         const int rot = o.kind == HQ_OP_ROT;
         auto fits = [&](const P &p) {
-            return __builtin_popcountll(p.high | Qh) <= h && p.nrot + rot <= kApMaxRot;
+            return __builtin_popcountll(p.high | Qh) <= h && p.nrot + rot <= kApMaxRot &&
+                   int(p.ops.size()) < kApMaxOps;
         };
         int i = int(ps.size()) - 1;
         while (i >= 0 && !(ps[i].qset & Q)) --i;
@@ -604,7 +627,7 @@ static hq_status launch_pass_t(const APass &ps, const AOp *dev_ops, void *phi, i
                                int P, double *partials, int nbx, cudaStream_t s)
 {
     using T2 = typename C2<R>::type;
-    const size_t smem = sizeof(T2) * (size_t(1) << (ps.R + ps.nh)) * (REV ? 2 : 1);
+    const size_t smem = sizeof(T2) * ((size_t(1) << (ps.R + ps.nh)) * (REV ? 2 : 1) + (sizeof(R) == 4 ? 8 * ps.no : 0));
     occupancy((const void *)k_adj_pass<R, REV>, kApThreads, smem);
     dim3 grid(nbx, batch);
     const int64_t stride = int64_t(1) << n;
