@@ -123,3 +123,46 @@ def test_trajectory_average_converges_to_density_matrix(hq):
         vals.append(hq.hq_expectation(st, H))
     vals = np.array(vals)
     assert abs(vals.mean() - exact) <= 5 * vals.std() / np.sqrt(len(vals)) + 1e-12
+
+
+def random_kraus(k, nK, rng):
+    """nK Kraus operators on k qubits from a random isometry (sum K^dag K = I)."""
+    D = 1 << k
+    A = rng.standard_normal((nK * D, D)) + 1j * rng.standard_normal((nK * D, D))
+    Q, _ = np.linalg.qr(A)
+    return [Q[i * D:(i + 1) * D, :] for i in range(nK)]
+
+
+@pytest.mark.parametrize("dtype", ["complex64", "complex128"])
+def test_trajectory_folds_gates_into_two_qubit_channels(hq, dtype):
+    """State-dependent two-qubit channels right after gates on the same
+    qubits (which the library folds into the channel's sampling) and after
+    gates on the same qubits in the other order or on other qubits (which it
+    applies on their own): branches and states against the oracle."""
+    n = 9
+    rng = np.random.default_rng(21)  # input only
+    srng = C.SplitMix64(5)
+    U = [C.random_unitary(2, srng) for _ in range(4)]
+    V = C.random_unitary(1, srng)
+    ops = [("gate", (2, 5), U[0]), ("gate", (2, 5), U[1]), ("kraus", (2, 5), random_kraus(2, 3, rng)),
+           ("gate", (5, 2), U[2]), ("kraus", (2, 5), random_kraus(2, 2, rng)),
+           ("gate", (7, 0), U[3]), ("gate", (3,), V), ("kraus", (0, 7), random_kraus(2, 4, rng)),
+           ("gate", (3,), V), ("kraus", (3,), C.depolarizing(0.3, 1)), ("kraus", (3,), random_kraus(1, 3, rng)),
+           ("kraus", (2, 5), random_kraus(2, 2, rng))]
+    psi0 = oracle.state_init(n, "+-01+-01+")
+    for trial in range(4):
+        u = rng.random(sum(1 for o in ops if o[0] == "kraus"))
+        psi, want, c = psi0.copy(), [], 0
+        for kind, qs, m in ops:
+            if kind == "gate":
+                psi = oracle.apply_gate(psi, n, qs, m)
+            else:
+                i, psi = N.trajectory_step(psi, n, list(qs), m, u[c])
+                want.append(i)
+                c += 1
+        st = torch.empty(1 << n, dtype=getattr(torch, dtype), device="cuda")
+        hq.hq_state_init(st, "+-01+-01+")
+        got = hq.hq_run_trajectory(st, ops, u)
+        assert got.tolist() == want, trial
+        err = np.abs(st.cpu().numpy().astype(np.complex128) - psi).max()
+        assert err <= (1e-12 if dtype == "complex128" else 2e-6), (trial, err)
