@@ -389,6 +389,34 @@ def measure_trajectories(args, T=8):
             "z0_mean": float(np.mean(z)), "timing": "wall clock, host waits included"}
 
 
+def measure_batch():
+    """Batched serving load: 512 circuits, n ~ U{10..24}, one persistent
+    launch replayed from a CUDA graph; largest-first queue (throughput) and
+    smallest-first queue (median latency)."""
+    import torch
+    from paper_2111_06868_gb300 import hq
+
+    cs = C.config_batch(512, seed=0)
+    Gb = sum(len(c.gates) for c in cs)
+    bres = {}
+    for name, small_first in (("largest_first", 0), ("smallest_first", 1)):
+        b = hq.Batch(cs, None, 13, 7, 0, small_first)
+        b.run()
+        e0, e1 = _events()
+        e0.record()
+        b.run()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        lat, span = b.latencies()
+        bres[name] = {"gate_apps_per_s": Gb / t, "s": t, "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                      "p99_ms": float(np.percentile(lat, 99)) / 1e3}
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+    return {"circuits": len(cs), "gates": Gb, "tile": [13, 7], "launches_per_run": 1, "graph": True, **bres}
+
+
 def measure_extras(args):
     """One measurement of every other workload (CUDA events)."""
     import torch
@@ -400,6 +428,13 @@ def measure_extras(args):
     G = len(circ.gates)
     st, t = _time_blocks(30, [(g.qubits, g.matrix) for g in circ.gates], "auto", torch.complex64)
     out["n30_per_gate_c64"] = {"gate_apps_per_s": G / t, "s": t, "launches": G}
+    del st
+    # the same circuit fused into blocks of <= 4 qubits on the exact FP32
+    # CUDA-core kernels (gather / monomial / diagonal; no tensor cores)
+    b4 = fuse(hq, 30, circ.gates, 4, args)
+    st, t4 = _time_blocks(30, b4, "cuda_core", torch.complex64)
+    out["n30_fused_k4_c64_cuda_core"] = {"blocks": len(b4), "gate_apps_per_s": G / t4, "s": t4,
+                                         "speedup_vs_per_gate": t / t4}
     del st
     # n=30, complex128 (FP64), unfused, on the first 120 gates
     sub = circ.gates[:120]
@@ -499,28 +534,7 @@ def measure_extras(args):
     del st, ref
     torch.cuda.empty_cache()
     out["adjoint_n20_batch64"] = measure_adjoint()
-    # batched serving load: 512 circuits, n ~ U{10..24}; largest-first queue
-    # (throughput) and smallest-first queue (median latency)
-    cs = C.config_batch(512, seed=0)
-    Gb = sum(len(c.gates) for c in cs)
-    bres = {}
-    for name, small_first in (("largest_first", 0), ("smallest_first", 1)):
-        b = hq.Batch(cs, None, 13, 7, 0, small_first)
-        b.run()
-        e0, e1 = _events()
-        e0.record()
-        b.run()
-        e1.record()
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1e3
-        lat, span = b.latencies()
-        bres[name] = {"gate_apps_per_s": Gb / t, "s": t, "p50_ms": float(np.percentile(lat, 50)) / 1e3,
-                      "p99_ms": float(np.percentile(lat, 99)) / 1e3}
-        b.close()
-        del b
-        torch.cuda.empty_cache()
-    out["batch512"] = {"circuits": len(cs), "gates": Gb, "tile": [13, 7], "launches_per_run": 1, "graph": True,
-                       **bres}
+    out["batch512"] = measure_batch()
     out["n12_one_circuit"] = measure_small_circuit(args)
     return out
 
@@ -559,7 +573,7 @@ def main():
     ap.add_argument("--ref-gates", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", choices=["adjoint", "trajectories"],
+    ap.add_argument("--only", choices=["adjoint", "trajectories", "batch"],
                     help="run one of the extra workloads alone (for profiling) and print its result")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -586,7 +600,12 @@ def main():
         dist.barrier()
     hq.load()
     if args.only:
-        res = measure_adjoint(("complex64",)) if args.only == "adjoint" else measure_trajectories(args, T=2)
+        if args.only == "adjoint":
+            res = measure_adjoint(("complex64",))
+        elif args.only == "batch":
+            res = measure_batch()
+        else:
+            res = measure_trajectories(args, T=2)
         print(json.dumps({"only": args.only, **res}))
         return
 

@@ -30,6 +30,7 @@
 #include <mutex>
 #include <vector>
 
+#include "hq_cp_async.cuh"
 #include "hq_internal.cuh"
 
 struct hq_batch {
@@ -96,16 +97,6 @@ __device__ __forceinline__ unsigned long long now_ns()
 
 __device__ __forceinline__ int ld_volatile(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
 
-// tile-local element i (R low bits, then the nh high bits) -> offset in the state
-__device__ __forceinline__ int64_t elem_offset(const BPass &ps, int64_t base, int i)
-{
-    int64_t off = base + (i & ((1 << ps.R) - 1));
-    const int hi = i >> ps.R;
-    for (int j = 0; j < ps.nh; ++j)
-        if ((hi >> j) & 1) off += int64_t(1) << ps.hb[j];
-    return off;
-}
-
 __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -113,6 +104,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
     __shared__ int s_pass, s_stop;
     __shared__ long long s_tile;
     __shared__ BPass s_ps;
+    __shared__ int64_t s_hioff[1 << kBMaxHigh];  // global offset of the tile's high-bit pattern h
     if (threadIdx.x == 0) atomicMin(p.t0, now_ns());
 
     for (;;) {
@@ -184,13 +176,35 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
             const int hb = ps.hb[j];
             base = ((base >> hb) << (hb + 1)) | (base & ((int64_t(1) << hb) - 1));
         }
+        // element i of the tile is at base + (i & rmask) + s_hioff[i >> R]
+        for (int h = threadIdx.x; h < (1 << ps.nh); h += blockDim.x) {
+            int64_t o = 0;
+            for (int j = 0; j < ps.nh; ++j)
+                if ((h >> j) & 1) o += int64_t(1) << ps.hb[j];
+            s_hioff[h] = o;
+        }
+        __syncthreads();
+        const int rmask = (1 << ps.R) - 1;
         // ---------------- load (or build |0..0>) ----------------
         if (ps.first) {
             for (int i = threadIdx.x; i < TS; i += blockDim.x)
                 tile[swz<float>(i)] = make_float2((base == 0 && i == 0) ? 1.f : 0.f, 0.f);
         } else {
-            for (int i = threadIdx.x; i < TS; i += blockDim.x)
-                tile[swz<float>(i)] = __ldcg(cc.state + elem_offset(ps, base, i));
+            // cp.async from L2 (other CTAs wrote the previous pass there), 16
+            // bytes per pair of amplitudes (R >= 1 keeps a pair in one run);
+            // two 8-byte copies where the row swizzle swaps the pair
+            for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
+                const float2 *g = cc.state + base + (i & rmask) + s_hioff[i >> ps.R];
+                const int f = (i >> 4) & 15;
+                if (f & 1) {
+                    cp_async8(&tile[i ^ f], g);
+                    cp_async8(&tile[(i + 1) ^ f], g + 1);
+                } else {
+                    cp_async16(&tile[i ^ f], g);
+                }
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
         }
         __syncthreads();
         // ---------------- gates, in order ----------------
@@ -243,7 +257,12 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
             __syncthreads();
         }
         // ---------------- store, then report the tile ----------------
-        for (int i = threadIdx.x; i < TS; i += blockDim.x) __stcg(cc.state + elem_offset(ps, base, i), tile[swz<float>(i)]);
+        for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
+            const int f = (i >> 4) & 15;
+            const float4 w = *reinterpret_cast<const float4 *>(&tile[(i ^ f) & ~1]);
+            __stcg(reinterpret_cast<float4 *>(cc.state + base + (i & rmask) + s_hioff[i >> ps.R]),
+                   (f & 1) ? make_float4(w.z, w.w, w.x, w.y) : w);
+        }
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
