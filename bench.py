@@ -417,6 +417,28 @@ def measure_batch():
     return {"circuits": len(cs), "gates": Gb, "tile": [13, 7], "launches_per_run": 1, "graph": True, **bres}
 
 
+def measure_expectation(reps=5):
+    """<psi|H|psi> at n=30 (complex64) for the ansatz Hamiltonian (29 ZZ and
+    30 X terms: several X-mask groups, the tiled path), wall clock of the
+    synchronous call."""
+    import torch
+    from paper_2111_06868_gb300 import hq
+
+    H = C.ansatz_hamiltonian(30)
+    st = torch.empty(1 << 30, dtype=torch.complex64, device="cuda")
+    hq.hq_state_init(st, "+")
+    e = hq.hq_expectation(st, H)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        e = hq.hq_expectation(st, H)
+    t = (time.perf_counter() - t0) / reps
+    del st
+    torch.cuda.empty_cache()
+    return {"terms": len(H), "s": t, "value": e, "expected_value": 15.0,
+            "state": "|+>^30: every ZZ term 0, every 0.5 X term 0.5"}
+
+
 def measure_extras(args):
     """One measurement of every other workload (CUDA events)."""
     import torch
@@ -534,6 +556,7 @@ def measure_extras(args):
     del st, ref
     torch.cuda.empty_cache()
     out["adjoint_n20_batch64"] = measure_adjoint()
+    out["n30_expectation_ansatz_hamiltonian"] = measure_expectation()
     out["batch512"] = measure_batch()
     out["n12_one_circuit"] = measure_small_circuit(args)
     return out
@@ -573,7 +596,7 @@ def main():
     ap.add_argument("--ref-gates", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", choices=["adjoint", "trajectories", "batch"],
+    ap.add_argument("--only", choices=["adjoint", "trajectories", "batch", "expect"],
                     help="run one of the extra workloads alone (for profiling) and print its result")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -604,6 +627,8 @@ def main():
             res = measure_adjoint(("complex64",))
         elif args.only == "batch":
             res = measure_batch()
+        elif args.only == "expect":
+            res = measure_expectation()
         else:
             res = measure_trajectories(args, T=2)
         print(json.dumps({"only": args.only, **res}))

@@ -17,6 +17,7 @@
 #include <string>
 #include <vector>
 
+#include "hq_cp_async.cuh"
 #include "hq_internal.cuh"
 
 namespace hq {
@@ -256,17 +257,14 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_tile(const TileExpParams
     for (int64_t tl = blockIdx.x; tl < g.total_tiles; tl += gridDim.x) {
         const int64_t base = tile_base(g, tl);
         const V *src = psi + base;
+        // cp.async: every copy of the tile in flight at once, one wait
         for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
             const int64_t o = g.runoff[i >> g.c] + (i & cmask);
-            if constexpr (sizeof(R) == 4) {
-                const float4 w = *reinterpret_cast<const float4 *>(src + o);
-                tile[i] = make_float2(w.x, w.y);
-                tile[i + 1] = make_float2(w.z, w.w);
-            } else {
-                tile[i] = src[o];
-                tile[i + 1] = src[o + 1];
-            }
+            cp_async16(&tile[i], src + o);
+            if constexpr (sizeof(R) == 8) cp_async16(&tile[i + 1], src + o + 1);
         }
+        cp_async_commit();
+        cp_async_wait<0>();
         for (int k = threadIdx.x; k < p.nt; k += blockDim.x) {
             const R sg = (__popcll(uint64_t(base) & p.t[k].zh) & 1) ? R(-1) : R(1);
             sw[k].x = sg * R(p.t[k].wr);
