@@ -254,11 +254,19 @@ hq_status hq_dm_apply(void *rho, int n, hq_dtype dt, const hq_dm_op *ops, int no
     }
     if (k_max == 0 || nops == 0)
         return hq_apply_blocks(rho, 2 * n, dt, gates.data(), nops, cfg, stream);
-    std::vector<hq_gate> blocks(nops);
-    int B = nops;
-    std::vector<double> bpool(size_t(nops) * (size_t(2) << (2 * k_max)));
-    st = hq_fuse_dag(2 * n, gates.data(), nops, k_max, kDmFuseRestarts, 0, blocks.data(), &B, bpool.data(),
-                     int64_t(bpool.size()), nullptr);
+    // room for a quarter of the ops as blocks first (fusion merges several
+    // ops per block), every op as its own block if that is not enough
+    std::vector<hq_gate> blocks;
+    std::vector<double> bpool;
+    int B = 0;
+    for (int cap : {std::min(nops, 64 + nops / 4), nops}) {
+        blocks.resize(size_t(cap));
+        bpool.assign(size_t(cap) * (size_t(2) << (2 * k_max)), 0.0);
+        B = cap;
+        st = hq_fuse_dag(2 * n, gates.data(), nops, k_max, kDmFuseRestarts, 0, blocks.data(), &B, bpool.data(),
+                         int64_t(bpool.size()), nullptr);
+        if (st != HQ_ERR_CAPACITY) break;
+    }
     if (st != HQ_OK) return st;
     return hq_apply_blocks(rho, 2 * n, dt, blocks.data(), B, cfg, stream);
 }

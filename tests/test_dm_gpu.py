@@ -181,3 +181,26 @@ def test_full_size_noisy_dm_properties(hq):
         sign = 1 - 2 * ((idx >> (n - 1 - q)) & 1).double()
         zq = float((diag * sign).sum())
         assert abs(hq.hq_dm_expectation(rho, [(1.0, ((q, "Z"),))]) - zq) <= 1e-6
+
+
+def test_many_unfusable_maps(hq):
+    """125 two-qubit maps along a chain, none of which can share a 4-vector-
+    qubit block with its neighbours: more blocks than the first fusion
+    attempt makes room for, so the library fuses again with room for all;
+    complex128 against the oracle."""
+    n = 6
+    srng = C.SplitMix64(31)
+    ops = []
+    for r in range(25):
+        for i in range(n - 1):
+            U = C.random_unitary(2, srng)
+            ops.append(("gate", (i, i + 1), U) if r % 2 else ("kraus", (i, i + 1), [np.sqrt(0.9) * U,
+                                                                                     np.sqrt(0.1) * np.eye(4)]))
+    want = oracle_dm(n, ops, "+" * n)
+    rho = torch.empty(1 << n, 1 << n, dtype=torch.complex128, device="cuda")
+    hq.hq_dm_init(rho, "+")
+    hq.hq_dm_apply(rho, ops, k_max=4)
+    assert np.abs(rho.cpu().numpy() - want).max() <= 1e-12
+    blocks = hq.hq_fuse(2 * n, [(tuple(qs) + tuple(n + q for q in qs), hq.hq_dm_superop([m] if k == "gate" else m))
+                                for k, qs, m in ops], 4, method="dag", restarts=8, seed=0)
+    assert len(blocks) > 64 + len(ops) // 4
