@@ -208,7 +208,12 @@ typedef struct {
  * Channels whose operators all have K_i^dag K_i = p_i I are sampled on the
  * host from p_i alone; the others on the device (reduced density matrix,
  * branch and renormalised operator picked by one CTA, no host round trip).
- * Synchronous once, at the end, when a channel was sampled on the device.
+ * The operators applied right before a device-sampled channel on the same
+ * qubits, in the same order, are folded into it (probabilities from
+ * A rho A^dag, K_i A / sqrt(p_i) applied): the same result in fewer passes.
+ * Synchronous once, at the end, when a channel was sampled on the device;
+ * device scratch (operators, partial sums) from the stream-ordered
+ * allocator, released before returning.
  * Errors: as hq_apply_gate and hq_apply_kraus_sampled; HQ_ERR_ARG (nops < 0).
  */
 hq_status hq_run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops, int nops, const double *u,
