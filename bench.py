@@ -242,6 +242,9 @@ def cpu_baseline(circ, seconds: float = 12.0, single_seconds: float = 6.0):
             "sample": f"first {done} of {len(circ.gates)} gates of the same n={n} circuit, complex128, "
                       f"unfused, OpenMP over {cores} threads ({dt:.1f} s)",
             "single_thread": {"value": done1 / dt1, "sample": f"first {done1} gates on 1 thread ({dt1:.1f} s)"},
+            # one gate touches 2^n amplitudes: the rate three qubits up is an eighth (not run: 128 GiB)
+            "n33_extrapolated": {"value": done / dt / 8, "note": f"extrapolated from n={n} as rate / 2^(33-{n})"}
+            if n == 30 else None,
             "cpu": cpu_model(), "nproc": os.cpu_count()}
 
 
