@@ -364,8 +364,18 @@ __global__ void __launch_bounds__(kApThreads, sizeof(R) == 4 ? (REV ? 3 : 4) : 2
                     for (int j = 0; j < kSweepOps; ++j) {
                         if (j >= nsw) break;
                         T2 mm[4];
+                        if constexpr (sizeof(R) == 4) {
+                            // the op's 4 entries are 32 contiguous, 32-byte aligned bytes
+                            const float4 *mv = reinterpret_cast<const float4 *>(mt + cx * 4 - (REV ? 8 * j : 0));
+                            const float4 a = mv[0], bq = mv[1];
+                            mm[0] = make_float2(a.x, a.y);
+                            mm[1] = make_float2(a.z, a.w);
+                            mm[2] = make_float2(bq.x, bq.y);
+                            mm[3] = make_float2(bq.z, bq.w);
+                        } else {
 #pragma unroll
-                        for (int r = 0; r < 4; ++r) mm[r] = mt[cx * 4 + r - (REV ? 8 * j : 0)];
+                            for (int r = 0; r < 4; ++r) mm[r] = mt[cx * 4 + r - (REV ? 8 * j : 0)];
+                        }
                         if (REV && ((rotmask >> j) & 1)) g[j] += pauli_im2(ax[j], x0, x1, l0, l1);
                         if ((diagmask >> j) & 1) {
                             x0 = cmul(mm[0], x0);

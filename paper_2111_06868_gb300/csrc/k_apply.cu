@@ -268,11 +268,11 @@ __device__ __forceinline__ void gather_rows_acc(const MatParam<R, K> &m, const t
     }
 }
 
-// Tile of 2^12 complex64 (32 KB per buffer, 3 CTAs per SM) for K <= 3; 2^11
-// for K = 4, whose 64-register, instruction-bound threads gain from the
-// extra CTAs (n=30, GB/s: K=3 4734-4959 at 12 bits vs 4536-4954 at 11;
-// K=4 2144-2175 vs 2404-2598).
-template <int K> constexpr int gather_pipe_tile_bits() { return K == 4 ? 11 : 12; }
+// Tile of 2^12 complex64 (32 KB per buffer, 3 CTAs per SM) for K = 3; 2^11
+// (16 KB, more CTAs) otherwise (n=30, GB/s at 12 / 11 bits: K=1 6455-6570 /
+// 6478-6596, K=2 6259-6458 / 6327-6547, K=3 5386-5704 / 5124-5810, K=4
+// 2144-2175 / 2404-2598 with 4-row chunks).
+template <int K> constexpr int gather_pipe_tile_bits() { return K == 3 ? 12 : 11; }
 
 // One tile in shared memory multiplied in place (every group of 2^K
 // amplitudes by the matrix); ends with a barrier.
