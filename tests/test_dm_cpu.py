@@ -90,3 +90,28 @@ def test_dm_validation_before_any_device_work(hq):
     assert lib.hq_dm_superop(1, 1, None, 0, None, None, S.ctypes.data_as(ctypes.c_void_p)) == -1
     assert lib.hq_dm_superop(4, 1, U.ctypes.data_as(ctypes.c_void_p), 0, None, None,
                              S.ctypes.data_as(ctypes.c_void_p)) == -4
+
+
+@pytest.mark.parametrize("name,ks", [("depolarizing1", C.depolarizing(0.3, 1)), ("depolarizing2", C.depolarizing(0.2, 2)),
+                                     ("dephasingX", C.dephasing(0.4, "X")), ("dephasingY", C.dephasing(0.1, "Y")),
+                                     ("amplitude_damping", C.amplitude_damping(0.3)),
+                                     ("generalized_damping", C.amplitude_damping(0.2, 0.15))])
+def test_channel_superops_preserve_trace(hq, name, ks):
+    """Every channel of Sec. 2.1 is trace preserving: vec(I)^T S = vec(I)^T;
+    Pauli channels are also unital: S vec(I) = vec(I); and the channel with
+    operators {K^dag} is the Hilbert-Schmidt adjoint of the one with {K}:
+    Tr(A^dag Lambda(B)) = Tr(Lambda*(A)^dag B)."""
+    S = hq.hq_dm_superop(ks)
+    d = ks[0].shape[0]
+    vI = np.eye(d).reshape(-1)
+    np.testing.assert_allclose(vI @ S, vI, atol=1e-14)
+    if not name.endswith("damping"):
+        np.testing.assert_allclose(S @ vI, vI, atol=1e-14)
+    Sa = hq.hq_dm_superop([K.conj().T for K in ks])
+    # Tr(A^dag Lambda(B)) = Tr(Lambda*(A)^dag B) for random A, B
+    rng = np.random.default_rng(d)  # input only
+    A = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    B = rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))
+    lhs = np.vdot(A.reshape(-1), S @ B.reshape(-1))
+    rhs = np.vdot(Sa @ A.reshape(-1), B.reshape(-1))
+    assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
