@@ -115,3 +115,26 @@ def test_channel_superops_preserve_trace(hq, name, ks):
     lhs = np.vdot(A.reshape(-1), S @ B.reshape(-1))
     rhs = np.vdot(Sa @ A.reshape(-1), B.reshape(-1))
     assert abs(lhs - rhs) <= 1e-12 * max(1.0, abs(lhs))
+
+
+def test_fused_superops_reproduce_the_oracle_density_matrix(hq):
+    """A noisy circuit at the density-matrix level on the host: every gate
+    and channel as its superoperator on vector qubits (q, n + q), fused by
+    hq_fuse_dag into <= 6-qubit blocks, applied to vec(rho) by the
+    state-vector oracle, equals the noise oracle's full-matrix evolution."""
+    import oracle
+
+    n = 4
+    circ = C.random_circuit(C.layout_for(n), 4, seed=3, two_qubit="cz")
+    ops = C.noisy_ops(circ, p1=0.05, p2=0.1, gamma=0.07)
+    rho = N.pure_dm(oracle.state_init(n, "+0-1"))
+    for kind, qs, m in ops:
+        rho = N.apply_unitary_dm(rho, n, list(qs), m) if kind == "gate" else N.apply_map(rho, n, list(qs), m)
+    sup = [(tuple(qs) + tuple(n + q for q in qs), hq.hq_dm_superop([m] if kind == "gate" else m))
+           for kind, qs, m in ops]
+    blocks = hq.hq_fuse(2 * n, sup, 6, method="dag", restarts=8, seed=0)
+    assert len(blocks) < len(sup)
+    v = N.pure_dm(oracle.state_init(n, "+0-1")).reshape(-1).copy()
+    for qs, M in blocks:
+        v = oracle.apply_gate(v, 2 * n, qs, M)
+    np.testing.assert_allclose(v.reshape(1 << n, 1 << n), rho, atol=1e-13)
