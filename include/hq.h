@@ -412,6 +412,19 @@ hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates,
 int hq_plan_passes(int n, const hq_gate *gates, int G, int max_blocks, int *records, int max_passes);
 
 /*
+ * hq_test_fail_next_allocs -- fault injection for tests of the error paths
+ * (no counterpart in the paper): the next `count` device scratch allocations
+ * the library takes from the stream-ordered allocator (hq_expectation,
+ * hq_reduced_density_matrix, the channel sampling of hq_apply_kraus_sampled
+ * and hq_run_trajectory, hq_dm_expectation, the CUDA-core wide blocks and
+ * the tile-pass engine of hq_apply_blocks) fail as if the device were out of
+ * memory; the entry point that meets one returns HQ_ERR_ALLOC (work it had
+ * enqueued before stays enqueued).  count = 0 turns it off.  Process-wide;
+ * host only.  Errors: HQ_ERR_ARG (count < 0).
+ */
+hq_status hq_test_fail_next_allocs(int count);
+
+/*
  * hq_expectation -- <psi|H|psi> = sum_t coeff_t <psi|P_t|psi> for a Pauli sum
  * (T terms), accumulated in double; a term of len 0 gives the squared norm.
  * Result written to *out_host.  SYNCHRONISES `stream`.  Uses device scratch

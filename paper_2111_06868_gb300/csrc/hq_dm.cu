@@ -16,6 +16,7 @@
 #include <cstring>
 #include <vector>
 
+#include "hq_fault.cuh"
 #include "hq_internal.cuh"
 
 namespace hq {
@@ -76,7 +77,7 @@ static hq_status run_dm_expectation(const void *rho, int n, const hq_pauli_term 
                               ((int64_t(1) << n) + kDmThreads - 1) / kDmThreads);
     const int nparts = grid * nchunks;
     double *scratch = nullptr;
-    if (cudaMallocAsync((void **)&scratch, sizeof(double) * (size_t(nparts) + 1), s) != cudaSuccess)
+    if (injected_alloc_failure() || cudaMallocAsync((void **)&scratch, sizeof(double) * (size_t(nparts) + 1), s) != cudaSuccess)
         return HQ_ERR_ALLOC;
     hq_status st = HQ_OK;
     for (int c = 0; c < nchunks && st == HQ_OK; ++c) {

@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "hq_cp_async.cuh"
+#include "hq_fault.cuh"
 #include "hq_internal.cuh"
 
 namespace hq {
@@ -768,7 +769,8 @@ static hq_status run_block(void *state, int n, const int *qubits, const double *
         hm[i].y = R(mat[2 * i + 1]);
     }
     T2 *dm = nullptr;
-    if (cudaMallocAsync((void **)&dm, sizeof(T2) * D * D, s) != cudaSuccess) return HQ_ERR_ALLOC;
+    if (injected_alloc_failure() || cudaMallocAsync((void **)&dm, sizeof(T2) * D * D, s) != cudaSuccess)
+        return HQ_ERR_ALLOC;
     HQ_CUDA(cudaMemcpyAsync(dm, hm.data(), sizeof(T2) * D * D, cudaMemcpyHostToDevice, s));
     const size_t smem = sizeof(T2) * (size_t(D * D) + (size_t(1) << g.L));
     const void *fn = (const void *)k_block<R, K>;

@@ -15,6 +15,7 @@
 #include <cstring>
 #include <vector>
 
+#include "hq_fault.cuh"
 #include "hq_internal.cuh"
 
 namespace hq {
@@ -139,7 +140,8 @@ static hq_status run_rdm(const void *state, int n, const int *qubits, double *ou
     const int grid = rdm_grid<R, K>(n);
     const int width = 2 * NE;
     double *scratch = nullptr;
-    if (cudaMallocAsync((void **)&scratch, sizeof(double) * (size_t(grid) + 1) * width, s) != cudaSuccess)
+    if (injected_alloc_failure() ||
+        cudaMallocAsync((void **)&scratch, sizeof(double) * (size_t(grid) + 1) * width, s) != cudaSuccess)
         return HQ_ERR_ALLOC;
     hq_status rc = rdm_partials<R, K>(state, n, qubits, scratch, s);
     double *out_dev = scratch + size_t(grid) * width;
@@ -507,7 +509,7 @@ hq_status run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops
     const size_t bytes = nd * sizeof(double) + sizeof(int) * (dev.size() + 1);
     char *ws = nullptr;
     if (!dev.empty()) {
-        if (cudaMallocAsync((void **)&ws, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
+        if (injected_alloc_failure() || cudaMallocAsync((void **)&ws, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
         HQ_CUDA(cudaMemcpyAsync(ws, hostbuf.data(), sizeof(double) * hostbuf.size(), cudaMemcpyHostToDevice, s));
         HQ_CUDA(cudaMemsetAsync(ws + nd * sizeof(double), 0, sizeof(int) * (dev.size() + 1), s));
     }

@@ -12,12 +12,14 @@
 // scratch and a single-CTA kernel sums them in a fixed order, so the result is
 // deterministic for a given launch shape.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "hq_cp_async.cuh"
+#include "hq_fault.cuh"
 #include "hq_internal.cuh"
 
 namespace hq {
@@ -503,7 +505,8 @@ hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pau
             const int grid = 3 * sm_count();
             double *scratch = nullptr;
             const size_t nd = 1 + passes.size() * size_t(grid);
-            if (cudaMallocAsync((void **)&scratch, sizeof(double) * nd, s) != cudaSuccess) return HQ_ERR_ALLOC;
+            if (injected_alloc_failure() || cudaMallocAsync((void **)&scratch, sizeof(double) * nd, s) != cudaSuccess)
+                return HQ_ERR_ALLOC;
             st = launch_tiled(state, n, dt, passes, grid, scratch, s);
             double result = 0;
             if (st == HQ_OK)
@@ -536,7 +539,8 @@ hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pau
     }
     const size_t npart = size_t(groups.size()) * gx;
     double *scratch = nullptr;
-    if (cudaMallocAsync((void **)&scratch, sizeof(double) * (npart + 1), s) != cudaSuccess) return HQ_ERR_ALLOC;
+    if (injected_alloc_failure() || cudaMallocAsync((void **)&scratch, sizeof(double) * (npart + 1), s) != cudaSuccess)
+        return HQ_ERR_ALLOC;
     hq_status rc = HQ_OK;
     for (auto &ch : chunks) {
         ExpParams p;
@@ -672,4 +676,24 @@ hq_status launch_expectation_static(const void *state, int n, hq_dtype dt, const
     return HQ_OK;
 }
 
+// ----------------------------------------------------------------------------
+// injected scratch-allocation failures (hq_test_fail_next_allocs)
+// ----------------------------------------------------------------------------
+static std::atomic<int> g_injected_alloc_failures{0};
+
+bool injected_alloc_failure()
+{
+    int left = g_injected_alloc_failures.load();
+    while (left > 0)
+        if (g_injected_alloc_failures.compare_exchange_weak(left, left - 1)) return true;
+    return false;
+}
+
 }  // namespace hq
+
+extern "C" hq_status hq_test_fail_next_allocs(int count)
+{
+    if (count < 0) return HQ_ERR_ARG;
+    hq::g_injected_alloc_failures.store(count);
+    return HQ_OK;
+}

@@ -112,6 +112,7 @@ def load(path: str | None = None):
         "hq_apply_kraus_sampled": ([V, I, I, V, I, I, V, ctypes.c_double, V, V], I),
         "hq_run_trajectory": ([V, I, I, V, I, V, V, V, V], I),
         "hq_simplify": ([I, V, I, I, ctypes.c_double, V], I),
+        "hq_test_fail_next_allocs": ([I], I),
         "hq_dm_superop": ([I, I, V, I, V, V, V], I),
         "hq_dm_init": ([V, I, I, ctypes.c_char_p, V], I),
         "hq_dm_apply": ([V, I, I, V, I, I, V, V], I),
@@ -659,3 +660,9 @@ def hq_dm_purity(rho, stream=None) -> float:
     out = ctypes.c_double(0.0)
     _check(load().hq_dm_purity(ptr, n, dt, ctypes.byref(out), _stream(stream)), "hq_dm_purity")
     return out.value
+
+
+def hq_test_fail_next_allocs(count: int) -> None:
+    """Make the library's next `count` device scratch allocations fail
+    (HQ_ERR_ALLOC), for tests of the error paths; 0 turns it off."""
+    _check(load().hq_test_fail_next_allocs(int(count)), "hq_test_fail_next_allocs")
