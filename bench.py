@@ -36,6 +36,10 @@ if ROOT not in sys.path:
 from paper_2111_06868_gb300 import circuits as C  # noqa: E402
 
 METRIC = "gate-apps/s"
+ARITH = {"tc_f16": "fp16 hi+lo split operands (3 products), fp32 accumulate in TMEM, fp64 norm",
+         "tc_bf16": "bf16 hi+lo split operands (3 products), fp32 accumulate in TMEM, fp64 norm",
+         "tc_pass": "fp16 hi+lo split operands (3 products), fp32 accumulate in TMEM, fp64 norm",
+         "cuda_core": "fp32 FMA on CUDA cores, fp64 norm", "auto": "fp32 FMA on CUDA cores, fp64 norm"}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
@@ -420,15 +424,15 @@ def measure_batch():
     return {"circuits": len(cs), "gates": Gb, "tile": [13, 7], "launches_per_run": 1, "graph": True, **bres}
 
 
-def measure_expectation(reps=5):
+def measure_expectation(reps=5, n=30):
     """<psi|H|psi> at n=30 (complex64) for the ansatz Hamiltonian (29 ZZ and
     30 X terms: several X-mask groups, the tiled path), wall clock of the
     synchronous call."""
     import torch
     from paper_2111_06868_gb300 import hq
 
-    H = C.ansatz_hamiltonian(30)
-    st = torch.empty(1 << 30, dtype=torch.complex64, device="cuda")
+    H = C.ansatz_hamiltonian(n)
+    st = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
     hq.hq_state_init(st, "+")
     e = hq.hq_expectation(st, H)
     torch.cuda.synchronize()
@@ -438,8 +442,95 @@ def measure_expectation(reps=5):
     t = (time.perf_counter() - t0) / reps
     del st
     torch.cuda.empty_cache()
-    return {"terms": len(H), "s": t, "value": e, "expected_value": 15.0,
-            "state": "|+>^30: every ZZ term 0, every 0.5 X term 0.5"}
+    return {"n": n, "terms": len(H), "s": t, "value": e, "expected_value": 0.5 * n,
+            "state": f"|+>^{n}: every ZZ term 0, every 0.5 X term 0.5"}
+
+
+def measure_fp_peaks(N=8192, reps=5):
+    """Non-tensor-core arithmetic peaks of this GPU, for the rooflines of the
+    complex128 kernels (FP64) and the CUDA-core blocks (FP32): cuBLAS DGEMM
+    and SGEMM (TF32 off) on N^3, 2 N^3 flop per product, best of `reps`
+    (CUDA events)."""
+    import torch
+
+    res = {}
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        for name, dt in (("fp64_dgemm_tflops", torch.float64), ("fp32_sgemm_tflops", torch.float32)):
+            a = torch.randn(N, N, dtype=dt, device="cuda")
+            b = torch.randn(N, N, dtype=dt, device="cuda")
+            c = a @ b
+            best = 1e30
+            for _ in range(reps):
+                e0, e1 = _events()
+                e0.record()
+                c = a @ b
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+            res[name] = 2 * N ** 3 / best / 1e12
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    torch.cuda.empty_cache()
+    res["how"] = f"torch.matmul {N}^3, 2 N^3 flop, best of {reps}, CUDA events; allow_tf32 False"
+    return res
+
+
+def measure_c128(args, circ):
+    """Configuration 2 in complex128: per gate and fused k <= 4 (exact FP64
+    kernels, no tensor cores); rates in unfused gate-apps/s, effective GB/s
+    = bytes of one read and write of the state per launch."""
+    import torch
+
+    G = len(circ.gates)
+    res = {"gates": G}
+    st, t = _time_blocks(30, [(g.qubits, g.matrix) for g in circ.gates], "auto", torch.complex128)
+    res["per_gate"] = {"launches": G, "gate_apps_per_s": G / t, "s": t, "GBps": G * 2 * (1 << 30) * 16 / t / 1e9}
+    del st
+    from paper_2111_06868_gb300 import hq
+
+    b4 = fuse(hq, 30, circ.gates, 4, args)
+    st, t4 = _time_blocks(30, b4, "cuda_core", torch.complex128)
+    res["fused_k4"] = {"blocks": len(b4), "gate_apps_per_s": G / t4, "s": t4,
+                       "GBps": len(b4) * 2 * (1 << 30) * 16 / t4 / 1e9}
+    del st
+    torch.cuda.empty_cache()
+    return res
+
+
+def measure_n28_vs_oracle(args):
+    """Relative L2 error against the oracle (complex128, gate by gate) of the
+    n=28 subset of the 33-qubit layout (942 gates), for every complex64 engine
+    on the fused k <= 6 blocks, and max-abs error of the complex128 per-gate
+    path; the oracle state is computed on the host cores (~80 s)."""
+    import torch
+    import oracle
+    from paper_2111_06868_gb300 import hq
+
+    c28 = C.config_n33(seed=args.seed, first=28)
+    t0 = time.perf_counter()
+    want = oracle.simulate(c28)
+    t_or = time.perf_counter() - t0
+    nw = np.linalg.norm(want)
+    st = torch.empty(1 << 28, dtype=torch.complex64, device="cuda")
+    errs = {}
+    b28 = fuse(hq, 28, c28.gates, 6, args)
+    for eng in ("tc_f16", "tc_bf16", "cuda_core"):
+        hq.hq_state_init(st)
+        hq.hq_apply_blocks(st, b28, engine=eng, tc_min_k=4)
+        errs[eng] = float(np.linalg.norm(st.cpu().numpy().astype(np.complex128) - want) / nw)
+    del st
+    st = torch.empty(1 << 28, dtype=torch.complex128, device="cuda")
+    hq.hq_state_init(st)
+    hq.hq_apply_blocks(st, c28.gates)
+    c128 = float(np.abs(st.cpu().numpy() - want).max())
+    del st
+    torch.cuda.empty_cache()
+    return {"gates": len(c28.gates), "blocks_k6": len(b28), "rel_l2": errs, "bar_rel_l2": 2e-5,
+            "c128_per_gate_max_abs": c128, "bar_max_abs": 1e-12, "oracle_s": t_or,
+            "oracle_threads": oracle.max_threads()}
 
 
 def measure_extras(args):
@@ -461,12 +552,9 @@ def measure_extras(args):
     out["n30_fused_k4_c64_cuda_core"] = {"blocks": len(b4), "gate_apps_per_s": G / t4, "s": t4,
                                          "speedup_vs_per_gate": t / t4}
     del st
-    # n=30, complex128 (FP64), unfused, on the first 120 gates
-    sub = circ.gates[:120]
-    st, t = _time_blocks(30, [(g.qubits, g.matrix) for g in sub], "auto", torch.complex128)
-    out["n30_per_gate_c128_first120"] = {"gate_apps_per_s": len(sub) / t, "s": t,
-                                         "GBps": len(sub) * 2 * (1 << 30) * 16 / t / 1e9}
-    del st
+    # n=30, complex128 (FP64): the whole circuit per gate, and fused into
+    # <= 4-qubit blocks on the exact kernels
+    out["n30_c128"] = measure_c128(args, circ)
     torch.cuda.empty_cache()
     # n=30 QFT, unfused: 435 controlled phases (the controlled-gate kernel reads
     # and writes only the amplitudes whose controls are 1), 30 H, 15 SWAP
@@ -535,34 +623,146 @@ def measure_extras(args):
     b33 = fuse(hq, 33, c33.gates, 6, args)
     st, t_tc = _time_blocks(33, b33, "tc_f16", torch.complex64)
     nrm = hq.hq_expectation(st, [(1.0, ())])
-    _, t_cc = _time_blocks(33, b33[:8], "cuda_core", torch.complex64)
-    t_cc = t_cc * len(b33) / 8
+    _, t_cc = _time_blocks(33, b33, "cuda_core", torch.complex64)
     out["n33_fused_k6"] = {"blocks": len(b33), "gates": len(c33.gates),
                            "tc_f16_gate_apps_per_s": len(c33.gates) / t_tc, "tc_f16_s": t_tc,
                            "tc_f16_GBps_per_block": len(b33) * 2 * (1 << 33) * 8 / t_tc / 1e9,
-                           "cuda_core_s_extrapolated_from_8_blocks": t_cc,
+                           "cuda_core_s": t_cc, "cuda_core_gate_apps_per_s": len(c33.gates) / t_cc,
                            "tc_speedup_vs_cuda_core": t_cc / t_tc, "norm_minus_1": nrm ** 0.5 - 1}
     del st
     torch.cuda.empty_cache()
-    # accuracy of the tensor-core path against FP64 on the n=28 subset
-    c28 = C.config_n33(seed=args.seed, first=28)
-    ref = torch.empty(1 << 28, dtype=torch.complex128, device="cuda")
-    hq.hq_state_init(ref)
-    hq.hq_apply_blocks(ref, c28.gates)
-    st = torch.empty(1 << 28, dtype=torch.complex64, device="cuda")
-    errs = {}
-    for eng in ("tc_f16", "tc_bf16", "cuda_core"):
-        hq.hq_state_init(st)
-        hq.hq_apply_blocks(st, fuse(hq, 28, c28.gates, 6, args), engine=eng, tc_min_k=4)
-        errs[eng] = (st.to(torch.complex128) - ref).norm().item() / ref.norm().item()
-    out["n28_subset_rel_l2_vs_fp64"] = {"gates": len(c28.gates), **errs, "bar": 2e-5}
-    del st, ref
-    torch.cuda.empty_cache()
+    # accuracy of every engine against the oracle on the n=28 subset
+    if not args.no_oracle_check:
+        out["n28_subset_vs_oracle"] = measure_n28_vs_oracle(args)
     out["adjoint_n20_batch64"] = measure_adjoint()
     out["n30_expectation_ansatz_hamiltonian"] = measure_expectation()
     out["batch512"] = measure_batch()
     out["n12_one_circuit"] = measure_small_circuit(args)
     return out
+
+
+def gpu_numa_info(device_index):
+    """NUMA node and local CPUs of the GPU (Linux sysfs via its PCI bus id),
+    and this process's CPU affinity."""
+    info = {"affinity": sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else None}
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={device_index}", "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True, timeout=10).stdout.strip()
+        bus = out.lower()
+        if bus.startswith("0000000"):
+            bus = bus[4:]
+        base = f"/sys/bus/pci/devices/{bus}"
+        with open(f"{base}/numa_node") as f:
+            info["gpu_numa_node"] = int(f.read().strip())
+        with open(f"{base}/local_cpulist") as f:
+            info["gpu_local_cpulist"] = f.read().strip()
+        info["pci_bus_id"] = bus
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+    return info
+
+
+def _cpulist(text):
+    cpus = set()
+    for part in text.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part.strip():
+            cpus.add(int(part))
+    return cpus
+
+
+def measure_e2e(args, hq, circ, blocks, state, stream, engine, dist):
+    """End to end through the public API: every step copies the state in from
+    pinned host memory, applies the fused blocks and reads the FP64 norm
+    back.  Two state buffers: the next step's input is copied on its own
+    stream while the current step computes.  The pinned buffer is allocated
+    (and first touched) by a thread bound to the GPU's local CPUs where the
+    system reports them.  Also measured: the H2D copy alone (GB/s), and a
+    variant that runs the fusion (hq_fuse_dag) of the next step's circuit on
+    the host while the current step's kernels run."""
+    import torch
+
+    n, G = circ.n, len(circ.gates)
+    cdt, S = state.dtype, state.element_size()
+    numa = gpu_numa_info(torch.cuda.current_device())
+    old_aff = os.sched_getaffinity(0) if hasattr(os, "sched_getaffinity") else None
+    local = _cpulist(numa.get("gpu_local_cpulist", "")) & (old_aff or set())
+    if local:
+        os.sched_setaffinity(0, local)
+    try:
+        host_in = torch.empty(1 << n, dtype=cdt, pin_memory=True)
+        host_in.zero_()
+        host_in[0] = 1
+    finally:
+        if local:
+            os.sched_setaffinity(0, old_aff)
+    numa["pinned_allocated_on_local_cpus"] = bool(local)
+    out = torch.zeros(1, dtype=torch.float64).pin_memory()
+    bufs = [state, torch.empty_like(state)]
+    copy_stream = torch.cuda.Stream()
+
+    # the H2D copy alone
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h2d = []
+    for _ in range(3):
+        c0.record(stream)
+        bufs[1].copy_(host_in, non_blocking=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        h2d.append(c0.elapsed_time(c1) / 1e3)
+    h2d_gbps = (1 << n) * S / min(h2d) / 1e9
+
+    def run(steps, start=None, refuse=False):
+        copied = [None, None]
+        cur_blocks = blocks
+        with torch.cuda.stream(copy_stream):
+            if start is not None:
+                copy_stream.wait_event(start)
+            bufs[0].copy_(host_in, non_blocking=True)
+            copied[0] = torch.cuda.Event()
+            copied[0].record(copy_stream)
+        for s in range(steps):
+            cur = bufs[s % 2]
+            stream.wait_event(copied[s % 2])
+            hq.hq_apply_blocks(cur, cur_blocks, engine=engine, tc_min_k=args.tc_min_k, stream=stream)
+            if s + 1 < steps:
+                nxt = (s + 1) % 2
+                # the buffer's previous step ended with a synchronous norm
+                with torch.cuda.stream(copy_stream):
+                    bufs[nxt].copy_(host_in, non_blocking=True)
+                    copied[nxt] = torch.cuda.Event()
+                    copied[nxt].record(copy_stream)
+                if refuse:  # next step's fusion on the host, under this step's kernels
+                    cur_blocks = fuse(hq, n, circ.gates, args.kmax, args)
+            out[0] = hq.hq_expectation(cur, [(1.0, ())], stream=stream)
+
+    def timed(steps, refuse=False):
+        run(2, refuse=refuse)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        run(steps, start=e0, refuse=refuse)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    e2e_steps = max(2, min(args.steps, 5))
+    et = timed(e2e_steps)
+    e2e_value, et = whole_job_rate(et, G * e2e_steps, dist, "cuda")
+    t_f = timed(e2e_steps, refuse=True)
+    del bufs
+    return {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": (1 << n) * S, "d2h_bytes_per_step": 8,
+            "ms_per_step": 1e3 * et / e2e_steps, "h2d_alone_GBps": h2d_gbps,
+            "h2d_alone_ms": 1e3 * min(h2d), "numa": numa,
+            "with_fusion_each_step": {"value": G * e2e_steps / t_f, "ms_per_step": 1e3 * t_f / e2e_steps,
+                                      "note": "hq_fuse_dag of the next step on the host under the current "
+                                              "step's kernels"},
+            "note": "pinned host state copied in and FP64 norm read back every step; the next step's copy "
+                    "overlaps the current step on a second stream (two state buffers)"}
 
 
 def whole_job_rate(local_seconds: float, local_units: float, dist=None, device=None):
@@ -599,7 +799,9 @@ def main():
     ap.add_argument("--ref-gates", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", choices=["adjoint", "trajectories", "batch", "expect"],
+    ap.add_argument("--no-oracle-check", action="store_true", help="skip the n=28 oracle comparison in extras")
+    ap.add_argument("--expect-n", type=int, default=30, help="state size of --only expect")
+    ap.add_argument("--only", choices=["adjoint", "trajectories", "batch", "expect", "peaks"],
                     help="run one of the extra workloads alone (for profiling) and print its result")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -631,7 +833,9 @@ def main():
         elif args.only == "batch":
             res = measure_batch()
         elif args.only == "expect":
-            res = measure_expectation()
+            res = measure_expectation(n=args.expect_n)
+        elif args.only == "peaks":
+            res = measure_fp_peaks()
         else:
             res = measure_trajectories(args, T=2)
         print(json.dumps({"only": args.only, **res}))
@@ -653,22 +857,26 @@ def main():
 
     passes = len(hq.hq_plan_passes(n, blocks)) if engine == "tc_pass" else 0
 
-    def step(events=None):
+    def step():
+        """One pass of the hot path through the public API: |0..0>, every fused
+        block in one hq_apply_blocks call, the FP64 norm (synchronous)."""
         hq.hq_state_init(state)
-        if engine == "tc_pass":
-            # the pass engine plans over the whole list: one call, bracketed
-            if events is not None:
-                events[0].record(stream)
+        hq.hq_apply_blocks(state, blocks, engine=engine, tc_min_k=args.tc_min_k)
+        return hq.hq_expectation(state, norm_term)
+
+    def step_per_block(events):
+        """The same step with one call per block, bracketed by CUDA events on
+        the launching stream (per-kernel durations for the roofline)."""
+        hq.hq_state_init(state)
+        if engine == "tc_pass":  # the pass engine plans over the whole list: one bracket
+            events[0].record(stream)
             hq.hq_apply_blocks(state, blocks, engine=engine)
-            if events is not None:
-                events[B].record(stream)
+            events[B].record(stream)
             return hq.hq_expectation(state, norm_term)
         for i, b in enumerate(blocks):
-            if events is not None:
-                events[i].record(stream)
+            events[i].record(stream)
             hq.hq_apply_blocks(state, [b], engine=engine, tc_min_k=args.tc_min_k)
-        if events is not None:
-            events[B].record(stream)
+        events[B].record(stream)
         return hq.hq_expectation(state, norm_term)
 
     for _ in range(args.warmup):
@@ -678,7 +886,6 @@ def main():
         dist.barrier()
     sampler = ClockSampler(local)
     sampler.start()
-    per_step_events = [[torch.cuda.Event(enable_timing=True) for _ in range(B + 1)] for _ in range(args.steps)]
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -686,16 +893,28 @@ def main():
         dist.barrier()
     t0.record(stream)
     for s in range(args.steps):
-        norm = step(per_step_events[s])
+        norm = step()
     t1.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = sampler.stop()
     elapsed = t0.elapsed_time(t1) / 1e3
     value, elapsed = whole_job_rate(elapsed, G * args.steps, dist, "cuda")
 
-    # per-class launch durations (CUDA events on the launching stream)
+    # second timed pass: per-block launches bracketed by events (roofline)
+    per_step_events = [[torch.cuda.Event(enable_timing=True) for _ in range(B + 1)] for _ in range(args.steps)]
+    step_per_block(per_step_events[0])
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for s in range(args.steps):
+        step_per_block(per_step_events[s])
+    p1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    per_block_step_s = p0.elapsed_time(p1) / 1e3 / args.steps
+
     durs = {}
     for ev in per_step_events:
         if engine == "tc_pass":  # one bracket per step; averaged over its passes
@@ -713,55 +932,9 @@ def main():
                      "GBps": bytes_per_launch / statistics.mean(v) / 1e9, "share": tot[c] / sum(tot.values())}
                  for c, v in durs.items()}
 
-    # end to end through the public API: pinned host state in, norm out.  Two
-    # state buffers: the next step's input is copied on its own stream while
-    # the current step computes (every step's copy and result read stay inside
-    # the timed region)
     e2e = None
     if not args.no_e2e:
-        host_in = torch.zeros(1 << n, dtype=cdt).pin_memory()
-        host_in[0] = 1
-        out = torch.zeros(1, dtype=torch.float64).pin_memory()
-        bufs = [state, torch.empty_like(state)]
-        copy_stream = torch.cuda.Stream()
-
-        def e2e_run(steps, start=None):
-            copied = [None, None]
-            with torch.cuda.stream(copy_stream):
-                if start is not None:
-                    copy_stream.wait_event(start)
-                bufs[0].copy_(host_in, non_blocking=True)
-                copied[0] = torch.cuda.Event()
-                copied[0].record(copy_stream)
-            for s in range(steps):
-                cur = bufs[s % 2]
-                stream.wait_event(copied[s % 2])
-                hq.hq_apply_blocks(cur, blocks, engine=engine, tc_min_k=args.tc_min_k, stream=stream)
-                if s + 1 < steps:
-                    nxt = (s + 1) % 2
-                    # the buffer's previous step ended with a synchronous norm
-                    with torch.cuda.stream(copy_stream):
-                        bufs[nxt].copy_(host_in, non_blocking=True)
-                        copied[nxt] = torch.cuda.Event()
-                        copied[nxt].record(copy_stream)
-                out[0] = hq.hq_expectation(cur, norm_term, stream=stream)
-
-        e2e_run(2)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e2e_steps = max(2, min(args.steps, 5))
-        torch.cuda.synchronize()
-        e0.record(stream)
-        e2e_run(e2e_steps, start=e0)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        et = e0.elapsed_time(e1) / 1e3
-        e2e_value, et = whole_job_rate(et, G * e2e_steps, dist, "cuda")
-        e2e = {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": (1 << n) * S,
-               "d2h_bytes_per_step": 8,
-               "note": "pinned host state copied in and FP64 norm read back every step; the next step's copy "
-                       "overlaps the current step on a second stream (two state buffers)"}
-        del bufs
+        e2e = measure_e2e(args, hq, circ, blocks, state, stream, engine, dist)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -780,6 +953,12 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if S == 8 else "f64", "data": "synthetic",
             "config": {"workload": desc, "n": n, "gates": G, "fused_blocks": B, "k_max": args.kmax,
+                       "arith": ARITH.get(engine, engine) if S == 8 else "fp64",
+                       "note": "the n=30 circuit of the per-gate / fused k<=4 configuration, run on the "
+                               "fused k<=6 tensor-core engine of the 33-qubit configuration"
+                               if n == 30 and engine.startswith("tc") else None,
+                       "timing": "value: one hq_apply_blocks call over all blocks per step; roofline: a "
+                                 "second pass with one call per block between CUDA events",
                        "fusion": (f"{args.fuse} ({args.fuse_restarts} restarts)" if args.fuse == "dag" else args.fuse),
                        "state": args.dtype, "engine": engine, "l2": (f"state ({S * (1 << n) / 2**30:g} GiB) larger than the 129 MB L2; no flush" if S << n > 129e6
                               else f"state ({S << n} B) fits in L2 and is not flushed"),
@@ -791,7 +970,7 @@ def main():
                          "kernel": dom, "peak_source": peak_kind,
                          "bytes_per_launch": bytes_per_launch},
             "per_class": per_class,
-            "norm2": norm, "fuse_s": fuse_s,
+            "norm2": norm, "fuse_s": fuse_s, "per_block_pass_ms_per_step": 1e3 * per_block_step_s,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "extras": extras,
             "gpu_launches": args.steps * (B + 3),
         }

@@ -388,6 +388,11 @@ hq_status hq_apply_gate(void *state, int n, hq_dtype dt, const int *qubits, int 
  * see hq_plan_passes.  It moves qubits between bit positions while it runs and
  * restores the caller's order before it returns (stream order).
  * Errors: as hq_apply_gate, plus HQ_ERR_ARG (G < 0 or unknown engine).
+ * On HQ_ERR_ALLOC the state is left as follows: the tensor-core engines and
+ * HQ_ENGINE_TC_PASS take their one scratch buffer before enqueueing any
+ * kernel, so the state is untouched; HQ_ENGINE_AUTO / HQ_ENGINE_CUDA_CORE
+ * allocate per wide (k = 5, 6) block, so the blocks before the one whose
+ * allocation failed have been applied and none after it.
  */
 hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates, int G, const hq_config *cfg,
                           void *stream);
@@ -416,8 +421,9 @@ int hq_plan_passes(int n, const hq_gate *gates, int G, int max_blocks, int *reco
  * (no counterpart in the paper): the next `count` device scratch allocations
  * the library takes from the stream-ordered allocator (hq_expectation,
  * hq_reduced_density_matrix, the channel sampling of hq_apply_kraus_sampled
- * and hq_run_trajectory, hq_dm_expectation, the CUDA-core wide blocks and
- * the tile-pass engine of hq_apply_blocks) fail as if the device were out of
+ * and hq_run_trajectory, hq_dm_expectation, and the matrix buffers of the
+ * CUDA-core wide blocks, the tensor-core engines and the tile-pass engine of
+ * hq_apply_blocks) fail as if the device were out of
  * memory; the entry point that meets one returns HQ_ERR_ALLOC (work it had
  * enqueued before stays enqueued).  count = 0 turns it off.  Process-wide;
  * host only.  Errors: HQ_ERR_ARG (count < 0).
@@ -545,6 +551,21 @@ hq_status hq_batch_run(hq_batch *b, void *stream);
  * out (2 s without progress).
  */
 hq_status hq_batch_latencies(hq_batch *b, void *stream, float *latency_us, double *makespan_us);
+
+/*
+ * hq_test_batch_wait_limit_ns -- for tests of the bounded-wait path (no
+ * counterpart in the paper).  The batch runner's scheduler gives up, raises
+ * the device error flag and ends its CTA once it has searched for `ns`
+ * nanoseconds without finding a tile it may run; the next hq_batch_latencies
+ * (or any other entry point that reads the flag) then returns HQ_ERR_TIMEOUT
+ * and clears it.  The default limit is 2 s; ns = 0 restores it.  The limit
+ * is a device variable of the current device, read by every launch of the
+ * runner from then on (graphs already instantiated included); set it while
+ * no batch run is in flight.  A run that gave up leaves its states partly
+ * evolved; the next run starts them again from |0..0>.
+ * Errors: HQ_ERR_CUDA.
+ */
+hq_status hq_test_batch_wait_limit_ns(unsigned long long ns);
 
 /* hq_batch_destroy -- release the graph and the handle (not the workspace). */
 void hq_batch_destroy(hq_batch *b);

@@ -771,12 +771,17 @@ static hq_status run_block(void *state, int n, const int *qubits, const double *
     T2 *dm = nullptr;
     if (injected_alloc_failure() || cudaMallocAsync((void **)&dm, sizeof(T2) * D * D, s) != cudaSuccess)
         return HQ_ERR_ALLOC;
-    HQ_CUDA(cudaMemcpyAsync(dm, hm.data(), sizeof(T2) * D * D, cudaMemcpyHostToDevice, s));
+    hq_status st = cuda_status("copy block matrix", cudaMemcpyAsync(dm, hm.data(), sizeof(T2) * D * D,
+                                                                    cudaMemcpyHostToDevice, s));
+    if (st != HQ_OK) {
+        cudaFreeAsync(dm, s);
+        return st;
+    }
     const size_t smem = sizeof(T2) * (size_t(D * D) + (size_t(1) << g.L));
     const void *fn = (const void *)k_block<R, K>;
     const int grid = grid_for(fn, kThreads, smem, g.total_tiles);
     k_block<R, K><<<grid, kThreads, smem, s>>>(g, dm, (T2 *)state);
-    hq_status st = cuda_status("k_block", cudaGetLastError());
+    st = cuda_status("k_block", cudaGetLastError());
     cudaFreeAsync(dm, s);
     return st;
 }

@@ -22,7 +22,8 @@
 // in shared memory instead of loading it.  Tile data written by other CTAs is read through L2 (ld.global.cg)
 // after an acquire fence, because L1 is not coherent within a launch.  Every
 // wait is bounded: with no progress for 2 s the kernel raises the device error
-// flag and exits (reported as HQ_ERR_TIMEOUT).  Per-circuit completion times
+// flag and exits (reported as HQ_ERR_TIMEOUT; hq_test_batch_wait_limit_ns
+// shortens the limit so that tests can take this path with a correct kernel).  Per-circuit completion times
 // come from %globaltimer.  The launch (counter reset + kernel) is captured once
 // into a CUDA graph and replayed by hq_batch_run.
 #include <algorithm>
@@ -51,6 +52,10 @@ extern __device__ unsigned int g_device_error;
 constexpr int kBThreads = 256;
 constexpr int kBMaxHigh = 8;
 constexpr uint64_t kBatchStallNs = 2000000000ull;
+// How long the scheduler may search without finding work before it gives up
+// (kBatchStallNs unless hq_test_batch_wait_limit_ns set another limit); read
+// once per CTA at the start of every launch.
+__device__ unsigned long long g_batch_stall_ns = kBatchStallNs;
 
 struct BGate {
     int k;          // 1 or 2
@@ -106,6 +111,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
     __shared__ BPass s_ps;
     __shared__ int64_t s_hioff[1 << kBMaxHigh];  // global offset of the tile's high-bit pattern h
     if (threadIdx.x == 0) atomicMin(p.t0, now_ns());
+    const unsigned long long stall_ns = *reinterpret_cast<const volatile unsigned long long *>(&g_batch_stall_ns);
 
     for (;;) {
         // ---------------- find work (warp 0) ----------------
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
                     }
                 }
                 if (found) break;
-                if (now_ns() - t_start > kBatchStallNs) {
+                if (now_ns() - t_start > stall_ns) {
                     if (lane == 0) atomicOr(&g_device_error, 2u);
                     stop = 1;
                     break;
@@ -577,6 +583,12 @@ extern "C" hq_status hq_batch_latencies(hq_batch *b, void *stream, float *latenc
     }
     if (makespan_us) *makespan_us = double(mx - t0) * 1e-3;
     return HQ_OK;
+}
+
+extern "C" hq_status hq_test_batch_wait_limit_ns(unsigned long long ns)
+{
+    const unsigned long long v = ns ? ns : kBatchStallNs;
+    return cuda_status("set scheduler wait limit", cudaMemcpyToSymbol(g_batch_stall_ns, &v, sizeof(v)));
 }
 
 extern "C" void hq_batch_destroy(hq_batch *b)

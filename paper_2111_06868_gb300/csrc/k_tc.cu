@@ -45,6 +45,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "hq_fault.cuh"
 #include "hq_tcgen05.cuh"
 
 namespace hq {
@@ -751,7 +752,8 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
     for (int g = 0; g < G; ++g)
         if (tc_eligible(n, gates[g], tc_min_k)) bytes += tc_matrix_bytes(n >= 13 ? 6 : gates[g].k);
     char *dmat = nullptr;
-    if (bytes && cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
+    if (bytes && (injected_alloc_failure() || cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess))
+        return HQ_ERR_ALLOC;
     hq_status st = HQ_OK;
     size_t off = 0;
     TcPrepared b;

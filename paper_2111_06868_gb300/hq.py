@@ -113,6 +113,7 @@ def load(path: str | None = None):
         "hq_run_trajectory": ([V, I, I, V, I, V, V, V, V], I),
         "hq_simplify": ([I, V, I, I, ctypes.c_double, V], I),
         "hq_test_fail_next_allocs": ([I], I),
+        "hq_test_batch_wait_limit_ns": ([ctypes.c_ulonglong], I),
         "hq_dm_superop": ([I, I, V, I, V, V, V], I),
         "hq_dm_init": ([V, I, I, ctypes.c_char_p, V], I),
         "hq_dm_apply": ([V, I, I, V, I, I, V, V], I),
@@ -666,3 +667,10 @@ def hq_test_fail_next_allocs(count: int) -> None:
     """Make the library's next `count` device scratch allocations fail
     (HQ_ERR_ALLOC), for tests of the error paths; 0 turns it off."""
     _check(load().hq_test_fail_next_allocs(int(count)), "hq_test_fail_next_allocs")
+
+
+def hq_test_batch_wait_limit_ns(ns: int) -> None:
+    """Let the batch runner's scheduler give up after `ns` nanoseconds without
+    work (HQ_ERR_TIMEOUT at the next hq_batch_latencies), for tests of the
+    bounded-wait path; 0 restores the 2 s default."""
+    _check(load().hq_test_batch_wait_limit_ns(int(ns)), "hq_test_batch_wait_limit_ns")

@@ -77,3 +77,70 @@ def test_density_matrix_expectation_reports_and_recovers(hq):
     H = [(1.0, ((0, "X"),)), (0.5, ((1, "Z"),))]
     expect_alloc_error(hq, lambda: hq.hq_dm_expectation(rho, H))
     assert abs(hq.hq_dm_expectation(rho, H) - 1.0) <= 1e-12
+
+
+def seeded_state(n, seed, dtype):
+    rng = np.random.default_rng(seed)  # input only
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    psi /= np.linalg.norm(psi)
+    st = torch.from_numpy(psi).to(getattr(torch, dtype)).cuda()
+    return st, st.cpu().numpy().astype(np.complex128)
+
+
+def rel_l2(got, want):
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+
+@pytest.mark.parametrize("engine", ["tc_f16", "tc_pass"])
+def test_tensor_core_matrix_buffer_reports_and_leaves_state(hq, engine):
+    """The tensor-core and tile-pass engines take their matrix buffer before
+    enqueueing any kernel: HQ_ERR_ALLOC leaves the state untouched."""
+    n = 15
+    st, psi = seeded_state(n, 7, "complex64")
+    rng = C.SplitMix64(3)
+    blocks = [((0, 3, 5, 8, 11, 14), C.random_unitary(6, rng)), ((1, 2, 4, 9, 12, 13), C.random_unitary(6, rng))]
+    before = st.clone()
+    expect_alloc_error(hq, lambda: hq.hq_apply_blocks(st, blocks, engine=engine))
+    torch.cuda.synchronize()
+    assert torch.equal(st, before)
+    hq.hq_apply_blocks(st, blocks, engine=engine)
+    for qs, m in blocks:
+        oracle.apply_gate(psi, n, qs, m)
+    assert rel_l2(st.cpu().numpy().astype(np.complex128), psi) <= 2e-6
+
+
+@pytest.mark.parametrize("dtype,tol", [("complex64", 2e-6), ("complex128", 1e-12)])
+def test_cuda_core_block_list_applies_the_prefix(hq, dtype, tol):
+    """CUDA-core wide blocks allocate one matrix copy each: after HQ_ERR_ALLOC
+    the blocks before the failing one have been applied and none after."""
+    n = 13
+    st, psi = seeded_state(n, 11, dtype)
+    rng = C.SplitMix64(5)
+    blocks = [((2, 7), C.random_unitary(2, rng)), ((0, 1, 4, 6, 9), C.random_unitary(5, rng)),
+              ((3, 5, 8, 10, 11, 12), C.random_unitary(6, rng))]
+    expect_alloc_error(hq, lambda: hq.hq_apply_blocks(st, blocks, engine="cuda_core"))
+    oracle.apply_gate(psi, n, *blocks[0])
+    got = st.cpu().numpy().astype(np.complex128)
+    err = np.abs(got - psi).max() if dtype == "complex128" else rel_l2(got, psi)
+    assert err <= tol
+    hq.hq_apply_blocks(st, blocks[1:], engine="cuda_core")
+    for qs, m in blocks[1:]:
+        oracle.apply_gate(psi, n, qs, m)
+    got = st.cpu().numpy().astype(np.complex128)
+    err = np.abs(got - psi).max() if dtype == "complex128" else rel_l2(got, psi)
+    assert err <= tol
+
+
+def test_kraus_sampled_reports_and_recovers(hq):
+    """A state-dependent channel whose scratch fails is not applied; the next
+    call samples the oracle's branch."""
+    n = 12
+    st, psi = seeded_state(n, 13, "complex128")
+    K = C.amplitude_damping(0.4)
+    before = st.clone()
+    expect_alloc_error(hq, lambda: hq.hq_apply_kraus_sampled(st, (4,), K, 0.3))
+    torch.cuda.synchronize()
+    assert torch.equal(st, before)
+    i, want = N.trajectory_step(psi, n, [4], K, 0.3)
+    assert hq.hq_apply_kraus_sampled(st, (4,), K, 0.3) == i
+    assert np.abs(st.cpu().numpy() - want).max() <= 1e-12

@@ -3,16 +3,17 @@
 Some callers cannot allocate device memory at the point of the call (all
 memory handed to their own pool, allocator calls forbidden in a serving loop,
 or another component capturing device work).  This file checks, through the C
-ABI, that the static-scratch variant returns what hq_expectation returns, on
-two calls in a row (the scratch keeps the previous call's contents), and that
-it refuses sums beyond its stated limit.  It is collected last on purpose and
-also passes when run alone in a fresh process.
+ABI, that the static-scratch variant returns what hq_expectation returns and
+what the CPU oracle computes on a copy of the same state, on two calls in a
+row (the scratch keeps the previous call's contents); that it takes no
+allocation (an injected allocation failure is still pending after it); and
+that it refuses sums beyond its stated limit.  It is collected last on
+purpose and also passes when run alone in a fresh process.
 """
-import math
-
 import numpy as np
 import pytest
 
+import oracle
 from paper_2111_06868_gb300 import circuits as C
 
 pytestmark = pytest.mark.gpu
@@ -52,15 +53,36 @@ def mixed_sum(n, seed):
     return H
 
 
-@pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-12), (torch.complex64, 2e-5)])
-def test_static_matches_allocating_entry_point_twice(hq, dtype, tol):
+# complex128: 1e-12; complex64: the library's expectation bar, 1e-5 x sum |coeff|
+@pytest.mark.parametrize("dtype,tol", [(torch.complex128, 1e-12), (torch.complex64, 1e-5)])
+def test_static_matches_allocating_entry_point_and_oracle_twice(hq, dtype, tol):
     # two different calls in a row: the second must not see the first's partial sums
     for n, seed in ((18, 1), (11, 2)):
         st = seeded_state(n, seed, dtype)
         H = mixed_sum(n, 10 + seed)
-        want = hq.hq_expectation(st, H)
+        scale = sum(abs(c) for c, _ in H)
+        want = oracle.expectation(st.cpu().numpy().astype(np.complex128), H)
         got = hq.hq_expectation_static(st, H)
-        assert abs(got - want) <= tol * max(1.0, abs(want)), (n, got, want)
+        assert abs(got - want) <= tol * scale, (n, got, want)
+        assert abs(got - hq.hq_expectation(st, H)) <= tol * scale
+
+
+def test_static_takes_no_allocation(hq):
+    """With one scratch-allocation failure injected, the static entry point
+    still succeeds, and the failure is left for the next allocating call."""
+    n = 16
+    st = seeded_state(n, 9, torch.complex128)
+    H = mixed_sum(n, 21)
+    want = oracle.expectation(st.cpu().numpy(), H)
+    hq.hq_test_fail_next_allocs(1)
+    try:
+        got = hq.hq_expectation_static(st, H)
+        with pytest.raises(hq.HQError) as e:
+            hq.hq_expectation(st, H)
+        assert e.value.name == "HQ_ERR_ALLOC"
+    finally:
+        hq.hq_test_fail_next_allocs(0)
+    assert abs(got - want) <= 1e-12 * sum(abs(c) for c, _ in H)
 
 
 def test_static_ansatz_hamiltonian(hq):
@@ -69,8 +91,8 @@ def test_static_ansatz_hamiltonian(hq):
     H = C.ansatz_hamiltonian(n)
     a = hq.hq_expectation_static(st, H)
     b = hq.hq_expectation_static(st, H)
-    want = hq.hq_expectation(st, H)
-    assert abs(a - want) <= 2e-5 * max(1.0, abs(want))
+    want = oracle.expectation(st.cpu().numpy().astype(np.complex128), H)
+    assert abs(a - want) <= 1e-5 * sum(abs(c) for c, _ in H)
     assert a == b
 
 
