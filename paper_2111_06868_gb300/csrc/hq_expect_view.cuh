@@ -1,0 +1,58 @@
+// hq_expect_view.cuh -- parameters of the register-view tile pass of the
+// Pauli-sum expectation (k_expect_view.cu), shared with its caller
+// (k_reduce.cu).
+#pragma once
+
+#include <vector>
+
+#include "hq_internal.cuh"
+
+namespace hq {
+
+constexpr int kEvMaxViews = 8;
+constexpr int kEvMaxTerms = 96;
+constexpr int kEvMaxGroups = 96;
+
+struct EvView {
+    int reg[5];   // tile-local positions of the register bits (NR of them), ascending
+    int thr[8];   // tile-local positions of the thread bits; thr[0..4] are the lane bits
+    int pj[32];   // swizzled shared-memory offset of register slot j
+    int g0, g1;   // its groups [g0, g1): diagonal groups first
+};
+struct EvTerm {
+    double w;       // diagonal: Re w; otherwise 2 Re w, or -2 Im w when imag
+    uint64_t zh;    // Z bits outside the tile (flat)
+    int zthr;       // Z bits on the view's thread positions (tile-local)
+    uint32_t smask; // bit j: parity of (j & register Z mask), off-diagonal terms
+    int view;
+    int imag;       // #Y odd: the pair sum takes Im(conj(a_j) a_{j^m})
+};
+struct EvGroup {
+    int m;   // X mask on the register bits (0: diagonal)
+    int h;   // register Z mask of a diagonal group
+    int t0, nt;
+    int view;
+};
+struct EvParams {
+    TileGeom g;
+    int nv, ng, nt;
+    EvView view[kEvMaxViews];
+    EvTerm term[kEvMaxTerms];
+    EvGroup grp[kEvMaxGroups];
+};
+// one term of a pass, in tile-local masks
+struct EvInTerm {
+    uint32_t xl, zl;  // X and Z masks on tile-local positions
+    uint64_t zh;      // Z bits outside the tile (flat)
+    double wr, wi;    // coeff * (-i)^#Y
+};
+
+// Views, terms and groups of one pass for tiles of L bits, NR register bits
+// and 2^slot_bits bank slots; false when a term does not fit (an X mask wider
+// than NR bits, more than kEvMaxViews views, or too many terms / groups).
+bool plan_expect_views(int L, int NR, int slot_bits, const std::vector<EvInTerm> &in, EvParams &p);
+// Launches one pass (grid CTAs, one per SM at most); partials[blockIdx.x].
+hq_status launch_expect_view(const void *state, hq_dtype dt, const EvParams &p, int grid, double *partials,
+                             cudaStream_t s);
+
+}  // namespace hq

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "hq_cp_async.cuh"
+#include "hq_expect_view.cuh"
 #include "hq_fault.cuh"
 #include "hq_internal.cuh"
 
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(kRedThreads) k_expect_final(const double *__re
 // popc(i & zl) and the tile base's part, folded into the weight once per tile.
 // ----------------------------------------------------------------------------
 constexpr int kTileTerms = 96;
+static_assert(kTileTerms <= kEvMaxTerms, "a tile pass must fit the register-view kernel's parameter block");
 struct TileTerm {
     int xl, zl;      // tile-local X and Z masks
     uint64_t zh;     // Z bits outside the tile
@@ -389,24 +391,26 @@ static hq_status build_groups(int n, const hq_pauli_term *terms, int T, std::vec
 }
 
 // Tile passes for the tiled evaluation: terms whose X mask has no bit above
-// the first tile go to pass 0; the others are packed greedily into passes of 7
-// low bits plus at most h higher bits.  Terms needing more than h higher bits
-// are left out (evaluated by the per-group kernel).
+// the first tile go to pass 0; the others are packed greedily into passes of
+// `low` low bits (1 KB runs) plus at most h = L - low higher bits.  Terms
+// needing more than h higher bits are left out (evaluated by the per-group
+// kernel).
 struct TilePass {
     std::vector<int> high;   // flat bits of the tile above the low run
     std::vector<Tm> terms;
 };
 
-static void plan_tile_passes(int n, int L, const std::vector<Tm> &tms, std::vector<TilePass> &passes,
+static void plan_tile_passes(int n, int L, int low, const std::vector<Tm> &tms, std::vector<TilePass> &passes,
                              std::vector<Tm> &rest)
 {
-    const int low = 7, h = L - low;
-    passes.assign(1, TilePass());
+    const int h = L - low;
+    passes.clear();
+    std::vector<Tm> low_terms;
     uint64_t cur = 0;
     int ci = -1;
     for (const Tm &m : tms) {
         if ((m.xm >> L) == 0) {
-            passes[0].terms.push_back(m);
+            low_terms.push_back(m);
             continue;
         }
         const uint64_t need = m.xm & ~((uint64_t(1) << low) - 1);
@@ -425,23 +429,78 @@ static void plan_tile_passes(int n, int L, const std::vector<Tm> &tms, std::vect
         for (int b = low; b < n; ++b)
             if ((cur >> b) & 1) passes[ci].high.push_back(b);
     }
-    if (passes[0].terms.empty()) passes.erase(passes.begin());
+    // the low tile's terms first, at most kTileTerms per pass (one parameter block)
+    std::vector<TilePass> first;
+    for (size_t i = 0; i < low_terms.size(); i += kTileTerms) {
+        first.emplace_back();
+        first.back().terms.assign(low_terms.begin() + i,
+                                  low_terms.begin() + std::min(low_terms.size(), i + size_t(kTileTerms)));
+    }
+    passes.insert(passes.begin(), first.begin(), first.end());
+}
+
+// One pass on the register-view kernel (k_expect_view.cu): the tile holds
+// the pass's high bits and the lowest other bits, L in all; false if its
+// terms do not fit the kernel's views (then the caller takes k_expect_tile).
+static bool try_view_pass(const void *state, int n, hq_dtype dt, const TilePass &tp, int grid, double *part,
+                          cudaStream_t s, hq_status &st)
+{
+    const int L = dt == HQ_C64 ? 13 : 12, NR = dt == HQ_C64 ? 5 : 4, SB = dt == HQ_C64 ? 4 : 3;
+    static thread_local EvParams ep;  // large: kept off the stack
+    std::memset(&ep, 0, sizeof(ep));
+    const int k = int(tp.high.size());
+    int q[64];
+    for (int j = 0; j < k; ++j) q[j] = n - 1 - tp.high[j];
+    make_geom(ep.g, n, k, q, L, 1);
+    int pos[64];
+    for (int b = 0; b < 64; ++b) pos[b] = -1;
+    for (int b = 0; b < ep.g.c; ++b) pos[b] = b;
+    for (int j = 0; j < ep.g.n_hi; ++j) pos[ep.g.hi_bits[j]] = ep.g.c + j;
+    uint64_t tmask = 0;
+    for (int b = 0; b < n; ++b)
+        if (pos[b] >= 0) tmask |= uint64_t(1) << b;
+    std::vector<EvInTerm> in;
+    for (const Tm &m : tp.terms) {
+        if (m.xm & ~tmask) return false;
+        EvInTerm t;
+        t.xl = t.zl = 0;
+        for (int b = 0; b < n; ++b) {
+            if ((m.xm >> b) & 1) t.xl |= 1u << pos[b];
+            if (((m.zm & tmask) >> b) & 1) t.zl |= 1u << pos[b];
+        }
+        t.zh = m.zm & ~tmask;
+        t.wr = m.wr;
+        t.wi = m.wi;
+        in.push_back(t);
+    }
+    if (!plan_expect_views(L, NR, SB, in, ep)) return false;
+    const int gx = int(std::min<int64_t>(std::min(grid, sm_count()), ep.g.total_tiles));
+    st = launch_expect_view(state, dt, ep, gx, part, s);
+    if (st == HQ_OK && gx < grid)
+        st = cuda_status("clear partials", cudaMemsetAsync(part + gx, 0, sizeof(double) * size_t(grid - gx), s));
+    return true;
 }
 
 // sum over the tile passes, into scratch[0]; scratch holds >= passes * grid + 1 doubles
 static hq_status launch_tiled(const void *state, int n, hq_dtype dt, const std::vector<TilePass> &passes, int grid,
                               double *scratch, cudaStream_t s)
 {
-    const int L = dt == HQ_C64 ? 13 : 12;
+    const int L = dt == HQ_C64 ? 13 : 12, low = dt == HQ_C64 ? 7 : 6;
     const size_t smem = (dt == HQ_C64 ? 8 : 16) * (size_t(1) << L);
     for (size_t pi = 0; pi < passes.size(); ++pi) {
         const TilePass &tp = passes[pi];
+        double *part = scratch + 1 + pi * size_t(grid);
+        hq_status vst = HQ_OK;
+        if (try_view_pass(state, n, dt, tp, grid, part, s, vst)) {
+            if (vst != HQ_OK) return vst;
+            continue;
+        }
         TileExpParams p;
         std::memset(&p, 0, sizeof(p));
         const int k = int(tp.high.size());
         int q[64];
         for (int j = 0; j < k; ++j) q[j] = n - 1 - tp.high[j];
-        make_geom(p.g, n, k, q, pi == 0 && k == 0 ? L : 7 + k, 1);
+        make_geom(p.g, n, k, q, k == 0 ? L : low + k, 1);
         // tile-local position of every tile bit: [0, c) then the high bits
         int pos[64];
         for (int b = 0; b < 64; ++b) pos[b] = -1;
@@ -470,7 +529,6 @@ static hq_status launch_tiled(const void *state, int n, hq_dtype dt, const std::
             tt.wi = m.wi;
         }
         const int gx = int(std::min<int64_t>(grid, p.g.total_tiles));
-        double *part = scratch + 1 + pi * size_t(grid);
         if (dt == HQ_C64) {
             occupancy((const void *)k_expect_tile<float>, kRedThreads, smem);
             k_expect_tile<float><<<gx, kRedThreads, smem, s>>>(p, (const float2 *)state, part);
@@ -500,7 +558,7 @@ hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pau
         const int ngroups = int(std::unique(xms.begin(), xms.end()) - xms.begin());
         std::vector<TilePass> passes;
         std::vector<Tm> rest;
-        plan_tile_passes(n, dt == HQ_C64 ? 13 : 12, tms, passes, rest);
+        plan_tile_passes(n, dt == HQ_C64 ? 13 : 12, dt == HQ_C64 ? 7 : 6, tms, passes, rest);
         if (ngroups >= 2 && rest.empty() && int(passes.size()) < ngroups) {
             const int grid = 3 * sm_count();
             double *scratch = nullptr;

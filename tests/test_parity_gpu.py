@@ -336,3 +336,74 @@ def test_popped_fused_circuit_expectation(hq, pinned):
     H = [(1.0, ((pinned[0], "Z"),)), (0.5, ((pinned[-1], "X"),))]
     want = oracle.expectation(oracle.simulate(circ), H)
     assert abs(hq.hq_expectation(st, H) - want) <= 1e-5 * 1.5
+
+
+def np_state(n, seed):
+    """Seeded normalised Gaussian state from numpy's generator (input only;
+    fast at the larger sizes)."""
+    rng = np.random.default_rng(seed)
+    psi = rng.standard_normal(1 << n) + 1j * rng.standard_normal(1 << n)
+    return psi / np.linalg.norm(psi)
+
+
+def structured_hamiltonian(n, seed):
+    """Terms of every shape the tiled kernels distinguish: diagonal strings
+    with Z on low, middle and high qubits; single X and Y; XX, YY, XY, YX on
+    neighbouring and distant pairs (more than four terms sharing one X mask);
+    X masks of three to six qubits with Z and Y mixed in; the identity."""
+    rng = C.SplitMix64(seed)
+
+    def coeff():
+        return rng.uniform() - 0.5
+
+    H = [(0.3, ())]
+
+    def add(c, term):
+        if len({q for q, _ in term}) == len(term):
+            H.append((c, term))
+
+    for q in range(n - 1):
+        H.append((coeff(), ((q, "Z"), (q + 1, "Z"))))
+    for q in range(0, n, 2):
+        add(coeff(), ((q, "Z"), ((q + 7) % n, "Z"), ((q + 11) % n, "Z")))
+    for q in range(n):
+        H.append((coeff(), ((q, "X"),)))
+        if q % 3 == 0:
+            H.append((coeff(), ((q, "Y"),)))
+    for q in range(0, n - 1, 2):
+        for a, b in (("X", "X"), ("Y", "Y"), ("X", "Y"), ("Y", "X"), ("Z", "X")):
+            H.append((coeff(), ((q, a), (q + 1, b))))
+    for q in range(0, n - 4, 5):
+        add(coeff(), ((q, "X"), (q + 2, "Y"), (q + 4, "X"), ((q + 8) % n, "Z")))
+        add(coeff(), tuple((q + j, "XY"[j % 2]) for j in range(min(6, n - q))))
+    return H
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n,seed", [(13, 5), (15, 6), (19, 7), (24, 8)])
+def test_expectation_structured_sums(hq, dt, n, seed):
+    """Register-view tile passes (diagonal strings by a Walsh-Hadamard
+    transform, X masks paired in registers or through shared memory) and the
+    fallback kernels, against the oracle."""
+    psi = np_state(n, 80 + n)
+    H = structured_hamiltonian(n, seed)
+    want = oracle.expectation(psi, H)
+    st = to_dev(psi, dt)
+    got = hq.hq_expectation(st, H)
+    tol = 1e-12 if dt == "c128" else 1e-5 * max(1.0, sum(abs(c) for c, _ in H))
+    assert abs(got - want) <= tol, (got, want)
+    # each term on its own (one X-mask group: the streaming kernel), summed
+    parts = sum(hq.hq_expectation(st, [t]) for t in H[:40])
+    assert abs(parts - oracle.expectation(psi, H[:40])) <= tol
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_expectation_ansatz_hamiltonian_large_state(hq, dt):
+    """The ansatz Hamiltonian at n = 22 (several tile passes, every X on its
+    own qubit) on a random state."""
+    n = 22
+    psi = np_state(n, 123)
+    H = C.ansatz_hamiltonian(n)
+    got = hq.hq_expectation(to_dev(psi, dt), H)
+    tol = 1e-12 if dt == "c128" else 1e-5 * sum(abs(c) for c, _ in H)
+    assert abs(got - oracle.expectation(psi, H)) <= tol
