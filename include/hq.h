@@ -519,6 +519,7 @@ typedef struct {
     int max_high;    /* high bits per pass, 1..8, < tile_bits (0 = 6) */
     int ctas_per_sm; /* persistent CTAs per SM (0 = as many as fit) */
     int small_first; /* queue circuits smallest first (lower median latency) instead of largest first */
+    int fuse_k;      /* width of the blocks a pass's gates are fused into (Sec. 3.1 compress), 1..3 (0 = 2) */
 } hq_batch_config;
 
 typedef struct hq_batch hq_batch; /* opaque plan + instantiated CUDA graph */

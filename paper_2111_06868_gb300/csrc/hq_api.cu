@@ -1,5 +1,6 @@
 // hq_api.cu -- the extern "C" entry points of libhq.so (declared in include/hq.h):
 // argument validation on the host, then kernel dispatch on the caller's stream.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -40,6 +41,109 @@ int sm_count()
         cached[dev] = v > 0 ? v : 1;
     }
     return cached[dev];
+}
+
+// ----------------------------------------------------------------------------
+// Host -> device uploads of small operands (matrices, channel data) through
+// pinned staging memory owned by the library.  A copy from pageable memory
+// makes the driver synchronise the stream first and goes through its own
+// bounce buffer; from pinned memory the copy is only enqueued, so the host
+// keeps enqueueing kernels.  Each host thread keeps, per device, a ring of
+// kStageSlots buffers; a slot is refilled only after the copy that last read
+// it has completed (an event recorded behind that copy).
+// ----------------------------------------------------------------------------
+namespace {
+constexpr int kStageSlots = 4;
+struct StageSlot {
+    void *host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+};
+struct StageRing {
+    StageSlot slot[kStageSlots];
+    int next = 0;
+    cudaStream_t side = nullptr;  // uploads that must not queue behind the caller's kernels
+};
+thread_local StageRing t_stage[64];
+
+hq_status stage_ring(StageRing **out)
+{
+    int dev = 0;
+    hq_status st = cuda_status("cudaGetDevice", cudaGetDevice(&dev));
+    if (st != HQ_OK) return st;
+    if (dev < 0 || dev >= 64) return HQ_ERR_ARG;
+    *out = &t_stage[dev];
+    return HQ_OK;
+}
+
+// fills the next slot with src and enqueues its copy to dst on stream `on`
+hq_status stage_copy(StageRing &ring, void *dst, const void *src, size_t bytes, cudaStream_t on, StageSlot **used)
+{
+    hq_status st = HQ_OK;
+    StageSlot &sl = ring.slot[ring.next];
+    ring.next = (ring.next + 1) % kStageSlots;
+    if (!sl.done && (st = cuda_status("create staging event",
+                                      cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming))) != HQ_OK)
+        return st;
+    if (sl.pending && (st = cuda_status("wait for staging slot", cudaEventSynchronize(sl.done))) != HQ_OK) return st;
+    sl.pending = false;
+    if (sl.cap < bytes) {
+        if (sl.host) cudaFreeHost(sl.host);
+        sl.host = nullptr;
+        sl.cap = 0;
+        const size_t cap = std::max(bytes, size_t(1) << 20);
+        if (cudaHostAlloc(&sl.host, cap, cudaHostAllocDefault) != cudaSuccess) {
+            sl.host = nullptr;
+            set_last_error_text("pinned staging buffer: cudaHostAlloc failed");
+            return HQ_ERR_ALLOC;
+        }
+        sl.cap = cap;
+    }
+    std::memcpy(sl.host, src, bytes);
+    if ((st = cuda_status("upload", cudaMemcpyAsync(dst, sl.host, bytes, cudaMemcpyHostToDevice, on))) != HQ_OK)
+        return st;
+    if ((st = cuda_status("record staging event", cudaEventRecord(sl.done, on))) != HQ_OK) return st;
+    sl.pending = true;
+    *used = &sl;
+    return HQ_OK;
+}
+}  // namespace
+
+hq_status upload_async(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) return HQ_OK;
+    StageRing *ring = nullptr;
+    StageSlot *sl = nullptr;
+    hq_status st = stage_ring(&ring);
+    if (st != HQ_OK) return st;
+    return stage_copy(*ring, dst, src, bytes, s, &sl);
+}
+
+hq_status upload_side(void *dst, const void *src, size_t bytes, cudaStream_t s, cudaEvent_t dst_ready)
+{
+    if (bytes == 0) return HQ_OK;
+    StageRing *ring = nullptr;
+    StageSlot *sl = nullptr;
+    hq_status st = stage_ring(&ring);
+    if (st != HQ_OK) return st;
+    if (!ring->side &&
+        (st = cuda_status("create upload stream", cudaStreamCreateWithFlags(&ring->side, cudaStreamNonBlocking))) !=
+            HQ_OK)
+        return st;
+    if (dst_ready && (st = cuda_status("order upload", cudaStreamWaitEvent(ring->side, dst_ready, 0))) != HQ_OK)
+        return st;
+    if ((st = stage_copy(*ring, dst, src, bytes, ring->side, &sl)) != HQ_OK) return st;
+    return cuda_status("wait for upload", cudaStreamWaitEvent(s, sl->done, 0));
+}
+
+cudaEvent_t call_event()
+{
+    static thread_local cudaEvent_t ev[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!ev[dev] && cudaEventCreateWithFlags(&ev[dev], cudaEventDisableTiming) != cudaSuccess) ev[dev] = nullptr;
+    return ev[dev];
 }
 
 hq_status check_qubits(int n, int k, const int *qubits, int kmax)

@@ -24,6 +24,17 @@ hq_status cuda_status(const char *what, cudaError_t e);  // HQ_OK or HQ_ERR_CUDA
     } while (0)
 
 int sm_count();  // SMs of the current device (cached per device)
+// Enqueues on `s` a copy of `bytes` host bytes at `src` to device `dst`
+// through the library's pinned staging memory (no stream synchronisation;
+// `src` may be reused as soon as this returns).  HQ_ERR_ALLOC if pinned memory
+// cannot be had, HQ_ERR_CUDA on a failed CUDA call.
+hq_status upload_async(void *dst, const void *src, size_t bytes, cudaStream_t s);
+// The same copy on the library's upload stream instead, ordered after the
+// event dst_ready (recorded on s once dst is allocated; NULL: no wait), with
+// s made to wait for it: it does not queue behind the kernels already on s.
+hq_status upload_side(void *dst, const void *src, size_t bytes, cudaStream_t s, cudaEvent_t dst_ready);
+// A per-thread, per-device event for one call's orderings (NULL on failure).
+cudaEvent_t call_event();
 // resident CTAs per SM of `fn` (sets the dynamic shared-memory attribute when
 // smem > 48 KB), and a grid of at most that many CTAs per SM
 int occupancy(const void *fn, int threads, size_t smem);
@@ -226,6 +237,9 @@ struct PassPlanEntry {
 void plan_passes(int n, const hq_gate *gates, int G, int max_blocks, std::vector<PassPlanEntry> &plan);
 hq_status launch_tc_passes(void *state, int n, const hq_gate *gates, int G, int max_blocks, cudaStream_t s);
 hq_status pass_error_status();
+// HQ_ERR_TIMEOUT (and the flag cleared) if a batch run's scheduler gave up
+// (k_batch.cu); device_error_status() checks it too.
+hq_status batch_error_status();
 
 // validation helpers (hq_api.cu)
 hq_status check_qubits(int n, int k, const int *qubits, int kmax);

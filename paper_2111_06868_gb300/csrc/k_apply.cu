@@ -771,8 +771,7 @@ static hq_status run_block(void *state, int n, const int *qubits, const double *
     T2 *dm = nullptr;
     if (injected_alloc_failure() || cudaMallocAsync((void **)&dm, sizeof(T2) * D * D, s) != cudaSuccess)
         return HQ_ERR_ALLOC;
-    hq_status st = cuda_status("copy block matrix", cudaMemcpyAsync(dm, hm.data(), sizeof(T2) * D * D,
-                                                                    cudaMemcpyHostToDevice, s));
+    hq_status st = upload_async(dm, hm.data(), sizeof(T2) * D * D, s);
     if (st != HQ_OK) {
         cudaFreeAsync(dm, s);
         return st;

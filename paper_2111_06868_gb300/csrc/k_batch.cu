@@ -2,7 +2,8 @@
 // (hq_batch_*), for serving-style loads.
 //
 // Each circuit is evolved from |0..0> by Sec. 4.2's gate-by-gate product, with
-// its gates grouped into "passes": a pass is one read and one write of the
+// its gates grouped into "passes" (and, inside a pass, fused by Sec. 3.1's
+// compress rule into blocks of at most fuse_k = 1..3 qubits): a pass is one read and one write of the
 // state, during which every tile of 2^(R+|H|) amplitudes -- the R lowest bits
 // (one contiguous run) plus a set H of at most h higher bits -- stays in shared
 // memory while the pass's gates are applied to it one after another.  Gates
@@ -47,7 +48,10 @@ struct hq_batch {
 
 namespace hq {
 
-extern __device__ unsigned int g_device_error;
+// Raised when the scheduler gave up (its own flag: device variables are not
+// shared between translation units of this library, which is built without
+// relocatable device code).
+__device__ unsigned int g_batch_error;
 
 constexpr int kBThreads = 256;
 constexpr int kBMaxHigh = 8;
@@ -57,11 +61,12 @@ constexpr uint64_t kBatchStallNs = 2000000000ull;
 // once per CTA at the start of every launch.
 __device__ unsigned long long g_batch_stall_ns = kBatchStallNs;
 
+constexpr int kBMaxFuse = 3;  // widest in-pass fused block
 struct BGate {
-    int k;          // 1 or 2
+    int k;          // 1..kBMaxFuse
     int diag;       // matrix is diagonal
-    int tpos[2];    // tile positions of qubits[0], qubits[1]
-    float2 m[16];   // 2^k x 2^k, row-major (complex64)
+    int tpos[kBMaxFuse];  // tile positions of qubits[0..k)
+    int moff;       // its 2^k x 2^k matrix (row-major, complex64) at mat[moff]
 };
 struct BPass {
     int circuit;
@@ -81,6 +86,7 @@ struct BatchParams {
     const BCircuit *circ;
     const BPass *pass;
     const BGate *gate;
+    const float2 *mat;
     int C, P;
     // per-run counters (zeroed by the graph before every launch)
     int *next_tile;          // [P]
@@ -110,6 +116,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
     __shared__ long long s_tile;
     __shared__ BPass s_ps;
     __shared__ int64_t s_hioff[1 << kBMaxHigh];  // global offset of the tile's high-bit pattern h
+    __shared__ __align__(16) float2 s_m3[64];     // matrix of the current 3-qubit block
     if (threadIdx.x == 0) atomicMin(p.t0, now_ns());
     const unsigned long long stall_ns = *reinterpret_cast<const volatile unsigned long long *>(&g_batch_stall_ns);
 
@@ -158,7 +165,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
                 }
                 if (found) break;
                 if (now_ns() - t_start > stall_ns) {
-                    if (lane == 0) atomicOr(&g_device_error, 2u);
+                    if (lane == 0) atomicOr(&g_batch_error, 1u);
                     stop = 1;
                     break;
                 }
@@ -216,16 +223,48 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
         // ---------------- gates, in order ----------------
         for (int gi = ps.g0; gi < ps.g0 + ps.ng; ++gi) {
             const BGate &gt = p.gate[gi];
+            const float2 *gm = p.mat + gt.moff;
             if (gt.diag) {
                 for (int i = threadIdx.x; i < TS; i += blockDim.x) {
-                    int r = (i >> gt.tpos[0]) & 1;
-                    if (gt.k == 2) r = (r << 1) | ((i >> gt.tpos[1]) & 1);
+                    int r = 0;
+                    for (int j = 0; j < gt.k; ++j) r = (r << 1) | ((i >> gt.tpos[j]) & 1);
                     const int D = 1 << gt.k;
-                    tile[swz<float>(i)] = cmul(gt.m[r * D + r], tile[swz<float>(i)]);
+                    tile[swz<float>(i)] = cmul(gm[r * D + r], tile[swz<float>(i)]);
+                }
+            } else if (gt.k == 3) {
+                // the 8 x 8 matrix from shared memory, two entries per load
+                // (kept out of registers: 128 of them would cap the CTAs per SM)
+                if (threadIdx.x < 32)
+                    reinterpret_cast<float4 *>(s_m3)[threadIdx.x] = reinterpret_cast<const float4 *>(gm)[threadIdx.x];
+                __syncthreads();
+                const int p0 = gt.tpos[0], p1 = gt.tpos[1], p2 = gt.tpos[2];
+                const int b0 = min(p0, min(p1, p2)), b2 = max(p0, max(p1, p2)), b1 = p0 + p1 + p2 - b0 - b2;
+                for (int grp = threadIdx.x; grp < TS / 8; grp += blockDim.x) {
+                    int i0 = ((grp >> b0) << (b0 + 1)) | (grp & ((1 << b0) - 1));
+                    i0 = ((i0 >> b1) << (b1 + 1)) | (i0 & ((1 << b1) - 1));
+                    i0 = ((i0 >> b2) << (b2 + 1)) | (i0 & ((1 << b2) - 1));
+                    int idx[8];
+                    float2 x[8];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        idx[r] = swz<float>(i0 | (((r >> 2) & 1) << p0) | (((r >> 1) & 1) << p1) | ((r & 1) << p2));
+                        x[r] = tile[idx[r]];
+                    }
+#pragma unroll 2
+                    for (int r = 0; r < 8; ++r) {
+                        float2 y = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int c = 0; c < 8; c += 2) {
+                            const float4 mm = reinterpret_cast<const float4 *>(s_m3)[(r * 8 + c) >> 1];
+                            cmac(y, make_float2(mm.x, mm.y), x[c]);
+                            cmac(y, make_float2(mm.z, mm.w), x[c + 1]);
+                        }
+                        tile[idx[r]] = y;
+                    }
                 }
             } else if (gt.k == 1) {
                 const int tp = gt.tpos[0];
-                const float2 m00 = gt.m[0], m01 = gt.m[1], m10 = gt.m[2], m11 = gt.m[3];
+                const float2 m00 = gm[0], m01 = gm[1], m10 = gm[2], m11 = gm[3];
                 for (int grp = threadIdx.x; grp < TS / 2; grp += blockDim.x) {
                     const int i0 = ((grp >> tp) << (tp + 1)) | (grp & ((1 << tp) - 1));
                     const int a = swz<float>(i0), b = swz<float>(i0 | (1 << tp));
@@ -255,7 +294,7 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
                     for (int r = 0; r < 4; ++r) {
                         float2 y = make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) cmac(y, gt.m[r * 4 + c], x[c]);
+                        for (int c = 0; c < 4; ++c) cmac(y, gm[r * 4 + c], x[c]);
                         tile[idx[r]] = y;
                     }
                 }
@@ -290,19 +329,34 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
     }
 }
 
+hq_status batch_error_status()
+{
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_batch_error, sizeof(v));
+    if (e != cudaSuccess) return cuda_status("read batch error flag", e);
+    if (v) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_batch_error, &zero, sizeof(zero));
+        if (e != cudaSuccess) return cuda_status("clear batch error flag", e);
+        return HQ_ERR_TIMEOUT;
+    }
+    return HQ_OK;
+}
+
 static size_t align_up256(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct BatchPlan {
     std::vector<BCircuit> circ;
     std::vector<BPass> pass;
     std::vector<BGate> gate;
+    std::vector<float2> mat;      // matrices of the fused in-pass blocks
     std::vector<int> first_pass;  // per circuit
     std::vector<int> prio;        // circuit ids, highest priority first
     int64_t total_gates = 0;
 };
 
 // Groups one circuit's gates into passes (see the file comment).
-static hq_status plan_circuit(const hq_circuit &c, int ci, int R0, int h, BatchPlan &pl)
+static hq_status plan_circuit(const hq_circuit &c, int ci, int R0, int h, int fuse_k, BatchPlan &pl)
 {
     const int n = c.n;
     const int R = std::min(n, R0);
@@ -357,18 +411,20 @@ static hq_status plan_circuit(const hq_circuit &c, int ci, int R0, int h, BatchP
             return -1;
         };
         // the pass's gates, fused with the same compress rule into blocks of at
-        // most 2 qubits (fewer sweeps over the tile in shared memory)
+        // most fuse_k qubits (fewer sweeps over the tile in shared memory, more
+        // multiply-adds per sweep: 2^fuse_k per amplitude)
         std::vector<hq_gate> pg;
         for (int g : ps[pi].gates) pg.push_back(c.gates[g]);
         std::vector<hq_gate> fb(std::max<size_t>(pg.size(), 1));
-        std::vector<double> pool(std::max<size_t>(pg.size(), 1) * 2 * 16);
+        std::vector<double> pool(std::max<size_t>(pg.size(), 1) * 2 * (size_t(1) << (2 * kBMaxFuse)));
         int nb = int(fb.size());
-        if (!pg.empty()) {
-            const hq_status fst = hq_fuse(n, pg.data(), int(pg.size()), 2, fb.data(), &nb, pool.data(),
+        if (!pg.empty() && fuse_k > 1) {
+            const hq_status fst = hq_fuse(n, pg.data(), int(pg.size()), fuse_k, fb.data(), &nb, pool.data(),
                                           int64_t(pool.size()), nullptr);
             if (fst != HQ_OK) return fst;
         } else {
-            nb = 0;
+            nb = int(pg.size());
+            for (int i = 0; i < nb; ++i) fb[i] = pg[i];
         }
         bp.ng = nb;
         for (int i = 0; i < nb; ++i) {
@@ -379,7 +435,8 @@ static hq_status plan_circuit(const hq_circuit &c, int ci, int R0, int h, BatchP
             bg.diag = is_diagonal(gt.k, gt.matrix);
             for (int j = 0; j < gt.k; ++j) bg.tpos[j] = tpos(n - 1 - gt.qubits[j]);
             const int D = 1 << gt.k;
-            for (int e = 0; e < D * D; ++e) bg.m[e] = make_float2(float(gt.matrix[2 * e]), float(gt.matrix[2 * e + 1]));
+            bg.moff = int(pl.mat.size());
+            for (int e = 0; e < D * D; ++e) pl.mat.push_back(make_float2(float(gt.matrix[2 * e]), float(gt.matrix[2 * e + 1])));
             pl.gate.push_back(bg);
         }
         pl.pass.push_back(bp);
@@ -389,17 +446,18 @@ static hq_status plan_circuit(const hq_circuit &c, int ci, int R0, int h, BatchP
 }
 
 struct BatchLayout {
-    size_t circ, pass, gate, prio, next_tile, done_tile, cur_pass, wm, end_ns, image, total, counters_begin,
+    size_t circ, pass, gate, mat, prio, next_tile, done_tile, cur_pass, wm, end_ns, image, total, counters_begin,
         counters_bytes;
 };
 
-static BatchLayout batch_layout(size_t C, size_t P, size_t G)
+static BatchLayout batch_layout(size_t C, size_t P, size_t G, size_t M)
 {
     BatchLayout L;
     L.circ = 0;
     L.pass = align_up256(L.circ + C * sizeof(BCircuit));
     L.gate = align_up256(L.pass + P * sizeof(BPass));
-    L.prio = align_up256(L.gate + std::max<size_t>(G, 1) * sizeof(BGate));
+    L.mat = align_up256(L.gate + std::max<size_t>(G, 1) * sizeof(BGate));
+    L.prio = align_up256(L.mat + std::max<size_t>(M, 1) * sizeof(float2));
     // per-run counters from here on, reset from the image before every run
     L.next_tile = align_up256(L.prio + C * sizeof(int));
     L.done_tile = L.next_tile + P * sizeof(int);
@@ -413,14 +471,17 @@ static BatchLayout batch_layout(size_t C, size_t P, size_t G)
     return L;
 }
 
-static hq_status check_batch(const hq_circuit *cs, int C, const hq_batch_config *cfg, int &R0, int &h, int &per_sm)
+static hq_status check_batch(const hq_circuit *cs, int C, const hq_batch_config *cfg, int &R0, int &h, int &per_sm,
+                             int &fuse_k)
 {
     if (C < 1) return HQ_ERR_ARG;
     if (!cs) return HQ_ERR_NULL;
     const int L = (cfg && cfg->tile_bits) ? cfg->tile_bits : 12;
     h = (cfg && cfg->max_high) ? cfg->max_high : 6;
     per_sm = (cfg && cfg->ctas_per_sm) ? cfg->ctas_per_sm : 0;
+    fuse_k = (cfg && cfg->fuse_k) ? cfg->fuse_k : 2;
     if (L < 6 || L > 13 || h < 1 || h > kBMaxHigh || h >= L || per_sm < 0 || per_sm > 8) return HQ_ERR_ARG;
+    if (fuse_k < 1 || fuse_k > kBMaxFuse) return HQ_ERR_ARG;
     R0 = L - h;
     for (int c = 0; c < C; ++c) {
         if (cs[c].n < 1 || cs[c].n > 30) return HQ_ERR_N_TOO_LARGE;
@@ -437,7 +498,7 @@ static hq_status check_batch(const hq_circuit *cs, int C, const hq_batch_config 
     return HQ_OK;
 }
 
-static hq_status plan_batch(const hq_circuit *cs, int C, int R0, int h, int small_first, BatchPlan &pl)
+static hq_status plan_batch(const hq_circuit *cs, int C, int R0, int h, int fuse_k, int small_first, BatchPlan &pl)
 {
     // priority order of the circuits: largest first (shortest
     // makespan) or smallest first (lowest median completion time)
@@ -449,7 +510,7 @@ static hq_status plan_batch(const hq_circuit *cs, int C, int R0, int h, int smal
     for (int c = 0; c < C; ++c) {
         pl.circ[c].state = static_cast<float2 *>(cs[c].state);
         pl.circ[c].n = cs[c].n;
-        hq_status st = plan_circuit(cs[c], c, R0, h, pl);
+        hq_status st = plan_circuit(cs[c], c, R0, h, fuse_k, pl);
         if (st != HQ_OK) return st;
     }
     pl.prio = order;
@@ -462,11 +523,11 @@ using namespace hq;
 
 extern "C" size_t hq_batch_workspace_bytes(const hq_circuit *cs, int C, const hq_batch_config *cfg)
 {
-    int R0, h, per_sm;
-    if (check_batch(cs, C, cfg, R0, h, per_sm) != HQ_OK) return 0;
+    int R0, h, per_sm, fuse_k;
+    if (check_batch(cs, C, cfg, R0, h, per_sm, fuse_k) != HQ_OK) return 0;
     BatchPlan pl;
-    if (plan_batch(cs, C, R0, h, cfg ? cfg->small_first : 0, pl) != HQ_OK) return 0;
-    return batch_layout(C, pl.pass.size(), pl.gate.size()).total;
+    if (plan_batch(cs, C, R0, h, fuse_k, cfg ? cfg->small_first : 0, pl) != HQ_OK) return 0;
+    return batch_layout(C, pl.pass.size(), pl.gate.size(), pl.mat.size()).total;
 }
 
 extern "C" hq_status hq_batch_create(const hq_circuit *cs, int C, const hq_batch_config *cfg, void *workspace,
@@ -474,15 +535,15 @@ extern "C" hq_status hq_batch_create(const hq_circuit *cs, int C, const hq_batch
 {
     if (!out) return HQ_ERR_NULL;
     *out = nullptr;
-    int R0, h, per_sm;
-    hq_status st = check_batch(cs, C, cfg, R0, h, per_sm);
+    int R0, h, per_sm, fuse_k;
+    hq_status st = check_batch(cs, C, cfg, R0, h, per_sm, fuse_k);
     if (st != HQ_OK) return st;
     if (!workspace) return HQ_ERR_NULL;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return HQ_ERR_ALIGN;
     BatchPlan pl;
-    if ((st = plan_batch(cs, C, R0, h, cfg ? cfg->small_first : 0, pl)) != HQ_OK) return st;
+    if ((st = plan_batch(cs, C, R0, h, fuse_k, cfg ? cfg->small_first : 0, pl)) != HQ_OK) return st;
     const size_t P = pl.pass.size();
-    const BatchLayout L = batch_layout(C, P, pl.gate.size());
+    const BatchLayout L = batch_layout(C, P, pl.gate.size(), pl.mat.size());
     if (ws_bytes < L.total) return HQ_ERR_CAPACITY;
     cudaStream_t s = (cudaStream_t)stream;
     char *ws = static_cast<char *>(workspace);
@@ -490,6 +551,8 @@ extern "C" hq_status hq_batch_create(const hq_circuit *cs, int C, const hq_batch
     HQ_CUDA(cudaMemcpyAsync(ws + L.pass, pl.pass.data(), P * sizeof(BPass), cudaMemcpyHostToDevice, s));
     if (!pl.gate.empty())
         HQ_CUDA(cudaMemcpyAsync(ws + L.gate, pl.gate.data(), pl.gate.size() * sizeof(BGate), cudaMemcpyHostToDevice, s));
+    if (!pl.mat.empty())
+        HQ_CUDA(cudaMemcpyAsync(ws + L.mat, pl.mat.data(), pl.mat.size() * sizeof(float2), cudaMemcpyHostToDevice, s));
     HQ_CUDA(cudaStreamSynchronize(s));
 
     HQ_CUDA(cudaMemcpyAsync(ws + L.prio, pl.prio.data(), C * sizeof(int), cudaMemcpyHostToDevice, s));
@@ -508,6 +571,7 @@ extern "C" hq_status hq_batch_create(const hq_circuit *cs, int C, const hq_batch
     bp.circ = reinterpret_cast<const BCircuit *>(ws + L.circ);
     bp.pass = reinterpret_cast<const BPass *>(ws + L.pass);
     bp.gate = reinterpret_cast<const BGate *>(ws + L.gate);
+    bp.mat = reinterpret_cast<const float2 *>(ws + L.mat);
     bp.C = C;
     bp.P = int(P);
     bp.next_tile = reinterpret_cast<int *>(ws + L.next_tile);

@@ -510,8 +510,7 @@ hq_status run_trajectory(void *state, int n, hq_dtype dt, const hq_noisy_op *ops
     char *ws = nullptr;
     if (!dev.empty()) {
         if (injected_alloc_failure() || cudaMallocAsync((void **)&ws, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
-        hq_status cs = cuda_status("copy channel data", cudaMemcpyAsync(ws, hostbuf.data(), sizeof(double) * hostbuf.size(),
-                                                                        cudaMemcpyHostToDevice, s));
+        hq_status cs = upload_async(ws, hostbuf.data(), sizeof(double) * hostbuf.size(), s);
         if (cs == HQ_OK)
             cs = cuda_status("clear chosen", cudaMemsetAsync(ws + nd * sizeof(double), 0, sizeof(int) * (dev.size() + 1), s));
         if (cs != HQ_OK) {

@@ -867,7 +867,7 @@ hq_status launch_tc_passes(void *state, int n, const hq_gate *gates, int G, int 
     uint4 *dmat = nullptr;
     const size_t bytes = hb.size() * sizeof(uint16_t);
     if (injected_alloc_failure() || cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
-    hq_status st = cuda_status("copy pass matrices", cudaMemcpyAsync(dmat, hb.data(), bytes, cudaMemcpyHostToDevice, s));
+    hq_status st = upload_async(dmat, hb.data(), bytes, s);
     bi = 0;
     for (size_t pi = 0; pi < plan.size() && st == HQ_OK; ++pi) {
         const PassPlanEntry &pl = plan[pi];

@@ -742,12 +742,17 @@ static void widen_to_6(int n, const hq_gate &gt, hq_gate &w, std::vector<double>
 }
 
 // Launches the gates in order: tensor-core blocks take their split matrix
-// from one device buffer allocated up front (each block is prepared on the
-// host and copied just before its launch, so the host work overlaps the
-// kernels already queued); the other gates go through launch_gate.
+// from one device buffer allocated up front.  The blocks are prepared on the
+// host in two chunks (the first two blocks, then the rest, prepared while the
+// first two run); each chunk's matrices go up in one copy from pinned staging
+// memory on the library's upload stream, ordered only after the buffer's
+// allocation, so an upload never waits behind this call's kernels (or behind
+// a large copy the caller queued after them).  The other gates go through
+// launch_gate.
 static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G, int tc_min_k, int split_bf16,
                                 int64_t nstates, cudaStream_t s)
 {
+    constexpr int kFirstChunk = 2;
     size_t bytes = 0;
     for (int g = 0; g < G; ++g)
         if (tc_eligible(n, gates[g], tc_min_k)) bytes += tc_matrix_bytes(n >= 13 ? 6 : gates[g].k);
@@ -755,28 +760,45 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
     if (bytes && (injected_alloc_failure() || cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess))
         return HQ_ERR_ALLOC;
     hq_status st = HQ_OK;
+    cudaEvent_t allocated = call_event();
+    if (!allocated) st = HQ_ERR_CUDA;
+    if (st == HQ_OK) st = cuda_status("record allocation", cudaEventRecord(allocated, s));
     size_t off = 0;
-    TcPrepared b;
-    for (int g = 0; g < G && st == HQ_OK; ++g) {
-        const hq_gate &gt = gates[g];
-        if (!tc_eligible(n, gt, tc_min_k)) {
-            st = launch_gate(state, n, HQ_C64, gt.k, gt.qubits, gt.matrix, nstates, HQ_ENGINE_AUTO, s);
-            continue;
+    std::vector<TcPrepared> prep;
+    std::vector<uint16_t> host;
+    for (int g0 = 0; g0 < G && st == HQ_OK;) {
+        const int g1 = g0 == 0 ? std::min(G, kFirstChunk) : G;
+        prep.assign(size_t(g1 - g0), TcPrepared());
+        host.clear();
+        for (int g = g0; g < g1; ++g) {
+            const hq_gate &gt = gates[g];
+            if (!tc_eligible(n, gt, tc_min_k)) continue;
+            TcPrepared &b = prep[size_t(g - g0)];
+            if (gt.k < 6 && n >= 13) {
+                hq_gate w;
+                std::vector<double> wm;
+                widen_to_6(n, gt, w, wm);
+                prepare_tc_any(state, n, 6, w.qubits, w.matrix, nstates, split_bf16, b);
+            } else {
+                prepare_tc_any(state, n, gt.k, gt.qubits, gt.matrix, nstates, split_bf16, b);
+            }
+            b.p.bmat = reinterpret_cast<const uint4 *>(dmat + off + host.size() * sizeof(uint16_t));
+            host.insert(host.end(), b.b.begin(), b.b.end());
         }
-        if (gt.k < 6 && n >= 13) {
-            hq_gate w;
-            std::vector<double> wm;
-            widen_to_6(n, gt, w, wm);
-            prepare_tc_any(state, n, 6, w.qubits, w.matrix, nstates, split_bf16, b);
-        } else {
-            prepare_tc_any(state, n, gt.k, gt.qubits, gt.matrix, nstates, split_bf16, b);
+        if (!host.empty()) {
+            st = upload_side(dmat + off, host.data(), host.size() * sizeof(uint16_t), s, allocated);
+            off += host.size() * sizeof(uint16_t);
         }
-        const size_t nb = b.b.size() * sizeof(uint16_t);
-        st = cuda_status("copy split matrix", cudaMemcpyAsync(dmat + off, b.b.data(), nb, cudaMemcpyHostToDevice, s));
-        if (st != HQ_OK) break;
-        b.p.bmat = reinterpret_cast<const uint4 *>(dmat + off);
-        st = b.launch(b.p, b.tmap, state, s);
-        off += nb;
+        for (int g = g0; g < g1 && st == HQ_OK; ++g) {
+            const hq_gate &gt = gates[g];
+            if (!tc_eligible(n, gt, tc_min_k)) {
+                st = launch_gate(state, n, HQ_C64, gt.k, gt.qubits, gt.matrix, nstates, HQ_ENGINE_AUTO, s);
+                continue;
+            }
+            TcPrepared &b = prep[size_t(g - g0)];
+            st = b.launch(b.p, b.tmap, state, s);
+        }
+        g0 = g1;
     }
     if (dmat) cudaFreeAsync(dmat, s);
     return st;
@@ -803,6 +825,8 @@ hq_status device_error_status()
 {
     const hq_status ps = pass_error_status();
     if (ps != HQ_OK) return ps;
+    const hq_status bs = batch_error_status();
+    if (bs != HQ_OK) return bs;
     unsigned int v = 0;
     cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_error, sizeof(v));
     if (e != cudaSuccess) return cuda_status("read device error flag", e);

@@ -83,7 +83,7 @@ class hq_circuit(ctypes.Structure):
 
 class hq_batch_config(ctypes.Structure):
     _fields_ = [("tile_bits", ctypes.c_int), ("max_high", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-                ("small_first", ctypes.c_int)]
+                ("small_first", ctypes.c_int), ("fuse_k", ctypes.c_int)]
 
 
 _lib = None
@@ -507,25 +507,26 @@ def _batch_structs(circuits, states):
 
 
 def hq_batch_workspace_bytes(circuits, tile_bits: int = 0, max_high: int = 0, ctas_per_sm: int = 0,
-                             small_first: int = 0) -> int:
+                             small_first: int = 0, fuse_k: int = 0) -> int:
     arr, keep = _batch_structs(circuits, None)
-    cfg = hq_batch_config(tile_bits, max_high, ctas_per_sm, small_first)
+    cfg = hq_batch_config(tile_bits, max_high, ctas_per_sm, small_first, fuse_k)
     return int(load().hq_batch_workspace_bytes(arr, len(circuits), ctypes.byref(cfg)))
 
 
 class Batch:
     """hq_batch_create / run / latencies / destroy over torch-owned buffers.
-    ``states`` (one complex64 tensor of 2^n per circuit) is allocated if not given."""
+    ``states`` (one complex64 tensor of 2^n per circuit) is allocated if not
+    given.  ``fuse_k``: width of the in-pass fused blocks (1..3; 0 = 2)."""
 
     def __init__(self, circuits, states=None, tile_bits: int = 0, max_high: int = 0, ctas_per_sm: int = 0,
-                 small_first: int = 0, stream=None):
+                 small_first: int = 0, fuse_k: int = 0, stream=None):
         import torch
 
         self.circuits = list(circuits)
         if states is None:
             states = [torch.empty(1 << c.n, dtype=torch.complex64, device="cuda") for c in self.circuits]
         self.states = states
-        self.cfg = hq_batch_config(tile_bits, max_high, ctas_per_sm, small_first)
+        self.cfg = hq_batch_config(tile_bits, max_high, ctas_per_sm, small_first, fuse_k)
         arr, keep = _batch_structs(self.circuits, states)
         need = load().hq_batch_workspace_bytes(arr, len(self.circuits), ctypes.byref(self.cfg))
         if need == 0:

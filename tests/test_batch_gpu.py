@@ -33,8 +33,10 @@ def rel_l2(got, want):
     return float(np.linalg.norm(got - want) / np.linalg.norm(want))
 
 
-@pytest.mark.parametrize("cfg", [(0, 0, 0, 0), (8, 3, 0, 1), (11, 5, 2, 0), (13, 7, 0, 1), (6, 1, 1, 0)])
+@pytest.mark.parametrize("cfg", [(0, 0, 0, 0), (8, 3, 0, 1), (11, 5, 2, 0), (13, 7, 0, 1), (6, 1, 1, 0),
+                                 (12, 6, 0, 0, 1), (12, 6, 0, 1, 3), (13, 7, 0, 0, 3), (8, 3, 0, 0, 3)])
 def test_batch_matches_oracle(hq, cfg):
+    """cfg = (tile_bits, max_high, ctas_per_sm, small_first[, fuse_k])."""
     cs = small_batch()
     b = hq.Batch(cs, None, *cfg)
     for rep in range(2):  # the second replay rebuilds every state from |0..0>
@@ -54,19 +56,23 @@ def test_batch_argument_errors(hq):
         hq.Batch([wide])
     with pytest.raises(hq.HQError, match="ARG"):
         hq.Batch([C.config_small(0)], None, 14, 6, 0)
+    with pytest.raises(hq.HQError, match="ARG"):
+        hq.Batch([C.config_small(0)], None, 12, 6, 0, 0, 4)  # in-pass fusion wider than 3 qubits
 
 
 @pytest.mark.slow
 def test_serving_load_512_circuits(hq):
-    """512 circuits, n ~ U{10..24}, depth ~ U{8..32}: sampled circuits against
-    the oracle, every state's norm on the GPU."""
+    """512 circuits, n ~ U{10..24}, depth ~ U{8..32}: every circuit of up to
+    20 qubits and four of 22 or more against the oracle, every state's norm on
+    the GPU."""
     cs = C.config_batch(512, seed=0)
     b = hq.Batch(cs)
     b.run()
     lat, span = b.latencies()
     assert np.all(lat > 0)
-    small = [i for i, c in enumerate(cs) if c.n <= 16][:12]
-    big = [i for i, c in enumerate(cs) if c.n >= 22][:2]
+    small = [i for i, c in enumerate(cs) if c.n <= 20]
+    big = [i for i, c in enumerate(cs) if c.n >= 22][:4]
+    assert len(small) > 300
     for i in small + big:
         want = oracle.simulate(cs[i])
         got = b.states[i].cpu().numpy().astype(np.complex128)
@@ -79,13 +85,22 @@ def test_serving_load_512_circuits(hq):
 
 
 def test_autotuner_picks_a_candidate(hq, tmp_path):
+    """The tuner times every (tile shape, fusion width) candidate, returns the
+    fastest, caches it, and its choice runs the batch to the oracle's states."""
     from paper_2111_06868_gb300 import autotune
 
     cs = small_batch()[:12]
-    cands = [(12, 6, 0, 0), (11, 5, 0, 1)]
-    best = autotune.tune(cs, candidates=cands, reps=2, cache_path=str(tmp_path / "a.json"))
-    assert best[:4] in cands
-    again = autotune.tune(cs, candidates=cands, reps=2, cache_path=str(tmp_path / "a.json"))
-    assert again[:4] == best[:4]
-    p50 = autotune.tune(cs, candidates=cands, reps=2, cache_path=str(tmp_path / "a.json"), objective="p50")
-    assert p50[:4] in cands
+    cands = autotune.candidates(0, tiles=[(12, 6, 0), (11, 5, 0)], widths=[1, 2, 3])
+    best, timings = autotune.tune(cs, cands=cands, reps=2, cache_path=str(tmp_path / "a.json"))
+    assert best in cands and len(timings) == len(cands)
+    assert timings[str(best)] == min(timings.values())
+    again, _ = autotune.tune(cs, cands=cands, reps=2, cache_path=str(tmp_path / "a.json"))
+    assert again == best
+    p50, _ = autotune.tune(cs, cands=cands, reps=2, cache_path=str(tmp_path / "a.json"), objective="p50")
+    assert p50 in cands
+    b = hq.Batch(cs, None, *best)
+    b.run()
+    b.latencies()
+    for c, st in zip(cs, b.states):
+        assert rel_l2(st.cpu().numpy().astype(np.complex128), oracle.simulate(c)) <= 2e-5
+    b.close()

@@ -36,9 +36,10 @@ def rel_l2(got, want):
 
 
 def test_scheduler_wait_runs_out_then_recovers(hq):
-    # 16- and 18-qubit circuits on 12-bit tiles: every pass has at most 64
-    # tiles, far fewer than the CTAs of the launch, so most CTAs find nothing
-    # to run while the first passes are in flight
+    # 16- to 18-qubit circuits on 12-bit tiles with 6 high bits: a first pass
+    # that fills its high bits has 2^(n - 12) tiles, far fewer than the
+    # launch's CTAs (several per SM), so most CTAs find nothing to run while
+    # the first passes are in flight
     cs = [C.random_circuit(C.layout_for(n), 10, seed, "cz") for n, seed in ((16, 1), (18, 2), (17, 3))]
     want = [oracle.simulate(c) for c in cs]
     b = hq.Batch(cs, None, 12, 6, 0, 0)
