@@ -39,7 +39,8 @@ METRIC = "gate-apps/s"
 ARITH = {"tc_f16": "fp16 hi+lo split operands (3 products), fp32 accumulate in TMEM, fp64 norm",
          "tc_bf16": "bf16 hi+lo split operands (3 products), fp32 accumulate in TMEM, fp64 norm",
          "tc_pass": "fp16 hi+lo split operands (3 products), fp32 accumulate in TMEM, fp64 norm",
-         "cuda_core": "fp32 FMA on CUDA cores, fp64 norm", "auto": "fp32 FMA on CUDA cores, fp64 norm"}
+         "cuda_core": "fp32 FMA on CUDA cores, fp64 norm", "auto": "fp32 FMA on CUDA cores, fp64 norm",
+         "df": "double-float (hi + lo fp32 pairs, error-free products and sums) on CUDA cores, fp64 norm"}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
@@ -398,16 +399,24 @@ def measure_trajectories(args, T=8):
 
 def measure_batch():
     """Batched serving load: 512 circuits, n ~ U{10..24}, one persistent
-    launch replayed from a CUDA graph; largest-first queue (throughput) and
-    smallest-first queue (median latency)."""
+    launch replayed from a CUDA graph.  The autotuner picks the in-pass fusion
+    width and the tile shape: for makespan with the largest-first queue
+    (throughput), for median latency with the smallest-first queue; the
+    hand-picked (13, 7) tile with 2-qubit fusion is timed beside them."""
     import torch
+    from paper_2111_06868_gb300 import autotune
     from paper_2111_06868_gb300 import hq
 
     cs = C.config_batch(512, seed=0)
     Gb = sum(len(c.gates) for c in cs)
-    bres = {}
-    for name, small_first in (("largest_first", 0), ("smallest_first", 1)):
-        b = hq.Batch(cs, None, 13, 7, 0, small_first)
+    states = [torch.empty(1 << c.n, dtype=torch.complex64, device="cuda") for c in cs]
+    t0 = time.perf_counter()
+    pick_span, tim_span = autotune.tune(cs, states, objective="makespan", small_first=0, cache_path=None)
+    pick_p50, tim_p50 = autotune.tune(cs, states, objective="p50", small_first=1, cache_path=None)
+    tune_s = time.perf_counter() - t0
+
+    def run(cfg):
+        b = hq.Batch(cs, states, *cfg)
         b.run()
         e0, e1 = _events()
         e0.record()
@@ -416,12 +425,19 @@ def measure_batch():
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
         lat, span = b.latencies()
-        bres[name] = {"gate_apps_per_s": Gb / t, "s": t, "p50_ms": float(np.percentile(lat, 50)) / 1e3,
-                      "p99_ms": float(np.percentile(lat, 99)) / 1e3}
         b.close()
-        del b
-        torch.cuda.empty_cache()
-    return {"circuits": len(cs), "gates": Gb, "tile": [13, 7], "launches_per_run": 1, "graph": True, **bres}
+        return {"config": list(cfg), "gate_apps_per_s": Gb / t, "s": t,
+                "p50_ms": float(np.percentile(lat, 50)) / 1e3, "p99_ms": float(np.percentile(lat, 99)) / 1e3}
+
+    res = {"circuits": len(cs), "gates": Gb, "launches_per_run": 1, "graph": True,
+           "config_fields": ["tile_bits", "max_high", "ctas_per_sm", "small_first", "fuse_k"],
+           "largest_first": run(pick_span), "smallest_first": run(pick_p50),
+           "hand_picked_largest_first": run((13, 7, 0, 0, 2)), "hand_picked_smallest_first": run((13, 7, 0, 1, 2)),
+           "tuned": {"makespan": {"choice": list(pick_span), "candidates_s": tim_span},
+                     "p50": {"choice": list(pick_p50), "candidates_s": tim_p50}, "tuning_s": tune_s}}
+    del states
+    torch.cuda.empty_cache()
+    return res
 
 
 def measure_expectation(reps=5, n=30):
@@ -496,6 +512,16 @@ def measure_c128(args, circ):
     res["fused_k4"] = {"blocks": len(b4), "gate_apps_per_s": G / t4, "s": t4,
                        "GBps": len(b4) * 2 * (1 << 30) * 16 / t4 / 1e9}
     del st
+    # the same in double-float arithmetic on the FP32 pipes (HQ_ENGINE_DF)
+    st, t = _time_blocks(30, [(g.qubits, g.matrix) for g in circ.gates], "df", torch.complex128)
+    res["per_gate_df"] = {"launches": G, "gate_apps_per_s": G / t, "s": t, "GBps": G * 2 * (1 << 30) * 16 / t / 1e9}
+    del st
+    for kk in (2, 3, 4):
+        bk = fuse(hq, 30, circ.gates, kk, args)
+        st, tk = _time_blocks(30, bk, "df", torch.complex128)
+        res[f"fused_k{kk}_df"] = {"blocks": len(bk), "gate_apps_per_s": G / tk, "s": tk,
+                                  "GBps": len(bk) * 2 * (1 << 30) * 16 / tk / 1e9}
+        del st
     torch.cuda.empty_cache()
     return res
 
@@ -526,11 +552,14 @@ def measure_n28_vs_oracle(args):
     hq.hq_state_init(st)
     hq.hq_apply_blocks(st, c28.gates)
     c128 = float(np.abs(st.cpu().numpy() - want).max())
+    hq.hq_state_init(st)
+    hq.hq_apply_blocks(st, fuse(hq, 28, c28.gates, 4, args), engine="df")
+    c128_df = float(np.abs(st.cpu().numpy() - want).max())
     del st
     torch.cuda.empty_cache()
     return {"gates": len(c28.gates), "blocks_k6": len(b28), "rel_l2": errs, "bar_rel_l2": 2e-5,
-            "c128_per_gate_max_abs": c128, "bar_max_abs": 1e-12, "oracle_s": t_or,
-            "oracle_threads": oracle.max_threads()}
+            "c128_per_gate_max_abs": c128, "c128_df_fused_k4_max_abs": c128_df, "bar_max_abs": 1e-12,
+            "oracle_s": t_or, "oracle_threads": oracle.max_threads()}
 
 
 def measure_extras(args):
@@ -792,7 +821,7 @@ def main():
                     help="hq_fuse_dag (DAG frontier, restarts) or hq_fuse (greedy rule)")
     ap.add_argument("--fuse-restarts", type=int, default=64)
     ap.add_argument("--dtype", default="complex64", choices=["complex64", "complex128"])
-    ap.add_argument("--engine", default="tc_f16", choices=["auto", "cuda_core", "tc_f16", "tc_bf16", "tc_pass"])
+    ap.add_argument("--engine", default="tc_f16", choices=["auto", "cuda_core", "tc_f16", "tc_bf16", "tc_pass", "df"])
     ap.add_argument("--tc-min-k", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' sub-measurements")
     ap.add_argument("--seed", type=int, default=0)
@@ -953,7 +982,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if S == 8 else "f64", "data": "synthetic",
             "config": {"workload": desc, "n": n, "gates": G, "fused_blocks": B, "k_max": args.kmax,
-                       "arith": ARITH.get(engine, engine) if S == 8 else "fp64",
+                       "arith": ARITH.get(engine, engine) if (S == 8 or engine == "df") else "fp64",
                        "note": "the n=30 circuit of the per-gate / fused k<=4 configuration, run on the "
                                "fused k<=6 tensor-core engine of the 33-qubit configuration"
                                if n == 30 and engine.startswith("tc") else None,

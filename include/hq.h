@@ -95,6 +95,9 @@ typedef struct {
 #define HQ_ENGINE_TC_BF16 3   /* same, BF16 hi+lo split (complex64) */
 #define HQ_ENGINE_TC_PASS 4   /* blocks (k <= 6) grouped two at a time into 13-qubit tile passes on tcgen05
                                  tensor cores, FP16 hi+lo split (complex64, n >= 14; smaller n: as TC_F16) */
+#define HQ_ENGINE_DF 5        /* complex128 only: diagonal gates and monomial / dense gates of k <= 4 in
+                                 double-float arithmetic (48-bit hi + lo float pairs) on the FP32 pipes;
+                                 controlled gates and k = 5, 6 blocks as HQ_ENGINE_CUDA_CORE */
 typedef struct {
     int engine;  /* HQ_ENGINE_* */
     int tc_min_k; /* blocks with k >= tc_min_k use the tensor-core engine (default 5) */
@@ -382,7 +385,8 @@ hq_status hq_apply_gate(void *state, int n, hq_dtype dt, const int *qubits, int 
 /*
  * hq_apply_blocks -- apply G gates / fused blocks in order (the evolution
  * loop of Sec. 4.2), choosing a kernel per block as configured (cfg NULL =
- * HQ_ENGINE_AUTO).  Tensor-core engines apply only to complex64 states.
+ * HQ_ENGINE_AUTO).  Tensor-core engines apply only to complex64 states,
+ * HQ_ENGINE_DF only to complex128 states (HQ_ERR_DTYPE otherwise).
  * HQ_ENGINE_TC_PASS applies the same operators in the same order (blocks
  * with disjoint targets may swap), up to two per read and write of the state:
  * see hq_plan_passes.  It moves qubits between bit positions while it runs and

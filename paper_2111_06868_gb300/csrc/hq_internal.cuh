@@ -196,6 +196,12 @@ constexpr int kMaxCtrlTargets = 2;
 bool use_control_path(int n, int k, const int *qubits, const double *matrix, int elem_bytes, int *ctrl_mask,
                       double *u);
 
+// complex128 gates in double-float arithmetic (k_apply_df.cu): diagonal
+// gates of any k, monomial and dense gates of k <= 4
+bool df_supported(int k, const double *matrix);
+hq_status launch_gate_df(void *state, int n, int k, const int *qubits, const double *matrix, int64_t nstates,
+                         cudaStream_t s);
+
 // noisy paths (k_noise.cu)
 // reduced density matrix of k <= 2 qubits (row-major 2^k x 2^k complex, host), synchronous
 hq_status launch_rdm(const void *state, int n, hq_dtype dt, const int *qubits, int k, double *out_host,

@@ -799,6 +799,9 @@ static hq_status dispatch(void *state, int n, int k, const int *qubits, const do
         default: return run_ctrl<R, 2>(state, n, k, qubits, cm, u, nstates, s);
         }
     }
+    // complex128 in double-float arithmetic on the FP32 pipes (k_apply_df.cu)
+    if constexpr (sizeof(R) == 8)
+        if (engine == HQ_ENGINE_DF && df_supported(k, mat)) return launch_gate_df(state, n, k, qubits, mat, nstates, s);
     if (is_diagonal(k, mat)) {
         switch (k) {
         case 1: return run_diag<R, 1>(state, n, qubits, mat, nstates, s);
