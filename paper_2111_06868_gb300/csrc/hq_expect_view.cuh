@@ -12,10 +12,11 @@ namespace hq {
 constexpr int kEvMaxViews = 8;
 constexpr int kEvMaxTerms = 96;
 constexpr int kEvMaxGroups = 96;
+constexpr int kEvThrBits = 9;  // 512 threads: 5 lane bits, 4 warp bits
 
 struct EvView {
     int reg[5];   // tile-local positions of the register bits (NR of them), ascending
-    int thr[8];   // tile-local positions of the thread bits; thr[0..4] are the lane bits
+    int thr[kEvThrBits];  // tile-local positions of the thread bits; thr[0..4] are the lane bits
     int pj[32];   // swizzled shared-memory offset of register slot j
     int g0, g1;   // its groups [g0, g1): diagonal groups first
 };
@@ -32,6 +33,7 @@ struct EvGroup {
     int h;   // register Z mask of a diagonal group
     int t0, nt;
     int view;
+    int need_re, need_im;  // some term takes Re / Im of the pair products
 };
 struct EvParams {
     TileGeom g;
@@ -47,10 +49,11 @@ struct EvInTerm {
     double wr, wi;    // coeff * (-i)^#Y
 };
 
-// Views, terms and groups of one pass for tiles of L bits, NR register bits
-// and 2^slot_bits bank slots; false when a term does not fit (an X mask wider
-// than NR bits, more than kEvMaxViews views, or too many terms / groups).
-bool plan_expect_views(int L, int NR, int slot_bits, const std::vector<EvInTerm> &in, EvParams &p);
+// Views, terms and groups of one pass for tiles of L bits, NR register bits,
+// 2^slot_bits bank slots and the shared-memory swizzle i ^ ((i >> 3) & swz);
+// false when a term does not fit (an X mask wider than NR bits, more than
+// kEvMaxViews views, or too many terms / groups).
+bool plan_expect_views(int L, int NR, int slot_bits, int swz, const std::vector<EvInTerm> &in, EvParams &p);
 // Launches one pass (grid CTAs, one per SM at most); partials[blockIdx.x].
 hq_status launch_expect_view(const void *state, hq_dtype dt, const EvParams &p, int grid, double *partials,
                              cudaStream_t s);

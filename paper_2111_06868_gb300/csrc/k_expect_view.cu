@@ -5,7 +5,7 @@
 //   <psi|P|psi> = sum_x conj(psi_x) w (-1)^popc(x & z) psi_{x ^ m}.
 // A tile of 2^L amplitudes (every X mask of the pass inside its bits) sits in
 // shared memory.  A view splits the L tile bits into NR register bits and
-// 8 thread bits: each of the 256 threads holds the E = 2^NR amplitudes that
+// 9 thread bits: each of the 512 threads holds the E = 2^NR amplitudes that
 // differ only in the register bits.  A term whose X mask lies in the register
 // bits of a view pairs registers (j, j ^ m); grouping the pair (x, x ^ m)
 // gives 2 s(j) Re(w q_j) with q_j = conj(a_j) a_{j^m}, s(j) the Z sign of
@@ -17,10 +17,13 @@
 // the Walsh-Hadamard transform of |a|^2 over the register bits: one
 // transform per tile and thread gives every register Z mask h at once.
 //
-// Shared memory: element i of a tile at i ^ ((i >> NR) & SLOTS-1), a linear
-// XOR swizzle under which the host picks, per view, the 5 lane bits so that
-// the 32 lanes of a warp hit every bank slot equally often.  Tiles come in by
-// cp.async, three stages, so two tiles are in flight while one is evaluated.
+// Shared memory: element i of a tile at i ^ ((i >> 3) & SWZ), a linear XOR
+// swizzle of the bank-slot bits (complex64: bits 1..3 from bits 4..6, which
+// keeps the pairs (2e, 2e + 1) of one 16-byte copy together; complex128:
+// bits 0..2 from bits 3..5); the host picks, per view, the 5 lane bits so
+// that the 32 lanes of a warp hit the bank slots as evenly as the swizzle
+// allows.  Tiles come in by 16-byte cp.async copies, three stages, so two
+// tiles are in flight while one is evaluated.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -30,21 +33,21 @@
 
 namespace hq {
 
-constexpr int kEvThreads = 256;
+constexpr int kEvThreads = 512;
 constexpr int kEvStages = 3;
 
 template <typename R> struct EvShape;
 template <> struct EvShape<float> {
-    static constexpr int NR = 5, SLOT_BITS = 4;  // 8-byte elements: 16 per 128-byte wavefront
+    static constexpr int NR = 4, SLOT_BITS = 4, SWZ = 0xE;  // 8-byte elements: 16 per 128-byte wavefront
 };
 template <> struct EvShape<double> {
-    static constexpr int NR = 4, SLOT_BITS = 3;  // 16-byte elements: 8 per wavefront
+    static constexpr int NR = 3, SLOT_BITS = 3, SWZ = 0x7;  // 16-byte elements: 8 per wavefront
 };
 
 template <typename R>
 __device__ __forceinline__ int ev_phys(int i)
 {
-    return i ^ ((i >> EvShape<R>::NR) & ((1 << EvShape<R>::SLOT_BITS) - 1));
+    return i ^ ((i >> 3) & EvShape<R>::SWZ);
 }
 
 // sum of v[0..N) as a balanced tree (independent adds, no long chain)
@@ -81,15 +84,24 @@ __device__ __forceinline__ R ev_xgroup(const typename C2<R>::type *a, const EvGr
     constexpr int TOP = 31 - __builtin_clz(M);
     constexpr int NP = E / 2;
     R vr[NP], vi[NP];
+    // Re(conj(x) y) and Im(conj(x) y) of every pair, each only when a term
+    // of the group needs it (branches uniform over the CTA)
+    if (gr.need_re) {
 #pragma unroll
-    for (int u = 0; u < NP; ++u) {
-        const int j = ((u >> TOP) << (TOP + 1)) | (u & ((1 << TOP) - 1));  // u-th slot with bit TOP clear
-        const auto x = a[j], y = a[j ^ M];
-        vr[u] = x.x * y.x + x.y * y.y;  // Re(conj(x) y)
-        vi[u] = x.x * y.y - x.y * y.x;  // Im(conj(x) y)
+        for (int u = 0; u < NP; ++u) {
+            const int j = ((u >> TOP) << (TOP + 1)) | (u & ((1 << TOP) - 1));  // u-th slot with bit TOP clear
+            vr[u] = a[j].x * a[j ^ M].x + a[j].y * a[j ^ M].y;
+        }
+    }
+    if (gr.need_im) {
+#pragma unroll
+        for (int u = 0; u < NP; ++u) {
+            const int j = ((u >> TOP) << (TOP + 1)) | (u & ((1 << TOP) - 1));
+            vi[u] = a[j].x * a[j ^ M].y - a[j].y * a[j ^ M].x;
+        }
     }
     // plain sums (terms with no Z on the register bits: the common case)
-    const R sr = tree_sum<NP, R>(vr), si = tree_sum<NP, R>(vi);
+    const R sr = gr.need_re ? tree_sum<NP, R>(vr) : R(0), si = gr.need_im ? tree_sum<NP, R>(vi) : R(0);
     R part = 0;
     for (int t = gr.t0; t < gr.t0 + gr.nt; ++t) {
         const EvTerm &tm = terms[t];
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(kEvThreads, 1) k_expect_view(const EvParams p,
         if (tid < E) s_pj[v][tid] = p.view[v].pj[tid];
         int tl = 0;
 #pragma unroll
-        for (int b = 0; b < 8; ++b)
+        for (int b = 0; b < kEvThrBits; ++b)
             if ((tid >> b) & 1) tl |= 1 << p.view[v].thr[b];
         s_pt[v][tid] = ev_phys<R>(tl);
     }
@@ -217,7 +229,7 @@ __global__ void __launch_bounds__(kEvThreads, 1) k_expect_view(const EvParams p,
         const int v = p.term[t].view;
         int tl = 0;
 #pragma unroll
-        for (int b = 0; b < 8; ++b)
+        for (int b = 0; b < kEvThrBits; ++b)
             if ((tid >> b) & 1) tl |= 1 << p.view[v].thr[b];
         const uint32_t bit = (__popc(tl & p.term[t].zthr) & 1u) << (t & 31);
         if (t < 32) ts0 |= bit;
@@ -232,14 +244,13 @@ __global__ void __launch_bounds__(kEvThreads, 1) k_expect_view(const EvParams p,
             const int64_t tl = blockIdx.x + it * gridDim.x;
             const V *src = psi + tile_base(g, tl);
             V *dst = stage_base + size_t(it % kEvStages) * TS;
-#pragma unroll 8
-            for (int k = 0; k < E; ++k) {
-                const int i = tid + k * kEvThreads;
-                const V *s = src + s_runoff[i >> g.c] + (i & cmask);
-                if constexpr (sizeof(R) == 4)
-                    cp_async8(&dst[ev_phys<R>(i)], s);
-                else
-                    cp_async16(&dst[ev_phys<R>(i)], s);
+            // 16-byte copies: complex64 pairs (2e, 2e + 1), which the swizzle
+            // keeps together (runs have >= 64 amplitudes), complex128 singles
+            constexpr int PER = sizeof(R) == 4 ? 2 : 1;
+#pragma unroll
+            for (int k = 0; k < E / PER; ++k) {
+                const int i = PER * (tid + k * kEvThreads);
+                cp_async16(&dst[ev_phys<R>(i)], src + s_runoff[i >> g.c] + (i & cmask));
             }
         }
         cp_async_commit();
@@ -347,10 +358,10 @@ int gf2_rank(std::vector<uint32_t> v)
 
 }  // namespace
 
-bool plan_expect_views(int L, int NR, int slot_bits, const std::vector<EvInTerm> &in, EvParams &p)
+bool plan_expect_views(int L, int NR, int slot_bits, int swz, const std::vector<EvInTerm> &in, EvParams &p)
 {
     const int nthr = L - NR;
-    if (nthr != 8 || int(in.size()) > kEvMaxTerms) return false;
+    if (nthr != kEvThrBits || int(in.size()) > kEvMaxTerms) return false;
     // register-bit sets: every off-diagonal term's X mask inside one of them
     std::vector<uint32_t> sets;
     std::vector<int> view_of(in.size(), 0);
@@ -392,11 +403,9 @@ bool plan_expect_views(int L, int NR, int slot_bits, const std::vector<EvInTerm>
             if (!((S >> pos) & 1)) thr.push_back(pos);
         // lanes: the 5 thread positions whose images on the bank-slot bits
         // under the swizzle have the largest rank
-        auto img = [&](int pos) {
-            uint32_t m = 0;
-            if (pos < slot_bits) m ^= 1u << pos;
-            if (pos >= NR && pos < NR + slot_bits) m ^= 1u << (pos - NR);
-            return m;
+        auto img = [&](int pos) {  // bank-slot bits of the swizzled position of bit pos
+            const uint32_t b = 1u << pos;
+            return (b ^ ((b >> 3) & uint32_t(swz))) & ((1u << slot_bits) - 1);
         };
         int best = -1, best_mask = 0;
         for (int msk = 0; msk < (1 << nthr); ++msk) {
@@ -419,7 +428,7 @@ bool plan_expect_views(int L, int NR, int slot_bits, const std::vector<EvInTerm>
             int off = 0;
             for (int b = 0; b < NR; ++b)
                 if ((j >> b) & 1) off |= 1 << vw.reg[b];
-            vw.pj[j] = off ^ ((off >> NR) & ((1 << slot_bits) - 1));
+            vw.pj[j] = off ^ ((off >> 3) & swz);
         }
     }
     // terms, grouped by (view, X mask in register bits, register Z mask for diagonals)
@@ -457,7 +466,7 @@ bool plan_expect_views(int L, int NR, int slot_bits, const std::vector<EvInTerm>
         std::memset(&tm, 0, sizeof(tm));
         tm.view = k.view;
         uint32_t zthr = 0;
-        for (int b = 0; b < 8; ++b)
+        for (int b = 0; b < kEvThrBits; ++b)
             if ((it.zl >> vw.thr[b]) & 1) zthr |= 1u << vw.thr[b];
         tm.zthr = int(zthr);
         tm.zh = it.zh;
@@ -484,8 +493,14 @@ bool plan_expect_views(int L, int NR, int slot_bits, const std::vector<EvInTerm>
             gr.t0 = int(i);
             gr.nt = 0;
             gr.view = k.view;
+            gr.need_re = gr.need_im = 0;
         }
-        ++p.grp[p.ng - 1].nt;
+        EvGroup &cur = p.grp[p.ng - 1];
+        ++cur.nt;
+        if (k.m) {
+            if (tm.imag) cur.need_im = 1;
+            else cur.need_re = 1;
+        }
     }
     for (int gi = p.ng - 1; gi >= 0; --gi) {  // groups are sorted by view
         EvView &vw = p.view[p.grp[gi].view];

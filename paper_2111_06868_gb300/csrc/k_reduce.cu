@@ -445,7 +445,8 @@ static void plan_tile_passes(int n, int L, int low, const std::vector<Tm> &tms, 
 static bool try_view_pass(const void *state, int n, hq_dtype dt, const TilePass &tp, int grid, double *part,
                           cudaStream_t s, hq_status &st)
 {
-    const int L = dt == HQ_C64 ? 13 : 12, NR = dt == HQ_C64 ? 5 : 4, SB = dt == HQ_C64 ? 4 : 3;
+    const int L = dt == HQ_C64 ? 13 : 12, NR = dt == HQ_C64 ? 4 : 3, SB = dt == HQ_C64 ? 4 : 3;
+    const int SWZ = dt == HQ_C64 ? 0xE : 0x7;  // the kernel's shared-memory swizzle
     static thread_local EvParams ep;  // large: kept off the stack
     std::memset(&ep, 0, sizeof(ep));
     const int k = int(tp.high.size());
@@ -473,7 +474,7 @@ static bool try_view_pass(const void *state, int n, hq_dtype dt, const TilePass 
         t.wi = m.wi;
         in.push_back(t);
     }
-    if (!plan_expect_views(L, NR, SB, in, ep)) return false;
+    if (!plan_expect_views(L, NR, SB, SWZ, in, ep)) return false;
     const int gx = int(std::min<int64_t>(std::min(grid, sm_count()), ep.g.total_tiles));
     st = launch_expect_view(state, dt, ep, gx, part, s);
     if (st == HQ_OK && gx < grid)

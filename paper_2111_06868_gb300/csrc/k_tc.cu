@@ -743,16 +743,16 @@ static void widen_to_6(int n, const hq_gate &gt, hq_gate &w, std::vector<double>
 
 // Launches the gates in order: tensor-core blocks take their split matrix
 // from one device buffer allocated up front.  The blocks are prepared on the
-// host in two chunks (the first two blocks, then the rest, prepared while the
-// first two run); each chunk's matrices go up in one copy from pinned staging
-// memory on the library's upload stream, ordered only after the buffer's
-// allocation, so an upload never waits behind this call's kernels (or behind
-// a large copy the caller queued after them).  The other gates go through
-// launch_gate.
+// host in chunks (two blocks, then four at a time, each prepared while the
+// previous chunk's kernels run); each chunk's matrices go up in one copy from
+// pinned staging memory on the library's upload stream, ordered only after
+// the buffer's allocation, so an upload never waits behind this call's
+// kernels (or behind a large copy the caller queued after them).  The other
+// gates go through launch_gate.
 static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G, int tc_min_k, int split_bf16,
                                 int64_t nstates, cudaStream_t s)
 {
-    constexpr int kFirstChunk = 2;
+    constexpr int kFirstChunk = 2, kChunk = 4;
     size_t bytes = 0;
     for (int g = 0; g < G; ++g)
         if (tc_eligible(n, gates[g], tc_min_k)) bytes += tc_matrix_bytes(n >= 13 ? 6 : gates[g].k);
@@ -767,7 +767,7 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
     std::vector<TcPrepared> prep;
     std::vector<uint16_t> host;
     for (int g0 = 0; g0 < G && st == HQ_OK;) {
-        const int g1 = g0 == 0 ? std::min(G, kFirstChunk) : G;
+        const int g1 = std::min(G, g0 + (g0 == 0 ? kFirstChunk : kChunk));
         prep.assign(size_t(g1 - g0), TcPrepared());
         host.clear();
         for (int g = g0; g < g1; ++g) {
