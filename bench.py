@@ -703,14 +703,16 @@ def _cpulist(text):
 
 
 def measure_e2e(args, hq, circ, blocks, state, stream, engine, dist):
-    """End to end through the public API: every step copies the state in from
-    pinned host memory, applies the fused blocks and reads the FP64 norm
-    back.  Two state buffers: the next step's input is copied on its own
-    stream while the current step computes.  The pinned buffer is allocated
+    """End to end through the public API: every step uploads the state from
+    pinned host memory (hq_state_upload: the SMs read the host buffer over
+    the CPU-GPU link), applies the fused blocks and reads the FP64 norm back,
+    in stream order.  Also measured: the H2D copy alone by the copy engine
+    and by hq_state_upload (GB/s); the copy-engine variant that overlaps the
+    next step's copy with the current step on a second stream; and a variant
+    that runs the fusion (hq_fuse_dag) of the next step's circuit on the host
+    while the current step's kernels run.  The pinned buffer is allocated
     (and first touched) by a thread bound to the GPU's local CPUs where the
-    system reports them.  Also measured: the H2D copy alone (GB/s), and a
-    variant that runs the fusion (hq_fuse_dag) of the next step's circuit on
-    the host while the current step's kernels run."""
+    system reports them."""
     import torch
 
     n, G = circ.n, len(circ.gates)
@@ -732,21 +734,33 @@ def measure_e2e(args, hq, circ, blocks, state, stream, engine, dist):
     bufs = [state, torch.empty_like(state)]
     copy_stream = torch.cuda.Stream()
 
-    # the H2D copy alone
-    torch.cuda.synchronize()
-    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    h2d = []
-    for _ in range(3):
-        c0.record(stream)
-        bufs[1].copy_(host_in, non_blocking=True)
-        c1.record(stream)
-        torch.cuda.synchronize()
-        h2d.append(c0.elapsed_time(c1) / 1e3)
-    h2d_gbps = (1 << n) * S / min(h2d) / 1e9
+    def timed_copy(fn, reps=3):
+        best = 1e30
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            fn()
+            c1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, c0.elapsed_time(c1) / 1e3)
+        return best
 
-    def run(steps, start=None, refuse=False):
-        copied = [None, None]
+    t_ce = timed_copy(lambda: bufs[1].copy_(host_in, non_blocking=True))
+    t_sm = timed_copy(lambda: hq.hq_state_upload(bufs[1], host_in, stream=stream))
+    nbytes = (1 << n) * S
+
+    def serial(steps, refuse=False):
         cur_blocks = blocks
+        for s in range(steps):
+            hq.hq_state_upload(state, host_in, stream=stream)
+            hq.hq_apply_blocks(state, cur_blocks, engine=engine, tc_min_k=args.tc_min_k, stream=stream)
+            if refuse and s + 1 < steps:  # next step's fusion on the host, under this step's kernels
+                cur_blocks = fuse(hq, n, circ.gates, args.kmax, args)
+            out[0] = hq.hq_expectation(state, [(1.0, ())], stream=stream)
+
+    def overlapped(steps, start=None):
+        copied = [None, None]
         with torch.cuda.stream(copy_stream):
             if start is not None:
                 copy_stream.wait_event(start)
@@ -756,42 +770,47 @@ def measure_e2e(args, hq, circ, blocks, state, stream, engine, dist):
         for s in range(steps):
             cur = bufs[s % 2]
             stream.wait_event(copied[s % 2])
-            hq.hq_apply_blocks(cur, cur_blocks, engine=engine, tc_min_k=args.tc_min_k, stream=stream)
+            hq.hq_apply_blocks(cur, blocks, engine=engine, tc_min_k=args.tc_min_k, stream=stream)
             if s + 1 < steps:
                 nxt = (s + 1) % 2
-                # the buffer's previous step ended with a synchronous norm
                 with torch.cuda.stream(copy_stream):
                     bufs[nxt].copy_(host_in, non_blocking=True)
                     copied[nxt] = torch.cuda.Event()
                     copied[nxt].record(copy_stream)
-                if refuse:  # next step's fusion on the host, under this step's kernels
-                    cur_blocks = fuse(hq, n, circ.gates, args.kmax, args)
             out[0] = hq.hq_expectation(cur, [(1.0, ())], stream=stream)
 
-    def timed(steps, refuse=False):
-        run(2, refuse=refuse)
+    def timed(fn, steps, **kw):
+        fn(2, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
         e0.record(stream)
-        run(steps, start=e0, refuse=refuse)
+        if fn is overlapped:
+            fn(steps, start=e0)
+        else:
+            fn(steps, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / 1e3
 
     e2e_steps = max(2, min(args.steps, 5))
-    et = timed(e2e_steps)
+    et = timed(serial, e2e_steps)
     e2e_value, et = whole_job_rate(et, G * e2e_steps, dist, "cuda")
-    t_f = timed(e2e_steps, refuse=True)
+    t_f = timed(serial, e2e_steps, refuse=True)
+    t_o = timed(overlapped, e2e_steps)
     del bufs
-    return {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": (1 << n) * S, "d2h_bytes_per_step": 8,
-            "ms_per_step": 1e3 * et / e2e_steps, "h2d_alone_GBps": h2d_gbps,
-            "h2d_alone_ms": 1e3 * min(h2d), "numa": numa,
+    return {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 8,
+            "ms_per_step": 1e3 * et / e2e_steps,
+            "h2d": {"sm_read_GBps": nbytes / t_sm / 1e9, "sm_read_ms": 1e3 * t_sm,
+                    "copy_engine_GBps": nbytes / t_ce / 1e9, "copy_engine_ms": 1e3 * t_ce},
+            "numa": numa,
             "with_fusion_each_step": {"value": G * e2e_steps / t_f, "ms_per_step": 1e3 * t_f / e2e_steps,
                                       "note": "hq_fuse_dag of the next step on the host under the current "
                                               "step's kernels"},
-            "note": "pinned host state copied in and FP64 norm read back every step; the next step's copy "
-                    "overlaps the current step on a second stream (two state buffers)"}
+            "copy_engine_overlapped": {"value": G * e2e_steps / t_o, "ms_per_step": 1e3 * t_o / e2e_steps,
+                                       "note": "torch copy_ from pinned memory on a second stream, the next "
+                                               "step's copy overlapping the current step (two buffers)"},
+            "note": "every step: hq_state_upload of the pinned host state (SM reads), hq_apply_blocks, FP64 "
+                    "norm read back; in stream order on one stream"}
 
 
 def whole_job_rate(local_seconds: float, local_units: float, dist=None, device=None):

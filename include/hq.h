@@ -121,6 +121,20 @@ const char *hq_version(void);
 hq_status hq_state_init(void *state, int n, hq_dtype dt, const char *tokens, void *stream);
 
 /*
+ * hq_state_upload -- copy a state of 2^n amplitudes of type dt from HOST
+ * memory `host` (16-byte aligned) into the device state `state` on `stream`,
+ * for callers that keep states in host memory (the Sec. 4.2 evolution then
+ * runs on the device copy).  Pinned host memory (cudaHostAlloc,
+ * cudaHostRegister) is read by the GPU's SMs directly over the CPU-GPU link;
+ * other host memory goes through cudaMemcpyAsync.  Asynchronous: the host
+ * buffer must stay valid and unchanged until the stream has passed this
+ * point.  Not in the paper.
+ * Errors: HQ_ERR_NULL, HQ_ERR_N_TOO_LARGE, HQ_ERR_DTYPE, HQ_ERR_ALIGN (either
+ * pointer), HQ_ERR_CUDA.
+ */
+hq_status hq_state_upload(void *state, const void *host, int n, hq_dtype dt, void *stream);
+
+/*
  * hq_fuse -- Sec. 3.1 compress(circuit, max_n_qubits): greedily merge the G
  * gates (host) into blocks of at most k_max qubits (1 <= k_max <= HQ_MAX_K).
  * A gate joins the latest earlier block that shares a qubit with it when the

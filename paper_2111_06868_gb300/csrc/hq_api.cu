@@ -227,6 +227,16 @@ hq_status hq_state_init(void *state, int n, hq_dtype dt, const char *tokens, voi
     return launch_init(state, n, dt, tokens, 1, (cudaStream_t)stream);
 }
 
+hq_status hq_state_upload(void *state, const void *host, int n, hq_dtype dt, void *stream)
+{
+    hq_status st = check_state(state, n, dt);
+    if (st != HQ_OK) return st;
+    if (!host) return HQ_ERR_NULL;
+    if (reinterpret_cast<uintptr_t>(host) & 15) return HQ_ERR_ALIGN;
+    const size_t bytes = (size_t(1) << n) * (dt == HQ_C64 ? 8 : 16);
+    return launch_upload(state, host, bytes, (cudaStream_t)stream);
+}
+
 int hq_gate_structure(int k, const double *matrix, int *control_mask, double *u)
 {
     if (!matrix) return HQ_ERR_NULL;

@@ -58,4 +58,34 @@ bool plan_expect_views(int L, int NR, int slot_bits, int swz, const std::vector<
 hq_status launch_expect_view(const void *state, hq_dtype dt, const EvParams &p, int grid, double *partials,
                              cudaStream_t s);
 
+// ----------------------------------------------------------------------------
+// register passes (k_expect_reg.cu): terms whose X mask is one flat bit >= 5
+// ----------------------------------------------------------------------------
+constexpr int kErMaxBits = 6;
+constexpr int kErMaxTerms = 96;
+struct ErTerm {
+    double w;         // 2 Re w, or -2 Im w when imag
+    uint64_t zrest;   // Z bits outside the lanes (0..4) and the pass's bits (flat)
+    uint32_t zlane;   // Z bits among flat bits 0..4
+    int bit;          // index of its X bit among the pass's bits
+    int imag;         // #Y odd: Im(conj(a_j) a_{j^m})
+};
+struct ErParams {
+    int n, H, nt;
+    int hb[kErMaxBits];  // the pass's flat bits, ascending, all >= 5
+    int need_re[kErMaxBits], need_im[kErMaxBits];
+    ErTerm term[kErMaxTerms];
+};
+struct EvInRegTerm {
+    uint64_t xm, zm;  // flat masks (xm: one bit of the pass)
+    double wr, wi;    // coeff * (-i)^#Y
+};
+// register bits of a pass: 6 (complex64), 5 (complex128)
+int expect_reg_max_bits(hq_dtype dt);
+// false if a term's X mask is not one of the pass's bits, a term has Z on
+// another of the pass's bits, or sizes exceed the limits
+bool plan_expect_reg(int n, int H, const int *high_bits, const std::vector<EvInRegTerm> &in, ErParams &p);
+hq_status launch_expect_reg(const void *state, hq_dtype dt, const ErParams &p, int grid, double *partials,
+                            cudaStream_t s);
+
 }  // namespace hq

@@ -175,6 +175,10 @@ __device__ __forceinline__ void tile_store(const TileGeom &g, double2 *__restric
     for (int i = threadIdx.x; i < TS; i += blockDim.x) base[g.runoff[i >> g.c] + (i & cmask)] = tile[swz<double>(i)];
 }
 
+// host -> device copy of `bytes` (a multiple of 16) into `state` (k_copy.cu):
+// read by the SMs when `host` is pinned, else by cudaMemcpyAsync
+hq_status launch_upload(void *state, const void *host, size_t bytes, cudaStream_t s);
+
 // kernels launched by the API layer (k_apply.cu)
 hq_status launch_init(void *state, int n, hq_dtype dt, const char *tokens, int64_t nstates, cudaStream_t s);
 hq_status launch_gate(void *state, int n, hq_dtype dt, int k, const int *qubits, const double *matrix,

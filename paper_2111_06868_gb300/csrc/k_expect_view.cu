@@ -22,8 +22,10 @@
 // keeps the pairs (2e, 2e + 1) of one 16-byte copy together; complex128:
 // bits 0..2 from bits 3..5); the host picks, per view, the 5 lane bits so
 // that the 32 lanes of a warp hit the bank slots as evenly as the swizzle
-// allows.  Tiles come in by 16-byte cp.async copies, three stages, so two
-// tiles are in flight while one is evaluated.
+// allows.  Tiles come in by 16-byte cp.async copies, two stages, so the
+// next tile is in flight while one is evaluated.  A diagonal term reads its
+// Walsh coefficient W[h] from a per-thread column in shared memory (h is a
+// runtime index; registers can only be picked by a chain of selects).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -34,7 +36,7 @@
 namespace hq {
 
 constexpr int kEvThreads = 512;
-constexpr int kEvStages = 3;
+constexpr int kEvStages = 2;
 
 template <typename R> struct EvShape;
 template <> struct EvShape<float> {
@@ -182,16 +184,16 @@ __device__ __forceinline__ R ev_xgroup_smem(const typename C2<R>::type *a, const
     return part;
 }
 
-// diagonal group: register Z mask H (compile time) -> W[H]
-template <typename R, int H>
-__device__ __forceinline__ R ev_pick(int h, const R *W)
+template <typename R>
+__host__ __device__ constexpr size_t ev_stage_bytes(int L)
 {
-    if constexpr (H >= (1 << EvShape<R>::NR)) {
-        return R(0);
-    } else {
-        if (h == H) return W[H];
-        return ev_pick<R, H + 1>(h, W);
-    }
+    return size_t(kEvStages) * sizeof(typename C2<R>::type) << L;
+}
+template <typename R>
+__host__ __device__ constexpr size_t ev_dyn_smem(int L)
+{
+    return ev_stage_bytes<R>(L) + sizeof(R) * (size_t(1) << EvShape<R>::NR) * kEvThreads +
+           sizeof(int) * kEvMaxViews * kEvThreads;
 }
 
 template <typename R>
@@ -201,10 +203,14 @@ __global__ void __launch_bounds__(kEvThreads, 1) k_expect_view(const EvParams p,
 {
     using V = typename C2<R>::type;
     constexpr int NR = EvShape<R>::NR, E = 1 << NR;
+    // dynamic shared memory: the tile stages, then per-thread tables
+    // (Walsh coefficients [E][threads], view offsets [views][threads])
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V *stage_base = reinterpret_cast<V *>(smem_raw);
+    R(*s_wht)[kEvThreads] = reinterpret_cast<R(*)[kEvThreads]>(smem_raw + ev_stage_bytes<R>(p.g.L));
+    int(*s_pt)[kEvThreads] =
+        reinterpret_cast<int(*)[kEvThreads]>(smem_raw + ev_stage_bytes<R>(p.g.L) + sizeof(R) * E * kEvThreads);
     __shared__ int s_pj[kEvMaxViews][32];
-    __shared__ int s_pt[kEvMaxViews][kEvThreads];
     __shared__ R s_sw[2][kEvMaxTerms];
     __shared__ int64_t s_runoff[64];
     __shared__ EvTerm s_term[kEvMaxTerms];
@@ -264,14 +270,13 @@ __global__ void __launch_bounds__(kEvThreads, 1) k_expect_view(const EvParams p,
     };
     __syncthreads();
     tile_signs(0, 0);
-    issue(0);
-    issue(1);
+    for (int st = 0; st < kEvStages - 1; ++st) issue(st);
 
     double acc = 0;
     R accr = 0, comp = 0;
     for (int64_t it = 0; it < mine; ++it) {
-        issue(it + 2);
-        cp_async_wait<2>();
+        issue(it + kEvStages - 1);
+        cp_async_wait<kEvStages - 1>();
         __syncthreads();
         tile_signs(it + 1, int((it + 1) & 1));
         const V *T = stage_base + size_t(it % kEvStages) * TS;
@@ -298,9 +303,11 @@ __global__ void __launch_bounds__(kEvThreads, 1) k_expect_view(const EvParams p,
                             W[j] = u + w;
                             W[j | s] = u - w;
                         }
+#pragma unroll
+                for (int j = 0; j < E; ++j) s_wht[j][tid] = W[j];  // read back by index: no select chain
                 for (; gi < g1 && p.grp[gi].m == 0; ++gi) {
                     const EvGroup &gr = p.grp[gi];
-                    const R Wh = ev_pick<R, 0>(gr.h, W);
+                    const R Wh = s_wht[gr.h][tid];
                     R c = 0;
                     for (int t = gr.t0; t < gr.t0 + gr.nt; ++t) {
                         const uint32_t word = t < 32 ? ts0 : (t < 64 ? ts1 : ts2);
@@ -513,8 +520,7 @@ bool plan_expect_views(int L, int NR, int slot_bits, int swz, const std::vector<
 hq_status launch_expect_view(const void *state, hq_dtype dt, const EvParams &p, int grid, double *partials,
                              cudaStream_t s)
 {
-    const size_t elem = dt == HQ_C64 ? 8 : 16;
-    const size_t smem = size_t(kEvStages) * elem * (size_t(1) << p.g.L);
+    const size_t smem = dt == HQ_C64 ? ev_dyn_smem<float>(p.g.L) : ev_dyn_smem<double>(p.g.L);
     if (dt == HQ_C64) {
         occupancy((const void *)k_expect_view<float>, kEvThreads, smem);
         k_expect_view<float><<<grid, kEvThreads, smem, s>>>(p, (const float2 *)state, partials);

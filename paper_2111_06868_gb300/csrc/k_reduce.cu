@@ -390,29 +390,58 @@ static hq_status build_groups(int n, const hq_pauli_term *terms, int T, std::vec
     return HQ_OK;
 }
 
-// Tile passes for the tiled evaluation: terms whose X mask has no bit above
-// the first tile go to pass 0; the others are packed greedily into passes of
+// Tile passes for the tiled evaluation.  Terms whose X mask has no bit
+// above the first tile go to the low tile's passes (at most kTileTerms terms
+// each); terms whose X mask is one bit above it go to register passes of up
+// to Hr such bits (k_expect_reg.cu, no shared memory) unless they have Z on
+// another bit of their pass; the others are packed greedily into passes of
 // `low` low bits (1 KB runs) plus at most h = L - low higher bits.  Terms
 // needing more than h higher bits are left out (evaluated by the per-group
 // kernel).
 struct TilePass {
-    std::vector<int> high;   // flat bits of the tile above the low run
+    std::vector<int> high;   // flat bits of the tile above the low run (register pass: its bits)
     std::vector<Tm> terms;
+    bool reg = false;        // register pass
 };
 
-static void plan_tile_passes(int n, int L, int low, const std::vector<Tm> &tms, std::vector<TilePass> &passes,
+static void plan_tile_passes(int n, int L, int low, int Hr, const std::vector<Tm> &tms, std::vector<TilePass> &passes,
                              std::vector<Tm> &rest)
 {
     const int h = L - low;
     passes.clear();
-    std::vector<Tm> low_terms;
+    std::vector<Tm> low_terms, single, multi;
+    for (const Tm &m : tms) {
+        if ((m.xm >> L) == 0) low_terms.push_back(m);
+        else if (__builtin_popcountll(m.xm) == 1) single.push_back(m);
+        else multi.push_back(m);
+    }
+    // register passes: the distinct single X bits, Hr per pass, ascending
+    std::vector<int> bits;
+    for (const Tm &m : single) bits.push_back(__builtin_ctzll(m.xm));
+    std::sort(bits.begin(), bits.end());
+    bits.erase(std::unique(bits.begin(), bits.end()), bits.end());
+    std::vector<TilePass> regs;
+    for (size_t i = 0; i < bits.size(); i += size_t(Hr)) {
+        TilePass tp;
+        tp.reg = true;
+        tp.high.assign(bits.begin() + i, bits.begin() + std::min(bits.size(), i + size_t(Hr)));
+        regs.push_back(tp);
+    }
+    for (const Tm &m : single) {
+        const int b = __builtin_ctzll(m.xm);
+        for (TilePass &tp : regs) {
+            if (std::find(tp.high.begin(), tp.high.end(), b) == tp.high.end()) continue;
+            uint64_t others = 0;
+            for (int x : tp.high)
+                if (x != b) others |= uint64_t(1) << x;
+            if ((m.zm & others) || int(tp.terms.size()) >= kErMaxTerms) multi.push_back(m);
+            else tp.terms.push_back(m);
+            break;
+        }
+    }
     uint64_t cur = 0;
     int ci = -1;
-    for (const Tm &m : tms) {
-        if ((m.xm >> L) == 0) {
-            low_terms.push_back(m);
-            continue;
-        }
+    for (const Tm &m : multi) {
         const uint64_t need = m.xm & ~((uint64_t(1) << low) - 1);
         if (__builtin_popcountll(need) > h) {
             rest.push_back(m);
@@ -429,6 +458,8 @@ static void plan_tile_passes(int n, int L, int low, const std::vector<Tm> &tms, 
         for (int b = low; b < n; ++b)
             if ((cur >> b) & 1) passes[ci].high.push_back(b);
     }
+    for (TilePass &tp : regs)
+        if (!tp.terms.empty()) passes.push_back(tp);
     // the low tile's terms first, at most kTileTerms per pass (one parameter block)
     std::vector<TilePass> first;
     for (size_t i = 0; i < low_terms.size(); i += kTileTerms) {
@@ -437,6 +468,21 @@ static void plan_tile_passes(int n, int L, int low, const std::vector<Tm> &tms, 
                                   low_terms.begin() + std::min(low_terms.size(), i + size_t(kTileTerms)));
     }
     passes.insert(passes.begin(), first.begin(), first.end());
+}
+
+// One register pass (k_expect_reg.cu); false if its terms do not fit.
+static bool try_reg_pass(const void *state, int n, hq_dtype dt, const TilePass &tp, int grid, double *part,
+                         cudaStream_t s, hq_status &st)
+{
+    static thread_local ErParams ep;
+    std::vector<EvInRegTerm> in;
+    for (const Tm &m : tp.terms) in.push_back({m.xm, m.zm, m.wr, m.wi});
+    if (!plan_expect_reg(n, int(tp.high.size()), tp.high.data(), in, ep)) return false;
+    const int gx = std::min(grid, sm_count());
+    st = launch_expect_reg(state, dt, ep, gx, part, s);
+    if (st == HQ_OK && gx < grid)
+        st = cuda_status("clear partials", cudaMemsetAsync(part + gx, 0, sizeof(double) * size_t(grid - gx), s));
+    return true;
 }
 
 // One pass on the register-view kernel (k_expect_view.cu): the tile holds
@@ -492,7 +538,8 @@ static hq_status launch_tiled(const void *state, int n, hq_dtype dt, const std::
         const TilePass &tp = passes[pi];
         double *part = scratch + 1 + pi * size_t(grid);
         hq_status vst = HQ_OK;
-        if (try_view_pass(state, n, dt, tp, grid, part, s, vst)) {
+        if (tp.reg ? try_reg_pass(state, n, dt, tp, grid, part, s, vst)
+                   : try_view_pass(state, n, dt, tp, grid, part, s, vst)) {
             if (vst != HQ_OK) return vst;
             continue;
         }
@@ -559,7 +606,7 @@ hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pau
         const int ngroups = int(std::unique(xms.begin(), xms.end()) - xms.begin());
         std::vector<TilePass> passes;
         std::vector<Tm> rest;
-        plan_tile_passes(n, dt == HQ_C64 ? 13 : 12, dt == HQ_C64 ? 7 : 6, tms, passes, rest);
+        plan_tile_passes(n, dt == HQ_C64 ? 13 : 12, dt == HQ_C64 ? 7 : 6, expect_reg_max_bits(dt), tms, passes, rest);
         if (ngroups >= 2 && rest.empty() && int(passes.size()) < ngroups) {
             const int grid = 3 * sm_count();
             double *scratch = nullptr;

@@ -104,6 +104,7 @@ def load(path: str | None = None):
         "hq_last_error": ([], ctypes.c_char_p),
         "hq_version": ([], ctypes.c_char_p),
         "hq_state_init": ([V, I, I, ctypes.c_char_p, V], I),
+        "hq_state_upload": ([V, V, I, I, V], I),
         "hq_fuse": ([I, V, I, I, V, P(I), V, ctypes.c_int64, V], I),
         "hq_fuse_dag": ([I, V, I, I, I, ctypes.c_uint64, V, P(I), V, ctypes.c_int64, V], I),
         "hq_gate_structure": ([I, V, P(I), V], I),
@@ -230,6 +231,16 @@ def hq_state_init(state, tokens: str | None = None, stream=None):
         if len(tok) != n:
             raise ValueError("need one token per qubit")
     _check(load().hq_state_init(ptr, n, dt, tok, _stream(stream)), "hq_state_init")
+    return state
+
+
+def hq_state_upload(state, host, stream=None):
+    """state (CUDA tensor) <- host (CPU tensor of the same dtype and size;
+    pinned memory is read by the GPU directly), asynchronously on the stream."""
+    ptr, n, dt = _state_args(state)
+    if host.is_cuda or not host.is_contiguous() or host.dtype != state.dtype or host.numel() != state.numel():
+        raise ValueError("host must be a contiguous CPU tensor of the state's dtype and size")
+    _check(load().hq_state_upload(ptr, ctypes.c_void_p(host.data_ptr()), n, dt, _stream(stream)), "hq_state_upload")
     return state
 
 

@@ -407,3 +407,60 @@ def test_expectation_ansatz_hamiltonian_large_state(hq, dt):
     got = hq.hq_expectation(to_dev(psi, dt), H)
     tol = 1e-12 if dt == "c128" else 1e-5 * sum(abs(c) for c, _ in H)
     assert abs(got - oracle.expectation(psi, H)) <= tol
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_expectation_single_x_with_z_strings(hq, dt):
+    """Terms whose X (or Y) is one high qubit, with Z on the lane bits, on
+    bits outside the pass, and on other bits of the same pass (those leave
+    the register passes for the shared-memory ones); several terms per qubit
+    and more single-X terms than one parameter block holds."""
+    n = 21
+    psi = np_state(n, 321)
+    rng = C.SplitMix64(77)
+    H = []
+    for q in range(n - 13):  # flat bits 13..20 are qubits 0..7
+        for _ in range(14):
+            zs = sorted({rng.randint(0, n - 1) for _ in range(rng.randint(0, 3))} - {q})
+            H.append((rng.uniform() - 0.5, ((q, "XY"[rng.randint(0, 1)]),) + tuple((z, "Z") for z in zs)))
+    H.append((0.7, ((0, "X"), (1, "Z"))))      # Z on another bit of the same register pass
+    H.append((0.4, ((3, "Y"), (n - 1, "Z"))))  # Z on flat bit 0 (a lane bit)
+    assert len(H) > 96
+    want = oracle.expectation(psi, H)
+    got = hq.hq_expectation(to_dev(psi, dt), H)
+    tol = 1e-12 if dt == "c128" else 1e-5 * sum(abs(c) for c, _ in H)
+    assert abs(got - want) <= tol, (got, want)
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_state_upload_from_host(hq, dt, pinned):
+    """hq_state_upload: pinned host memory read by the SMs, pageable memory
+    through the driver; the device state equals the host bytes exactly, and
+    evolving it gives the oracle's state."""
+    n = 17
+    psi = np_state(n, 55)
+    host = torch.from_numpy(psi).to(DT[dt])
+    if pinned:
+        host = host.pin_memory()
+    st = torch.empty(1 << n, dtype=DT[dt], device="cuda")
+    hq.hq_state_upload(st, host)
+    torch.cuda.synchronize()
+    assert torch.equal(st.cpu(), host)
+    M = C.random_unitary(2, C.SplitMix64(4))
+    hq.hq_apply_blocks(st, [((3, 11), M)])
+    want = oracle.apply_gate(host.numpy().astype(np.complex128), n, (3, 11), M)
+    got = st.cpu().numpy().astype(np.complex128)
+    tol = 1e-12 if dt == "c128" else 2e-6
+    assert np.abs(got - want).max() <= tol
+
+
+def test_state_upload_argument_errors(hq):
+    st = torch.empty(1 << 6, dtype=torch.complex64, device="cuda")
+    host = torch.zeros(1 << 6, dtype=torch.complex64)
+    with pytest.raises(ValueError):
+        hq.hq_state_upload(st, host[:32])
+    lib = hq.load()
+    assert lib.hq_state_upload(hq.ctypes.c_void_p(st.data_ptr()), None, 6, hq.HQ_C64, None) == -1
+    assert lib.hq_state_upload(hq.ctypes.c_void_p(st.data_ptr()), hq.ctypes.c_void_p(host.data_ptr() + 8), 6,
+                               hq.HQ_C64, None) == -13
