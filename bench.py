@@ -170,13 +170,16 @@ def block_class(qs, m, engine, tc_min_k, n=30, elem_bytes=8):
     sector_bits = 2 if elem_bytes == 8 else 1
     if nc and k - nc <= 2 and any((mask >> j) & 1 and n - 1 - q >= sector_bits for j, q in enumerate(qs)):
         return f"k_ctrl_kt{k - nc}"
+    df = "_df" if engine == "df" and elem_bytes == 16 else ""
     if not np.any(m[~np.eye(d, dtype=bool)]):
-        return f"k_diag_k{k}"
+        return f"k_diag{df}_k{k}"
     nz = np.abs(m) > 4 * np.finfo(np.float64).eps * np.abs(m).max()
     if k <= 4 and np.all(nz.sum(axis=0) == 1) and np.all(nz.sum(axis=1) == 1):
-        return f"k_mono_k{k}"
+        return f"k_mono{df}_k{k}"
     if engine.startswith("tc") and k >= max(tc_min_k, 4) and n >= k + 7:
         return f"k_tc_{engine[3:]}_k{6 if n >= 13 else k}"
+    if engine == "df" and elem_bytes == 16 and k <= 4:
+        return f"k_gather_df_k{k}"
     return f"k_gather_k{k}" if k <= 4 else f"k_block_k{k}"
 
 

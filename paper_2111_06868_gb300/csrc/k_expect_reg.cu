@@ -30,8 +30,11 @@ namespace {
 
 constexpr int kErThreads = 256;
 
+// two CTAs (16 warps) per SM while the registers allow it
+template <typename R, int H> constexpr int er_min_blocks() { return H <= (sizeof(R) == 4 ? 5 : 4) ? 2 : 1; }
+
 template <typename R, int H>
-__global__ void __launch_bounds__(kErThreads, 1) k_expect_reg(const ErParams p,
+__global__ void __launch_bounds__(kErThreads, er_min_blocks<R, H>()) k_expect_reg(const ErParams p,
                                                               const typename C2<R>::type *__restrict__ psi,
                                                               double *__restrict__ partials)
 {
@@ -50,9 +53,19 @@ __global__ void __launch_bounds__(kErThreads, 1) k_expect_reg(const ErParams p,
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (kErThreads / 32);
     const int64_t units = int64_t(1) << (p.n - 5 - H);
+    // units per step: with few register bits a warp takes several units at
+    // once, so that each thread keeps 32 (complex128: 16) loads in flight
+    constexpr int TARGET = sizeof(R) == 4 ? 32 : 16;
+    constexpr int U = E >= TARGET ? 1 : TARGET / E;
     double acc = 0;
     R accr = 0, comp = 0;
-    for (int64_t u = int64_t(blockIdx.x) * (kErThreads / 32) + (threadIdx.x >> 5); u < units; u += warps) {
+    for (int64_t u0 = (int64_t(blockIdx.x) * (kErThreads / 32) + (threadIdx.x >> 5)) * U; u0 < units;
+         u0 += warps * U) {
+      V au[U][E];
+      int64_t xu[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int64_t u = u0 + k;  // units is a power of two >= U whenever U > 1 units exist
         // flat index of slot 0 of this lane: u over the bits outside 0..4 and hb
         int64_t x = u << 5;
 #pragma unroll
@@ -61,10 +74,18 @@ __global__ void __launch_bounds__(kErThreads, 1) k_expect_reg(const ErParams p,
             x = ((x >> hb) << (hb + 1)) | (x & ((int64_t(1) << hb) - 1));
         }
         x |= lane;
-        const V *src = psi + x;
-        V a[E];
+        xu[k] = x;
+        if (u < units) {
+            const V *src = psi + x;
 #pragma unroll
-        for (int j = 0; j < E; ++j) a[j] = __ldcs(src + s_off[j]);
+            for (int j = 0; j < E; ++j) au[k][j] = __ldcs(src + s_off[j]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (u0 + k >= units) break;
+        const V *a = au[k];
+        const int64_t x = xu[k];
         // pair sums per register bit (four partial sums against long chains)
         R sre[H], sim[H];
 #pragma unroll
@@ -107,6 +128,7 @@ __global__ void __launch_bounds__(kErThreads, 1) k_expect_reg(const ErParams p,
         } else {
             acc += part;
         }
+      }
     }
     if constexpr (sizeof(R) == 4) acc = double(accr) - double(comp);
     const double s = block_sum(acc);
@@ -116,8 +138,8 @@ __global__ void __launch_bounds__(kErThreads, 1) k_expect_reg(const ErParams p,
 template <typename R, int H>
 hq_status launch_reg_h(const void *state, const ErParams &p, int grid, double *partials, cudaStream_t s)
 {
-    occupancy((const void *)k_expect_reg<R, H>, kErThreads, 0);
-    k_expect_reg<R, H><<<grid, kErThreads, 0, s>>>(p, (const typename C2<R>::type *)state, partials);
+    const int g = std::min(grid, sm_count() * occupancy((const void *)k_expect_reg<R, H>, kErThreads, 0));
+    k_expect_reg<R, H><<<g, kErThreads, 0, s>>>(p, (const typename C2<R>::type *)state, partials);
     return cuda_status("k_expect_reg", cudaGetLastError());
 }
 

@@ -214,12 +214,21 @@ __global__ void __launch_bounds__(kEvThreads, 1) k_expect_view(const EvParams p,
     __shared__ R s_sw[2][kEvMaxTerms];
     __shared__ int64_t s_runoff[64];
     __shared__ EvTerm s_term[kEvMaxTerms];
+    // the groups and each view's group range: read with runtime indices in
+    // the loops below, from shared memory (not the parameter space)
+    __shared__ EvGroup s_grp[kEvMaxGroups];
+    __shared__ int s_vg[kEvMaxViews][2];
 
     const TileGeom &g = p.g;
     const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
     const int tid = threadIdx.x;
     for (int k = tid; k < (1 << (g.L - g.c)); k += kEvThreads) s_runoff[k] = g.runoff[k];
     for (int k = tid; k < p.nt; k += kEvThreads) s_term[k] = p.term[k];
+    for (int k = tid; k < p.ng; k += kEvThreads) s_grp[k] = p.grp[k];
+    if (tid < p.nv) {
+        s_vg[tid][0] = p.view[tid].g0;
+        s_vg[tid][1] = p.view[tid].g1;
+    }
     for (int v = 0; v < p.nv; ++v) {
         if (tid < E) s_pj[v][tid] = p.view[v].pj[tid];
         int tl = 0;
@@ -287,9 +296,9 @@ __global__ void __launch_bounds__(kEvThreads, 1) k_expect_view(const EvParams p,
             const int pt = s_pt[v][tid];
 #pragma unroll
             for (int j = 0; j < E; ++j) a[j] = T[pt ^ s_pj[v][j]];
-            const int g0 = p.view[v].g0, g1 = p.view[v].g1;
+            const int g0 = s_vg[v][0], g1 = s_vg[v][1];
             int gi = g0;
-            if (gi < g1 && p.grp[gi].m == 0) {
+            if (gi < g1 && s_grp[gi].m == 0) {
                 // diagonal terms: Walsh-Hadamard transform of |a|^2
                 R W[E];
 #pragma unroll
@@ -305,8 +314,8 @@ __global__ void __launch_bounds__(kEvThreads, 1) k_expect_view(const EvParams p,
                         }
 #pragma unroll
                 for (int j = 0; j < E; ++j) s_wht[j][tid] = W[j];  // read back by index: no select chain
-                for (; gi < g1 && p.grp[gi].m == 0; ++gi) {
-                    const EvGroup &gr = p.grp[gi];
+                for (; gi < g1 && s_grp[gi].m == 0; ++gi) {
+                    const EvGroup &gr = s_grp[gi];
                     const R Wh = s_wht[gr.h][tid];
                     R c = 0;
                     for (int t = gr.t0; t < gr.t0 + gr.nt; ++t) {
@@ -317,7 +326,7 @@ __global__ void __launch_bounds__(kEvThreads, 1) k_expect_view(const EvParams p,
                 }
             }
             for (; gi < g1; ++gi) {
-                const EvGroup &gr = p.grp[gi];
+                const EvGroup &gr = s_grp[gi];
                 if (gr.m & (gr.m - 1))
                     part += ev_xgroup_smem<R>(a, T, pt, s_pj[v], gr, s_term, sw, ts0, ts1, ts2);
                 else

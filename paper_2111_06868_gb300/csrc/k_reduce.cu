@@ -421,10 +421,13 @@ static void plan_tile_passes(int n, int L, int low, int Hr, const std::vector<Tm
     std::sort(bits.begin(), bits.end());
     bits.erase(std::unique(bits.begin(), bits.end()), bits.end());
     std::vector<TilePass> regs;
-    for (size_t i = 0; i < bits.size(); i += size_t(Hr)) {
+    const size_t nreg = (bits.size() + size_t(Hr) - 1) / size_t(Hr);  // as few passes as fit, bits spread evenly
+    for (size_t r = 0, i = 0; r < nreg; ++r) {
+        const size_t take = (bits.size() - i + (nreg - r) - 1) / (nreg - r);
         TilePass tp;
         tp.reg = true;
-        tp.high.assign(bits.begin() + i, bits.begin() + std::min(bits.size(), i + size_t(Hr)));
+        tp.high.assign(bits.begin() + i, bits.begin() + i + take);
+        i += take;
         regs.push_back(tp);
     }
     for (const Tm &m : single) {
@@ -478,10 +481,10 @@ static bool try_reg_pass(const void *state, int n, hq_dtype dt, const TilePass &
     std::vector<EvInRegTerm> in;
     for (const Tm &m : tp.terms) in.push_back({m.xm, m.zm, m.wr, m.wi});
     if (!plan_expect_reg(n, int(tp.high.size()), tp.high.data(), in, ep)) return false;
-    const int gx = std::min(grid, sm_count());
-    st = launch_expect_reg(state, dt, ep, gx, part, s);
-    if (st == HQ_OK && gx < grid)
-        st = cuda_status("clear partials", cudaMemsetAsync(part + gx, 0, sizeof(double) * size_t(grid - gx), s));
+    // the kernel takes at most `grid` CTAs (fewer when its occupancy is lower)
+    // and writes one partial each; the slots after them are cleared first
+    st = cuda_status("clear partials", cudaMemsetAsync(part, 0, sizeof(double) * size_t(grid), s));
+    if (st == HQ_OK) st = launch_expect_reg(state, dt, ep, grid, part, s);
     return true;
 }
 
