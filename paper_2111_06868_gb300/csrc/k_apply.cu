@@ -350,11 +350,12 @@ __global__ void __launch_bounds__(kThreads) k_gather(const TileGeom g, const Mat
 // whose swizzle is odd (the two amplitudes trade places) as two 8-byte
 // copies.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void tile_load_async(const TileGeom &g, const float2 *__restrict__ base, float2 *tile)
+__device__ __forceinline__ void tile_load_async(const TileGeom &g, const int64_t *runoff,
+                                                const float2 *__restrict__ base, float2 *tile)
 {
     const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
     for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
-        const float2 *src = base + g.runoff[i >> g.c] + (i & cmask);
+        const float2 *src = base + runoff[i >> g.c] + (i & cmask);
         const int f = (i >> 4) & 15;
         if (f & 1) {
             cp_async8(&tile[i ^ f], src);
@@ -366,27 +367,44 @@ __device__ __forceinline__ void tile_load_async(const TileGeom &g, const float2 
 }
 
 
+__device__ __forceinline__ void tile_store_r(const TileGeom &g, const int64_t *runoff, float2 *__restrict__ base,
+                                             const float2 *tile)
+{
+    const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
+    for (int i = threadIdx.x * 2; i < TS; i += blockDim.x * 2) {
+        const int f = (i >> 4) & 15;
+        const float4 w = *reinterpret_cast<const float4 *>(&tile[(i ^ f) & ~1]);
+        const float4 v = (f & 1) ? make_float4(w.z, w.w, w.x, w.y) : w;
+        *reinterpret_cast<float4 *>(base + runoff[i >> g.c] + (i & cmask)) = v;
+    }
+}
+
 // Every tile of g through `op` (which multiplies a tile in shared memory in
 // place and ends with a barrier), with the copy of the CTA's next tile in
 // flight meanwhile.  Dynamic shared memory: two tiles of 2^g.L complex64.
+// The run offsets are read from shared memory (an index into the parameter
+// block that depends on the thread costs an indexed constant load per copy).
 template <typename Op>
 __device__ __forceinline__ void tiles_pipelined(const TileGeom &g, float2 *__restrict__ state, Op op)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int64_t s_runoff[1 << HQ_MAX_K];
     float2 *cur = reinterpret_cast<float2 *>(smem_raw), *nxt = cur + (1 << g.L);
+    for (int j = threadIdx.x; j < (1 << (g.L - g.c)); j += blockDim.x) s_runoff[j] = g.runoff[j];
+    __syncthreads();
     int64_t t = blockIdx.x;
     if (t >= g.total_tiles) return;
-    tile_load_async(g, state + tile_base(g, t), cur);
+    tile_load_async(g, s_runoff, state + tile_base(g, t), cur);
     cp_async_commit();
     for (; t < g.total_tiles; t += gridDim.x) {
         const int64_t tn = t + gridDim.x;
         // nxt was last read by the store of tile t - grid, before the barrier that ended it
-        if (tn < g.total_tiles) tile_load_async(g, state + tile_base(g, tn), nxt);
+        if (tn < g.total_tiles) tile_load_async(g, s_runoff, state + tile_base(g, tn), nxt);
         cp_async_commit();  // possibly empty: every thread waits on the same group count
         cp_async_wait<1>(); // this thread's copies of tile t have landed
         __syncthreads();    // ... and everyone else's
         op(cur);
-        tile_store(g, state + tile_base(g, t), cur);
+        tile_store_r(g, s_runoff, state + tile_base(g, t), cur);
         __syncthreads();
         float2 *const tmp = cur;
         cur = nxt;

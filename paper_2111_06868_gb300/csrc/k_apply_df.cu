@@ -156,29 +156,41 @@ __device__ __forceinline__ double2 df_row(const float4 *m, const DfC *v)
 // ---------------------------------------------------------------------------
 // tiles: two buffers per CTA, the next tile's copy in flight
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void tile_load_async16(const TileGeom &g, const double2 *__restrict__ base, double2 *tile)
+// run offsets from shared memory (a runtime index into the parameter block
+// costs an indexed constant load per amplitude)
+__device__ __forceinline__ void tile_load_async16(const TileGeom &g, const int64_t *runoff,
+                                                  const double2 *__restrict__ base, double2 *tile)
 {
     const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
-    for (int i = threadIdx.x; i < TS; i += blockDim.x) cp_async16(&tile[swz<double>(i)], base + g.runoff[i >> g.c] + (i & cmask));
+    for (int i = threadIdx.x; i < TS; i += blockDim.x) cp_async16(&tile[swz<double>(i)], base + runoff[i >> g.c] + (i & cmask));
+}
+__device__ __forceinline__ void tile_store16(const TileGeom &g, const int64_t *runoff, double2 *__restrict__ base,
+                                             const double2 *tile)
+{
+    const int TS = 1 << g.L, cmask = (1 << g.c) - 1;
+    for (int i = threadIdx.x; i < TS; i += blockDim.x) base[runoff[i >> g.c] + (i & cmask)] = tile[swz<double>(i)];
 }
 
 template <typename Op>
 __device__ __forceinline__ void df_tiles(const TileGeom &g, double2 *__restrict__ state, Op op)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int64_t s_runoff[1 << HQ_MAX_K];
     double2 *cur = reinterpret_cast<double2 *>(smem_raw), *nxt = cur + (1 << g.L);
+    for (int j = threadIdx.x; j < (1 << (g.L - g.c)); j += blockDim.x) s_runoff[j] = g.runoff[j];
+    __syncthreads();
     int64_t t = blockIdx.x;
     if (t >= g.total_tiles) return;
-    tile_load_async16(g, state + tile_base(g, t), cur);
+    tile_load_async16(g, s_runoff, state + tile_base(g, t), cur);
     cp_async_commit();
     for (; t < g.total_tiles; t += gridDim.x) {
         const int64_t tn = t + gridDim.x;
-        if (tn < g.total_tiles) tile_load_async16(g, state + tile_base(g, tn), nxt);
+        if (tn < g.total_tiles) tile_load_async16(g, s_runoff, state + tile_base(g, tn), nxt);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
         op(cur);
-        tile_store(g, state + tile_base(g, t), cur);
+        tile_store16(g, s_runoff, state + tile_base(g, t), cur);
         __syncthreads();
         double2 *const tmp = cur;
         cur = nxt;

@@ -42,13 +42,17 @@ __global__ void __launch_bounds__(kErThreads, er_min_blocks<R, H>()) k_expect_re
     constexpr int E = 1 << H, NP = E / 2;
     __shared__ int64_t s_off[E];  // flat offset of register slot j
     __shared__ ErTerm s_term[kErMaxTerms];
+    __shared__ R s_w[kErMaxTerms];  // the weights in the state's precision (no FP64 conversion per unit)
     for (int j = threadIdx.x; j < E; j += blockDim.x) {
         int64_t o = 0;
         for (int b = 0; b < H; ++b)
             if ((j >> b) & 1) o += int64_t(1) << p.hb[b];
         s_off[j] = o;
     }
-    for (int t = threadIdx.x; t < p.nt; t += blockDim.x) s_term[t] = p.term[t];
+    for (int t = threadIdx.x; t < p.nt; t += blockDim.x) {
+        s_term[t] = p.term[t];
+        s_w[t] = R(p.term[t].w);
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (kErThreads / 32);
@@ -119,7 +123,7 @@ __global__ void __launch_bounds__(kErThreads, er_min_blocks<R, H>()) k_expect_re
             for (int i = 0; i < H; ++i)
                 if (tm.bit == i) S = tm.imag ? sim[i] : sre[i];
             const uint32_t sg = (__popc(uint32_t(lane) & tm.zlane) + __popcll(uint64_t(x) & tm.zrest)) & 1u;
-            part += sg ? -R(tm.w) * S : R(tm.w) * S;
+            part += sg ? -s_w[t] * S : s_w[t] * S;
         }
         if constexpr (sizeof(R) == 4) {
             const R y = part - comp, s2 = accr + y;
