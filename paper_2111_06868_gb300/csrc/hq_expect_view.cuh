@@ -88,4 +88,29 @@ bool plan_expect_reg(int n, int H, const int *high_bits, const std::vector<EvInR
 hq_status launch_expect_reg(const void *state, hq_dtype dt, const ErParams &p, int grid, double *partials,
                             cudaStream_t s);
 
+// ----------------------------------------------------------------------------
+// the low-bit warp pass (k_expect_low.cu): diagonal strings and one-bit X
+// masks on the lowest 5 + RB flat bits (RB = 6 complex64, 5 complex128)
+// ----------------------------------------------------------------------------
+constexpr int kElMaxTerms = 96;
+constexpr int kElMaxBits = 6;
+struct ElTerm {
+    double w;        // diagonal: Re w; X terms: 2 Re w, or -2 Im w when imag
+    uint64_t zunit;  // Z bits above the unit (flat)
+    uint32_t zlane;  // Z bits on the lane bits of the term's layout (5 bits)
+    int h;           // diagonal: Z on the register bits; X terms: the register bit of the X
+    int imag;
+};
+struct ElParams {
+    int n, nt, nd, na, nb;        // terms: nd diagonal, then na in layout A, then nb in layout B
+    int need[2][kElMaxBits];      // per layout and register bit: 1 Re sums, 2 Im sums
+    ElTerm term[kElMaxTerms];
+};
+// flat bits a unit spans: 11 (complex64), 10 (complex128)
+int expect_low_bits(hq_dtype dt);
+// takes the terms it can (taken[t] = 1), at most kElMaxTerms; false if none
+bool plan_expect_low(int n, hq_dtype dt, const std::vector<EvInRegTerm> &in, ElParams &p, std::vector<int> &taken);
+hq_status launch_expect_low(const void *state, hq_dtype dt, const ElParams &p, int grid, double *partials,
+                            cudaStream_t s);
+
 }  // namespace hq

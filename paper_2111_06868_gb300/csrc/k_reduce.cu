@@ -390,42 +390,76 @@ static hq_status build_groups(int n, const hq_pauli_term *terms, int T, std::vec
     return HQ_OK;
 }
 
-// Tile passes for the tiled evaluation.  Terms whose X mask has no bit
-// above the first tile go to the low tile's passes (at most kTileTerms terms
-// each); terms whose X mask is one bit above it go to register passes of up
-// to Hr such bits (k_expect_reg.cu, no shared memory) unless they have Z on
-// another bit of their pass; the others are packed greedily into passes of
-// `low` low bits (1 KB runs) plus at most h = L - low higher bits.  Terms
-// needing more than h higher bits are left out (evaluated by the per-group
-// kernel).
+// Tile passes for the tiled evaluation, one read of the state each:
+//   * the low pass (k_expect_low.cu): the diagonal terms and the terms whose
+//     X mask is one of the lowest UB flat bits (at most kElMaxTerms);
+//   * register passes (k_expect_reg.cu): terms whose X mask is one bit at or
+//     above UB, up to Hr such bits per pass (not those with Z on another
+//     bit of their pass);
+//   * shared-memory tile passes (k_expect_view.cu, else k_expect_tile): the
+//     rest -- X masks inside the L lowest bits in the low tile, the others
+//     packed greedily into tiles of `low` low bits (1 KB runs) plus at most
+//     h = L - low higher bits.  Terms needing more than h higher bits are
+//     left out (the caller then takes the per-group kernel).
+enum PassKind { kPassView = 0, kPassReg = 1, kPassLow = 2 };
 struct TilePass {
     std::vector<int> high;   // flat bits of the tile above the low run (register pass: its bits)
     std::vector<Tm> terms;
-    bool reg = false;        // register pass
+    int kind = kPassView;
 };
 
-static void plan_tile_passes(int n, int L, int low, int Hr, const std::vector<Tm> &tms, std::vector<TilePass> &passes,
+static void plan_tile_passes(int n, hq_dtype dt, const std::vector<Tm> &tms, std::vector<TilePass> &passes,
                              std::vector<Tm> &rest)
 {
+    const int L = dt == HQ_C64 ? 13 : 12, low = dt == HQ_C64 ? 7 : 6;
+    const int Hr = expect_reg_max_bits(dt), UB = expect_low_bits(dt);
     const int h = L - low;
     passes.clear();
-    std::vector<Tm> low_terms, single, multi;
+    // the low pass takes what it can of the diagonal and low one-bit-X terms
+    std::vector<Tm> cand, others;
     for (const Tm &m : tms) {
+        const bool one = __builtin_popcountll(m.xm) == 1;
+        if (m.xm == 0 || (one && __builtin_ctzll(m.xm) < UB)) cand.push_back(m);
+        else others.push_back(m);
+    }
+    TilePass lowp;
+    lowp.kind = kPassLow;
+    if (!cand.empty() && n >= UB) {
+        std::vector<EvInRegTerm> in;
+        for (const Tm &m : cand) in.push_back({m.xm, m.zm, m.wr, m.wi});
+        static thread_local ElParams ep;
+        std::vector<int> taken;
+        plan_expect_low(n, dt, in, ep, taken);
+        for (size_t t = 0; t < cand.size(); ++t) (taken[t] ? lowp.terms : others).push_back(cand[t]);
+    } else {
+        others.insert(others.end(), cand.begin(), cand.end());
+    }
+    std::vector<Tm> low_terms, single, multi;
+    for (const Tm &m : others) {
         if ((m.xm >> L) == 0) low_terms.push_back(m);
         else if (__builtin_popcountll(m.xm) == 1) single.push_back(m);
         else multi.push_back(m);
     }
-    // register passes: the distinct single X bits, Hr per pass, ascending
+    // one-bit X terms of the low tile that the low pass left (above UB) go to register passes too
+    for (auto it = low_terms.begin(); it != low_terms.end();) {
+        if (__builtin_popcountll(it->xm) == 1 && __builtin_ctzll(it->xm) >= UB) {
+            single.push_back(*it);
+            it = low_terms.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    // register passes: the distinct single X bits, as few passes as fit, bits spread evenly
     std::vector<int> bits;
     for (const Tm &m : single) bits.push_back(__builtin_ctzll(m.xm));
     std::sort(bits.begin(), bits.end());
     bits.erase(std::unique(bits.begin(), bits.end()), bits.end());
     std::vector<TilePass> regs;
-    const size_t nreg = (bits.size() + size_t(Hr) - 1) / size_t(Hr);  // as few passes as fit, bits spread evenly
+    const size_t nreg = (bits.size() + size_t(Hr) - 1) / size_t(Hr);
     for (size_t r = 0, i = 0; r < nreg; ++r) {
         const size_t take = (bits.size() - i + (nreg - r) - 1) / (nreg - r);
         TilePass tp;
-        tp.reg = true;
+        tp.kind = kPassReg;
         tp.high.assign(bits.begin() + i, bits.begin() + i + take);
         i += take;
         regs.push_back(tp);
@@ -434,11 +468,15 @@ static void plan_tile_passes(int n, int L, int low, int Hr, const std::vector<Tm
         const int b = __builtin_ctzll(m.xm);
         for (TilePass &tp : regs) {
             if (std::find(tp.high.begin(), tp.high.end(), b) == tp.high.end()) continue;
-            uint64_t others = 0;
+            uint64_t obits = 0;
             for (int x : tp.high)
-                if (x != b) others |= uint64_t(1) << x;
-            if ((m.zm & others) || int(tp.terms.size()) >= kErMaxTerms) multi.push_back(m);
-            else tp.terms.push_back(m);
+                if (x != b) obits |= uint64_t(1) << x;
+            if ((m.zm & obits) || int(tp.terms.size()) >= kErMaxTerms) {
+                if ((m.xm >> L) == 0) low_terms.push_back(m);
+                else multi.push_back(m);
+            } else {
+                tp.terms.push_back(m);
+            }
             break;
         }
     }
@@ -465,12 +503,29 @@ static void plan_tile_passes(int n, int L, int low, int Hr, const std::vector<Tm
         if (!tp.terms.empty()) passes.push_back(tp);
     // the low tile's terms first, at most kTileTerms per pass (one parameter block)
     std::vector<TilePass> first;
+    if (!lowp.terms.empty()) first.push_back(lowp);
     for (size_t i = 0; i < low_terms.size(); i += kTileTerms) {
         first.emplace_back();
         first.back().terms.assign(low_terms.begin() + i,
                                   low_terms.begin() + std::min(low_terms.size(), i + size_t(kTileTerms)));
     }
     passes.insert(passes.begin(), first.begin(), first.end());
+}
+
+// The low pass (k_expect_low.cu); false if its terms do not all fit.
+static bool try_low_pass(const void *state, int n, hq_dtype dt, const TilePass &tp, int grid, double *part,
+                         cudaStream_t s, hq_status &st)
+{
+    static thread_local ElParams ep;
+    std::vector<EvInRegTerm> in;
+    for (const Tm &m : tp.terms) in.push_back({m.xm, m.zm, m.wr, m.wi});
+    std::vector<int> taken;
+    if (!plan_expect_low(n, dt, in, ep, taken)) return false;
+    for (int t : taken)
+        if (!t) return false;
+    st = cuda_status("clear partials", cudaMemsetAsync(part, 0, sizeof(double) * size_t(grid), s));
+    if (st == HQ_OK) st = launch_expect_low(state, dt, ep, grid, part, s);
+    return true;
 }
 
 // One register pass (k_expect_reg.cu); false if its terms do not fit.
@@ -541,8 +596,10 @@ static hq_status launch_tiled(const void *state, int n, hq_dtype dt, const std::
         const TilePass &tp = passes[pi];
         double *part = scratch + 1 + pi * size_t(grid);
         hq_status vst = HQ_OK;
-        if (tp.reg ? try_reg_pass(state, n, dt, tp, grid, part, s, vst)
-                   : try_view_pass(state, n, dt, tp, grid, part, s, vst)) {
+        const bool done = tp.kind == kPassLow   ? try_low_pass(state, n, dt, tp, grid, part, s, vst)
+                          : tp.kind == kPassReg ? try_reg_pass(state, n, dt, tp, grid, part, s, vst)
+                                                : try_view_pass(state, n, dt, tp, grid, part, s, vst);
+        if (done) {
             if (vst != HQ_OK) return vst;
             continue;
         }
@@ -609,7 +666,7 @@ hq_status launch_expectation(const void *state, int n, hq_dtype dt, const hq_pau
         const int ngroups = int(std::unique(xms.begin(), xms.end()) - xms.begin());
         std::vector<TilePass> passes;
         std::vector<Tm> rest;
-        plan_tile_passes(n, dt == HQ_C64 ? 13 : 12, dt == HQ_C64 ? 7 : 6, expect_reg_max_bits(dt), tms, passes, rest);
+        plan_tile_passes(n, dt, tms, passes, rest);
         if (ngroups >= 2 && rest.empty() && int(passes.size()) < ngroups) {
             const int grid = 3 * sm_count();
             double *scratch = nullptr;

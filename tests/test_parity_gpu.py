@@ -464,3 +464,25 @@ def test_state_upload_argument_errors(hq):
     assert lib.hq_state_upload(hq.ctypes.c_void_p(st.data_ptr()), None, 6, hq.HQ_C64, None) == -1
     assert lib.hq_state_upload(hq.ctypes.c_void_p(st.data_ptr()), hq.ctypes.c_void_p(host.data_ptr() + 8), 6,
                                hq.HQ_C64, None) == -13
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_expectation_low_pass_overflow_and_lane_signs(hq, dt):
+    """More diagonal and low one-bit-X terms than the low pass holds (the
+    rest go to the shared-memory passes), X and Y on every low qubit with Z
+    on lane bits, on the other layout's lane bits and above the unit."""
+    n = 16
+    psi = np_state(n, 404)
+    rng = C.SplitMix64(405)
+    H = []
+    for _ in range(110):
+        zs = sorted({rng.randint(0, n - 1) for _ in range(rng.randint(1, 4))})
+        H.append((rng.uniform() - 0.5, tuple((z, "Z") for z in zs)))
+    for q in range(n - 11, n):  # flat bits 0..10
+        for op in "XY":
+            zs = sorted({rng.randint(0, n - 1) for _ in range(2)} - {q})
+            H.append((rng.uniform() - 0.5, ((q, op),) + tuple((z, "Z") for z in zs)))
+    want = oracle.expectation(psi, H)
+    got = hq.hq_expectation(to_dev(psi, dt), H)
+    tol = 1e-12 if dt == "c128" else 1e-5 * sum(abs(c) for c, _ in H)
+    assert abs(got - want) <= tol, (got, want)
