@@ -157,11 +157,10 @@ def test_engine_rejects_complex64(hq):
 
 
 @pytest.mark.slow
-def test_n28_subset_fused_against_oracle(hq):
+def test_n28_subset_fused_against_oracle(hq, n28_oracle):
     """The 28-qubit subset of the 33-qubit layout (942 gates) fused into
     blocks of at most 4 qubits, in double-float, against the oracle."""
-    circ = C.config_n33(seed=0, first=28)
-    want = oracle.simulate(circ)
+    circ, want = n28_oracle
     st = torch.empty(1 << 28, dtype=torch.complex128, device="cuda")
     hq.hq_state_init(st)
     hq.hq_apply_blocks(st, hq.hq_fuse(28, circ.gates, 4, method="dag"), engine="df")

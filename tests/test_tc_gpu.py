@@ -194,14 +194,6 @@ def test_fused_grid_circuit_bf16_error_reported(hq):
     assert err <= 5e-3
 
 
-@pytest.fixture(scope="module")
-def n28_oracle():
-    """The 28-qubit subset of the 33-qubit layout (942 gates) simulated by the
-    oracle, gate by gate in complex128 (4 GiB)."""
-    circ = C.config_n33(seed=0, first=28)
-    return circ, oracle.simulate(circ)
-
-
 @pytest.mark.slow
 @pytest.mark.parametrize("engine,bar", [("tc_f16", 2e-5), ("cuda_core", 2e-5), ("tc_bf16", 5e-3)])
 def test_n28_subset_against_oracle(hq, n28_oracle, engine, bar):
