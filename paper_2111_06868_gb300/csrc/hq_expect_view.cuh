@@ -90,7 +90,7 @@ hq_status launch_expect_reg(const void *state, hq_dtype dt, const ErParams &p, i
 
 // ----------------------------------------------------------------------------
 // the low-bit warp pass (k_expect_low.cu): diagonal strings and one-bit X
-// masks on the lowest 5 + RB flat bits (RB = 6 complex64, 5 complex128)
+// masks on the lowest 5 + RB flat bits (RB = 5)
 // ----------------------------------------------------------------------------
 constexpr int kElMaxTerms = 96;
 constexpr int kElMaxBits = 6;
@@ -106,7 +106,7 @@ struct ElParams {
     int need[2][kElMaxBits];      // per layout and register bit: 1 Re sums, 2 Im sums
     ElTerm term[kElMaxTerms];
 };
-// flat bits a unit spans: 11 (complex64), 10 (complex128)
+// flat bits a unit spans (10: five lane and five register bits)
 int expect_low_bits(hq_dtype dt);
 // takes the terms it can (taken[t] = 1), at most kElMaxTerms; false if none
 bool plan_expect_low(int n, hq_dtype dt, const std::vector<EvInRegTerm> &in, ElParams &p, std::vector<int> &taken);

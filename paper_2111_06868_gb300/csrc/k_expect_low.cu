@@ -2,8 +2,8 @@
 // strings, and terms whose X mask is one of the lowest flat bits, in one
 // read of the state with no barrier between warps.
 //
-// A warp takes units of 2^(5+RB) consecutive amplitudes (RB = 6 for
-// complex64, 5 for complex128): lane l holds amplitudes l + 32 j,
+// A warp takes units of 2^(5+RB) consecutive amplitudes (RB = 5): lane l
+// holds amplitudes l + 32 j,
 // j < 2^RB, so lanes run over flat bits 0..4 and registers over bits
 // 5..4+RB (each load instruction reads one 256-byte run).  In that layout
 //   * a diagonal string w (-1)^popc(x & z) sums to
@@ -16,8 +16,8 @@
 //     (j, j | 2^i): 2 s Re(w conj(a_j) a_{j|2^i}) summed over the pairs;
 // then the warp transposes the unit through its own shared-memory region
 // (element e at e ^ ((e >> 5) & 31): both layouts conflict-free) so that lane
-// l holds amplitudes 32 l + i' (i' over bits 0..4, and bit 10 for complex64
-// as the sixth register bit) and the terms with one X bit among bits 0..4
+// l holds amplitudes 32 l + i' (i' over bits 0..4; with a sixth register
+// bit, bit 10 as well) and the terms with one X bit among bits 0..4
 // pair registers the same way.  Terms with Z on another register bit of
 // their layout are not taken (they go to the shared-memory tile passes).
 // Per thread, sums are formed per unit in the state's precision
@@ -37,10 +37,10 @@ constexpr int kElWarps = kElThreads / 32;
 
 template <typename R> struct ElShape;
 template <> struct ElShape<float> {
-    static constexpr int RB = 6;
+    static constexpr int RB = 5, MIN_BLOCKS = 2;  // 16 warps per SM (a sixth register bit: 8, latency-bound)
 };
 template <> struct ElShape<double> {
-    static constexpr int RB = 5;
+    static constexpr int RB = 5, MIN_BLOCKS = 1;
 };
 
 template <typename R>
@@ -87,7 +87,7 @@ __device__ __forceinline__ void el_all_pairs(const typename C2<R>::type *a, cons
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kElThreads, 1) k_expect_low(const ElParams p,
+__global__ void __launch_bounds__(kElThreads, ElShape<R>::MIN_BLOCKS) k_expect_low(const ElParams p,
                                                               const typename C2<R>::type *__restrict__ psi,
                                                               double *__restrict__ partials)
 {
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kElThreads, 1) k_expect_low(const ElParams p,
             }
             __syncwarp();
             // lane l now takes e = 32 l' ... : register i' < 32 is flat bits 0..4,
-            // register bit 5 (complex64) is flat bit 10, the lane flat bits 5..9
+            // a sixth register bit (RB = 6) would be flat bit 10; the lane is flat bits 5..9
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 const int e = ((j >> 5) << 10) | (lane << 5) | (j & 31);
