@@ -54,6 +54,11 @@ bool adj_plan(int n, hq_dtype dt, const hq_op *ops, int G, AdjPlan &plan);
 hq_status adj_launch_pass(hq_dtype dt, bool rev, const APass &ps, const AOp *dev_ops, void *phi, int n, int batch,
                           const double2 *cs, int P, double *partials, int nbx, cudaStream_t s);
 
+// The same pass for complex128 states in double-float arithmetic
+// (k_adjoint_df.cu); adj_launch_pass takes it for HQ_C128.
+hq_status adj_launch_pass_df(bool rev, const APass &ps, const AOp *dev_ops, void *phi, int n, int batch,
+                             const double2 *cs, int P, double *partials, int nbx, cudaStream_t s);
+
 // cs[i] = (cos theta_i/2, sin theta_i/2)
 hq_status adj_half_angles(const double *theta, int64_t count, double2 *cs, cudaStream_t s);
 

@@ -652,8 +652,8 @@ hq_status adj_launch_pass(hq_dtype dt, bool rev, const APass &ps, const AOp *dev
     if (dt == HQ_C64)
         return rev ? launch_pass_t<float, true>(ps, dev_ops, phi, n, batch, cs, P, partials, nbx, s)
                    : launch_pass_t<float, false>(ps, dev_ops, phi, n, batch, cs, P, partials, nbx, s);
-    return rev ? launch_pass_t<double, true>(ps, dev_ops, phi, n, batch, cs, P, partials, nbx, s)
-               : launch_pass_t<double, false>(ps, dev_ops, phi, n, batch, cs, P, partials, nbx, s);
+    // complex128: double-float arithmetic on the FP32 pipes (k_adjoint_df.cu)
+    return adj_launch_pass_df(rev, ps, dev_ops, phi, n, batch, cs, P, partials, nbx, s);
 }
 
 hq_status adj_half_angles(const double *theta, int64_t count, double2 *cs, cudaStream_t s)

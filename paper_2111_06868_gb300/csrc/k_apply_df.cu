@@ -7,20 +7,11 @@
 // dense 1-qubit gate needs 16 flop per amplitude, 15.6 ms at n = 30 against
 // 5.1 ms of HBM time, and a fused 4-qubit block 128 flop.  Here every double
 // is carried as an unevaluated sum hi + lo of two floats (48 significant
-// bits):
-//   * products by Dekker's method with an FMA: p = x_h y_h exactly as
-//     p + fma(x_h, y_h, -p), plus the cross terms x_h y_l + x_l y_h;
-//   * sums by Knuth's two-sum: s = a + b and its exact rounding error
-//     (a - (s - bb)) + (b - bb), bb = s - a, collected in a float beside s;
-//   * the result renormalised once per output by a fast two-sum;
-//   * doubles split into (hi, lo) and rebuilt from them with integer
-//     operations on their bit fields, so that no instruction of the kernels
-//     runs on the FP64 pipe.
-// Every rounding is to nearest in FP32 (the intrinsics below are never
-// contracted into FMAs).  The error of one output against exact arithmetic
+// bits) with error-free products and sums (hq_df.cuh), and doubles are split
+// and rebuilt in integer arithmetic, so that no instruction of the kernels
+// runs on the FP64 pipe.  The error of one output against exact arithmetic
 // is a few units of 2^-48 relative to the sum of the magnitudes of its
-// products; magnitudes below 2^-126 are flushed to zero (2^-74 for the lo
-// part), far under the 1e-12 bar of complex128.
+// products, far under the 1e-12 bar of complex128.
 //
 // Kernels: k_gather_df<K> (dense, K <= 4) and k_mono_df<K> (one nonzero per
 // row, K <= 4) on tiles of 2^11 amplitudes in shared memory, two buffers per
@@ -30,6 +21,7 @@
 #include <cstring>
 
 #include "hq_cp_async.cuh"
+#include "hq_df.cuh"
 #include "hq_internal.cuh"
 
 namespace hq {
@@ -38,120 +30,6 @@ namespace {
 
 constexpr int kDfThreads = 256;
 constexpr int kDfTileBits = 11;  // 2^11 complex128 = 32 KB per buffer
-
-// ---------------------------------------------------------------------------
-// conversions (integer arithmetic on the bit fields)
-// ---------------------------------------------------------------------------
-struct DfC {
-    float rh, rl, ih, il;  // re = rh + rl, im = ih + il
-};
-
-// d = hi + lo to 48 bits: hi = d truncated to 24 significant bits, lo = the
-// remaining 29 mantissa bits (rounded to 24); |d| < 2^-126 gives 0.
-__device__ __forceinline__ void df_split(double d, float &hi, float &lo)
-{
-    const unsigned long long b = __double_as_longlong(d);
-    const uint32_t hw = uint32_t(b >> 32), lw = uint32_t(b);
-    const uint32_t sgn = hw & 0x80000000u;
-    const uint32_t ex = (hw >> 20) & 0x7FFu;  // biased exponent (1023)
-    // exponent rebiased to 127, top 23 of the 52 mantissa bits
-    const uint32_t hb = sgn | (((hw & 0x7FFFFFFFu) - 0x38000000u) << 3) | (lw >> 29);
-    // remaining 29 mantissa bits, scaled by 2^(e - 52): exponent field e - 52 + 127
-    const float lo_mag = __fmul_rn(__uint2float_rn(lw & 0x1FFFFFFFu), __uint_as_float((ex - 948u) << 23));
-    hi = ex > 896u ? __uint_as_float(hb) : 0.f;
-    lo = ex > 948u ? __uint_as_float(__float_as_uint(lo_mag) | sgn) : 0.f;
-}
-
-// The double nearest below |h + l| in magnitude (truncated to 53 bits), for a
-// normalised pair (|l| <= ulp(h) / 2); |h| < 2^-126 gives 0.
-__device__ __forceinline__ double df_join(float h, float l)
-{
-    const uint32_t hb = __float_as_uint(h), lb = __float_as_uint(l);
-    const int eh = int((hb >> 23) & 0xFFu), el = int((lb >> 23) & 0xFFu);
-    if (eh == 0) return 0.0;
-    // h = M 2^(eh - 127 - 52) with M of 53 bits
-    unsigned long long M = (unsigned long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
-    if (el != 0) {
-        const unsigned long long ml = (lb & 0x7FFFFFu) | 0x800000u;
-        const int sh = el - eh + 29;  // l = (ml << sh) 2^(eh - 127 - 52)
-        const unsigned long long Ml = sh >= 0 ? (ml << sh) : (sh > -24 ? (ml >> -sh) : 0ull);
-        M = ((hb ^ lb) >> 31) ? M - Ml : M + Ml;
-    }
-    int e = eh + 896;  // biased double exponent of h
-    if (M >> 53) {
-        M >>= 1;
-        ++e;
-    } else if (!(M >> 52)) {
-        M <<= 1;
-        --e;
-    }
-    return __longlong_as_double((long long)((((unsigned long long)(hb >> 31)) << 63) |
-                                            ((unsigned long long)e << 52) | (M & ((1ull << 52) - 1))));
-}
-
-__device__ __forceinline__ DfC df_load(const double2 v)
-{
-    DfC c;
-    df_split(v.x, c.rh, c.rl);
-    df_split(v.y, c.ih, c.il);
-    return c;
-}
-
-// ---------------------------------------------------------------------------
-// error-free accumulation of real products
-// ---------------------------------------------------------------------------
-struct DfAcc {
-    float s, c;  // value s + c, c collecting the exact rounding errors
-};
-
-// a = (x_h + x_l)(y_h + y_l), the first term of a sum
-__device__ __forceinline__ DfAcc df_first(float xh, float xl, float yh, float yl)
-{
-    const float p = __fmul_rn(xh, yh);
-    float e = __fmaf_rn(xh, yh, -p);
-    e = __fmaf_rn(xh, yl, e);
-    e = __fmaf_rn(xl, yh, e);
-    return {p, e};
-}
-
-// a += (x_h + x_l)(y_h + y_l)
-__device__ __forceinline__ void df_add_prod(DfAcc &a, float xh, float xl, float yh, float yl)
-{
-    const float p = __fmul_rn(xh, yh);
-    float e = __fmaf_rn(xh, yh, -p);
-    e = __fmaf_rn(xh, yl, e);
-    e = __fmaf_rn(xl, yh, e);
-    const float s = __fadd_rn(a.s, p);
-    const float bb = __fsub_rn(s, a.s);
-    const float t = __fadd_rn(__fsub_rn(a.s, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    a.s = s;
-    a.c = __fadd_rn(a.c, __fadd_rn(t, e));
-}
-
-__device__ __forceinline__ double df_finish(const DfAcc &a)
-{
-    const float h = __fadd_rn(a.s, a.c);
-    const float l = __fsub_rn(a.c, __fsub_rn(h, a.s));
-    return df_join(h, l);
-}
-
-// out = sum_c m[c] v[c] (complex) over the row's NC entries
-template <int NC>
-__device__ __forceinline__ double2 df_row(const float4 *m, const DfC *v)
-{
-    DfAcc re = df_first(m[0].x, m[0].y, v[0].rh, v[0].rl);
-    df_add_prod(re, -m[0].z, -m[0].w, v[0].ih, v[0].il);
-    DfAcc im = df_first(m[0].x, m[0].y, v[0].ih, v[0].il);
-    df_add_prod(im, m[0].z, m[0].w, v[0].rh, v[0].rl);
-#pragma unroll
-    for (int c = 1; c < NC; ++c) {
-        df_add_prod(re, m[c].x, m[c].y, v[c].rh, v[c].rl);
-        df_add_prod(re, -m[c].z, -m[c].w, v[c].ih, v[c].il);
-        df_add_prod(im, m[c].x, m[c].y, v[c].ih, v[c].il);
-        df_add_prod(im, m[c].z, m[c].w, v[c].rh, v[c].rl);
-    }
-    return make_double2(df_finish(re), df_finish(im));
-}
 
 // ---------------------------------------------------------------------------
 // tiles: two buffers per CTA, the next tile's copy in flight
@@ -214,11 +92,11 @@ __device__ __forceinline__ void df_gather_item(const DfMat<K> &m, const double2 
                                                double2 *out)
 {
     constexpr int D = 1 << K, NR = df_rows<K>();
-    DfC v[D];
+    df::C v[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) v[c] = df_load(tile[swz<double>(ib + g.toff[c])]);
+    for (int c = 0; c < D; ++c) v[c] = df::load(tile[swz<double>(ib + g.toff[c])]);
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr) out[rr] = df_row<D>(m.a[R0 + rr], v);
+    for (int rr = 0; rr < NR; ++rr) out[rr] = df::row_d<D>(m.a[R0 + rr], v);
 }
 
 template <int K>
@@ -294,8 +172,8 @@ __global__ void __launch_bounds__(kDfThreads) k_mono_df(const TileGeom g, const 
             double2 out[1 << K];
 #pragma unroll
             for (int r = 0; r < (1 << K); ++r) {
-                const DfC v = df_load(tile[swz<double>(ib + m.src[r])]);
-                out[r] = df_row<1>(&m.d[r], &v);
+                const df::C v = df::load(tile[swz<double>(ib + m.src[r])]);
+                out[r] = df::row_d<1>(&m.d[r], &v);
             }
 #pragma unroll
             for (int r = 0; r < (1 << K); ++r) tile[swz<double>(ib + g.toff[r])] = out[r];
@@ -323,8 +201,8 @@ __global__ void __launch_bounds__(kDfThreads) k_diag_df(const DfDiag<K> p, doubl
         int r = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j) r |= int((x >> p.b[j]) & 1) << (K - 1 - j);
-        const DfC v = df_load(state[x]);
-        state[x] = df_row<1>(&d[r], &v);
+        const df::C v = df::load(state[x]);
+        state[x] = df::row_d<1>(&d[r], &v);
     }
 }
 
