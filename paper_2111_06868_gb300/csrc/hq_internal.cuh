@@ -250,6 +250,9 @@ hq_status pass_error_status();
 // HQ_ERR_TIMEOUT (and the flag cleared) if a batch run's scheduler gave up
 // (k_batch.cu); device_error_status() checks it too.
 hq_status batch_error_status();
+// HQ_ERR_TIMEOUT (and the flag cleared) if a staged expectation pass gave up
+// a bounded wait (k_expect_reg.cu); device_error_status() checks it too.
+hq_status expect_error_status();
 
 // validation helpers (hq_api.cu)
 hq_status check_qubits(int n, int k, const int *qubits, int kmax);

@@ -51,41 +51,6 @@ __host__ __device__ constexpr size_t el_smem_bytes()
            sizeof(R) * (size_t(1) << ElShape<R>::RB) * kElThreads;
 }
 
-// pair sums of register bit I: Re (and Im when needed) of conj(a_j) a_{j|2^I}
-template <typename R, int I, int E>
-__device__ __forceinline__ void el_pair_sums(const typename C2<R>::type *a, bool need_re, bool need_im, R &sre, R &sim)
-{
-    sre = 0;
-    sim = 0;
-    if (need_re) {
-        R q[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int v = 0; v < E / 2; ++v) {
-            const int j = ((v >> I) << (I + 1)) | (v & ((1 << I) - 1));
-            q[v & 3] += a[j].x * a[j | (1 << I)].x + a[j].y * a[j | (1 << I)].y;
-        }
-        sre = (q[0] + q[1]) + (q[2] + q[3]);
-    }
-    if (need_im) {
-        R q[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int v = 0; v < E / 2; ++v) {
-            const int j = ((v >> I) << (I + 1)) | (v & ((1 << I) - 1));
-            q[v & 3] += a[j].x * a[j | (1 << I)].y - a[j].y * a[j | (1 << I)].x;
-        }
-        sim = (q[0] + q[1]) + (q[2] + q[3]);
-    }
-}
-
-template <typename R, int RB, int I = 0>
-__device__ __forceinline__ void el_all_pairs(const typename C2<R>::type *a, const int *need, R *sre, R *sim)
-{
-    if constexpr (I < RB) {
-        el_pair_sums<R, I, (1 << RB)>(a, need[I] & 1, need[I] & 2, sre[I], sim[I]);
-        el_all_pairs<R, RB, I + 1>(a, need, sre, sim);
-    }
-}
-
 template <typename R>
 __global__ void __launch_bounds__(kElThreads, ElShape<R>::MIN_BLOCKS) k_expect_low(const ElParams p,
                                                               const typename C2<R>::type *__restrict__ psi,
@@ -97,45 +62,34 @@ __global__ void __launch_bounds__(kElThreads, ElShape<R>::MIN_BLOCKS) k_expect_l
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     V *ubuf = reinterpret_cast<V *>(smem_raw) + (size_t(warp) << UB);
     R(*s_w)[kElThreads] = reinterpret_cast<R(*)[kElThreads]>(smem_raw + size_t(kElWarps) * (sizeof(V) << UB));
-    __shared__ ElTerm s_term[kElMaxTerms];
-    __shared__ R s_wt[kElMaxTerms];
-    __shared__ int s_need[2][kElMaxBits];
+    __shared__ ExT<R> s_t[kElMaxTerms];
+    __shared__ int s_rg[2][kElMaxBits][3];
     for (int t = threadIdx.x; t < p.nt; t += blockDim.x) {
-        s_term[t] = p.term[t];
-        s_wt[t] = R(p.term[t].w);
+        const ElTerm &tm = p.term[t];
+        s_t[t] = ExT<R>{R(tm.w), tm.zc, tm.h};
     }
-    if (threadIdx.x < 2 * kElMaxBits) s_need[threadIdx.x / kElMaxBits][threadIdx.x % kElMaxBits] =
-        p.need[threadIdx.x / kElMaxBits][threadIdx.x % kElMaxBits];
+    if (threadIdx.x < 2 * kElMaxBits * 3) (&s_rg[0][0][0])[threadIdx.x] = (&p.rg[0][0][0])[threadIdx.x];
     __syncthreads();
-    // this lane's part of every term's sign (Z on the lane bits of its layout)
-    uint32_t ls[3] = {0u, 0u, 0u};
-    for (int t = 0; t < p.nt; ++t)
-        if (__popc(uint32_t(lane) & p.term[t].zlane) & 1) {
-            if (t < 32) ls[0] |= 1u << t;
-            else if (t < 64) ls[1] |= 1u << (t - 32);
-            else ls[2] |= 1u << (t - 64);
-        }
-    const uint32_t ls0 = ls[0], ls1 = ls[1], ls2 = ls[2];
+    const int nd = p.nd;
+    const bool any_a = s_rg[0][RB - 1][2] > s_rg[0][0][0], any_b = s_rg[1][RB - 1][2] > s_rg[1][0][0];
     const int64_t units = int64_t(1) << (p.n - UB);
     const int64_t warps = int64_t(gridDim.x) * kElWarps;
     double acc = 0;
     R accr = 0, comp = 0;
     for (int64_t u = int64_t(blockIdx.x) * kElWarps + warp; u < units; u += warps) {
-        const int64_t base = u << UB;
         V a[E];
-        const V *src = psi + base + lane;
+        const V *src = psi + (u << UB) + lane;
 #pragma unroll
-        for (int j = 0; j < E; ++j) a[j] = __ldcs(src + 32 * j);
+        for (int j = 0; j < E; ++j) a[j] = ex_ld(src + 32 * j);
+        // sign argument of every term: the unit index above the lane index
+        // (n <= 37, so it fits 32 bits)
+        const uint32_t ul = (uint32_t(u) << 5) | uint32_t(lane);
         R part = 0;
-        auto term_sign = [&](int t) -> bool {
-            const uint32_t w = t < 32 ? ls0 : (t < 64 ? ls1 : ls2);
-            return (((w >> (t & 31)) & 1u) + (__popcll(uint64_t(base) & s_term[t].zunit) & 1u)) & 1u;
-        };
         // diagonal strings: Walsh-Hadamard transform of |a|^2 over the register bits
-        if (p.nd > 0) {
+        if (nd > 0) {
             R W[E];
 #pragma unroll
-            for (int j = 0; j < E; ++j) W[j] = a[j].x * a[j].x + a[j].y * a[j].y;
+            for (int j = 0; j < E; ++j) W[j] = fma(a[j].x, a[j].x, a[j].y * a[j].y);
 #pragma unroll
             for (int s = 1; s < E; s <<= 1)
 #pragma unroll
@@ -147,27 +101,16 @@ __global__ void __launch_bounds__(kElThreads, ElShape<R>::MIN_BLOCKS) k_expect_l
                     }
 #pragma unroll
             for (int j = 0; j < E; ++j) s_w[j][threadIdx.x] = W[j];
-            for (int t = 0; t < p.nd; ++t) {
-                const R v = s_w[s_term[t].h][threadIdx.x] * s_wt[t];
-                part += term_sign(t) ? -v : v;
+#pragma unroll 4
+            for (int t = 0; t < nd; ++t) {
+                const ExT<R> e = s_t[t];
+                part = fma(ex_flip(e.w, __popc(ul & e.zc)), s_w[e.h][threadIdx.x], part);
             }
         }
-        // one X bit among the register bits (layout A)
-        if (p.na > 0) {
-            R sre[RB], sim[RB];
-            el_all_pairs<R, RB>(a, s_need[0], sre, sim);
-            for (int t = p.nd; t < p.nd + p.na; ++t) {
-                const ElTerm &tm = s_term[t];
-                R S = 0;
-#pragma unroll
-                for (int i = 0; i < RB; ++i)
-                    if (tm.h == i) S = tm.imag ? sim[i] : sre[i];
-                const R v = s_wt[t] * S;
-                part += term_sign(t) ? -v : v;
-            }
-        }
-        // one X bit among flat bits 0..4 (layout B, after the transpose)
-        if (p.nb > 0) {
+        // one X bit among the register bits (layout A: lanes = flat bits 0..4)
+        if (any_a) ex_x_terms<R, RB>(a, s_rg[0], s_t, ul, part);
+        // one X bit among flat bits 0..4 (layout B, after the transpose: lanes = flat bits 5..9)
+        if (any_b) {
             __syncwarp();
 #pragma unroll
             for (int j = 0; j < E; ++j) {
@@ -175,24 +118,13 @@ __global__ void __launch_bounds__(kElThreads, ElShape<R>::MIN_BLOCKS) k_expect_l
                 ubuf[e ^ ((e >> 5) & 31)] = a[j];
             }
             __syncwarp();
-            // lane l now takes e = 32 l' ... : register i' < 32 is flat bits 0..4,
-            // a sixth register bit (RB = 6) would be flat bit 10; the lane is flat bits 5..9
+            // lane l now takes e = 32 l + i': register i' is flat bits 0..4, the lane flat bits 5..9
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 const int e = ((j >> 5) << 10) | (lane << 5) | (j & 31);
                 a[j] = ubuf[e ^ ((e >> 5) & 31)];
             }
-            R sre[RB], sim[RB];
-            el_all_pairs<R, RB>(a, s_need[1], sre, sim);
-            for (int t = p.nd + p.na; t < p.nt; ++t) {
-                const ElTerm &tm = s_term[t];
-                R S = 0;
-#pragma unroll
-                for (int i = 0; i < RB; ++i)
-                    if (tm.h == i) S = tm.imag ? sim[i] : sre[i];
-                const R v = s_wt[t] * S;
-                part += term_sign(t) ? -v : v;
-            }
+            ex_x_terms<R, RB>(a, s_rg[1], s_t, ul, part);
         }
         if constexpr (sizeof(R) == 4) {
             const R y = part - comp, s2 = accr + y;
@@ -212,73 +144,84 @@ __global__ void __launch_bounds__(kElThreads, ElShape<R>::MIN_BLOCKS) k_expect_l
 int expect_low_bits(hq_dtype dt) { return 5 + (dt == HQ_C64 ? ElShape<float>::RB : ElShape<double>::RB); }
 
 // layout A: lanes = flat bits 0..4, registers = bits 5..4+RB;
-// layout B: registers = bits 0..4 (+ bit 10 as register bit 5 for RB = 6),
-// lanes = bits 5..9
+// layout B: registers = bits 0..4, lanes = bits 5..9
 bool plan_expect_low(int n, hq_dtype dt, const std::vector<EvInRegTerm> &in, ElParams &p, std::vector<int> &taken)
 {
     const int RB = dt == HQ_C64 ? ElShape<float>::RB : ElShape<double>::RB;
     const int UB = 5 + RB;
     std::memset(&p, 0, sizeof(p));
     taken.assign(in.size(), 0);
-    if (n < UB) return false;
+    // the kernel forms signs from (unit index << 5 | lane) in 32 bits
+    if (n < UB || n - UB + 5 > 32) return false;
     p.n = n;
-    auto regA = [&](int b) { return b >= 5 && b < UB ? b - 5 : -1; };      // register index in layout A
-    auto regB = [&](int b) { return b < 5 ? b : (RB == 6 && b == 10 ? 5 : -1); };
-    const uint64_t lowA = 31, lowB = uint64_t(31) << 5;                   // lane bits
+    const uint64_t lowA = 31, lowB = uint64_t(31) << 5;  // lane bits of layouts A and B
     const uint64_t regmaskA = ((uint64_t(1) << UB) - 1) & ~lowA;
-    const uint64_t regmaskB = 31 | (RB == 6 ? uint64_t(1) << 10 : 0);
-    const uint64_t unit = ~((uint64_t(1) << UB) - 1);
-    std::vector<ElTerm> d, a, b;
+    const uint64_t regmaskB = 31;
+    struct X {
+        double w;
+        uint32_t zc;
+    };
+    std::vector<ElTerm> d;
+    std::vector<X> xs[2][kElMaxBits][2];  // layout, register bit, Re / Im
+    int count = 0;
     for (size_t t = 0; t < in.size(); ++t) {
-        if (d.size() + a.size() + b.size() >= size_t(kElMaxTerms)) break;  // the rest: other passes
+        if (count >= kElMaxTerms) break;  // the rest: other passes
         const EvInRegTerm &it = in[t];
-        ElTerm tm;
-        std::memset(&tm, 0, sizeof(tm));
-        tm.zunit = it.zm & unit;
+        const uint32_t zu = uint32_t(it.zm >> UB);
         if (it.xm == 0) {
+            ElTerm tm;
+            std::memset(&tm, 0, sizeof(tm));
             tm.w = it.wr;  // #Y = 0
-            int h = 0;
-            for (int bit = 5; bit < UB; ++bit)
-                if ((it.zm >> bit) & 1) h |= 1 << (bit - 5);
-            tm.h = h;
-            tm.zlane = uint32_t(it.zm & lowA);
+            tm.h = int((it.zm >> 5) & uint64_t((1 << RB) - 1));
+            tm.zc = (zu << 5) | uint32_t(it.zm & lowA);
             d.push_back(tm);
             taken[t] = 1;
+            ++count;
             continue;
         }
         if (__builtin_popcountll(it.xm) != 1) continue;
         const int xb = __builtin_ctzll(it.xm);
-        tm.imag = it.wi != 0.0;
-        tm.w = tm.imag ? -2.0 * it.wi : 2.0 * it.wr;
-        if (regA(xb) >= 0) {
+        const bool imag = it.wi != 0.0;
+        const double w = imag ? -2.0 * it.wi : 2.0 * it.wr;
+        int layout, h;
+        uint32_t zlane;
+        if (xb >= 5 && xb < UB) {
             if (it.zm & regmaskA & ~it.xm) continue;  // Z on another register bit of layout A
-            tm.h = regA(xb);
-            tm.zlane = uint32_t(it.zm & lowA);
-            a.push_back(tm);
-            taken[t] = 1;
-        } else if (regB(xb) >= 0) {
+            layout = 0;
+            h = xb - 5;
+            zlane = uint32_t(it.zm & lowA);
+        } else if (xb < 5) {
             if (it.zm & regmaskB & ~it.xm) continue;  // Z on another register bit of layout B
-            tm.h = regB(xb);
-            tm.zlane = uint32_t((it.zm & lowB) >> 5);
-            b.push_back(tm);
-            taken[t] = 1;
+            layout = 1;
+            h = xb;
+            zlane = uint32_t((it.zm & lowB) >> 5);
+        } else {
+            continue;
         }
+        xs[layout][h][imag ? 1 : 0].push_back({w, (zu << 5) | zlane});
+        taken[t] = 1;
+        ++count;
     }
-    p.nd = int(d.size());
-    p.na = int(a.size());
-    p.nb = int(b.size());
-    p.nt = p.nd + p.na + p.nb;
-    if (p.nt == 0) return false;
+    if (count == 0) return false;
     int k = 0;
     for (const ElTerm &tm : d) p.term[k++] = tm;
-    for (const ElTerm &tm : a) {
-        p.need[0][tm.h] |= tm.imag ? 2 : 1;
-        p.term[k++] = tm;
-    }
-    for (const ElTerm &tm : b) {
-        p.need[1][tm.h] |= tm.imag ? 2 : 1;
-        p.term[k++] = tm;
-    }
+    p.nd = k;
+    for (int L = 0; L < 2; ++L)
+        for (int h = 0; h < kElMaxBits; ++h) {
+            p.rg[L][h][0] = k;
+            for (int im = 0; im < 2; ++im) {
+                for (const X &x : xs[L][h][im]) {
+                    ElTerm &tm = p.term[k++];
+                    std::memset(&tm, 0, sizeof(tm));
+                    tm.w = x.w;
+                    tm.zc = x.zc;
+                    tm.h = h;
+                }
+                if (im == 0) p.rg[L][h][1] = k;
+            }
+            p.rg[L][h][2] = k;
+        }
+    p.nt = k;
     return true;
 }
 

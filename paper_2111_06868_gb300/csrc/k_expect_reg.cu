@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "hq_expect_view.cuh"
+#include "hq_tcgen05.cuh"
 
 namespace hq {
 
@@ -33,28 +34,27 @@ constexpr int kErThreads = 256;
 // two CTAs (16 warps) per SM while the registers allow it
 template <typename R, int H> constexpr int er_min_blocks() { return H <= (sizeof(R) == 4 ? 5 : 4) ? 2 : 1; }
 
+// trailing zeros of g > 0, folded at compile time for unrolled loop indices
+__host__ __device__ constexpr int er_ctz(int g) { return (g & 1) ? 0 : 1 + er_ctz(g >> 1); }
+
 template <typename R, int H>
 __global__ void __launch_bounds__(kErThreads, er_min_blocks<R, H>()) k_expect_reg(const ErParams p,
                                                               const typename C2<R>::type *__restrict__ psi,
                                                               double *__restrict__ partials)
 {
     using V = typename C2<R>::type;
-    constexpr int E = 1 << H, NP = E / 2;
-    __shared__ int64_t s_off[E];  // flat offset of register slot j
-    __shared__ ErTerm s_term[kErMaxTerms];
-    __shared__ R s_w[kErMaxTerms];  // the weights in the state's precision (no FP64 conversion per unit)
-    for (int j = threadIdx.x; j < E; j += blockDim.x) {
-        int64_t o = 0;
-        for (int b = 0; b < H; ++b)
-            if ((j >> b) & 1) o += int64_t(1) << p.hb[b];
-        s_off[j] = o;
-    }
+    constexpr int E = 1 << H;
+    __shared__ ExT<R> s_t[kErMaxTerms];
+    __shared__ int s_rg[kErMaxBits][3];
     for (int t = threadIdx.x; t < p.nt; t += blockDim.x) {
-        s_term[t] = p.term[t];
-        s_w[t] = R(p.term[t].w);
+        const ErTerm &tm = p.term[t];
+        s_t[t] = ExT<R>{R(tm.w), tm.zc, tm.bit};
     }
+    if (threadIdx.x < kErMaxBits * 3) (&s_rg[0][0])[threadIdx.x] = (&p.rg[0][0])[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    // distance of the pass's bits, in elements: the loads walk the 2^H slots
+    // in Gray-code order, one pointer step each
     const int64_t warps = int64_t(gridDim.x) * (kErThreads / 32);
     const int64_t units = int64_t(1) << (p.n - 5 - H);
     // units per step: with few register bits a warp takes several units at
@@ -66,7 +66,6 @@ __global__ void __launch_bounds__(kErThreads, er_min_blocks<R, H>()) k_expect_re
     for (int64_t u0 = (int64_t(blockIdx.x) * (kErThreads / 32) + (threadIdx.x >> 5)) * U; u0 < units;
          u0 += warps * U) {
       V au[U][E];
-      int64_t xu[U];
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         const int64_t u = u0 + k;  // units is a power of two >= U whenever U > 1 units exist
@@ -78,53 +77,25 @@ __global__ void __launch_bounds__(kErThreads, er_min_blocks<R, H>()) k_expect_re
             x = ((x >> hb) << (hb + 1)) | (x & ((int64_t(1) << hb) - 1));
         }
         x |= lane;
-        xu[k] = x;
         if (u < units) {
-            const V *src = psi + x;
+            const V *ptr = psi + x;
+            au[k][0] = ex_ld(ptr);
 #pragma unroll
-            for (int j = 0; j < E; ++j) au[k][j] = __ldcs(src + s_off[j]);
+            for (int g = 1; g < E; ++g) {
+                const int b = er_ctz(g), j = g ^ (g >> 1);
+                const int64_t d = int64_t(1) << p.hb[b];
+                ptr += ((j >> b) & 1) ? d : -d;
+                au[k][j] = ex_ld(ptr);
+            }
         }
       }
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         if (u0 + k >= units) break;
-        const V *a = au[k];
-        const int64_t x = xu[k];
-        // pair sums per register bit (four partial sums against long chains)
-        R sre[H], sim[H];
-#pragma unroll
-        for (int i = 0; i < H; ++i) {
-            sre[i] = 0;
-            sim[i] = 0;
-            if (p.need_re[i]) {
-                R q[4] = {0, 0, 0, 0};
-#pragma unroll
-                for (int v = 0; v < NP; ++v) {
-                    const int j = ((v >> i) << (i + 1)) | (v & ((1 << i) - 1));
-                    q[v & 3] += a[j].x * a[j | (1 << i)].x + a[j].y * a[j | (1 << i)].y;
-                }
-                sre[i] = (q[0] + q[1]) + (q[2] + q[3]);
-            }
-            if (p.need_im[i]) {
-                R q[4] = {0, 0, 0, 0};
-#pragma unroll
-                for (int v = 0; v < NP; ++v) {
-                    const int j = ((v >> i) << (i + 1)) | (v & ((1 << i) - 1));
-                    q[v & 3] += a[j].x * a[j | (1 << i)].y - a[j].y * a[j | (1 << i)].x;
-                }
-                sim[i] = (q[0] + q[1]) + (q[2] + q[3]);
-            }
-        }
+        // sign argument: the unit index above the lane index (n - H <= 32)
+        const uint32_t ul = (uint32_t(u0 + k) << 5) | uint32_t(lane);
         R part = 0;
-        for (int t = 0; t < p.nt; ++t) {
-            const ErTerm &tm = s_term[t];
-            R S = 0;
-#pragma unroll
-            for (int i = 0; i < H; ++i)
-                if (tm.bit == i) S = tm.imag ? sim[i] : sre[i];
-            const uint32_t sg = (__popc(uint32_t(lane) & tm.zlane) + __popcll(uint64_t(x) & tm.zrest)) & 1u;
-            part += sg ? -s_w[t] * S : s_w[t] * S;
-        }
+        ex_x_terms<R, H>(au[k], s_rg, s_t, ul, part);
         if constexpr (sizeof(R) == 4) {
             const R y = part - comp, s2 = accr + y;
             comp = (s2 - accr) - y;
@@ -137,6 +108,151 @@ __global__ void __launch_bounds__(kErThreads, er_min_blocks<R, H>()) k_expect_re
     if constexpr (sizeof(R) == 4) acc = double(accr) - double(comp);
     const double s = block_sum(acc);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// ----------------------------------------------------------------------------
+// staged variant: the runs come into a ring of shared-memory stages by bulk
+// copies, so the bytes in flight per SM do not depend on registers
+// ----------------------------------------------------------------------------
+__device__ unsigned int g_expect_error;  // bit 0: a bounded wait ran out
+
+constexpr int er_clamp(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+constexpr int er_log2(int v) { return v <= 1 ? 0 : 1 + er_log2(v >> 1); }
+
+template <typename R, int H> struct ErStage {
+    static constexpr int E = 1 << H;
+    static constexpr int VB = int(sizeof(typename C2<R>::type));
+    // consumer warps: a stage of E runs of 32 NW amplitudes comes to about 64 KB
+    static constexpr int NW = er_clamp(65536 / (E * 32 * VB), 1, 8);
+    static constexpr int LW = er_log2(NW);
+    static constexpr int RUN = 32 * NW;  // amplitudes per run
+    static constexpr int STAGE_BYTES = E * RUN * VB;
+    static constexpr int S = er_clamp(196608 / STAGE_BYTES, 2, 8);
+    static constexpr int THREADS = 32 * (NW + 1);
+};
+
+// One CTA per SM.  The super-unit v (the bits outside the run bits 0..4+LW
+// and the pass's bits) fills one stage: E runs, one per slot j, each of RUN
+// contiguous amplitudes.  Warp NW issues the bulk copies; consumer warp w
+// takes amplitudes 32 w + lane of every run into registers, releases the
+// stage and pairs its registers as in k_expect_reg.  Every wait is bounded:
+// on expiry bit 0 of g_expect_error is set and the CTA stops early, after
+// waiting (bounded again) for the copies it issued.
+template <typename R, int H>
+__global__ void __launch_bounds__(ErStage<R, H>::THREADS, 1) k_expect_reg_staged(const ErParams p,
+                                                                   const typename C2<R>::type *__restrict__ psi,
+                                                                   double *__restrict__ partials)
+{
+    using V = typename C2<R>::type;
+    using St = ErStage<R, H>;
+    constexpr int E = St::E, NW = St::NW, LW = St::LW, RUN = St::RUN, S = St::S;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    V *stage = reinterpret_cast<V *>(smem_raw);  // [S][E][RUN]
+    __shared__ __align__(8) uint64_t full[S], empty[S];
+    __shared__ ExT<R> s_t[kErMaxTerms];
+    __shared__ int s_rg[kErMaxBits][3];
+    __shared__ int s_abort;
+    for (int t = threadIdx.x; t < p.nt; t += blockDim.x) {
+        const ErTerm &tm = p.term[t];
+        s_t[t] = ExT<R>{R(tm.w), tm.zc, tm.bit};
+    }
+    if (threadIdx.x < kErMaxBits * 3) (&s_rg[0][0])[threadIdx.x] = (&p.rg[0][0])[threadIdx.x];
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < S; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], NW);
+        }
+        s_abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t nsu = int64_t(1) << (p.n - 5 - LW - H);
+    const int64_t m = int64_t(blockIdx.x) < nsu ? (nsu - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    double acc = 0;
+    R accr = 0, comp = 0;
+    if (warp == NW) {
+        int64_t issued = 0;
+        for (int64_t i = 0; i < m; ++i) {
+            const int k = int(i % S);
+            if (i >= S && !mbar_wait(&empty[k], uint32_t((i / S) - 1) & 1u, &s_abort, &g_expect_error)) break;
+            const int64_t v = int64_t(blockIdx.x) + i * gridDim.x;
+            int64_t x = v << (5 + LW);
+#pragma unroll
+            for (int b = 0; b < H; ++b) {
+                const int hb = p.hb[b];
+                x = ((x >> hb) << (hb + 1)) | (x & ((int64_t(1) << hb) - 1));
+            }
+            if (lane == 0) mbar_expect_tx(&full[k], uint32_t(St::STAGE_BYTES));
+            __syncwarp();
+            for (int j = lane; j < E; j += 32) {
+                int64_t off = 0;
+#pragma unroll
+                for (int b = 0; b < H; ++b)
+                    if ((j >> b) & 1) off += int64_t(1) << p.hb[b];
+                bulk_g2s(smem_u32(stage + (size_t(k) * E + j) * RUN), psi + x + off, uint32_t(RUN * St::VB),
+                         &full[k]);
+            }
+            issued = i + 1;
+        }
+        // after an abort, wait (bounded) for the last copy issued into each stage
+        if (s_abort && lane == 0) {
+            for (int64_t i = issued - 1; i >= 0 && i >= issued - S; --i) {
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(&full[i % S], uint32_t(i / S) & 1u))
+                    if (globaltimer() - t0 > kWaitNs) break;
+            }
+        }
+    } else {
+        for (int64_t i = 0; i < m; ++i) {
+            const int k = int(i % S);
+            if (!mbar_wait(&full[k], uint32_t(i / S) & 1u, &s_abort, &g_expect_error)) break;
+            V a[E];
+            const V *src = stage + size_t(k) * E * RUN + 32 * warp + lane;
+#pragma unroll
+            for (int j = 0; j < E; ++j) a[j] = src[size_t(j) * RUN];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[k]);  // release: the reads above come first
+            const int64_t v = int64_t(blockIdx.x) + i * gridDim.x;
+            // sign argument: the unit index (v, warp) above the lane index
+            const uint32_t ul = (uint32_t((v << LW) | warp) << 5) | uint32_t(lane);
+            R part = 0;
+            ex_x_terms<R, H>(a, s_rg, s_t, ul, part);
+            if constexpr (sizeof(R) == 4) {
+                const R y = part - comp, s2 = accr + y;
+                comp = (s2 - accr) - y;
+                accr = s2;
+            } else {
+                acc += part;
+            }
+        }
+    }
+    if constexpr (sizeof(R) == 4) acc = double(accr) - double(comp);
+    const double sum = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
+template <typename R, int H> bool staged_fits(const ErParams &p)
+{
+    using St = ErStage<R, H>;
+    return p.hb[0] >= 5 + St::LW && p.n >= 5 + St::LW + H;
+}
+
+template <typename R, int H>
+hq_status launch_staged_h(const void *state, const ErParams &p, int grid, double *partials, cudaStream_t s)
+{
+    using St = ErStage<R, H>;
+    const size_t smem = size_t(St::S) * St::STAGE_BYTES;
+    static bool attr = false;  // one device per process
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute((const void *)k_expect_reg_staged<R, H>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return cuda_status("k_expect_reg_staged smem", e);
+        attr = true;
+    }
+    const int g = std::min(grid, sm_count());
+    k_expect_reg_staged<R, H><<<g, St::THREADS, smem, s>>>(p, (const typename C2<R>::type *)state, partials);
+    return cuda_status("k_expect_reg_staged", cudaGetLastError());
 }
 
 template <typename R, int H>
@@ -153,38 +269,63 @@ int expect_reg_max_bits(hq_dtype dt) { return dt == HQ_C64 ? 6 : 5; }
 
 bool plan_expect_reg(int n, int H, const int *high_bits, const std::vector<EvInRegTerm> &in, ErParams &p)
 {
-    if (H < 1 || H > kErMaxBits || n < 5 + H || int(in.size()) > kErMaxTerms) return false;
+    // the kernel forms signs from (unit index << 5 | lane) in 32 bits
+    if (H < 1 || H > kErMaxBits || n < 5 + H || n - H > 32 || int(in.size()) > kErMaxTerms) return false;
     std::memset(&p, 0, sizeof(p));
     p.n = n;
     p.H = H;
+    uint64_t hmask = 0;
     for (int i = 0; i < H; ++i) {
         p.hb[i] = high_bits[i];
-        if (high_bits[i] < 5 || (i > 0 && high_bits[i] <= high_bits[i - 1])) return false;
+        if (high_bits[i] < 5 || high_bits[i] >= n || (i > 0 && high_bits[i] <= high_bits[i - 1])) return false;
+        hmask |= uint64_t(1) << high_bits[i];
     }
-    p.nt = int(in.size());
-    for (int t = 0; t < p.nt; ++t) {
-        const EvInRegTerm &it = in[t];
-        ErTerm &tm = p.term[t];
+    struct X {
+        double w;
+        uint32_t zc;
+    };
+    std::vector<X> xs[kErMaxBits][2];  // pass bit, Re / Im
+    for (const EvInRegTerm &it : in) {
         int bit = -1;
         for (int i = 0; i < H; ++i)
             if (it.xm == (uint64_t(1) << p.hb[i])) bit = i;
         if (bit < 0) return false;
-        tm.bit = bit;
-        tm.imag = it.wi != 0.0;
-        tm.w = tm.imag ? -2.0 * it.wi : 2.0 * it.wr;
-        tm.zlane = uint32_t(it.zm & 31u);
-        uint64_t zreg = 0, hmask = 0;
-        for (int i = 0; i < H; ++i) {
-            hmask |= uint64_t(1) << p.hb[i];
-            if ((it.zm >> p.hb[i]) & 1) zreg |= uint64_t(1) << i;
+        if (it.zm & hmask & ~it.xm) return false;  // Z on another bit of the pass: not taken here
+        const bool imag = it.wi != 0.0;
+        // Z on the unit's bits (flat bits >= 5 outside the pass), packed as the unit index packs them
+        uint32_t zu = 0;
+        for (int b = 5, k = 0; b < n; ++b) {
+            if ((hmask >> b) & 1) continue;
+            if ((it.zm >> b) & 1) zu |= uint32_t(1) << k;
+            ++k;
         }
-        zreg &= ~(uint64_t(1) << bit);  // a pair's first slot has the X bit clear
-        if (zreg) return false;          // Z on another bit of the pass: not taken here
-        tm.zrest = it.zm & ~hmask & ~uint64_t(31);
-        if (tm.imag) p.need_im[bit] = 1;
-        else p.need_re[bit] = 1;
+        xs[bit][imag ? 1 : 0].push_back({imag ? -2.0 * it.wi : 2.0 * it.wr, (zu << 5) | uint32_t(it.zm & 31u)});
     }
+    int k = 0;
+    for (int i = 0; i < H; ++i) {
+        p.rg[i][0] = k;
+        for (int im = 0; im < 2; ++im) {
+            for (const X &x : xs[i][im]) p.term[k++] = ErTerm{x.w, x.zc, i};
+            if (im == 0) p.rg[i][1] = k;
+        }
+        p.rg[i][2] = k;
+    }
+    p.nt = k;
     return true;
+}
+
+hq_status expect_error_status()
+{
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_expect_error, sizeof(v));
+    if (e != cudaSuccess) return cuda_status("read expectation error flag", e);
+    if (v) {
+        const unsigned int zero = 0;
+        e = cudaMemcpyToSymbol(g_expect_error, &zero, sizeof(zero));
+        if (e != cudaSuccess) return cuda_status("clear expectation error flag", e);
+        return HQ_ERR_TIMEOUT;
+    }
+    return HQ_OK;
 }
 
 hq_status launch_expect_reg(const void *state, hq_dtype dt, const ErParams &p, int grid, double *partials,
@@ -195,17 +336,27 @@ hq_status launch_expect_reg(const void *state, hq_dtype dt, const ErParams &p, i
         case 1: return launch_reg_h<float, 1>(state, p, grid, partials, s);
         case 2: return launch_reg_h<float, 2>(state, p, grid, partials, s);
         case 3: return launch_reg_h<float, 3>(state, p, grid, partials, s);
-        case 4: return launch_reg_h<float, 4>(state, p, grid, partials, s);
-        case 5: return launch_reg_h<float, 5>(state, p, grid, partials, s);
-        case 6: return launch_reg_h<float, 6>(state, p, grid, partials, s);
+        case 4:
+            if (staged_fits<float, 4>(p)) return launch_staged_h<float, 4>(state, p, grid, partials, s);
+            return launch_reg_h<float, 4>(state, p, grid, partials, s);
+        case 5:
+            if (staged_fits<float, 5>(p)) return launch_staged_h<float, 5>(state, p, grid, partials, s);
+            return launch_reg_h<float, 5>(state, p, grid, partials, s);
+        case 6:
+            if (staged_fits<float, 6>(p)) return launch_staged_h<float, 6>(state, p, grid, partials, s);
+            return launch_reg_h<float, 6>(state, p, grid, partials, s);
         }
     } else {
         switch (p.H) {
         case 1: return launch_reg_h<double, 1>(state, p, grid, partials, s);
         case 2: return launch_reg_h<double, 2>(state, p, grid, partials, s);
         case 3: return launch_reg_h<double, 3>(state, p, grid, partials, s);
-        case 4: return launch_reg_h<double, 4>(state, p, grid, partials, s);
-        case 5: return launch_reg_h<double, 5>(state, p, grid, partials, s);
+        case 4:
+            if (staged_fits<double, 4>(p)) return launch_staged_h<double, 4>(state, p, grid, partials, s);
+            return launch_reg_h<double, 4>(state, p, grid, partials, s);
+        case 5:
+            if (staged_fits<double, 5>(p)) return launch_staged_h<double, 5>(state, p, grid, partials, s);
+            return launch_reg_h<double, 5>(state, p, grid, partials, s);
         }
     }
     return HQ_ERR_ARG;

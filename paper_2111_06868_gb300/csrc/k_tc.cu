@@ -827,6 +827,8 @@ hq_status device_error_status()
     if (ps != HQ_OK) return ps;
     const hq_status bs = batch_error_status();
     if (bs != HQ_OK) return bs;
+    const hq_status es = expect_error_status();
+    if (es != HQ_OK) return es;
     unsigned int v = 0;
     cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_error, sizeof(v));
     if (e != cudaSuccess) return cuda_status("read device error flag", e);
