@@ -87,24 +87,50 @@ __global__ void __launch_bounds__(kElThreads, ElShape<R>::MIN_BLOCKS) k_expect_l
         R part = 0;
         // diagonal strings: Walsh-Hadamard transform of |a|^2 over the register bits
         if (nd > 0) {
-            R W[E];
+            if constexpr (sizeof(R) == 4) {
+                // packed: Wp[i] = (W[2i], W[2i+1]); stages above the first pair whole float2s
+                float2 Wp[E / 2];
 #pragma unroll
-            for (int j = 0; j < E; ++j) W[j] = fma(a[j].x, a[j].x, a[j].y * a[j].y);
+                for (int i = 0; i < E / 2; ++i) {
+                    const float x = fma(a[2 * i].x, a[2 * i].x, a[2 * i].y * a[2 * i].y);
+                    const float y = fma(a[2 * i + 1].x, a[2 * i + 1].x, a[2 * i + 1].y * a[2 * i + 1].y);
+                    Wp[i] = make_float2(x + y, x - y);
+                }
 #pragma unroll
-            for (int s = 1; s < E; s <<= 1)
+                for (int t = 1; t < E / 2; t <<= 1)
 #pragma unroll
-                for (int j = 0; j < E; ++j)
-                    if (!(j & s)) {
-                        const R x = W[j], y = W[j | s];
-                        W[j] = x + y;
-                        W[j | s] = x - y;
-                    }
+                    for (int i = 0; i < E / 2; ++i)
+                        if (!(i & t)) {
+                            const float2 x = Wp[i], y = Wp[i | t];
+                            Wp[i] = ex_fadd2(x, y);
+                            Wp[i | t] = ex_fsub2(x, y);
+                        }
 #pragma unroll
-            for (int j = 0; j < E; ++j) s_w[j][threadIdx.x] = W[j];
+                for (int i = 0; i < E / 2; ++i) {
+                    s_w[2 * i][threadIdx.x] = Wp[i].x;
+                    s_w[2 * i + 1][threadIdx.x] = Wp[i].y;
+                }
+            } else {
+                R W[E];
+#pragma unroll
+                for (int j = 0; j < E; ++j) W[j] = fma(a[j].x, a[j].x, a[j].y * a[j].y);
+#pragma unroll
+                for (int s = 1; s < E; s <<= 1)
+#pragma unroll
+                    for (int j = 0; j < E; ++j)
+                        if (!(j & s)) {
+                            const R x = W[j], y = W[j | s];
+                            W[j] = x + y;
+                            W[j | s] = x - y;
+                        }
+#pragma unroll
+                for (int j = 0; j < E; ++j) s_w[j][threadIdx.x] = W[j];
+            }
+            const R *sw = &s_w[0][threadIdx.x];  // term h reads sw[h * kElThreads]
 #pragma unroll 4
             for (int t = 0; t < nd; ++t) {
                 const ExT<R> e = s_t[t];
-                part = fma(ex_flip(e.w, __popc(ul & e.zc)), s_w[e.h][threadIdx.x], part);
+                part = fma(ex_flip(e.w, __popc(ul & e.zc)), sw[e.h], part);
             }
         }
         // one X bit among the register bits (layout A: lanes = flat bits 0..4)
@@ -172,7 +198,7 @@ bool plan_expect_low(int n, hq_dtype dt, const std::vector<EvInRegTerm> &in, ElP
             ElTerm tm;
             std::memset(&tm, 0, sizeof(tm));
             tm.w = it.wr;  // #Y = 0
-            tm.h = int((it.zm >> 5) & uint64_t((1 << RB) - 1));
+            tm.h = int((it.zm >> 5) & uint64_t((1 << RB) - 1)) * kElThreads;  // offset of W[h] in s_w
             tm.zc = (zu << 5) | uint32_t(it.zm & lowA);
             d.push_back(tm);
             taken[t] = 1;

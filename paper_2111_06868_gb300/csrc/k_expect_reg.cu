@@ -122,20 +122,45 @@ constexpr int er_log2(int v) { return v <= 1 ? 0 : 1 + er_log2(v >> 1); }
 template <typename R, int H> struct ErStage {
     static constexpr int E = 1 << H;
     static constexpr int VB = int(sizeof(typename C2<R>::type));
-    // consumer warps: a stage of E runs of 32 NW amplitudes comes to about 64 KB
+    // columns of 32 amplitudes: a stage of E runs of 32 NW amplitudes comes to about 64 KB
     static constexpr int NW = er_clamp(65536 / (E * 32 * VB), 1, 8);
     static constexpr int LW = er_log2(NW);
-    static constexpr int RUN = 32 * NW;  // amplitudes per run
+    // with fewer than 8 columns, two warps share a column: each holds half the slots
+    static constexpr int SPLIT = NW < 8 ? 2 : 1;
+    static constexpr int CW = NW * SPLIT;  // consumer warps
+    static constexpr int RUN = 32 * NW;    // amplitudes per run
     static constexpr int STAGE_BYTES = E * RUN * VB;
     static constexpr int S = er_clamp(196608 / STAGE_BYTES, 2, 8);
-    static constexpr int THREADS = 32 * (NW + 1);
+    static constexpr int THREADS = 32 * (CW + 1);
 };
+
+// sum over j < N of Re(conj(lo_j) up_j) (IM: Im)
+template <int N, bool IM, typename V>
+__device__ __forceinline__ auto er_cross(const V *lo, const V *up) -> decltype(lo->x)
+{
+    using R = decltype(lo->x);
+    R q[2] = {0, 0};
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        if constexpr (IM) {
+            q[j & 1] = fma(lo[j].x, up[j].y, q[j & 1]);
+            q[j & 1] = fma(-lo[j].y, up[j].x, q[j & 1]);
+        } else {
+            q[j & 1] = fma(lo[j].x, up[j].x, q[j & 1]);
+            q[j & 1] = fma(lo[j].y, up[j].y, q[j & 1]);
+        }
+    }
+    return q[0] + q[1];
+}
 
 // One CTA per SM.  The super-unit v (the bits outside the run bits 0..4+LW
 // and the pass's bits) fills one stage: E runs, one per slot j, each of RUN
-// contiguous amplitudes.  Warp NW issues the bulk copies; consumer warp w
-// takes amplitudes 32 w + lane of every run into registers, releases the
-// stage and pairs its registers as in k_expect_reg.  Every wait is bounded:
+// contiguous amplitudes.  The last warp issues the bulk copies; consumer warp
+// w takes amplitudes 32 (w % NW) + lane of every run (SPLIT = 2: of the half
+// of the slots that w / NW selects) into registers, releases the stage and
+// pairs its registers as in k_expect_reg.  With SPLIT = 2 the pairs across
+// the halves (the pass's top bit) are split between the two warps, each
+// reading the partner half of its share from the stage.  Every wait is bounded:
 // on expiry bit 0 of g_expect_error is set and the CTA stops early, after
 // waiting (bounded again) for the copies it issued.
 template <typename R, int H>
@@ -145,7 +170,8 @@ __global__ void __launch_bounds__(ErStage<R, H>::THREADS, 1) k_expect_reg_staged
 {
     using V = typename C2<R>::type;
     using St = ErStage<R, H>;
-    constexpr int E = St::E, NW = St::NW, LW = St::LW, RUN = St::RUN, S = St::S;
+    constexpr int E = St::E, NW = St::NW, LW = St::LW, RUN = St::RUN, S = St::S, CW = St::CW;
+    constexpr int SPLIT = St::SPLIT, EL = E / SPLIT, HL = H - (SPLIT == 2 ? 1 : 0);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     V *stage = reinterpret_cast<V *>(smem_raw);  // [S][E][RUN]
     __shared__ __align__(8) uint64_t full[S], empty[S];
@@ -160,7 +186,7 @@ __global__ void __launch_bounds__(ErStage<R, H>::THREADS, 1) k_expect_reg_staged
     if (threadIdx.x == 0) {
         for (int k = 0; k < S; ++k) {
             mbar_init(&full[k], 1);
-            mbar_init(&empty[k], NW);
+            mbar_init(&empty[k], CW);
         }
         s_abort = 0;
         fence_mbar_init();
@@ -171,7 +197,7 @@ __global__ void __launch_bounds__(ErStage<R, H>::THREADS, 1) k_expect_reg_staged
     const int64_t m = int64_t(blockIdx.x) < nsu ? (nsu - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     double acc = 0;
     R accr = 0, comp = 0;
-    if (warp == NW) {
+    if (warp == CW) {
         int64_t issued = 0;
         for (int64_t i = 0; i < m; ++i) {
             const int k = int(i % S);
@@ -207,17 +233,39 @@ __global__ void __launch_bounds__(ErStage<R, H>::THREADS, 1) k_expect_reg_staged
         for (int64_t i = 0; i < m; ++i) {
             const int k = int(i % S);
             if (!mbar_wait(&full[k], uint32_t(i / S) & 1u, &s_abort, &g_expect_error)) break;
-            V a[E];
-            const V *src = stage + size_t(k) * E * RUN + 32 * warp + lane;
+            const int col = warp % NW, hf = warp / NW;
+            V a[EL];
+            const V *src = stage + size_t(k) * E * RUN + 32 * col + lane;
 #pragma unroll
-            for (int j = 0; j < E; ++j) a[j] = src[size_t(j) * RUN];
+            for (int j = 0; j < EL; ++j) a[j] = src[size_t(hf * EL + j) * RUN];
+            // SPLIT = 2: pairs (j, j + EL) of the top bit, j in [hf EL/2, (hf+1) EL/2): the
+            // partner half of each from the stage
+            V b[SPLIT == 2 ? EL / 2 : 1];
+            if constexpr (SPLIT == 2) {
+#pragma unroll
+                for (int j = 0; j < EL / 2; ++j) b[j] = src[size_t((1 - hf) * EL + hf * (EL / 2) + j) * RUN];
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[k]);  // release: the reads above come first
             const int64_t v = int64_t(blockIdx.x) + i * gridDim.x;
-            // sign argument: the unit index (v, warp) above the lane index
-            const uint32_t ul = (uint32_t((v << LW) | warp) << 5) | uint32_t(lane);
+            // sign argument: the unit index (v, column) above the lane index
+            const uint32_t ul = (uint32_t((v << LW) | col) << 5) | uint32_t(lane);
             R part = 0;
-            ex_x_terms<R, H>(a, s_rg, s_t, ul, part);
+            ex_x_terms<R, HL>(a, s_rg, s_t, ul, part);
+            if constexpr (SPLIT == 2) {
+                const int t0 = s_rg[HL][0], t1 = s_rg[HL][1], t2 = s_rg[HL][2];
+                // lower / upper elements of its pairs: (a, b) for hf = 0, (b, a + EL/2) for hf = 1
+                if (t1 > t0) {
+                    R c = 0;
+                    for (int t = t0; t < t1; ++t) c += ex_flip(s_t[t].w, __popc(ul & s_t[t].zc));
+                    part = fma(c, hf ? er_cross<EL / 2, false>(b, a + EL / 2) : er_cross<EL / 2, false>(a, b), part);
+                }
+                if (t2 > t1) {
+                    R c = 0;
+                    for (int t = t1; t < t2; ++t) c += ex_flip(s_t[t].w, __popc(ul & s_t[t].zc));
+                    part = fma(c, hf ? er_cross<EL / 2, true>(b, a + EL / 2) : er_cross<EL / 2, true>(a, b), part);
+                }
+            }
             if constexpr (sizeof(R) == 4) {
                 const R y = part - comp, s2 = accr + y;
                 comp = (s2 - accr) - y;
