@@ -10,6 +10,7 @@ namespace hq {
 constexpr int kApMaxHigh = 8;
 constexpr int kApMaxRot = 128;  // rotations per pass (one shared-memory accumulator each)
 constexpr int kApMaxOps = 96;   // ops per pass (complex64: their 2x2 matrices stay in shared memory)
+constexpr int kApRunBits = 3;   // register positions of a run (2^3 amplitudes per state and thread)
 
 // One gate of a pass, at tile positions tpos (qubits[0], qubits[1]).
 struct AOp {
@@ -30,6 +31,14 @@ struct AOp {
     // swax its axis, swdiag / swreal its 2x2 matrices diagonal / real (exact
     // zeros); swprod: their product is 0 general, 1 diagonal, 2 real
     int swrot, swax, swdiag, swreal, swprod;
+    // register run (complex64): ops [ru0, ru0 + run) of the pass, whole
+    // sweeps, go through registers together: a thread holds the 2^kApRunBits
+    // amplitudes that differ in the tile positions rq[] and applies every
+    // sweep of the run to them between one load and one store.  swj: the
+    // register index of this op's sweep position swt (-1: an all-diagonal
+    // sweep, applied elementwise).  run = 0: no run (dense two-qubit gate).
+    int ru0, run, swj;
+    int rq[4];
 };
 
 struct APass {

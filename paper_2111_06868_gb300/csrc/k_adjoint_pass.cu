@@ -161,9 +161,260 @@ __device__ __forceinline__ void adj_tile_out(const double2 *tile, double2 *dst, 
     for (int i = threadIdx.x; i < TS; i += blockDim.x) dst[base + (i & rmask) + hioff[i >> r]] = tile[swz<double>(i)];
 }
 
+// ----------------------------------------------------------------------------
+// register runs (complex64)
+// ----------------------------------------------------------------------------
+// p with a zero bit inserted at position j
+__host__ __device__ constexpr int run_ins0(int p, int j) { return ((p >> j) << (j + 1)) | (p & ((1 << j) - 1)); }
+
+// application order of a sweep's ops (reverse: the adjoints backwards) and
+// the kind of each applied matrix
+struct SweepMasks {
+    unsigned rot, diag, real;
+    unsigned ax;  // byte j: the axis of applied op j (rotations)
+};
+template <bool REV> __device__ __forceinline__ SweepMasks sweep_masks(const AOp &s, int len)
+{
+    SweepMasks m{0u, 0u, 0u, 0u};
+    const int nsw = REV ? len : 1;
+#pragma unroll
+    for (int j = 0; j < kSweepOps; ++j) {
+        if (j >= nsw) break;
+        if (REV) {
+            const int cj = len - 1 - j;  // op j applied = op cj of the sweep in circuit order
+            if ((s.swrot >> cj) & 1) {
+                m.rot |= 1u << j;
+                m.ax |= unsigned((s.swax >> (8 * cj)) & 255) << (8 * j);
+            }
+            if ((s.swdiag >> cj) & 1) m.diag |= 1u << j;
+            else if ((s.swreal >> cj) & 1) m.real |= 1u << j;
+        } else if (s.swprod == 1) {
+            m.diag |= 1u;
+        } else if (s.swprod == 2) {
+            m.real |= 1u;
+        }
+    }
+    return m;
+}
+
+// the two context matrices (cx = 0, 1) of applied op j at mt
+template <bool REV>
+__device__ __forceinline__ void run_mats(const float2 *mt, int j, float2 (&m0)[4], float2 (&m1)[4])
+{
+    const float4 *mv = reinterpret_cast<const float4 *>(mt - (REV ? 8 * j : 0));
+    const float4 a = mv[0], b = mv[1], c = mv[2], d = mv[3];
+    m0[0] = make_float2(a.x, a.y); m0[1] = make_float2(a.z, a.w);
+    m0[2] = make_float2(b.x, b.y); m0[3] = make_float2(b.z, b.w);
+    m1[0] = make_float2(c.x, c.y); m1[1] = make_float2(c.z, c.w);
+    m1[2] = make_float2(d.x, d.y); m1[3] = make_float2(d.z, d.w);
+}
+
+// Im<l|P x> over the pairs (r0, r0 | 2^JT) for the Pauli P of `axis`
+// (warp-uniform; one short loop per axis)
+template <int Q, int JT>
+__device__ __forceinline__ float run_pauli_im(int axis, const float2 (&x)[1 << Q], const float2 (&l)[1 << Q])
+{
+    float g = 0.f;
+    if (axis == 'X') {
+#pragma unroll
+        for (int p = 0; p < (1 << (Q - 1)); ++p) {
+            const int r0 = run_ins0(p, JT), r1 = r0 | (1 << JT);
+            g += (l[r0].x * x[r1].y - l[r0].y * x[r1].x) + (l[r1].x * x[r0].y - l[r1].y * x[r0].x);
+        }
+    } else if (axis == 'Y') {
+#pragma unroll
+        for (int p = 0; p < (1 << (Q - 1)); ++p) {
+            const int r0 = run_ins0(p, JT), r1 = r0 | (1 << JT);
+            g += (l[r1].x * x[r0].x + l[r1].y * x[r0].y) - (l[r0].x * x[r1].x + l[r0].y * x[r1].y);
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < (1 << (Q - 1)); ++p) {
+            const int r0 = run_ins0(p, JT), r1 = r0 | (1 << JT);
+            g += (l[r0].x * x[r0].y - l[r0].y * x[r0].x) - (l[r1].x * x[r1].y - l[r1].y * x[r1].x);
+        }
+    }
+    return g;
+}
+
+// warp total of g added to the rotation's FP64 accumulator
+__device__ __forceinline__ void run_grad(double *gacc, int slot, float g)
+{
+    for (int o = 16; o > 0; o >>= 1) g += __shfl_down_sync(0xffffffffu, g, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&gacc[slot], double(g));
+}
+
+// a pair sweep on register bit JT: pairs (r0, r0 | 2^JT); the context bit of
+// r0 (bit r0 of mc) picks the matrix.  Its ops in a loop (the code stays
+// small): reverse, each rotation's Im<l|P x> first, then the matrix.
+template <int Q, int JT, bool REV>
+__device__ __forceinline__ void run_pair_sweep(float2 (&x)[1 << Q], float2 (&l)[1 << Q], const AOp *pops, int f,
+                                               int len, const float2 *mt, const SweepMasks &sm, uint32_t mc,
+                                               double *gacc)
+{
+    const int nsw = REV ? len : 1;
+    // the context bit is one value for all of a thread's pairs unless it is
+    // one of the register positions (the same for every thread of the run)
+    const bool cvar = mc != 0u && mc != (1u << (1 << Q)) - 1u;
+#pragma unroll 1
+    for (int j = 0; j < nsw; ++j) {
+        if (REV && ((sm.rot >> j) & 1)) run_grad(gacc, pops[f + len - 1 - j].slot, run_pauli_im<Q, JT>(int((sm.ax >> (8 * j)) & 255u), x, l));
+        const float2 *mj = mt - (REV ? 8 * j : 0);
+        const bool dg = (sm.diag >> j) & 1;
+        if (!cvar) {
+            const float4 *mv = reinterpret_cast<const float4 *>(mj + (mc & 1u) * 4);
+            const float4 a = mv[0], b = mv[1];
+            const float2 mm[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                                  make_float2(b.z, b.w)};
+#pragma unroll
+            for (int p = 0; p < (1 << (Q - 1)); ++p) {
+                const int r0 = run_ins0(p, JT), r1 = r0 | (1 << JT);
+                if (dg) {
+                    x[r0] = cmul(mm[0], x[r0]);
+                    x[r1] = cmul(mm[3], x[r1]);
+                    if (REV) {
+                        l[r0] = cmul(mm[0], l[r0]);
+                        l[r1] = cmul(mm[3], l[r1]);
+                    }
+                } else {
+                    mul2(mm, x[r0], x[r1]);
+                    if (REV) mul2(mm, l[r0], l[r1]);
+                }
+            }
+        } else {
+            // per pair, the matrix of its context value (broadcast loads)
+#pragma unroll
+            for (int p = 0; p < (1 << (Q - 1)); ++p) {
+                const int r0 = run_ins0(p, JT), r1 = r0 | (1 << JT);
+                const float4 *mv = reinterpret_cast<const float4 *>(mj + ((mc >> r0) & 1u) * 4);
+                const float4 a = mv[0], b = mv[1];
+                const float2 mm[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                                      make_float2(b.z, b.w)};
+                mul2(mm, x[r0], x[r1]);
+                if (REV) mul2(mm, l[r0], l[r1]);
+            }
+        }
+    }
+}
+
+// an all-diagonal sweep, elementwise: element r takes the entry of context
+// bit (bit r of mc) and pair bit (bit r of mt_bits); its Z rotations' Im<l|Z x>
+// carries the sign of the pair bit
+template <int Q, bool REV>
+__device__ __forceinline__ void run_diag_sweep(float2 (&x)[1 << Q], float2 (&l)[1 << Q], const AOp *pops, int f,
+                                               int len, const float2 *mt, const SweepMasks &sm, uint32_t mc,
+                                               uint32_t mt_bits, double *gacc)
+{
+    const int nsw = REV ? len : 1;
+#pragma unroll 1
+    for (int j = 0; j < nsw; ++j) {
+        if (REV && ((sm.rot >> j) & 1)) {
+            float g = 0.f;
+#pragma unroll
+            for (int r = 0; r < (1 << Q); ++r) {
+                const float v = l[r].x * x[r].y - l[r].y * x[r].x;
+                g += ((mt_bits >> r) & 1u) ? -v : v;
+            }
+            run_grad(gacc, pops[f + len - 1 - j].slot, g);
+        }
+        float2 m0[4], m1[4];
+        run_mats<REV>(mt, j, m0, m1);
+#pragma unroll
+        for (int r = 0; r < (1 << Q); ++r) {
+            const bool cx = (mc >> r) & 1u, bt = (mt_bits >> r) & 1u;
+            const float2 e = cx ? (bt ? m1[3] : m1[0]) : (bt ? m0[3] : m0[0]);
+            x[r] = cmul(e, x[r]);
+            if (REV) l[r] = cmul(e, l[r]);
+        }
+    }
+}
+
+// One register run: ops [ru0, ru0 + run) of the pass (pops = its first op),
+// on the tiles tp (and tl) of 2^L amplitudes.  Each thread takes groups of
+// 2^Q amplitudes that differ in the run's register positions, applies every
+// sweep of the run in order (reverse: backwards) and stores them; rotation
+// gradients go to gacc per sweep as in the shared-memory sweeps.
+template <bool REV>
+__device__ __forceinline__ void adj_run(const AOp *__restrict__ pops, int ru0, int run, float2 *tp, float2 *tl,
+                                        int L, const float2 *mtab, double *gacc)
+{
+    constexpr int Q = kApRunBits, E = 1 << Q;
+    int rq[Q];  // ascending
+#pragma unroll
+    for (int j = 0; j < Q; ++j) rq[j] = pops[ru0].rq[j];
+    // the swizzle is linear over XOR: swz(base | bits) = swz(base) ^ swz(bits)
+    int sq[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) sq[j] = swz<float>(1 << rq[j]);
+    const int ng = 1 << (L - Q);
+    for (int g0 = 0; g0 < ng; g0 += blockDim.x) {
+        const int grp = g0 + int(threadIdx.x);
+        const bool act = grp < ng;
+        // the group's bits on the positions outside the register positions
+        int base = grp;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) base = run_ins0(base, rq[j]);
+        const int sb = swz<float>(base);
+        // shared-memory index of register element r (recomputed for the
+        // stores: the registers go to the amplitudes)
+        auto idx = [&](int r) {
+            int i = sb;
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+                if ((r >> j) & 1) i ^= sq[j];
+            return i;
+        };
+        float2 x[E], lv[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            x[r] = act ? tp[idx(r)] : make_float2(0.f, 0.f);
+            lv[r] = (REV && act) ? tl[idx(r)] : make_float2(0.f, 0.f);
+        }
+        // bit p of each register element, as an E-bit mask
+        auto pmask = [&](int p) -> uint32_t {
+            if (p < 0) return 0u;
+            uint32_t m = ((base >> p) & 1) ? (1u << E) - 1u : 0u;
+#pragma unroll
+            for (int j = 0; j < Q; ++j)
+                if (p == rq[j]) {
+                    m = 0;
+#pragma unroll
+                    for (int r = 0; r < E; ++r)
+                        if ((r >> j) & 1) m |= 1u << r;
+                }
+            return m;
+        };
+        int e = REV ? ru0 + run - 1 : ru0;
+        for (int done = 0; done < run;) {
+            const AOp &so = pops[e];
+            const int f = so.sw0, len = so.swn;
+            const SweepMasks sm = sweep_masks<REV>(so, len);
+            const float2 *mt = mtab + size_t(REV ? f + len - 1 : f) * 8;
+            const uint32_t mc = pmask(so.swc);
+            static_assert(Q == 3, "one case per register bit");
+            switch (so.swj) {
+            case 0: run_pair_sweep<Q, 0, REV>(x, lv, pops, f, len, mt, sm, mc, gacc); break;
+            case 1: run_pair_sweep<Q, 1, REV>(x, lv, pops, f, len, mt, sm, mc, gacc); break;
+            case 2: run_pair_sweep<Q, 2, REV>(x, lv, pops, f, len, mt, sm, mc, gacc); break;
+            default: run_diag_sweep<Q, REV>(x, lv, pops, f, len, mt, sm, mc, pmask(so.swt), gacc); break;
+            }
+            done += len;
+            e = REV ? f - 1 : f + len;
+        }
+        if (act) {
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int i = idx(r);
+                tp[i] = x[r];
+                if (REV) tl[i] = lv[r];
+            }
+        }
+    }
+}
+
 // one pass over the tiles of parameter set blockIdx.y
 template <typename R, bool REV>
-__global__ void __launch_bounds__(kApThreads, sizeof(R) == 4 ? (REV ? 3 : 4) : 2) k_adj_pass(const APass ps, const AOp *__restrict__ ops,
+__global__ void __launch_bounds__(kApThreads, sizeof(R) == 4 ? 3 : 2) k_adj_pass(const APass ps, const AOp *__restrict__ ops,
                                                          typename C2<R>::type *__restrict__ phi, int64_t lam_off,
                                                          int64_t stride, const double2 *__restrict__ cs, int P,
                                                          double *__restrict__ partials, int batch)
@@ -231,6 +482,14 @@ __global__ void __launch_bounds__(kApThreads, sizeof(R) == 4 ? (REV ? 3 : 4) : 2
         // sweeps in circuit order (reverse: last sweep first, its ops backwards)
         for (int q = 0; q < ps.no;) {
             const AOp &last = ops[ps.o0 + (REV ? ps.no - 1 - q : q)];
+            if constexpr (sizeof(R) == 4) {
+                if (last.run > 0) {
+                    adj_run<REV>(ops + ps.o0, last.ru0, last.run, tp, tl, L, mtab, gacc);
+                    __syncthreads();
+                    q += last.run;
+                    continue;
+                }
+            }
             const int f = last.sw0, len = last.swn;
             if (last.kind == 1) {
                 const AOp &op = last;
@@ -537,6 +796,60 @@ static void build_sweeps(std::vector<AOp> &v, int cap)
     v.swap(out);
 }
 
+// Groups consecutive sweeps (in circuit order; built by build_sweeps) into
+// register runs: a run's sweeps visit pairs of at most Q = kApRunBits
+// distinct tile positions (all-diagonal sweeps, applied elementwise, add
+// none), so a thread can hold the 2^Q amplitudes that differ in them and
+// carry them through every sweep of the run.  Dense two-qubit gates stay
+// outside runs.  L: the pass's tile bits (runs need L >= Q).
+static void build_runs(std::vector<AOp> &v, int L)
+{
+    constexpr int Q = kApRunBits;
+    for (AOp &o : v) {
+        o.ru0 = 0;
+        o.run = 0;
+        o.swj = -1;
+        for (int j = 0; j < 4; ++j) o.rq[j] = -1;
+    }
+    if (L < Q) return;
+    size_t i = 0;
+    while (i < v.size()) {
+        if (v[i].kind == 1) {  // a dense two-qubit gate: its own sweep, no run
+            i += size_t(v[i].swn);
+            continue;
+        }
+        uint64_t set = 0;
+        size_t e = i;
+        while (e < v.size() && v[e].kind != 1) {
+            const int len = v[e].swn;
+            const bool all_diag = v[e].swdiag == (1 << len) - 1;
+            const uint64_t req = all_diag ? 0 : uint64_t(1) << v[e].swt;
+            if (__builtin_popcountll(set | req) > Q) break;
+            set |= req;
+            e += size_t(len);
+        }
+        // register positions: the run's sweep positions, then the lowest others
+        int rq[4] = {-1, -1, -1, -1}, nq = 0;
+        for (int p = 0; p < L && nq < Q; ++p)
+            if ((set >> p) & 1) rq[nq++] = p;
+        for (int p = 0; p < L && nq < Q; ++p)
+            if (!((set >> p) & 1)) rq[nq++] = p;
+        std::sort(rq, rq + Q);
+        for (size_t k = i; k < e; ++k) {
+            AOp &o = v[k];
+            o.ru0 = int(i);
+            o.run = int(e - i);
+            for (int j = 0; j < Q; ++j) o.rq[j] = rq[j];
+            const bool all_diag = o.swdiag == (1 << o.swn) - 1;
+            o.swj = -1;
+            if (!all_diag)
+                for (int j = 0; j < Q; ++j)
+                    if (rq[j] == o.swt) o.swj = j;
+        }
+        i = e;
+    }
+}
+
 bool adj_plan(int n, hq_dtype dt, const hq_op *ops, int G, AdjPlan &plan)
 {
     for (int g = 0; g < G; ++g)
@@ -626,6 +939,7 @@ bool adj_plan(int n, hq_dtype dt, const hq_op *ops, int G, AdjPlan &plan)
         // complex128 is bound by FP64 arithmetic, which merging does not
         // reduce: one op per sweep there
         build_sweeps(pv, dt == HQ_C64 ? kSweepOps : 1);
+        if (dt == HQ_C64) build_runs(pv, ap.R + ap.nh);
         plan.op.insert(plan.op.end(), pv.begin(), pv.end());
         plan.pass.push_back(ap);
     }

@@ -66,7 +66,9 @@ struct BGate {
     int k;          // 1..kBMaxFuse
     int diag;       // matrix is diagonal
     int tpos[kBMaxFuse];  // tile positions of qubits[0..k)
-    int moff;       // its 2^k x 2^k matrix (row-major, complex64) at mat[moff]
+    int moff;       // its matrix (complex64) at mat[moff]: the 2^k diagonal entries when diag,
+                    // else 2^k x 2^k row-major; moff even (16-byte aligned)
+    int mcnt;       // float4 words of it (entries rounded up to even, / 2)
 };
 struct BPass {
     int circuit;
@@ -116,7 +118,10 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
     __shared__ long long s_tile;
     __shared__ BPass s_ps;
     __shared__ int64_t s_hioff[1 << kBMaxHigh];  // global offset of the tile's high-bit pattern h
-    __shared__ __align__(16) float2 s_m3[64];     // matrix of the current 3-qubit block
+    // matrices of the current gate and the next one (the next is copied in
+    // while the current one is applied; the barrier after each gate orders
+    // both)
+    __shared__ __align__(16) float2 s_mat[2][64];
     if (threadIdx.x == 0) atomicMin(p.t0, now_ns());
     const unsigned long long stall_ns = *reinterpret_cast<const volatile unsigned long long *>(&g_batch_stall_ns);
 
@@ -219,47 +224,51 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
             cp_async_commit();
             cp_async_wait<0>();
         }
+        if (ps.ng > 0 && threadIdx.x < p.gate[ps.g0].mcnt)
+            reinterpret_cast<float4 *>(s_mat[0])[threadIdx.x] =
+                reinterpret_cast<const float4 *>(p.mat + p.gate[ps.g0].moff)[threadIdx.x];
         __syncthreads();
         // ---------------- gates, in order ----------------
         for (int gi = ps.g0; gi < ps.g0 + ps.ng; ++gi) {
             const BGate &gt = p.gate[gi];
-            const float2 *gm = p.mat + gt.moff;
+            const int buf = (gi - ps.g0) & 1;
+            const float2 *gm = s_mat[buf];
+            if (gi + 1 < ps.g0 + ps.ng && threadIdx.x < p.gate[gi + 1].mcnt)
+                reinterpret_cast<float4 *>(s_mat[buf ^ 1])[threadIdx.x] =
+                    reinterpret_cast<const float4 *>(p.mat + p.gate[gi + 1].moff)[threadIdx.x];
             if (gt.diag) {
                 for (int i = threadIdx.x; i < TS; i += blockDim.x) {
                     int r = 0;
                     for (int j = 0; j < gt.k; ++j) r = (r << 1) | ((i >> gt.tpos[j]) & 1);
-                    const int D = 1 << gt.k;
-                    tile[swz<float>(i)] = cmul(gm[r * D + r], tile[swz<float>(i)]);
+                    tile[swz<float>(i)] = cmul(gm[r], tile[swz<float>(i)]);
                 }
             } else if (gt.k == 3) {
                 // the 8 x 8 matrix from shared memory, two entries per load
                 // (kept out of registers: 128 of them would cap the CTAs per SM)
-                if (threadIdx.x < 32)
-                    reinterpret_cast<float4 *>(s_m3)[threadIdx.x] = reinterpret_cast<const float4 *>(gm)[threadIdx.x];
-                __syncthreads();
                 const int p0 = gt.tpos[0], p1 = gt.tpos[1], p2 = gt.tpos[2];
                 const int b0 = min(p0, min(p1, p2)), b2 = max(p0, max(p1, p2)), b1 = p0 + p1 + p2 - b0 - b2;
                 for (int grp = threadIdx.x; grp < TS / 8; grp += blockDim.x) {
                     int i0 = ((grp >> b0) << (b0 + 1)) | (grp & ((1 << b0) - 1));
                     i0 = ((i0 >> b1) << (b1 + 1)) | (i0 & ((1 << b1) - 1));
                     i0 = ((i0 >> b2) << (b2 + 1)) | (i0 & ((1 << b2) - 1));
-                    int idx[8];
+                    // the swizzle is linear over XOR: element r sits at
+                    // swz(i0) ^ (swizzled bits of r's positions)
+                    const int sb = swz<float>(i0), s0 = swz<float>(1 << p0), s1 = swz<float>(1 << p1),
+                              s2 = swz<float>(1 << p2);
+                    auto idx = [&](int r) { return sb ^ ((r & 4) ? s0 : 0) ^ ((r & 2) ? s1 : 0) ^ ((r & 1) ? s2 : 0); };
                     float2 x[8];
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) {
-                        idx[r] = swz<float>(i0 | (((r >> 2) & 1) << p0) | (((r >> 1) & 1) << p1) | ((r & 1) << p2));
-                        x[r] = tile[idx[r]];
-                    }
+                    for (int r = 0; r < 8; ++r) x[r] = tile[idx(r)];
 #pragma unroll 2
                     for (int r = 0; r < 8; ++r) {
                         float2 y = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int c = 0; c < 8; c += 2) {
-                            const float4 mm = reinterpret_cast<const float4 *>(s_m3)[(r * 8 + c) >> 1];
+                            const float4 mm = reinterpret_cast<const float4 *>(gm)[(r * 8 + c) >> 1];
                             cmac(y, make_float2(mm.x, mm.y), x[c]);
                             cmac(y, make_float2(mm.z, mm.w), x[c + 1]);
                         }
-                        tile[idx[r]] = y;
+                        tile[idx(r)] = y;
                     }
                 }
             } else if (gt.k == 1) {
@@ -294,7 +303,11 @@ __global__ void __launch_bounds__(kBThreads) k_batch(const BatchParams p)
                     for (int r = 0; r < 4; ++r) {
                         float2 y = make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) cmac(y, gm[r * 4 + c], x[c]);
+                        for (int c = 0; c < 4; c += 2) {
+                            const float4 mm = reinterpret_cast<const float4 *>(gm)[(r * 4 + c) >> 1];
+                            cmac(y, make_float2(mm.x, mm.y), x[c]);
+                            cmac(y, make_float2(mm.z, mm.w), x[c + 1]);
+                        }
                         tile[idx[r]] = y;
                     }
                 }
@@ -436,7 +449,15 @@ static hq_status plan_circuit(const hq_circuit &c, int ci, int R0, int h, int fu
             for (int j = 0; j < gt.k; ++j) bg.tpos[j] = tpos(n - 1 - gt.qubits[j]);
             const int D = 1 << gt.k;
             bg.moff = int(pl.mat.size());
-            for (int e = 0; e < D * D; ++e) pl.mat.push_back(make_float2(float(gt.matrix[2 * e]), float(gt.matrix[2 * e + 1])));
+            if (bg.diag) {
+                for (int r = 0; r < D; ++r)
+                    pl.mat.push_back(make_float2(float(gt.matrix[2 * (r * D + r)]), float(gt.matrix[2 * (r * D + r) + 1])));
+            } else {
+                for (int e = 0; e < D * D; ++e)
+                    pl.mat.push_back(make_float2(float(gt.matrix[2 * e]), float(gt.matrix[2 * e + 1])));
+            }
+            if (pl.mat.size() & 1) pl.mat.push_back(make_float2(0.f, 0.f));
+            bg.mcnt = int(pl.mat.size() - size_t(bg.moff)) / 2;
             pl.gate.push_back(bg);
         }
         pl.pass.push_back(bp);

@@ -79,6 +79,48 @@ def test_mixed_gates_and_y_terms(hq, dt, tol, tokens):
         assert rel_err(g[b], g_o) <= tol
 
 
+def diagonal_mix_circuit(n, n_gates, seed):
+    """Rotations about X, Y, Z, dense one-qubit unitaries, CZ and CPhase on
+    random pairs (diagonal two-qubit gates whose second qubit lands inside and
+    outside the register positions of a run) and a few fSim gates."""
+    rng = C.SplitMix64(seed)
+    gates, p = [], 0
+    for _ in range(n_gates):
+        kind = rng.randint(0, 9)
+        q = rng.randint(0, n - 1)
+        q2 = (q + 1 + rng.randint(0, n - 2)) % n
+        if kind <= 3:
+            ax = "XYZ"[rng.randint(0, 2)]
+            gates.append(C.Gate("R" + ax, (q,), None, ax, p))
+            p += 1
+        elif kind <= 5:
+            gates.append(C.Gate("U", (q,), C.random_unitary(1, rng)))
+        elif kind == 6:
+            gates.append(C.Gate("CZ", (q, q2), C.cz()))
+        elif kind <= 8:
+            gates.append(C.Gate("CP", (q, q2), C.cphase(0.3 + rng.uniform())))
+        else:
+            gates.append(C.Gate("fSim", (q, q2), C.fsim(0.4, 0.9)))
+    return C.Circuit(n, gates, p)
+
+
+@pytest.mark.parametrize("n,seed", [(5, 1), (13, 3), (14, 4)])
+def test_register_runs_against_oracle(hq, n, seed):
+    """complex64 passes carry runs of sweeps through registers: every mix of
+    context bits (inside or outside a run's register positions), elementwise
+    diagonal sweeps and dense two-qubit gates between runs against the
+    oracle's adjoint."""
+    circ = diagonal_mix_circuit(n, 160, seed)
+    H = mixed_hamiltonian(n)
+    th = np.array([[2 * math.pi * ((5 * i + 7 * b + seed) % 13) / 13 for i in range(circ.n_params)]
+                   for b in range(3)])
+    e, g = hq.hq_adjoint_grad(circ, H, th, dtype="complex64")
+    for b in range(3):
+        e_o, g_o = oracle.adjoint_grad(circ, H, th[b])
+        assert abs(e[b] - e_o) <= 1e-4 * max(1, abs(e_o))
+        assert rel_err(g[b], g_o) <= 1e-4
+
+
 @pytest.mark.parametrize("checkpoints", [1, 3, 7])
 def test_checkpoints_do_not_change_result(hq, checkpoints):
     circ = C.ansatz(8, 3)
