@@ -84,35 +84,6 @@ __device__ __forceinline__ double ex_flip(double w, uint32_t c)
     return __longlong_as_double(__double_as_longlong(w) ^ (static_cast<long long>(c) << 63));
 }
 
-// packed FP32 pairs (one instruction for both lanes of a float2)
-__device__ __forceinline__ float2 ex_ffma2(float2 a, float2 b, float2 c)
-{
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
-__device__ __forceinline__ float2 ex_fadd2(float2 a, float2 b)
-{
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 ex_fsub2(float2 a, float2 b)
-{
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-
 // sum over the pairs (j, j | 2^I), bit I of j clear, of Re(conj(a_j) a_{j|2^I})
 // (IM: Im of the same products); partial sums against long chains (complex64
 // Re: the x and y products in the two lanes of packed FMAs)
@@ -125,7 +96,7 @@ __device__ __forceinline__ auto ex_pair_sum(const V *a) -> decltype(a->x)
 #pragma unroll
         for (int v = 0; v < E / 2; ++v) {
             const int j = ((v >> I) << (I + 1)) | (v & ((1 << I) - 1));
-            q[v & 1] = ex_ffma2(a[j], a[j | (1 << I)], q[v & 1]);
+            q[v & 1] = pk_fma(a[j], a[j | (1 << I)], q[v & 1]);
         }
         return (q[0].x + q[0].y) + (q[1].x + q[1].y);
     } else {

@@ -209,6 +209,22 @@ __device__ __forceinline__ void run_mats(const float2 *mt, int j, float2 (&m0)[4
     m1[2] = make_float2(d.x, d.y); m1[3] = make_float2(d.z, d.w);
 }
 
+// packed complex products: m x = m (x.x, x.x) + q (x.y, x.y) with q = (-m.y, m.x)
+__device__ __forceinline__ float2 run_cmul_pk(float2 m, float2 q, float2 x)
+{
+    return pk_fma(m, make_float2(x.x, x.x), pk_mul(q, make_float2(x.y, x.y)));
+}
+// (x0, x1) <- M (x0, x1), M's entries m[] and their q[] forms
+__device__ __forceinline__ void run_mul2_pk(const float2 (&m)[4], const float2 (&q)[4], float2 &x0, float2 &x1)
+{
+    const float2 a0 = make_float2(x0.x, x0.x), b0 = make_float2(x0.y, x0.y);
+    const float2 a1 = make_float2(x1.x, x1.x), b1 = make_float2(x1.y, x1.y);
+    const float2 y0 = pk_fma(m[0], a0, pk_fma(q[0], b0, pk_fma(m[1], a1, pk_mul(q[1], b1))));
+    const float2 y1 = pk_fma(m[2], a0, pk_fma(q[2], b0, pk_fma(m[3], a1, pk_mul(q[3], b1))));
+    x0 = y0;
+    x1 = y1;
+}
+
 // Im<l|P x> over the pairs (r0, r0 | 2^JT) for the Pauli P of `axis`
 // (warp-uniform; one short loop per axis)
 template <int Q, int JT>
@@ -260,25 +276,63 @@ __device__ __forceinline__ void run_pair_sweep(float2 (&x)[1 << Q], float2 (&l)[
     for (int j = 0; j < nsw; ++j) {
         if (REV && ((sm.rot >> j) & 1)) run_grad(gacc, pops[f + len - 1 - j].slot, run_pauli_im<Q, JT>(int((sm.ax >> (8 * j)) & 255u), x, l));
         const float2 *mj = mt - (REV ? 8 * j : 0);
-        const bool dg = (sm.diag >> j) & 1;
+        const bool dg = (sm.diag >> j) & 1, re = (sm.real >> j) & 1;
         if (!cvar) {
+            // packed FP32: m x = m (x.x, x.x) + m' (x.y, x.y), m' = (-m.y, m.x)
             const float4 *mv = reinterpret_cast<const float4 *>(mj + (mc & 1u) * 4);
             const float4 a = mv[0], b = mv[1];
-            const float2 mm[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
-                                  make_float2(b.z, b.w)};
+            const float2 m[4] = {make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(b.x, b.y),
+                                 make_float2(b.z, b.w)};
+            if (dg) {
+                const float2 q0 = make_float2(-m[0].y, m[0].x), q3 = make_float2(-m[3].y, m[3].x);
+#pragma unroll
+                for (int p = 0; p < (1 << (Q - 1)); ++p) {
+                    const int r0 = run_ins0(p, JT), r1 = r0 | (1 << JT);
+                    x[r0] = run_cmul_pk(m[0], q0, x[r0]);
+                    x[r1] = run_cmul_pk(m[3], q3, x[r1]);
+                    if (REV) {
+                        l[r0] = run_cmul_pk(m[0], q0, l[r0]);
+                        l[r1] = run_cmul_pk(m[3], q3, l[r1]);
+                    }
+                }
+            } else if (re) {
+                const float2 s0 = make_float2(m[0].x, m[0].x), s1 = make_float2(m[1].x, m[1].x),
+                             s2 = make_float2(m[2].x, m[2].x), s3 = make_float2(m[3].x, m[3].x);
+#pragma unroll
+                for (int p = 0; p < (1 << (Q - 1)); ++p) {
+                    const int r0 = run_ins0(p, JT), r1 = r0 | (1 << JT);
+                    const float2 x0 = x[r0], x1 = x[r1];
+                    x[r0] = pk_fma(s0, x0, pk_mul(s1, x1));
+                    x[r1] = pk_fma(s2, x0, pk_mul(s3, x1));
+                    if (REV) {
+                        const float2 l0 = l[r0], l1 = l[r1];
+                        l[r0] = pk_fma(s0, l0, pk_mul(s1, l1));
+                        l[r1] = pk_fma(s2, l0, pk_mul(s3, l1));
+                    }
+                }
+            } else {
+                float2 q[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) q[k] = make_float2(-m[k].y, m[k].x);
+#pragma unroll
+                for (int p = 0; p < (1 << (Q - 1)); ++p) {
+                    const int r0 = run_ins0(p, JT), r1 = r0 | (1 << JT);
+                    run_mul2_pk(m, q, x[r0], x[r1]);
+                    if (REV) run_mul2_pk(m, q, l[r0], l[r1]);
+                }
+            }
+        } else if (dg) {
+            // per pair, the diagonal entries of its context value
 #pragma unroll
             for (int p = 0; p < (1 << (Q - 1)); ++p) {
                 const int r0 = run_ins0(p, JT), r1 = r0 | (1 << JT);
-                if (dg) {
-                    x[r0] = cmul(mm[0], x[r0]);
-                    x[r1] = cmul(mm[3], x[r1]);
-                    if (REV) {
-                        l[r0] = cmul(mm[0], l[r0]);
-                        l[r1] = cmul(mm[3], l[r1]);
-                    }
-                } else {
-                    mul2(mm, x[r0], x[r1]);
-                    if (REV) mul2(mm, l[r0], l[r1]);
+                const float2 *md = mj + ((mc >> r0) & 1u) * 4;
+                const float2 d0 = md[0], d1 = md[3];
+                x[r0] = cmul(d0, x[r0]);
+                x[r1] = cmul(d1, x[r1]);
+                if (REV) {
+                    l[r0] = cmul(d0, l[r0]);
+                    l[r1] = cmul(d1, l[r1]);
                 }
             }
         } else {

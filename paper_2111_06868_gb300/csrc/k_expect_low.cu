@@ -102,8 +102,8 @@ __global__ void __launch_bounds__(kElThreads, ElShape<R>::MIN_BLOCKS) k_expect_l
                     for (int i = 0; i < E / 2; ++i)
                         if (!(i & t)) {
                             const float2 x = Wp[i], y = Wp[i | t];
-                            Wp[i] = ex_fadd2(x, y);
-                            Wp[i | t] = ex_fsub2(x, y);
+                            Wp[i] = pk_add(x, y);
+                            Wp[i | t] = pk_sub(x, y);
                         }
 #pragma unroll
                 for (int i = 0; i < E / 2; ++i) {
