@@ -124,8 +124,9 @@ class ClockSampler:
 
 
 def fuse(hq, n, gates, kmax, args):
-    """The fusion step (host): hq_fuse_dag by default, hq_fuse on --fuse greedy."""
-    return hq.hq_fuse(n, gates, kmax, method=args.fuse, restarts=args.fuse_restarts)
+    """The fusion step (host): hq_fuse_beam by default (--fuse-width kept
+    sequences), hq_fuse_dag on --fuse dag, hq_fuse on --fuse greedy."""
+    return hq.hq_fuse(n, gates, kmax, method=args.fuse, restarts=args.fuse_restarts, width=args.fuse_width)
 
 
 def kernel_sources_sha(kernel_class):
@@ -712,7 +713,7 @@ def measure_e2e(args, hq, circ, blocks, state, stream, engine, dist):
     in stream order.  Also measured: the H2D copy alone by the copy engine
     and by hq_state_upload (GB/s); the copy-engine variant that overlaps the
     next step's copy with the current step on a second stream; and a variant
-    that runs the fusion (hq_fuse_dag) of the next step's circuit on the host
+    that runs the fusion (the bench's --fuse rule) of the next step's circuit on the host
     while the current step's kernels run.  The pinned buffer is allocated
     (and first touched) by a thread bound to the GPU's local CPUs where the
     system reports them."""
@@ -807,7 +808,8 @@ def measure_e2e(args, hq, circ, blocks, state, stream, engine, dist):
                     "copy_engine_GBps": nbytes / t_ce / 1e9, "copy_engine_ms": 1e3 * t_ce},
             "numa": numa,
             "with_fusion_each_step": {"value": G * e2e_steps / t_f, "ms_per_step": 1e3 * t_f / e2e_steps,
-                                      "note": "hq_fuse_dag of the next step on the host under the current "
+                                      "fusion": args.fuse,
+                                      "note": "the fusion of the next step on the host under the current "
                                               "step's kernels"},
             "copy_engine_overlapped": {"value": G * e2e_steps / t_o, "ms_per_step": 1e3 * t_o / e2e_steps,
                                        "note": "torch copy_ from pinned memory on a second stream, the next "
@@ -839,9 +841,11 @@ def main():
     ap.add_argument("--impl", default="hq", choices=["hq", "reference"])
     ap.add_argument("--workload", default="n30", choices=["n30", "n33", "n27", "n12"])
     ap.add_argument("--kmax", type=int, default=6)
-    ap.add_argument("--fuse", default="dag", choices=["dag", "greedy"],
-                    help="hq_fuse_dag (DAG frontier, restarts) or hq_fuse (greedy rule)")
+    ap.add_argument("--fuse", default="beam", choices=["beam", "dag", "greedy"],
+                    help="hq_fuse_beam (beam search over DAG-frontier blocks), hq_fuse_dag (DAG frontier, "
+                         "restarts) or hq_fuse (greedy rule)")
     ap.add_argument("--fuse-restarts", type=int, default=64)
+    ap.add_argument("--fuse-width", type=int, default=128, help="kept sequences of hq_fuse_beam")
     ap.add_argument("--dtype", default="complex64", choices=["complex64", "complex128"])
     ap.add_argument("--engine", default="tc_f16", choices=["auto", "cuda_core", "tc_f16", "tc_bf16", "tc_pass", "df"])
     ap.add_argument("--tc-min-k", type=int, default=4)
@@ -1010,7 +1014,8 @@ def main():
                                if n == 30 and engine.startswith("tc") else None,
                        "timing": "value: one hq_apply_blocks call over all blocks per step; roofline: a "
                                  "second pass with one call per block between CUDA events",
-                       "fusion": (f"{args.fuse} ({args.fuse_restarts} restarts)" if args.fuse == "dag" else args.fuse),
+                       "fusion": (f"dag ({args.fuse_restarts} restarts)" if args.fuse == "dag" else
+                                  f"beam (width {args.fuse_width})" if args.fuse == "beam" else args.fuse),
                        "state": args.dtype, "engine": engine, "l2": (f"state ({S * (1 << n) / 2**30:g} GiB) larger than the 129 MB L2; no flush" if S << n > 129e6
                               else f"state ({S << n} B) fits in L2 and is not flushed"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",

@@ -178,6 +178,28 @@ hq_status hq_fuse_dag(int n, const hq_gate *gates, int G, int k_max, int restart
                       hq_gate *blocks, int *B, double *pool, int64_t pool_len, int *gate_block);
 
 /*
+ * hq_fuse_beam -- Sec. 3.1 compress(circuit, max_n_qubits) by a beam search
+ * over the block sequences of hq_fuse_dag: the same output (blocks of at most
+ * k_max qubits, qubits ascending, matrix = product of the members in FP64),
+ * in as few or fewer blocks.  Each step extends every one of the `width`
+ * kept sequences by one block (proposed from each frontier gate by the
+ * hq_fuse_dag growth rule, once with the lowest-index tie-break and three
+ * times with SplitMix64 tie-breaks seeded from seed, the step and the
+ * sequence), keeps the `width` extensions that have absorbed the most gates
+ * (3 points per multi-qubit gate, 1 per single-qubit gate; one per distinct
+ * DAG frontier), and stops at the first sequence that absorbs every gate;
+ * hq_fuse_dag's merge pass follows.  The result is never worse than
+ * hq_fuse_dag's first run, and the same for the same arguments on any host.
+ *   width: 1..4096 kept sequences.
+ *   other arguments, ownership and errors: as hq_fuse (width out of range:
+ *   HQ_ERR_ARG).
+ * Host only; no device work; spreads the sequences over up to 16 host
+ * threads.  Cost: about width x (a few ms per 1000 gates) of CPU time.
+ */
+hq_status hq_fuse_beam(int n, const hq_gate *gates, int G, int k_max, int width, uint64_t seed,
+                       hq_gate *blocks, int *B, double *pool, int64_t pool_len, int *gate_block);
+
+/*
  * hq_reduced_density_matrix -- the reduced density matrix of k <= 2 qubits
  * of a pure state: rho_ab = sum over the other qubits' indices y of
  * psi(y, a) conj(psi(y, b)), a and b local indices with qubits[0] as MSB

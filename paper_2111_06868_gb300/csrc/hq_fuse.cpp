@@ -22,6 +22,8 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <thread>
+#include <unordered_set>
 #include <vector>
 
 #include "../../include/hq.h"
@@ -201,6 +203,95 @@ public:
         return out;
     }
 
+    // Beam search over block sequences: every step extends each of the
+    // `width` kept sequences by one block, proposed from each frontier gate
+    // by grow() (once with the lowest-index tie-break, kBeamVariants - 1
+    // times with random ones), and keeps the `width` extensions that have
+    // absorbed the most (score as above; one per distinct frontier).  The
+    // first sequence that absorbs every gate is returned, merged.
+    std::vector<Blk> beam(int width, uint64_t seed) const
+    {
+        constexpr int kBeamVariants = 4;
+        struct State {
+            Ptr ptr;
+            int score;
+            std::vector<uint64_t> sets;
+        };
+        int total = 0;
+        for (int g = 0; g < G_; ++g) total += weight_[g];
+        std::vector<State> cur(1);
+        cur[0].ptr.fill(0);
+        cur[0].score = 0;
+        std::vector<uint64_t> done_sets;
+        bool done = total == 0;
+        for (int step = 0; !done; ++step) {
+            // children of state i depend only on (seed, step, i), so any thread
+            // split gives the same list
+            std::vector<std::vector<State>> kids(cur.size());
+            auto expand = [&](size_t i) {
+                const State &st = cur[i];
+                SplitMix64 rng{seed ^ (uint64_t(step) << 32) ^ (uint64_t(i) * 0x9e3779b97f4a7c15ull)};
+                for (int q = 0; q < n_; ++q) {
+                    if (st.ptr[q] >= int(per_q_[q].size())) continue;
+                    const int g0 = per_q_[q][st.ptr[q]];
+                    if (__builtin_ctzll(mask_[g0]) != q || !is_head(g0, st.ptr)) continue;
+                    for (int v = 0; v < kBeamVariants; ++v) {
+                        const uint64_t S = grow(mask_[g0], st.ptr, v ? &rng : nullptr);
+                        State c;
+                        c.score = st.score + absorb(S, st.ptr, c.ptr, nullptr);
+                        c.sets = st.sets;
+                        c.sets.push_back(S);
+                        kids[i].push_back(std::move(c));
+                    }
+                }
+            };
+            const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+            const size_t nt = std::min<size_t>(hw, cur.size());
+            if (nt <= 1) {
+                for (size_t i = 0; i < cur.size(); ++i) expand(i);
+            } else {
+                std::vector<std::thread> th;
+                for (size_t t = 0; t < nt; ++t)
+                    th.emplace_back([&, t]() {
+                        for (size_t i = t; i < cur.size(); i += nt) expand(i);
+                    });
+                for (auto &x : th) x.join();
+            }
+            std::vector<State> all;
+            for (auto &k : kids)
+                for (auto &c : k) all.push_back(std::move(c));
+            std::stable_sort(all.begin(), all.end(), [](const State &a, const State &b) { return a.score > b.score; });
+            if (all.empty()) break;  // unreachable: a non-empty frontier always has a head gate
+            if (all[0].score == total) {
+                done_sets = all[0].sets;
+                done = true;
+                break;
+            }
+            std::vector<State> next;
+            std::unordered_set<uint64_t> seen;  // FNV-1a of the frontier (a collision only drops a candidate)
+            for (auto &c : all) {
+                if (int(next.size()) >= width) break;
+                uint64_t h = 1469598103934665603ull;
+                for (int q = 0; q < n_; ++q) h = (h ^ uint64_t(c.ptr[q])) * 1099511628211ull;
+                if (!seen.insert(h).second) continue;
+                next.push_back(std::move(c));
+            }
+            cur = std::move(next);
+        }
+        // replay the chosen sets from the start for the members
+        std::vector<Blk> out;
+        Ptr ptr{};
+        for (uint64_t S : done_sets) {
+            Blk b{S, {}};
+            Ptr nx;
+            absorb(S, ptr, nx, &b.members);
+            ptr = nx;
+            out.push_back(std::move(b));
+        }
+        merge(out);
+        return out;
+    }
+
 private:
     using Ptr = std::array<int, 64>;
 
@@ -347,6 +438,20 @@ extern "C" hq_status hq_fuse_dag(int n, const hq_gate *gates, int G, int k_max, 
         if (bl.size() < best.size()) best = std::move(bl);
     }
     return emit_blocks(best, gates, blocks, B, pool, pool_len, gate_block);
+}
+
+extern "C" hq_status hq_fuse_beam(int n, const hq_gate *gates, int G, int k_max, int width, uint64_t seed,
+                                  hq_gate *blocks, int *B, double *pool, int64_t pool_len, int *gate_block)
+{
+    hq_status st = check_gates(n, gates, G, k_max, B, blocks, pool);
+    if (st != HQ_OK) return st;
+    if (width < 1 || width > 4096) return HQ_ERR_ARG;
+    const Frontier f(n, gates, G, k_max);
+    std::vector<Blk> bl = f.beam(width, seed);
+    // never worse than the single greedy run
+    std::vector<Blk> one = f.run(nullptr);
+    if (one.size() < bl.size()) bl = std::move(one);
+    return emit_blocks(bl, gates, blocks, B, pool, pool_len, gate_block);
 }
 
 // ----------------------------------------------------------------------------

@@ -107,6 +107,7 @@ def load(path: str | None = None):
         "hq_state_upload": ([V, V, I, I, V], I),
         "hq_fuse": ([I, V, I, I, V, P(I), V, ctypes.c_int64, V], I),
         "hq_fuse_dag": ([I, V, I, I, I, ctypes.c_uint64, V, P(I), V, ctypes.c_int64, V], I),
+        "hq_fuse_beam": ([I, V, I, I, I, ctypes.c_uint64, V, P(I), V, ctypes.c_int64, V], I),
         "hq_gate_structure": ([I, V, P(I), V], I),
         "hq_pop": ([I, V, I, V, I, I, V], I),
         "hq_reduced_density_matrix": ([V, I, I, V, I, V, V], I),
@@ -327,9 +328,10 @@ def hq_gate_structure(matrix):
 
 
 def hq_fuse(n: int, gates: Iterable, k_max: int, with_members: bool = False, method: str = "greedy",
-            restarts: int = 64, seed: int = 0):
+            restarts: int = 64, seed: int = 0, width: int = 128):
     """Returns blocks as a list of (qubits tuple, complex128 matrix).
-    method "greedy": hq_fuse; "dag": hq_fuse_dag with `restarts` and `seed`."""
+    method "greedy": hq_fuse; "dag": hq_fuse_dag with `restarts` and `seed`;
+    "beam": hq_fuse_beam with `width` and `seed`."""
     keep: list = []
     arr, G = _gates_array(gates, keep)
     cap = max(1, G)
@@ -343,6 +345,8 @@ def hq_fuse(n: int, gates: Iterable, k_max: int, with_members: bool = False, met
         _check(load().hq_fuse(n, arr, G, k_max, *tail), "hq_fuse")
     elif method == "dag":
         _check(load().hq_fuse_dag(n, arr, G, k_max, restarts, seed, *tail), "hq_fuse_dag")
+    elif method == "beam":
+        _check(load().hq_fuse_beam(n, arr, G, k_max, width, seed, *tail), "hq_fuse_beam")
     else:
         raise ValueError(f"unknown fusion method {method!r}")
     out = []

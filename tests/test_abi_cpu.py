@@ -143,6 +143,49 @@ def test_fuse_dag_is_deterministic_and_not_worse(hq):
         assert len(dag) <= len(one)
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_fuse_beam_keeps_qubit_order_and_state(hq, seed):
+    circ = C.random_circuit(C.grid(3, 4), 12, seed=seed, two_qubit="fsim" if seed % 2 else "cz")
+    for kmax, width in ((3, 8), (4, 32), (6, 128)):
+        blocks, members = hq.hq_fuse(12, circ.gates, kmax, with_members=True, method="beam", width=width,
+                                     seed=seed)
+        assert per_qubit_block_order_kept(12, circ.gates, members)
+        assert all(len(q) <= kmax for q, _ in blocks)
+        assert sorted(set(members.tolist())) == list(range(len(blocks)))  # every block holds a gate
+        psi0 = oracle.state_init(12, "+-+0-+-1+-+-")
+        fused = C.Circuit(12, [C.Gate("B", q, m) for q, m in blocks])
+        np.testing.assert_allclose(oracle.apply_circuit(psi0.copy(), fused),
+                                   oracle.apply_circuit(psi0.copy(), circ), atol=1e-12)
+
+
+def test_fuse_beam_is_deterministic_and_not_worse(hq):
+    """The beam search places fewer blocks than the frontier restarts on the
+    grid circuits (n=30: 43 -> 39, n=33: 57 -> 53 at k_max = 6, width 128),
+    never more than the frontier rule's first run, and the same blocks for
+    the same arguments."""
+    for circ, bound in [(C.config_n30(0), 40), (C.config_n33(0), 54)]:
+        beam = hq.hq_fuse(circ.n, circ.gates, 6, method="beam", width=128)
+        one = hq.hq_fuse(circ.n, circ.gates, 6, method="dag", restarts=1)
+        dag = hq.hq_fuse(circ.n, circ.gates, 6, method="dag")
+        assert len(beam) <= bound < len(dag) <= len(one)
+        again = hq.hq_fuse(circ.n, circ.gates, 6, method="beam", width=128)
+        assert [q for q, _ in again] == [q for q, _ in beam]
+        assert all(np.array_equal(a, b) for (_, a), (_, b) in zip(again, beam))
+    # width 1 is the frontier rule with four proposals per frontier gate
+    circ = C.config_n30(0)
+    assert len(hq.hq_fuse(30, circ.gates, 6, method="beam", width=1)) <= len(one)
+
+
+def test_fuse_beam_errors_and_empty(hq):
+    circ = C.Circuit(4, [C.Gate("U", (0, 1, 2), np.eye(8, dtype=np.complex128))])
+    for w in (0, 4097):
+        with pytest.raises(hq.HQError, match="ARG"):
+            hq.hq_fuse(4, circ.gates, 3, method="beam", width=w)
+    with pytest.raises(hq.HQError, match="K_TOO_LARGE"):
+        hq.hq_fuse(4, circ.gates, 2, method="beam")
+    assert hq.hq_fuse(3, [], 4, method="beam") == []
+
+
 def test_fuse_grid_circuit_reduces_passes(hq):
     circ = C.config_n30(0)
     for kmax, bound in [(2, 845), (4, 300), (6, 200)]:
