@@ -707,16 +707,18 @@ def _cpulist(text):
 
 
 def measure_e2e(args, hq, circ, blocks, state, stream, engine, dist):
-    """End to end through the public API: every step uploads the state from
-    pinned host memory (hq_state_upload: the SMs read the host buffer over
-    the CPU-GPU link), applies the fused blocks and reads the FP64 norm back,
-    in stream order.  Also measured: the H2D copy alone by the copy engine
-    and by hq_state_upload (GB/s); the copy-engine variant that overlaps the
-    next step's copy with the current step on a second stream; and a variant
-    that runs the fusion (the bench's --fuse rule) of the next step's circuit on the host
-    while the current step's kernels run.  The pinned buffer is allocated
-    (and first touched) by a thread bound to the GPU's local CPUs where the
-    system reports them."""
+    """End to end through the public API, as a user of Sec. 4.2's simulate()
+    gets the result: every step is one hq_simulate call (the block matrices
+    go up from host memory inside it; |0..0>, the blocks and the FP64 norm)
+    and the final state read back into pinned host memory, in stream order.
+    Also measured: the same with the state uploaded from pinned host memory
+    (hq_state_upload: the SMs read the host buffer over the CPU-GPU link),
+    hq_apply_blocks and the norm instead; the H2D and D2H copies alone (GB/s);
+    the copy-engine variant that overlaps the next step's upload with the
+    current step on a second stream; and a variant that runs the fusion of
+    the next step's circuit on the host while the current step's kernels run.
+    The pinned buffers are allocated (and first touched) by a thread bound to
+    the GPU's local CPUs where the system reports them."""
     import torch
 
     n, G = circ.n, len(circ.gates)
@@ -730,6 +732,8 @@ def measure_e2e(args, hq, circ, blocks, state, stream, engine, dist):
         host_in = torch.empty(1 << n, dtype=cdt, pin_memory=True)
         host_in.zero_()
         host_in[0] = 1
+        host_out = torch.empty(1 << n, dtype=cdt, pin_memory=True)
+        host_out.zero_()
     finally:
         if local:
             os.sched_setaffinity(0, old_aff)
@@ -752,15 +756,24 @@ def measure_e2e(args, hq, circ, blocks, state, stream, engine, dist):
 
     t_ce = timed_copy(lambda: bufs[1].copy_(host_in, non_blocking=True))
     t_sm = timed_copy(lambda: hq.hq_state_upload(bufs[1], host_in, stream=stream))
+    t_d2h = timed_copy(lambda: host_out.copy_(bufs[1], non_blocking=True))
     nbytes = (1 << n) * S
+    # matrices the library uploads per step: the split B operand of every tensor-core block
+    tc_bytes = sum(2 * (2 * 64) ** 2 * 2 for q, m in blocks
+                   if block_class(q, m, engine, args.tc_min_k, n, S).startswith("k_tc"))
 
-    def serial(steps, refuse=False):
+    def simulate_read(steps, refuse=False):
         cur_blocks = blocks
         for s in range(steps):
-            hq.hq_state_upload(state, host_in, stream=stream)
-            hq.hq_apply_blocks(state, cur_blocks, engine=engine, tc_min_k=args.tc_min_k, stream=stream)
-            if refuse and s + 1 < steps:  # next step's fusion on the host, under this step's kernels
+            out[0] = hq.hq_simulate(state, cur_blocks, engine=engine, tc_min_k=args.tc_min_k, stream=stream)
+            host_out.copy_(state, non_blocking=True)
+            if refuse and s + 1 < steps:  # next step's fusion on the host, under this step's copy
                 cur_blocks = fuse(hq, n, circ.gates, args.kmax, args)
+
+    def upload(steps):
+        for s in range(steps):
+            hq.hq_state_upload(state, host_in, stream=stream)
+            hq.hq_apply_blocks(state, blocks, engine=engine, tc_min_k=args.tc_min_k, stream=stream)
             out[0] = hq.hq_expectation(state, [(1.0, ())], stream=stream)
 
     def overlapped(steps, start=None):
@@ -797,25 +810,32 @@ def measure_e2e(args, hq, circ, blocks, state, stream, engine, dist):
         return e0.elapsed_time(e1) / 1e3
 
     e2e_steps = max(2, min(args.steps, 5))
-    et = timed(serial, e2e_steps)
+    et = timed(simulate_read, e2e_steps)
     e2e_value, et = whole_job_rate(et, G * e2e_steps, dist, "cuda")
-    t_f = timed(serial, e2e_steps, refuse=True)
+    t_f = timed(simulate_read, e2e_steps, refuse=True)
+    t_u = timed(upload, e2e_steps)
     t_o = timed(overlapped, e2e_steps)
     del bufs
-    return {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": 8,
+    return {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": tc_bytes, "d2h_bytes_per_step": nbytes + 8,
             "ms_per_step": 1e3 * et / e2e_steps,
+            "note": "every step: hq_simulate (|0..0>, the fused blocks with their matrices uploaded from host "
+                    "memory inside the call, FP64 norm read back), then the final state copied into pinned "
+                    "host memory; in stream order on one stream",
             "h2d": {"sm_read_GBps": nbytes / t_sm / 1e9, "sm_read_ms": 1e3 * t_sm,
                     "copy_engine_GBps": nbytes / t_ce / 1e9, "copy_engine_ms": 1e3 * t_ce},
+            "d2h": {"copy_engine_GBps": nbytes / t_d2h / 1e9, "copy_engine_ms": 1e3 * t_d2h},
             "numa": numa,
             "with_fusion_each_step": {"value": G * e2e_steps / t_f, "ms_per_step": 1e3 * t_f / e2e_steps,
                                       "fusion": args.fuse,
                                       "note": "the fusion of the next step on the host under the current "
-                                              "step's kernels"},
+                                              "step's state read-back"},
+            "state_upload": {"value": G * e2e_steps / t_u, "ms_per_step": 1e3 * t_u / e2e_steps,
+                             "h2d_bytes_per_step": nbytes + tc_bytes, "d2h_bytes_per_step": 8,
+                             "note": "every step: hq_state_upload of the pinned host state (SM reads), "
+                                     "hq_apply_blocks, FP64 norm read back"},
             "copy_engine_overlapped": {"value": G * e2e_steps / t_o, "ms_per_step": 1e3 * t_o / e2e_steps,
                                        "note": "torch copy_ from pinned memory on a second stream, the next "
-                                               "step's copy overlapping the current step (two buffers)"},
-            "note": "every step: hq_state_upload of the pinned host state (SM reads), hq_apply_blocks, FP64 "
-                    "norm read back; in stream order on one stream"}
+                                               "step's copy overlapping the current step (two buffers)"}}
 
 
 def whole_job_rate(local_seconds: float, local_units: float, dist=None, device=None):
@@ -913,11 +933,10 @@ def main():
     passes = len(hq.hq_plan_passes(n, blocks)) if engine == "tc_pass" else 0
 
     def step():
-        """One pass of the hot path through the public API: |0..0>, every fused
-        block in one hq_apply_blocks call, the FP64 norm (synchronous)."""
-        hq.hq_state_init(state)
-        hq.hq_apply_blocks(state, blocks, engine=engine, tc_min_k=args.tc_min_k)
-        return hq.hq_expectation(state, norm_term)
+        """One pass of the hot path through the public API: one hq_simulate
+        call (Sec. 4.2 simulate: |0..0>, every fused block, the FP64 norm;
+        synchronous)."""
+        return hq.hq_simulate(state, blocks, engine=engine, tc_min_k=args.tc_min_k)
 
     def step_per_block(events):
         """The same step with one call per block, bracketed by CUDA events on
@@ -1002,7 +1021,11 @@ def main():
         extras = measure_extras(args)
 
     if rank == 0:
-        eff_gbs = B * bytes_per_launch * args.steps / (elapsed / world) / 1e9
+        # bytes a step moves: the first tensor-core block only writes (its input
+        # is computed from the tokens), the last sums the norm as it writes
+        first_tc, last_tc = classes[0].startswith("k_tc"), classes[-1].startswith("k_tc")
+        passes_rw = 2 * B - (1 if first_tc else -1) + (0 if last_tc else 1)
+        eff_gbs = passes_rw * (bytes_per_launch // 2) * args.steps / (elapsed / world) / 1e9
         rec = {
             "metric": METRIC, "value": value, "unit": "gate-apps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
@@ -1012,8 +1035,9 @@ def main():
                        "note": "the n=30 circuit of the per-gate / fused k<=4 configuration, run on the "
                                "fused k<=6 tensor-core engine of the 33-qubit configuration"
                                if n == 30 and engine.startswith("tc") else None,
-                       "timing": "value: one hq_apply_blocks call over all blocks per step; roofline: a "
-                                 "second pass with one call per block between CUDA events",
+                       "timing": "value: one hq_simulate call per step (init folded into the first "
+                                 "block, norm into the last); roofline: a second pass with hq_state_init, "
+                                 "one hq_apply_blocks call per block between CUDA events, and the norm",
                        "fusion": (f"dag ({args.fuse_restarts} restarts)" if args.fuse == "dag" else
                                   f"beam (width {args.fuse_width})" if args.fuse == "beam" else args.fuse),
                        "state": args.dtype, "engine": engine, "l2": (f"state ({S * (1 << n) / 2**30:g} GiB) larger than the 129 MB L2; no flush" if S << n > 129e6
@@ -1028,7 +1052,7 @@ def main():
             "per_class": per_class,
             "norm2": norm, "fuse_s": fuse_s, "per_block_pass_ms_per_step": 1e3 * per_block_step_s,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "extras": extras,
-            "gpu_launches": args.steps * (B + 3),
+            "gpu_launches": args.steps * (B + (0 if first_tc else 1) + (0 if last_tc else 1)),
         }
         print(json.dumps(rec))
     if dist:

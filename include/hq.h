@@ -438,6 +438,33 @@ hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates,
                           void *stream);
 
 /*
+ * hq_simulate -- Sec. 4.2 simulate(circuit, initial_state): state <- the
+ * gates / fused blocks applied in order (as hq_apply_blocks applies them with
+ * cfg) to the Sec. 4.1 product state of `tokens` (as hq_state_init; NULL =
+ * |0..0>); with norm2_host set, also the squared norm sum |psi_x|^2 of the
+ * result, accumulated in double.  The same result as hq_state_init,
+ * hq_apply_blocks and hq_expectation of the identity in a row, in fewer
+ * passes over the state on the tensor-core engines (complex64): a first
+ * block that runs on the tensor cores computes its input amplitudes from the
+ * tokens instead of reading an initialised state, and a last one that does
+ * sums |psi_x|^2 of what it writes (each square split exactly into two
+ * floats, float-pair sums by TwoSum within a tile, FP64 across tiles, the
+ * per-warp sums added on the host in a fixed order: the exact sum of the
+ * stored amplitudes to ~1e-13 relative).  Other engines
+ * and blocks run the separate passes.
+ *   state: out, 2^n amplitudes (DEVICE, caller-owned, 16-byte aligned); its
+ *          previous contents are never read.
+ *   norm2_host: out (may be NULL); when set the call SYNCHRONISES `stream`
+ *          and reports a device-side timeout as HQ_ERR_TIMEOUT; when NULL it
+ *          only enqueues work.
+ * Device scratch (split matrices, per-warp norm sums) from the stream-ordered
+ * allocator, released before returning.
+ * Errors: as hq_state_init and hq_apply_blocks; HQ_ERR_TIMEOUT.
+ */
+hq_status hq_simulate(void *state, int n, hq_dtype dt, const char *tokens, const hq_gate *gates, int G,
+                      const hq_config *cfg, double *norm2_host, void *stream);
+
+/*
  * hq_plan_passes -- the plan HQ_ENGINE_TC_PASS executes for these gates (for
  * inspection and tests).  A pass holds a tile of 13 physical bit positions
  * that includes bits 0..6, applies up to max_blocks (1 or 2) of the gates to

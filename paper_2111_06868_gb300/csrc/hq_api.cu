@@ -290,6 +290,43 @@ hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates,
     return HQ_OK;
 }
 
+hq_status hq_simulate(void *state, int n, hq_dtype dt, const char *tokens, const hq_gate *gates, int G,
+                      const hq_config *cfg, double *norm2_host, void *stream)
+{
+    hq_status st = check_state(state, n, dt);
+    if (st != HQ_OK) return st;
+    if (G < 0) return HQ_ERR_ARG;
+    if (G > 0 && !gates) return HQ_ERR_NULL;
+    if (tokens)
+        for (int q = 0; q < n; ++q)
+            if (tokens[q] != '0' && tokens[q] != '1' && tokens[q] != '+' && tokens[q] != '-') return HQ_ERR_TOKEN;
+    const int engine = cfg ? cfg->engine : HQ_ENGINE_AUTO;
+    const int tc_min_k = (cfg && cfg->tc_min_k > 0) ? cfg->tc_min_k : 5;
+    if (engine < HQ_ENGINE_AUTO || engine > HQ_ENGINE_DF) return HQ_ERR_ARG;
+    if ((engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16 || engine == HQ_ENGINE_TC_PASS) && dt != HQ_C64)
+        return HQ_ERR_DTYPE;
+    if (engine == HQ_ENGINE_DF && dt != HQ_C128) return HQ_ERR_DTYPE;
+    for (int g = 0; g < G; ++g) {
+        if ((st = check_qubits(n, gates[g].k, gates[g].qubits, HQ_MAX_K)) != HQ_OK) return st;
+        if (!gates[g].matrix) return HQ_ERR_NULL;
+    }
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16) {
+        st = launch_tc_simulate(state, n, tokens, gates, G, tc_min_k, engine == HQ_ENGINE_TC_BF16, norm2_host, s);
+    } else {
+        if ((st = launch_init(state, n, dt, tokens, 1, s)) != HQ_OK) return st;
+        if ((st = hq_apply_blocks(state, n, dt, gates, G, cfg, stream)) != HQ_OK) return st;
+        if (norm2_host) {
+            hq_pauli_term id;
+            std::memset(&id, 0, sizeof(id));
+            id.coeff = 1.0;
+            st = launch_expectation(state, n, dt, &id, 1, norm2_host, s);
+        }
+    }
+    if (st != HQ_OK || !norm2_host) return st;
+    return device_error_status();
+}
+
 hq_status hq_reduced_density_matrix(const void *state, int n, hq_dtype dt, const int *qubits, int k,
                                     double *rho_host, void *stream)
 {

@@ -273,6 +273,11 @@ hq_status device_error_status();
 // split matrices are prepared on the host and copied in one transfer.
 hq_status launch_tc_blocks(void *state, int n, const hq_gate *gates, int G, int tc_min_k, int split_bf16,
                            cudaStream_t s);
+// The same with the product state of `tokens` as input and, when norm2_host
+// is set, the FP64 squared norm of the result (synchronous then): the first
+// and last blocks fold the initialisation and the norm in when they run on k_tc.
+hq_status launch_tc_simulate(void *state, int n, const char *tokens, const hq_gate *gates, int G, int tc_min_k,
+                             int split_bf16, double *norm2_host, cudaStream_t s);
 
 // Tile passes (k_pass.cu).  One pass holds a 13-bit tile that contains the 7
 // lowest physical bits, applies up to two fused blocks to it and permutes its

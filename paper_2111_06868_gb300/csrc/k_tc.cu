@@ -58,6 +58,13 @@ struct TcParams {
     float out_mul;            // 1 / s_M
     TileLoad ld;              // how tiles are copied into shared memory
     int am_pair16;            // AM mapping: a thread's two amplitudes are adjacent (16-byte reads)
+    // synth != 0: the input is the Sec. 4.1 product state, computed in place of
+    // reading the tile: amplitude of flat index x (below 2^n) is
+    // [x & init_fixed == init_val] (-1)^popc(x & init_minus) init_amp
+    int synth;
+    float init_amp;
+    uint64_t init_fixed, init_val, init_minus;
+    double *norm_part;        // non-null: sums of |out|^2 per epilogue warp, [gridDim.x][8]
 };
 
 template <int K>
@@ -170,17 +177,35 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                 b = xt[am_gb[gi] + am_off[2 * j + 1]];
             }
         };
-        if (warp == 0 && int64_t(blockIdx.x) < g.total_tiles) load_tile(blockIdx.x, 0);
-        int it = 0, issued = 0, loaded = (int64_t(blockIdx.x) < g.total_tiles) ? 1 : 0;
+        const bool synth = p.synth != 0;
+        if (!synth && warp == 0 && int64_t(blockIdx.x) < g.total_tiles) load_tile(blockIdx.x, 0);
+        int it = 0, issued = 0, loaded = (!synth && int64_t(blockIdx.x) < g.total_tiles) ? 1 : 0;
         float prov = 0.f;  // scale of the largest tile maximum seen so far (0: none yet)
         for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
             const int buf = it & 1;
             // the buffer of tile it-1 was read by every producer before the last barrier
-            if (t + gridDim.x < g.total_tiles) {
+            if (!synth && t + gridDim.x < g.total_tiles) {
                 if (warp == 0) load_tile(t + gridDim.x, buf ^ 1);
                 ++loaded;
             }
-            const bool landed = mbar_wait(&bar[4 + buf], uint32_t((it / 2) & 1), abort_flag, &g_device_error);
+            bool landed = true;
+            if (synth) {
+                // the product state's amplitudes of tile t, written into buffer
+                // buf (its last reader, tile it-2, is behind every producer)
+                float2 *xw = reinterpret_cast<float2 *>(smem + Lay::kOffTile + buf * Lay::kTileBytes);
+                const int64_t tb = tile_base(g, t);
+                const uint64_t in_state = (uint64_t(1) << g.n) - 1;
+                const int cmask = (1 << g.c) - 1;
+                for (int i = tid; i < (1 << g.L); i += NP) {
+                    const uint64_t y = uint64_t(tb + g.runoff[i >> g.c] + (i & cmask)) & in_state;
+                    float v = ((y & p.init_fixed) == p.init_val) ? p.init_amp : 0.f;
+                    if (__popcll(y & p.init_minus) & 1) v = -v;
+                    xw[i] = make_float2(v, 0.f);
+                }
+                named_bar_sync(3, NP);
+            } else {
+                landed = mbar_wait(&bar[4 + buf], uint32_t((it / 2) & 1), abort_flag, &g_device_error);
+            }
             const float2 *xt = reinterpret_cast<const float2 *>(smem + Lay::kOffTile + buf * Lay::kTileBytes);
             const float2 *x = xt + ibase;
             // One power-of-two scale per tile.  The split needs only that no
@@ -336,8 +361,29 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
             for (int j = 0; j < CP / 8; ++j) am_go[j] = g.goff[part * (CP / 2) + 4 * j + p4];
         }
         int it = 0;
+        const bool want_norm = p.norm_part != nullptr;
+        // this thread's sum of |out|^2 within a tile as a float pair: each
+        // square split exactly into its rounded value and error (fmaf), the
+        // rounded squares added by TwoSum (Knuth) into ns, every error term
+        // added plainly into ne (they are ~2^-24 of the sum, so their own
+        // rounding is ~2^-48 of it); FP64 across tiles.  The _rn intrinsics
+        // keep the compiler from contracting a product and a sum into one FMA.
+        double nsum = 0.0;
+        auto sq_acc = [](float &sum, float &err, float2 o) {
+            const float hx = __fmul_rn(o.x, o.x), hy = __fmul_rn(o.y, o.y);
+            float e = __fadd_rn(fmaf(o.x, o.x, -hx), fmaf(o.y, o.y, -hy));
+            auto two_sum = [&](float b) {
+                const float t = __fadd_rn(sum, b), bp = __fsub_rn(t, sum), ap = __fsub_rn(t, bp);
+                e = __fadd_rn(e, __fadd_rn(__fsub_rn(sum, ap), __fsub_rn(b, bp)));
+                sum = t;
+            };
+            two_sum(hx);
+            two_sum(hy);
+            err = __fadd_rn(err, e);
+        };
         for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
             const int buf = it & 1;
+            float ns = 0.f, ne = 0.f;
             // warp-uniform exit: tcgen05.ld below is .sync.aligned
             if (!__all_sync(0xffffffffu, mbar_wait(&bar[buf], uint32_t((it / 2) & 1), abort_flag, &g_device_error))) break;
             tc_fence_after();
@@ -360,11 +406,13 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                             o.x = __uint_as_float(v[4 * j + 2 * u]) * mul;
                             o.y = __uint_as_float(v[4 * j + 2 * u + 1]) * mul;
                             gd[am_go[j]] = o;
+                            if (want_norm) sq_acc(ns, ne, o);
                         }
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(&bar[2 + buf]);
+                if (want_norm) nsum += double(ns) + double(ne);
                 continue;
             }
             const float mul = inv_scale[buf] * p.out_mul;
@@ -383,6 +431,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                         o.x = __uint_as_float(v[2 * u]) * mul;
                         o.y = __uint_as_float(v[2 * u + 1]) * mul;
                         gdst[g.goff[c0 / 2 + u]] = o;
+                        if (want_norm) sq_acc(ns, ne, o);
                     }
                 }
             };
@@ -390,6 +439,12 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
             else drain_part(std::integral_constant<int, SPLIT - 1>{});
             tc_fence_before();
             mbar_arrive(&bar[2 + buf]);
+            if (want_norm) nsum += double(ns) + double(ne);
+        }
+        if (want_norm) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nsum += __shfl_xor_sync(0xffffffffu, nsum, o);
+            if ((tid & 31) == 0) p.norm_part[size_t(blockIdx.x) * 8 + ew] = nsum;
         }
     }
     tc_fence_before();
@@ -656,6 +711,8 @@ static void prepare_tc(void *state, int n, const int *qubits, const double *mat,
     sort_targets(K, qubits, mat, qs, ms);
     make_geom(p.g, n, K, qs, K + 7, nstates);
     p.out_mul = prepare_b<BF16>(K, ms.data(), out.b);
+    p.synth = 0;
+    p.norm_part = nullptr;
     make_tile_map(p.g, n, nstates, state, p.ld, out.tmap);
     out.launch = prefer_am(p.g, K, p.am_pair16) ? &launch_tc<K, BF16, true> : &launch_tc<K, BF16, false>;
 }
@@ -749,19 +806,36 @@ static void widen_to_6(int n, const hq_gate &gt, hq_gate &w, std::vector<double>
 // the buffer's allocation, so an upload never waits behind this call's
 // kernels (or behind a large copy the caller queued after them).  The other
 // gates go through launch_gate.
+// What hq_simulate adds to a block list: the first block's input computed
+// from the product state (no state read, no separate initialisation) and the
+// squared norm summed by the last block's epilogue (no separate read).
+struct TcListExtras {
+    bool synth_first = false;
+    float init_amp = 0.f;
+    uint64_t init_fixed = 0, init_val = 0, init_minus = 0;
+    bool norm_last = false;
+    std::vector<double> *norm_slots = nullptr;  // out (host): the epilogue warps' partial sums
+};
+
 static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G, int tc_min_k, int split_bf16,
-                                int64_t nstates, cudaStream_t s)
+                                int64_t nstates, cudaStream_t s, const TcListExtras *ex = nullptr)
 {
     constexpr int kFirstChunk = 2, kChunk = 4;
     size_t bytes = 0;
     for (int g = 0; g < G; ++g)
         if (tc_eligible(n, gates[g], tc_min_k)) bytes += tc_matrix_bytes(n >= 13 ? 6 : gates[g].k);
+    // norm partials after the matrices: one slot per epilogue warp of every CTA
+    const bool norm = ex && ex->norm_last && G > 0 && tc_eligible(n, gates[G - 1], tc_min_k);
+    const size_t norm_off = bytes, norm_slots = size_t(sm_count()) * 4 * 8;
+    if (norm) bytes += norm_slots * sizeof(double);
     char *dmat = nullptr;
     if (bytes && (injected_alloc_failure() || cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess))
         return HQ_ERR_ALLOC;
     hq_status st = HQ_OK;
+    double *norm_part = norm ? reinterpret_cast<double *>(dmat + norm_off) : nullptr;
+    if (norm) st = cuda_status("clear norm partials", cudaMemsetAsync(norm_part, 0, norm_slots * sizeof(double), s));
     cudaEvent_t allocated = call_event();
-    if (!allocated) st = HQ_ERR_CUDA;
+    if (st == HQ_OK && !allocated) st = HQ_ERR_CUDA;
     if (st == HQ_OK) st = cuda_status("record allocation", cudaEventRecord(allocated, s));
     size_t off = 0;
     std::vector<TcPrepared> prep;
@@ -784,6 +858,14 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
             }
             b.p.bmat = reinterpret_cast<const uint4 *>(dmat + off + host.size() * sizeof(uint16_t));
             host.insert(host.end(), b.b.begin(), b.b.end());
+            if (g == 0 && ex && ex->synth_first) {
+                b.p.synth = 1;
+                b.p.init_amp = ex->init_amp;
+                b.p.init_fixed = ex->init_fixed;
+                b.p.init_val = ex->init_val;
+                b.p.init_minus = ex->init_minus;
+            }
+            if (g == G - 1 && norm) b.p.norm_part = norm_part;
         }
         if (!host.empty()) {
             st = upload_side(dmat + off, host.data(), host.size() * sizeof(uint16_t), s, allocated);
@@ -800,8 +882,60 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
         }
         g0 = g1;
     }
+    if (st == HQ_OK && norm) {
+        ex->norm_slots->assign(norm_slots, 0.0);
+        st = cuda_status("read norm partials", cudaMemcpyAsync(ex->norm_slots->data(), norm_part,
+                                                               norm_slots * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     if (dmat) cudaFreeAsync(dmat, s);
     return st;
+}
+
+// Sec. 4.2 simulate(circuit, initial_state) on the tensor-core engines
+// (complex64): the product state of `tokens`, the blocks in order, and the
+// FP64 squared norm when norm2_host is set.  When the first block runs on
+// k_tc its tiles are computed from the tokens instead of being read (the
+// state is not initialised separately); when the last one does, its epilogue
+// sums |out|^2 (per thread: exact squares, a float-pair sum by TwoSum within
+// a tile, FP64 across tiles; the host adds the warps' sums in a fixed
+// order).
+// Otherwise the initialisation kernel and the streaming norm run as separate
+// passes.
+hq_status launch_tc_simulate(void *state, int n, const char *tokens, const hq_gate *gates, int G, int tc_min_k,
+                             int split_bf16, double *norm2_host, cudaStream_t s)
+{
+    TcListExtras ex;
+    int m = 0;
+    for (int q = 0; q < n; ++q) {
+        const char t = tokens ? tokens[q] : '0';
+        const uint64_t bit = 1ull << (n - 1 - q);
+        if (t == '0') ex.init_fixed |= bit;
+        else if (t == '1') { ex.init_fixed |= bit; ex.init_val |= bit; }
+        else if (t == '+') ++m;
+        else if (t == '-') { ++m; ex.init_minus |= bit; }
+        else return HQ_ERR_TOKEN;
+    }
+    ex.init_amp = float(std::pow(2.0, -0.5 * m));  // the value hq_state_init writes
+    ex.synth_first = G > 0 && tc_eligible(n, gates[0], tc_min_k);
+    ex.norm_last = norm2_host != nullptr;
+    std::vector<double> slots;
+    ex.norm_slots = &slots;
+    hq_status st = HQ_OK;
+    if (!ex.synth_first && (st = launch_init(state, n, HQ_C64, tokens, 1, s)) != HQ_OK) return st;
+    if ((st = launch_tc_list(state, n, gates, G, tc_min_k, split_bf16, 1, s, &ex)) != HQ_OK) return st;
+    if (!norm2_host) return HQ_OK;
+    const bool fused_norm = G > 0 && tc_eligible(n, gates[G - 1], tc_min_k);
+    if (!fused_norm) {
+        hq_pauli_term id;
+        std::memset(&id, 0, sizeof(id));
+        id.coeff = 1.0;
+        return launch_expectation(state, n, HQ_C64, &id, 1, norm2_host, s);
+    }
+    if ((st = cuda_status("simulate sync", cudaStreamSynchronize(s))) != HQ_OK) return st;
+    double sum = 0.0;
+    for (double v : slots) sum += v;
+    *norm2_host = sum;
+    return HQ_OK;
 }
 
 hq_status launch_tc_block(void *state, int n, int k, const int *qubits, const double *matrix, int64_t nstates,

@@ -124,6 +124,7 @@ def load(path: str | None = None):
         "hq_plan_passes": ([I, V, I, I, V, I], I),
         "hq_apply_gate": ([V, I, I, V, I, V, V], I),
         "hq_apply_blocks": ([V, I, I, V, I, V, V], I),
+        "hq_simulate": ([V, I, I, ctypes.c_char_p, V, I, V, P(D), V], I),
         "hq_expectation": ([V, I, I, V, I, P(D), V], I),
         "hq_expectation_static": ([V, I, I, V, I, P(D), V], I),
         "hq_adjoint_workspace_bytes": ([I, I, I, I, I, I], ctypes.c_size_t),
@@ -370,6 +371,26 @@ def hq_apply_blocks(state, blocks: Iterable, engine: str | int = "auto", tc_min_
     cfg = hq_config(ENGINES[engine] if isinstance(engine, str) else int(engine), tc_min_k)
     _check(load().hq_apply_blocks(ptr, n, dt, arr, G, ctypes.byref(cfg), _stream(stream)), "hq_apply_blocks")
     return state
+
+
+def hq_simulate(state, blocks: Iterable, tokens: str | None = None, engine: str | int = "auto", tc_min_k: int = 5,
+                norm: bool = True, stream=None):
+    """state <- blocks applied to the product state of `tokens` (None: |0..0>).
+    Returns the FP64 squared norm of the result when `norm` (the call then
+    synchronises), else None."""
+    ptr, n, dt = _state_args(state)
+    tok = None
+    if tokens is not None:
+        tok = (tokens * n if len(tokens) == 1 else tokens).encode()
+        if len(tok) != n:
+            raise ValueError("need one token per qubit")
+    keep: list = []
+    arr, G = _gates_array(blocks, keep)
+    cfg = hq_config(ENGINES[engine] if isinstance(engine, str) else int(engine), tc_min_k)
+    out = ctypes.c_double(0.0)
+    _check(load().hq_simulate(ptr, n, dt, tok, arr, G, ctypes.byref(cfg), ctypes.byref(out) if norm else None,
+                              _stream(stream)), "hq_simulate")
+    return out.value if norm else None
 
 
 def hq_reduced_density_matrix(state, qubits: Sequence[int], stream=None) -> np.ndarray:
