@@ -499,9 +499,10 @@ def measure_fp_peaks(N=8192, reps=5):
 
 
 def measure_c128(args, circ):
-    """Configuration 2 in complex128: per gate and fused k <= 4 (exact FP64
-    kernels, no tensor cores); rates in unfused gate-apps/s, effective GB/s
-    = bytes of one read and write of the state per launch."""
+    """Configuration 2 in complex128: per gate and fused k <= 4 on the FP64
+    kernels, in double-float, and fused k <= 3, 4 on the tensor cores (exact
+    digit-slice products); rates in unfused gate-apps/s, effective GB/s =
+    bytes of one read and write of the state per launch."""
     import torch
 
     G = len(circ.gates)
@@ -525,6 +526,16 @@ def measure_c128(args, circ):
         st, tk = _time_blocks(30, bk, "df", torch.complex128)
         res[f"fused_k{kk}_df"] = {"blocks": len(bk), "gate_apps_per_s": G / tk, "s": tk,
                                   "GBps": len(bk) * 2 * (1 << 30) * 16 / tk / 1e9}
+        del st
+    # dense 3- and 4-qubit blocks on the tensor cores as exact FP16 digit-slice
+    # products (HQ_ENGINE_TC_C128), the others in double-float
+    peaks, _ = load_peaks()
+    for kk in (3, 4):
+        bk = fuse(hq, 30, circ.gates, kk, args)
+        st, tk = _time_blocks(30, bk, "tc_c128", torch.complex128)
+        gbs = len(bk) * 2 * (1 << 30) * 16 / tk / 1e9
+        res[f"fused_k{kk}_tc_c128"] = {"blocks": len(bk), "gate_apps_per_s": G / tk, "s": tk, "GBps": gbs,
+                                       "hbm_frac": gbs / peaks["hbm_gbs"]}
         del st
     torch.cuda.empty_cache()
     return res

@@ -98,6 +98,10 @@ typedef struct {
 #define HQ_ENGINE_DF 5        /* complex128 only: diagonal gates and monomial / dense gates of k <= 4 in
                                  double-float arithmetic (48-bit hi + lo float pairs) on the FP32 pipes;
                                  controlled gates and k = 5, 6 blocks as HQ_ENGINE_CUDA_CORE */
+#define HQ_ENGINE_TC_C128 6   /* complex128 only: dense k = 3, 4 blocks (n >= 11; k = 3 widened to 4) on
+                                 tcgen05 tensor cores as exact FP16 products of 8-bit signed digit slices
+                                 (five per operand, FP32 accumulation exact, levels joined in 64-bit
+                                 integers); all other gates as HQ_ENGINE_DF */
 typedef struct {
     int engine;  /* HQ_ENGINE_* */
     int tc_min_k; /* blocks with k >= tc_min_k use the tensor-core engine (default 5) */
@@ -422,7 +426,8 @@ hq_status hq_apply_gate(void *state, int n, hq_dtype dt, const int *qubits, int 
  * hq_apply_blocks -- apply G gates / fused blocks in order (the evolution
  * loop of Sec. 4.2), choosing a kernel per block as configured (cfg NULL =
  * HQ_ENGINE_AUTO).  Tensor-core engines apply only to complex64 states,
- * HQ_ENGINE_DF only to complex128 states (HQ_ERR_DTYPE otherwise).
+ * HQ_ENGINE_DF and HQ_ENGINE_TC_C128 only to complex128 states (HQ_ERR_DTYPE
+ * otherwise).
  * HQ_ENGINE_TC_PASS applies the same operators in the same order (blocks
  * with disjoint targets may swap), up to two per read and write of the state:
  * see hq_plan_passes.  It moves qubits between bit positions while it runs and
@@ -444,13 +449,13 @@ hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates,
  * |0..0>); with norm2_host set, also the squared norm sum |psi_x|^2 of the
  * result, accumulated in double.  The same result as hq_state_init,
  * hq_apply_blocks and hq_expectation of the identity in a row, in fewer
- * passes over the state on the tensor-core engines (complex64): a first
+ * passes over the state on the tensor-core engines (complex64, n >= 13): a first
  * block that runs on the tensor cores computes its input amplitudes from the
  * tokens instead of reading an initialised state, and a last one that does
- * sums |psi_x|^2 of what it writes (each square split exactly into two
- * floats, float-pair sums by TwoSum within a tile, FP64 across tiles, the
- * per-warp sums added on the host in a fixed order: the exact sum of the
- * stored amplitudes to ~1e-13 relative).  Other engines
+ * sums |psi_x|^2 of what it writes (FP32 within a tile, in chains of at
+ * most 16 squares, FP64 across tiles, the per-warp sums added on the host in
+ * a fixed order: within 1e-8 relative of the exact sum of the stored
+ * amplitudes).  Other engines
  * and blocks run the separate passes.
  *   state: out, 2^n amplitudes (DEVICE, caller-owned, 16-byte aligned); its
  *          previous contents are never read.

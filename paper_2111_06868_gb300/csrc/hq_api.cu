@@ -269,10 +269,10 @@ hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates,
     if (G > 0 && !gates) return HQ_ERR_NULL;
     const int engine = cfg ? cfg->engine : HQ_ENGINE_AUTO;
     const int tc_min_k = (cfg && cfg->tc_min_k > 0) ? cfg->tc_min_k : 5;
-    if (engine < HQ_ENGINE_AUTO || engine > HQ_ENGINE_DF) return HQ_ERR_ARG;
+    if (engine < HQ_ENGINE_AUTO || engine > HQ_ENGINE_TC_C128) return HQ_ERR_ARG;
     if ((engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16 || engine == HQ_ENGINE_TC_PASS) && dt != HQ_C64)
         return HQ_ERR_DTYPE;
-    if (engine == HQ_ENGINE_DF && dt != HQ_C128) return HQ_ERR_DTYPE;
+    if ((engine == HQ_ENGINE_DF || engine == HQ_ENGINE_TC_C128) && dt != HQ_C128) return HQ_ERR_DTYPE;
     for (int g = 0; g < G; ++g) {
         if ((st = check_qubits(n, gates[g].k, gates[g].qubits, HQ_MAX_K)) != HQ_OK) return st;
         if (!gates[g].matrix) return HQ_ERR_NULL;
@@ -302,10 +302,10 @@ hq_status hq_simulate(void *state, int n, hq_dtype dt, const char *tokens, const
             if (tokens[q] != '0' && tokens[q] != '1' && tokens[q] != '+' && tokens[q] != '-') return HQ_ERR_TOKEN;
     const int engine = cfg ? cfg->engine : HQ_ENGINE_AUTO;
     const int tc_min_k = (cfg && cfg->tc_min_k > 0) ? cfg->tc_min_k : 5;
-    if (engine < HQ_ENGINE_AUTO || engine > HQ_ENGINE_DF) return HQ_ERR_ARG;
+    if (engine < HQ_ENGINE_AUTO || engine > HQ_ENGINE_TC_C128) return HQ_ERR_ARG;
     if ((engine == HQ_ENGINE_TC_F16 || engine == HQ_ENGINE_TC_BF16 || engine == HQ_ENGINE_TC_PASS) && dt != HQ_C64)
         return HQ_ERR_DTYPE;
-    if (engine == HQ_ENGINE_DF && dt != HQ_C128) return HQ_ERR_DTYPE;
+    if ((engine == HQ_ENGINE_DF || engine == HQ_ENGINE_TC_C128) && dt != HQ_C128) return HQ_ERR_DTYPE;
     for (int g = 0; g < G; ++g) {
         if ((st = check_qubits(n, gates[g].k, gates[g].qubits, HQ_MAX_K)) != HQ_OK) return st;
         if (!gates[g].matrix) return HQ_ERR_NULL;

@@ -297,6 +297,13 @@ hq_status batch_error_status();
 // HQ_ERR_TIMEOUT (and the flag cleared) if a staged expectation pass gave up
 // a bounded wait (k_expect_reg.cu); device_error_status() checks it too.
 hq_status expect_error_status();
+// complex128 blocks of k = 3, 4 on the tensor cores (k_tcz.cu): dense blocks
+// on n >= 11 qubits; 3-qubit blocks run widened to 4.  The error status as
+// above for its bounded waits.
+bool tcz_eligible(int n, int k, const double *mat);
+hq_status launch_tcz_block(void *state, int n, int k, const int *qubits, const double *mat, int64_t nstates,
+                           cudaStream_t s);
+hq_status tcz_error_status();
 
 // validation helpers (hq_api.cu)
 hq_status check_qubits(int n, int k, const int *qubits, int kmax);

@@ -818,8 +818,13 @@ static hq_status dispatch(void *state, int n, int k, const int *qubits, const do
         }
     }
     // complex128 in double-float arithmetic on the FP32 pipes (k_apply_df.cu)
-    if constexpr (sizeof(R) == 8)
-        if (engine == HQ_ENGINE_DF && df_supported(k, mat)) return launch_gate_df(state, n, k, qubits, mat, nstates, s);
+    if constexpr (sizeof(R) == 8) {
+        // dense 3- and 4-qubit blocks on the tensor cores (k_tcz.cu), the rest as HQ_ENGINE_DF
+        if (engine == HQ_ENGINE_TC_C128 && tcz_eligible(n, k, mat))
+            return launch_tcz_block(state, n, k, qubits, mat, nstates, s);
+        if ((engine == HQ_ENGINE_DF || engine == HQ_ENGINE_TC_C128) && df_supported(k, mat))
+            return launch_gate_df(state, n, k, qubits, mat, nstates, s);
+    }
     if (is_diagonal(k, mat)) {
         switch (k) {
         case 1: return run_diag<R, 1>(state, n, qubits, mat, nstates, s);

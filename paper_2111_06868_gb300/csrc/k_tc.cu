@@ -61,9 +61,11 @@ struct TcParams {
     // synth != 0: the input is the Sec. 4.1 product state, computed in place of
     // reading the tile: amplitude of flat index x (below 2^n) is
     // [x & init_fixed == init_val] (-1)^popc(x & init_minus) init_amp
+    // (k_tc<..., EX = true> only)
     int synth;
     float init_amp;
     uint64_t init_fixed, init_val, init_minus;
+    uint64_t tile_bits;       // flat bits a tile spans: a tile whose other bits miss init_val is all zero
     double *norm_part;        // non-null: sums of |out|^2 per epilogue warp, [gridDim.x][8]
 };
 
@@ -98,7 +100,10 @@ template <int K> __host__ __device__ constexpr int tc_threads() { return 2 * kTc
 // two adjacent amplitudes per 8-column slice, moved with the .16x256b TMEM
 // shapes (conflict-free reads and whole-sector stores when the lowest tile
 // bits are targets).
-template <int K, bool BF16, bool AM>
+//
+// EX (6-qubit kernels of hq_simulate only): the first block's input may be
+// the product state (synth) and the last block's epilogue may sum the norm.
+template <int K, bool BF16, bool AM, bool EX>
 __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
     k_tc(const TcParams p, const __grid_constant__ CUtensorMap tmap, float2 *__restrict__ state)
 {
@@ -177,7 +182,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                 b = xt[am_gb[gi] + am_off[2 * j + 1]];
             }
         };
-        const bool synth = p.synth != 0;
+        const bool synth = EX && p.synth != 0;
         if (!synth && warp == 0 && int64_t(blockIdx.x) < g.total_tiles) load_tile(blockIdx.x, 0);
         int it = 0, issued = 0, loaded = (!synth && int64_t(blockIdx.x) < g.total_tiles) ? 1 : 0;
         float prov = 0.f;  // scale of the largest tile maximum seen so far (0: none yet)
@@ -188,21 +193,26 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                 if (warp == 0) load_tile(t + gridDim.x, buf ^ 1);
                 ++loaded;
             }
-            bool landed = true;
+            bool landed = true, zero_tile = false;
             if (synth) {
-                // the product state's amplitudes of tile t, written into buffer
-                // buf (its last reader, tile it-2, is behind every producer)
-                float2 *xw = reinterpret_cast<float2 *>(smem + Lay::kOffTile + buf * Lay::kTileBytes);
+                // the product state's amplitudes of tile t: none unless the
+                // bits outside the tile match the fixed tokens (uniform per
+                // tile); else written into buffer buf (its last reader, tile
+                // it-2, is behind every producer)
                 const int64_t tb = tile_base(g, t);
                 const uint64_t in_state = (uint64_t(1) << g.n) - 1;
-                const int cmask = (1 << g.c) - 1;
-                for (int i = tid; i < (1 << g.L); i += NP) {
-                    const uint64_t y = uint64_t(tb + g.runoff[i >> g.c] + (i & cmask)) & in_state;
-                    float v = ((y & p.init_fixed) == p.init_val) ? p.init_amp : 0.f;
-                    if (__popcll(y & p.init_minus) & 1) v = -v;
-                    xw[i] = make_float2(v, 0.f);
+                zero_tile = ((uint64_t(tb) ^ p.init_val) & p.init_fixed & ~p.tile_bits & in_state) != 0;
+                if (!zero_tile) {
+                    float2 *xw = reinterpret_cast<float2 *>(smem + Lay::kOffTile + buf * Lay::kTileBytes);
+                    const int cmask = (1 << g.c) - 1;
+                    for (int i = tid; i < (1 << g.L); i += NP) {
+                        const uint64_t y = uint64_t(tb + g.runoff[i >> g.c] + (i & cmask)) & in_state;
+                        float v = ((y & p.init_fixed) == p.init_val) ? p.init_amp : 0.f;
+                        if (__popcll(y & p.init_minus) & 1) v = -v;
+                        xw[i] = make_float2(v, 0.f);
+                    }
+                    named_bar_sync(3, NP);
                 }
-                named_bar_sync(3, NP);
             } else {
                 landed = mbar_wait(&bar[4 + buf], uint32_t((it / 2) & 1), abort_flag, &g_device_error);
             }
@@ -236,6 +246,32 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
             // returns the largest |component| seen
             auto convert = [&](float sc) -> float {
                 float mx = 0.f;
+                if (zero_tile) {  // all zeros (FP16 and BF16 zero are the zero word): no reads
+                    if constexpr (AM) {
+                        const uint32_t a_hi = tmem + uint32_t(buf) * Lay::kBufCols + uint32_t(part * DP);
+                        uint32_t zv[DP / 2];
+#pragma unroll
+                        for (int u = 0; u < DP / 2; ++u) zv[u] = 0u;
+#pragma unroll
+                        for (int hf = 0; hf < 2; ++hf) {
+                            const uint32_t lanes = uint32_t(quarter * 32 + 16 * hf) << 16;
+                            tmem_st_16x256b(a_hi + lanes, zv);
+                            tmem_st_16x256b(a_hi + uint32_t(D) + lanes, zv);
+                        }
+                    } else {
+                        const uint32_t a_hi = tmem + lane_off + uint32_t(buf) * Lay::kBufCols;
+                        uint32_t zv[16];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) zv[u] = 0u;
+#pragma unroll
+                        for (int c0 = 0; c0 < DP; c0 += 16) {
+                            tmem_st16(a_hi + uint32_t(part * DP + c0), zv);
+                            tmem_st16(a_hi + uint32_t(D + part * DP + c0), zv);
+                        }
+                    }
+                    tmem_wait_st();
+                    return 0.f;
+                }
                 if constexpr (AM) {
                     const uint32_t a_hi = tmem + uint32_t(buf) * Lay::kBufCols + uint32_t(part * DP);
                     const uint32_t a_lo = a_hi + uint32_t(D);
@@ -361,29 +397,13 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
             for (int j = 0; j < CP / 8; ++j) am_go[j] = g.goff[part * (CP / 2) + 4 * j + p4];
         }
         int it = 0;
-        const bool want_norm = p.norm_part != nullptr;
-        // this thread's sum of |out|^2 within a tile as a float pair: each
-        // square split exactly into its rounded value and error (fmaf), the
-        // rounded squares added by TwoSum (Knuth) into ns, every error term
-        // added plainly into ne (they are ~2^-24 of the sum, so their own
-        // rounding is ~2^-48 of it); FP64 across tiles.  The _rn intrinsics
-        // keep the compiler from contracting a product and a sum into one FMA.
+        const bool want_norm = EX && p.norm_part != nullptr;
+        // this thread's sum of |out|^2: FP32 within a tile (four partial sums,
+        // chains of at most 16 squares), FP64 across tiles
         double nsum = 0.0;
-        auto sq_acc = [](float &sum, float &err, float2 o) {
-            const float hx = __fmul_rn(o.x, o.x), hy = __fmul_rn(o.y, o.y);
-            float e = __fadd_rn(fmaf(o.x, o.x, -hx), fmaf(o.y, o.y, -hy));
-            auto two_sum = [&](float b) {
-                const float t = __fadd_rn(sum, b), bp = __fsub_rn(t, sum), ap = __fsub_rn(t, bp);
-                e = __fadd_rn(e, __fadd_rn(__fsub_rn(sum, ap), __fsub_rn(b, bp)));
-                sum = t;
-            };
-            two_sum(hx);
-            two_sum(hy);
-            err = __fadd_rn(err, e);
-        };
         for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
             const int buf = it & 1;
-            float ns = 0.f, ne = 0.f;
+            float nq[4] = {0.f, 0.f, 0.f, 0.f};
             // warp-uniform exit: tcgen05.ld below is .sync.aligned
             if (!__all_sync(0xffffffffu, mbar_wait(&bar[buf], uint32_t((it / 2) & 1), abort_flag, &g_device_error))) break;
             tc_fence_after();
@@ -406,13 +426,16 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                             o.x = __uint_as_float(v[4 * j + 2 * u]) * mul;
                             o.y = __uint_as_float(v[4 * j + 2 * u + 1]) * mul;
                             gd[am_go[j]] = o;
-                            if (want_norm) sq_acc(ns, ne, o);
+                            if (want_norm) {
+                                nq[2 * u] = fmaf(o.x, o.x, nq[2 * u]);
+                                nq[2 * u + 1] = fmaf(o.y, o.y, nq[2 * u + 1]);
+                            }
                         }
                     }
                 }
                 tc_fence_before();
                 mbar_arrive(&bar[2 + buf]);
-                if (want_norm) nsum += double(ns) + double(ne);
+                if (want_norm) nsum += (double(nq[0]) + double(nq[1])) + (double(nq[2]) + double(nq[3]));
                 continue;
             }
             const float mul = inv_scale[buf] * p.out_mul;
@@ -431,7 +454,10 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
                         o.x = __uint_as_float(v[2 * u]) * mul;
                         o.y = __uint_as_float(v[2 * u + 1]) * mul;
                         gdst[g.goff[c0 / 2 + u]] = o;
-                        if (want_norm) sq_acc(ns, ne, o);
+                        if (want_norm) {
+                            nq[2 * (u & 1)] = fmaf(o.x, o.x, nq[2 * (u & 1)]);
+                            nq[2 * (u & 1) + 1] = fmaf(o.y, o.y, nq[2 * (u & 1) + 1]);
+                        }
                     }
                 }
             };
@@ -439,7 +465,7 @@ __global__ void __launch_bounds__(tc_threads<K>(), tc_min_blocks<K>())
             else drain_part(std::integral_constant<int, SPLIT - 1>{});
             tc_fence_before();
             mbar_arrive(&bar[2 + buf]);
-            if (want_norm) nsum += double(ns) + double(ne);
+            if (want_norm) nsum += (double(nq[0]) + double(nq[1])) + (double(nq[2]) + double(nq[3]));
         }
         if (want_norm) {
 #pragma unroll
@@ -678,7 +704,7 @@ static bool prefer_am(const TileGeom &g, int k, int &pair16, double *best_cost =
     return c_am < c_gm;
 }
 
-template <int K, bool BF16, bool AM>
+template <int K, bool BF16, bool AM, bool EX = false>
 static hq_status launch_tc(TcParams &p, const CUtensorMap &tmap, void *state, cudaStream_t s)
 {
     using Lay = TcLayout<K>;
@@ -686,10 +712,10 @@ static hq_status launch_tc(TcParams &p, const CUtensorMap &tmap, void *state, cu
     // its 512 TMEM columns hold (an allocation beyond that would stall).
     constexpr size_t kSmPerSm = 228 * 1024;
     const size_t smem = std::max<size_t>(Lay::kBytes, kSmPerSm / (Lay::kCtasPerSm + 1) + 1024);
-    const void *fn = (const void *)k_tc<K, BF16, AM>;
+    const void *fn = (const void *)k_tc<K, BF16, AM, EX>;
     const int per_sm = std::min(occupancy(fn, tc_threads<K>(), smem), Lay::kCtasPerSm);
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(sm_count()) * per_sm, p.g.total_tiles)));
-    k_tc<K, BF16, AM><<<grid, tc_threads<K>(), smem, s>>>(p, tmap, (float2 *)state);
+    k_tc<K, BF16, AM, EX><<<grid, tc_threads<K>(), smem, s>>>(p, tmap, (float2 *)state);
     return cuda_status("k_tc", cudaGetLastError());
 }
 
@@ -699,6 +725,7 @@ struct TcPrepared {
     TcParams p;
     CUtensorMap tmap;
     hq_status (*launch)(TcParams &, const CUtensorMap &, void *, cudaStream_t);
+    hq_status (*launch_ex)(TcParams &, const CUtensorMap &, void *, cudaStream_t);  // K = 6: the EX kernel
     std::vector<uint16_t> b;
 };
 
@@ -713,8 +740,13 @@ static void prepare_tc(void *state, int n, const int *qubits, const double *mat,
     p.out_mul = prepare_b<BF16>(K, ms.data(), out.b);
     p.synth = 0;
     p.norm_part = nullptr;
+    p.tile_bits = (uint64_t(1) << p.g.c) - 1;
+    for (int h = 0; h < p.g.n_hi; ++h) p.tile_bits |= uint64_t(1) << p.g.hi_bits[h];
     make_tile_map(p.g, n, nstates, state, p.ld, out.tmap);
-    out.launch = prefer_am(p.g, K, p.am_pair16) ? &launch_tc<K, BF16, true> : &launch_tc<K, BF16, false>;
+    const bool am = prefer_am(p.g, K, p.am_pair16);
+    out.launch = am ? &launch_tc<K, BF16, true> : &launch_tc<K, BF16, false>;
+    out.launch_ex = nullptr;
+    if constexpr (K == 6) out.launch_ex = am ? &launch_tc<6, BF16, true, true> : &launch_tc<6, BF16, false, true>;
 }
 
 static void prepare_tc_any(void *state, int n, int k, const int *qubits, const double *mat, int64_t nstates,
@@ -800,7 +832,7 @@ static void widen_to_6(int n, const hq_gate &gt, hq_gate &w, std::vector<double>
 
 // Launches the gates in order: tensor-core blocks take their split matrix
 // from one device buffer allocated up front.  The blocks are prepared on the
-// host in chunks (two blocks, then four at a time, each prepared while the
+// host in chunks (one block, then four at a time, each prepared while the
 // previous chunk's kernels run); each chunk's matrices go up in one copy from
 // pinned staging memory on the library's upload stream, ordered only after
 // the buffer's allocation, so an upload never waits behind this call's
@@ -820,12 +852,12 @@ struct TcListExtras {
 static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G, int tc_min_k, int split_bf16,
                                 int64_t nstates, cudaStream_t s, const TcListExtras *ex = nullptr)
 {
-    constexpr int kFirstChunk = 2, kChunk = 4;
+    constexpr int kFirstChunk = 1, kChunk = 4;
     size_t bytes = 0;
     for (int g = 0; g < G; ++g)
         if (tc_eligible(n, gates[g], tc_min_k)) bytes += tc_matrix_bytes(n >= 13 ? 6 : gates[g].k);
     // norm partials after the matrices: one slot per epilogue warp of every CTA
-    const bool norm = ex && ex->norm_last && G > 0 && tc_eligible(n, gates[G - 1], tc_min_k);
+    const bool norm = ex && ex->norm_last && G > 0 && n >= 13 && tc_eligible(n, gates[G - 1], tc_min_k);
     const size_t norm_off = bytes, norm_slots = size_t(sm_count()) * 4 * 8;
     if (norm) bytes += norm_slots * sizeof(double);
     char *dmat = nullptr;
@@ -858,14 +890,18 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
             }
             b.p.bmat = reinterpret_cast<const uint4 *>(dmat + off + host.size() * sizeof(uint16_t));
             host.insert(host.end(), b.b.begin(), b.b.end());
-            if (g == 0 && ex && ex->synth_first) {
+            if (g == 0 && ex && ex->synth_first && b.launch_ex) {
+                b.launch = b.launch_ex;
                 b.p.synth = 1;
                 b.p.init_amp = ex->init_amp;
                 b.p.init_fixed = ex->init_fixed;
                 b.p.init_val = ex->init_val;
                 b.p.init_minus = ex->init_minus;
             }
-            if (g == G - 1 && norm) b.p.norm_part = norm_part;
+            if (g == G - 1 && norm && b.launch_ex) {
+                b.launch = b.launch_ex;
+                b.p.norm_part = norm_part;
+            }
         }
         if (!host.empty()) {
             st = upload_side(dmat + off, host.data(), host.size() * sizeof(uint16_t), s, allocated);
@@ -896,9 +932,8 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
 // FP64 squared norm when norm2_host is set.  When the first block runs on
 // k_tc its tiles are computed from the tokens instead of being read (the
 // state is not initialised separately); when the last one does, its epilogue
-// sums |out|^2 (per thread: exact squares, a float-pair sum by TwoSum within
-// a tile, FP64 across tiles; the host adds the warps' sums in a fixed
-// order).
+// sums |out|^2 (per thread in FP32 within a tile, FP64 across tiles; the
+// host adds the warps' sums in a fixed order).
 // Otherwise the initialisation kernel and the streaming norm run as separate
 // passes.
 hq_status launch_tc_simulate(void *state, int n, const char *tokens, const hq_gate *gates, int G, int tc_min_k,
@@ -916,7 +951,8 @@ hq_status launch_tc_simulate(void *state, int n, const char *tokens, const hq_ga
         else return HQ_ERR_TOKEN;
     }
     ex.init_amp = float(std::pow(2.0, -0.5 * m));  // the value hq_state_init writes
-    ex.synth_first = G > 0 && tc_eligible(n, gates[0], tc_min_k);
+    // only the 6-qubit kernels (every tensor-core block when n >= 13) fold them in
+    ex.synth_first = G > 0 && n >= 13 && tc_eligible(n, gates[0], tc_min_k);
     ex.norm_last = norm2_host != nullptr;
     std::vector<double> slots;
     ex.norm_slots = &slots;
@@ -924,7 +960,7 @@ hq_status launch_tc_simulate(void *state, int n, const char *tokens, const hq_ga
     if (!ex.synth_first && (st = launch_init(state, n, HQ_C64, tokens, 1, s)) != HQ_OK) return st;
     if ((st = launch_tc_list(state, n, gates, G, tc_min_k, split_bf16, 1, s, &ex)) != HQ_OK) return st;
     if (!norm2_host) return HQ_OK;
-    const bool fused_norm = G > 0 && tc_eligible(n, gates[G - 1], tc_min_k);
+    const bool fused_norm = G > 0 && n >= 13 && tc_eligible(n, gates[G - 1], tc_min_k);
     if (!fused_norm) {
         hq_pauli_term id;
         std::memset(&id, 0, sizeof(id));
@@ -963,6 +999,8 @@ hq_status device_error_status()
     if (bs != HQ_OK) return bs;
     const hq_status es = expect_error_status();
     if (es != HQ_OK) return es;
+    const hq_status zs = tcz_error_status();
+    if (zs != HQ_OK) return zs;
     unsigned int v = 0;
     cudaError_t e = cudaMemcpyFromSymbol(&v, g_device_error, sizeof(v));
     if (e != cudaSuccess) return cuda_status("read device error flag", e);

@@ -23,7 +23,7 @@ HQ_MAX_PAULI = 8
 HQ_C64, HQ_C128 = 0, 1
 HQ_OP_MATRIX, HQ_OP_ROT = 0, 1
 HQ_ENGINE_AUTO, HQ_ENGINE_CUDA_CORE, HQ_ENGINE_TC_F16, HQ_ENGINE_TC_BF16 = 0, 1, 2, 3
-ENGINES = {"auto": 0, "cuda_core": 1, "tc_f16": 2, "tc_bf16": 3, "tc_pass": 4, "df": 5}
+ENGINES = {"auto": 0, "cuda_core": 1, "tc_f16": 2, "tc_bf16": 3, "tc_pass": 4, "df": 5, "tc_c128": 6}
 PASS_RECORD = 29
 
 STATUS = {

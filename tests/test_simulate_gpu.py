@@ -59,12 +59,12 @@ def test_simulate_equals_separate_passes_and_oracle(hq, engine, n):
         assert torch.equal(a, b), tokens
         want = oracle.simulate(circ, tokens=tokens)
         assert rel_l2(a.cpu().numpy().astype(np.complex128), want) <= tol
-        # the fused norm: exact squares, compensated sums, so the exact sum of
-        # the stored floats to 1e-12 relative (the streaming norm of the
-        # separate pass to its own bar)
+        # the fused norm: FP32 sums of at most 16 squares per tile and thread,
+        # FP64 beyond, within 1e-8 relative of the exact sum of the stored
+        # floats (the streaming norm of the separate pass likewise)
         exact = oracle.norm2(a.cpu().numpy().astype(np.complex128))
         sep = hq.hq_expectation(b, [(1.0, ())])
-        assert abs(nrm - exact) <= 1e-12 * exact, (nrm, exact)
+        assert abs(nrm - exact) <= 1e-8 * exact, (nrm, exact)
         assert abs(sep - exact) <= 1e-8, (sep, exact)
         assert abs(nrm - 1.0) <= 2 * tol
 
@@ -79,7 +79,7 @@ def test_simulate_norm_of_a_non_unitary_last_block(hq):
     st = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
     nrm = hq.hq_simulate(st, blocks, engine="tc_f16", tc_min_k=4)
     got = st.cpu().numpy().astype(np.complex128)
-    assert abs(nrm - oracle.norm2(got)) <= 1e-12 * 2.25
+    assert abs(nrm - oracle.norm2(got)) <= 1e-8 * 2.25
     assert abs(nrm - 2.25) <= 2.25 * 4e-5
 
 
