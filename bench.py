@@ -40,7 +40,9 @@ ARITH = {"tc_f16": "fp16 hi+lo split operands (3 products), fp32 accumulate in T
          "tc_bf16": "bf16 hi+lo split operands (3 products), fp32 accumulate in TMEM, fp64 norm",
          "tc_pass": "fp16 hi+lo split operands (3 products), fp32 accumulate in TMEM, fp64 norm",
          "cuda_core": "fp32 FMA on CUDA cores, fp64 norm", "auto": "fp32 FMA on CUDA cores, fp64 norm",
-         "df": "double-float (hi + lo fp32 pairs, error-free products and sums) on CUDA cores, fp64 norm"}
+         "df": "double-float (hi + lo fp32 pairs, error-free products and sums) on CUDA cores, fp64 norm",
+         "tc_c128": "dense k=3,4 blocks: fp16 products of 8-bit digit slices (6 per operand), exact fp32 "
+                    "accumulate per level, levels joined in 64-bit integers; other gates double-float; fp64 norm"}
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
@@ -134,7 +136,7 @@ def kernel_sources_sha(kernel_class):
     figures to the code they were measured on)."""
     import hashlib
 
-    files = {"k_tc": ["k_tc.cu", "hq_tcgen05.cuh"], "k_gather": ["k_apply.cu"], "k_diag": ["k_apply.cu"], "k_block": ["k_apply.cu"]}
+    files = {"k_tcz": ["k_tcz.cu", "hq_tcgen05.cuh"], "k_tc": ["k_tc.cu", "hq_tcgen05.cuh"], "k_gather": ["k_apply.cu"], "k_diag": ["k_apply.cu"], "k_block": ["k_apply.cu"]}
     key = next((k for k in files if kernel_class.startswith(k)), None)
     if key is None:
         return None
@@ -171,15 +173,18 @@ def block_class(qs, m, engine, tc_min_k, n=30, elem_bytes=8):
     sector_bits = 2 if elem_bytes == 8 else 1
     if nc and k - nc <= 2 and any((mask >> j) & 1 and n - 1 - q >= sector_bits for j, q in enumerate(qs)):
         return f"k_ctrl_kt{k - nc}"
-    df = "_df" if engine == "df" and elem_bytes == 16 else ""
+    df = "_df" if engine in ("df", "tc_c128") and elem_bytes == 16 else ""
     if not np.any(m[~np.eye(d, dtype=bool)]):
         return f"k_diag{df}_k{k}"
     nz = np.abs(m) > 4 * np.finfo(np.float64).eps * np.abs(m).max()
     if k <= 4 and np.all(nz.sum(axis=0) == 1) and np.all(nz.sum(axis=1) == 1):
         return f"k_mono{df}_k{k}"
-    if engine.startswith("tc") and k >= max(tc_min_k, 4) and n >= k + 7:
+    if engine == "tc_c128":
+        if elem_bytes == 16 and k in (3, 4) and n >= 11:
+            return "k_tcz_k4"
+    elif engine.startswith("tc") and k >= max(tc_min_k, 4) and n >= k + 7:
         return f"k_tc_{engine[3:]}_k{6 if n >= 13 else k}"
-    if engine == "df" and elem_bytes == 16 and k <= 4:
+    if engine in ("df", "tc_c128") and elem_bytes == 16 and k <= 4:
         return f"k_gather_df_k{k}"
     return f"k_gather_k{k}" if k <= 4 else f"k_block_k{k}"
 
@@ -878,7 +883,7 @@ def main():
     ap.add_argument("--fuse-restarts", type=int, default=64)
     ap.add_argument("--fuse-width", type=int, default=128, help="kept sequences of hq_fuse_beam")
     ap.add_argument("--dtype", default="complex64", choices=["complex64", "complex128"])
-    ap.add_argument("--engine", default="tc_f16", choices=["auto", "cuda_core", "tc_f16", "tc_bf16", "tc_pass", "df"])
+    ap.add_argument("--engine", default="tc_f16", choices=["auto", "cuda_core", "tc_f16", "tc_bf16", "tc_pass", "df", "tc_c128"])
     ap.add_argument("--tc-min-k", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' sub-measurements")
     ap.add_argument("--seed", type=int, default=0)
@@ -1042,7 +1047,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if S == 8 else "f64", "data": "synthetic",
             "config": {"workload": desc, "n": n, "gates": G, "fused_blocks": B, "k_max": args.kmax,
-                       "arith": ARITH.get(engine, engine) if (S == 8 or engine == "df") else "fp64",
+                       "arith": ARITH.get(engine, engine) if (S == 8 or engine in ("df", "tc_c128")) else "fp64",
                        "note": "the n=30 circuit of the per-gate / fused k<=4 configuration, run on the "
                                "fused k<=6 tensor-core engine of the 33-qubit configuration"
                                if n == 30 and engine.startswith("tc") else None,
@@ -1063,7 +1068,8 @@ def main():
             "per_class": per_class,
             "norm2": norm, "fuse_s": fuse_s, "per_block_pass_ms_per_step": 1e3 * per_block_step_s,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks, "extras": extras,
-            "gpu_launches": args.steps * (B + (0 if first_tc else 1) + (0 if last_tc else 1)),
+            # per step: the blocks, k_init unless folded, the norm (k_expect + k_expect_final) unless folded
+            "gpu_launches": args.steps * (B + (0 if first_tc else 1) + (0 if last_tc else 2)),
         }
         print(json.dumps(rec))
     if dist:

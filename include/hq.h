@@ -100,7 +100,7 @@ typedef struct {
                                  controlled gates and k = 5, 6 blocks as HQ_ENGINE_CUDA_CORE */
 #define HQ_ENGINE_TC_C128 6   /* complex128 only: dense k = 3, 4 blocks (n >= 11; k = 3 widened to 4) on
                                  tcgen05 tensor cores as exact FP16 products of 8-bit signed digit slices
-                                 (five per operand, FP32 accumulation exact, levels joined in 64-bit
+                                 (six per operand, FP32 accumulation exact, levels joined in 64-bit
                                  integers); all other gates as HQ_ENGINE_DF */
 typedef struct {
     int engine;  /* HQ_ENGINE_* */
