@@ -14,34 +14,41 @@
 //
 // Every double of a group is written as an integer V = round(v 2^(1069 - E))
 // with E the largest biased exponent in the group (|V| <= 2^47), and V as six
-// signed base-256 digits, V = sum_i d_i 2^(8 (5 - i)), |d_i| <= 128; the
-// matrix likewise with one exponent for the whole matrix (host, FP64).  A
-// digit is an integer of at most 8 bits, so FP16 holds it exactly and the
-// product of two is exact; K = 32 such products sum to at most 2^19, and the
-// up to six slice products of one level l = i + j (i = A's digit, j = B's)
-// to less than 2^22, below FP32's 2^24: every FP32 accumulation in the
-// tensor core is exact.  The six levels l = 0..5 each have their own
-// accumulator (21 slice products per tile); the levels 6..10 that are
-// dropped weigh ~2^-44 of a typical output (random digits), the rounding of
-// the inputs to 47 bits 2^-48 of the group's largest entry.  The epilogue
-// joins the levels exactly in 64-bit integers, sum_l acc_l 2^(8 (5 - l))
-// (< 2^60), and builds the double from it with integer operations (clz,
-// shift, round half up, exponent), so no step uses the FP64 pipe.
+// signed base-256 digits, V = sum_i d_i 2^(8 (5 - i)), |d_i| <= 128: with
+// W = V + 0x808080808080 (every byte offset by 128; 0 < W < 2^49), the five
+// low bytes of W and the rest, W >> 40, each minus 128, so no carries are
+// propagated.  The matrix is cut likewise
+// (|d| <= 128) with one exponent for the whole matrix (host, FP64).  A digit
+// is an integer of at most 8 bits, so FP16 holds it exactly and the product
+// of two is exact; K = 32 such products sum to at most 2^19, and the up to
+// six slice products of one level l = i + j (i = A's digit, j = B's) to less
+// than 2^22, below FP32's 2^24: every FP32 accumulation in the tensor core is
+// exact.  The six levels l = 0..5 each have their own accumulator (21 slice
+// products per tile); the levels 6..10 that are dropped weigh ~2^-44 of a
+// typical output (random digits), the rounding of the inputs to 47 bits 2^-48
+// of the group's largest entry.  The epilogue joins the levels exactly in
+// 64-bit integers, sum_l acc_l 2^(8 (5 - l)) (< 2^60), and builds the double
+// from it with integer operations (clz, shift, round half up, exponent), so
+// no step uses the FP64 pipe.
 //
-// Kernel shape (persistent, one CTA per SM, 256 threads):
-//   producers (warps 0-3, thread = group = TMEM lane): warp 0 lane 0..31
-//     issue the NEXT tile's bulk copies (one per contiguous run, completing
-//     on an mbarrier); each producer reads its group's 16 amplitudes of the
-//     current tile from shared memory, takes the group exponent, writes the
-//     six digit slices to TMEM (A operand, 16 columns each) once the previous
-//     tile's MMAs have read them, and stores the exponent for the epilogue;
-//     thread 0 issues the 21 x 2 MMAs (A from TMEM, B slices from shared
+// Kernel shape (persistent, one CTA per SM, 512 threads, two per group in
+// each role; a warp reaches the TMEM lanes 32 (warp mod 4) .. + 31):
+//   producers (warps 0-7; warp w: group = TMEM lane 32 (w mod 4) + lane,
+//     amplitudes 8 (w div 4) .. + 7 of it): warp 0 lanes 0..31 issue the NEXT
+//     tile's bulk copies (one per contiguous run, completing on an mbarrier);
+//     each producer reads its 8 amplitudes of the current tile from shared
+//     memory, the two halves of a group swap their largest exponents through
+//     shared memory, each writes its six digit slices to TMEM (A operand, 8 of
+//     the 16 columns of each slice) once the previous tile's MMAs have read
+//     them; thread 0 issues the 21 x 2 MMAs (A from TMEM, B slices from shared
 //     memory) and commits them to an mbarrier.
-//   epilogue (warps 4-7): waits for a tile's MMAs, reads the six level
-//     accumulators of its lane, joins them and stores the 16 outputs.
+//   epilogue (warps 8-15; warp w: outputs 8 ((w div 4) mod 2) .. + 7 of the
+//     group of lane 32 (w mod 4) + lane): waits for a tile's MMAs, reads the
+//     six level accumulators of its outputs, joins them and stores them.
 // Staging buffers and the accumulators (192 TMEM columns each) are double-
-// buffered, the A slices (96 columns) single-buffered.  Every wait is
-// bounded (%globaltimer, 2 s): on expiry
+// buffered, the A slices (96 columns) single-buffered; a tile's digits are
+// formed in registers before the wait for the previous tile's MMAs.  Every
+// wait is bounded (%globaltimer, 2 s): on expiry
 // the kernel raises its error flag, leaves its loops, waits for its own copies
 // and MMAs, frees its TMEM and returns; the next synchronous entry point
 // reports HQ_ERR_TIMEOUT.
@@ -63,18 +70,24 @@ __device__ unsigned int g_tcz_error;  // bit 0: a wait of k_tcz timed out
 namespace {
 
 constexpr int kZD = 16, kZD2 = 32;              // amplitudes per group; GEMM K = N
+constexpr int kZH = kZD / 2;                     // amplitudes (outputs) per producer (epilogue) thread
 constexpr int kZSlices = 6;                      // digits per operand = accumulated levels
-constexpr int kZThreads = 2 * kTcGroups;         // 128 producers + 128 epilogue threads
+constexpr int kZProd = 2 * kTcGroups;            // producers: two per group
+constexpr int kZThreads = 4 * kTcGroups;         // 256 producers + 256 epilogue threads
 constexpr int kZTileBytes = kTcGroups * kZD * 16;   // 32 KB of complex128
 constexpr int kZBSliceBytes = kZD2 * kZD2 * 2;      // one B digit slice, 32 x 32 FP16
 constexpr uint32_t kZAccCol = 16 * kZSlices;     // A slices at columns 16 i; then the accumulators:
 constexpr uint32_t kZAccCols = 32 * kZSlices;    // level l of buffer b at kZAccCol + b kZAccCols + 32 l
 constexpr uint32_t kZTmemCols = 512;             // 96 + 2 x 192 = 480 used
 constexpr int kZOffTile = kZSlices * kZBSliceBytes;  // B slices first (12 KB)
-constexpr int kZOffExp = kZOffTile + 2 * kZTileBytes;  // int[2][128]: group exponents
-constexpr int kZOffBar = kZOffExp + 2 * kTcGroups * 4;  // mma_done[2], acc_free[2], full[2]
+constexpr int kZOffExp = kZOffTile + 2 * kZTileBytes;   // int[2][128]: group exponents (epilogue)
+constexpr int kZOffPart = kZOffExp + 2 * kTcGroups * 4;  // int[2][128]: largest exponent of each half
+constexpr int kZOffBar = kZOffPart + 2 * kTcGroups * 4;  // mma_done[2], acc_free[2], full[2]
 constexpr int kZOffMisc = kZOffBar + 6 * 8;              // TMEM address, abort flag
 constexpr int kZBytes = kZOffMisc + 16;
+constexpr uint64_t kZCenter = 0x808080808080ull;  // 128 in each of the six bytes
+// 0x4B400000 (the bit pattern of 1.5 * 2^23) in each of the six levels' weights, mod 2^64
+constexpr uint64_t kZBias = 0x8B8B8B8B8B400000ull;
 
 struct TczParams {
     TileGeom g;         // K = 4, L = 11
@@ -82,13 +95,11 @@ struct TczParams {
     int eb;             // the matrix exponent E_B (biased)
 };
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
 {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_st_x8(uint32_t taddr, const uint32_t (&r)[8])
@@ -101,47 +112,60 @@ __device__ __forceinline__ void tmem_st_x8(uint32_t taddr, const uint32_t (&r)[8
 // biased exponent field of the double with high word hi (0 for zeros and subnormals)
 __device__ __forceinline__ int dexp(uint32_t hi) { return int((hi >> 20) & 0x7FFu); }
 
-// exact float of a small integer d (|d| < 2^22): 1.5 * 2^23 + d has unit spacing
-__device__ __forceinline__ float small_int_float(int d) { return __int_as_float(0x4B400000 + d) - 12582912.0f; }
-// the integer held by an integer-valued float f (|f| < 2^22)
-__device__ __forceinline__ int float_small_int(float f) { return __float_as_int(__fadd_rn(f, 12582912.0f)) - 0x4B400000; }
-
-// The six signed digits of v (high word hi, low word lo) at group exponent
-// emax: V = round(m 2^(e - emax - 6)), m the 53-bit significand, then
-// d_5 .. d_1 = the signed low byte (t = V + 128; d = (t & 255) - 128; V = t >> 8)
-// and d_0 = what is left.
-__device__ __forceinline__ void digits(uint32_t hi, uint32_t lo, int emax, float (&d)[kZSlices])
+// W = V + 0x808080808080 for the double (hi, lo) at group exponent emax:
+// V = round(m 2^(e - emax - 6)), m the 53-bit significand, with the double's
+// sign (zeros and subnormals give V = 0).  |V| <= 2^47, so 0 < W < 2^49;
+// byte b < 5 of W minus 128 is the digit of weight 2^(8 b), (W >> 40) - 128
+// the digit of weight 2^40.
+__device__ __forceinline__ uint64_t centered(uint32_t hi, uint32_t lo, int emax)
 {
     const int e = dexp(hi);
-    const int s = emax - e + 6;  // >= 6
-    int64_t V = 0;
-    if (e != 0 && s < 63) {
-        const uint64_t m = (uint64_t((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
-        V = int64_t((m + (uint64_t(1) << (s - 1))) >> s);
-        if (hi >> 31) V = -V;
-    }
-#pragma unroll
-    for (int i = kZSlices - 1; i > 0; --i) {
-        const int64_t t = V + 128;
-        d[i] = small_int_float(int(t & 255) - 128);
-        V = t >> 8;
-    }
-    d[0] = small_int_float(int(V));
+    const uint64_t m = e ? ((uint64_t((hi & 0xFFFFFu) | 0x100000u) << 32) | lo) : 0;
+    const int t = min(emax - e + 5, 63);
+    const uint64_t M = ((m >> t) + 1) >> 1;  // round half up
+    const uint64_t S = uint64_t(int64_t(int32_t(hi) >> 31));  // 0, or all ones if negative
+    return kZCenter + ((M ^ S) - S);
+}
+
+// FP16 pair (digit of a, digit of b) from byte B of the words a (real parts)
+// and b (imaginary parts): 0x6400 | byte is the half 1024 + byte, exactly;
+// subtracting 1152 leaves byte - 128, exactly.
+template <int B>
+__device__ __forceinline__ uint32_t digit_pair(uint32_t a, uint32_t b)
+{
+    const uint32_t p = (__byte_perm(a, b, B | ((4 + B) << 8)) & 0x00FF00FFu) | 0x64006400u;
+    const __half2 d = __hadd2(*reinterpret_cast<const __half2 *>(&p), __halves2half2(__ushort_as_half(0xE480),
+                                                                                       __ushort_as_half(0xE480)));
+    return *reinterpret_cast<const uint32_t *>(&d);
+}
+// the same for the top digits, (W >> 40) - 128 in [-128, 128], from the high
+// words (W >> 32 < 2^17): 0x6400 | u is the half 1024 + u for u < 1024
+__device__ __forceinline__ uint32_t top_digit_pair(uint32_t a, uint32_t b)
+{
+    const uint32_t p = (a >> 8) | ((b >> 8) << 16) | 0x64006400u;
+    const __half2 d = __hadd2(*reinterpret_cast<const __half2 *>(&p), __halves2half2(__ushort_as_half(0xE480),
+                                                                                       __ushort_as_half(0xE480)));
+    return *reinterpret_cast<const uint32_t *>(&d);
 }
 
 // sum_l acc_l 2^(8 (5 - l)) 2^x as a double, built with integer operations
-// (rounded half up to 53 bits; results below the normal range flush to zero)
-__device__ __forceinline__ double join_levels(const int (&a)[kZSlices], int x)
+// (rounded half up to 53 bits; results below the normal range flush to zero).
+// v[l][col] holds level l's accumulator, an integer-valued float below 2^22
+// in magnitude: adding 1.5 * 2^23 makes its bit pattern 0x4B400000 + acc
+// exactly, and the offsets of all levels are taken off once, modulo 2^64
+// (the true sum is below 2^60 in magnitude).
+__device__ __forceinline__ double join_levels(const uint32_t (&v)[kZSlices][8], int col, int x)
 {
-    int64_t w = 0;
+    uint64_t u = 0;
 #pragma unroll
-    for (int l = 0; l < kZSlices; ++l) w += int64_t(a[l]) * (int64_t(1) << (8 * (kZSlices - 1 - l)));
+    for (int l = 0; l < kZSlices; ++l) u = (u << 8) + __float_as_uint(__uint_as_float(v[l][col]) + 12582912.0f);
+    const int64_t w = int64_t(u - kZBias);
     if (w == 0) return 0.0;
     const uint64_t sign = w < 0 ? (uint64_t(1) << 63) : 0;
-    uint64_t u = w < 0 ? uint64_t(-w) : uint64_t(w);
-    const int lz = __clzll(u);
-    u <<= lz;
-    const uint64_t mant = (u >> 11) + ((u >> 10) & 1);  // in [2^52, 2^53]
+    uint64_t a = w < 0 ? uint64_t(-w) : uint64_t(w);
+    const int lz = __clzll(a);
+    a <<= lz;
+    const uint64_t mant = (a >> 11) + ((a >> 10) & 1);  // in [2^52, 2^53]
     const int ef = 63 - lz + x + 1022;                   // exponent field - 1 (mant's bit 52 adds one)
     if (ef <= 0) return 0.0;
     return __longlong_as_double(int64_t(sign | ((uint64_t(ef) << 52) + mant)));
@@ -154,7 +178,8 @@ __global__ void __launch_bounds__(kZThreads, 1) k_tcz(const TczParams p, double2
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kZOffBar);  // [0,1] mma_done, [2,3] acc_free, [4,5] full
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kZOffMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kZOffMisc + 4);
-    int *gexp = reinterpret_cast<int *>(smem + kZOffExp);  // [2][128]
+    int *gexp = reinterpret_cast<int *>(smem + kZOffExp);   // [2][128]
+    int *part = reinterpret_cast<int *>(smem + kZOffPart);  // [half][128]
     const TileGeom &g = p.g;
     const int tid = threadIdx.x, warp = tid >> 5;
 
@@ -163,8 +188,8 @@ __global__ void __launch_bounds__(kZThreads, 1) k_tcz(const TczParams p, double2
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
-        mbar_init(&bar[2], kZThreads - NP);
-        mbar_init(&bar[3], kZThreads - NP);
+        mbar_init(&bar[2], kZThreads - kZProd);
+        mbar_init(&bar[3], kZThreads - kZProd);
         mbar_init(&bar[4], 1);
         mbar_init(&bar[5], 1);
         *abort_flag = 0;
@@ -180,10 +205,11 @@ __global__ void __launch_bounds__(kZThreads, 1) k_tcz(const TczParams p, double2
 
     const int quarter = warp & 3;
     const int n = quarter * 32 + (tid & 31);  // group within the tile = TMEM lane
+    const int h = (warp >> 2) & 1;            // which half of the group's amplitudes (outputs)
     const uint32_t lane_off = uint32_t(quarter * 32) << 16;
     const int ibase = group_base<4>(g, n);
 
-    if (tid < NP) {
+    if (tid < kZProd) {
         // ---------------- producers + MMA issue ----------------
         constexpr uint32_t idesc = instr_desc(kTcGroups, kZD2, false);
         // warp 0 copies tile t into buffer sb, one bulk copy per contiguous run
@@ -208,51 +234,57 @@ __global__ void __launch_bounds__(kZThreads, 1) k_tcz(const TczParams p, double2
                 if (warp == 0) load_tile(t + gridDim.x, buf ^ 1);
                 ++loaded;
             }
-            const bool landed = mbar_wait(&bar[4 + buf], uint32_t((it / 2) & 1), abort_flag, &g_tcz_error);
-            // accumulator buffer buf is free once the epilogue of tile it - 2
-            // released it; the A slices once the MMAs of tile it - 1 are done
-            const bool ok =
-                landed && (it < 2 || mbar_wait(&bar[2 + buf], uint32_t((it / 2 - 1) & 1), abort_flag, &g_tcz_error)) &&
-                (it < 1 || mbar_wait(&bar[buf ^ 1], uint32_t(((it - 1) / 2) & 1), abort_flag, &g_tcz_error));
+            // the tile has landed; the group exponents of buffer buf are free
+            // once the epilogue of tile it - 2 released its accumulators
+            bool ok = mbar_wait(&bar[4 + buf], uint32_t((it / 2) & 1), abort_flag, &g_tcz_error) &&
+                      (it < 2 || mbar_wait(&bar[2 + buf], uint32_t((it / 2 - 1) & 1), abort_flag, &g_tcz_error));
+            uint32_t hw[2 * kZH], lw[2 * kZH];
+            int pmax = 0;
             if (ok) {
                 const double2 *x = reinterpret_cast<const double2 *>(smem + kZOffTile + buf * kZTileBytes) + ibase;
-                // this group's amplitudes (the offsets are compile-time indices into the parameters)
-                uint32_t hw[2 * kZD], lw[2 * kZD];
-                int emax = 0;
 #pragma unroll
-                for (int r = 0; r < kZD; ++r) {
-                    const double2 v = x[g.toff[r]];
-                    hw[2 * r] = uint32_t(__double2hiint(v.x));
-                    lw[2 * r] = uint32_t(__double2loint(v.x));
-                    hw[2 * r + 1] = uint32_t(__double2hiint(v.y));
-                    lw[2 * r + 1] = uint32_t(__double2loint(v.y));
-                    emax = max(emax, max(dexp(hw[2 * r]), dexp(hw[2 * r + 1])));
+                for (int c = 0; c < kZH; ++c) {
+                    const double2 v = x[g.toff[kZH * h + c]];
+                    hw[2 * c] = uint32_t(__double2hiint(v.x));
+                    lw[2 * c] = uint32_t(__double2loint(v.x));
+                    hw[2 * c + 1] = uint32_t(__double2hiint(v.y));
+                    lw[2 * c + 1] = uint32_t(__double2loint(v.y));
+                    pmax = max(pmax, max(dexp(hw[2 * c]), dexp(hw[2 * c + 1])));
                 }
-                gexp[buf * kTcGroups + n] = emax;
-                const uint32_t a0 = tmem + lane_off;
+            }
+            // the two halves of a group swap their largest exponents
+            part[h * NP + n] = pmax;
+            named_bar_sync(3, kZProd);
+            const int emax = max(part[n], part[NP + n]);
+            if (h == 0) gexp[buf * NP + n] = emax;
+            uint32_t hv[kZSlices][kZH];
+            if (ok) {
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    uint32_t hv[kZSlices][8];
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const int r = 8 * half + c;
-                        float dre[kZSlices], dim[kZSlices];
-                        digits(hw[2 * r], lw[2 * r], emax, dre);
-                        digits(hw[2 * r + 1], lw[2 * r + 1], emax, dim);
-#pragma unroll
-                        for (int i = 0; i < kZSlices; ++i) {
-                            const __half2 h = __floats2half2_rn(dre[i], dim[i]);
-                            hv[i][c] = *reinterpret_cast<const uint32_t *>(&h);
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < kZSlices; ++i) tmem_st_x8(a0 + uint32_t(16 * i + 8 * half), hv[i]);
+                for (int c = 0; c < kZH; ++c) {
+                    const uint64_t wr = centered(hw[2 * c], lw[2 * c], emax);
+                    const uint64_t wi = centered(hw[2 * c + 1], lw[2 * c + 1], emax);
+                    const uint32_t rl = uint32_t(wr), rh = uint32_t(wr >> 32);
+                    const uint32_t il = uint32_t(wi), ih = uint32_t(wi >> 32);
+                    // slice i holds the digit of weight 2^(8 (5 - i)): byte 5 - i of W, W >> 40 for i = 0
+                    hv[0][c] = top_digit_pair(rh, ih);
+                    hv[1][c] = digit_pair<0>(rh, ih);
+                    hv[2][c] = digit_pair<3>(rl, il);
+                    hv[3][c] = digit_pair<2>(rl, il);
+                    hv[4][c] = digit_pair<1>(rl, il);
+                    hv[5][c] = digit_pair<0>(rl, il);
                 }
+            }
+            // the A slices are free once the MMAs of tile it - 1 are done
+            ok = ok && (it < 1 || mbar_wait(&bar[buf ^ 1], uint32_t(((it - 1) / 2) & 1), abort_flag, &g_tcz_error));
+            if (ok) {
+                const uint32_t a0 = tmem + lane_off + uint32_t(kZH * h);
+#pragma unroll
+                for (int i = 0; i < kZSlices; ++i) tmem_st_x8(a0 + uint32_t(16 * i), hv[i]);
                 tmem_wait_st();
             }
             tc_fence_before();
             // every producer takes the same exit decision
-            if (named_bar_or(2, NP, !ok || *abort_flag)) break;
+            if (named_bar_or(2, kZProd, !ok || *abort_flag)) break;
             if (tid == 0) {
                 __threadfence_block();  // the group exponents before the MMAs the epilogue waits for
                 tc_fence_after();
@@ -295,25 +327,19 @@ __global__ void __launch_bounds__(kZThreads, 1) k_tcz(const TczParams p, double2
             // warp-uniform exit: tcgen05.ld below is .sync.aligned
             if (!__all_sync(0xffffffffu, mbar_wait(&bar[buf], uint32_t((it / 2) & 1), abort_flag, &g_tcz_error))) break;
             tc_fence_after();
-            const int x = gexp[buf * kTcGroups + n] + p.eb - 2098;
+            const int x = gexp[buf * NP + n] + p.eb - 2098;
             double2 *gdst = state + tile_base(g, t) + ibase;
-            const uint32_t acc0 = tmem + lane_off + kZAccCol + uint32_t(buf) * kZAccCols;
+            // outputs r = 8 h + 4 q + c, columns 2 r + {Re, Im} of every level
+            const uint32_t acc0 = tmem + lane_off + kZAccCol + uint32_t(buf) * kZAccCols + uint32_t(2 * kZH * h);
+#pragma unroll 1
+            for (int q = 0; q < 2; ++q) {
+                uint32_t v[kZSlices][8];
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                uint32_t v[kZSlices][16];
-#pragma unroll
-                for (int l = 0; l < kZSlices; ++l) tmem_ld16(acc0 + uint32_t(32 * l + 16 * half), v[l]);
+                for (int l = 0; l < kZSlices; ++l) tmem_ld8(acc0 + uint32_t(32 * l + 8 * q), v[l]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    int are[kZSlices], aim[kZSlices];
-#pragma unroll
-                    for (int l = 0; l < kZSlices; ++l) {
-                        are[l] = float_small_int(__uint_as_float(v[l][2 * c]));
-                        aim[l] = float_small_int(__uint_as_float(v[l][2 * c + 1]));
-                    }
-                    gdst[g.goff[8 * half + c]] = make_double2(join_levels(are, x), join_levels(aim, x));
-                }
+                for (int c = 0; c < 4; ++c)
+                    gdst[g.goff[kZH * h + 4 * q + c]] = make_double2(join_levels(v, 2 * c, x), join_levels(v, 2 * c + 1, x));
             }
             tc_fence_before();
             mbar_arrive(&bar[2 + buf]);
