@@ -15,43 +15,48 @@
 // Every double of a group is written as an integer V = round(v 2^(1069 - E))
 // with E the largest biased exponent in the group (|V| <= 2^47), and V as six
 // signed base-256 digits, V = sum_i d_i 2^(8 (5 - i)), |d_i| <= 128: with
-// W = V + 0x808080808080 (every byte offset by 128; 0 < W < 2^49), the five
-// low bytes of W and the rest, W >> 40, each minus 128, so no carries are
-// propagated.  The matrix is cut likewise
+// W = |V| + 0x808080808080 (every byte offset by 128; W < 2^49), the five
+// low bytes of W and the rest, W >> 40, each minus 128 and times the sign of
+// V, so no carries are propagated.  The matrix is cut likewise
 // (|d| <= 128) with one exponent for the whole matrix (host, FP64).  A digit
 // is an integer of at most 8 bits, so FP16 holds it exactly and the product
 // of two is exact; K = 32 such products sum to at most 2^19, and the up to
 // six slice products of one level l = i + j (i = A's digit, j = B's) to less
 // than 2^22, below FP32's 2^24: every FP32 accumulation in the tensor core is
 // exact.  The six levels l = 0..5 each have their own accumulator (21 slice
-// products per tile); the levels 6..10 that are dropped weigh ~2^-44 of a
+// products per tile, in 6 MMAs per K step); the levels 6..10 that are dropped weigh ~2^-44 of a
 // typical output (random digits), the rounding of the inputs to 47 bits 2^-48
 // of the group's largest entry.  The epilogue joins the levels exactly in
 // 64-bit integers, sum_l acc_l 2^(8 (5 - l)) (< 2^60), and builds the double
 // from it with integer operations (clz, shift, round half up, exponent), so
 // no step uses the FP64 pipe.
 //
-// Kernel shape (persistent, one CTA per SM, 512 threads, two per group in
-// each role; a warp reaches the TMEM lanes 32 (warp mod 4) .. + 31):
+// Kernel shape (persistent, one CTA per SM, 17 warps: two threads per group
+// in each of two roles, and one control warp; a warp reaches the TMEM lanes
+// 32 (warp mod 4) .. + 31):
 //   producers (warps 0-7; warp w: group = TMEM lane 32 (w mod 4) + lane,
-//     amplitudes 8 (w div 4) .. + 7 of it): warp 0 lanes 0..31 issue the NEXT
-//     tile's bulk copies (one per contiguous run, completing on an mbarrier);
-//     each producer reads its 8 amplitudes of the current tile from shared
-//     memory, the two halves of a group swap their largest exponents through
-//     shared memory, each writes its six digit slices to TMEM (A operand, 8 of
-//     the 16 columns of each slice) once the previous tile's MMAs have read
-//     them; thread 0 issues the 21 x 2 MMAs (A from TMEM, B slices from shared
-//     memory) and commits them to an mbarrier.
+//     amplitudes 8 (w div 4) .. + 7 of it): each reads its 8 amplitudes of the
+//     current tile from shared memory and releases the stage, the two halves
+//     of a group swap their largest exponents through shared memory, each
+//     writes its six digit slices to TMEM (A operand, 8 of the 16 columns of
+//     each slice; the first four amplitudes' digits are formed before the
+//     wait for the previous tile's MMAs) and arrives on an mbarrier.
 //   epilogue (warps 8-15; warp w: outputs 8 ((w div 4) mod 2) .. + 7 of the
 //     group of lane 32 (w mod 4) + lane): waits for a tile's MMAs, reads the
 //     six level accumulators of its outputs, joins them and stores them.
-// Staging buffers and the accumulators (192 TMEM columns each) are double-
-// buffered, the A slices (96 columns) single-buffered; a tile's digits are
-// formed in registers before the wait for the previous tile's MMAs.  Every
-// wait is bounded (%globaltimer, 2 s): on expiry
-// the kernel raises its error flag, leaves its loops, waits for its own copies
-// and MMAs, frees its TMEM and returns; the next synchronous entry point
-// reports HQ_ERR_TIMEOUT.
+//   control (warp 16): keeps up to four tiles in shared memory (bulk copies,
+//     one per contiguous run, completing on a stage's mbarrier; a stage is
+//     refilled once the producers released it) and, from lane 0, issues a
+//     tile's 6 x 2 MMAs (A slice i from TMEM against the B slices 0 .. 5 - i
+//     side by side in shared memory, into the levels i .. 5) once its A
+//     slices are written and its accumulator buffer is free, committing the
+//     first K step's 6 to one mbarrier (the producers of that half may then
+//     write the next tile's columns) and all of them to another.
+// The accumulators (192 TMEM columns each) are double-buffered, the A slices
+// (96 columns) single-buffered.  Every wait is bounded (%globaltimer, 2 s):
+// on expiry the kernel raises its error flag, leaves its loops, waits for
+// its own copies and MMAs, frees its TMEM and returns; the next synchronous
+// entry point reports HQ_ERR_TIMEOUT.
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -73,17 +78,24 @@ constexpr int kZD = 16, kZD2 = 32;              // amplitudes per group; GEMM K 
 constexpr int kZH = kZD / 2;                     // amplitudes (outputs) per producer (epilogue) thread
 constexpr int kZSlices = 6;                      // digits per operand = accumulated levels
 constexpr int kZProd = 2 * kTcGroups;            // producers: two per group
-constexpr int kZThreads = 4 * kTcGroups;         // 256 producers + 256 epilogue threads
+constexpr int kZEpi = 2 * kTcGroups;             // epilogue threads: two per group
+constexpr int kZCtrlWarp = (kZProd + kZEpi) / 32;  // the warp that issues the tile copies and the MMAs
+constexpr int kZThreads = kZProd + kZEpi + 32;
+constexpr int kZStages = 4;                      // tiles in shared memory (up to 3 copies in flight)
 constexpr int kZTileBytes = kTcGroups * kZD * 16;   // 32 KB of complex128
 constexpr int kZBSliceBytes = kZD2 * kZD2 * 2;      // one B digit slice, 32 x 32 FP16
 constexpr uint32_t kZAccCol = 16 * kZSlices;     // A slices at columns 16 i; then the accumulators:
 constexpr uint32_t kZAccCols = 32 * kZSlices;    // level l of buffer b at kZAccCol + b kZAccCols + 32 l
 constexpr uint32_t kZTmemCols = 512;             // 96 + 2 x 192 = 480 used
 constexpr int kZOffTile = kZSlices * kZBSliceBytes;  // B slices first (12 KB)
-constexpr int kZOffExp = kZOffTile + 2 * kZTileBytes;   // int[2][128]: group exponents (epilogue)
-constexpr int kZOffPart = kZOffExp + 2 * kTcGroups * 4;  // int[2][128]: largest exponent of each half
-constexpr int kZOffBar = kZOffPart + 2 * kTcGroups * 4;  // mma_done[2], acc_free[2], full[2]
-constexpr int kZOffMisc = kZOffBar + 6 * 8;              // TMEM address, abort flag
+constexpr int kZOffExp = kZOffTile + kZStages * kZTileBytes;  // int[2][128]: group exponents (epilogue)
+constexpr int kZOffPart = kZOffExp + 2 * kTcGroups * 4;       // int[2][2][128]: largest exponent of each half
+constexpr int kZOffBar = kZOffPart + 4 * kTcGroups * 4;
+// mbarriers: mma_done[2] (a tile's MMAs), acc_free[2], full[stages],
+// tile_free[stages], a_full, a_free0 (the MMAs of a tile's first K step)
+constexpr int kZBarAccFree = 2, kZBarFull = 4, kZBarTileFree = kZBarFull + kZStages, kZBarAFull = kZBarTileFree + kZStages;
+constexpr int kZBarAFree0 = kZBarAFull + 1;
+constexpr int kZOffMisc = kZOffBar + (kZBarAFree0 + 1) * 8;  // TMEM address, abort flag
 constexpr int kZBytes = kZOffMisc + 16;
 constexpr uint64_t kZCenter = 0x808080808080ull;  // 128 in each of the six bytes
 // 0x4B400000 (the bit pattern of 1.5 * 2^23) in each of the six levels' weights, mod 2^64
@@ -93,6 +105,7 @@ struct TczParams {
     TileGeom g;         // K = 4, L = 11
     const uint4 *bmat;  // kZSlices B digit slices, each in K-major core-matrix order
     int eb;             // the matrix exponent E_B (biased)
+    uint32_t w8, w16, w24;  // 2^8, 2^16, 2^24 (multipliers of the epilogue's multiply-add chain)
 };
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
@@ -102,64 +115,85 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
                  : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_st_x8(uint32_t taddr, const uint32_t (&r)[8])
+__device__ __forceinline__ void tmem_st_x4(uint32_t taddr, const uint32_t (&r)[4])
 {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
-                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(r[0]), "r"(r[1]),
+                 "r"(r[2]), "r"(r[3])
                  : "memory");
 }
 
 // biased exponent field of the double with high word hi (0 for zeros and subnormals)
 __device__ __forceinline__ int dexp(uint32_t hi) { return int((hi >> 20) & 0x7FFu); }
 
-// W = V + 0x808080808080 for the double (hi, lo) at group exponent emax:
-// V = round(m 2^(e - emax - 6)), m the 53-bit significand, with the double's
-// sign (zeros and subnormals give V = 0).  |V| <= 2^47, so 0 < W < 2^49;
-// byte b < 5 of W minus 128 is the digit of weight 2^(8 b), (W >> 40) - 128
-// the digit of weight 2^40.
+// W = |V| + 0x808080808080 for the double (hi, lo) at group exponent emax:
+// |V| = round(m 2^(e - emax - 6)), m the 53-bit significand (zeros and
+// subnormals give 0).  |V| <= 2^47, so 0x808080808080 <= W < 2^49; byte b < 5
+// of W minus 128 is the digit of weight 2^(8 b) of |V|, (W >> 40) - 128 (in
+// [0, 128]) the digit of weight 2^40.  The sign is applied to the digits.
 __device__ __forceinline__ uint64_t centered(uint32_t hi, uint32_t lo, int emax)
 {
     const int e = dexp(hi);
     const uint64_t m = e ? ((uint64_t((hi & 0xFFFFFu) | 0x100000u) << 32) | lo) : 0;
     const int t = min(emax - e + 5, 63);
-    const uint64_t M = ((m >> t) + 1) >> 1;  // round half up
-    const uint64_t S = uint64_t(int64_t(int32_t(hi) >> 31));  // 0, or all ones if negative
-    return kZCenter + ((M ^ S) - S);
+    return kZCenter + (((m >> t) + 1) >> 1);  // round half up
+}
+
+// The FP16 sign factors (s_re, s_im) = (+-1, +-1) of an amplitude whose
+// doubles have high words hre, him, and (-1152 s_re, -1152 s_im).
+__device__ __forceinline__ void digit_signs(uint32_t hre, uint32_t him, uint32_t &S, uint32_t &K)
+{
+    const uint32_t sb = __byte_perm(hre, him, 0x7030) & 0x80008000u;  // the sign bits at bits 15 and 31
+    S = sb | 0x3C003C00u;
+    K = sb ^ 0xE480E480u;
 }
 
 // FP16 pair (digit of a, digit of b) from byte B of the words a (real parts)
 // and b (imaginary parts): 0x6400 | byte is the half 1024 + byte, exactly;
-// subtracting 1152 leaves byte - 128, exactly.
+// (1024 + byte) s - 1152 s = s (byte - 128), exactly, with s the sign.
 template <int B>
-__device__ __forceinline__ uint32_t digit_pair(uint32_t a, uint32_t b)
+__device__ __forceinline__ uint32_t digit_pair(uint32_t a, uint32_t b, uint32_t S, uint32_t K)
 {
     const uint32_t p = (__byte_perm(a, b, B | ((4 + B) << 8)) & 0x00FF00FFu) | 0x64006400u;
-    const __half2 d = __hadd2(*reinterpret_cast<const __half2 *>(&p), __halves2half2(__ushort_as_half(0xE480),
-                                                                                       __ushort_as_half(0xE480)));
+    const __half2 d = __hfma2(*reinterpret_cast<const __half2 *>(&p), *reinterpret_cast<const __half2 *>(&S),
+                              *reinterpret_cast<const __half2 *>(&K));
     return *reinterpret_cast<const uint32_t *>(&d);
 }
-// the same for the top digits, (W >> 40) - 128 in [-128, 128], from the high
+// the same for the top digits, (W >> 40) - 128 in [0, 128], from the high
 // words (W >> 32 < 2^17): 0x6400 | u is the half 1024 + u for u < 1024
-__device__ __forceinline__ uint32_t top_digit_pair(uint32_t a, uint32_t b)
+__device__ __forceinline__ uint32_t top_digit_pair(uint32_t a, uint32_t b, uint32_t S, uint32_t K)
 {
     const uint32_t p = (a >> 8) | ((b >> 8) << 16) | 0x64006400u;
-    const __half2 d = __hadd2(*reinterpret_cast<const __half2 *>(&p), __halves2half2(__ushort_as_half(0xE480),
-                                                                                       __ushort_as_half(0xE480)));
+    const __half2 d = __hfma2(*reinterpret_cast<const __half2 *>(&p), *reinterpret_cast<const __half2 *>(&S),
+                              *reinterpret_cast<const __half2 *>(&K));
     return *reinterpret_cast<const uint32_t *>(&d);
+}
+
+// a * b + c, 64-bit (the multiply-add pipe; b is kept out of the compiler's
+// sight so that the products are not turned into shifts on the integer pipe)
+__device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
 }
 
 // sum_l acc_l 2^(8 (5 - l)) 2^x as a double, built with integer operations
 // (rounded half up to 53 bits; results below the normal range flush to zero).
 // v[l][col] holds level l's accumulator, an integer-valued float below 2^22
-// in magnitude: adding 1.5 * 2^23 makes its bit pattern 0x4B400000 + acc
-// exactly, and the offsets of all levels are taken off once, modulo 2^64
-// (the true sum is below 2^60 in magnitude).
-__device__ __forceinline__ double join_levels(const uint32_t (&v)[kZSlices][8], int col, int x)
+// in magnitude: adding 1.5 * 2^23 makes its bit pattern b_l = 0x4B400000 + acc
+// exactly.  sum_l b_l 2^(8 (5 - l)) is formed modulo 2^64 (levels 2..5 by a
+// multiply-add chain, levels 0 and 1 in the high word) and the offsets of
+// all levels are taken off once (the true sum is below 2^60 in magnitude).
+// w8, w16, w24 = 2^8, 2^16, 2^24.
+__device__ __forceinline__ double join_levels(const uint32_t (&v)[kZSlices][8], int col, int x, uint32_t w8,
+                                              uint32_t w16, uint32_t w24)
 {
-    uint64_t u = 0;
+    uint32_t b[kZSlices];
 #pragma unroll
-    for (int l = 0; l < kZSlices; ++l) u = (u << 8) + __float_as_uint(__uint_as_float(v[l][col]) + 12582912.0f);
-    const int64_t w = int64_t(u - kZBias);
+    for (int l = 0; l < kZSlices; ++l) b[l] = __float_as_uint(__uint_as_float(v[l][col]) + 12582912.0f);
+    const uint64_t lo = mad_wide(b[2], w24, mad_wide(b[3], w16, mad_wide(b[4], w8, uint64_t(b[5]))));
+    const uint32_t hi = b[0] * w8 + b[1];
+    const int64_t w = int64_t(lo + (uint64_t(hi) << 32) - kZBias);
     if (w == 0) return 0.0;
     const uint64_t sign = w < 0 ? (uint64_t(1) << 63) : 0;
     uint64_t a = w < 0 ? uint64_t(-w) : uint64_t(w);
@@ -175,23 +209,27 @@ __global__ void __launch_bounds__(kZThreads, 1) k_tcz(const TczParams p, double2
 {
     constexpr int NP = kTcGroups;
     extern __shared__ __align__(1024) unsigned char smem[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kZOffBar);  // [0,1] mma_done, [2,3] acc_free, [4,5] full
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kZOffBar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kZOffMisc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + kZOffMisc + 4);
     int *gexp = reinterpret_cast<int *>(smem + kZOffExp);   // [2][128]
-    int *part = reinterpret_cast<int *>(smem + kZOffPart);  // [half][128]
+    int *part = reinterpret_cast<int *>(smem + kZOffPart);  // [2][half][128]
     const TileGeom &g = p.g;
     const int tid = threadIdx.x, warp = tid >> 5;
 
     for (int i = tid; i < kZSlices * kZBSliceBytes / 16; i += kZThreads)
         reinterpret_cast<uint4 *>(smem)[i] = p.bmat[i];
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_init(&bar[2], kZThreads - kZProd);
-        mbar_init(&bar[3], kZThreads - kZProd);
-        mbar_init(&bar[4], 1);
-        mbar_init(&bar[5], 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar[b], 1);                 // mma_done: the MMAs' commit
+            mbar_init(&bar[kZBarAccFree + b], kZEpi);
+        }
+        for (int s = 0; s < kZStages; ++s) {
+            mbar_init(&bar[kZBarFull + s], 1);     // the copies' transaction count
+            mbar_init(&bar[kZBarTileFree + s], kZProd);
+        }
+        mbar_init(&bar[kZBarAFull], kZProd);
+        mbar_init(&bar[kZBarAFree0], 1);
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -210,116 +248,82 @@ __global__ void __launch_bounds__(kZThreads, 1) k_tcz(const TczParams p, double2
     const int ibase = group_base<4>(g, n);
 
     if (tid < kZProd) {
-        // ---------------- producers + MMA issue ----------------
-        constexpr uint32_t idesc = instr_desc(kTcGroups, kZD2, false);
-        // warp 0 copies tile t into buffer sb, one bulk copy per contiguous run
-        auto load_tile = [&](int64_t t, int sb) {
-            const int lane = tid & 31;
-            uint64_t *fb = &bar[4 + sb];
-            const uint32_t dst = smem_base + kZOffTile + uint32_t(sb * kZTileBytes);
-            fence_proxy_async();
-            if (lane == 0) mbar_expect_tx(fb, uint32_t(kZTileBytes));
-            __syncwarp();
-            const int nruns = 1 << (g.L - g.c);
-            const uint32_t run_bytes = uint32_t(16) << g.c;
-            const double2 *src = state + tile_base(g, t);
-            for (int j = lane; j < nruns; j += 32) bulk_g2s(dst + uint32_t(j) * run_bytes, src + g.runoff[j], run_bytes, fb);
-        };
-        if (warp == 0 && int64_t(blockIdx.x) < g.total_tiles) load_tile(blockIdx.x, 0);
-        int it = 0, issued = 0, loaded = (int64_t(blockIdx.x) < g.total_tiles) ? 1 : 0;
+        // ---------------- producers ----------------
+        int soff[kZH];  // this thread's amplitudes within a tile
+#pragma unroll
+        for (int c = 0; c < kZH; ++c) soff[c] = ibase + g.toff[kZH * h + c];
+        int it = 0;
+        bool fail = false;
         for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
-            const int buf = it & 1;
-            // buffer buf ^ 1 was last read (tile it - 1) before the last barrier
-            if (t + gridDim.x < g.total_tiles) {
-                if (warp == 0) load_tile(t + gridDim.x, buf ^ 1);
-                ++loaded;
-            }
-            // the tile has landed; the group exponents of buffer buf are free
-            // once the epilogue of tile it - 2 released its accumulators
-            bool ok = mbar_wait(&bar[4 + buf], uint32_t((it / 2) & 1), abort_flag, &g_tcz_error) &&
-                      (it < 2 || mbar_wait(&bar[2 + buf], uint32_t((it / 2 - 1) & 1), abort_flag, &g_tcz_error));
+            const int s = it % kZStages, buf = it & 1;
+            bool ok = !fail && mbar_wait(&bar[kZBarFull + s], uint32_t((it / kZStages) & 1), abort_flag, &g_tcz_error);
             uint32_t hw[2 * kZH], lw[2 * kZH];
             int pmax = 0;
             if (ok) {
-                const double2 *x = reinterpret_cast<const double2 *>(smem + kZOffTile + buf * kZTileBytes) + ibase;
+                const double2 *x = reinterpret_cast<const double2 *>(smem + kZOffTile + s * kZTileBytes);
 #pragma unroll
                 for (int c = 0; c < kZH; ++c) {
-                    const double2 v = x[g.toff[kZH * h + c]];
+                    const double2 v = x[soff[c]];
                     hw[2 * c] = uint32_t(__double2hiint(v.x));
                     lw[2 * c] = uint32_t(__double2loint(v.x));
                     hw[2 * c + 1] = uint32_t(__double2hiint(v.y));
                     lw[2 * c + 1] = uint32_t(__double2loint(v.y));
                     pmax = max(pmax, max(dexp(hw[2 * c]), dexp(hw[2 * c + 1])));
                 }
+                mbar_arrive(&bar[kZBarTileFree + s]);  // the stage may be refilled
             }
-            // the two halves of a group swap their largest exponents
-            part[h * NP + n] = pmax;
-            named_bar_sync(3, kZProd);
-            const int emax = max(part[n], part[NP + n]);
-            if (h == 0) gexp[buf * NP + n] = emax;
-            uint32_t hv[kZSlices][kZH];
-            if (ok) {
+            // the two halves of a group swap their largest exponents; every
+            // producer takes the same exit decision here
+            int *pt = part + (it & 1) * 2 * NP;
+            pt[h * NP + n] = pmax;
+            if (named_bar_or(3, kZProd, !ok || *abort_flag)) break;
+            const int emax = max(pt[n], pt[NP + n]);
+            // the group exponents of buffer buf are free once the epilogue of
+            // tile it - 2 released its accumulators
+            ok = it < 2 || mbar_wait(&bar[kZBarAccFree + buf], uint32_t((it / 2 - 1) & 1), abort_flag, &g_tcz_error);
+            if (ok && h == 0) gexp[buf * NP + n] = emax;
+            // digits of the first four amplitudes before the wait for the
+            // previous tile's MMAs, of the other four after it
+            uint32_t hv[kZSlices][4];
+            auto cut = [&](int c0) {
 #pragma unroll
-                for (int c = 0; c < kZH; ++c) {
-                    const uint64_t wr = centered(hw[2 * c], lw[2 * c], emax);
-                    const uint64_t wi = centered(hw[2 * c + 1], lw[2 * c + 1], emax);
+                for (int c = 0; c < 4; ++c) {
+                    const uint64_t wr = centered(hw[2 * (c0 + c)], lw[2 * (c0 + c)], emax);
+                    const uint64_t wi = centered(hw[2 * (c0 + c) + 1], lw[2 * (c0 + c) + 1], emax);
+                    uint32_t S, K;
+                    digit_signs(hw[2 * (c0 + c)], hw[2 * (c0 + c) + 1], S, K);
                     const uint32_t rl = uint32_t(wr), rh = uint32_t(wr >> 32);
                     const uint32_t il = uint32_t(wi), ih = uint32_t(wi >> 32);
                     // slice i holds the digit of weight 2^(8 (5 - i)): byte 5 - i of W, W >> 40 for i = 0
-                    hv[0][c] = top_digit_pair(rh, ih);
-                    hv[1][c] = digit_pair<0>(rh, ih);
-                    hv[2][c] = digit_pair<3>(rl, il);
-                    hv[3][c] = digit_pair<2>(rl, il);
-                    hv[4][c] = digit_pair<1>(rl, il);
-                    hv[5][c] = digit_pair<0>(rl, il);
+                    hv[0][c] = top_digit_pair(rh, ih, S, K);
+                    hv[1][c] = digit_pair<0>(rh, ih, S, K);
+                    hv[2][c] = digit_pair<3>(rl, il, S, K);
+                    hv[3][c] = digit_pair<2>(rl, il, S, K);
+                    hv[4][c] = digit_pair<1>(rl, il, S, K);
+                    hv[5][c] = digit_pair<0>(rl, il, S, K);
                 }
-            }
-            // the A slices are free once the MMAs of tile it - 1 are done
-            ok = ok && (it < 1 || mbar_wait(&bar[buf ^ 1], uint32_t(((it - 1) / 2) & 1), abort_flag, &g_tcz_error));
+            };
+            const uint32_t a0 = tmem + lane_off + uint32_t(kZH * h);
+            if (ok) cut(0);
+            // this half's A columns (K step h) are free once the MMAs of tile
+            // it - 1 that read them are done: the first K step's are committed
+            // on their own, the second K step's with the whole tile
+            ok = ok && (it < 1 || (h == 0 ? mbar_wait(&bar[kZBarAFree0], uint32_t((it - 1) & 1), abort_flag, &g_tcz_error)
+                                          : mbar_wait(&bar[buf ^ 1], uint32_t(((it - 1) / 2) & 1), abort_flag,
+                                                      &g_tcz_error)));
             if (ok) {
-                const uint32_t a0 = tmem + lane_off + uint32_t(kZH * h);
 #pragma unroll
-                for (int i = 0; i < kZSlices; ++i) tmem_st_x8(a0 + uint32_t(16 * i), hv[i]);
+                for (int i = 0; i < kZSlices; ++i) tmem_st_x4(a0 + uint32_t(16 * i), hv[i]);
+                cut(4);
+#pragma unroll
+                for (int i = 0; i < kZSlices; ++i) tmem_st_x4(a0 + uint32_t(16 * i + 4), hv[i]);
                 tmem_wait_st();
+                tc_fence_before();
+                mbar_arrive(&bar[kZBarAFull]);
             }
-            tc_fence_before();
-            // every producer takes the same exit decision
-            if (named_bar_or(2, kZProd, !ok || *abort_flag)) break;
-            if (tid == 0) {
-                __threadfence_block();  // the group exponents before the MMAs the epilogue waits for
-                tc_fence_after();
-                constexpr uint32_t sbo = kZD2 * 16;
-#pragma unroll
-                for (int l = 0; l < kZSlices; ++l) {
-                    const uint32_t acc = tmem + kZAccCol + uint32_t(buf) * kZAccCols + uint32_t(32 * l);
-#pragma unroll
-                    for (int i = 0; i <= l; ++i) {
-                        const int j = l - i;
-                        const uint32_t bj = smem_base + uint32_t(j * kZBSliceBytes);
-#pragma unroll
-                        for (int ks = 0; ks < kZD2 / 16; ++ks)
-                            mma_ts(acc, tmem + uint32_t(16 * i + 8 * ks), smem_desc(bj + uint32_t(ks) * 256u, 128, sbo),
-                                   idesc, (i > 0 || ks > 0) ? 1u : 0u);
-                    }
-                }
-                mma_commit(&bar[buf]);
-            }
-            ++issued;
+            fail = !ok;
         }
-        // no bulk copy may land after the CTA exits, and the last commit of
-        // each buffer must land before TMEM is freed
-        if (tid == 0) {
-            volatile int no_abort = 0;
-            for (int b = 0; b < 2; ++b) {
-                const int cnt = (loaded + 1 - b) / 2;
-                if (cnt > 0) mbar_wait(&bar[4 + b], uint32_t((cnt - 1) & 1), &no_abort, &g_tcz_error);
-            }
-            for (int b = 0; b < 2; ++b) {
-                const int cnt = (issued + 1 - b) / 2;
-                if (cnt > 0) mbar_wait(&bar[b], uint32_t((cnt - 1) & 1), &no_abort, &g_tcz_error);
-            }
-        }
-    } else {
+    } else if (warp < kZCtrlWarp) {
         // ---------------- epilogue ----------------
         int it = 0;
         for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
@@ -339,10 +343,86 @@ __global__ void __launch_bounds__(kZThreads, 1) k_tcz(const TczParams p, double2
                 tmem_wait_ld();
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    gdst[g.goff[kZH * h + 4 * q + c]] = make_double2(join_levels(v, 2 * c, x), join_levels(v, 2 * c + 1, x));
+                    gdst[g.goff[kZH * h + 4 * q + c]] = make_double2(join_levels(v, 2 * c, x, p.w8, p.w16, p.w24),
+                                                                   join_levels(v, 2 * c + 1, x, p.w8, p.w16, p.w24));
             }
             tc_fence_before();
-            mbar_arrive(&bar[2 + buf]);
+            mbar_arrive(&bar[kZBarAccFree + buf]);
+        }
+    } else {
+        // ---------------- tile copies and MMA issue ----------------
+        const int lane = tid & 31;
+        // copies tile t into stage sb, one bulk copy per contiguous run
+        auto load_tile = [&](int64_t t, int sb) {
+            uint64_t *fb = &bar[kZBarFull + sb];
+            const uint32_t dst = smem_base + kZOffTile + uint32_t(sb * kZTileBytes);
+            fence_proxy_async();
+            if (lane == 0) mbar_expect_tx(fb, uint32_t(kZTileBytes));
+            __syncwarp();
+            const int nruns = 1 << (g.L - g.c);
+            const uint32_t run_bytes = uint32_t(16) << g.c;
+            const double2 *src = state + tile_base(g, t);
+            for (int j = lane; j < nruns; j += 32) bulk_g2s(dst + uint32_t(j) * run_bytes, src + g.runoff[j], run_bytes, fb);
+        };
+        // the B slices as one K-major operand of 6 x 32 rows, per K step
+        uint64_t bdesc[2];
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) bdesc[ks] = smem_desc(smem_base + uint32_t(ks * 256), 128, kZD2 * 16);
+        int loaded = 0, issued = 0, it = 0;
+        for (; loaded < kZStages && int64_t(blockIdx.x) + int64_t(loaded) * gridDim.x < g.total_tiles; ++loaded)
+            load_tile(int64_t(blockIdx.x) + int64_t(loaded) * gridDim.x, loaded);
+        for (int64_t t = blockIdx.x; t < g.total_tiles; t += gridDim.x, ++it) {
+            const int s = it % kZStages, buf = it & 1;
+            // stage s takes tile it + stages once the producers have read tile it
+            const int64_t tn = t + int64_t(kZStages) * gridDim.x;
+            if (tn < g.total_tiles) {
+                if (!__all_sync(0xffffffffu, mbar_wait(&bar[kZBarTileFree + s], uint32_t((it / kZStages) & 1),
+                                                       abort_flag, &g_tcz_error)))
+                    break;
+                load_tile(tn, s);
+                ++loaded;
+            }
+            // the producers have written tile it's A slices, and accumulator
+            // buffer buf is free once the epilogue of tile it - 2 released it
+            const bool ready =
+                mbar_wait(&bar[kZBarAFull], uint32_t(it & 1), abort_flag, &g_tcz_error) &&
+                (it < 2 || mbar_wait(&bar[kZBarAccFree + buf], uint32_t((it / 2 - 1) & 1), abort_flag, &g_tcz_error));
+            if (!__all_sync(0xffffffffu, ready)) break;
+            if (lane == 0) {
+                __threadfence_block();  // the group exponents before the MMAs the epilogue waits for
+                tc_fence_after();
+                // per K step, A slice i against the B slices 0 .. 5 - i side by
+                // side (N = 32 (6 - i): the slices are consecutive 32-row
+                // groups of one K-major operand) into the levels i .. 5 (the
+                // level accumulators are consecutive 32-column groups); the
+                // first product of the tile starts every level
+                const uint32_t acc = tmem + kZAccCol + uint32_t(buf) * kZAccCols;
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+#pragma unroll
+                    for (int i = 0; i < kZSlices; ++i)
+                        mma_ts(acc + uint32_t(32 * i), tmem + uint32_t(16 * i + 8 * ks), bdesc[ks],
+                               instr_desc(kTcGroups, kZD2 * (kZSlices - i), false), (i > 0 || ks > 0) ? 1u : 0u);
+                    if (ks == 0) mma_commit(&bar[kZBarAFree0]);
+                }
+                mma_commit(&bar[buf]);
+            }
+            __syncwarp();
+            ++issued;
+        }
+        // no bulk copy may land after the CTA exits, and the last commit of
+        // each buffer must land before TMEM is freed
+        if (lane == 0) {
+            volatile int no_abort = 0;
+            for (int sb = 0; sb < kZStages; ++sb) {
+                const int cnt = (loaded - sb + kZStages - 1) / kZStages;  // copies into stage sb
+                if (cnt > 0) mbar_wait(&bar[kZBarFull + sb], uint32_t((cnt - 1) & 1), &no_abort, &g_tcz_error);
+            }
+            for (int b = 0; b < 2; ++b) {
+                const int cnt = (issued + 1 - b) / 2;
+                if (cnt > 0) mbar_wait(&bar[b], uint32_t((cnt - 1) & 1), &no_abort, &g_tcz_error);
+            }
+            if (issued > 0) mbar_wait(&bar[kZBarAFree0], uint32_t((issued - 1) & 1), &no_abort, &g_tcz_error);
         }
     }
     tc_fence_before();
@@ -435,13 +515,16 @@ hq_status launch_tcz_block(void *state, int n, int k, const int *qubits, const d
     make_geom(p.g, n, 4, qs, 11, nstates);
     std::vector<uint16_t> bh;
     p.eb = prepare_bz(mat, bh);
+    p.w8 = 1u << 8;
+    p.w16 = 1u << 16;
+    p.w24 = 1u << 24;
     const size_t bytes = bh.size() * sizeof(uint16_t);
     char *dmat = nullptr;
     if (injected_alloc_failure() || cudaMallocAsync((void **)&dmat, bytes, s) != cudaSuccess) return HQ_ERR_ALLOC;
     hq_status st = upload_async(dmat, bh.data(), bytes, s);
     if (st == HQ_OK) {
         p.bmat = reinterpret_cast<const uint4 *>(dmat);
-        // padded so that two CTAs never share an SM (each holds all 512 TMEM columns)
+        // more than half of an SM's shared memory: two CTAs never share an SM (each holds all 512 TMEM columns)
         const size_t smem = std::max<size_t>(kZBytes, 228 * 1024 / 2 + 1024);
         const void *fn = (const void *)k_tcz;
         const int per_sm = std::min(occupancy(fn, kZThreads, smem), 1);
