@@ -549,8 +549,9 @@ def measure_c128(args, circ):
 def measure_n28_vs_oracle(args):
     """Relative L2 error against the oracle (complex128, gate by gate) of the
     n=28 subset of the 33-qubit layout (942 gates), for every complex64 engine
-    on the fused k <= 6 blocks, and max-abs error of the complex128 per-gate
-    path; the oracle state is computed on the host cores (~80 s)."""
+    on the fused k <= 6 blocks, and max-abs error of the complex128 paths
+    (per gate; fused k <= 4 in double-float and on the tensor cores); the
+    oracle state is computed on the host cores (~80 s)."""
     import torch
     import oracle
     from paper_2111_06868_gb300 import hq
@@ -572,13 +573,18 @@ def measure_n28_vs_oracle(args):
     hq.hq_state_init(st)
     hq.hq_apply_blocks(st, c28.gates)
     c128 = float(np.abs(st.cpu().numpy() - want).max())
+    b4 = fuse(hq, 28, c28.gates, 4, args)
     hq.hq_state_init(st)
-    hq.hq_apply_blocks(st, fuse(hq, 28, c28.gates, 4, args), engine="df")
+    hq.hq_apply_blocks(st, b4, engine="df")
     c128_df = float(np.abs(st.cpu().numpy() - want).max())
+    hq.hq_state_init(st)
+    hq.hq_apply_blocks(st, b4, engine="tc_c128")
+    c128_tc = float(np.abs(st.cpu().numpy() - want).max())
     del st
     torch.cuda.empty_cache()
     return {"gates": len(c28.gates), "blocks_k6": len(b28), "rel_l2": errs, "bar_rel_l2": 2e-5,
-            "c128_per_gate_max_abs": c128, "c128_df_fused_k4_max_abs": c128_df, "bar_max_abs": 1e-12,
+            "c128_per_gate_max_abs": c128, "c128_df_fused_k4_max_abs": c128_df,
+            "c128_tc_c128_fused_k4_max_abs": c128_tc, "bar_max_abs": 1e-12,
             "oracle_s": t_or, "oracle_threads": oracle.max_threads()}
 
 
