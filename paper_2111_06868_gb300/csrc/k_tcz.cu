@@ -134,8 +134,8 @@ __device__ __forceinline__ int dexp(uint32_t hi) { return int((hi >> 20) & 0x7FF
 __device__ __forceinline__ uint64_t centered(uint32_t hi, uint32_t lo, int emax)
 {
     const int e = dexp(hi);
-    const uint64_t m = e ? ((uint64_t((hi & 0xFFFFFu) | 0x100000u) << 32) | lo) : 0;
-    const int t = min(emax - e + 5, 63);
+    const uint64_t m = (uint64_t((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+    const int t = e ? min(emax - e + 5, 63) : 63;  // m >> 63 = 0: zeros and subnormals
     return kZCenter + (((m >> t) + 1) >> 1);  // round half up
 }
 
@@ -193,12 +193,13 @@ __device__ __forceinline__ double join_levels(const uint32_t (&v)[kZSlices][8], 
     uint32_t b[kZSlices];
 #pragma unroll
     for (int l = 0; l < kZSlices; ++l) b[l] = __float_as_uint(__uint_as_float(v[l][col]) + 12582912.0f);
-    const uint64_t lo = mad_wide(b[2], w24, mad_wide(b[3], w16, mad_wide(b[4], w8, uint64_t(b[5]))));
-    const uint32_t hi = b[0] * w8 + b[1];
-    const int64_t w = int64_t(lo + (uint64_t(hi) << 32) - kZBias);
+    // the offsets enter the chain as its start (b_5 - bias, modulo 2^64)
+    const uint64_t lo = mad_wide(b[2], w24, mad_wide(b[3], w16, mad_wide(b[4], w8, mad_wide(b[5], 1u, 0ull - kZBias))));
+    const uint32_t hi = b[0] * w8 + b[1] + uint32_t(lo >> 32);  // levels 0 and 1 go to the high word
+    const int64_t w = int64_t((uint64_t(hi) << 32) | uint32_t(lo));
     const int64_t bits = __double_as_longlong(__ll2double_rn(w));
-    const int e = int((bits >> 52) & 0x7FF);
-    return (w == 0 || e + x <= 0) ? 0.0 : __longlong_as_double(bits + (int64_t(x) << 52));
+    const int e = int((bits >> 52) & 0x7FF);  // 0 only for w = 0
+    return (e == 0 || e + x <= 0) ? 0.0 : __longlong_as_double(bits + (int64_t(x) << 52));
 }
 
 __global__ void __launch_bounds__(kZThreads, 1) k_tcz(const TczParams p, double2 *__restrict__ state)
