@@ -1095,7 +1095,10 @@ def main():
     if rank == 0:
         # bytes a step moves: the first tensor-core block only writes (its input
         # is computed from the tokens), the last sums the norm as it writes
-        first_tc, last_tc = classes[0].startswith("k_tc"), classes[-1].startswith("k_tc")
+        first_tc = classes[0].startswith("k_tc")
+        # hq_simulate runs a structured last block of 4..6 qubits on k_tc too, to fold the norm in
+        last_tc = classes[-1].startswith("k_tc") or (engine in ("tc_f16", "tc_bf16") and n >= 13 and
+                                                     4 <= len(blocks[-1][0]) <= 6)
         passes_rw = 2 * B - (1 if first_tc else -1) + (0 if last_tc else 1)
         eff_gbs = passes_rw * (bytes_per_launch // 2) * args.steps / (elapsed / world) / 1e9
         rec = {

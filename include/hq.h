@@ -455,8 +455,11 @@ hq_status hq_apply_blocks(void *state, int n, hq_dtype dt, const hq_gate *gates,
  * sums |psi_x|^2 of what it writes (FP32 within a tile, in chains of at
  * most 16 squares, FP64 across tiles, the per-warp sums added on the host in
  * a fixed order: within 1e-8 relative of the exact sum of the stored
- * amplitudes).  Other engines
- * and blocks run the separate passes.
+ * amplitudes).  With norm2_host set, a last block of 4..6 qubits that a
+ * structured kernel would take (diagonal, monomial, controlled) runs on the
+ * tensor cores as well, so that it sums the norm: its result then carries
+ * the split-precision rounding instead of being exact in FP32.  Other
+ * engines and blocks run the separate passes.
  *   state: out, 2^n amplitudes (DEVICE, caller-owned, 16-byte aligned); its
  *          previous contents are never read.
  *   norm2_host: out (may be NULL); when set the call SYNCHRONISES `stream`

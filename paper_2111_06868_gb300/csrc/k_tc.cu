@@ -846,6 +846,7 @@ struct TcListExtras {
     float init_amp = 0.f;
     uint64_t init_fixed = 0, init_val = 0, init_minus = 0;
     bool norm_last = false;
+    bool force_last = false;  // the last block runs on k_tc even if a structured kernel would take it
     std::vector<double> *norm_slots = nullptr;  // out (host): the epilogue warps' partial sums
 };
 
@@ -853,11 +854,14 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
                                 int64_t nstates, cudaStream_t s, const TcListExtras *ex = nullptr)
 {
     constexpr int kFirstChunk = 1, kChunk = 4;
+    auto eligible = [&](int g) {
+        return tc_eligible(n, gates[g], tc_min_k) || (ex && ex->force_last && g == G - 1);
+    };
     size_t bytes = 0;
     for (int g = 0; g < G; ++g)
-        if (tc_eligible(n, gates[g], tc_min_k)) bytes += tc_matrix_bytes(n >= 13 ? 6 : gates[g].k);
+        if (eligible(g)) bytes += tc_matrix_bytes(n >= 13 ? 6 : gates[g].k);
     // norm partials after the matrices: one slot per epilogue warp of every CTA
-    const bool norm = ex && ex->norm_last && G > 0 && n >= 13 && tc_eligible(n, gates[G - 1], tc_min_k);
+    const bool norm = ex && ex->norm_last && G > 0 && n >= 13 && eligible(G - 1);
     const size_t norm_off = bytes, norm_slots = size_t(sm_count()) * 4 * 8;
     if (norm) bytes += norm_slots * sizeof(double);
     char *dmat = nullptr;
@@ -878,7 +882,7 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
         host.clear();
         for (int g = g0; g < g1; ++g) {
             const hq_gate &gt = gates[g];
-            if (!tc_eligible(n, gt, tc_min_k)) continue;
+            if (!eligible(g)) continue;
             TcPrepared &b = prep[size_t(g - g0)];
             if (gt.k < 6 && n >= 13) {
                 hq_gate w;
@@ -909,7 +913,7 @@ static hq_status launch_tc_list(void *state, int n, const hq_gate *gates, int G,
         }
         for (int g = g0; g < g1 && st == HQ_OK; ++g) {
             const hq_gate &gt = gates[g];
-            if (!tc_eligible(n, gt, tc_min_k)) {
+            if (!eligible(g)) {
                 st = launch_gate(state, n, HQ_C64, gt.k, gt.qubits, gt.matrix, nstates, HQ_ENGINE_AUTO, s);
                 continue;
             }
@@ -954,13 +958,16 @@ hq_status launch_tc_simulate(void *state, int n, const char *tokens, const hq_ga
     // only the 6-qubit kernels (every tensor-core block when n >= 13) fold them in
     ex.synth_first = G > 0 && n >= 13 && tc_eligible(n, gates[0], tc_min_k);
     ex.norm_last = norm2_host != nullptr;
+    // a structured last block of 4..6 qubits (diagonal, monomial, controlled)
+    // runs on k_tc too, so that its epilogue sums the norm (one pass less)
+    ex.force_last = norm2_host && G > 0 && n >= 13 && gates[G - 1].k >= 4 && gates[G - 1].k <= 6;
     std::vector<double> slots;
     ex.norm_slots = &slots;
     hq_status st = HQ_OK;
     if (!ex.synth_first && (st = launch_init(state, n, HQ_C64, tokens, 1, s)) != HQ_OK) return st;
     if ((st = launch_tc_list(state, n, gates, G, tc_min_k, split_bf16, 1, s, &ex)) != HQ_OK) return st;
     if (!norm2_host) return HQ_OK;
-    const bool fused_norm = G > 0 && n >= 13 && tc_eligible(n, gates[G - 1], tc_min_k);
+    const bool fused_norm = G > 0 && n >= 13 && (tc_eligible(n, gates[G - 1], tc_min_k) || ex.force_last);
     if (!fused_norm) {
         hq_pauli_term id;
         std::memset(&id, 0, sizeof(id));

@@ -109,6 +109,43 @@ def test_simulate_with_blocks_off_the_tensor_cores(hq, where):
     assert rel_l2(a.cpu().numpy().astype(np.complex128), oracle.simulate(circ, tokens=tokens)) <= 2e-5
 
 
+def _monomial_4q(seed):
+    """A 4-qubit permutation with phases (one nonzero per row and column)."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(16)
+    m = np.zeros((16, 16), np.complex128)
+    m[np.arange(16), perm] = np.exp(1j * rng.uniform(0, 2 * np.pi, 16))
+    return m
+
+
+def test_simulate_folds_the_norm_into_a_structured_last_block(hq):
+    """A last block that the monomial kernel would take runs on the tensor
+    cores inside hq_simulate so that its epilogue sums the norm: the state
+    meets the oracle within the complex64 bar and the separate passes (exact
+    monomial kernel) within split-precision rounding; the norm is that of
+    the stored state."""
+    n = 14
+    circ, blocks = grid_blocks(hq, n, 6, seed=9)
+    qs = (1, 4, 7, 11)
+    m = _monomial_4q(9)
+    s, _, _ = hq.hq_gate_structure(m)
+    assert s & 2  # monomial
+    blocks = blocks + [(qs, m)]
+    circ = C.Circuit(n, circ.gates + [C.Gate("P", qs, m)])
+    tokens = "+-" * 7
+    a = torch.empty(1 << n, dtype=torch.complex64, device="cuda")
+    nrm = hq.hq_simulate(a, blocks, tokens=tokens, engine="tc_f16", tc_min_k=4)
+    b = torch.empty_like(a)
+    hq.hq_state_init(b, tokens)
+    hq.hq_apply_blocks(b, blocks, engine="tc_f16", tc_min_k=4)
+    got = a.cpu().numpy().astype(np.complex128)
+    sep = b.cpu().numpy().astype(np.complex128)
+    assert rel_l2(got, oracle.simulate(circ, tokens=tokens)) <= 2e-5
+    assert rel_l2(got, sep) <= 1e-6
+    assert abs(nrm - oracle.norm2(got)) <= 1e-8 * oracle.norm2(got)
+    assert abs(nrm - 1.0) <= 4e-5
+
+
 @pytest.mark.parametrize("dtype,engine,tol", [(torch.complex128, "auto", 1e-12), (torch.complex128, "df", 1e-12),
                                               (torch.complex64, "auto", 2e-5), (torch.complex64, "cuda_core", 2e-5)])
 def test_simulate_other_engines(hq, dtype, engine, tol):
