@@ -413,11 +413,61 @@ __device__ __forceinline__ void tiles_pipelined(const TileGeom &g, float2 *__res
     cp_async_wait<0>();
 }
 
+// K = 4 in complex64: as gather_tile's chunked form, with the matrix read
+// from shared memory (every lane of a warp reads the same entry: a
+// broadcast) at a row offset known only at run time, so that one copy of the
+// unrolled 4 x 16 multiply-add body serves all four row chunks (four
+// constant-operand copies of it did not stay in the instruction cache).
+// (Packed FMAs with the entries stored as (Re, Re, -Im, Im) took 20 % longer:
+// one 16-byte shared load per complex multiply-add.)
+template <int LB>
+__device__ __forceinline__ void gather_tile_k4_sh(const TileGeom &g, const float2 (*msh)[16], float2 *tile)
+{
+    constexpr int K = 4, NR = gather_rows<float, K>(), TPG = gather_tpg<float, K>(), NI = gather_items<float, K, LB>();
+    const int ngroups = (1 << g.L) >> K;
+    float2 acc[NI][NR];
+    int ibs[NI], chunk[NI];
+#pragma unroll
+    for (int it = 0; it < NI; ++it) {
+        const int w = it * kThreads + threadIdx.x;
+        const int wi = w >> 5;
+        chunk[it] = wi % TPG;
+        const int grp = (wi / TPG) * 32 + (w & 31);
+        ibs[it] = -1;
+#pragma unroll
+        for (int rr = 0; rr < NR; ++rr) acc[it][rr].x = acc[it][rr].y = 0;
+        if (grp < ngroups) {
+            ibs[it] = group_base<K>(g, grp);
+            const float2 (*mr)[16] = msh + chunk[it] * NR;
+#pragma unroll
+            for (int c = 0; c < (1 << K); ++c) {
+                const float2 v = tile[swz<float>(ibs[it] + g.toff[c])];
+#pragma unroll
+                for (int rr = 0; rr < NR; ++rr) cmac(acc[it][rr], mr[rr][c], v);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < NI; ++it)
+        if (ibs[it] >= 0)
+#pragma unroll
+            for (int rr = 0; rr < NR; ++rr) tile[swz<float>(ibs[it] + g.toff[chunk[it] * NR + rr])] = acc[it][rr];
+    __syncthreads();
+}
+
 template <int K>
 __global__ void __launch_bounds__(kThreads) k_gather_pipe(const TileGeom g, const MatParam<float, K> m,
                                                           float2 *__restrict__ state)
 {
-    tiles_pipelined(g, state, [&](float2 *tile) { gather_tile<float, K, gather_pipe_tile_bits<K>()>(g, m, tile); });
+    if constexpr (K == 4) {
+        __shared__ float2 msh[16][16];
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) msh[i >> 4][i & 15] = m.a[i >> 4][i & 15];
+        // (tiles_pipelined's first barrier orders these stores before the reads)
+        tiles_pipelined(g, state, [&](float2 *tile) { gather_tile_k4_sh<gather_pipe_tile_bits<K>()>(g, msh, tile); });
+    } else {
+        tiles_pipelined(g, state, [&](float2 *tile) { gather_tile<float, K, gather_pipe_tile_bits<K>()>(g, m, tile); });
+    }
 }
 
 // ----------------------------------------------------------------------------
