@@ -9,7 +9,10 @@
 //     picked on the device from k_rdm's partial sums and a caller-drawn
 //     uniform, and the renormalised Kraus operator applied, with no host
 //     round trip.
-// Partial sums are FP64 per CTA and joined by one CTA in a fixed order.
+// Each thread sums its share of a complex64 state in FP32 with a compensation
+// term (complex128 in FP64), the CTA sums in FP64; one CTA joins the CTAs'
+// sums in a fixed order.  At most two CTAs per SM, so that few partial
+// sums reach that join.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -38,9 +41,21 @@ __global__ void __launch_bounds__(kNoiseThreads) k_rdm(const RdmParam<R, K> p, c
 {
     using T2 = typename C2<R>::type;
     constexpr int D = 1 << K, NE = rdm_entries<K>();
-    double ar[NE], ai[NE];
+    // per-thread sums in R; in FP32 each carries a compensation term (Kahan),
+    // so that the FP64 pipe is used once per thread, not once per chunk
+    R ar[NE], ai[NE], cr[NE], ci[NE];
 #pragma unroll
-    for (int e = 0; e < NE; ++e) ar[e] = ai[e] = 0;
+    for (int e = 0; e < NE; ++e) ar[e] = ai[e] = cr[e] = ci[e] = 0;
+    auto add = [](R &sum, R &comp, R x) {
+        if constexpr (sizeof(R) == 4) {
+            const R y = x - comp;
+            const R t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        } else {
+            sum += x;
+        }
+    };
     const int64_t stride = int64_t(gridDim.x) * blockDim.x * kRdmUnroll;
     for (int64_t f0 = int64_t(blockIdx.x) * blockDim.x * kRdmUnroll + threadIdx.x; f0 < groups; f0 += stride) {
         T2 v[kRdmUnroll][D];
@@ -73,14 +88,14 @@ __global__ void __launch_bounds__(kNoiseThreads) k_rdm(const RdmParam<R, K> p, c
                     sr += v[u][a].x * v[u][b].x + v[u][a].y * v[u][b].y;
                     si += v[u][a].y * v[u][b].x - v[u][a].x * v[u][b].y;
                 }
-                ar[e] += double(sr);
-                ai[e] += double(si);
+                add(ar[e], cr[e], sr);
+                add(ai[e], ci[e], si);
             }
     }
 #pragma unroll
     for (int e = 0; e < NE; ++e) {
-        const double sr = block_sum(ar[e]);
-        const double si = block_sum(ai[e]);
+        const double sr = block_sum(double(ar[e]) - double(cr[e]));
+        const double si = block_sum(double(ai[e]) - double(ci[e]));
         if (threadIdx.x == 0) {
             partials[(int64_t(blockIdx.x) * NE + e) * 2] = sr;
             partials[(int64_t(blockIdx.x) * NE + e) * 2 + 1] = si;
@@ -117,10 +132,13 @@ template <typename R, int K> static RdmParam<R, K> rdm_param(int n, const int *q
     return p;
 }
 
+// at most two CTAs per SM: enough loads in flight for HBM, and few partial
+// sums for the one-CTA pass that joins them
 template <typename R, int K> static int rdm_grid(int n)
 {
     const int64_t per_cta = int64_t(kNoiseThreads) * kRdmUnroll;
-    return grid_for((const void *)k_rdm<R, K>, kNoiseThreads, 0, ((int64_t(1) << (n - K)) + per_cta - 1) / per_cta);
+    return int(std::min<int64_t>(2 * sm_count(), grid_for((const void *)k_rdm<R, K>, kNoiseThreads, 0,
+                                                          ((int64_t(1) << (n - K)) + per_cta - 1) / per_cta)));
 }
 
 // per-CTA partial sums (rdm_grid<R, K>(n) rows of 2 * rdm_entries<K>() doubles)
@@ -199,59 +217,99 @@ struct PickArgs {
     int *status;      // set to 1 when every p_i is 0
 };
 
+// D = 2^K: the thread-0 part below works on arrays of fixed size (in
+// registers, loops unrolled)
+template <int D>
 __global__ void __launch_bounds__(kNoiseThreads) k_kraus_pick(const PickArgs a)
 {
-    __shared__ double tri[2 * rdm_entries<2>()];
-    for (int j = 0; j < a.width; ++j) {
-        double v = 0;
-        for (int i = threadIdx.x; i < a.nparts; i += blockDim.x) v += a.partials[int64_t(i) * a.width + j];
-        const double s = block_sum(v);
-        if (threadIdx.x == 0) tri[j] = s;
+    constexpr int W = 2 * rdm_entries<2>();  // widest partial-sum row
+    __shared__ double tri[W];
+    // the operators, their Gram matrices and the absorbed gates, staged by
+    // the whole CTA (thread 0 then reads shared memory, not global memory)
+    __shared__ double sK[kMaxKraus * 2 * 16], sG[kMaxKraus * 2 * 16], sA[2 * 16];
+    {
+        const int n2 = a.nK * 2 * a.D * a.D;
+        for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+            sK[i] = a.K[i];
+            sG[i] = a.G[i];
+        }
+        for (int i = threadIdx.x; i < 2 * a.D * a.D; i += blockDim.x) sA[i] = a.A[i];
+    }
+    // the columns of the partial sums, by one warp: rows per lane, then a
+    // shuffle tree (GB300's FP64 pipe is slow enough that every FP64 warp
+    // instruction counts: the other warps only stage the matrices)
+    if (threadIdx.x < 32) {
+        double v[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) v[j] = 0;
+        for (int i = threadIdx.x; i < a.nparts; i += 32)
+#pragma unroll
+            for (int j = 0; j < W; ++j)
+                if (j < a.width) v[j] += a.partials[int64_t(i) * a.width + j];
+#pragma unroll
+        for (int j = 0; j < W; ++j)
+            if (j < a.width) {  // the same for every lane
+                double x = v[j];
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (threadIdx.x == 0) tri[j] = x;
+            }
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    const int D = a.D, DD = D * D;
-    double r0r[4][4], r0i[4][4];
+    constexpr int DD = D * D;
+    double r0r[D][D], r0i[D][D];
+#pragma unroll
     for (int x = 0, e = 0; x < D; ++x)
+#pragma unroll
         for (int y = x; y < D; ++y, ++e) {
             r0r[x][y] = r0r[y][x] = tri[2 * e];
             r0i[x][y] = tri[2 * e + 1];
             r0i[y][x] = -tri[2 * e + 1];
         }
     // rho = A rho0 A^dag: T = A rho0, then rho[x][y] = sum_z T[x][z] conj(A[y][z])
-    double tr_[4][4], ti_[4][4], rr[4][4], ri[4][4];
+    double tr_[D][D], ti_[D][D], rr[D][D], ri[D][D];
+#pragma unroll
     for (int x = 0; x < D; ++x)
+#pragma unroll
         for (int y = 0; y < D; ++y) {
             double sr = 0, si = 0;
+#pragma unroll
             for (int z = 0; z < D; ++z) {
-                const double ar = a.A[2 * (x * D + z)], ai = a.A[2 * (x * D + z) + 1];
+                const double ar = sA[2 * (x * D + z)], ai = sA[2 * (x * D + z) + 1];
                 sr += ar * r0r[z][y] - ai * r0i[z][y];
                 si += ar * r0i[z][y] + ai * r0r[z][y];
             }
             tr_[x][y] = sr;
             ti_[x][y] = si;
         }
+#pragma unroll
     for (int x = 0; x < D; ++x)
+#pragma unroll
         for (int y = 0; y < D; ++y) {
             double sr = 0, si = 0;
+#pragma unroll
             for (int z = 0; z < D; ++z) {
-                const double br = a.A[2 * (y * D + z)], bi = -a.A[2 * (y * D + z) + 1];
+                const double br = sA[2 * (y * D + z)], bi = -sA[2 * (y * D + z) + 1];
                 sr += tr_[x][z] * br - ti_[x][z] * bi;
                 si += tr_[x][z] * bi + ti_[x][z] * br;
             }
             rr[x][y] = sr;
             ri[x][y] = si;
         }
-    double p[kMaxKraus], total = 0;
-    for (int i = 0; i < a.nK; ++i) {
-        // p_i = Tr(K rho K^dag) = Tr(rho K^dag K) = sum_rc rho[r][c] G[c][r]
-        const double *G = a.G + size_t(i) * 2 * DD;
+    // p_i = Tr(K rho K^dag) = Tr(rho K^dag K) = sum_rc rho[r][c] G[c][r]
+    // (computed again where it is needed, rather than kept in an array
+    // indexed at run time)
+    auto prob = [&](int i) {
+        const double *G = sG + size_t(i) * 2 * DD;
         double t = 0;
+#pragma unroll
         for (int r = 0; r < D; ++r)
+#pragma unroll
             for (int c = 0; c < D; ++c) t += rr[r][c] * G[2 * (c * D + r)] - ri[r][c] * G[2 * (c * D + r) + 1];
-        p[i] = fmax(t, 0.0);
-        total += p[i];
-    }
+        return fmax(t, 0.0);
+    };
+    double total = 0;
+    for (int i = 0; i < a.nK; ++i) total += prob(i);
     if (!(total > 0)) {
         *a.status = 1;
         *a.chosen = -1;
@@ -262,25 +320,29 @@ __global__ void __launch_bounds__(kNoiseThreads) k_kraus_pick(const PickArgs a)
     // nonzero one if rounding leaves none)
     const double target = *a.u * total;
     int pick = -1;
-    double cum = 0;
+    double cum = 0, ppick = 0;
     for (int i = 0; i < a.nK; ++i) {
-        cum += p[i];
-        if (p[i] > 0) pick = i;
-        if (cum > target && p[i] > 0) {
+        const double pi = prob(i);
+        cum += pi;
+        if (pi > 0) {
             pick = i;
-            break;
+            ppick = pi;
+            if (cum > target) break;
         }
     }
-    const double sc = 1.0 / sqrt(p[pick]);
-    const double *Kp = a.K + size_t(pick) * 2 * DD;
+    const double sc = 1.0 / sqrt(ppick);
+    const double *Kp = sK + size_t(pick) * 2 * DD;
     bool identity = true;
+#pragma unroll
     for (int r = 0; r < D; ++r)
+#pragma unroll
         for (int c = 0; c < D; ++c) {
             // (K_pick A)[r][c] / sqrt(p_pick)
             double mr = 0, mi = 0;
+#pragma unroll
             for (int z = 0; z < D; ++z) {
                 const double kr = Kp[2 * (r * D + z)], ki = Kp[2 * (r * D + z) + 1];
-                const double ar = a.A[2 * (z * D + c)], ai = a.A[2 * (z * D + c) + 1];
+                const double ar = sA[2 * (z * D + c)], ai = sA[2 * (z * D + c) + 1];
                 mr += kr * ar - ki * ai;
                 mi += kr * ai + ki * ar;
             }
@@ -288,7 +350,9 @@ __global__ void __launch_bounds__(kNoiseThreads) k_kraus_pick(const PickArgs a)
             mi *= sc;
             a.sel[2 * (r * D + c)] = mr;
             a.sel[2 * (r * D + c) + 1] = mi;
-            identity = identity && hypot(mr - (r == c ? 1.0 : 0.0), mi) <= 4.0 * 2.220446049250313e-16;
+            // |m - delta| <= 4 eps, compared squared (no hypot on the slow FP64 pipe)
+            const double dr = mr - (r == c ? 1.0 : 0.0);
+            identity = identity && dr * dr + mi * mi <= 16.0 * 2.220446049250313e-16 * 2.220446049250313e-16;
         }
     a.sel[2 * DD] = identity ? 1.0 : 0.0;
     *a.chosen = pick;
@@ -352,11 +416,13 @@ static hq_status sample_on_device(void *state, int n, const int *qubits, PickArg
     a.nparts = rdm_grid<R, K>(n);
     a.width = 2 * rdm_entries<K>();
     a.D = 1 << K;
-    k_kraus_pick<<<1, kNoiseThreads, 0, s>>>(a);
+    k_kraus_pick<1 << K><<<1, kNoiseThreads, 0, s>>>(a);
     if ((st = cuda_status("k_kraus_pick", cudaGetLastError())) != HQ_OK) return st;
     const RdmParam<R, K> p = rdm_param<R, K>(n, qubits);
     const int64_t groups = int64_t(1) << p.free_bits;
-    k_apply_sel<R, K><<<rdm_grid<R, K>(n), kNoiseThreads, 0, s>>>(p, a.sel, (typename C2<R>::type *)state, groups);
+    const int64_t per_cta = int64_t(kNoiseThreads) * kRdmUnroll;
+    const int agrid = grid_for((const void *)k_apply_sel<R, K>, kNoiseThreads, 0, (groups + per_cta - 1) / per_cta);
+    k_apply_sel<R, K><<<agrid, kNoiseThreads, 0, s>>>(p, a.sel, (typename C2<R>::type *)state, groups);
     return cuda_status("k_apply_sel", cudaGetLastError());
 }
 
